@@ -1,0 +1,351 @@
+"""FP64 CPU oracle for the DIA kernel fit of PyTorchDIA (arXiv 2104.13715).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` import this package.  The product library never
+loads it and shares no code with it: the direct loops live in ``dia_oracle.c``
+(compiled here with the system C compiler), the linear algebra is numpy.
+
+Pieces (each cites the passage it follows):
+
+* :func:`model`, :func:`loss_grad`, :func:`pixel_terms` -- the image model
+  (Sec. 2.1, Eq. 2), the noise models (Eq. 5, Eq. 6) and the loss (Eq. 7,
+  Eq. 11 with the Huber rho of Eq. 10 or a Cauchy rho as the Student-t drop-in
+  named in Sec. 2.4), by direct loops in FP64.
+* :func:`gram`, :func:`normal_solve` -- the Bramich (2008) normal equations
+  for the fixed-variance chi^2 (Sec. 1 and Sec. 2.1): A = sum w phi phi^T,
+  b = sum w phi I with phi_p = [R window of p, 1], solved by Cholesky.
+* :func:`newton` -- for the losses that are not quadratic in theta: Newton
+  steps with the exact Hessian sum_p l''(M_p) phi_p phi_p^T (M is linear in
+  theta), Levenberg damping where it is not positive definite, backtracking
+  on the FP64 loss.
+* :func:`diff_image`, :func:`sigma_clip`, :func:`fit_clipped` -- the
+  difference image I - M and the kappa-sigma clipping of B08 (Sec. 2.4,
+  Sec. 4.2).
+
+Conventions: theta = [K row-major over (row offset, column offset), B0];
+``K[a, b]`` multiplies ``R[i - h + a, j - h + b]`` for the target pixel
+(i, j), with h = m // 2, so ``a = b = h`` is the kernel centre and a +1 pixel
+shift of the target in x and y gives a delta at ``a = b = h - 1`` (Sec. 3.4
+test iii).  Only the valid region i, j in [h, N - h) enters the fit.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dia_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_dia_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+RHO = {"gauss": 0, "huber": 1, "cauchy": 2}
+NOISE = {"fixed": 0, "ccd": 1, "emccd": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile ``dia_oracle.c`` into ``_dia_oracle.so`` (plain gcc, OpenMP)."""
+    if not force and os.path.exists(_LIB_PATH) and \
+            os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        up = ctypes.POINTER(ctypes.c_uint8)
+        i = ctypes.c_int
+        lib.oracle_model.argtypes = [dp, i, i, i, i, dp, dp, i]
+        lib.oracle_model.restype = i
+        lib.oracle_pixel_terms.argtypes = [dp, up, dp, dp, i, i, i, i, dp, dp,
+                                           dp, dp, dp, dp]
+        lib.oracle_pixel_terms.restype = i
+        lib.oracle_loss_grad.argtypes = [dp, dp, up, dp, dp, i, i, i, i, dp, dp,
+                                         dp, dp, i]
+        lib.oracle_loss_grad.restype = i
+        lib.oracle_ndata.argtypes = [up, i, i, i, i]
+        lib.oracle_ndata.restype = ctypes.c_longlong
+        _lib = lib
+        return lib
+
+
+@dataclass
+class LossSpec:
+    """Loss choice: rho in {gauss, huber, cauchy}, variance model in
+    {fixed, ccd, emccd} (Eq. 5, Eq. 6), and their constants."""
+    rho: str = "gauss"
+    noise: str = "fixed"
+    sigma0: float = 0.0        # read noise (image units), CCD model
+    gain: float = 1.0          # G (CCD) or G_total (EMCCD)
+    excess: float = 2.0        # EMCCD excess noise factor E (Sec. 2.1)
+    huber_c: float = 1.345     # Huber threshold (Sec. 2.4)
+    var: float = 1.0           # scalar fixed variance when no map is given
+    var_floor: float = 1e-6    # lower clamp of a model-dependent variance
+
+    def params(self) -> np.ndarray:
+        return np.array([RHO[self.rho], NOISE[self.noise], self.sigma0, self.gain,
+                         self.excess, self.huber_c, self.var, self.var_floor],
+                        dtype=np.float64)
+
+
+def _d(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, ctype=ctypes.c_double):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _u8(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _shape(R, m):
+    H, W = R.shape
+    if m < 1 or m % 2 == 0 or m > min(H, W):
+        raise ValueError(f"kernel side m={m} must be odd and <= image side")
+    return H, W
+
+
+def n_params(m: int) -> int:
+    return m * m + 1
+
+
+def ndata(shape, m, mask=None) -> int:
+    """Valid, unmasked pixel count N_data = (N - 2h)^2 without a mask (Sec. 2.1)."""
+    H, W = shape
+    mk = _u8(mask)
+    return int(_load().oracle_ndata(_ptr(mk, ctypes.c_uint8), H, W, W, m))
+
+
+def model(R, theta, m, nthreads: int = 0) -> np.ndarray:
+    """Model image M = R (x) K + B0 over the valid region (Eq. 2)."""
+    R = _d(R)
+    H, W = _shape(R, m)
+    th = _d(theta)
+    h = m // 2
+    out = np.empty((H - 2 * h, W - 2 * h), dtype=np.float64)
+    rc = _load().oracle_model(_ptr(R), H, W, W, m, _ptr(th), _ptr(out), nthreads)
+    if rc:
+        raise ValueError("oracle_model: bad arguments")
+    return out
+
+
+def pixel_terms(I, M, m, spec: LossSpec, mask=None, var=None, flat=None):
+    """Per-pixel (loss, dl/dM, d2l/dM2, z) over the valid region; masked pixels
+    get zero loss and derivatives (z is still reported)."""
+    I = _d(I)
+    H, W = I.shape
+    h = m // 2
+    M = _d(M)
+    assert M.shape == (H - 2 * h, W - 2 * h)
+    outs = [np.empty_like(M) for _ in range(4)]
+    rc = _load().oracle_pixel_terms(_ptr(I), _ptr(_u8(mask), ctypes.c_uint8),
+                                    _ptr(_d(var)), _ptr(_d(flat)), H, W, W, m,
+                                    _ptr(spec.params()), _ptr(M),
+                                    *[_ptr(o) for o in outs])
+    if rc:
+        raise ValueError("oracle_pixel_terms: bad arguments")
+    return tuple(outs)
+
+
+def loss_grad(R, I, m, theta, spec: LossSpec = None, mask=None, var=None, flat=None,
+              nthreads: int = 0):
+    """FP64 loss L(theta) and gradient dL/dtheta (Eq. 7 / Eq. 11, summed over the
+    unmasked valid pixels).  Returns (L, grad[m*m+1])."""
+    spec = spec or LossSpec()
+    R = _d(R)
+    I = _d(I)
+    H, W = _shape(R, m)
+    assert I.shape == R.shape
+    th = _d(theta)
+    assert th.shape == (n_params(m),)
+    loss = np.zeros(1)
+    grad = np.zeros(n_params(m))
+    mk = _u8(mask)
+    vv = _d(var)
+    ff = _d(flat)
+    rc = _load().oracle_loss_grad(_ptr(R), _ptr(I), _ptr(mk, ctypes.c_uint8), _ptr(vv),
+                                  _ptr(ff), H, W, W, m, _ptr(spec.params()), _ptr(th),
+                                  _ptr(loss), _ptr(grad), nthreads)
+    if rc:
+        raise ValueError(f"oracle_loss_grad failed ({rc})")
+    return float(loss[0]), grad
+
+
+def loss(R, I, m, theta, spec: LossSpec = None, mask=None, var=None, flat=None):
+    return loss_grad(R, I, m, theta, spec, mask, var, flat)[0]
+
+
+def _windows(R, m):
+    return np.lib.stride_tricks.sliding_window_view(R, (m, m))
+
+
+def gram(R, m, weights, rhs=None, block_rows: int = 64):
+    """A = sum_p w_p phi_p phi_p^T and (optionally) b = sum_p rhs_p phi_p, where
+    phi_p = [R window of valid pixel p (m*m, row-major), 1].  ``weights`` and
+    ``rhs`` are arrays over the valid region.  This is the B08 normal matrix
+    when w = 1/sigma^2 and rhs = I/sigma^2 (Sec. 1)."""
+    R = _d(R)
+    H, W = _shape(R, m)
+    h = m // 2
+    Hv, Wv = H - 2 * h, W - 2 * h
+    n = n_params(m)
+    win = _windows(R, m)
+    A = np.zeros((n, n))
+    b = np.zeros(n) if rhs is not None else None
+    for y0 in range(0, Hv, block_rows):
+        y1 = min(Hv, y0 + block_rows)
+        phi = np.empty(((y1 - y0) * Wv, n))
+        phi[:, : n - 1] = win[y0:y1].reshape(-1, m * m)
+        phi[:, n - 1] = 1.0
+        w = np.asarray(weights[y0:y1], dtype=np.float64).reshape(-1)
+        A += (phi * w[:, None]).T @ phi
+        if rhs is not None:
+            b += phi.T @ np.asarray(rhs[y0:y1], dtype=np.float64).reshape(-1)
+    return (A, b) if rhs is not None else A
+
+
+class Degenerate(RuntimeError):
+    """The normal matrix / Hessian is singular (e.g. constant R, all masked)."""
+
+
+def _valid(a, m):
+    h = m // 2
+    return a[h:a.shape[0] - h, h:a.shape[1] - h]
+
+
+def normal_solve(R, I, m, mask=None, var=None, var_scalar: float = 1.0):
+    """B08 linear least squares for the fixed-variance chi^2: solve A theta = b
+    by Cholesky (Sec. 1; Sec. 2.1 'fixed estimates for sigma')."""
+    R = _d(R)
+    I = _d(I)
+    H, W = _shape(R, m)
+    Iv = _valid(I, m)
+    w = np.ones_like(Iv) / var_scalar if var is None else 1.0 / _valid(_d(var), m)
+    if mask is not None:
+        w = w * (_valid(np.asarray(mask), m) != 0)
+    A, b = gram(R, m, w, w * Iv)
+    try:
+        L = np.linalg.cholesky(A)
+    except np.linalg.LinAlgError as e:
+        raise Degenerate(str(e))
+    y = np.linalg.solve(L, b)
+    return np.linalg.solve(L.T, y)
+
+
+def hessian(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None):
+    """Exact Hessian sum_p l''(M_p) phi_p phi_p^T (M is linear in theta)."""
+    M = model(R, theta, m)
+    _, _, d2, _ = pixel_terms(I, M, m, spec, mask, var, flat)
+    return gram(R, m, d2)
+
+
+def newton(R, I, m, theta0, spec: LossSpec, mask=None, var=None, flat=None,
+           max_iter: int = 50, rtol: float = 1e-13, verbose: bool = False):
+    """Damped Newton iteration on the FP64 loss to its stationary point.
+
+    Step: solve (H + lam diag(H)) d = -g with lam = 0 unless H is not positive
+    definite; backtrack on the loss (Armijo, c = 1e-4).  Stops when the step is
+    below rtol relative to theta or the loss no longer decreases."""
+    th = _d(theta0).copy()
+    L, g = loss_grad(R, I, m, th, spec, mask, var, flat)
+    for it in range(max_iter):
+        Hm = hessian(R, I, m, th, spec, mask, var, flat)
+        dH = np.diag(Hm).copy()
+        if np.all(dH == 0):
+            raise Degenerate("zero Hessian")
+        lam = 0.0
+        while True:
+            try:
+                C = np.linalg.cholesky(Hm + lam * np.diag(np.abs(dH) + 1e-300))
+                break
+            except np.linalg.LinAlgError:
+                lam = 1e-6 if lam == 0.0 else lam * 10.0
+                if lam > 1e12:
+                    raise Degenerate("Hessian not positive definite")
+        d = -np.linalg.solve(C.T, np.linalg.solve(C, g))
+        t = 1.0
+        slope = float(g @ d)
+        while True:
+            Lt, gt = loss_grad(R, I, m, th + t * d, spec, mask, var, flat)
+            if Lt <= L + 1e-4 * t * slope or t < 1e-12:
+                break
+            t *= 0.5
+        step = t * d
+        th = th + step
+        dec = L - Lt
+        L, g = Lt, gt
+        if verbose:
+            print(f"newton it={it} L={L:.17g} |step|={np.max(np.abs(step)):.3e}")
+        if np.max(np.abs(step)) <= rtol * (1.0 + np.max(np.abs(th))) or dec <= 0.0:
+            break
+    return th
+
+
+def fit(R, I, m, spec: LossSpec = None, mask=None, var=None, flat=None,
+        theta0=None, max_iter: int = 50):
+    """The minimiser of the loss.  Fixed-variance Gaussian: the B08 normal
+    solve.  Otherwise: Newton from theta0 (default: the normal solve with the
+    scalar variance, which is the B08 first iteration)."""
+    spec = spec or LossSpec()
+    if spec.rho == "gauss" and spec.noise == "fixed":
+        return normal_solve(R, I, m, mask, var, spec.var)
+    if theta0 is None:
+        theta0 = normal_solve(R, I, m, mask, var if spec.noise == "fixed" else None,
+                              spec.var if spec.noise == "fixed" else 1.0)
+    return newton(R, I, m, theta0, spec, mask, var, flat, max_iter=max_iter)
+
+
+def diff_image(R, I, m, theta) -> np.ndarray:
+    """Difference image D = I - M over the valid region (Sec. 1)."""
+    return _valid(_d(I), m) - model(R, theta, m)
+
+
+def sigma_clip(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None,
+               kappa: float = 5.0) -> np.ndarray:
+    """Mask (full image, uint8, 1 = use) after clipping |z| > kappa on the
+    valid region, z = (I - M)/sigma (B08 clipping, Sec. 4.2).  Clipping is
+    cumulative: a pixel already masked stays masked."""
+    I = _d(I)
+    H, W = I.shape
+    h = m // 2
+    M = model(R, theta, m)
+    _, _, _, z = pixel_terms(I, M, m, spec, None, var, flat)
+    out = np.ones((H, W), np.uint8) if mask is None else np.array(mask, np.uint8)
+    v = out[h:H - h, h:W - h]
+    v[np.abs(z) > kappa] = 0
+    return out
+
+
+def fit_clipped(R, I, m, spec: LossSpec, mask=None, var=None, flat=None,
+                passes: int = 3, kappa: float = 5.0, theta0=None):
+    """Fit, then `passes` times: clip at kappa and refit from the current theta.
+    Returns (theta, mask)."""
+    th = fit(R, I, m, spec, mask, var, flat, theta0)
+    mk = None if mask is None else np.array(mask, np.uint8)
+    for _ in range(passes):
+        mk = sigma_clip(R, I, m, th, spec, mk, var, flat, kappa)
+        th = fit(R, I, m, spec, mk, var, flat, theta0=th)
+    return th, mk

@@ -1,0 +1,272 @@
+/*
+ * FP64 CPU oracle for the DIA kernel fit (PyTorchDIA, arXiv 2104.13715).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the test-suite, the smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no header, constant or helper with the CUDA
+ * path: every definition below is written out again from the paper.
+ *
+ * What it computes, by direct nested loops in double precision:
+ *
+ *   model image     M_ij = sum_{l,m} K_lm R_(i+l)(j+m) + B0           (Sec. 2.1, Eq. 2)
+ *                   with centred offsets l,m in [-h, h], kernel side 2h+1,
+ *                   defined only where the whole kernel footprint lies
+ *                   inside R, i.e. i,j in [h, N-h)                     (Sec. 2.1, N_data)
+ *   pixel variance  fixed map / CCD  s0^2/F^2 + M/(G F)                (Sec. 2.1, Eq. 5)
+ *                   EMCCD  E M/(G_tot F)                                (Sec. 2.1, Eq. 6)
+ *   pixel loss      rho(z) + ln(sigma), z = (I - M)/sigma               (Sec. 2.3, Eq. 7;
+ *                   rho = z^2/2 (Gaussian), Huber (Sec. 2.4, Eq. 10),   Sec. 2.4, Eq. 11)
+ *                   Cauchy ln(1+z^2) (a Student-t drop-in, Sec. 2.4)
+ *   total loss      L = sum over unmasked valid pixels
+ *   gradient        dL/dK_lm = sum_p dl/dM_p R_(p+lm),  dL/dB0 = sum_p dl/dM_p
+ *
+ * The per-pixel curvature d2l/dM2 is exported too: because M is linear in
+ * theta = [K, B0], the Hessian of L is sum_p (d2l/dM2)_p phi_p phi_p^T with
+ * phi_p = [R window of p, 1]; the Python side forms that product.
+ *
+ * Readings of points the paper leaves open (the same ones the CUDA path takes):
+ *   - with a fixed variance the ln(sigma) term is a constant and is dropped;
+ *   - a model-dependent variance is clamped below at var_floor, and where it
+ *     is clamped its derivative with respect to M is taken as zero;
+ *   - the constant normalisation terms (N/2 ln 2pi, the Huber Q) are dropped.
+ *
+ * Threading: rows of the valid region are independent; each row's sums are
+ * kept separately and added in row order, so the result does not depend on
+ * the number of threads.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* loss shapes rho(z) */
+#define ORC_RHO_GAUSS 0
+#define ORC_RHO_HUBER 1
+#define ORC_RHO_CAUCHY 2
+/* variance models */
+#define ORC_VAR_FIXED 0
+#define ORC_VAR_CCD 1
+#define ORC_VAR_EMCCD 2
+
+/* params[] layout (all doubles):
+ *  0 rho kind, 1 variance kind, 2 sigma0 (read noise), 3 gain G (or G_total),
+ *  4 excess factor E, 5 huber c, 6 scalar fixed variance (used when no map),
+ *  7 variance floor                                                          */
+
+typedef struct {
+    int rho, noise;
+    double sigma0, gain, excess, c, var_scalar, var_floor;
+} spec_t;
+
+static spec_t read_spec(const double *p)
+{
+    spec_t s;
+    s.rho = (int)p[0];
+    s.noise = (int)p[1];
+    s.sigma0 = p[2];
+    s.gain = p[3];
+    s.excess = p[4];
+    s.c = p[5];
+    s.var_scalar = p[6];
+    s.var_floor = p[7];
+    return s;
+}
+
+/* Loss of one pixel and its first two derivatives with respect to M. */
+static void pixel_terms(const spec_t *s, double I, double M, double vmap, double F,
+                        double *ell, double *d1, double *d2, double *zout)
+{
+    double v, dv;
+    if (s->noise == ORC_VAR_FIXED) {
+        v = vmap;
+        dv = 0.0;
+    } else if (s->noise == ORC_VAR_CCD) {
+        v = s->sigma0 * s->sigma0 / (F * F) + M / (s->gain * F);
+        dv = 1.0 / (s->gain * F);
+    } else {
+        v = s->excess * M / (s->gain * F);
+        dv = s->excess / (s->gain * F);
+    }
+    if (s->noise != ORC_VAR_FIXED && v < s->var_floor) {
+        v = s->var_floor;
+        dv = 0.0;
+    }
+    double sd = sqrt(v);
+    double r = I - M;
+    double z = r / sd;
+    /* z = (I - M) v^{-1/2};  v linear in M, so d2v/dM2 = 0 */
+    double dz = -1.0 / sd - 0.5 * z * dv / v;
+    double d2z = dv / (v * sd) + 0.75 * z * dv * dv / (v * v);
+
+    double rho, rho1, rho2;
+    if (s->rho == ORC_RHO_GAUSS) {
+        rho = 0.5 * z * z;
+        rho1 = z;
+        rho2 = 1.0;
+    } else if (s->rho == ORC_RHO_HUBER) {
+        double az = fabs(z);
+        if (az <= s->c) {
+            rho = 0.5 * z * z;
+            rho1 = z;
+            rho2 = 1.0;
+        } else {
+            rho = s->c * (az - 0.5 * s->c);
+            rho1 = (z > 0 ? s->c : -s->c);
+            rho2 = 0.0;
+        }
+    } else {
+        double q = 1.0 + z * z;
+        rho = log(q);
+        rho1 = 2.0 * z / q;
+        rho2 = 2.0 * (1.0 - z * z) / (q * q);
+    }
+
+    double e = rho, g1 = rho1 * dz, g2 = rho2 * dz * dz + rho1 * d2z;
+    if (s->noise != ORC_VAR_FIXED) {
+        /* ln(sigma) = ln(v)/2 */
+        e += 0.5 * log(v);
+        g1 += 0.5 * dv / v;
+        g2 -= 0.5 * dv * dv / (v * v);
+    }
+    if (ell) *ell = e;
+    if (d1) *d1 = g1;
+    if (d2) *d2 = g2;
+    if (zout) *zout = z;
+}
+
+static double model_at(const double *R, int ld, int m, const double *theta, int i, int j)
+{
+    int h = m / 2;
+    double acc = 0.0;
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b)
+            acc += theta[a * m + b] * R[(size_t)(i - h + a) * ld + (j - h + b)];
+    return acc + theta[m * m];
+}
+
+static int check_args(int H, int W, int ld, int m)
+{
+    if (m < 1 || (m % 2) == 0) return -1;
+    if (H < m || W < m || ld < W) return -1;
+    return 0;
+}
+
+static void set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* M over the valid region, row-major (H-2h) x (W-2h). */
+int oracle_model(const double *R, int H, int W, int ld, int m, const double *theta,
+                 double *M_out, int nthreads)
+{
+    if (check_args(H, W, ld, m)) return -1;
+    int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < Hv; ++y)
+        for (int x = 0; x < Wv; ++x)
+            M_out[(size_t)y * Wv + x] = model_at(R, ld, m, theta, y + h, x + h);
+    return 0;
+}
+
+/* Per-pixel terms over the valid region from a given model image M (valid
+ * layout).  Any of the outputs may be NULL.  Masked pixels get zeros. */
+int oracle_pixel_terms(const double *I, const uint8_t *mask, const double *var,
+                       const double *flat, int H, int W, int ld, int m,
+                       const double *params, const double *M,
+                       double *ell_out, double *d1_out, double *d2_out, double *z_out)
+{
+    if (check_args(H, W, ld, m)) return -1;
+    spec_t s = read_spec(params);
+    int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h;
+    for (int y = 0; y < Hv; ++y)
+        for (int x = 0; x < Wv; ++x) {
+            size_t q = (size_t)(y + h) * ld + (x + h), o = (size_t)y * Wv + x;
+            int use = mask ? (mask[q] != 0) : 1;
+            double e = 0, g1 = 0, g2 = 0, z = 0;
+            double vm = var ? var[q] : s.var_scalar;
+            double F = flat ? flat[q] : 1.0;
+            pixel_terms(&s, I[q], M[o], vm, F, &e, &g1, &g2, &z);
+            if (!use) {
+                e = 0;
+                g1 = 0;
+                g2 = 0;
+            }
+            if (ell_out) ell_out[o] = e;
+            if (d1_out) d1_out[o] = g1;
+            if (d2_out) d2_out[o] = g2;
+            if (z_out) z_out[o] = z;
+        }
+    return 0;
+}
+
+/* Loss and gradient (m*m + 1 entries: K row-major, then B0) at theta. */
+int oracle_loss_grad(const double *R, const double *I, const uint8_t *mask,
+                     const double *var, const double *flat, int H, int W, int ld, int m,
+                     const double *params, const double *theta, double *loss_out,
+                     double *grad_out, int nthreads)
+{
+    if (check_args(H, W, ld, m)) return -1;
+    spec_t s = read_spec(params);
+    int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h, n = m * m + 1;
+    double *row_loss = (double *)calloc((size_t)Hv, sizeof(double));
+    double *row_grad = (double *)calloc((size_t)Hv * n, sizeof(double));
+    if (!row_loss || !row_grad) {
+        free(row_loss);
+        free(row_grad);
+        return -2;
+    }
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int y = 0; y < Hv; ++y) {
+        int i = y + h;
+        double *gr = row_grad + (size_t)y * n;
+        double ls = 0.0;
+        for (int x = 0; x < Wv; ++x) {
+            int j = x + h;
+            size_t q = (size_t)i * ld + j;
+            if (mask && mask[q] == 0) continue;
+            double M = model_at(R, ld, m, theta, i, j);
+            double e, g1;
+            double vm = var ? var[q] : s.var_scalar;
+            double F = flat ? flat[q] : 1.0;
+            pixel_terms(&s, I[q], M, vm, F, &e, &g1, NULL, NULL);
+            ls += e;
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b)
+                    gr[a * m + b] += g1 * R[(size_t)(i - h + a) * ld + (j - h + b)];
+            gr[m * m] += g1;
+        }
+        row_loss[y] = ls;
+    }
+    double L = 0.0;
+    for (int k = 0; k < n; ++k) grad_out[k] = 0.0;
+    for (int y = 0; y < Hv; ++y) {
+        L += row_loss[y];
+        for (int k = 0; k < n; ++k) grad_out[k] += row_grad[(size_t)y * n + k];
+    }
+    *loss_out = L;
+    free(row_loss);
+    free(row_grad);
+    return 0;
+}
+
+/* Number of valid, unmasked pixels (N_data, Sec. 2.1). */
+long long oracle_ndata(const uint8_t *mask, int H, int W, int ld, int m)
+{
+    if (check_args(H, W, ld, m)) return -1;
+    int h = m / 2;
+    long long n = 0;
+    for (int i = h; i < H - h; ++i)
+        for (int j = h; j < W - h; ++j)
+            n += mask ? (mask[(size_t)i * ld + j] != 0) : 1;
+    return n;
+}
