@@ -1,0 +1,208 @@
+/*
+ * dia.h -- C ABI of the GB300 (sm_103a) DIA kernel-fit library.
+ *
+ * The library fits the model image of Bramich (2008) as used by PyTorchDIA
+ * (arXiv 2104.13715):
+ *
+ *     M_ij = sum_{l,m} K_lm R_(i+l)(j+m) + B0                 (Sec. 2.1, Eq. 2)
+ *
+ * to a target image I by minimising a per-pixel negative log-likelihood
+ * (Sec. 2.3, Eq. 7; Sec. 2.4, Eq. 11) with Adam followed by L-BFGS
+ * (Sec. 2.3, Sec. 2.8).  Every step of the fit runs in this library's own
+ * CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Images: float32, row-major, H rows by W columns, row pitch `ld` elements
+ *   (ld >= W).  The reference R, target I and the optional per-pixel maps
+ *   (mask, fixed variance, flat field) share H, W and ld; the mask is one
+ *   byte per pixel with the same pitch in elements (= bytes).
+ * Kernel: odd side m = 2h+1, 1 <= m <= min(H, W), m <= DIA_MAX_M.
+ *   K[a][b] (a, b in [0, m)) multiplies R[i-h+a][j-h+b] for the target pixel
+ *   (i, j): centred offsets l = a-h, m = b-h as in Eq. 2.  A target moved by
+ *   +1 pixel in x and y is fitted by a delta at a = b = h-1 (Sec. 3.4 iii).
+ * Valid region: only pixels with i in [h, H-h) and j in [h, W-h) enter the
+ *   loss (Sec. 2.1: the convolution is undefined within half a kernel width
+ *   of the edge); the difference image covers exactly that region,
+ *   (H-2h) x (W-2h), row-major, dense, its (0,0) at pixel (h, h).
+ * theta: float64 vector of n = m*m + 1 entries: K row-major, then B0.
+ * Mask: nonzero = use the pixel, 0 = masked.  The mask refers to target
+ *   pixels; a bad reference pixel must be masked (dilated by h) by the caller.
+ * Memory: unless a pair says DIA_MEM_HOST, every pointer is a DEVICE pointer
+ *   owned by the caller.  The library never frees or keeps caller memory and
+ *   allocates no device memory inside these calls: all scratch lives in the
+ *   caller's `workspace` (size from dia_workspace_size()).  It does create
+ *   and cache, per host thread, one internal stream and CUDA graphs.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *   work is ordered on it; dia_fit and dia_fit_batch return after the fit
+ *   (they wait on the stream to poll the convergence flag); dia_loss_grad
+ *   and dia_diff_image are asynchronous.
+ * Errors: every entry returns a dia_status and never aborts or throws.
+ *   Arguments are validated before any launch (DIA_ERR_ARG).  A CUDA error
+ *   is reported as DIA_ERR_CUDA; dia_last_cuda_error() gives its code.
+ */
+#ifndef DIA_H
+#define DIA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIA_MAX_M 31           /* largest odd kernel side of the fused kernels */
+#define DIA_ABI_VERSION 1
+
+typedef enum {
+    DIA_OK = 0,
+    DIA_ERR_ARG = 1,           /* invalid argument (checked before any launch) */
+    DIA_ERR_CUDA = 2,          /* a CUDA call failed */
+    DIA_ERR_NONFINITE = 3,     /* loss or gradient became NaN/Inf */
+    DIA_ERR_MAXITER = 4,       /* iteration cap reached; outputs hold the last theta */
+    DIA_ERR_LINESEARCH = 5,    /* L-BFGS line search found no decrease */
+    DIA_ERR_DEGENERATE = 6,    /* no usable pixel (all masked) */
+    DIA_ERR_TIMEOUT = 7,       /* host wall-clock limit while polling */
+    DIA_ERR_WORKSPACE = 8,     /* workspace too small or misaligned */
+    DIA_ERR_UNSUPPORTED = 9    /* e.g. m > DIA_MAX_M */
+} dia_status;
+
+/* Loss shape rho(z) of the pixel residual z = (I - M)/sigma. */
+typedef enum {
+    DIA_RHO_GAUSS = 0,         /* z^2/2                        (Eq. 7)  */
+    DIA_RHO_HUBER = 1,         /* Huber with threshold c       (Eq. 10) */
+    DIA_RHO_CAUCHY = 2         /* ln(1 + z^2), the Student-t nu=1 drop-in (Sec. 2.4) */
+} dia_rho;
+
+/* Pixel variance sigma^2. */
+typedef enum {
+    DIA_VAR_FIXED = 0,         /* var map, else var_scalar; ln sigma dropped (constant) */
+    DIA_VAR_CCD = 1,           /* sigma0^2/F^2 + M/(G F)       (Eq. 5) */
+    DIA_VAR_EMCCD = 2          /* E M/(G F), G = G_total       (Eq. 6) */
+} dia_var_model;
+
+typedef struct {
+    int32_t rho;               /* dia_rho */
+    int32_t var_model;         /* dia_var_model */
+    float sigma0;              /* read noise (image units), CCD */
+    float gain;                /* G (CCD) or G_total (EMCCD), > 0 */
+    float excess;              /* EMCCD excess noise factor E (paper: 2) */
+    float huber_c;             /* Huber threshold c (paper: 1.345) */
+    float var_scalar;          /* fixed variance when the pair has no var map (> 0) */
+    float var_floor;           /* model-dependent variance clamp (> 0); where
+                                  clamped, dsigma^2/dM is taken as 0 */
+} dia_loss_spec;
+
+typedef enum { DIA_MEM_DEVICE = 0, DIA_MEM_HOST = 1 } dia_mem;
+
+/* One reference/target pair. */
+typedef struct {
+    const float *ref;          /* R, H x W pitch ld (background-subtracted, Sec. 2.8) */
+    const float *img;          /* I, H x W pitch ld */
+    const uint8_t *mask;       /* nullable: every pixel used */
+    const float *var;          /* nullable: fixed variance map (DIA_VAR_FIXED) */
+    const float *flat;         /* nullable: flat field F (CCD/EMCCD), else 1 */
+    int32_t H, W, ld;
+    int32_t m;                 /* odd kernel side */
+    int32_t mem;               /* dia_mem: where the pointers above AND the
+                                  outputs of the call live */
+} dia_pair;
+
+/* Optimiser settings (Sec. 2.8).  dia_opts_default() fills the paper's
+ * values; a NULL dia_opts* means those defaults. */
+typedef struct {
+    double lr_kernel;          /* Adam learning rate of the kernel pixels (1e-3) */
+    double lr_b0;              /* Adam learning rate of B0 (10; the paper uses 1, 10 or 100) */
+    double beta1, beta2;       /* Adam moment decays (0.9, 0.999) */
+    double adam_eps;           /* Adam epsilon (1e-8) */
+    double switch_tol;         /* |dL/L| between Adam steps that hands over to L-BFGS (1e-6) */
+    int32_t max_adam_iters;    /* Adam step cap (5000) */
+    int32_t history;           /* L-BFGS memory (100, at most 128) */
+    double rel_tol;            /* stop when |dL/L| between L-BFGS steps < rel_tol (1e-9) */
+    double grad_tol;           /* or when every |dL/dtheta_k| / N_data < grad_tol (1e-7) */
+    int32_t max_lbfgs_iters;   /* L-BFGS iteration cap (1000) */
+    int32_t max_evals;         /* cap on loss+gradient evaluations per fit, all passes (20000) */
+    int32_t clip_passes;       /* sigma-clip-and-refit passes after the first fit (0) */
+    float clip_kappa;          /* clip |z| > kappa (5, Sec. 4.2) */
+    int32_t init;              /* 0: box-car K = 1/m^2, 1: Gaussian of init_sigma,
+                                  2: theta0; B0 = median of the unmasked valid I
+                                  for 0 and 1 (Sec. 2.8) */
+    double init_sigma;         /* Gaussian init width phi_K (px) */
+    const double *theta0;      /* HOST pointer, n entries, used when init == 2 */
+    int32_t graph_iters;       /* optimiser iterations per CUDA-graph launch (16) */
+    double timeout_s;          /* host polling limit per fit (600 s) */
+} dia_opts;
+
+typedef struct {
+    int32_t status;            /* dia_status of the fit */
+    int32_t adam_iters, lbfgs_iters, evals;
+    int32_t clip_passes_done;
+    int64_t ndata;             /* unmasked valid pixels at the end (N_data) */
+    double loss;               /* final loss, sum over pixels (float64) */
+    double grad_inf;           /* max |dL/dtheta| / N_data at the end */
+    double scale;              /* photometric scale P = sum K (Eq. 3) */
+    double b0;                 /* fitted B0 */
+} dia_fit_info;
+
+/* Human-readable status name (static string). */
+const char *dia_status_str(int32_t status);
+
+/* Version of this ABI (DIA_ABI_VERSION). */
+int32_t dia_abi_version(void);
+
+/* CUDA error code of the last DIA_ERR_CUDA on this host thread (0 if none). */
+int32_t dia_last_cuda_error(void);
+
+/* Fill `opts` with the paper's defaults (values in the field comments). */
+dia_status dia_opts_default(dia_opts *opts);
+
+/* Workspace bytes needed by dia_loss_grad / dia_fit / dia_diff_image for an
+ * H x W image of row pitch ld, kernel side m, with `clip` != 0 if dia_fit
+ * will clip (clip_passes > 0) or return a mask, and `mem` = DIA_MEM_HOST if
+ * the pair's buffers are on the host (the images are then staged through the
+ * workspace).  Returns 0 for invalid sizes.  The workspace must be 256-byte
+ * aligned device memory; its contents need no initialisation. */
+size_t dia_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m, int32_t clip, int32_t mem);
+
+/* One loss + gradient evaluation at theta (Sec. 2.3, Eq. 7 / Eq. 11).
+ *   theta     device float64[n]  (read; the kernel works in float32 pixels)
+ *   loss_out  device float64[1]  L = sum over unmasked valid pixels
+ *   grad_out  device float64[n]  dL/dtheta, same layout as theta
+ * The fused kernel computes M, the per-pixel loss and dL/dM and the
+ * correlation of dL/dM with R in one pass, never storing M; per-CTA sums are
+ * float32 over one tile and float64 across tiles and CTAs, reduced in a
+ * fixed order (bitwise repeatable).  The pair must be DIA_MEM_DEVICE.
+ * Asynchronous on `stream`. */
+dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss,
+                         const double *theta, double *loss_out, double *grad_out,
+                         void *workspace, size_t workspace_bytes, void *stream);
+
+/* Difference image D = I - M over the valid region (Sec. 1) for theta
+ * (device float64[n]); diff_out is (H-2h) x (W-2h) float32.  Asynchronous. */
+dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff_out,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Fit theta = [K, B0] (Sec. 2.9 algorithm): initialise, Adam until the
+ * relative loss change drops below switch_tol, then L-BFGS with a
+ * strong-Wolfe line search until rel_tol / grad_tol; optionally clip
+ * |z| > kappa and refit clip_passes times.  Each optimiser iteration is one
+ * fused evaluation, a float64 reduction and a one-CTA float64 optimiser
+ * step, replayed graph_iters at a time from a CUDA graph.
+ * Outputs (all nullable; device pointers, or host pointers if the pair is
+ * DIA_MEM_HOST):
+ *   theta_out  float64[n]; K_out float32[m*m]; b0_out float32[1];
+ *   diff_out   float32 (H-2h) x (W-2h) difference image at the final theta;
+ *   mask_out   uint8 H x W final mask (input mask with clipped pixels zeroed).
+ * info (HOST, nullable) receives counters, final loss, P = sum K, B0.
+ * Returns the fit status (also in info->status); on DIA_ERR_MAXITER the
+ * outputs hold the last accepted theta. */
+dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_opts *opts,
+                   double *theta_out, float *K_out, float *b0_out, float *diff_out,
+                   uint8_t *mask_out, dia_fit_info *info,
+                   void *workspace, size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIA_H */

@@ -1,0 +1,597 @@
+// C ABI of the DIA kernel-fit library (declarations and contract in include/dia.h).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <set>
+#include <string>
+#include <utility>
+
+#include "../../include/dia.h"
+#include "dia_dispatch.h"
+#include "dia_eval.cuh"
+#include "dia_ops.cuh"
+
+using namespace dia;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+#define DIA_CK(expr)                               \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) {                   \
+            g_last_cuda = (int)_e;                 \
+            return DIA_ERR_CUDA;                   \
+        }                                          \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxGrid = 1024;   // CTAs of the fused kernel (partials are sized for this)
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+    size_t state, sel, hist, red, partials, theta, trial, grad, glo, m1, m2, dir, S, Y, rho, ahist,
+        pdiag, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
+        total;
+    int G, n_tiles, tiles_x, np, n, kp;
+};
+
+bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInfo &ki, Layout &L) {
+    const int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h;
+    L.tiles_x = (Wv + kTW - 1) / kTW;
+    const int tiles_y = (Hv + ki.th - 1) / ki.th;
+    L.n_tiles = L.tiles_x * tiles_y;
+    L.G = L.n_tiles < kMaxGrid ? L.n_tiles : kMaxGrid;
+    L.np = ki.np;
+    L.n = m * m + 1;
+    L.kp = ki.kp;
+    const size_t n8 = (size_t)L.n * 8;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    L.state = take(sizeof(FitState));
+    L.sel = take(sizeof(SelectState));
+    L.hist = take(2048 * 4);
+    L.red = take((size_t)L.np * 8);
+    L.partials = take((size_t)L.G * L.np * 8);
+    L.theta = take(n8);
+    L.trial = take(n8);
+    L.grad = take(n8);
+    L.glo = take(n8);
+    L.m1 = take(n8);
+    L.m2 = take(n8);
+    L.dir = take(n8);
+    L.S = take(n8 * kHistMax);
+    L.Y = take(n8 * kHistMax);
+    L.rho = take(8 * kHistMax);
+    L.ahist = take(8 * kHistMax);
+    L.pdiag = take(n8);
+    L.kpad = take((size_t)(m * ki.kp + 4) * 4);
+    const size_t plane = (size_t)H * (mem == DIA_MEM_HOST ? W : ld);
+    L.mask = clip ? take(plane) : 0;
+    if (mem == DIA_MEM_HOST) {
+        L.stage_R = take(plane * 4);
+        L.stage_I = take(plane * 4);
+        L.stage_var = take(plane * 4);
+        L.stage_flat = take(plane * 4);
+        L.stage_mask = take(plane);
+        L.stage_diff = take((size_t)Hv * Wv * 4);
+        L.stage_out = take((size_t)(m * m + 1) * 4);
+    } else {
+        L.stage_R = L.stage_I = L.stage_var = L.stage_flat = L.stage_mask = L.stage_diff =
+            L.stage_out = 0;
+    }
+    L.total = o;
+    return true;
+}
+
+bool dims_ok(int H, int W, int ld, int m) {
+    if (H <= 0 || W <= 0 || ld < W) return false;
+    if (m < 1 || (m & 1) == 0 || m > H || m > W) return false;
+    if ((long long)H * ld > (1LL << 40)) return false;
+    return true;
+}
+
+dia_status check_pair(const dia_pair *p) {
+    if (!p || !p->ref || !p->img) return DIA_ERR_ARG;
+    if (p->mem != DIA_MEM_DEVICE && p->mem != DIA_MEM_HOST) return DIA_ERR_ARG;
+    if (!dims_ok(p->H, p->W, p->ld, p->m)) return DIA_ERR_ARG;
+    if (p->m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
+    return DIA_OK;
+}
+
+dia_status check_loss(const dia_loss_spec *l, const dia_pair *p) {
+    if (!l) return DIA_ERR_ARG;
+    if (l->rho < 0 || l->rho > 2 || l->var_model < 0 || l->var_model > 2) return DIA_ERR_ARG;
+    if (l->var_model == DIA_VAR_FIXED) {
+        if (!p->var && !(l->var_scalar > 0.f)) return DIA_ERR_ARG;
+    } else {
+        if (!(l->gain > 0.f) || !(l->var_floor > 0.f)) return DIA_ERR_ARG;
+        if (l->var_model == DIA_VAR_EMCCD && !(l->excess > 0.f)) return DIA_ERR_ARG;
+    }
+    if (l->rho == DIA_RHO_HUBER && !(l->huber_c > 0.f)) return DIA_ERR_ARG;
+    return DIA_OK;
+}
+
+LossParams to_params(const dia_loss_spec *l) {
+    LossParams lp;
+    lp.rho = l->rho;
+    lp.var_model = l->var_model;
+    lp.s0sq = l->sigma0 * l->sigma0;
+    lp.inv_gain = (l->gain > 0.f) ? 1.0f / l->gain : 1.0f;
+    lp.excess = l->excess;
+    lp.huber_c = l->huber_c;
+    lp.var_scalar = l->var_scalar;
+    lp.var_floor = l->var_floor;
+    return lp;
+}
+
+int device_sms() {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+std::mutex g_attr_mu;
+std::set<std::pair<int, const void *>> g_attr_done;
+
+cudaError_t prepare_kernel(const void *fn, int smem, int nt, int *occ) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_attr_mu);
+        if (!g_attr_done.count({dev, fn})) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            g_attr_done.insert({dev, fn});
+        }
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, nt, smem);
+}
+
+cudaError_t launch_eval(const KernelInfo &ki, int mode, const EvalArgs &a, int grid, cudaStream_t s) {
+    void *params[] = {(void *)&a};
+    return cudaLaunchKernel(ki.fn[mode], dim3(grid), dim3(ki.nt), params, ki.smem, s);
+}
+
+// Everything one fit/eval needs on the device side.
+struct Ctx {
+    KernelInfo ki;
+    Layout L;
+    char *ws;
+    dia_pair dp;    // device view of the pair (staged if the caller's was on the host)
+    EvalArgs ea;
+    int grid;
+    FitState *st;
+    SelectState *sel;
+    OptBuffers ob;
+    float *kpad;
+    double *red, *partials;
+};
+
+dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void *workspace,
+                 size_t ws_bytes, cudaStream_t s, Ctx &c) {
+    dia_status rc = check_pair(pair);
+    if (rc != DIA_OK) return rc;
+    if (loss) {
+        rc = check_loss(loss, pair);
+        if (rc != DIA_OK) return rc;
+    }
+    if (!kernel_info(pair->m, &c.ki)) return DIA_ERR_UNSUPPORTED;
+    make_layout(pair->H, pair->W, pair->ld, pair->m, clip, pair->mem, c.ki, c.L);
+    if (!workspace || ws_bytes < c.L.total || ((uintptr_t)workspace % kAlign) != 0)
+        return DIA_ERR_WORKSPACE;
+    c.ws = (char *)workspace;
+    c.dp = *pair;
+    const int H = pair->H, W = pair->W;
+    if (pair->mem == DIA_MEM_HOST) {
+        // stage the inputs densely (pitch W)
+        auto up = [&](size_t off, const void *src, size_t elt) -> cudaError_t {
+            return cudaMemcpy2DAsync(c.ws + off, (size_t)W * elt, src, (size_t)pair->ld * elt,
+                                     (size_t)W * elt, H, cudaMemcpyHostToDevice, s);
+        };
+        DIA_CK(up(c.L.stage_R, pair->ref, 4));
+        DIA_CK(up(c.L.stage_I, pair->img, 4));
+        c.dp.ref = (const float *)(c.ws + c.L.stage_R);
+        c.dp.img = (const float *)(c.ws + c.L.stage_I);
+        if (pair->var) {
+            DIA_CK(up(c.L.stage_var, pair->var, 4));
+            c.dp.var = (const float *)(c.ws + c.L.stage_var);
+        }
+        if (pair->flat) {
+            DIA_CK(up(c.L.stage_flat, pair->flat, 4));
+            c.dp.flat = (const float *)(c.ws + c.L.stage_flat);
+        }
+        if (pair->mask) {
+            DIA_CK(up(c.L.stage_mask, pair->mask, 1));
+            c.dp.mask = (const uint8_t *)(c.ws + c.L.stage_mask);
+        }
+        c.dp.ld = W;
+        c.dp.mem = DIA_MEM_DEVICE;
+    }
+    int occ = 1;
+    DIA_CK(prepare_kernel(c.ki.fn[kModeGrad], c.ki.smem, c.ki.nt, &occ));
+    int occ2 = 1;
+    DIA_CK(prepare_kernel(c.ki.fn[kModeForward], c.ki.smem, c.ki.nt, &occ2));
+    if (occ < 1) occ = 1;
+    long long g = (long long)device_sms() * occ;
+    if (g > c.L.G) g = c.L.G;
+    c.grid = (int)g;
+
+    const int h = pair->m / 2;
+    EvalArgs &a = c.ea;
+    memset(&a, 0, sizeof(a));
+    a.R = c.dp.ref;
+    a.I = c.dp.img;
+    a.mask = c.dp.mask;
+    a.var = c.dp.var;
+    a.flat = c.dp.flat;
+    a.H = H;
+    a.W = W;
+    a.ld = c.dp.ld;
+    a.Hv = H - 2 * h;
+    a.Wv = W - 2 * h;
+    a.tiles_x = c.L.tiles_x;
+    a.n_tiles = c.L.n_tiles;
+    c.kpad = (float *)(c.ws + c.L.kpad);
+    a.Kpad = c.kpad;
+    c.partials = (double *)(c.ws + c.L.partials);
+    a.partials = c.partials;
+    a.clip_kappa = 5.0f;
+    if (loss) a.lp = to_params(loss);
+    c.red = (double *)(c.ws + c.L.red);
+    c.st = (FitState *)(c.ws + c.L.state);
+    c.sel = (SelectState *)(c.ws + c.L.sel);
+    c.ob.theta = (double *)(c.ws + c.L.theta);
+    c.ob.trial = (double *)(c.ws + c.L.trial);
+    c.ob.grad = (double *)(c.ws + c.L.grad);
+    c.ob.glo = (double *)(c.ws + c.L.glo);
+    c.ob.m1 = (double *)(c.ws + c.L.m1);
+    c.ob.m2 = (double *)(c.ws + c.L.m2);
+    c.ob.dir = (double *)(c.ws + c.L.dir);
+    c.ob.S = (double *)(c.ws + c.L.S);
+    c.ob.Y = (double *)(c.ws + c.L.Y);
+    c.ob.rho = (double *)(c.ws + c.L.rho);
+    c.ob.ahist = (double *)(c.ws + c.L.ahist);
+    c.ob.pdiag = (double *)(c.ws + c.L.pdiag);
+    return DIA_OK;
+}
+
+// ---------------------------------------------------------------- graph cache
+struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::list<GraphEntry> g_graphs;   // most recent first
+constexpr size_t kMaxGraphs = 16;
+
+cudaStream_t capture_stream() {
+    thread_local int dev_of = -1;
+    thread_local cudaStream_t cs = nullptr;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cs == nullptr || dev_of != dev) {
+        cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        dev_of = dev;
+    }
+    return cs;
+}
+
+template <class T>
+void append(std::string &k, const T &v) {
+    k.append(reinterpret_cast<const char *>(&v), sizeof(T));
+}
+
+// One optimiser iteration = fused evaluation, float64 reduction, optimiser step.
+cudaError_t enqueue_iteration(const Ctx &c, const EvalArgs &ea, const StepArgs &sa, cudaStream_t s) {
+    cudaError_t e = launch_eval(c.ki, kModeGrad, ea, c.grid, s);
+    if (e != cudaSuccess) return e;
+    e = launch_reduce(c.partials, c.grid, c.L.np, c.red, &c.st->done, s);
+    if (e != cudaSuccess) return e;
+    return launch_step(sa, s);
+}
+
+dia_status get_graph(const Ctx &c, const EvalArgs &ea, const StepArgs &sa, int iters,
+                     cudaGraphExec_t *out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string key;
+    append(key, dev);
+    append(key, ea);
+    append(key, sa);
+    append(key, iters);
+    append(key, c.grid);
+    append(key, c.ki);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it)
+        if (it->key == key) {
+            g_graphs.splice(g_graphs.begin(), g_graphs, it);
+            *out = it->exec;
+            return DIA_OK;
+        }
+    cudaStream_t cs = capture_stream();
+    DIA_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < iters && e == cudaSuccess; ++i) e = enqueue_iteration(c, ea, sa, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        g_last_cuda = (int)(e != cudaSuccess ? e : e2);
+        return DIA_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    DIA_CK(e);
+    g_graphs.push_front({key, ex});
+    if (g_graphs.size() > kMaxGraphs) {
+        cudaGraphExecDestroy(g_graphs.back().exec);
+        g_graphs.pop_back();
+    }
+    *out = ex;
+    return DIA_OK;
+}
+
+void fill_opts_default(dia_opts *o) {
+    memset(o, 0, sizeof(*o));
+    o->lr_kernel = 1e-3;
+    o->lr_b0 = 10.0;
+    o->beta1 = 0.9;
+    o->beta2 = 0.999;
+    o->adam_eps = 1e-8;
+    o->switch_tol = 1e-6;
+    o->max_adam_iters = 5000;
+    o->history = 100;
+    o->rel_tol = 1e-9;
+    o->grad_tol = 1e-7;
+    o->max_lbfgs_iters = 1000;
+    o->max_evals = 20000;
+    o->clip_passes = 0;
+    o->clip_kappa = 5.0f;
+    o->init = 0;
+    o->init_sigma = 1.0;
+    o->theta0 = nullptr;
+    o->graph_iters = 16;
+    o->timeout_s = 600.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dia_status_str(int32_t s) {
+    switch (s) {
+        case DIA_OK: return "DIA_OK";
+        case DIA_ERR_ARG: return "DIA_ERR_ARG";
+        case DIA_ERR_CUDA: return "DIA_ERR_CUDA";
+        case DIA_ERR_NONFINITE: return "DIA_ERR_NONFINITE";
+        case DIA_ERR_MAXITER: return "DIA_ERR_MAXITER";
+        case DIA_ERR_LINESEARCH: return "DIA_ERR_LINESEARCH";
+        case DIA_ERR_DEGENERATE: return "DIA_ERR_DEGENERATE";
+        case DIA_ERR_TIMEOUT: return "DIA_ERR_TIMEOUT";
+        case DIA_ERR_WORKSPACE: return "DIA_ERR_WORKSPACE";
+        case DIA_ERR_UNSUPPORTED: return "DIA_ERR_UNSUPPORTED";
+        default: return "DIA_ERR_UNKNOWN";
+    }
+}
+
+int32_t dia_abi_version(void) { return DIA_ABI_VERSION; }
+
+int32_t dia_last_cuda_error(void) { return g_last_cuda; }
+
+dia_status dia_opts_default(dia_opts *opts) {
+    if (!opts) return DIA_ERR_ARG;
+    fill_opts_default(opts);
+    return DIA_OK;
+}
+
+size_t dia_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m, int32_t clip, int32_t mem) {
+    if (!dims_ok(H, W, ld, m) || m > DIA_MAX_M) return 0;
+    if (mem != DIA_MEM_DEVICE && mem != DIA_MEM_HOST) return 0;
+    KernelInfo ki;
+    if (!kernel_info(m, &ki)) return 0;
+    Layout L;
+    make_layout(H, W, ld, m, clip != 0, mem, ki, L);
+    return L.total;
+}
+
+dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
+                         double *loss_out, double *grad_out, void *workspace,
+                         size_t workspace_bytes, void *stream) {
+    if (!pair || pair->mem != DIA_MEM_DEVICE || !loss || !theta || !loss_out || !grad_out)
+        return DIA_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    dia_status rc = setup(pair, loss, 0, workspace, workspace_bytes, s, c);
+    if (rc != DIA_OK) return rc;
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.kpad, s));
+    DIA_CK(launch_eval(c.ki, kModeGrad, c.ea, c.grid, s));
+    DIA_CK(launch_reduce(c.partials, c.grid, c.L.np, c.red, nullptr, s));
+    DIA_CK(launch_emit_loss_grad(c.red, pair->m, loss_out, grad_out, s));
+    return DIA_OK;
+}
+
+dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff_out,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    if (!pair || pair->mem != DIA_MEM_DEVICE || !theta || !diff_out) return DIA_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    dia_loss_spec ls;
+    memset(&ls, 0, sizeof(ls));
+    ls.var_scalar = 1.f;
+    dia_status rc = setup(pair, &ls, 0, workspace, workspace_bytes, s, c);
+    if (rc != DIA_OK) return rc;
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.kpad, s));
+    EvalArgs ea = c.ea;
+    ea.diff_out = diff_out;
+    DIA_CK(launch_eval(c.ki, kModeForward, ea, c.grid, s));
+    return DIA_OK;
+}
+
+dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_opts *opts_in,
+                   double *theta_out, float *K_out, float *b0_out, float *diff_out,
+                   uint8_t *mask_out, dia_fit_info *info, void *workspace,
+                   size_t workspace_bytes, void *stream) {
+    dia_opts opts;
+    if (opts_in)
+        opts = *opts_in;
+    else
+        fill_opts_default(&opts);
+    if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
+        opts.graph_iters > 1024 || opts.clip_passes < 0 || opts.max_adam_iters < 0 ||
+        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.init < 0 || opts.init > 2 ||
+        (opts.init == 2 && !opts.theta0) || (opts.init == 1 && !(opts.init_sigma > 0.0)) ||
+        !(opts.timeout_s > 0.0))
+        return DIA_ERR_ARG;
+    if (!pair || !loss) return DIA_ERR_ARG;
+    const int clip = opts.clip_passes > 0 || mask_out != nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    dia_status rc = setup(pair, loss, clip, workspace, workspace_bytes, s, c);
+    if (rc != DIA_OK) return rc;
+    const int m = pair->m, n = m * m + 1, h = m / 2;
+    const int H = c.dp.H, W = c.dp.W, ld = c.dp.ld;
+    const bool host = pair->mem == DIA_MEM_HOST;
+
+    // working mask (clipping only ever removes pixels)
+    uint8_t *wmask = nullptr;
+    if (clip) {
+        wmask = (uint8_t *)(c.ws + c.L.mask);
+        if (c.dp.mask)
+            DIA_CK(cudaMemcpyAsync(wmask, c.dp.mask, (size_t)H * ld, cudaMemcpyDeviceToDevice, s));
+        else
+            DIA_CK(cudaMemsetAsync(wmask, 1, (size_t)H * ld, s));
+        c.ea.mask = wmask;
+    }
+    c.ea.clip_kappa = opts.clip_kappa;
+
+    // initial theta (Sec. 2.8)
+    const int start_phase = opts.max_adam_iters > 0 ? kPhaseAdam : kPhaseLbfgsStart;
+    if (opts.init == 2) {
+        DIA_CK(cudaMemcpyAsync(c.ob.theta, opts.theta0, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+        DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, 2, 0.0, nullptr, start_phase, s));
+    } else {
+        int mgrid = device_sms() * 4;
+        DIA_CK(launch_median(c.dp.img, c.ea.mask, H, W, ld, m, (uint32_t *)(c.ws + c.L.hist),
+                             c.sel, mgrid, s));
+        DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, opts.init, opts.init_sigma, c.sel,
+                           start_phase, s));
+    }
+
+    EvalArgs ea = c.ea;
+    ea.done_flag = &c.st->done;
+    StepArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.st = c.st;
+    sa.b = c.ob;
+    sa.red = c.red;
+    sa.Kpad = c.kpad;
+    sa.n = n;
+    sa.mk = m;
+    sa.kp = c.ki.kp;
+    sa.p.lr_kernel = opts.lr_kernel;
+    sa.p.lr_b0 = opts.lr_b0;
+    sa.p.beta1 = opts.beta1;
+    sa.p.beta2 = opts.beta2;
+    sa.p.adam_eps = opts.adam_eps;
+    sa.p.switch_tol = opts.switch_tol;
+    sa.p.rel_tol = opts.rel_tol;
+    sa.p.grad_tol = opts.grad_tol;
+    sa.p.max_adam = opts.max_adam_iters;
+    sa.p.history = opts.history;
+    sa.p.max_lbfgs = opts.max_lbfgs_iters;
+    sa.p.max_evals = opts.max_evals;
+
+    cudaGraphExec_t gx = nullptr;
+    rc = get_graph(c, ea, sa, opts.graph_iters, &gx);
+    if (rc != DIA_OK) return rc;
+
+    const auto t0 = std::chrono::steady_clock::now();
+    FitState hs;
+    memset(&hs, 0, sizeof(hs));
+    int status = DIA_OK, passes_done = 0;
+    for (int pass = 0; pass <= opts.clip_passes; ++pass) {
+        if (pass > 0) {
+            // clip |z| > kappa at the current theta, then refit from it
+            EvalArgs ca = c.ea;
+            ca.mask_out = wmask;
+            DIA_CK(launch_eval(c.ki, kModeForward, ca, c.grid, s));
+            DIA_CK(launch_restart(c.st, c.kpad, c.ob, m, c.ki.kp, s));
+            passes_done = pass;
+        }
+        for (;;) {
+            DIA_CK(cudaGraphLaunch(gx, s));
+            DIA_CK(cudaMemcpyAsync(&hs, c.st, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            DIA_CK(cudaStreamSynchronize(s));
+            if (hs.done) break;
+            const double el =
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > opts.timeout_s) {
+                status = DIA_ERR_TIMEOUT;
+                break;
+            }
+        }
+        if (status != DIA_OK) break;
+        if (hs.status != DIA_OK && hs.status != DIA_ERR_MAXITER) break;
+    }
+    DIA_CK(cudaMemcpyAsync(&hs, c.st, sizeof(FitState), cudaMemcpyDeviceToHost, s));
+    DIA_CK(cudaStreamSynchronize(s));
+    if (status == DIA_OK) status = hs.status;
+
+    // outputs at the accepted theta (Kpad holds it after the pass finished)
+    if (diff_out) {
+        EvalArgs da = c.ea;
+        da.diff_out = host ? (float *)(c.ws + c.L.stage_diff) : diff_out;
+        DIA_CK(launch_eval(c.ki, kModeForward, da, c.grid, s));
+        if (host)
+            DIA_CK(cudaMemcpyAsync(diff_out, da.diff_out, (size_t)(H - 2 * h) * (W - 2 * h) * 4,
+                                   cudaMemcpyDeviceToHost, s));
+    }
+    if (host) {
+        float *kst = (float *)(c.ws + c.L.stage_out);
+        DIA_CK(launch_pack_outputs(c.ob.theta, m, nullptr, kst, kst + m * m, s));
+        if (theta_out)
+            DIA_CK(cudaMemcpyAsync(theta_out, c.ob.theta, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+        if (K_out) DIA_CK(cudaMemcpyAsync(K_out, kst, (size_t)m * m * 4, cudaMemcpyDeviceToHost, s));
+        if (b0_out) DIA_CK(cudaMemcpyAsync(b0_out, kst + m * m, 4, cudaMemcpyDeviceToHost, s));
+        if (mask_out)
+            DIA_CK(cudaMemcpy2DAsync(mask_out, pair->ld, wmask, W, W, H, cudaMemcpyDeviceToHost, s));
+    } else {
+        DIA_CK(launch_pack_outputs(c.ob.theta, m, theta_out, K_out, b0_out, s));
+        if (mask_out)
+            DIA_CK(cudaMemcpyAsync(mask_out, wmask, (size_t)H * ld, cudaMemcpyDeviceToDevice, s));
+    }
+    if (info) {
+        double th[DIA_MAX_M * DIA_MAX_M + 1];
+        DIA_CK(cudaMemcpyAsync(th, c.ob.theta, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+        DIA_CK(cudaStreamSynchronize(s));
+        double P = 0.0;
+        for (int k = 0; k < n - 1; ++k) P += th[k];
+        info->status = status;
+        info->adam_iters = hs.it_adam;
+        info->lbfgs_iters = hs.it_lbfgs;
+        info->evals = hs.evals;
+        info->clip_passes_done = passes_done;
+        info->ndata = (int64_t)llround(hs.ndata);
+        info->loss = hs.L_sum;
+        info->grad_inf = hs.grad_inf;
+        info->scale = P;
+        info->b0 = th[n - 1];
+    } else {
+        DIA_CK(cudaStreamSynchronize(s));
+    }
+    return (dia_status)status;
+}
+
+}  // extern "C"

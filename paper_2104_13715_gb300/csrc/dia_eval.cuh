@@ -1,0 +1,365 @@
+// Fused DIA evaluation kernel: forward convolution, per-pixel loss and the
+// kernel/background gradient in one pass over the image (sm_103a).
+//
+// Model (Sec. 2.1, Eq. 2): for an output pixel p = (y, x) of the valid region,
+//   M_p = sum_{a,b} K[a][b] R[y+a][x+b] + B0        (valid-region coordinates)
+// Loss (Sec. 2.3 Eq. 7, Sec. 2.4 Eq. 10-11): l_p = rho(z_p) + ln sigma_p with
+// z = (I - M)/sigma and sigma^2 from the fixed map or the CCD / EMCCD models
+// (Eq. 5, Eq. 6).  Gradient: dL/dK[a][b] = sum_p g_p R[y+a][x+b],
+// dL/dB0 = sum_p g_p with g_p = dl_p/dM_p.
+//
+// One CTA owns a TH x TW tile of output pixels at a time (persistent loop over
+// tiles).  Per tile:
+//   1. the R tile plus its (m-1) halo is staged in shared memory;
+//   2. forward: warp w computes rows [w*QF, (w+1)*QF) of the tile, lane l the
+//      four columns [4l, 4l+4); each R row is loaded once into a register
+//      window and reused by all QF output rows and all m kernel columns;
+//      K is read from shared memory as warp-uniform (broadcast) float4 loads;
+//   3. epilogue: M stays in registers, the loss terms and g_p are formed in
+//      float32 and g_p is written to a shared-memory tile (never to HBM);
+//   4. backward: warp w owns kernel rows a in [a_lo, a_hi); lanes split the
+//      columns; each R row window is reused by every owned kernel row, the
+//      m column offsets and the four pixels of the lane;
+//   5. the float32 tile sums are reduced over the warp and added in float64
+//      to per-CTA shared accumulators.
+// At the end each CTA writes m*m + 5 float64 partials (loss, dK, dB0, pixel
+// count, and two curvature sums for the optimiser's diagonal preconditioner);
+// a separate kernel sums them in a fixed order.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dia {
+
+constexpr int kTW = 128;  // tile width: 32 lanes x 4 pixels
+
+enum EvalMode { kModeGrad = 0, kModeForward = 1 };
+
+struct LossParams {
+    int rho;          // 0 gauss, 1 huber, 2 cauchy
+    int var_model;    // 0 fixed, 1 ccd, 2 emccd
+    float s0sq;       // sigma0^2
+    float inv_gain;   // 1/G
+    float excess;     // E
+    float huber_c;
+    float var_scalar;
+    float var_floor;
+};
+
+struct EvalArgs {
+    const float *R;
+    const float *I;
+    const uint8_t *mask;   // nullable
+    const float *var;      // nullable
+    const float *flat;     // nullable
+    int H, W, ld;
+    int Hv, Wv;            // valid region
+    int tiles_x, n_tiles;
+    const float *Kpad;     // m rows of KP floats (zero padded), then B0
+    double *partials;      // [gridDim.x][m*m + 5]
+    float *diff_out;       // forward mode: D = I - M over the valid region (nullable)
+    uint8_t *mask_out;     // forward mode: clip |z| > kappa (nullable)
+    float clip_kappa;
+    const int *done_flag;  // nullable: nonzero -> return at once
+    LossParams lp;
+};
+
+__host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
+
+// Pixel loss and g = dl/dM (float32).  Returns the loss; writes g, z and a
+// non-negative curvature weight kappa ~ d2l/dM2 (Gauss-Newton / IRLS weight
+// rho'(z)/z / v, plus the Fisher term (v'/v)^2 / 2 of a model-dependent
+// variance) used only to precondition the optimiser.
+__device__ __forceinline__ float pixel_loss(const LossParams &lp, float I, float M, float vmap,
+                                            float F, float &g, float &z, float &kappa) {
+    float v, dv;
+    if (lp.var_model == 0) {
+        v = vmap;
+        dv = 0.f;
+    } else {
+        const float invGF = lp.inv_gain / F;
+        if (lp.var_model == 1) {
+            v = lp.s0sq / (F * F) + M * invGF;
+            dv = invGF;
+        } else {
+            v = lp.excess * M * invGF;
+            dv = lp.excess * invGF;
+        }
+        if (v < lp.var_floor) {
+            v = lp.var_floor;
+            dv = 0.f;
+        }
+    }
+    const float inv_v = 1.0f / v;
+    const float inv_s = sqrtf(inv_v);
+    const float r = I - M;
+    z = r * inv_s;
+    // dz/dM = -1/s - z v'/(2v)
+    const float dz = -inv_s - 0.5f * z * dv * inv_v;
+    float rho, rho1, wz;  // wz = rho'(z)/z
+    if (lp.rho == 0) {
+        rho = 0.5f * z * z;
+        rho1 = z;
+        wz = 1.f;
+    } else if (lp.rho == 1) {
+        const float c = lp.huber_c, az = fabsf(z);
+        if (az <= c) {
+            rho = 0.5f * z * z;
+            rho1 = z;
+            wz = 1.f;
+        } else {
+            rho = c * (az - 0.5f * c);
+            rho1 = copysignf(c, z);
+            wz = c / az;
+        }
+    } else {
+        const float q = z * z;
+        rho = log1pf(q);
+        wz = 2.0f / (1.0f + q);
+        rho1 = z * wz;
+    }
+    float ell = rho;
+    g = rho1 * dz;
+    kappa = wz * inv_v;
+    if (lp.var_model != 0) {
+        ell += 0.5f * logf(v);
+        g += 0.5f * dv * inv_v;
+        kappa += 0.5f * (dv * inv_v) * (dv * inv_v);
+    }
+    return ell;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int MK, int NW, int QF>
+struct EvalShape {
+    static constexpr int TH = NW * QF;
+    static constexpr int RROWS = TH + MK - 1;
+    static constexpr int RP = round4(kTW + MK - 1);      // R tile pitch (floats)
+    static constexpr int RWIN = round4(MK + 3);          // register window per lane
+    static constexpr int KP = round4(MK);                // K row pitch (floats)
+    static constexpr int QB = (MK + NW - 1) / NW;         // max kernel rows per warp (backward)
+    static constexpr int NP = MK * MK + 5;               // partials per CTA
+    static constexpr int NT = NW * 32;
+    // shared memory layout (bytes)
+    static constexpr int OFF_R = 0;
+    static constexpr int SZ_R = RROWS * RP * 4;
+    static constexpr int OFF_G = OFF_R + SZ_R;
+    static constexpr int SZ_G = TH * kTW * 4;
+    static constexpr int OFF_K = OFF_G + SZ_G;
+    static constexpr int SZ_K = (MK * KP + 4) * 4;
+    static constexpr int OFF_D = (OFF_K + SZ_K + 15) & ~15;
+    static constexpr int SZ_D = (MK * MK + 5 * NW) * 8;
+    static constexpr int SMEM = OFF_D + SZ_D;
+};
+
+template <int MK, int NW, int QF, int MODE>
+__global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
+    using S = EvalShape<MK, NW, QF>;
+    constexpr int TH = S::TH, RP = S::RP, RWIN = S::RWIN, KP = S::KP, QB = S::QB;
+    constexpr int H2 = MK / 2;
+    if (args.done_flag != nullptr && *((volatile const int *)args.done_flag) != 0) return;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *Rs = reinterpret_cast<float *>(smem + S::OFF_R);
+    float *gs = reinterpret_cast<float *>(smem + S::OFF_G);
+    float *Ks = reinterpret_cast<float *>(smem + S::OFF_K);
+    double *acc64 = reinterpret_cast<double *>(smem + S::OFF_D);  // dK[MK*MK], then per warp
+                                                                  // {loss, dB0, count, kR2, k}
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int i = tid; i < MK * KP + 4; i += S::NT) Ks[i] = args.Kpad[i];
+    if (MODE == kModeGrad)
+        for (int i = tid; i < MK * MK + 5 * NW; i += S::NT) acc64[i] = 0.0;
+    __syncthreads();
+    const float B0 = Ks[MK * KP];
+
+    // kernel rows owned by this warp in the backward pass (balanced split)
+    const int a_lo = (warp * MK) / NW;
+    const int nqb = ((warp + 1) * MK) / NW - a_lo;
+
+    for (int tile = blockIdx.x; tile < args.n_tiles; tile += gridDim.x) {
+        const int ty0 = (tile / args.tiles_x) * TH;
+        const int tx0 = (tile % args.tiles_x) * kTW;
+
+        // ---- 1. stage the R tile (+ halo); outside the image -> 0
+        for (int i = tid; i < S::RROWS * RP; i += S::NT) {
+            const int r = i / RP, c = i - r * RP;
+            const int gy = ty0 + r, gx = tx0 + c;
+            float v = 0.f;
+            if (gy < args.H && gx < args.W) v = __ldg(args.R + (size_t)gy * args.ld + gx);
+            Rs[i] = v;
+        }
+        __syncthreads();
+
+        // ---- 2. forward: acc[q][p] = sum_{a,b} K[a][b] R[y0+q+a][x+p+b]
+        float acc[QF][4];
+#pragma unroll
+        for (int q = 0; q < QF; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
+
+        const float *rbase = Rs + (warp * QF) * RP + 4 * lane;
+#pragma unroll 1
+        for (int r = 0; r < QF + MK - 1; ++r) {
+            float win[RWIN];
+            const float4 *rp4 = reinterpret_cast<const float4 *>(rbase + r * RP);
+#pragma unroll
+            for (int v4 = 0; v4 < RWIN / 4; ++v4) {
+                const float4 t = rp4[v4];
+                win[4 * v4 + 0] = t.x;
+                win[4 * v4 + 1] = t.y;
+                win[4 * v4 + 2] = t.z;
+                win[4 * v4 + 3] = t.w;
+            }
+#pragma unroll
+            for (int q = 0; q < QF; ++q) {
+                const int a = r - q;
+                if (a >= 0 && a < MK) {
+                    const float4 *k4 = reinterpret_cast<const float4 *>(Ks + a * KP);
+#pragma unroll
+                    for (int b4 = 0; b4 < KP / 4; ++b4) {
+                        const float4 kk = k4[b4];
+                        const float kv[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+                        for (int bb = 0; bb < 4; ++bb) {
+                            const int b = 4 * b4 + bb;
+                            if (b < MK) {
+#pragma unroll
+                                for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(kv[bb], win[p + b], acc[q][p]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+
+        // ---- 3. epilogue: loss terms, g -> shared tile
+        float lsum = 0.f, gsum = 0.f, cnt = 0.f, ksum = 0.f, kr2sum = 0.f;
+#pragma unroll
+        for (int q = 0; q < QF; ++q) {
+            const int yl = warp * QF + q;
+            const int y = ty0 + yl;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int xl = 4 * lane + p;
+                const int x = tx0 + xl;
+                float gval = 0.f;
+                if (y < args.Hv && x < args.Wv) {
+                    const size_t off = (size_t)(y + H2) * args.ld + (x + H2);
+                    const bool use = (args.mask == nullptr) || (args.mask[off] != 0);
+                    const float M = acc[q][p] + B0;
+                    const float Iv = __ldg(args.I + off);
+                    const float vm = args.var ? __ldg(args.var + off) : args.lp.var_scalar;
+                    const float F = args.flat ? __ldg(args.flat + off) : 1.0f;
+                    float g, z, kap;
+                    const float ell = pixel_loss(args.lp, Iv, M, vm, F, g, z, kap);
+                    if (MODE == kModeGrad) {
+                        if (use) {
+                            const float rc = Rs[(yl + H2) * RP + xl + H2];
+                            lsum += ell;
+                            gsum += g;
+                            cnt += 1.f;
+                            ksum += kap;
+                            kr2sum = fmaf(kap * rc, rc, kr2sum);
+                            gval = g;
+                        }
+                    } else {
+                        if (args.diff_out) args.diff_out[(size_t)y * args.Wv + x] = Iv - M;
+                        if (args.mask_out && use && fabsf(z) > args.clip_kappa) args.mask_out[off] = 0;
+                    }
+                }
+                if (MODE == kModeGrad) gs[yl * kTW + xl] = gval;
+            }
+        }
+        if (MODE != kModeGrad) {
+            __syncthreads();  // Rs reused by the next tile
+            continue;
+        }
+        lsum = warp_sum(lsum);
+        gsum = warp_sum(gsum);
+        cnt = warp_sum(cnt);
+        ksum = warp_sum(ksum);
+        kr2sum = warp_sum(kr2sum);
+        if (lane == 0) {
+            double *w5 = acc64 + MK * MK + 5 * warp;
+            w5[0] += (double)lsum;
+            w5[1] += (double)gsum;
+            w5[2] += (double)cnt;
+            w5[3] += (double)kr2sum;
+            w5[4] += (double)ksum;
+        }
+        __syncthreads();  // g tile complete
+
+        // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b], a in [a_lo, a_lo+nqb)
+        float dk[QB][MK];
+#pragma unroll
+        for (int qb = 0; qb < QB; ++qb)
+#pragma unroll
+            for (int b = 0; b < MK; ++b) dk[qb][b] = 0.f;
+
+        const float *rb2 = Rs + a_lo * RP + 4 * lane;
+        const float *gb = gs + 4 * lane;
+#pragma unroll 1
+        for (int rr = 0; rr < TH + nqb - 1; ++rr) {
+            float win[RWIN];
+            const float4 *rp4 = reinterpret_cast<const float4 *>(rb2 + rr * RP);
+#pragma unroll
+            for (int v4 = 0; v4 < RWIN / 4; ++v4) {
+                const float4 t = rp4[v4];
+                win[4 * v4 + 0] = t.x;
+                win[4 * v4 + 1] = t.y;
+                win[4 * v4 + 2] = t.z;
+                win[4 * v4 + 3] = t.w;
+            }
+#pragma unroll
+            for (int qb = 0; qb < QB; ++qb) {
+                const int y = rr - qb;
+                if (qb < nqb && y >= 0 && y < TH) {
+                    const float4 g4 = *reinterpret_cast<const float4 *>(gb + y * kTW);
+#pragma unroll
+                    for (int b = 0; b < MK; ++b) {
+                        float t = dk[qb][b];
+                        t = fmaf(g4.x, win[b + 0], t);
+                        t = fmaf(g4.y, win[b + 1], t);
+                        t = fmaf(g4.z, win[b + 2], t);
+                        t = fmaf(g4.w, win[b + 3], t);
+                        dk[qb][b] = t;
+                    }
+                }
+            }
+        }
+        // ---- 5. tile sums -> float64 (each kernel row is owned by one warp)
+#pragma unroll
+        for (int qb = 0; qb < QB; ++qb) {
+            if (qb < nqb) {
+#pragma unroll
+                for (int b = 0; b < MK; ++b) {
+                    const float s = warp_sum(dk[qb][b]);
+                    if (lane == 0) acc64[(a_lo + qb) * MK + b] += (double)s;
+                }
+            }
+        }
+        __syncthreads();  // Rs, gs reused by the next tile
+    }
+
+    if (MODE == kModeGrad) {
+        __syncthreads();
+        double *out = args.partials + (size_t)blockIdx.x * S::NP;
+        for (int i = tid; i < MK * MK; i += S::NT) out[1 + i] = acc64[i];
+        if (tid < 5) {
+            // tid 0: loss, 1: dB0, 2: pixel count, 3: sum kappa R^2, 4: sum kappa
+            double t = 0.0;
+            for (int w = 0; w < NW; ++w) t += acc64[MK * MK + 5 * w + tid];
+            out[tid == 0 ? 0 : MK * MK + tid] = t;
+        }
+    }
+}
+
+}  // namespace dia

@@ -1,0 +1,631 @@
+// Reduction, optimiser, initialisation and median kernels (see dia_ops.cuh).
+#include <cmath>
+#include <cstring>
+
+#include "dia_ops.cuh"
+
+namespace dia {
+
+// ----------------------------------------------------------------------------
+// Float64 sum of the per-CTA partials in a fixed order (bitwise repeatable).
+// Block b handles entries [32b, 32b+32); its 8 warps take every 8th CTA row.
+__global__ void __launch_bounds__(256) reduce_kernel(const double *__restrict__ partials, int G,
+                                                     int NP, double *__restrict__ out,
+                                                     const int *done) {
+    if (done != nullptr && *((volatile const int *)done) != 0) return;
+    __shared__ double sh[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (e < NP)
+        for (int g = warp; g < G; g += 8) s += partials[(size_t)g * NP + e];
+    sh[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && e < NP) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += sh[w][lane];
+        out[e] = t;
+    }
+}
+
+cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
+                          cudaStream_t s) {
+    reduce_kernel<<<(NP + 31) / 32, 256, 0, s>>>(partials, G, NP, out, done);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ void write_kpad(const double *th, int mk, int kp, float *Kpad, int tid,
+                                           int nt) {
+    for (int i = tid; i < mk * kp; i += nt) {
+        const int a = i / kp, b = i - a * kp;
+        Kpad[i] = (b < mk) ? (float)th[a * mk + b] : 0.f;
+    }
+    if (tid == 0) {
+        Kpad[mk * kp] = (float)th[mk * mk];
+        Kpad[mk * kp + 1] = Kpad[mk * kp + 2] = Kpad[mk * kp + 3] = 0.f;
+    }
+}
+
+__global__ void prep_kpad_kernel(const double *theta, int mk, int kp, float *Kpad) {
+    write_kpad(theta, mk, kp, Kpad, threadIdx.x, blockDim.x);
+}
+
+cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, float *Kpad, cudaStream_t s) {
+    prep_kpad_kernel<<<1, 256, 0, s>>>(theta, mk, kp, Kpad);
+    return cudaGetLastError();
+}
+
+__global__ void emit_kernel(const double *red, int mk, double *loss, double *grad) {
+    const int n = mk * mk + 1;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) grad[k] = red[1 + k];
+    if (threadIdx.x == 0) *loss = red[0];
+}
+
+cudaError_t launch_emit_loss_grad(const double *red, int mk, double *loss, double *grad,
+                                  cudaStream_t s) {
+    emit_kernel<<<1, 256, 0, s>>>(red, mk, loss, grad);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// One-CTA float64 helpers
+constexpr int kStepThreads = 256;
+
+__device__ double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kStepThreads / 32; ++w) t += sh[w];
+    return t;
+}
+
+__device__ double block_max(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = sh[0];
+#pragma unroll
+    for (int w = 1; w < kStepThreads / 32; ++w) t = fmax(t, sh[w]);
+    return t;
+}
+
+__device__ double dot(const double *x, const double *y, int n, double *sh) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += kStepThreads) s += x[k] * y[k];
+    return block_sum(s, sh);
+}
+
+enum { kActContinue = 0, kActAcceptTrial = 1, kActAcceptLo = 2, kActFail = 3 };
+
+struct StepShared {
+    double red[kStepThreads / 32];
+    double gt[1024];     // scaled gradient at the trial point
+    int act, finish_status, copy_glo;
+    double new_alpha;
+};
+
+__device__ void set_trial(const StepArgs &a, double alpha) {
+    const OptBuffers &b = a.b;
+    for (int k = threadIdx.x; k < a.n; k += kStepThreads) b.trial[k] = b.theta[k] + alpha * b.dir[k];
+    __syncthreads();
+    write_kpad(b.trial, a.mk, a.kp, a.Kpad, threadIdx.x, kStepThreads);
+}
+
+// Finish the pass: theta is the answer; the next evaluation (if any) sees it.
+__device__ void finish(const StepArgs &a, int status) {
+    FitState *st = a.st;
+    for (int k = threadIdx.x; k < a.n; k += kStepThreads) a.b.trial[k] = a.b.theta[k];
+    __syncthreads();
+    write_kpad(a.b.theta, a.mk, a.kp, a.Kpad, threadIdx.x, kStepThreads);
+    if (threadIdx.x == 0) {
+        st->status = status;
+        st->phase = kPhaseDone;
+        st->L_sum = st->L * st->ndata;
+        __threadfence();
+        st->done = 1;
+    }
+}
+
+// Diagonal preconditioner from the curvature sums of the last evaluation:
+// kernel pixels ~ 1/sum(kappa R^2), B0 ~ 1/sum(kappa) (Gauss-Newton diagonal
+// with the kernel-pixel entries approximated by the centre pixel).
+__device__ void update_precond(const StepArgs &a) {
+    const double dk = a.red[a.n + 2], db = a.red[a.n + 3];
+    const double pk = (dk > 0.0 && isfinite(dk)) ? 1.0 / dk : 1.0;
+    const double pb = (db > 0.0 && isfinite(db)) ? 1.0 / db : 1.0;
+    const double N = a.red[a.n + 1];
+    for (int k = threadIdx.x; k < a.n; k += kStepThreads)
+        a.b.pdiag[k] = N * ((k == a.n - 1) ? pb : pk);   // the loss is scaled by 1/N
+}
+
+// New L-BFGS direction by the two-loop recursion (Nocedal & Wright Alg. 7.4)
+// with the initial inverse Hessian tau * pdiag, tau = s'y / y'Py of the newest
+// pair, and the start of its line search.
+__device__ void start_line_search(const StepArgs &a, StepShared &sm) {
+    FitState *st = a.st;
+    const OptBuffers &b = a.b;
+    const int n = a.n, tid = threadIdx.x, H = a.p.history;
+    const int hl = st->hist_len, head = st->hist_head;
+    for (int k = tid; k < n; k += kStepThreads) b.dir[k] = b.grad[k];   // q = g
+    __syncthreads();
+    for (int j = 0; j < hl; ++j) {                                       // newest -> oldest
+        const int i = (head - 1 - j + H) % H;
+        const double al = b.rho[i] * dot(b.S + (size_t)i * n, b.dir, n, sm.red);
+        if (tid == 0) b.ahist[i] = al;
+        for (int k = tid; k < n; k += kStepThreads) b.dir[k] -= al * b.Y[(size_t)i * n + k];
+        __syncthreads();
+    }
+    double tau = 1.0;
+    if (hl > 0) {
+        const int i = (head - 1 + H) % H;
+        const double sy = 1.0 / b.rho[i];
+        double ypy = 0.0;
+        for (int k = tid; k < n; k += kStepThreads) {
+            const double y = b.Y[(size_t)i * n + k];
+            ypy += y * b.pdiag[k] * y;
+        }
+        ypy = block_sum(ypy, sm.red);
+        tau = sy / ypy;
+    }
+    for (int k = tid; k < n; k += kStepThreads) b.dir[k] *= tau * b.pdiag[k];
+    __syncthreads();
+    for (int j = hl - 1; j >= 0; --j) {                                  // oldest -> newest
+        const int i = (head - 1 - j + H) % H;
+        const double be = b.rho[i] * dot(b.Y + (size_t)i * n, b.dir, n, sm.red);
+        const double al = b.ahist[i];
+        for (int k = tid; k < n; k += kStepThreads) b.dir[k] += (al - be) * b.S[(size_t)i * n + k];
+        __syncthreads();
+    }
+    for (int k = tid; k < n; k += kStepThreads) b.dir[k] = -b.dir[k];
+    __syncthreads();
+    double gd0 = dot(b.grad, b.dir, n, sm.red);
+    if (!(gd0 < 0.0) || !isfinite(gd0)) {          // not a descent direction: preconditioned SD
+        for (int k = tid; k < n; k += kStepThreads) b.dir[k] = -b.pdiag[k] * b.grad[k];
+        __syncthreads();
+        gd0 = dot(b.grad, b.dir, n, sm.red);
+        if (tid == 0) st->hist_len = 0;
+    }
+    for (int k = tid; k < n; k += kStepThreads) b.glo[k] = b.grad[k];
+    if (tid == 0) {
+        st->gd0 = gd0;
+        st->alpha = 1.0;   // L-BFGS learning rate 1 (Sec. 2.8)
+        st->lo = 0.0;
+        st->L_lo = st->L;
+        st->gd_lo = gd0;
+        st->hi = -1.0;
+        st->ls_evals = 0;
+    }
+    __syncthreads();
+    set_trial(a, 1.0);
+}
+
+// Line-search decision for the trial alpha (thread 0).  Wolfe conditions, or
+// the approximate Wolfe conditions of Hager & Zhang (2005), which rely on the
+// float64 directional derivative when loss differences fall below the
+// float32 pixel-rounding level; brackets are updated on the sign of phi'.
+__device__ int line_search_decide(FitState *st, double Lt, double gdt, double &na, int &copy_glo) {
+    const double al = st->alpha, L0 = st->L, gd0 = st->gd0;
+    const double delta = 0.1, sigma = 0.9, eps_f = 1e-6 * fabs(L0);
+    copy_glo = 0;
+    const bool wolfe = (Lt <= L0 + delta * al * gd0) && (gdt >= sigma * gd0);
+    const bool approx = (Lt <= L0 + eps_f) && ((2.0 * delta - 1.0) * gd0 >= gdt) && (gdt >= sigma * gd0);
+    if (isfinite(Lt) && (wolfe || approx)) return kActAcceptTrial;
+    if (gdt >= 0.0 || !isfinite(Lt)) {
+        st->hi = al; st->L_hi = Lt; st->gd_hi = isfinite(gdt) ? gdt : 1.0;
+    } else if (Lt <= L0 + eps_f) {
+        st->lo = al; st->L_lo = Lt; st->gd_lo = gdt;
+        copy_glo = 1;
+    } else {
+        st->hi = al; st->L_hi = Lt; st->gd_hi = gdt;   // too high with a negative slope
+    }
+    if (st->hi < 0.0) {
+        na = 5.0 * al;                                  // no bracket yet: expand
+    } else {
+        const double a0 = st->lo, a1 = st->hi, w = a1 - a0;
+        na = 0.5 * (a0 + a1);
+        if (st->gd_hi >= 0.0 && st->gd_hi > st->gd_lo) {   // secant on phi'
+            const double c = (a0 * st->gd_hi - a1 * st->gd_lo) / (st->gd_hi - st->gd_lo);
+            if (isfinite(c) && c > a0 + 0.01 * w && c < a1 - 0.01 * w) na = c;
+        }
+    }
+    st->ls_evals += 1;
+    const bool collapsed = st->hi >= 0.0 && (st->hi - st->lo) <= 1e-13 * fmax(1.0, st->lo);
+    if (st->ls_evals >= 30 || collapsed || na > 1e10) {
+        return (st->lo > 0.0) ? kActAcceptLo : kActFail;
+    }
+    return kActContinue;
+}
+
+__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+    FitState *st = a.st;
+    if (*((volatile int *)&st->done) != 0) return;
+    __shared__ StepShared sm;
+    const OptBuffers &b = a.b;
+    const OptParams &p = a.p;
+    const int n = a.n, tid = threadIdx.x;
+
+    const double N = a.red[n + 1];
+    if (!(N > 0.0)) {
+        finish(a, 6 /* DIA_ERR_DEGENERATE */);
+        return;
+    }
+    const double invN = 1.0 / N;
+    const double Lt = a.red[0] * invN;
+    bool bad = !isfinite(Lt);
+    for (int k = tid; k < n; k += kStepThreads) {
+        const double g = a.red[1 + k] * invN;
+        sm.gt[k] = g;
+        bad |= !isfinite(g);
+    }
+    const int nbad = __syncthreads_or(bad);
+    if (tid == 0) {
+        st->evals += 1;
+        st->ndata = N;
+    }
+    if (nbad) {
+        finish(a, 3 /* DIA_ERR_NONFINITE */);
+        return;
+    }
+
+    int phase = st->phase;
+    if (phase == kPhaseAdam) {
+        const bool sw = (st->it_adam > 0 && fabs(Lt - st->L_prev) <= p.switch_tol * fabs(st->L_prev)) ||
+                        st->it_adam >= p.max_adam;
+        if (!sw) {
+            // Adam step (Kingma & Ba), per-parameter learning rates (Sec. 2.8)
+            const double b1t = st->b1t * p.beta1, b2t = st->b2t * p.beta2;
+            const double bc1 = 1.0 - b1t, bc2 = 1.0 - b2t;
+            for (int k = tid; k < n; k += kStepThreads) {
+                const double g = sm.gt[k];
+                const double m1 = p.beta1 * b.m1[k] + (1.0 - p.beta1) * g;
+                const double m2 = p.beta2 * b.m2[k] + (1.0 - p.beta2) * g * g;
+                b.m1[k] = m1;
+                b.m2[k] = m2;
+                const double lr = (k == n - 1) ? p.lr_b0 : p.lr_kernel;
+                const double th = b.theta[k] - lr * (m1 / bc1) / (sqrt(m2 / bc2) + p.adam_eps);
+                b.theta[k] = th;
+                b.trial[k] = th;
+            }
+            __syncthreads();
+            write_kpad(b.trial, a.mk, a.kp, a.Kpad, tid, kStepThreads);
+            if (tid == 0) {
+                st->b1t = b1t;
+                st->b2t = b2t;
+                st->L_prev = Lt;
+                st->L = Lt;
+                st->it_adam += 1;
+                sm.finish_status = (st->evals >= p.max_evals) ? 4 /* DIA_ERR_MAXITER */ : -1;
+            }
+            __syncthreads();
+            if (sm.finish_status >= 0) finish(a, sm.finish_status);
+            return;
+        }
+        phase = kPhaseLbfgsStart;  // hand over to L-BFGS at the point just evaluated
+    }
+
+    if (phase == kPhaseLbfgsStart) {
+        update_precond(a);
+        double mx = 0.0;
+        for (int k = tid; k < n; k += kStepThreads) {
+            b.grad[k] = sm.gt[k];
+            mx = fmax(mx, fabs(sm.gt[k]));
+        }
+        const double ginf = block_max(mx, sm.red);
+        if (tid == 0) {
+            st->L = Lt;
+            st->L_sum = Lt * N;
+            st->grad_inf = ginf;
+            st->hist_len = 0;
+            st->hist_head = 0;
+            st->ls_restarts = 0;
+            st->phase = kPhaseLbfgs;
+        }
+        __syncthreads();
+        if (ginf < p.grad_tol) {
+            finish(a, 0);
+            return;
+        }
+        start_line_search(a, sm);
+        return;
+    }
+
+    // ---- L-BFGS line search: trial = theta + alpha * dir was evaluated
+    const double gdt = dot(sm.gt, b.dir, n, sm.red);
+    if (tid == 0) {
+        double na = st->alpha;
+        int copy_glo = 0;
+        int act = line_search_decide(st, Lt, gdt, na, copy_glo);
+        if (act == kActContinue && st->evals >= p.max_evals) act = (st->lo > 0.0) ? kActAcceptLo : kActFail;
+        sm.act = act;
+        sm.copy_glo = copy_glo;
+        sm.new_alpha = na;
+    }
+    __syncthreads();
+    const int act = sm.act;
+    if (sm.copy_glo)
+        for (int k = tid; k < n; k += kStepThreads) b.glo[k] = sm.gt[k];
+    __syncthreads();
+
+    if (act == kActContinue) {
+        if (tid == 0) st->alpha = sm.new_alpha;
+        set_trial(a, sm.new_alpha);
+        return;
+    }
+    if (act == kActFail) {
+        // restart from preconditioned steepest descent (at most twice in a
+        // row), else stop: no decrease is found at this precision
+        if (tid == 0) {
+            sm.finish_status = -1;
+            if (st->evals >= p.max_evals) {
+                sm.finish_status = 4; /* DIA_ERR_MAXITER */
+            } else if (st->hist_len > 0 && st->ls_restarts < 2) {
+                st->hist_len = 0;
+                st->ls_restarts += 1;
+            } else {
+                sm.finish_status = st->it_lbfgs > 0 ? 0 : 5 /* DIA_ERR_LINESEARCH */;
+            }
+        }
+        __syncthreads();
+        if (sm.finish_status < 0)
+            start_line_search(a, sm);
+        else
+            finish(a, sm.finish_status);
+        return;
+    }
+
+    // ---- accept: the trial point, or the best point of the search
+    const bool use_trial = (act == kActAcceptTrial);
+    const double aacc = use_trial ? st->alpha : st->lo;
+    const double Lacc = use_trial ? Lt : st->L_lo;
+    const double *gacc = use_trial ? sm.gt : b.glo;
+    const int H = p.history, head = st->hist_head;
+    double *Sn = b.S + (size_t)head * n, *Yn = b.Y + (size_t)head * n;
+    for (int k = tid; k < n; k += kStepThreads) {
+        Sn[k] = aacc * b.dir[k];
+        Yn[k] = gacc[k] - b.grad[k];
+    }
+    __syncthreads();
+    const double sy = dot(Sn, Yn, n, sm.red);
+    const double yy = dot(Yn, Yn, n, sm.red);
+    double mx = 0.0;
+    for (int k = tid; k < n; k += kStepThreads) {
+        b.theta[k] += Sn[k];
+        b.grad[k] = gacc[k];
+        mx = fmax(mx, fabs(gacc[k]));
+    }
+    const double ginf = block_max(mx, sm.red);
+    if (use_trial) update_precond(a);
+    if (tid == 0) {
+        const double Lold = st->L;
+        if (sy > 1e-12 * yy && sy > 0.0) {   // curvature pair kept only if y's > 0
+            b.rho[head] = 1.0 / sy;
+            st->hist_head = (head + 1) % H;
+            st->hist_len = min(st->hist_len + 1, H);
+        }
+        st->L = Lacc;
+        st->L_sum = Lacc * N;
+        st->grad_inf = ginf;
+        st->it_lbfgs += 1;
+        st->ls_restarts = 0;
+        // convergence (Sec. 2.8): every |dL/dtheta| below grad_tol, or the
+        // relative loss change between steps below rel_tol
+        if (ginf < p.grad_tol || fabs(Lold - Lacc) <= p.rel_tol * fabs(Lacc))
+            sm.finish_status = 0;
+        else if (st->it_lbfgs >= p.max_lbfgs || st->evals >= p.max_evals)
+            sm.finish_status = 4; /* DIA_ERR_MAXITER */
+        else
+            sm.finish_status = -1;
+    }
+    __syncthreads();
+    if (sm.finish_status >= 0) {
+        finish(a, sm.finish_status);
+        return;
+    }
+    start_line_search(a, sm);
+}
+
+cudaError_t launch_step(const StepArgs &a, cudaStream_t s) {
+    step_kernel<<<1, kStepThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Initialisation: K box-car (1/m^2) or a normalised Gaussian (Sec. 2.8, Sec. 5.1),
+// B0 = median of the unmasked valid target pixels; or theta already in place.
+__global__ void init_kernel(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int mode,
+                            double sigma, const SelectState *sel, int start_phase) {
+    __shared__ double sh[kStepThreads / 32];
+    const int n = mk * mk + 1, tid = threadIdx.x, h = mk / 2;
+    if (mode == 0 || mode == 1) {
+        double w = 0.0;
+        for (int k = tid; k < n - 1; k += kStepThreads) {
+            double v = 1.0;
+            if (mode == 1) {
+                const int a = k / mk - h, c = k % mk - h;
+                v = exp(-(double)(a * a + c * c) / (2.0 * sigma * sigma));
+            }
+            b.theta[k] = v;
+            w += v;
+        }
+        w = block_sum(w, sh);
+        for (int k = tid; k < n - 1; k += kStepThreads) b.theta[k] /= w;
+        if (tid == 0) b.theta[n - 1] = sel->median;
+    }
+    __syncthreads();
+    for (int k = tid; k < n; k += kStepThreads) {
+        b.trial[k] = b.theta[k];
+        b.m1[k] = 0.0;
+        b.m2[k] = 0.0;
+    }
+    __syncthreads();
+    write_kpad(b.theta, mk, kp, Kpad, tid, kStepThreads);
+    if (tid == 0) {
+        FitState z;
+        memset(&z, 0, sizeof(z));
+        z.b1t = 1.0;
+        z.b2t = 1.0;
+        z.phase = start_phase;
+        z.median = sel ? sel->median : 0.0;
+        if (sel && sel->degenerate) {
+            z.status = 6; /* DIA_ERR_DEGENERATE */
+            z.phase = kPhaseDone;
+            z.done = 1;
+        }
+        *st = z;
+    }
+}
+
+cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,
+                        double init_sigma, const SelectState *sel, int start_phase,
+                        cudaStream_t s) {
+    init_kernel<<<1, kStepThreads, 0, s>>>(st, b, Kpad, mk, kp, init_mode, init_sigma, sel,
+                                           start_phase);
+    return cudaGetLastError();
+}
+
+// Restart the optimiser from the accepted theta (refit after clipping): the
+// next evaluation at theta starts L-BFGS afresh.
+__global__ void restart_kernel(FitState *st, float *Kpad, OptBuffers b, int mk, int kp) {
+    const int n = mk * mk + 1;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) b.trial[k] = b.theta[k];
+    __syncthreads();
+    write_kpad(b.theta, mk, kp, Kpad, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) {
+        st->done = 0;
+        st->phase = kPhaseLbfgsStart;
+        st->status = 0;
+        st->hist_len = 0;
+        st->hist_head = 0;
+        st->ls_restarts = 0;
+    }
+}
+
+cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp,
+                           cudaStream_t s) {
+    restart_kernel<<<1, 256, 0, s>>>(st, Kpad, b, mk, kp);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Exact median by radix select over the order-preserving keys of the unmasked
+// valid target pixels: three histogram passes (11, 11, 10 bits) per rank, for
+// the two middle ranks (N-1)/2 and N/2; the median is their mean.
+constexpr int kBins = 2048;
+
+__global__ void hist_kernel(const float *__restrict__ I, const uint8_t *__restrict__ mask, int H,
+                            int W, int ld, int h, uint32_t *__restrict__ hist,
+                            const SelectState *sel, int slot, int pass) {
+    __shared__ uint32_t sh[kBins];
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int Hv = H - 2 * h, Wv = W - 2 * h;
+    const long long total = (long long)Hv * Wv;
+    const uint32_t pre = (pass == 0) ? 0u : sel->prefix[slot];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / Wv), x = (int)(i - (long long)y * Wv);
+        const size_t off = (size_t)(y + h) * ld + (x + h);
+        if (mask && mask[off] == 0) continue;
+        const uint32_t k = float_key(I[off]);
+        uint32_t bin;
+        if (pass == 0) {
+            bin = k >> 21;
+        } else if (pass == 1) {
+            if ((k >> 21) != (pre >> 21)) continue;
+            bin = (k >> 10) & 0x7ffu;
+        } else {
+            if ((k >> 10) != (pre >> 10)) continue;
+            bin = k & 0x3ffu;
+        }
+        atomicAdd(&sh[bin], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+__global__ void select_kernel(uint32_t *hist, SelectState *sel, int slot, int pass) {
+    // one thread walks the bins (at most 2048)
+    if (threadIdx.x == 0) {
+        if (pass == 0 && slot == 0) {
+            unsigned long long tot = 0;
+            for (int i = 0; i < kBins; ++i) tot += hist[i];
+            sel->count = tot;
+            sel->degenerate = (tot == 0);
+            sel->rank[0] = tot ? (uint32_t)((tot - 1) / 2) : 0u;
+            sel->rank[1] = tot ? (uint32_t)(tot / 2) : 0u;
+        }
+        const int shift = (pass == 0) ? 21 : (pass == 1 ? 10 : 0);
+        const int nb = (pass == 2) ? 1024 : 2048;
+        uint32_t k = sel->rank[slot];
+        unsigned long long cum = 0;
+        int bin = nb - 1;
+        for (int i = 0; i < nb; ++i) {
+            if (cum + hist[i] > k) {
+                bin = i;
+                break;
+            }
+            cum += hist[i];
+        }
+        sel->rank[slot] = (uint32_t)(k - cum);
+        sel->prefix[slot] = (pass == 0 ? 0u : sel->prefix[slot]) | ((uint32_t)bin << shift);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) hist[i] = 0;
+}
+
+__device__ inline float key_float(uint32_t k) {
+    const uint32_t u = (k & 0x80000000u) ? (k ^ 0x80000000u) : ~k;
+    return __uint_as_float(u);
+}
+
+__global__ void median_finish_kernel(SelectState *sel) {
+    if (threadIdx.x == 0)
+        sel->median = sel->degenerate ? 0.0
+                                      : 0.5 * ((double)key_float(sel->prefix[0]) +
+                                               (double)key_float(sel->prefix[1]));
+}
+
+__global__ void zero_u32(uint32_t *p, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+}
+
+cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int ld, int mk,
+                          uint32_t *hist, SelectState *sel, int grid, cudaStream_t s) {
+    const int h = mk / 2;
+    zero_u32<<<1, 1024, 0, s>>>(hist, kBins);
+    for (int slot = 0; slot < 2; ++slot)
+        for (int pass = 0; pass < 3; ++pass) {
+            hist_kernel<<<grid, 512, 0, s>>>(I, mask, H, W, ld, h, hist, sel, slot, pass);
+            select_kernel<<<1, 1024, 0, s>>>(hist, sel, slot, pass);
+        }
+    median_finish_kernel<<<1, 32, 0, s>>>(sel);
+    return cudaGetLastError();
+}
+
+__global__ void pack_kernel(const double *theta, int mk, double *theta_out, float *K_out,
+                            float *b0_out) {
+    const int n = mk * mk + 1;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        if (theta_out) theta_out[k] = theta[k];
+        if (K_out && k < n - 1) K_out[k] = (float)theta[k];
+    }
+    if (threadIdx.x == 0 && b0_out) *b0_out = (float)theta[n - 1];
+}
+
+cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, float *K_out,
+                                float *b0_out, cudaStream_t s) {
+    pack_kernel<<<1, 256, 0, s>>>(theta, mk, theta_out, K_out, b0_out);
+    return cudaGetLastError();
+}
+
+}  // namespace dia

@@ -1,0 +1,93 @@
+// Small kernels around the fused evaluation: the float64 cross-CTA reduction,
+// the on-device optimiser (Adam, then L-BFGS with a strong-Wolfe line search,
+// Sec. 2.3 and Sec. 2.8), initialisation (box-car or Gaussian kernel, B0 =
+// median of the target, Sec. 2.8) and output packing.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dia {
+
+constexpr int kHistMax = 128;  // largest L-BFGS memory
+
+enum Phase { kPhaseAdam = 0, kPhaseLbfgs = 1, kPhaseLbfgsStart = 2, kPhaseDone = 3 };
+
+// Optimiser state, float64, resident in the caller's workspace.  The first
+// fields are read back by the host after every graph launch.
+struct FitState {
+    int done;        // 1 once the fit pass has finished (evaluation kernels exit early)
+    int phase;       // Phase
+    int status;      // dia_status of the pass
+    int it_adam, it_lbfgs, evals;
+    int ls_evals, hist_len, hist_head, ls_restarts, pad0, pad1;
+    double ndata;    // unmasked valid pixels of the last evaluation
+    double L;        // scaled loss (L_sum / N) at the accepted theta
+    double L_sum;    // unscaled loss at the accepted theta
+    double grad_inf; // max |g| of the scaled loss at the accepted theta
+    double L_prev;   // previous Adam loss
+    double gd0;      // phi'(0) of the current line search
+    double alpha;    // step being evaluated
+    double lo, L_lo, gd_lo, hi, L_hi, gd_hi;  // line-search bracket (hi < 0: none yet)
+    double b1t, b2t; // Adam beta powers
+    double median;   // B0 initialisation
+};
+
+struct OptParams {
+    double lr_kernel, lr_b0, beta1, beta2, adam_eps, switch_tol;
+    double rel_tol, grad_tol;
+    int max_adam, history, max_lbfgs, max_evals;
+};
+
+// Float64 vectors of the optimiser (n = m*m + 1 each, S and Y are history x n;
+// pdiag is the diagonal preconditioner, an approximate inverse Hessian diagonal).
+struct OptBuffers {
+    double *theta, *trial, *grad, *glo, *m1, *m2, *dir, *S, *Y, *rho, *ahist, *pdiag;
+};
+
+struct StepArgs {
+    FitState *st;
+    OptBuffers b;
+    const double *red;   // reduced partials: loss, dK[m*m], dB0, count, sum kR^2, sum k
+    float *Kpad;         // float32 copy of the trial theta for the next evaluation
+    int n, mk, kp;
+    OptParams p;
+};
+
+// Order-preserving map float -> uint32 (for the radix-select median).
+__host__ __device__ inline uint32_t float_key(float f) {
+#ifdef __CUDA_ARCH__
+    uint32_t u = __float_as_uint(f);
+#else
+    uint32_t u;
+    memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+struct SelectState {
+    uint32_t prefix[2];
+    uint32_t rank[2];
+    unsigned long long count;
+    int degenerate;
+    double median;
+};
+
+// host launchers (dia_ops.cu)
+cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
+                          cudaStream_t s);
+cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, float *Kpad, cudaStream_t s);
+cudaError_t launch_emit_loss_grad(const double *red, int mk, double *loss, double *grad,
+                                  cudaStream_t s);
+cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,
+                        double init_sigma, const SelectState *sel, int start_phase,
+                        cudaStream_t s);
+cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp,
+                           cudaStream_t s);
+cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int ld, int mk,
+                          uint32_t *hist, SelectState *sel, int grid, cudaStream_t s);
+cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, float *K_out,
+                                float *b0_out, cudaStream_t s);
+
+}  // namespace dia

@@ -1,0 +1,278 @@
+"""ctypes binding of the C ABI in ``include/dia.h`` (argument marshalling only).
+
+Every function here forwards to the CUDA library ``_dia_cuda.so``; there is no
+CPU path.  If the library is missing the import of this module raises.  PyTorch
+supplies device memory (images, outputs, the workspace) and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_dia_cuda.so")
+
+DIA_OK, DIA_ERR_ARG, DIA_ERR_CUDA, DIA_ERR_NONFINITE, DIA_ERR_MAXITER = 0, 1, 2, 3, 4
+DIA_ERR_LINESEARCH, DIA_ERR_DEGENERATE, DIA_ERR_TIMEOUT, DIA_ERR_WORKSPACE = 5, 6, 7, 8
+DIA_ERR_UNSUPPORTED = 9
+DIA_MAX_M = 31
+RHO = {"gauss": 0, "huber": 1, "cauchy": 2}
+VAR = {"fixed": 0, "ccd": 1, "emccd": 2}
+MEM_DEVICE, MEM_HOST = 0, 1
+
+
+class LossSpec(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_int32), ("var_model", ctypes.c_int32),
+                ("sigma0", ctypes.c_float), ("gain", ctypes.c_float),
+                ("excess", ctypes.c_float), ("huber_c", ctypes.c_float),
+                ("var_scalar", ctypes.c_float), ("var_floor", ctypes.c_float)]
+
+
+class Pair(ctypes.Structure):
+    _fields_ = [("ref", ctypes.c_void_p), ("img", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("var", ctypes.c_void_p), ("flat", ctypes.c_void_p),
+                ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("ld", ctypes.c_int32),
+                ("m", ctypes.c_int32), ("mem", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("lr_kernel", ctypes.c_double), ("lr_b0", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("adam_eps", ctypes.c_double), ("switch_tol", ctypes.c_double),
+                ("max_adam_iters", ctypes.c_int32), ("history", ctypes.c_int32),
+                ("rel_tol", ctypes.c_double), ("grad_tol", ctypes.c_double),
+                ("max_lbfgs_iters", ctypes.c_int32), ("max_evals", ctypes.c_int32),
+                ("clip_passes", ctypes.c_int32), ("clip_kappa", ctypes.c_float),
+                ("init", ctypes.c_int32), ("init_sigma", ctypes.c_double),
+                ("theta0", ctypes.c_void_p), ("graph_iters", ctypes.c_int32),
+                ("timeout_s", ctypes.c_double)]
+
+
+class FitInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("adam_iters", ctypes.c_int32),
+                ("lbfgs_iters", ctypes.c_int32), ("evals", ctypes.c_int32),
+                ("clip_passes_done", ctypes.c_int32), ("ndata", ctypes.c_int64),
+                ("loss", ctypes.c_double), ("grad_inf", ctypes.c_double),
+                ("scale", ctypes.c_double), ("b0", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every symbol include/dia.h declares, with its ctypes signature.
+_P = ctypes.POINTER
+_SIGS = {
+    "dia_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
+    "dia_abi_version": (ctypes.c_int32, []),
+    "dia_last_cuda_error": (ctypes.c_int32, []),
+    "dia_opts_default": (ctypes.c_int32, [_P(Opts)]),
+    "dia_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 6),
+    "dia_loss_grad": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.c_void_p]),
+    "dia_diff_image": (ctypes.c_int32, [_P(Pair), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "dia_fit": (ctypes.c_int32, [_P(Pair), _P(LossSpec), _P(Opts), ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, _P(FitInfo), ctypes.c_void_p, ctypes.c_size_t,
+                                 ctypes.c_void_p]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build() "
+            "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class DiaError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        name = lib.dia_status_str(status).decode()
+        extra = f" (cuda error {lib.dia_last_cuda_error()})" if status == DIA_ERR_CUDA else ""
+        super().__init__(f"{what}: {name}{extra}")
+
+
+def _check(status, what):
+    if status != DIA_OK:
+        raise DiaError(status, what)
+
+
+def status_str(s: int) -> str:
+    return lib.dia_status_str(s).decode()
+
+
+def loss_spec(rho="gauss", noise="fixed", sigma0=0.0, gain=1.0, excess=2.0, huber_c=1.345,
+              var=1.0, var_floor=1e-6, **_ignored) -> LossSpec:
+    """dia_loss_spec from the plain loss keys shared with the oracle."""
+    return LossSpec(RHO[rho], VAR[noise], sigma0, gain, excess, huber_c, var, var_floor)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _check(lib.dia_opts_default(ctypes.byref(o)), "dia_opts_default")
+    for k, v in kw.items():
+        if k == "theta0":
+            raise ValueError("pass theta0 to fit()")
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _img(t, H, W, name, dtype=torch.float32):
+    if t is None:
+        return None
+    if t.dtype != dtype or t.dim() != 2 or tuple(t.shape) != (H, W) or t.stride(1) != 1:
+        raise ValueError(f"{name}: expected a row-major {dtype} tensor of shape {(H, W)}")
+    return t
+
+
+def make_pair(R, I, m, mask=None, var=None, flat=None):
+    """dia_pair over torch tensors (all on one CUDA device, or all on the host
+    in pinned or pageable memory).  Returns (pair, keep-alive list)."""
+    H, W = R.shape
+    ld = R.stride(0)
+    host = not R.is_cuda
+    for name, t in (("I", I), ("mask", mask), ("var", var), ("flat", flat)):
+        if t is not None:
+            if t.is_cuda == host:
+                raise ValueError(f"{name} must live where R lives")
+            if t.stride(0) != ld:
+                raise ValueError(f"{name} must share R's row pitch")
+    _img(R, H, W, "R")
+    _img(I, H, W, "I")
+    _img(mask, H, W, "mask", torch.uint8)
+    _img(var, H, W, "var")
+    _img(flat, H, W, "flat")
+    p = Pair(R.data_ptr(), I.data_ptr(), mask.data_ptr() if mask is not None else None,
+             var.data_ptr() if var is not None else None,
+             flat.data_ptr() if flat is not None else None, H, W, ld, m,
+             MEM_HOST if host else MEM_DEVICE)
+    return p, [R, I, mask, var, flat]
+
+
+def workspace_size(H, W, m, ld=None, clip=False, host=False) -> int:
+    n = lib.dia_workspace_size(H, W, ld or W, m, int(bool(clip)), MEM_HOST if host else MEM_DEVICE)
+    if n == 0:
+        raise DiaError(DIA_ERR_ARG, "dia_workspace_size")
+    return n
+
+
+def workspace(H, W, m, ld=None, clip=False, host=False, device=None) -> torch.Tensor:
+    """A device workspace tensor (256-byte aligned by the caching allocator)."""
+    n = workspace_size(H, W, m, ld, clip, host)
+    return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
+def loss_grad(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, ws=None,
+              stream=None):
+    """One fused evaluation on the device: returns (loss[1], grad[n]) float64 tensors."""
+    pair, keep = make_pair(R, I, m, mask, var, flat)
+    if not R.is_cuda:
+        raise ValueError("loss_grad takes device tensors")
+    theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
+    n = m * m + 1
+    if theta.numel() != n:
+        raise ValueError(f"theta must have {n} entries")
+    ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
+    loss = torch.empty(1, dtype=torch.float64, device=R.device)
+    grad = torch.empty(n, dtype=torch.float64, device=R.device)
+    st = lib.dia_loss_grad(ctypes.byref(pair), ctypes.byref(spec), _ptr(theta), _ptr(loss),
+                           _ptr(grad), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "dia_loss_grad")
+    return loss, grad
+
+
+def diff_image(R, I, m, theta, ws=None, stream=None):
+    pair, keep = make_pair(R, I, m)
+    theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
+    ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
+    h = m // 2
+    out = torch.empty((pair.H - 2 * h, pair.W - 2 * h), dtype=torch.float32, device=R.device)
+    _check(lib.dia_diff_image(ctypes.byref(pair), _ptr(theta), _ptr(out), _ptr(ws), ws.numel(),
+                              _stream(stream)), "dia_diff_image")
+    return out
+
+
+def fit(R, I, m, spec: LossSpec, opts: Opts = None, mask=None, var=None, flat=None,
+        theta0=None, want_diff=True, want_mask=False, ws=None, stream=None, check=True):
+    """dia_fit.  Tensors on one CUDA device, or all on the host (the library
+    then stages them through the workspace and returns host tensors).
+    Returns dict(theta, K, b0, diff, mask, info)."""
+    pair, keep = make_pair(R, I, m, mask, var, flat)
+    host = pair.mem == MEM_HOST
+    dev = R.device
+    opts = opts if opts is not None else default_opts()
+    o = Opts.from_buffer_copy(opts)
+    th0 = None
+    if theta0 is not None:
+        th0 = np.ascontiguousarray(np.asarray(theta0, dtype=np.float64))
+        o.theta0 = th0.ctypes.data
+        o.init = 2
+    clip = o.clip_passes > 0 or want_mask
+    if ws is None:
+        ws = workspace(pair.H, pair.W, m, pair.ld, clip, host,
+                       device=None if host else dev)
+    n = m * m + 1
+    h = m // 2
+    kw = dict(device=dev)
+    if host:
+        kw["pin_memory"] = R.is_pinned()
+    theta = torch.empty(n, dtype=torch.float64, **kw)
+    K = torch.empty((m, m), dtype=torch.float32, **kw)
+    b0 = torch.empty(1, dtype=torch.float32, **kw)
+    diff = torch.empty((pair.H - 2 * h, pair.W - 2 * h), dtype=torch.float32, **kw) \
+        if want_diff else None
+    mk = torch.empty((pair.H, pair.ld), dtype=torch.uint8, **kw)[:, :pair.W] \
+        if want_mask else None
+    info = FitInfo()
+    st = lib.dia_fit(ctypes.byref(pair), ctypes.byref(spec), ctypes.byref(o), _ptr(theta),
+                     _ptr(K), _ptr(b0), _ptr(diff), _ptr(mk), ctypes.byref(info), _ptr(ws),
+                     ws.numel(), _stream(stream))
+    if check and st not in (DIA_OK, DIA_ERR_MAXITER):
+        raise DiaError(st, "dia_fit")
+    return dict(theta=theta, K=K, b0=b0, diff=diff, mask=mk, info=info.as_dict(), status=st)
+
+
+class DiaLossGrad(torch.autograd.Function):
+    """L(theta) with the hand-written fused backward (Sec. 2.3).
+
+    forward runs one fused pass that returns the loss and keeps only the
+    gradient vector (m*m + 1 float64 values): no model image or other
+    activation is stored; backward scales that gradient by grad_output."""
+
+    @staticmethod
+    def forward(ctx, theta, R, I, m, spec, mask=None, var=None, flat=None):
+        loss, grad = loss_grad(R, I, m, theta.detach(), spec, mask, var, flat)
+        ctx.save_for_backward(grad)
+        return loss.reshape(()).to(theta.dtype)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (grad,) = ctx.saved_tensors
+        return (gout * grad).to(gout.dtype), None, None, None, None, None, None, None
+
+
+def dia_loss(theta, R, I, m, spec, mask=None, var=None, flat=None):
+    return DiaLossGrad.apply(theta, R, I, m, spec, mask, var, flat)

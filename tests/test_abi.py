@@ -1,0 +1,82 @@
+"""The C-ABI library loads and exports every entry point include/dia.h
+declares; host-side argument checks need no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dia.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dia_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    import __graft_entry__ as g
+    from paper_2104_13715_gb300 import build
+    build.build()
+    from paper_2104_13715_gb300 import native
+    return native
+
+
+def test_every_declared_symbol_is_exported(native):
+    names = _declared()
+    assert "dia_fit" in names and "dia_loss_grad" in names
+    lib = ctypes.CDLL(native.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding wraps each of them
+    assert set(names) <= set(native._SIGS)
+
+
+def test_status_strings_and_version(native):
+    assert native.status_str(0) == "DIA_OK"
+    assert native.status_str(9) == "DIA_ERR_UNSUPPORTED"
+    assert native.lib.dia_abi_version() == 1
+
+
+def test_default_opts_are_the_paper_values(native):
+    o = native.default_opts()
+    assert o.lr_kernel == 1e-3            # Sec. 2.8
+    assert o.switch_tol == 1e-6           # Sec. 2.8
+    assert o.clip_kappa == 5.0            # Sec. 4.2
+    assert o.grad_tol == 1e-7             # Sec. 2.8
+
+
+@pytest.mark.parametrize("H,W,ld,m,ok", [(128, 128, 128, 11, True), (10, 10, 10, 11, False),
+                                         (64, 64, 60, 5, False), (64, 64, 64, 4, False),
+                                         (64, 64, 64, 33, False), (33, 40, 48, 31, True),
+                                         (1, 1, 1, 1, True)])
+def test_workspace_size_validation(native, H, W, ld, m, ok):
+    n = native.lib.dia_workspace_size(H, W, ld, m, 0, 0)
+    assert (n > 0) == ok
+    if ok:
+        assert n % 256 == 0
+        assert native.lib.dia_workspace_size(H, W, ld, m, 1, 1) > n
+
+
+def test_arguments_rejected_before_any_launch(native):
+    # NULL pair / bad kernel side: DIA_ERR_ARG without touching a GPU
+    assert native.lib.dia_loss_grad(None, None, None, None, None, None, 0, None) == native.DIA_ERR_ARG
+    p = native.Pair(1, 2, None, None, None, 16, 16, 16, 4, 0)      # even m
+    spec = native.loss_spec()
+    assert native.lib.dia_loss_grad(ctypes.byref(p), ctypes.byref(spec), 1, 1, 1, None, 0,
+                                    None) == native.DIA_ERR_ARG
+    p = native.Pair(1, 2, None, None, None, 40, 40, 40, 33, 0)     # m > DIA_MAX_M
+    assert native.lib.dia_loss_grad(ctypes.byref(p), ctypes.byref(spec), 1, 1, 1, None, 0,
+                                    None) == native.DIA_ERR_UNSUPPORTED
+    bad = native.loss_spec(noise="ccd", gain=0.0)
+    p = native.Pair(1, 2, None, None, None, 16, 16, 16, 3, 0)
+    assert native.lib.dia_loss_grad(ctypes.byref(p), ctypes.byref(bad), 1, 1, 1, None, 0,
+                                    None) == native.DIA_ERR_ARG
+    # workspace too small
+    assert native.lib.dia_loss_grad(ctypes.byref(p), ctypes.byref(spec), 1, 1, 1, 256, 8,
+                                    None) == native.DIA_ERR_WORKSPACE
+    o = native.default_opts(history=0)
+    assert native.lib.dia_fit(ctypes.byref(p), ctypes.byref(spec), ctypes.byref(o), None, None,
+                              None, None, None, None, None, 0, None) == native.DIA_ERR_ARG

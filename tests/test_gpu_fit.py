@@ -1,0 +1,156 @@
+"""Fit parity (dia_fit through the C ABI) with the FP64 oracle optimum.
+
+Tolerances (stated for the whole fit): max |K - K*| <= 1e-4 |sum K*| and
+|B0 - B0*| <= 1e-4 x sky, sky being the target's median background."""
+import numpy as np
+import pytest
+import torch
+from scipy import signal
+
+import oracle
+from paper_2104_13715_gb300 import synth
+from tests._helpers import SPECS, field, ospec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2104_13715_gb300 import native
+    return native
+
+
+def _fit(nat, d, m, spec, opts=None, mask=None, var=None, **kw):
+    dev = torch.device("cuda")
+    t = lambda a, dt=torch.float32: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    return nat.fit(t(d["R"]), t(d["I"]), m, nat.loss_spec(**spec), opts, mask=t(mask, torch.uint8),
+                   var=t(var), **kw)
+
+
+def _check(theta, ref, sky, tol=1e-4):
+    K, Kr = theta[:-1], ref[:-1]
+    ek = np.max(np.abs(K - Kr)) / abs(Kr.sum())
+    eb = abs(theta[-1] - ref[-1]) / sky
+    assert ek <= tol and eb <= tol, (ek, eb)
+    return ek, eb
+
+
+def test_stamp128_m11_chi2_matches_normal_equations(nat):
+    d = synth.workload("stamp128_m11_chi2", seed=0)
+    m = d["m"]
+    out = _fit(nat, d, m, d["loss"])
+    th = out["theta"].cpu().numpy()
+    ref = oracle.normal_solve(d["R"], d["I"], m)
+    _check(th, ref, float(np.median(d["I"])))
+    assert out["info"]["status"] == 0
+    # difference image at the fitted theta
+    D = out["diff"].cpu().numpy()
+    Do = oracle.diff_image(d["R"], d["I"], m, th)
+    assert np.max(np.abs(D - Do)) <= 1e-5 * np.max(np.abs(d["I"]))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_chi2_with_variance_map_and_mask(nat, seed):
+    m = 9
+    d = field(200, 180, m, seed=seed)
+    rng = np.random.default_rng(seed)
+    mask = (rng.random(d["R"].shape) > 0.05).astype(np.uint8)
+    var = (25.0 + np.maximum(d["I"], 0)).astype(np.float32)
+    out = _fit(nat, d, m, SPECS["gauss-fixed"], mask=mask, var=var)
+    ref = oracle.normal_solve(d["R"], d["I"], m, mask=mask, var=var)
+    _check(out["theta"].cpu().numpy(), ref, float(np.median(d["I"])))
+
+
+def _noiseless_pair(seed, shape=(142, 142)):
+    rng = np.random.default_rng(seed)
+    p = synth.PairSpec(size=shape, n_stars=60, m=1, fwhm_ref=2.5, kernel_sigma=0.0, sky=0.0,
+                       ref_noise=False, flux_law="paper")
+    R = synth.make_pair(p, seed)["R"].astype(np.float64)
+    return R, rng
+
+
+def test_noiseless_identity_and_shift(nat):
+    """Sec. 3.4 tests (i) and (iii): the identity and the +1 px shift."""
+    R, _ = _noiseless_pair(0)
+    m = 9
+    for shift, peak in [(0, (4, 4)), (1, (3, 3))]:
+        I = np.full_like(R, 50.0)
+        if shift:
+            I[1:, 1:] += R[:-1, :-1]
+        else:
+            I += R
+        d = dict(R=R.astype(np.float32), I=I.astype(np.float32))
+        out = _fit(nat, d, m, SPECS["gauss-fixed"])
+        th = out["theta"].cpu().numpy()
+        K = th[:-1].reshape(m, m)
+        assert np.unravel_index(np.argmax(K), K.shape) == peak
+        ref = oracle.normal_solve(d["R"], d["I"], m)
+        _check(th, ref, 50.0)
+
+
+def test_noiseless_gaussian_kernel(nat):
+    """Sec. 3.4 test (ii): phi_K = 1.5, recovered with P = sum K."""
+    R, _ = _noiseless_pair(1)
+    m = 11
+    yy, xx = np.mgrid[-5:6, -5:6]
+    Kt = np.exp(-(xx ** 2 + yy ** 2) / (2 * 1.5 ** 2))
+    Kt *= 1.2 / Kt.sum()
+    I = np.full_like(R, 80.0)
+    I[5:-5, 5:-5] = signal.correlate2d(R, Kt, mode="valid") + 80.0
+    d = dict(R=R.astype(np.float32), I=I.astype(np.float32))
+    out = _fit(nat, d, m, SPECS["gauss-fixed"])
+    th = out["theta"].cpu().numpy()
+    ref = oracle.normal_solve(d["R"], d["I"], m)
+    _check(th, ref, 80.0)
+    assert abs(th[:-1].sum() - 1.2) / 1.2 <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["gauss-ccd", "huber-ccd", "gauss-emccd"])
+def test_model_dependent_variance_fit(nat, name):
+    """Nonlinear losses: the GPU optimum vs the oracle's FP64 Newton optimum."""
+    m = 11
+    d = field(256, 256, m, seed=21, sky=150.0)
+    spec = SPECS[name]
+    out = _fit(nat, d, m, spec)
+    th = out["theta"].cpu().numpy()
+    ref = oracle.newton(d["R"], d["I"], m, th, ospec(spec))
+    _check(th, ref, float(np.median(d["I"])))
+
+
+def test_cauchy_clip_fit(nat):
+    """Robust Cauchy loss with a mask, outliers and three clipped refits."""
+    m = 13
+    p = synth.WORKLOADS["ccd4096_m25_cauchy_clip3"]
+    spec = synth.PairSpec(**{**p.__dict__, "size": (320, 300), "n_stars": 350, "m": m})
+    d = synth.make_pair(spec, 3)
+    loss = d["loss"]
+    opts = nat.default_opts(clip_passes=loss["clip_passes"], clip_kappa=loss["kappa"])
+    out = _fit(nat, d, m, loss, opts, mask=d["mask"], var=d["var"], want_mask=True)
+    th = out["theta"].cpu().numpy()
+    mk = out["mask"].cpu().numpy()
+    os_ = oracle.LossSpec(rho="cauchy", noise="fixed")
+    # the returned mask = input mask with |z| > kappa pixels removed (cumulative)
+    assert np.all(mk <= d["mask"])
+    # theta is the optimum for that mask
+    ref = oracle.newton(d["R"], d["I"], m, th, os_, mask=mk, var=d["var"])
+    _check(th, ref, float(np.median(d["I"])))
+    # the last clip pass left no unmasked pixel far beyond kappa at the final theta
+    M = oracle.model(d["R"], ref, m)
+    _, _, _, z = oracle.pixel_terms(d["I"], M, m, os_, mask=None, var=d["var"])
+    h = m // 2
+    keep = mk[h:-h, h:-h] != 0
+    assert np.max(np.abs(z[keep])) <= 5.0 * 1.01
+
+
+def test_host_buffers_end_to_end(nat):
+    """The same fit with host (pinned) buffers staged by the library."""
+    d = synth.workload("stamp128_m11_chi2", seed=3)
+    m = d["m"]
+    R = torch.from_numpy(d["R"]).pin_memory()
+    I = torch.from_numpy(d["I"]).pin_memory()
+    out = nat.fit(R, I, m, nat.loss_spec(**d["loss"]))
+    assert not out["theta"].is_cuda
+    ref = oracle.normal_solve(d["R"], d["I"], m)
+    _check(out["theta"].numpy(), ref, float(np.median(d["I"])))
+    dev = _fit(nat, d, m, d["loss"])
+    assert np.array_equal(dev["theta"].cpu().numpy(), out["theta"].numpy())
