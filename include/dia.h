@@ -118,9 +118,11 @@ typedef struct {
     double switch_tol;         /* |dL/L| between Adam steps that hands over to L-BFGS (1e-6) */
     int32_t max_adam_iters;    /* Adam step cap (5000) */
     int32_t history;           /* L-BFGS memory (100, at most 128) */
-    double rel_tol;            /* stop when |dL/L| between L-BFGS steps < rel_tol (1e-9) */
-    double grad_tol;           /* or when every |dL/dtheta_k| / N_data < grad_tol (1e-7) */
-    int32_t max_lbfgs_iters;   /* L-BFGS iteration cap (1000) */
+    double rel_tol;            /* if > 0: stop when |dL/L| between L-BFGS steps < rel_tol
+                                  (0 = off: the loss is flat along ill-conditioned kernel
+                                  directions, so this test can stop far from the optimum) */
+    double grad_tol;           /* stop when every |dL/dtheta_k| / N_data < grad_tol (1e-7) */
+    int32_t max_lbfgs_iters;   /* L-BFGS iteration cap (3000) */
     int32_t max_evals;         /* cap on loss+gradient evaluations per fit, all passes (20000) */
     int32_t clip_passes;       /* sigma-clip-and-refit passes after the first fit (0) */
     float clip_kappa;          /* clip |z| > kappa (5, Sec. 4.2) */
@@ -131,6 +133,8 @@ typedef struct {
     const double *theta0;      /* HOST pointer, n entries, used when init == 2 */
     int32_t graph_iters;       /* optimiser iterations per CUDA-graph launch (16) */
     double timeout_s;          /* host polling limit per fit (600 s) */
+    int32_t stall_iters;       /* limit of numerical precision: stop when max|dL/dtheta| has
+                                  not halved over this many accepted L-BFGS steps (250) */
 } dia_opts;
 
 typedef struct {
@@ -142,6 +146,10 @@ typedef struct {
     double grad_inf;           /* max |dL/dtheta| / N_data at the end */
     double scale;              /* photometric scale P = sum K (Eq. 3) */
     double b0;                 /* fitted B0 */
+    int32_t reason;            /* why the last pass stopped: 1 grad_tol, 2 rel_tol, 3 stall
+                                  (precision limit), 4 line search, 5 max iterations,
+                                  6 max evaluations, 7 non-finite, 8 degenerate */
+    int64_t kernel_launches;   /* CUDA kernels this call launched (graph nodes included) */
 } dia_fit_info;
 
 /* Human-readable status name (static string). */

@@ -353,9 +353,10 @@ void fill_opts_default(dia_opts *o) {
     o->switch_tol = 1e-6;
     o->max_adam_iters = 5000;
     o->history = 100;
-    o->rel_tol = 1e-9;
+    o->rel_tol = 0.0;
+    o->stall_iters = 250;
     o->grad_tol = 1e-7;
-    o->max_lbfgs_iters = 1000;
+    o->max_lbfgs_iters = 3000;
     o->max_evals = 20000;
     o->clip_passes = 0;
     o->clip_kappa = 5.0f;
@@ -450,7 +451,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         fill_opts_default(&opts);
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.clip_passes < 0 || opts.max_adam_iters < 0 ||
-        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.init < 0 || opts.init > 2 ||
+        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.init < 0 || opts.init > 2 ||
         (opts.init == 2 && !opts.theta0) || (opts.init == 1 && !(opts.init_sigma > 0.0)) ||
         !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
@@ -478,15 +479,18 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
 
     // initial theta (Sec. 2.8)
     const int start_phase = opts.max_adam_iters > 0 ? kPhaseAdam : kPhaseLbfgsStart;
+    long long launches = 0;   // kernels this call launches (graph nodes included)
     if (opts.init == 2) {
         DIA_CK(cudaMemcpyAsync(c.ob.theta, opts.theta0, (size_t)n * 8, cudaMemcpyHostToDevice, s));
         DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, 2, 0.0, nullptr, start_phase, s));
+        launches += 1;
     } else {
         int mgrid = device_sms() * 4;
         DIA_CK(launch_median(c.dp.img, c.ea.mask, H, W, ld, m, (uint32_t *)(c.ws + c.L.hist),
                              c.sel, mgrid, s));
         DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, opts.init, opts.init_sigma, c.sel,
                            start_phase, s));
+        launches += kMedianLaunches + 1;
     }
 
     EvalArgs ea = c.ea;
@@ -512,6 +516,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     sa.p.history = opts.history;
     sa.p.max_lbfgs = opts.max_lbfgs_iters;
     sa.p.max_evals = opts.max_evals;
+    sa.p.stall_iters = opts.stall_iters;
 
     cudaGraphExec_t gx = nullptr;
     rc = get_graph(c, ea, sa, opts.graph_iters, &gx);
@@ -528,10 +533,12 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             ca.mask_out = wmask;
             DIA_CK(launch_eval(c.ki, kModeForward, ca, c.grid, s));
             DIA_CK(launch_restart(c.st, c.kpad, c.ob, m, c.ki.kp, s));
+            launches += 2;
             passes_done = pass;
         }
         for (;;) {
             DIA_CK(cudaGraphLaunch(gx, s));
+            launches += 3LL * opts.graph_iters;
             DIA_CK(cudaMemcpyAsync(&hs, c.st, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
             DIA_CK(cudaStreamSynchronize(s));
             if (hs.done) break;
@@ -554,6 +561,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         EvalArgs da = c.ea;
         da.diff_out = host ? (float *)(c.ws + c.L.stage_diff) : diff_out;
         DIA_CK(launch_eval(c.ki, kModeForward, da, c.grid, s));
+        launches += 1;
         if (host)
             DIA_CK(cudaMemcpyAsync(diff_out, da.diff_out, (size_t)(H - 2 * h) * (W - 2 * h) * 4,
                                    cudaMemcpyDeviceToHost, s));
@@ -561,6 +569,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     if (host) {
         float *kst = (float *)(c.ws + c.L.stage_out);
         DIA_CK(launch_pack_outputs(c.ob.theta, m, nullptr, kst, kst + m * m, s));
+        launches += 1;
         if (theta_out)
             DIA_CK(cudaMemcpyAsync(theta_out, c.ob.theta, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
         if (K_out) DIA_CK(cudaMemcpyAsync(K_out, kst, (size_t)m * m * 4, cudaMemcpyDeviceToHost, s));
@@ -569,6 +578,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             DIA_CK(cudaMemcpy2DAsync(mask_out, pair->ld, wmask, W, W, H, cudaMemcpyDeviceToHost, s));
     } else {
         DIA_CK(launch_pack_outputs(c.ob.theta, m, theta_out, K_out, b0_out, s));
+        launches += 1;
         if (mask_out)
             DIA_CK(cudaMemcpyAsync(mask_out, wmask, (size_t)H * ld, cudaMemcpyDeviceToDevice, s));
     }
@@ -588,6 +598,8 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         info->grad_inf = hs.grad_inf;
         info->scale = P;
         info->b0 = th[n - 1];
+        info->reason = hs.reason;
+        info->kernel_launches = launches;
     } else {
         DIA_CK(cudaStreamSynchronize(s));
     }

@@ -121,13 +121,14 @@ __device__ void set_trial(const StepArgs &a, double alpha) {
 }
 
 // Finish the pass: theta is the answer; the next evaluation (if any) sees it.
-__device__ void finish(const StepArgs &a, int status) {
+__device__ void finish(const StepArgs &a, int status, int reason) {
     FitState *st = a.st;
     for (int k = threadIdx.x; k < a.n; k += kStepThreads) a.b.trial[k] = a.b.theta[k];
     __syncthreads();
     write_kpad(a.b.theta, a.mk, a.kp, a.Kpad, threadIdx.x, kStepThreads);
     if (threadIdx.x == 0) {
         st->status = status;
+        st->reason = reason;
         st->phase = kPhaseDone;
         st->L_sum = st->L * st->ndata;
         __threadfence();
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
 
     const double N = a.red[n + 1];
     if (!(N > 0.0)) {
-        finish(a, 6 /* DIA_ERR_DEGENERATE */);
+        finish(a, 6 /* DIA_ERR_DEGENERATE */, kStopDegenerate);
         return;
     }
     const double invN = 1.0 / N;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
         st->ndata = N;
     }
     if (nbad) {
-        finish(a, 3 /* DIA_ERR_NONFINITE */);
+        finish(a, 3 /* DIA_ERR_NONFINITE */, kStopNonfinite);
         return;
     }
 
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
                 sm.finish_status = (st->evals >= p.max_evals) ? 4 /* DIA_ERR_MAXITER */ : -1;
             }
             __syncthreads();
-            if (sm.finish_status >= 0) finish(a, sm.finish_status);
+            if (sm.finish_status >= 0) finish(a, sm.finish_status, kStopMaxEvals);
             return;
         }
         phase = kPhaseLbfgsStart;  // hand over to L-BFGS at the point just evaluated
@@ -327,11 +328,13 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
             st->hist_len = 0;
             st->hist_head = 0;
             st->ls_restarts = 0;
+            st->ginf_best = ginf;
+            st->stall = 0;
             st->phase = kPhaseLbfgs;
         }
         __syncthreads();
         if (ginf < p.grad_tol) {
-            finish(a, 0);
+            finish(a, 0, kStopGradTol);
             return;
         }
         start_line_search(a, sm);
@@ -365,8 +368,10 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
         // row), else stop: no decrease is found at this precision
         if (tid == 0) {
             sm.finish_status = -1;
+            sm.act = kStopLineSearch;
             if (st->evals >= p.max_evals) {
                 sm.finish_status = 4; /* DIA_ERR_MAXITER */
+                sm.act = kStopMaxEvals;
             } else if (st->hist_len > 0 && st->ls_restarts < 2) {
                 st->hist_len = 0;
                 st->ls_restarts += 1;
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
         if (sm.finish_status < 0)
             start_line_search(a, sm);
         else
-            finish(a, sm.finish_status);
+            finish(a, sm.finish_status, sm.act);
         return;
     }
 
@@ -416,18 +421,33 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
         st->grad_inf = ginf;
         st->it_lbfgs += 1;
         st->ls_restarts = 0;
-        // convergence (Sec. 2.8): every |dL/dtheta| below grad_tol, or the
-        // relative loss change between steps below rel_tol
-        if (ginf < p.grad_tol || fabs(Lold - Lacc) <= p.rel_tol * fabs(Lacc))
-            sm.finish_status = 0;
-        else if (st->it_lbfgs >= p.max_lbfgs || st->evals >= p.max_evals)
-            sm.finish_status = 4; /* DIA_ERR_MAXITER */
-        else
-            sm.finish_status = -1;
+        if (ginf < 0.5 * st->ginf_best) {
+            st->ginf_best = ginf;
+            st->stall = 0;
+        } else {
+            st->stall += 1;
+        }
+        // Convergence (Sec. 2.8): every |dL/dtheta| below grad_tol, or the
+        // limit of numerical precision: max|g| has not halved for stall_iters
+        // accepted steps (float32 pixel rounding sets a floor on the
+        // gradient), or, if enabled, a relative loss change below rel_tol.
+        sm.finish_status = -1;
+        sm.act = kStopNone;
+        if (ginf < p.grad_tol) {
+            sm.finish_status = 0; sm.act = kStopGradTol;
+        } else if (p.rel_tol > 0.0 && fabs(Lold - Lacc) < p.rel_tol * fabs(Lacc)) {
+            sm.finish_status = 0; sm.act = kStopRelTol;
+        } else if (st->stall >= p.stall_iters) {
+            sm.finish_status = 0; sm.act = kStopStall;
+        } else if (st->it_lbfgs >= p.max_lbfgs) {
+            sm.finish_status = 4; sm.act = kStopMaxIter; /* DIA_ERR_MAXITER */
+        } else if (st->evals >= p.max_evals) {
+            sm.finish_status = 4; sm.act = kStopMaxEvals;
+        }
     }
     __syncthreads();
     if (sm.finish_status >= 0) {
-        finish(a, sm.finish_status);
+        finish(a, sm.finish_status, sm.act);
         return;
     }
     start_line_search(a, sm);

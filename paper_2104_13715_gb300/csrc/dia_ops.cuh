@@ -13,6 +13,12 @@ constexpr int kHistMax = 128;  // largest L-BFGS memory
 
 enum Phase { kPhaseAdam = 0, kPhaseLbfgs = 1, kPhaseLbfgsStart = 2, kPhaseDone = 3 };
 
+// Why a fit pass stopped (FitState::reason, dia_fit_info::reason).
+enum StopReason {
+    kStopNone = 0, kStopGradTol = 1, kStopRelTol = 2, kStopStall = 3, kStopLineSearch = 4,
+    kStopMaxIter = 5, kStopMaxEvals = 6, kStopNonfinite = 7, kStopDegenerate = 8
+};
+
 // Optimiser state, float64, resident in the caller's workspace.  The first
 // fields are read back by the host after every graph launch.
 struct FitState {
@@ -20,11 +26,12 @@ struct FitState {
     int phase;       // Phase
     int status;      // dia_status of the pass
     int it_adam, it_lbfgs, evals;
-    int ls_evals, hist_len, hist_head, ls_restarts, pad0, pad1;
+    int ls_evals, hist_len, hist_head, ls_restarts, stall, reason;
     double ndata;    // unmasked valid pixels of the last evaluation
     double L;        // scaled loss (L_sum / N) at the accepted theta
     double L_sum;    // unscaled loss at the accepted theta
     double grad_inf; // max |g| of the scaled loss at the accepted theta
+    double ginf_best; // smallest grad_inf so far (stall detection)
     double L_prev;   // previous Adam loss
     double gd0;      // phi'(0) of the current line search
     double alpha;    // step being evaluated
@@ -36,7 +43,7 @@ struct FitState {
 struct OptParams {
     double lr_kernel, lr_b0, beta1, beta2, adam_eps, switch_tol;
     double rel_tol, grad_tol;
-    int max_adam, history, max_lbfgs, max_evals;
+    int max_adam, history, max_lbfgs, max_evals, stall_iters;
 };
 
 // Float64 vectors of the optimiser (n = m*m + 1 each, S and Y are history x n;
@@ -85,6 +92,7 @@ cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp,
                         cudaStream_t s);
 cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp,
                            cudaStream_t s);
+constexpr int kMedianLaunches = 14;   // kernels launch_median enqueues
 cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int ld, int mk,
                           uint32_t *hist, SelectState *sel, int grid, cudaStream_t s);
 cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, float *K_out,

@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
                 ("clip_passes", ctypes.c_int32), ("clip_kappa", ctypes.c_float),
                 ("init", ctypes.c_int32), ("init_sigma", ctypes.c_double),
                 ("theta0", ctypes.c_void_p), ("graph_iters", ctypes.c_int32),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("stall_iters", ctypes.c_int32)]
 
 
 class FitInfo(ctypes.Structure):
@@ -56,7 +56,8 @@ class FitInfo(ctypes.Structure):
                 ("lbfgs_iters", ctypes.c_int32), ("evals", ctypes.c_int32),
                 ("clip_passes_done", ctypes.c_int32), ("ndata", ctypes.c_int64),
                 ("loss", ctypes.c_double), ("grad_inf", ctypes.c_double),
-                ("scale", ctypes.c_double), ("b0", ctypes.c_double)]
+                ("scale", ctypes.c_double), ("b0", ctypes.c_double),
+                ("reason", ctypes.c_int32), ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
