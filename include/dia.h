@@ -209,6 +209,34 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
                    uint8_t *mask_out, dia_fit_info *info,
                    void *workspace, size_t workspace_bytes, void *stream);
 
+/* Size of the fixed device scratch array used by dia_loss_grad_noalloc. */
+#define DIA_NOALLOC_SCRATCH_BYTES (2u << 20)
+
+/* dia_loss_grad without a caller workspace and without any device
+ * allocation.  The paper has no counterpart: this is an interface for
+ * callers that cannot call cudaMalloc or hold a workspace of their own --
+ * e.g. code embedded in a host application that owns all device memory
+ * through its own pool and forbids outside allocations, or a pipeline that
+ * must not allocate once running.  Inputs and outputs are the same as for
+ * dia_loss_grad (device pointers owned by the caller, DIA_MEM_DEVICE pair).
+ *
+ * Scratch: one file-scope device array of DIA_NOALLOC_SCRATCH_BYTES bytes
+ * (2 MiB), which every GPU that loads the library keeps until the process
+ * exits.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents: calls that overlap on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  Nothing in the array needs to start at zero: every call
+ * overwrites what it reads.  The number of CTAs is capped so that their
+ * partial sums fit the array; a kernel size whose scratch cannot fit is
+ * refused with DIA_ERR_WORKSPACE (none with m <= DIA_MAX_M), m > DIA_MAX_M
+ * with DIA_ERR_UNSUPPORTED.  Results equal dia_loss_grad's up to the order
+ * of the float64 cross-CTA sums.  Asynchronous on `stream`. */
+dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss_spec *loss,
+                                 const double *theta, double *loss_out, double *grad_out,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,9 @@ _SIGS = {
                                        ctypes.c_void_p]),
     "dia_diff_image": (ctypes.c_int32, [_P(Pair), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "dia_loss_grad_noalloc": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
     "dia_fit": (ctypes.c_int32, [_P(Pair), _P(LossSpec), _P(Opts), ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, _P(FitInfo), ctypes.c_void_p, ctypes.c_size_t,
@@ -202,6 +205,26 @@ def loss_grad(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, ws
     st = lib.dia_loss_grad(ctypes.byref(pair), ctypes.byref(spec), _ptr(theta), _ptr(loss),
                            _ptr(grad), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "dia_loss_grad")
+    return loss, grad
+
+
+def loss_grad_noalloc(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None,
+                      stream=None):
+    """dia_loss_grad_noalloc: the same evaluation without a workspace (the
+    library's fixed device scratch array is used instead).  Returns
+    (loss[1], grad[n]) float64 tensors."""
+    pair, keep = make_pair(R, I, m, mask, var, flat)
+    if not R.is_cuda:
+        raise ValueError("loss_grad_noalloc takes device tensors")
+    theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
+    n = m * m + 1
+    if theta.numel() != n:
+        raise ValueError(f"theta must have {n} entries")
+    loss = torch.empty(1, dtype=torch.float64, device=R.device)
+    grad = torch.empty(n, dtype=torch.float64, device=R.device)
+    st = lib.dia_loss_grad_noalloc(ctypes.byref(pair), ctypes.byref(spec), _ptr(theta),
+                                   _ptr(loss), _ptr(grad), _stream(stream))
+    _check(st, "dia_loss_grad_noalloc")
     return loss, grad
 
 
