@@ -426,6 +426,8 @@ def run_kernel_only(args):
     R, I = up(d["R"], torch.float32), up(d["I"], torch.float32)
     mask, var = up(d.get("mask"), torch.uint8), up(d.get("var"), torch.float32)
     spec = nat.loss_spec(**_loss_kw(d))
+    if args.variant is not None:
+        nat.select_kernel_variant(m, args.variant)
     ws = nat.workspace(H, W, m, device=dev)
     th = torch.full((m * m + 1,), 1.0 / (m * m), dtype=torch.float64, device=dev)
     th[-1] = float(np.median(d["I"]))
@@ -442,7 +444,8 @@ def run_kernel_only(args):
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     h = m // 2
     npx = int(d["mask"][h:H - h, h:W - h].sum()) if d.get("mask") is not None else (H - 2 * h) * (W - 2 * h)
-    print(json.dumps({"kernel_only": args.workload, "H": H, "W": W, "m": m, "ms_per_eval": ms,
+    print(json.dumps({"kernel_only": args.workload, "H": H, "W": W, "m": m,
+                      "variant": nat.kernel_variant_desc(m), "ms_per_eval": ms,
                       "tflops_algorithmic": 4.0 * m * m * npx / ms / 1e9}), flush=True)
 
 
@@ -462,6 +465,7 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the fused loss+gradient kernel alone (ncu driver)")
     ap.add_argument("--size", type=int, default=None, help="image side override (--kernel-only)")
+    ap.add_argument("--variant", type=int, default=None, help="tile variant (--kernel-only)")
     args = ap.parse_args()
     if args.kernel_only:
         run_kernel_only(args)

@@ -164,12 +164,28 @@ int32_t dia_last_cuda_error(void);
 /* Fill `opts` with the paper's defaults (values in the field comments). */
 dia_status dia_opts_default(dia_opts *opts);
 
+/* Tile variants of the fused kernel (shape choices of the same computation:
+ * warps per CTA, output rows per warp; the autotuner picks one per kernel
+ * side and image size).  dia_kernel_variants(m) is their number (0 if m is
+ * unsupported); dia_select_kernel_variant(m, v) makes variant v the one every
+ * later call with kernel side m uses (process-wide, default 0; not safe to
+ * change while another host thread is launching work of the same m);
+ * dia_kernel_variant_desc(m, v, ...) describes variant v (v < 0: the
+ * selected one); output pointers are nullable host pointers.  Results of all
+ * variants agree up to the order of float32 tile sums. */
+int32_t dia_kernel_variants(int32_t m);
+dia_status dia_select_kernel_variant(int32_t m, int32_t variant);
+dia_status dia_kernel_variant_desc(int32_t m, int32_t variant, int32_t *warps,
+                                   int32_t *rows_per_warp, int32_t *tile_rows,
+                                   int32_t *smem_bytes);
+
 /* Workspace bytes needed by dia_loss_grad / dia_fit / dia_diff_image for an
  * H x W image of row pitch ld, kernel side m, with `clip` != 0 if dia_fit
  * will clip (clip_passes > 0) or return a mask, and `mem` = DIA_MEM_HOST if
  * the pair's buffers are on the host (the images are then staged through the
  * workspace).  Returns 0 for invalid sizes.  The workspace must be 256-byte
- * aligned device memory; its contents need no initialisation. */
+ * aligned device memory; its contents need no initialisation.  The size
+ * covers every tile variant of m. */
 size_t dia_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m, int32_t clip, int32_t mem);
 
 /* One loss + gradient evaluation at theta (Sec. 2.3, Eq. 7 / Eq. 11).

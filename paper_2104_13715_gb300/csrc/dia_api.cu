@@ -46,7 +46,17 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
     L.tiles_x = (Wv + kTW - 1) / kTW;
     const int tiles_y = (Hv + ki.th - 1) / ki.th;
     L.n_tiles = L.tiles_x * tiles_y;
-    L.G = L.n_tiles < kMaxGrid ? L.n_tiles : kMaxGrid;
+    // partial slots for the tile variant with the most tiles, so that one
+    // workspace serves whichever variant is selected
+    int max_tiles = L.n_tiles;
+    for (int v = 0; v < kernel_variants(m); ++v) {
+        KernelInfo kv;
+        if (kernel_info_variant(m, v, &kv)) {
+            const int t = L.tiles_x * ((Hv + kv.th - 1) / kv.th);
+            if (t > max_tiles) max_tiles = t;
+        }
+    }
+    L.G = max_tiles < kMaxGrid ? max_tiles : kMaxGrid;
     L.np = ki.np;
     L.n = m * m + 1;
     L.kp = ki.kp;
@@ -390,6 +400,30 @@ const char *dia_status_str(int32_t s) {
 int32_t dia_abi_version(void) { return DIA_ABI_VERSION; }
 
 int32_t dia_last_cuda_error(void) { return g_last_cuda; }
+
+int32_t dia_kernel_variants(int32_t m) {
+    if (m < 1 || m > DIA_MAX_M || (m & 1) == 0) return 0;
+    return kernel_variants(m);
+}
+
+dia_status dia_select_kernel_variant(int32_t m, int32_t variant) {
+    if (m < 1 || m > DIA_MAX_M || (m & 1) == 0) return DIA_ERR_ARG;
+    return select_variant(m, variant) ? DIA_OK : DIA_ERR_ARG;
+}
+
+dia_status dia_kernel_variant_desc(int32_t m, int32_t variant, int32_t *warps,
+                                   int32_t *rows_per_warp, int32_t *tile_rows,
+                                   int32_t *smem_bytes) {
+    if (m < 1 || m > DIA_MAX_M || (m & 1) == 0) return DIA_ERR_ARG;
+    if (variant < 0) variant = selected_variant(m);
+    KernelInfo ki;
+    if (!kernel_info_variant(m, variant, &ki)) return DIA_ERR_ARG;
+    if (warps) *warps = ki.nw;
+    if (rows_per_warp) *rows_per_warp = ki.qf;
+    if (tile_rows) *tile_rows = ki.th;
+    if (smem_bytes) *smem_bytes = ki.smem;
+    return DIA_OK;
+}
 
 dia_status dia_opts_default(dia_opts *opts) {
     if (!opts) return DIA_ERR_ARG;

@@ -1,24 +1,108 @@
-// Kernel-side dispatch for the fused evaluation kernels.
+// Kernel-side and tile-variant dispatch of the fused evaluation kernels
+// (generated by gen_instances.py).
+#include <atomic>
+
 #include "dia_dispatch.h"
 
 namespace dia {
 
-#define DIA_DECL(MKV) bool kernel_info_##MKV(KernelInfo *o);
-DIA_DECL(1) DIA_DECL(3) DIA_DECL(5) DIA_DECL(7) DIA_DECL(9) DIA_DECL(11) DIA_DECL(13)
-DIA_DECL(15) DIA_DECL(17) DIA_DECL(19) DIA_DECL(21) DIA_DECL(23) DIA_DECL(25) DIA_DECL(27)
-DIA_DECL(29) DIA_DECL(31)
-#undef DIA_DECL
+bool kernel_info_1_0(KernelInfo *o);
+bool kernel_info_3_0(KernelInfo *o);
+bool kernel_info_5_0(KernelInfo *o);
+bool kernel_info_7_0(KernelInfo *o);
+bool kernel_info_9_0(KernelInfo *o);
+bool kernel_info_11_0(KernelInfo *o);
+bool kernel_info_13_0(KernelInfo *o);
+bool kernel_info_15_0(KernelInfo *o);
+bool kernel_info_17_0(KernelInfo *o);
+bool kernel_info_19_0(KernelInfo *o);
+bool kernel_info_21_0(KernelInfo *o);
+bool kernel_info_23_0(KernelInfo *o);
+bool kernel_info_25_0(KernelInfo *o);
+bool kernel_info_25_1(KernelInfo *o);
+bool kernel_info_25_2(KernelInfo *o);
+bool kernel_info_25_3(KernelInfo *o);
+bool kernel_info_25_4(KernelInfo *o);
+bool kernel_info_25_5(KernelInfo *o);
+bool kernel_info_27_0(KernelInfo *o);
+bool kernel_info_29_0(KernelInfo *o);
+bool kernel_info_31_0(KernelInfo *o);
 
-bool kernel_info(int mk, KernelInfo *o) {
+namespace {
+std::atomic<int> g_selected[kMaxKernelSide + 1];
+}
+
+int kernel_variants(int mk) {
     switch (mk) {
-#define DIA_CASE(MKV) \
-    case MKV: return kernel_info_##MKV(o);
-        DIA_CASE(1) DIA_CASE(3) DIA_CASE(5) DIA_CASE(7) DIA_CASE(9) DIA_CASE(11) DIA_CASE(13)
-        DIA_CASE(15) DIA_CASE(17) DIA_CASE(19) DIA_CASE(21) DIA_CASE(23) DIA_CASE(25)
-        DIA_CASE(27) DIA_CASE(29) DIA_CASE(31)
-#undef DIA_CASE
+        case 1: return 1;
+        case 3: return 1;
+        case 5: return 1;
+        case 7: return 1;
+        case 9: return 1;
+        case 11: return 1;
+        case 13: return 1;
+        case 15: return 1;
+        case 17: return 1;
+        case 19: return 1;
+        case 21: return 1;
+        case 23: return 1;
+        case 25: return 6;
+        case 27: return 1;
+        case 29: return 1;
+        case 31: return 1;
+        default: return 0;
+    }
+}
+
+bool kernel_info_variant(int mk, int v, KernelInfo *o) {
+    switch (mk) {
+        case 1:
+            switch (v) { case 0: return kernel_info_1_0(o); default: return false; }
+        case 3:
+            switch (v) { case 0: return kernel_info_3_0(o); default: return false; }
+        case 5:
+            switch (v) { case 0: return kernel_info_5_0(o); default: return false; }
+        case 7:
+            switch (v) { case 0: return kernel_info_7_0(o); default: return false; }
+        case 9:
+            switch (v) { case 0: return kernel_info_9_0(o); default: return false; }
+        case 11:
+            switch (v) { case 0: return kernel_info_11_0(o); default: return false; }
+        case 13:
+            switch (v) { case 0: return kernel_info_13_0(o); default: return false; }
+        case 15:
+            switch (v) { case 0: return kernel_info_15_0(o); default: return false; }
+        case 17:
+            switch (v) { case 0: return kernel_info_17_0(o); default: return false; }
+        case 19:
+            switch (v) { case 0: return kernel_info_19_0(o); default: return false; }
+        case 21:
+            switch (v) { case 0: return kernel_info_21_0(o); default: return false; }
+        case 23:
+            switch (v) { case 0: return kernel_info_23_0(o); default: return false; }
+        case 25:
+            switch (v) { case 0: return kernel_info_25_0(o); case 1: return kernel_info_25_1(o); case 2: return kernel_info_25_2(o); case 3: return kernel_info_25_3(o); case 4: return kernel_info_25_4(o); case 5: return kernel_info_25_5(o); default: return false; }
+        case 27:
+            switch (v) { case 0: return kernel_info_27_0(o); default: return false; }
+        case 29:
+            switch (v) { case 0: return kernel_info_29_0(o); default: return false; }
+        case 31:
+            switch (v) { case 0: return kernel_info_31_0(o); default: return false; }
         default: return false;
     }
 }
+
+bool select_variant(int mk, int v) {
+    if (mk < 1 || mk > kMaxKernelSide || v < 0 || v >= kernel_variants(mk)) return false;
+    g_selected[mk].store(v);
+    return true;
+}
+
+int selected_variant(int mk) {
+    if (mk < 1 || mk > kMaxKernelSide) return 0;
+    return g_selected[mk].load();
+}
+
+bool kernel_info(int mk, KernelInfo *o) { return kernel_info_variant(mk, selected_variant(mk), o); }
 
 }  // namespace dia

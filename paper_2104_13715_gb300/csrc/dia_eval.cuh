@@ -10,7 +10,8 @@
 //
 // One CTA owns a TH x TW tile of output pixels at a time (persistent loop over
 // tiles).  Per tile:
-//   1. the R tile plus its (m-1) halo is staged in shared memory;
+//   1. the R tile plus its (m-1) halo is staged in shared memory with
+//      cp.async, double-buffered so the next tile's copy overlaps compute;
 //   2. forward: warp w computes rows [w*QF, (w+1)*QF) of the tile, lane l the
 //      four columns [4l, 4l+4); each R row is loaded once into a register
 //      window and reused by all QF output rows and all m kernel columns;
@@ -20,8 +21,8 @@
 //   4. backward: warp w owns kernel rows a in [a_lo, a_hi); lanes split the
 //      columns; each R row window is reused by every owned kernel row, the
 //      m column offsets and the four pixels of the lane;
-//   5. the float32 tile sums are reduced over the warp and added in float64
-//      to per-CTA shared accumulators.
+//   5. per-lane float32 sums (at most 4096 pixels each) are reduced over the
+//      warp and added in float64 to per-CTA shared accumulators.
 // At the end each CTA writes m*m + 5 float64 partials (loss, dK, dB0, pixel
 // count, and two curvature sums for the optimiser's diagonal preconditioner);
 // a separate kernel sums them in a fixed order.
@@ -130,6 +131,50 @@ __device__ __forceinline__ float pixel_loss(const LossParams &lp, float I, float
     return ell;
 }
 
+// Asynchronous global -> shared copies (cp.async); a source size below the
+// copy size fills the rest with zeros.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Stage the R tile (rows ty0.., columns tx0.., RROWS x RP) into dst; zeros
+// outside the image.  16-byte copies when rows are 16-byte aligned.
+template <int RROWS, int RP, int NT>
+__device__ __forceinline__ void stage_tile(float *dst, const EvalArgs &a, int ty0, int tx0,
+                                           bool vec) {
+    if (vec) {
+        constexpr int CH = RP / 4;
+        for (int i = threadIdx.x; i < RROWS * CH; i += NT) {
+            const int r = i / CH, c4 = i - r * CH;
+            const int gy = ty0 + r, gx = tx0 + 4 * c4;
+            int bytes = 0;
+            const float *src = a.R;
+            if (gy < a.H && gx < a.W) {
+                bytes = (a.W - gx >= 4) ? 16 : 4 * (a.W - gx);
+                src = a.R + (size_t)gy * a.ld + gx;
+            }
+            cp_async16(dst + r * RP + 4 * c4, src, bytes);
+        }
+    } else {
+        for (int i = threadIdx.x; i < RROWS * RP; i += NT) {
+            const int r = i / RP, c = i - r * RP;
+            const int gy = ty0 + r, gx = tx0 + c;
+            const bool in = gy < a.H && gx < a.W;
+            cp_async4(dst + i, in ? a.R + (size_t)gy * a.ld + gx : a.R, in ? 4 : 0);
+        }
+    }
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -148,9 +193,13 @@ struct EvalShape {
     static constexpr int NT = NW * 32;
     // shared memory layout (bytes)
     static constexpr int OFF_R = 0;
-    static constexpr int SZ_R = RROWS * RP * 4;
-    static constexpr int OFF_G = OFF_R + SZ_R;
-    static constexpr int SZ_G = TH * kTW * 4;
+    static constexpr int SZ_R = RROWS * RP * 4;          // one R tile buffer (two are kept)
+    static constexpr int GPAD = QB - 1;                  // zero rows above and below the g tile
+    static constexpr int OFF_G = OFF_R + 2 * SZ_R;
+    // tiles between float64 flushes: each lane's float32 sums then cover at
+    // most 4096 pixels
+    static constexpr int FLUSH = (4096 / (4 * TH)) > 0 ? (4096 / (4 * TH)) : 1;
+    static constexpr int SZ_G = (TH + 2 * GPAD) * kTW * 4;
     static constexpr int OFF_K = OFF_G + SZ_G;
     static constexpr int SZ_K = (MK * KP + 4) * 4;
     static constexpr int OFF_D = (OFF_K + SZ_K + 15) & ~15;
@@ -158,15 +207,51 @@ struct EvalShape {
     static constexpr int SMEM = OFF_D + SZ_D;
 };
 
-template <int MK, int NW, int QF, int MODE>
-__global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
+// Backward rows of one warp owning NQ kernel rows a_lo .. a_lo+NQ-1:
+// dk[qb][b] += sum_y sum_p g[y][x+p] R[y+a_lo+qb][x+b+p], y = rr - qb.  The g
+// tile has QB-1 zero rows above and below, so every y read is in bounds and
+// no branch separates the NQ rows' FMAs.
+template <int MK, int QB, int NQ, int RP, int RWIN>
+__device__ __forceinline__ void bwd_rows(const float *rb2, const float *gb, int TH,
+                                         float (&dk)[QB][MK]) {
+#pragma unroll 1
+    for (int rr = 0; rr < TH + NQ - 1; ++rr) {
+        float win[RWIN];
+        const float4 *rp4 = reinterpret_cast<const float4 *>(rb2 + rr * RP);
+#pragma unroll
+        for (int v4 = 0; v4 < RWIN / 4; ++v4) {
+            const float4 t = rp4[v4];
+            win[4 * v4 + 0] = t.x;
+            win[4 * v4 + 1] = t.y;
+            win[4 * v4 + 2] = t.z;
+            win[4 * v4 + 3] = t.w;
+        }
+        float4 g4[NQ];
+#pragma unroll
+        for (int qb = 0; qb < NQ; ++qb) g4[qb] = *reinterpret_cast<const float4 *>(gb + (rr - qb) * kTW);
+        // pixel p outer: consecutive FMAs update different accumulators
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+#pragma unroll
+            for (int qb = 0; qb < NQ; ++qb) {
+                const float gv = p == 0 ? g4[qb].x : p == 1 ? g4[qb].y : p == 2 ? g4[qb].z : g4[qb].w;
+#pragma unroll
+                for (int b = 0; b < MK; ++b) dk[qb][b] = fmaf(gv, win[b + p], dk[qb][b]);
+            }
+        }
+    }
+}
+
+template <int MK, int NW, int QF, int MINB, int MODE>
+__global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args) {
     using S = EvalShape<MK, NW, QF>;
     constexpr int TH = S::TH, RP = S::RP, RWIN = S::RWIN, KP = S::KP, QB = S::QB;
     constexpr int H2 = MK / 2;
     if (args.done_flag != nullptr && *((volatile const int *)args.done_flag) != 0) return;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    float *Rs = reinterpret_cast<float *>(smem + S::OFF_R);
+    float *Rbuf0 = reinterpret_cast<float *>(smem + S::OFF_R);
+    float *Rbuf1 = Rbuf0 + S::RROWS * RP;
     float *gs = reinterpret_cast<float *>(smem + S::OFF_G);
     float *Ks = reinterpret_cast<float *>(smem + S::OFF_K);
     double *acc64 = reinterpret_cast<double *>(smem + S::OFF_D);  // dK[MK*MK], then per warp
@@ -175,8 +260,14 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int i = tid; i < MK * KP + 4; i += S::NT) Ks[i] = args.Kpad[i];
-    if (MODE == kModeGrad)
+    if (MODE == kModeGrad) {
         for (int i = tid; i < MK * MK + 5 * NW; i += S::NT) acc64[i] = 0.0;
+        for (int i = tid; i < S::GPAD * kTW; i += S::NT) {
+            gs[i] = 0.f;
+            gs[(S::GPAD + TH) * kTW + i] = 0.f;
+        }
+    }
+    float *gt = gs + S::GPAD * kTW;   // g tile row 0
     __syncthreads();
     const float B0 = Ks[MK * KP];
 
@@ -184,19 +275,60 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
     const int a_lo = (warp * MK) / NW;
     const int nqb = ((warp + 1) * MK) / NW - a_lo;
 
-    for (int tile = blockIdx.x; tile < args.n_tiles; tile += gridDim.x) {
+    // per-lane float32 sums, flushed to the float64 CTA accumulators every
+    // FLUSH tiles: dK rows owned by this warp, and loss / dB0 / count /
+    // curvature sums of the lane's pixels
+    float dk[QB][MK];
+#pragma unroll
+    for (int qb = 0; qb < QB; ++qb)
+#pragma unroll
+        for (int b = 0; b < MK; ++b) dk[qb][b] = 0.f;
+    float lsum = 0.f, gsum = 0.f, cnt = 0.f, ksum = 0.f, kr2sum = 0.f;
+    int since_flush = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int qb = 0; qb < QB; ++qb) {
+            if (qb < nqb) {
+#pragma unroll
+                for (int b = 0; b < MK; ++b) {
+                    const float sm = warp_sum(dk[qb][b]);
+                    if (lane == 0) acc64[(a_lo + qb) * MK + b] += (double)sm;
+                    dk[qb][b] = 0.f;
+                }
+            }
+        }
+        const float l = warp_sum(lsum), g = warp_sum(gsum), c = warp_sum(cnt);
+        const float k = warp_sum(ksum), kr = warp_sum(kr2sum);
+        if (lane == 0) {
+            double *w5 = acc64 + MK * MK + 5 * warp;
+            w5[0] += (double)l;
+            w5[1] += (double)g;
+            w5[2] += (double)c;
+            w5[3] += (double)kr;
+            w5[4] += (double)k;
+        }
+        lsum = gsum = cnt = ksum = kr2sum = 0.f;
+    };
+
+    // ---- 1. R tiles (+ halo) are staged with cp.async, the next tile's copy
+    // overlapping the current tile's compute (two buffers)
+    const bool vec = ((args.ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(args.R) & 15) == 0);
+    if (blockIdx.x < args.n_tiles)
+        stage_tile<S::RROWS, RP, S::NT>(Rbuf0, args, (blockIdx.x / args.tiles_x) * TH,
+                                        (blockIdx.x % args.tiles_x) * kTW, vec);
+    cp_async_commit();
+    int buf = 0;
+    for (int tile = blockIdx.x; tile < args.n_tiles; tile += gridDim.x, buf ^= 1) {
         const int ty0 = (tile / args.tiles_x) * TH;
         const int tx0 = (tile % args.tiles_x) * kTW;
-
-        // ---- 1. stage the R tile (+ halo); outside the image -> 0
-        for (int i = tid; i < S::RROWS * RP; i += S::NT) {
-            const int r = i / RP, c = i - r * RP;
-            const int gy = ty0 + r, gx = tx0 + c;
-            float v = 0.f;
-            if (gy < args.H && gx < args.W) v = __ldg(args.R + (size_t)gy * args.ld + gx);
-            Rs[i] = v;
-        }
+        const int nxt = tile + gridDim.x;
+        if (nxt < args.n_tiles)
+            stage_tile<S::RROWS, RP, S::NT>(buf ? Rbuf0 : Rbuf1, args, (nxt / args.tiles_x) * TH,
+                                            (nxt % args.tiles_x) * kTW, vec);
+        cp_async_commit();
+        cp_async_wait<1>();   // this tile's copies have landed
         __syncthreads();
+        const float *Rs = buf ? Rbuf1 : Rbuf0;
 
         // ---- 2. forward: acc[q][p] = sum_{a,b} K[a][b] R[y0+q+a][x+p+b]
         float acc[QF][4];
@@ -206,8 +338,57 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
             for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
 
         const float *rbase = Rs + (warp * QF) * RP + 4 * lane;
+        const float4 *K4 = reinterpret_cast<const float4 *>(Ks);
+        // R rows r with every output row q of the warp active (kernel row a = r - q
+        // in [0, MK)): no branch, all QF x 4 accumulators interleaved per K column
 #pragma unroll 1
-        for (int r = 0; r < QF + MK - 1; ++r) {
+        for (int r = QF - 1; r <= MK - 1; ++r) {
+            float win[RWIN];
+            const float4 *rp4 = reinterpret_cast<const float4 *>(rbase + r * RP);
+#pragma unroll
+            for (int v4 = 0; v4 < RWIN / 4; ++v4) {
+                const float4 t = rp4[v4];
+                win[4 * v4 + 0] = t.x;
+                win[4 * v4 + 1] = t.y;
+                win[4 * v4 + 2] = t.z;
+                win[4 * v4 + 3] = t.w;
+            }
+            // K columns in groups of 4; the next group's broadcast loads are
+            // issued before the current group's FMAs
+            float4 kq[QF], kn[QF];
+#pragma unroll
+            for (int q = 0; q < QF; ++q) kq[q] = K4[(r - q) * (KP / 4)];
+#pragma unroll
+            for (int b4 = 0; b4 < KP / 4; ++b4) {
+                if (b4 + 1 < KP / 4) {
+#pragma unroll
+                    for (int q = 0; q < QF; ++q) kn[q] = K4[(r - q) * (KP / 4) + b4 + 1];
+                }
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const int b = 4 * b4 + bb;
+                    if (b < MK) {
+#pragma unroll
+                        for (int q = 0; q < QF; ++q) {
+                            const float kv = bb == 0 ? kq[q].x : bb == 1 ? kq[q].y : bb == 2 ? kq[q].z : kq[q].w;
+#pragma unroll
+                            for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(kv, win[p + b], acc[q][p]);
+                        }
+                    }
+                }
+                if (b4 + 1 < KP / 4) {
+#pragma unroll
+                    for (int q = 0; q < QF; ++q) kq[q] = kn[q];
+                }
+            }
+        }
+        // the first and last QF-1 R rows feed only some output rows (with
+        // MK < QF - 1 there is no interior and every row is done here once)
+        constexpr bool kSplit = MK >= QF - 1;
+        constexpr int kEdges = kSplit ? 2 * (QF - 1) : (QF + MK - 1);
+#pragma unroll 1
+        for (int e = 0; e < kEdges; ++e) {
+            const int r = kSplit ? ((e < QF - 1) ? e : (MK + e - (QF - 1))) : e;
             float win[RWIN];
             const float4 *rp4 = reinterpret_cast<const float4 *>(rbase + r * RP);
 #pragma unroll
@@ -222,10 +403,9 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
             for (int q = 0; q < QF; ++q) {
                 const int a = r - q;
                 if (a >= 0 && a < MK) {
-                    const float4 *k4 = reinterpret_cast<const float4 *>(Ks + a * KP);
 #pragma unroll
                     for (int b4 = 0; b4 < KP / 4; ++b4) {
-                        const float4 kk = k4[b4];
+                        const float4 kk = K4[a * (KP / 4) + b4];
                         const float kv[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
                         for (int bb = 0; bb < 4; ++bb) {
@@ -241,7 +421,6 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
         }
 
         // ---- 3. epilogue: loss terms, g -> shared tile
-        float lsum = 0.f, gsum = 0.f, cnt = 0.f, ksum = 0.f, kr2sum = 0.f;
 #pragma unroll
         for (int q = 0; q < QF; ++q) {
             const int yl = warp * QF + q;
@@ -275,81 +454,34 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
                         if (args.mask_out && use && fabsf(z) > args.clip_kappa) args.mask_out[off] = 0;
                     }
                 }
-                if (MODE == kModeGrad) gs[yl * kTW + xl] = gval;
+                if (MODE == kModeGrad) gt[yl * kTW + xl] = gval;
             }
         }
         if (MODE != kModeGrad) {
-            __syncthreads();  // Rs reused by the next tile
+            __syncthreads();  // the R buffer is refilled two tiles later
             continue;
-        }
-        lsum = warp_sum(lsum);
-        gsum = warp_sum(gsum);
-        cnt = warp_sum(cnt);
-        ksum = warp_sum(ksum);
-        kr2sum = warp_sum(kr2sum);
-        if (lane == 0) {
-            double *w5 = acc64 + MK * MK + 5 * warp;
-            w5[0] += (double)lsum;
-            w5[1] += (double)gsum;
-            w5[2] += (double)cnt;
-            w5[3] += (double)kr2sum;
-            w5[4] += (double)ksum;
         }
         __syncthreads();  // g tile complete
 
         // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b], a in [a_lo, a_lo+nqb)
-        float dk[QB][MK];
-#pragma unroll
-        for (int qb = 0; qb < QB; ++qb)
-#pragma unroll
-            for (int b = 0; b < MK; ++b) dk[qb][b] = 0.f;
-
         const float *rb2 = Rs + a_lo * RP + 4 * lane;
-        const float *gb = gs + 4 * lane;
-#pragma unroll 1
-        for (int rr = 0; rr < TH + nqb - 1; ++rr) {
-            float win[RWIN];
-            const float4 *rp4 = reinterpret_cast<const float4 *>(rb2 + rr * RP);
-#pragma unroll
-            for (int v4 = 0; v4 < RWIN / 4; ++v4) {
-                const float4 t = rp4[v4];
-                win[4 * v4 + 0] = t.x;
-                win[4 * v4 + 1] = t.y;
-                win[4 * v4 + 2] = t.z;
-                win[4 * v4 + 3] = t.w;
-            }
-#pragma unroll
-            for (int qb = 0; qb < QB; ++qb) {
-                const int y = rr - qb;
-                if (qb < nqb && y >= 0 && y < TH) {
-                    const float4 g4 = *reinterpret_cast<const float4 *>(gb + y * kTW);
-#pragma unroll
-                    for (int b = 0; b < MK; ++b) {
-                        float t = dk[qb][b];
-                        t = fmaf(g4.x, win[b + 0], t);
-                        t = fmaf(g4.y, win[b + 1], t);
-                        t = fmaf(g4.z, win[b + 2], t);
-                        t = fmaf(g4.w, win[b + 3], t);
-                        dk[qb][b] = t;
-                    }
-                }
-            }
+        const float *gb = gt + 4 * lane;
+        if (nqb == QB)
+            bwd_rows<MK, QB, QB, RP, RWIN>(rb2, gb, TH, dk);
+        else if (QB > 1 && nqb == QB - 1)
+            bwd_rows<MK, QB, (QB > 1 ? QB - 1 : 1), RP, RWIN>(rb2, gb, TH, dk);
+        // ---- 5. float32 sums -> float64 every FLUSH tiles (each kernel row
+        // is owned by one warp, so the warps write disjoint accumulators)
+        if (++since_flush == S::FLUSH) {
+            flush();
+            since_flush = 0;
         }
-        // ---- 5. tile sums -> float64 (each kernel row is owned by one warp)
-#pragma unroll
-        for (int qb = 0; qb < QB; ++qb) {
-            if (qb < nqb) {
-#pragma unroll
-                for (int b = 0; b < MK; ++b) {
-                    const float s = warp_sum(dk[qb][b]);
-                    if (lane == 0) acc64[(a_lo + qb) * MK + b] += (double)s;
-                }
-            }
-        }
-        __syncthreads();  // Rs, gs reused by the next tile
+        __syncthreads();  // R buffer and g tile are reused
     }
+    cp_async_wait<0>();
 
     if (MODE == kModeGrad) {
+        if (since_flush > 0) flush();
         __syncthreads();
         double *out = args.partials + (size_t)blockIdx.x * S::NP;
         for (int i = tid; i < MK * MK; i += S::NT) out[1 + i] = acc64[i];

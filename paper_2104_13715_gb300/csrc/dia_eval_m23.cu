@@ -1,4 +1,4 @@
-// Fused evaluation kernels for kernel sides: 23
+// Fused evaluation kernels for kernel sides [23] (generated by gen_instances.py)
 #include "dia_eval_inst.cuh"
 
-DIA_EVAL_INST(23, 8, 8)
+DIA_EVAL_INST(23, 0, 8, 8, 1)

@@ -1,4 +1,4 @@
-// Fused evaluation kernels for kernel sides: 27
+// Fused evaluation kernels for kernel sides [27] (generated by gen_instances.py)
 #include "dia_eval_inst.cuh"
 
-DIA_EVAL_INST(27, 9, 8)
+DIA_EVAL_INST(27, 0, 9, 8, 1)

@@ -1,4 +1,4 @@
-// Fused evaluation kernels for kernel sides: 29
+// Fused evaluation kernels for kernel sides [29] (generated by gen_instances.py)
 #include "dia_eval_inst.cuh"
 
-DIA_EVAL_INST(29, 10, 8)
+DIA_EVAL_INST(29, 0, 10, 8, 1)

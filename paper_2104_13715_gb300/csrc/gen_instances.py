@@ -1,0 +1,87 @@
+"""Generate the per-kernel-side instantiation units of the fused kernel and the
+dispatch table (run after editing VARIANTS; the outputs are committed)."""
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# kernel side -> list of tile variants (NW warps, QF output rows per warp in the
+# forward pass, MINB minimum resident CTAs per SM for the register budget).
+# Variant 0 is the default; the autotuner may pick another at run time.
+VARIANTS = {
+    1: [(8, 8, 1)], 3: [(8, 8, 1)], 5: [(8, 8, 1)], 7: [(8, 8, 1)],
+    9: [(9, 8, 1)], 11: [(11, 8, 1)], 13: [(13, 8, 1)], 15: [(8, 8, 1)],
+    17: [(9, 8, 1)], 19: [(10, 8, 1)], 21: [(7, 8, 1)], 23: [(8, 8, 1)],
+    25: [(9, 8, 1), (9, 4, 1), (13, 4, 1), (9, 4, 2), (7, 8, 1), (13, 8, 1)],
+    27: [(9, 8, 1)], 29: [(10, 8, 1)], 31: [(11, 8, 1)],
+}
+GROUPS = [[1, 3, 5, 7], [9, 11], [13, 15], [17], [19], [21], [23], [25], [27], [29], [31]]
+
+
+def main():
+    for f in os.listdir(HERE):
+        if f.startswith("dia_eval_m") and f.endswith(".cu"):
+            os.remove(os.path.join(HERE, f))
+    for grp in GROUPS:
+        lines = [f"// Fused evaluation kernels for kernel sides {grp} (generated by gen_instances.py)",
+                 '#include "dia_eval_inst.cuh"', ""]
+        for mk in grp:
+            for v, (nw, qf, mb) in enumerate(VARIANTS[mk]):
+                lines.append(f"DIA_EVAL_INST({mk}, {v}, {nw}, {qf}, {mb})")
+        with open(os.path.join(HERE, f"dia_eval_m{grp[0]:02d}.cu"), "w") as fh:
+            fh.write("\n".join(lines) + "\n")
+    decl, cases = [], []
+    for mk, vs in VARIANTS.items():
+        for v in range(len(vs)):
+            decl.append(f"bool kernel_info_{mk}_{v}(KernelInfo *o);")
+        inner = " ".join(f"case {v}: return kernel_info_{mk}_{v}(o);" for v in range(len(vs)))
+        cases.append(f"        case {mk}:\n            switch (v) {{ {inner} default: return false; }}")
+    counts = ", ".join(f"{{{mk}, {len(vs)}}}" for mk, vs in VARIANTS.items())
+    src = f"""// Kernel-side and tile-variant dispatch of the fused evaluation kernels
+// (generated by gen_instances.py).
+#include <atomic>
+
+#include "dia_dispatch.h"
+
+namespace dia {{
+
+{chr(10).join(decl)}
+
+namespace {{
+std::atomic<int> g_selected[kMaxKernelSide + 1];
+}}
+
+int kernel_variants(int mk) {{
+    switch (mk) {{
+{chr(10).join(f"        case {mk}: return {len(vs)};" for mk, vs in VARIANTS.items())}
+        default: return 0;
+    }}
+}}
+
+bool kernel_info_variant(int mk, int v, KernelInfo *o) {{
+    switch (mk) {{
+{chr(10).join(cases)}
+        default: return false;
+    }}
+}}
+
+bool select_variant(int mk, int v) {{
+    if (mk < 1 || mk > kMaxKernelSide || v < 0 || v >= kernel_variants(mk)) return false;
+    g_selected[mk].store(v);
+    return true;
+}}
+
+int selected_variant(int mk) {{
+    if (mk < 1 || mk > kMaxKernelSide) return 0;
+    return g_selected[mk].load();
+}}
+
+bool kernel_info(int mk, KernelInfo *o) {{ return kernel_info_variant(mk, selected_variant(mk), o); }}
+
+}}  // namespace dia
+"""
+    with open(os.path.join(HERE, "dia_dispatch.cu"), "w") as fh:
+        fh.write(src)
+
+
+if __name__ == "__main__":
+    main()

@@ -71,6 +71,10 @@ _SIGS = {
     "dia_last_cuda_error": (ctypes.c_int32, []),
     "dia_opts_default": (ctypes.c_int32, [_P(Opts)]),
     "dia_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 6),
+    "dia_kernel_variants": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_select_kernel_variant": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
+    "dia_kernel_variant_desc": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]
+                                + [_P(ctypes.c_int32)] * 4),
     "dia_loss_grad": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                        ctypes.c_void_p]),
@@ -117,6 +121,21 @@ def _check(status, what):
 
 def status_str(s: int) -> str:
     return lib.dia_status_str(s).decode()
+
+
+def kernel_variants(m: int) -> int:
+    return lib.dia_kernel_variants(m)
+
+
+def select_kernel_variant(m: int, variant: int) -> None:
+    _check(lib.dia_select_kernel_variant(m, variant), "dia_select_kernel_variant")
+
+
+def kernel_variant_desc(m: int, variant: int = -1) -> dict:
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib.dia_kernel_variant_desc(m, variant, *[ctypes.byref(x) for x in v]),
+           "dia_kernel_variant_desc")
+    return dict(zip(("warps", "rows_per_warp", "tile_rows", "smem_bytes"), (x.value for x in v)))
 
 
 def loss_spec(rho="gauss", noise="fixed", sigma0=0.0, gain=1.0, excess=2.0, huber_c=1.345,

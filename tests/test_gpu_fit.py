@@ -62,9 +62,11 @@ def test_chi2_with_variance_map_and_mask(nat, seed):
 
 
 def _noiseless_pair(seed, shape=(142, 142)):
+    """A reference generated as in Sec. 3.1 (including its 10x-lower-variance
+    noise, steps vi-vii); the target is then a noiseless transform of it."""
     rng = np.random.default_rng(seed)
-    p = synth.PairSpec(size=shape, n_stars=60, m=1, fwhm_ref=2.5, kernel_sigma=0.0, sky=0.0,
-                       ref_noise=False, flux_law="paper")
+    p = synth.PairSpec(size=shape, n_stars=60, m=1, fwhm_ref=2.5, kernel_sigma=0.0, sky=100.0,
+                       ref_noise=True, flux_law="paper")
     R = synth.make_pair(p, seed)["R"].astype(np.float64)
     return R, rng
 

@@ -41,6 +41,23 @@ def test_every_kernel_side_gauss_fixed(nat, m):
     assert rel_inf(g, go) <= TOL_G
 
 
+def test_every_tile_variant(nat):
+    """Each tile variant of each kernel side gives the oracle's loss and gradient."""
+    for m in range(1, 32, 2):
+        nv = nat.kernel_variants(m)
+        d = field(140, 270, m, seed=50 + m)
+        th = theta_start(m, d["I"], np.random.default_rng(m), jitter=0.3)
+        Lo, go = oracle.loss_grad(d["R"], d["I"], m, th, ospec(SPECS["huber-ccd"]))
+        try:
+            for v in range(nv):
+                nat.select_kernel_variant(m, v)
+                L, g = _run(nat, d, m, th, SPECS["huber-ccd"])
+                assert L == pytest.approx(Lo, rel=TOL_L), (m, v)
+                assert rel_inf(g, go) <= TOL_G, (m, v)
+        finally:
+            nat.select_kernel_variant(m, 0)
+
+
 @pytest.mark.parametrize("name", list(SPECS))
 @pytest.mark.parametrize("m", [5, 19, 25])
 def test_losses_with_mask_and_maps(nat, name, m):
