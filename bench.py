@@ -266,6 +266,9 @@ def run_ours(args, rank, world, local_rank):
     clip = opts.clip_passes > 0
     ws = nat.workspace(H, W, m, clip=clip, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # tile shape of the fused kernel for this (m, image size): autotuned, cached
+    from paper_2104_13715_gb300 import autotune
+    tuned = autotune.tune(R, I, m, spec, mask=mask, var=var, stream=stream)
 
     def step():
         return nat.fit(R, I, m, spec, opts, mask=mask, var=var, ws=ws, stream=stream,
@@ -333,7 +336,8 @@ def run_ours(args, rank, world, local_rank):
     traffic = _traffic_record()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
             "frac": achieved / peak_tf, "traffic": traffic,
-            "kernel": "dia::eval_kernel<25,9,8,grad> (fused forward + loss + weight gradient)",
+            "kernel": "dia::eval_kernel (fused forward + loss + weight gradient), tile " +
+                      json.dumps(nat.kernel_variant_desc(m)),
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (max SM clock, "
                           f"{src} peaks file); FP32 FMA pipe",
             "algorithmic": f"4*m^2 flop x {npx} unmasked valid px = {flops / 1e9:.2f} GFLOP per launch",
@@ -398,7 +402,9 @@ def run_ours(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(args, d), "fits_per_s": fits_per_s,
+            "config": {**_config(args, d), "tile": nat.kernel_variant_desc(m),
+                       "tile_variant": tuned.get("variant")},
+            "fits_per_s": fits_per_s,
             "evals_per_fit": evals_all / (args.steps * world),
             "fit_info": {k: last.get(k) for k in ("status", "adam_iters", "lbfgs_iters", "evals",
                                                   "clip_passes_done", "reason", "ndata")},

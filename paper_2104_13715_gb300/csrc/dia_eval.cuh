@@ -18,9 +18,11 @@
 //      K is read from shared memory as warp-uniform (broadcast) float4 loads;
 //   3. epilogue: M stays in registers, the loss terms and g_p are formed in
 //      float32 and g_p is written to a shared-memory tile (never to HBM);
-//   4. backward: warp w owns kernel rows a in [a_lo, a_hi); lanes split the
-//      columns; each R row window is reused by every owned kernel row, the
-//      m column offsets and the four pixels of the lane;
+//   4. backward: with m = NW*KF + RM, warp w owns kernel rows [w*KF, (w+1)*KF)
+//      over the whole tile plus the RM last rows on its own QF-row slice
+//      (equal work per warp); lanes split the columns; each R row window is
+//      reused by every kernel row it feeds, the m column offsets and the
+//      four pixels of the lane;
 //   5. per-lane float32 sums (at most 4096 pixels each) are reduced over the
 //      warp and added in float64 to per-CTA shared accumulators.
 // At the end each CTA writes m*m + 5 float64 partials (loss, dK, dB0, pixel
@@ -181,20 +183,28 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-template <int MK, int NW, int QF>
+// SPLIT selects how the backward's kernel rows are shared among the warps:
+// 0 = whole rows, ceil(MK/NW) or floor(MK/NW) per warp; 1 = MK = NW*KF + RM
+// with KF whole rows per warp and the RM last rows split by tile-row slices.
+template <int MK, int NW, int QF, int SPLIT>
 struct EvalShape {
     static constexpr int TH = NW * QF;
     static constexpr int RROWS = TH + MK - 1;
     static constexpr int RP = round4(kTW + MK - 1);      // R tile pitch (floats)
     static constexpr int RWIN = round4(MK + 3);          // register window per lane
     static constexpr int KP = round4(MK);                // K row pitch (floats)
-    static constexpr int QB = (MK + NW - 1) / NW;         // max kernel rows per warp (backward)
+    // backward split: MK = NW*KF + RM; warp w owns kernel rows [w*KF, (w+1)*KF)
+    // over the whole tile and the RM last rows on its own QF-row slice, so
+    // every warp does the same work
+    static constexpr int KF = SPLIT ? MK / NW : (MK + NW - 1) / NW;
+    static constexpr int RM = SPLIT ? MK % NW : 0;
+    static constexpr int QB = KF + RM;                   // dK rows held per lane
     static constexpr int NP = MK * MK + 5;               // partials per CTA
     static constexpr int NT = NW * 32;
     // shared memory layout (bytes)
     static constexpr int OFF_R = 0;
     static constexpr int SZ_R = RROWS * RP * 4;          // one R tile buffer (two are kept)
-    static constexpr int GPAD = QB - 1;                  // zero rows above and below the g tile
+    static constexpr int GPAD = KF > 2 ? KF - 1 : 1;     // zero rows above and below the g tile
     static constexpr int OFF_G = OFF_R + 2 * SZ_R;
     // tiles between float64 flushes: each lane's float32 sums then cover at
     // most 4096 pixels
@@ -203,21 +213,26 @@ struct EvalShape {
     static constexpr int OFF_K = OFF_G + SZ_G;
     static constexpr int SZ_K = (MK * KP + 4) * 4;
     static constexpr int OFF_D = (OFF_K + SZ_K + 15) & ~15;
-    static constexpr int SZ_D = (MK * MK + 5 * NW) * 8;
+    // float64: dK rows with one owner, per-warp copies of the RM shared rows,
+    // per-warp {loss, dB0, count, kR^2, k}
+    static constexpr int OFF_D_RM = MK * MK;
+    static constexpr int OFF_D_W5 = OFF_D_RM + NW * RM * MK;
+    static constexpr int SZ_D = (OFF_D_W5 + 5 * NW) * 8;
     static constexpr int SMEM = OFF_D + SZ_D;
 };
 
-// Backward rows of one warp owning NQ kernel rows a_lo .. a_lo+NQ-1:
-// dk[qb][b] += sum_y sum_p g[y][x+p] R[y+a_lo+qb][x+b+p], y = rr - qb.  The g
-// tile has QB-1 zero rows above and below, so every y read is in bounds and
-// no branch separates the NQ rows' FMAs.
-template <int MK, int QB, int NQ, int RP, int RWIN>
-__device__ __forceinline__ void bwd_rows(const float *rb2, const float *gb, int TH,
-                                         float (&dk)[QB][MK]) {
+// Backward rows: dk[OFF+qb][b] += sum_rr sum_p g[y][x+p] R[r0+rr][x+b+p] with
+// y = y0 + rr - qb, for NQ kernel rows.  Whole-tile rows (SLICE = false)
+// rely on the zero rows around the g tile; slice rows (SLICE = true) keep
+// y inside [y0, y0 + NS) and read a zero row otherwise.  Each R row window is
+// loaded once and used by all NQ kernel rows, m column offsets and 4 pixels.
+template <int MK, int QB, int OFF, int NQ, int RP, int RWIN, bool SLICE, int NS>
+__device__ __forceinline__ void bwd_rows(const float *rrow, const float *g0, const float *gzero,
+                                         int n_rr, float (&dk)[QB][MK]) {
 #pragma unroll 1
-    for (int rr = 0; rr < TH + NQ - 1; ++rr) {
+    for (int rr = 0; rr < n_rr; ++rr) {
         float win[RWIN];
-        const float4 *rp4 = reinterpret_cast<const float4 *>(rb2 + rr * RP);
+        const float4 *rp4 = reinterpret_cast<const float4 *>(rrow + rr * RP);
 #pragma unroll
         for (int v4 = 0; v4 < RWIN / 4; ++v4) {
             const float4 t = rp4[v4];
@@ -228,7 +243,11 @@ __device__ __forceinline__ void bwd_rows(const float *rb2, const float *gb, int 
         }
         float4 g4[NQ];
 #pragma unroll
-        for (int qb = 0; qb < NQ; ++qb) g4[qb] = *reinterpret_cast<const float4 *>(gb + (rr - qb) * kTW);
+        for (int qb = 0; qb < NQ; ++qb) {
+            const float *gp = g0 + (rr - qb) * kTW;
+            if (SLICE && (rr - qb < 0 || rr - qb >= NS)) gp = gzero;
+            g4[qb] = *reinterpret_cast<const float4 *>(gp);
+        }
         // pixel p outer: consecutive FMAs update different accumulators
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -236,15 +255,15 @@ __device__ __forceinline__ void bwd_rows(const float *rb2, const float *gb, int 
             for (int qb = 0; qb < NQ; ++qb) {
                 const float gv = p == 0 ? g4[qb].x : p == 1 ? g4[qb].y : p == 2 ? g4[qb].z : g4[qb].w;
 #pragma unroll
-                for (int b = 0; b < MK; ++b) dk[qb][b] = fmaf(gv, win[b + p], dk[qb][b]);
+                for (int b = 0; b < MK; ++b) dk[OFF + qb][b] = fmaf(gv, win[b + p], dk[OFF + qb][b]);
             }
         }
     }
 }
 
-template <int MK, int NW, int QF, int MINB, int MODE>
+template <int MK, int NW, int QF, int MINB, int SPLIT, int MODE>
 __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args) {
-    using S = EvalShape<MK, NW, QF>;
+    using S = EvalShape<MK, NW, QF, SPLIT>;
     constexpr int TH = S::TH, RP = S::RP, RWIN = S::RWIN, KP = S::KP, QB = S::QB;
     constexpr int H2 = MK / 2;
     if (args.done_flag != nullptr && *((volatile const int *)args.done_flag) != 0) return;
@@ -261,7 +280,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
 
     for (int i = tid; i < MK * KP + 4; i += S::NT) Ks[i] = args.Kpad[i];
     if (MODE == kModeGrad) {
-        for (int i = tid; i < MK * MK + 5 * NW; i += S::NT) acc64[i] = 0.0;
+        for (int i = tid; i < S::OFF_D_W5 + 5 * NW; i += S::NT) acc64[i] = 0.0;
         for (int i = tid; i < S::GPAD * kTW; i += S::NT) {
             gs[i] = 0.f;
             gs[(S::GPAD + TH) * kTW + i] = 0.f;
@@ -271,9 +290,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
     __syncthreads();
     const float B0 = Ks[MK * KP];
 
-    // kernel rows owned by this warp in the backward pass (balanced split)
-    const int a_lo = (warp * MK) / NW;
-    const int nqb = ((warp + 1) * MK) / NW - a_lo;
+    constexpr int KF = S::KF, RM = S::RM;
+    // whole-tile kernel rows of this warp: [a_lo, a_lo + nq)
+    const int a_lo = SPLIT ? warp * KF : (warp * MK) / NW;
+    const int nq = SPLIT ? KF : ((warp + 1) * MK) / NW - a_lo;
 
     // per-lane float32 sums, flushed to the float64 CTA accumulators every
     // FLUSH tiles: dK rows owned by this warp, and loss / dB0 / count /
@@ -288,19 +308,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
     auto flush = [&]() {
 #pragma unroll
         for (int qb = 0; qb < QB; ++qb) {
-            if (qb < nqb) {
+            if (qb < KF && qb >= nq) continue;
+            double *dst = (qb < KF) ? acc64 + (a_lo + qb) * MK
+                                    : acc64 + S::OFF_D_RM + (warp * RM + (qb - KF)) * MK;
 #pragma unroll
-                for (int b = 0; b < MK; ++b) {
-                    const float sm = warp_sum(dk[qb][b]);
-                    if (lane == 0) acc64[(a_lo + qb) * MK + b] += (double)sm;
-                    dk[qb][b] = 0.f;
-                }
+            for (int b = 0; b < MK; ++b) {
+                const float sm = warp_sum(dk[qb][b]);
+                if (lane == 0) dst[b] += (double)sm;
+                dk[qb][b] = 0.f;
             }
         }
         const float l = warp_sum(lsum), g = warp_sum(gsum), c = warp_sum(cnt);
         const float k = warp_sum(ksum), kr = warp_sum(kr2sum);
         if (lane == 0) {
-            double *w5 = acc64 + MK * MK + 5 * warp;
+            double *w5 = acc64 + S::OFF_D_W5 + 5 * warp;
             w5[0] += (double)l;
             w5[1] += (double)g;
             w5[2] += (double)c;
@@ -353,17 +374,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
                 win[4 * v4 + 2] = t.z;
                 win[4 * v4 + 3] = t.w;
             }
-            // K columns in groups of 4; the next group's broadcast loads are
-            // issued before the current group's FMAs
-            float4 kq[QF], kn[QF];
-#pragma unroll
-            for (int q = 0; q < QF; ++q) kq[q] = K4[(r - q) * (KP / 4)];
+            // K columns in groups of 4 (warp-uniform broadcast loads)
 #pragma unroll
             for (int b4 = 0; b4 < KP / 4; ++b4) {
-                if (b4 + 1 < KP / 4) {
+                float4 kq[QF];
 #pragma unroll
-                    for (int q = 0; q < QF; ++q) kn[q] = K4[(r - q) * (KP / 4) + b4 + 1];
-                }
+                for (int q = 0; q < QF; ++q) kq[q] = K4[(r - q) * (KP / 4) + b4];
 #pragma unroll
                 for (int bb = 0; bb < 4; ++bb) {
                     const int b = 4 * b4 + bb;
@@ -375,10 +391,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
                             for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(kv, win[p + b], acc[q][p]);
                         }
                     }
-                }
-                if (b4 + 1 < KP / 4) {
-#pragma unroll
-                    for (int q = 0; q < QF; ++q) kq[q] = kn[q];
                 }
             }
         }
@@ -464,12 +476,19 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
         __syncthreads();  // g tile complete
 
         // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b], a in [a_lo, a_lo+nqb)
-        const float *rb2 = Rs + a_lo * RP + 4 * lane;
-        const float *gb = gt + 4 * lane;
-        if (nqb == QB)
-            bwd_rows<MK, QB, QB, RP, RWIN>(rb2, gb, TH, dk);
-        else if (QB > 1 && nqb == QB - 1)
-            bwd_rows<MK, QB, (QB > 1 ? QB - 1 : 1), RP, RWIN>(rb2, gb, TH, dk);
+        const float *gzero = gs + 4 * lane;   // a zero row above the g tile
+        if (KF > 0 && nq == KF)
+            bwd_rows<MK, QB, 0, (KF > 0 ? KF : 1), RP, RWIN, false, TH>(
+                Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 1, dk);
+        else if (KF > 1 && nq == KF - 1)   // SPLIT 0: the warps with one row fewer
+            bwd_rows<MK, QB, 0, (KF > 1 ? KF - 1 : 1), RP, RWIN, false, TH>(
+                Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 2, dk);
+        if (RM > 0) {
+            const int ys = warp * QF;          // this warp's slice of the tile rows
+            bwd_rows<MK, QB, KF, (RM > 0 ? RM : 1), RP, RWIN, true, QF>(
+                Rs + (NW * KF + ys) * RP + 4 * lane, gt + ys * kTW + 4 * lane, gzero,
+                QF + RM - 1, dk);
+        }
         // ---- 5. float32 sums -> float64 every FLUSH tiles (each kernel row
         // is owned by one warp, so the warps write disjoint accumulators)
         if (++since_flush == S::FLUSH) {
@@ -484,11 +503,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
         if (since_flush > 0) flush();
         __syncthreads();
         double *out = args.partials + (size_t)blockIdx.x * S::NP;
-        for (int i = tid; i < MK * MK; i += S::NT) out[1 + i] = acc64[i];
+        for (int i = tid; i < (MK - RM) * MK; i += S::NT) out[1 + i] = acc64[i];
+        for (int i = tid; i < RM * MK; i += S::NT) {   // shared rows: per-warp copies, fixed order
+            double t = 0.0;
+            for (int w = 0; w < NW; ++w) t += acc64[S::OFF_D_RM + w * RM * MK + i];
+            out[1 + (MK - RM) * MK + i] = t;
+        }
         if (tid < 5) {
             // tid 0: loss, 1: dB0, 2: pixel count, 3: sum kappa R^2, 4: sum kappa
             double t = 0.0;
-            for (int w = 0; w < NW; ++w) t += acc64[MK * MK + 5 * w + tid];
+            for (int w = 0; w < NW; ++w) t += acc64[S::OFF_D_W5 + 5 * w + tid];
             out[tid == 0 ? 0 : MK * MK + tid] = t;
         }
     }

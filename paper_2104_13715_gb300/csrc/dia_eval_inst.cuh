@@ -1,14 +1,14 @@
-// Instantiation helper: DIA_EVAL_INST(MK, V, NW, QF, MINB) defines
+// Instantiation helper: DIA_EVAL_INST(MK, V, NW, QF, MINB, SPLIT) defines
 // kernel_info_<MK>_<V>() for the fused kernel of side MK, tile variant V.
 #pragma once
 
 #include "dia_dispatch.h"
 #include "dia_eval.cuh"
 
-#define DIA_EVAL_INST(MKV, VAR, NWV, QFV, MBV)                                                 \
+#define DIA_EVAL_INST(MKV, VAR, NWV, QFV, MBV, SPV)                                               \
     namespace dia {                                                                            \
     bool kernel_info_##MKV##_##VAR(KernelInfo *o) {                                            \
-        using S = EvalShape<MKV, NWV, QFV>;                                                    \
+        using S = EvalShape<MKV, NWV, QFV, SPV>;                                               \
         o->mk = MKV;                                                                           \
         o->variant = VAR;                                                                      \
         o->nw = NWV;                                                                           \
@@ -19,8 +19,8 @@
         o->smem = S::SMEM;                                                                     \
         o->np = S::NP;                                                                         \
         o->kp = S::KP;                                                                         \
-        o->fn[kModeGrad] = (const void *)&eval_kernel<MKV, NWV, QFV, MBV, kModeGrad>;          \
-        o->fn[kModeForward] = (const void *)&eval_kernel<MKV, NWV, QFV, MBV, kModeForward>;    \
+        o->fn[kModeGrad] = (const void *)&eval_kernel<MKV, NWV, QFV, MBV, SPV, kModeGrad>;     \
+        o->fn[kModeForward] = (const void *)&eval_kernel<MKV, NWV, QFV, MBV, SPV, kModeForward>; \
         return true;                                                                           \
     }                                                                                          \
     }

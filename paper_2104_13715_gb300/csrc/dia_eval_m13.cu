@@ -1,5 +1,7 @@
 // Fused evaluation kernels for kernel sides [13, 15] (generated by gen_instances.py)
 #include "dia_eval_inst.cuh"
 
-DIA_EVAL_INST(13, 0, 13, 8, 1)
-DIA_EVAL_INST(15, 0, 8, 8, 1)
+DIA_EVAL_INST(13, 0, 12, 4, 1, 1)
+DIA_EVAL_INST(13, 1, 13, 4, 1, 0)
+DIA_EVAL_INST(15, 0, 12, 4, 1, 1)
+DIA_EVAL_INST(15, 1, 8, 8, 1, 0)

@@ -5,14 +5,25 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 # kernel side -> list of tile variants (NW warps, QF output rows per warp in the
-# forward pass, MINB minimum resident CTAs per SM for the register budget).
+# forward pass, MINB minimum resident CTAs per SM for the register budget,
+# SPLIT = backward row split: 0 whole rows ceil/floor per warp, 1 equal work
+# with the MK % NW last rows split by tile-row slices).
 # Variant 0 is the default; the autotuner may pick another at run time.
 VARIANTS = {
-    1: [(8, 8, 1)], 3: [(8, 8, 1)], 5: [(8, 8, 1)], 7: [(8, 8, 1)],
-    9: [(9, 8, 1)], 11: [(11, 8, 1)], 13: [(13, 8, 1)], 15: [(8, 8, 1)],
-    17: [(9, 8, 1)], 19: [(10, 8, 1)], 21: [(7, 8, 1)], 23: [(8, 8, 1)],
-    25: [(9, 8, 1), (9, 4, 1), (13, 4, 1), (9, 4, 2), (7, 8, 1), (13, 8, 1)],
-    27: [(9, 8, 1)], 29: [(10, 8, 1)], 31: [(11, 8, 1)],
+    1: [(8, 8, 1, 0)], 3: [(8, 8, 1, 0)], 5: [(8, 8, 1, 0)],
+    7: [(8, 8, 1, 0), (8, 4, 1, 0)],
+    9: [(8, 8, 1, 1), (8, 4, 1, 1)],
+    11: [(8, 8, 1, 1), (8, 4, 1, 1), (12, 4, 1, 0)],
+    13: [(12, 4, 1, 1), (13, 4, 1, 0)],
+    15: [(12, 4, 1, 1), (8, 8, 1, 0)],
+    17: [(8, 8, 1, 1), (8, 4, 1, 1)],
+    19: [(8, 4, 1, 1), (8, 8, 1, 1), (10, 4, 1, 0)],
+    21: [(7, 4, 1, 0), (7, 8, 1, 0), (8, 4, 1, 0)],
+    23: [(8, 4, 1, 0), (8, 8, 1, 0)],
+    25: [(12, 4, 1, 1), (12, 2, 1, 1), (13, 4, 1, 0), (9, 4, 1, 0), (8, 4, 1, 0)],
+    27: [(9, 4, 1, 0), (12, 4, 1, 0)],
+    29: [(10, 4, 1, 0), (8, 4, 1, 0)],
+    31: [(8, 4, 1, 0), (11, 4, 1, 0)],
 }
 GROUPS = [[1, 3, 5, 7], [9, 11], [13, 15], [17], [19], [21], [23], [25], [27], [29], [31]]
 
@@ -25,8 +36,8 @@ def main():
         lines = [f"// Fused evaluation kernels for kernel sides {grp} (generated by gen_instances.py)",
                  '#include "dia_eval_inst.cuh"', ""]
         for mk in grp:
-            for v, (nw, qf, mb) in enumerate(VARIANTS[mk]):
-                lines.append(f"DIA_EVAL_INST({mk}, {v}, {nw}, {qf}, {mb})")
+            for v, (nw, qf, mb, sp) in enumerate(VARIANTS[mk]):
+                lines.append(f"DIA_EVAL_INST({mk}, {v}, {nw}, {qf}, {mb}, {sp})")
         with open(os.path.join(HERE, f"dia_eval_m{grp[0]:02d}.cu"), "w") as fh:
             fh.write("\n".join(lines) + "\n")
     decl, cases = [], []
