@@ -18,6 +18,7 @@ bool kernel_info_11_1(KernelInfo *o);
 bool kernel_info_11_2(KernelInfo *o);
 bool kernel_info_13_0(KernelInfo *o);
 bool kernel_info_13_1(KernelInfo *o);
+bool kernel_info_13_2(KernelInfo *o);
 bool kernel_info_15_0(KernelInfo *o);
 bool kernel_info_15_1(KernelInfo *o);
 bool kernel_info_17_0(KernelInfo *o);
@@ -34,7 +35,6 @@ bool kernel_info_25_0(KernelInfo *o);
 bool kernel_info_25_1(KernelInfo *o);
 bool kernel_info_25_2(KernelInfo *o);
 bool kernel_info_25_3(KernelInfo *o);
-bool kernel_info_25_4(KernelInfo *o);
 bool kernel_info_27_0(KernelInfo *o);
 bool kernel_info_27_1(KernelInfo *o);
 bool kernel_info_29_0(KernelInfo *o);
@@ -54,13 +54,13 @@ int kernel_variants(int mk) {
         case 7: return 2;
         case 9: return 2;
         case 11: return 3;
-        case 13: return 2;
+        case 13: return 3;
         case 15: return 2;
         case 17: return 2;
         case 19: return 3;
         case 21: return 3;
         case 23: return 2;
-        case 25: return 5;
+        case 25: return 4;
         case 27: return 2;
         case 29: return 2;
         case 31: return 2;
@@ -83,7 +83,7 @@ bool kernel_info_variant(int mk, int v, KernelInfo *o) {
         case 11:
             switch (v) { case 0: return kernel_info_11_0(o); case 1: return kernel_info_11_1(o); case 2: return kernel_info_11_2(o); default: return false; }
         case 13:
-            switch (v) { case 0: return kernel_info_13_0(o); case 1: return kernel_info_13_1(o); default: return false; }
+            switch (v) { case 0: return kernel_info_13_0(o); case 1: return kernel_info_13_1(o); case 2: return kernel_info_13_2(o); default: return false; }
         case 15:
             switch (v) { case 0: return kernel_info_15_0(o); case 1: return kernel_info_15_1(o); default: return false; }
         case 17:
@@ -95,7 +95,7 @@ bool kernel_info_variant(int mk, int v, KernelInfo *o) {
         case 23:
             switch (v) { case 0: return kernel_info_23_0(o); case 1: return kernel_info_23_1(o); default: return false; }
         case 25:
-            switch (v) { case 0: return kernel_info_25_0(o); case 1: return kernel_info_25_1(o); case 2: return kernel_info_25_2(o); case 3: return kernel_info_25_3(o); case 4: return kernel_info_25_4(o); default: return false; }
+            switch (v) { case 0: return kernel_info_25_0(o); case 1: return kernel_info_25_1(o); case 2: return kernel_info_25_2(o); case 3: return kernel_info_25_3(o); default: return false; }
         case 27:
             switch (v) { case 0: return kernel_info_27_0(o); case 1: return kernel_info_27_1(o); default: return false; }
         case 29:

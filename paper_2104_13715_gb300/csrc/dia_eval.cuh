@@ -23,8 +23,10 @@
 //      (equal work per warp); lanes split the columns; each R row window is
 //      reused by every kernel row it feeds, the m column offsets and the
 //      four pixels of the lane;
-//   5. per-lane float32 sums (at most 4096 pixels each) are reduced over the
-//      warp and added in float64 to per-CTA shared accumulators.
+//   5. dK: per-lane float32 sums over one tile, reduced over the warp by a
+//      halving butterfly and added to per-warp Kahan-compensated float32
+//      shared accumulators; loss sums: per-lane float32 over <= 4096 pixels,
+//      then float64.  Everything is combined in float64 at the end.
 // At the end each CTA writes m*m + 5 float64 partials (loss, dK, dB0, pixel
 // count, and two curvature sums for the optimiser's diagonal preconditioner);
 // a separate kernel sums them in a fixed order.
@@ -183,6 +185,57 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+template <int RWIN>
+__device__ __forceinline__ void load_win(float (&win)[RWIN], const float *row) {
+    const float4 *rp4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int v4 = 0; v4 < RWIN / 4; ++v4) {
+        const float4 t = rp4[v4];
+        win[4 * v4 + 0] = t.x;
+        win[4 * v4 + 1] = t.y;
+        win[4 * v4 + 2] = t.z;
+        win[4 * v4 + 3] = t.w;
+    }
+}
+
+// Warp reduction of N per-lane values by halving: at each of the five
+// butterfly stages a lane keeps one half of its values (chosen by its lane
+// bit), adds the partner's copy of that half, and sends the other half.
+// Afterwards lane L holds the warp sums of NF = ceil(N/32) entries, entry j
+// being value index base(L) + j; halving_index() gives that index (or -1 for
+// a padding slot).  75 values cost 75 shuffles instead of 375.
+template <int N>
+struct Halving {
+    static constexpr int H1 = (N + 1) / 2, H2 = (H1 + 1) / 2, H3 = (H2 + 1) / 2, H4 = (H3 + 1) / 2,
+                         H5 = (H4 + 1) / 2;
+};
+
+template <int N, int O>
+__device__ __forceinline__ void halve(const float *v, float *w, bool up) {
+    constexpr int H = (N + 1) / 2;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float lo = v[i];
+        const float hi = (i + H < N) ? v[i + H] : 0.f;
+        const float keep = up ? hi : lo;
+        const float send = up ? lo : hi;
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ int halving_index(int lane, int j) {
+    using Hv = Halving<N>;
+    const int hs[5] = {Hv::H1, Hv::H2, Hv::H3, Hv::H4, Hv::H5};
+    const int ns[5] = {N, Hv::H1, Hv::H2, Hv::H3, Hv::H4};   // sizes before each stage
+    int p = j;
+    for (int st = 4; st >= 0; --st) {
+        if (lane & (16 >> st)) p += hs[st];
+        if (p >= ns[st]) return -1;
+    }
+    return p;
+}
+
 // SPLIT selects how the backward's kernel rows are shared among the warps:
 // 0 = whole rows, ceil(MK/NW) or floor(MK/NW) per warp; 1 = MK = NW*KF + RM
 // with KF whole rows per warp and the RM last rows split by tile-row slices.
@@ -213,12 +266,13 @@ struct EvalShape {
     static constexpr int OFF_K = OFF_G + SZ_G;
     static constexpr int SZ_K = (MK * KP + 4) * 4;
     static constexpr int OFF_D = (OFF_K + SZ_K + 15) & ~15;
-    // float64: dK rows with one owner, per-warp copies of the RM shared rows,
-    // per-warp {loss, dB0, count, kR^2, k}
-    static constexpr int OFF_D_RM = MK * MK;
-    static constexpr int OFF_D_W5 = OFF_D_RM + NW * RM * MK;
-    static constexpr int SZ_D = (OFF_D_W5 + 5 * NW) * 8;
-    static constexpr int SMEM = OFF_D + SZ_D;
+    // float64 per-warp {loss, dB0, count, kR^2, k}
+    static constexpr int SZ_D = 5 * NW * 8;
+    // float32 Kahan pairs (sum, compensation) of each warp's QB x MK dK rows
+    static constexpr int NK = QB * MK;
+    static constexpr int OFF_KS = OFF_D + SZ_D;
+    static constexpr int SZ_KS = NW * 2 * NK * 4;
+    static constexpr int SMEM = OFF_KS + SZ_KS;
 };
 
 // Backward rows: dk[OFF+qb][b] += sum_rr sum_p g[y][x+p] R[r0+rr][x+b+p] with
@@ -227,42 +281,62 @@ struct EvalShape {
 // y inside [y0, y0 + NS) and read a zero row otherwise.  Each R row window is
 // loaded once and used by all NQ kernel rows, m column offsets and 4 pixels.
 template <int MK, int QB, int OFF, int NQ, int RP, int RWIN, bool SLICE, int NS>
-__device__ __forceinline__ void bwd_rows(const float *rrow, const float *g0, const float *gzero,
-                                         int n_rr, float (&dk)[QB][MK]) {
-#pragma unroll 1
-    for (int rr = 0; rr < n_rr; ++rr) {
-        float win[RWIN];
-        const float4 *rp4 = reinterpret_cast<const float4 *>(rrow + rr * RP);
+__device__ __forceinline__ void bwd_row(const float (&win)[RWIN], const float *g0, const float *gzero,
+                                        int rr, float (&dk)[QB * MK]) {
+    float4 g4[NQ];
 #pragma unroll
-        for (int v4 = 0; v4 < RWIN / 4; ++v4) {
-            const float4 t = rp4[v4];
-            win[4 * v4 + 0] = t.x;
-            win[4 * v4 + 1] = t.y;
-            win[4 * v4 + 2] = t.z;
-            win[4 * v4 + 3] = t.w;
-        }
-        float4 g4[NQ];
+    for (int qb = 0; qb < NQ; ++qb) {
+        const float *gp = g0 + (rr - qb) * kTW;
+        if (SLICE && (rr - qb < 0 || rr - qb >= NS)) gp = gzero;
+        g4[qb] = *reinterpret_cast<const float4 *>(gp);
+    }
+    // pixel p outer: consecutive FMAs update different accumulators
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
 #pragma unroll
         for (int qb = 0; qb < NQ; ++qb) {
-            const float *gp = g0 + (rr - qb) * kTW;
-            if (SLICE && (rr - qb < 0 || rr - qb >= NS)) gp = gzero;
-            g4[qb] = *reinterpret_cast<const float4 *>(gp);
-        }
-        // pixel p outer: consecutive FMAs update different accumulators
+            const float gv = p == 0 ? g4[qb].x : p == 1 ? g4[qb].y : p == 2 ? g4[qb].z : g4[qb].w;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-#pragma unroll
-            for (int qb = 0; qb < NQ; ++qb) {
-                const float gv = p == 0 ? g4[qb].x : p == 1 ? g4[qb].y : p == 2 ? g4[qb].z : g4[qb].w;
-#pragma unroll
-                for (int b = 0; b < MK; ++b) dk[OFF + qb][b] = fmaf(gv, win[b + p], dk[OFF + qb][b]);
-            }
+            for (int b = 0; b < MK; ++b)
+                dk[(OFF + qb) * MK + b] = fmaf(gv, win[b + p], dk[(OFF + qb) * MK + b]);
         }
     }
 }
 
-template <int MK, int NW, int QF, int MINB, int SPLIT, int MODE>
-__global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args) {
+// Backward rows: dk[OFF+qb][b] += sum_rr sum_p g[y][x+p] R[r0+rr][x+b+p] with
+// y = y0 + rr - qb, for NQ kernel rows.  Whole-tile rows (SLICE = false)
+// rely on the zero rows around the g tile; slice rows (SLICE = true) keep
+// y inside [y0, y0 + NS) and read a zero row otherwise.  Each R row window is
+// loaded once and used by all NQ kernel rows, m column offsets and 4 pixels;
+// with PF the next row's window is loaded while the current one is used.
+template <int MK, int QB, int OFF, int NQ, int RP, int RWIN, bool SLICE, int NS, int PF>
+__device__ __forceinline__ void bwd_rows(const float *rrow, const float *g0, const float *gzero,
+                                         int n_rr, float (&dk)[QB * MK]) {
+    if (PF) {
+        float wa[RWIN], wb[RWIN];
+        load_win<RWIN>(wa, rrow);
+#pragma unroll 1
+        for (int rr = 0; rr < n_rr; rr += 2) {
+            const bool two = rr + 1 < n_rr;
+            if (two) load_win<RWIN>(wb, rrow + (rr + 1) * RP);
+            bwd_row<MK, QB, OFF, NQ, RP, RWIN, SLICE, NS>(wa, g0, gzero, rr, dk);
+            if (two) {
+                if (rr + 2 < n_rr) load_win<RWIN>(wa, rrow + (rr + 2) * RP);
+                bwd_row<MK, QB, OFF, NQ, RP, RWIN, SLICE, NS>(wb, g0, gzero, rr + 1, dk);
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int rr = 0; rr < n_rr; ++rr) {
+            float win[RWIN];
+            load_win<RWIN>(win, rrow + rr * RP);
+            bwd_row<MK, QB, OFF, NQ, RP, RWIN, SLICE, NS>(win, g0, gzero, rr, dk);
+        }
+    }
+}
+
+template <int MK, int NW, int QF, int PF, int SPLIT, int MODE>
+__global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
     using S = EvalShape<MK, NW, QF, SPLIT>;
     constexpr int TH = S::TH, RP = S::RP, RWIN = S::RWIN, KP = S::KP, QB = S::QB;
     constexpr int H2 = MK / 2;
@@ -273,14 +347,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
     float *Rbuf1 = Rbuf0 + S::RROWS * RP;
     float *gs = reinterpret_cast<float *>(smem + S::OFF_G);
     float *Ks = reinterpret_cast<float *>(smem + S::OFF_K);
-    double *acc64 = reinterpret_cast<double *>(smem + S::OFF_D);  // dK[MK*MK], then per warp
-                                                                  // {loss, dB0, count, kR2, k}
+    double *acc64 = reinterpret_cast<double *>(smem + S::OFF_D);  // per warp {loss, dB0, count, kR2, k}
+    float *kahan = reinterpret_cast<float *>(smem + S::OFF_KS);    // per warp [NK sums | NK comps]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int i = tid; i < MK * KP + 4; i += S::NT) Ks[i] = args.Kpad[i];
     if (MODE == kModeGrad) {
-        for (int i = tid; i < S::OFF_D_W5 + 5 * NW; i += S::NT) acc64[i] = 0.0;
+        for (int i = tid; i < 5 * NW; i += S::NT) acc64[i] = 0.0;
+        for (int i = tid; i < NW * 2 * S::NK; i += S::NT) kahan[i] = 0.f;
         for (int i = tid; i < S::GPAD * kTW; i += S::NT) {
             gs[i] = 0.f;
             gs[(S::GPAD + TH) * kTW + i] = 0.f;
@@ -295,33 +370,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
     const int a_lo = SPLIT ? warp * KF : (warp * MK) / NW;
     const int nq = SPLIT ? KF : ((warp + 1) * MK) / NW - a_lo;
 
-    // per-lane float32 sums, flushed to the float64 CTA accumulators every
-    // FLUSH tiles: dK rows owned by this warp, and loss / dB0 / count /
-    // curvature sums of the lane's pixels
-    float dk[QB][MK];
-#pragma unroll
-    for (int qb = 0; qb < QB; ++qb)
-#pragma unroll
-        for (int b = 0; b < MK; ++b) dk[qb][b] = 0.f;
+    // per-lane float32 loss / dB0 / count / curvature sums, flushed to the
+    // per-warp float64 accumulators every FLUSH tiles (<= 4096 px per lane)
     float lsum = 0.f, gsum = 0.f, cnt = 0.f, ksum = 0.f, kr2sum = 0.f;
     int since_flush = 0;
     auto flush = [&]() {
-#pragma unroll
-        for (int qb = 0; qb < QB; ++qb) {
-            if (qb < KF && qb >= nq) continue;
-            double *dst = (qb < KF) ? acc64 + (a_lo + qb) * MK
-                                    : acc64 + S::OFF_D_RM + (warp * RM + (qb - KF)) * MK;
-#pragma unroll
-            for (int b = 0; b < MK; ++b) {
-                const float sm = warp_sum(dk[qb][b]);
-                if (lane == 0) dst[b] += (double)sm;
-                dk[qb][b] = 0.f;
-            }
-        }
         const float l = warp_sum(lsum), g = warp_sum(gsum), c = warp_sum(cnt);
         const float k = warp_sum(ksum), kr = warp_sum(kr2sum);
         if (lane == 0) {
-            double *w5 = acc64 + S::OFF_D_W5 + 5 * warp;
+            double *w5 = acc64 + 5 * warp;
             w5[0] += (double)l;
             w5[1] += (double)g;
             w5[2] += (double)c;
@@ -330,6 +387,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
         }
         lsum = gsum = cnt = ksum = kr2sum = 0.f;
     };
+    // dK of one tile: per-lane float32 sums over the tile's 4 x TH pixels,
+    // reduced over the warp by halving and added (Kahan-compensated float32)
+    // to this warp's shared accumulators
+    constexpr int NK = S::NK, NF = Halving<NK>::H5;
+    float *ksum_w = kahan + warp * 2 * NK;
+    int kidx[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) kidx[j] = halving_index<NK>(lane, j);
 
     // ---- 1. R tiles (+ halo) are staged with cp.async, the next tile's copy
     // overlapping the current tile's compute (two buffers)
@@ -362,18 +427,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
         const float4 *K4 = reinterpret_cast<const float4 *>(Ks);
         // R rows r with every output row q of the warp active (kernel row a = r - q
         // in [0, MK)): no branch, all QF x 4 accumulators interleaved per K column
-#pragma unroll 1
-        for (int r = QF - 1; r <= MK - 1; ++r) {
-            float win[RWIN];
-            const float4 *rp4 = reinterpret_cast<const float4 *>(rbase + r * RP);
-#pragma unroll
-            for (int v4 = 0; v4 < RWIN / 4; ++v4) {
-                const float4 t = rp4[v4];
-                win[4 * v4 + 0] = t.x;
-                win[4 * v4 + 1] = t.y;
-                win[4 * v4 + 2] = t.z;
-                win[4 * v4 + 3] = t.w;
-            }
+        auto fwd_interior = [&](const float (&win)[RWIN], int r) {
             // K columns in groups of 4 (warp-uniform broadcast loads)
 #pragma unroll
             for (int b4 = 0; b4 < KP / 4; ++b4) {
@@ -392,6 +446,28 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
                         }
                     }
                 }
+            }
+        };
+        if (PF) {
+            // the next row's window is loaded while the current one is used
+            float wa[RWIN], wb[RWIN];
+            if (QF - 1 <= MK - 1) load_win<RWIN>(wa, rbase + (QF - 1) * RP);
+#pragma unroll 1
+            for (int r = QF - 1; r <= MK - 1; r += 2) {
+                const bool two = r + 1 <= MK - 1;
+                if (two) load_win<RWIN>(wb, rbase + (r + 1) * RP);
+                fwd_interior(wa, r);
+                if (two) {
+                    if (r + 2 <= MK - 1) load_win<RWIN>(wa, rbase + (r + 2) * RP);
+                    fwd_interior(wb, r + 1);
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int r = QF - 1; r <= MK - 1; ++r) {
+                float win[RWIN];
+                load_win<RWIN>(win, rbase + r * RP);
+                fwd_interior(win, r);
             }
         }
         // the first and last QF-1 R rows feed only some output rows (with
@@ -475,22 +551,44 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
         }
         __syncthreads();  // g tile complete
 
-        // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b], a in [a_lo, a_lo+nqb)
+        // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b]
+        float dk[NK];
+#pragma unroll
+        for (int i = 0; i < NK; ++i) dk[i] = 0.f;
         const float *gzero = gs + 4 * lane;   // a zero row above the g tile
         if (KF > 0 && nq == KF)
-            bwd_rows<MK, QB, 0, (KF > 0 ? KF : 1), RP, RWIN, false, TH>(
+            bwd_rows<MK, QB, 0, (KF > 0 ? KF : 1), RP, RWIN, false, TH, PF>(
                 Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 1, dk);
         else if (KF > 1 && nq == KF - 1)   // SPLIT 0: the warps with one row fewer
-            bwd_rows<MK, QB, 0, (KF > 1 ? KF - 1 : 1), RP, RWIN, false, TH>(
+            bwd_rows<MK, QB, 0, (KF > 1 ? KF - 1 : 1), RP, RWIN, false, TH, PF>(
                 Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 2, dk);
         if (RM > 0) {
             const int ys = warp * QF;          // this warp's slice of the tile rows
-            bwd_rows<MK, QB, KF, (RM > 0 ? RM : 1), RP, RWIN, true, QF>(
+            bwd_rows<MK, QB, KF, (RM > 0 ? RM : 1), RP, RWIN, true, QF, 0>(
                 Rs + (NW * KF + ys) * RP + 4 * lane, gt + ys * kTW + 4 * lane, gzero,
                 QF + RM - 1, dk);
         }
-        // ---- 5. float32 sums -> float64 every FLUSH tiles (each kernel row
-        // is owned by one warp, so the warps write disjoint accumulators)
+        // ---- 5. warp-reduce this tile's dK and add it to the warp's accumulators
+        {
+            using Hv = Halving<NK>;
+            float w1[Hv::H1], w2[Hv::H2], w3[Hv::H3], w4[Hv::H4], w5[Hv::H5];
+            halve<NK, 16>(dk, w1, lane & 16);
+            halve<Hv::H1, 8>(w1, w2, lane & 8);
+            halve<Hv::H2, 4>(w2, w3, lane & 4);
+            halve<Hv::H3, 2>(w3, w4, lane & 2);
+            halve<Hv::H4, 1>(w4, w5, lane & 1);
+#pragma unroll
+            for (int j = 0; j < NF; ++j) {
+                const int ix = kidx[j];
+                if (ix >= 0) {
+                    float *sm = ksum_w + ix, *cm = ksum_w + NK + ix;
+                    const float y = w5[j] - *cm;
+                    const float t = *sm + y;
+                    *cm = (t - *sm) - y;
+                    *sm = t;
+                }
+            }
+        }
         if (++since_flush == S::FLUSH) {
             flush();
             since_flush = 0;
@@ -503,16 +601,32 @@ __global__ void __launch_bounds__(NW * 32, MINB) eval_kernel(const EvalArgs args
         if (since_flush > 0) flush();
         __syncthreads();
         double *out = args.partials + (size_t)blockIdx.x * S::NP;
-        for (int i = tid; i < (MK - RM) * MK; i += S::NT) out[1 + i] = acc64[i];
-        for (int i = tid; i < RM * MK; i += S::NT) {   // shared rows: per-warp copies, fixed order
+        // rows with one owner warp (w, qb < nq(w)); the RM shared rows summed
+        // over the warps' copies in a fixed order
+        for (int i = tid; i < MK * MK; i += S::NT) {
+            const int a = i / MK, b = i - a * MK;
             double t = 0.0;
-            for (int w = 0; w < NW; ++w) t += acc64[S::OFF_D_RM + w * RM * MK + i];
-            out[1 + (MK - RM) * MK + i] = t;
+            if (a < MK - RM) {
+                int w = SPLIT ? a / KF : 0;
+                if (!SPLIT) {
+                    while (w + 1 < NW && ((w + 1) * MK) / NW <= a) ++w;
+                }
+                const int qb = a - (SPLIT ? w * KF : (w * MK) / NW);
+                const float *kw = kahan + w * 2 * NK;
+                t = (double)kw[qb * MK + b] - (double)kw[NK + qb * MK + b];
+            } else {
+                const int qb = KF + (a - (MK - RM));
+                for (int w = 0; w < NW; ++w) {
+                    const float *kw = kahan + w * 2 * NK;
+                    t += (double)kw[qb * MK + b] - (double)kw[NK + qb * MK + b];
+                }
+            }
+            out[1 + i] = t;
         }
         if (tid < 5) {
             // tid 0: loss, 1: dB0, 2: pixel count, 3: sum kappa R^2, 4: sum kappa
             double t = 0.0;
-            for (int w = 0; w < NW; ++w) t += acc64[S::OFF_D_W5 + 5 * w + tid];
+            for (int w = 0; w < NW; ++w) t += acc64[5 * w + tid];
             out[tid == 0 ? 0 : MK * MK + tid] = t;
         }
     }

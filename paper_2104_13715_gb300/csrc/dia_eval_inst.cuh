@@ -1,4 +1,4 @@
-// Instantiation helper: DIA_EVAL_INST(MK, V, NW, QF, MINB, SPLIT) defines
+// Instantiation helper: DIA_EVAL_INST(MK, V, NW, QF, PF, SPLIT) defines
 // kernel_info_<MK>_<V>() for the fused kernel of side MK, tile variant V.
 #pragma once
 
@@ -13,7 +13,7 @@
         o->variant = VAR;                                                                      \
         o->nw = NWV;                                                                           \
         o->qf = QFV;                                                                           \
-        o->minb = MBV;                                                                         \
+        o->minb = MBV;   /* prefetch flag */                                                                         \
         o->th = S::TH;                                                                         \
         o->nt = S::NT;                                                                         \
         o->smem = S::SMEM;                                                                     \

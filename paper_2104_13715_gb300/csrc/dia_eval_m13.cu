@@ -2,6 +2,7 @@
 #include "dia_eval_inst.cuh"
 
 DIA_EVAL_INST(13, 0, 12, 4, 1, 1)
-DIA_EVAL_INST(13, 1, 13, 4, 1, 0)
+DIA_EVAL_INST(13, 1, 12, 4, 0, 1)
+DIA_EVAL_INST(13, 2, 13, 4, 0, 0)
 DIA_EVAL_INST(15, 0, 12, 4, 1, 1)
-DIA_EVAL_INST(15, 1, 8, 8, 1, 0)
+DIA_EVAL_INST(15, 1, 12, 4, 0, 1)

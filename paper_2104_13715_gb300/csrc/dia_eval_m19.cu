@@ -2,5 +2,5 @@
 #include "dia_eval_inst.cuh"
 
 DIA_EVAL_INST(19, 0, 8, 4, 1, 1)
-DIA_EVAL_INST(19, 1, 8, 8, 1, 1)
-DIA_EVAL_INST(19, 2, 10, 4, 1, 0)
+DIA_EVAL_INST(19, 1, 8, 4, 0, 1)
+DIA_EVAL_INST(19, 2, 10, 4, 0, 0)

@@ -5,25 +5,25 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 # kernel side -> list of tile variants (NW warps, QF output rows per warp in the
-# forward pass, MINB minimum resident CTAs per SM for the register budget,
+# forward pass, PF = 1 to load the next R-row window while the current one is used,
 # SPLIT = backward row split: 0 whole rows ceil/floor per warp, 1 equal work
 # with the MK % NW last rows split by tile-row slices).
 # Variant 0 is the default; the autotuner may pick another at run time.
 VARIANTS = {
-    1: [(8, 8, 1, 0)], 3: [(8, 8, 1, 0)], 5: [(8, 8, 1, 0)],
-    7: [(8, 8, 1, 0), (8, 4, 1, 0)],
-    9: [(8, 8, 1, 1), (8, 4, 1, 1)],
-    11: [(8, 8, 1, 1), (8, 4, 1, 1), (12, 4, 1, 0)],
-    13: [(12, 4, 1, 1), (13, 4, 1, 0)],
-    15: [(12, 4, 1, 1), (8, 8, 1, 0)],
-    17: [(8, 8, 1, 1), (8, 4, 1, 1)],
-    19: [(8, 4, 1, 1), (8, 8, 1, 1), (10, 4, 1, 0)],
-    21: [(7, 4, 1, 0), (7, 8, 1, 0), (8, 4, 1, 0)],
-    23: [(8, 4, 1, 0), (8, 8, 1, 0)],
-    25: [(12, 4, 1, 1), (12, 2, 1, 1), (13, 4, 1, 0), (9, 4, 1, 0), (8, 4, 1, 0)],
-    27: [(9, 4, 1, 0), (12, 4, 1, 0)],
-    29: [(10, 4, 1, 0), (8, 4, 1, 0)],
-    31: [(8, 4, 1, 0), (11, 4, 1, 0)],
+    1: [(8, 8, 0, 0)], 3: [(8, 8, 0, 0)], 5: [(8, 8, 0, 0)],
+    7: [(8, 4, 0, 0), (8, 8, 0, 0)],
+    9: [(8, 4, 0, 1), (8, 8, 0, 1)],
+    11: [(8, 4, 1, 1), (8, 4, 0, 1), (12, 4, 0, 0)],
+    13: [(12, 4, 1, 1), (12, 4, 0, 1), (13, 4, 0, 0)],
+    15: [(12, 4, 1, 1), (12, 4, 0, 1)],
+    17: [(8, 4, 0, 1), (8, 4, 1, 1)],
+    19: [(8, 4, 1, 1), (8, 4, 0, 1), (10, 4, 0, 0)],
+    21: [(8, 4, 0, 0), (8, 4, 1, 0), (7, 4, 0, 0)],
+    23: [(8, 4, 0, 0), (8, 4, 1, 0)],
+    25: [(12, 4, 0, 1), (12, 4, 1, 1), (13, 4, 0, 0), (12, 2, 0, 1)],
+    27: [(9, 4, 0, 0), (9, 4, 1, 0)],
+    29: [(10, 4, 0, 0), (10, 4, 1, 0)],
+    31: [(8, 4, 0, 0), (8, 4, 1, 0)],
 }
 GROUPS = [[1, 3, 5, 7], [9, 11], [13, 15], [17], [19], [21], [23], [25], [27], [29], [31]]
 
