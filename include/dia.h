@@ -135,6 +135,8 @@ typedef struct {
     double timeout_s;          /* host polling limit per fit (600 s) */
     int32_t stall_iters;       /* limit of numerical precision: stop when max|dL/dtheta| has
                                   not halved over this many accepted L-BFGS steps (250) */
+    int32_t use_graph;         /* 1: replay optimiser iterations from a CUDA graph (default);
+                                  0: launch them one by one (the plain form) */
 } dia_opts;
 
 typedef struct {
@@ -224,6 +226,27 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
                    double *theta_out, float *K_out, float *b0_out, float *diff_out,
                    uint8_t *mask_out, dia_fit_info *info,
                    void *workspace, size_t workspace_bytes, void *stream);
+
+/* Batched fits (SURVEY config: many stamp pairs of uneven sizes and kernel
+ * sides in one launch per iteration).  `pairs` is a HOST array of npairs
+ * DIA_MEM_DEVICE pairs (each with its own H, W, ld, m, maps); one loss spec
+ * and one dia_opts apply to all (clip_passes must be 0; init 0 or 1).
+ * Every optimiser iteration of the whole batch is two kernels: a persistent
+ * fused evaluation over work items (a pair and a range of its tiles, largest
+ * first, from an atomic queue) and one optimiser CTA per pair; converged
+ * pairs drop out.  graph_iters iterations are replayed from a CUDA graph.
+ * Outputs: theta_out (device, nullable) packs the pairs' theta vectors in
+ * order, pair i at offset sum_{j<i} (m_j^2 + 1); diff_out (nullable HOST
+ * array of npairs device pointers, entries nullable) receives each pair's
+ * difference image; infos (nullable HOST array of npairs) the per-pair
+ * counters and status.  Returns DIA_OK, or the first error; per-pair fit
+ * statuses are in infos.  The workspace (256-byte aligned device memory) is
+ * dia_batch_workspace_size(pairs, npairs, opts) bytes (0 if invalid). */
+size_t dia_batch_workspace_size(const dia_pair *pairs, int32_t npairs, const dia_opts *opts);
+dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs, const dia_loss_spec *loss,
+                         const dia_opts *opts, double *theta_out, float *const *diff_out,
+                         dia_fit_info *infos, void *workspace, size_t workspace_bytes,
+                         void *stream);
 
 /* Size of the fixed device scratch array used by dia_loss_grad_noalloc. */
 #define DIA_NOALLOC_SCRATCH_BYTES (2u << 20)

@@ -375,6 +375,7 @@ void fill_opts_default(dia_opts *o) {
     o->theta0 = nullptr;
     o->graph_iters = 16;
     o->timeout_s = 600.0;
+    o->use_graph = 1;
 }
 
 }  // namespace
@@ -553,8 +554,10 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     sa.p.stall_iters = opts.stall_iters;
 
     cudaGraphExec_t gx = nullptr;
-    rc = get_graph(c, ea, sa, opts.graph_iters, &gx);
-    if (rc != DIA_OK) return rc;
+    if (opts.use_graph) {
+        rc = get_graph(c, ea, sa, opts.graph_iters, &gx);
+        if (rc != DIA_OK) return rc;
+    }
 
     const auto t0 = std::chrono::steady_clock::now();
     FitState hs;
@@ -571,7 +574,11 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             passes_done = pass;
         }
         for (;;) {
-            DIA_CK(cudaGraphLaunch(gx, s));
+            if (opts.use_graph) {
+                DIA_CK(cudaGraphLaunch(gx, s));
+            } else {
+                for (int i = 0; i < opts.graph_iters; ++i) DIA_CK(enqueue_iteration(c, ea, sa, s));
+            }
             launches += 3LL * opts.graph_iters;
             DIA_CK(cudaMemcpyAsync(&hs, c.st, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
             DIA_CK(cudaStreamSynchronize(s));

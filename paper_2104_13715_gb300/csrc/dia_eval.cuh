@@ -335,14 +335,17 @@ __device__ __forceinline__ void bwd_rows(const float *rrow, const float *g0, con
     }
 }
 
+// The fused pass over tiles t_begin, t_begin + t_step, ... < t_end of one
+// pair; the CTA's partial sums (m*m + 5 float64) go to `out`.  Called by
+// the single-pair kernel (tiles strided over the grid) and by the batched
+// kernel (a contiguous tile range of one pair per work item).
 template <int MK, int NW, int QF, int PF, int SPLIT, int MODE>
-__global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
+__device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned char *smem, int t_begin,
+                                              int t_end, int t_step, double *out) {
     using S = EvalShape<MK, NW, QF, SPLIT>;
     constexpr int TH = S::TH, RP = S::RP, RWIN = S::RWIN, KP = S::KP, QB = S::QB;
     constexpr int H2 = MK / 2;
-    if (args.done_flag != nullptr && *((volatile const int *)args.done_flag) != 0) return;
 
-    extern __shared__ __align__(16) unsigned char smem[];
     float *Rbuf0 = reinterpret_cast<float *>(smem + S::OFF_R);
     float *Rbuf1 = Rbuf0 + S::RROWS * RP;
     float *gs = reinterpret_cast<float *>(smem + S::OFF_G);
@@ -399,16 +402,16 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
     // ---- 1. R tiles (+ halo) are staged with cp.async, the next tile's copy
     // overlapping the current tile's compute (two buffers)
     const bool vec = ((args.ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(args.R) & 15) == 0);
-    if (blockIdx.x < args.n_tiles)
-        stage_tile<S::RROWS, RP, S::NT>(Rbuf0, args, (blockIdx.x / args.tiles_x) * TH,
-                                        (blockIdx.x % args.tiles_x) * kTW, vec);
+    if (t_begin < t_end)
+        stage_tile<S::RROWS, RP, S::NT>(Rbuf0, args, (t_begin / args.tiles_x) * TH,
+                                        (t_begin % args.tiles_x) * kTW, vec);
     cp_async_commit();
     int buf = 0;
-    for (int tile = blockIdx.x; tile < args.n_tiles; tile += gridDim.x, buf ^= 1) {
+    for (int tile = t_begin; tile < t_end; tile += t_step, buf ^= 1) {
         const int ty0 = (tile / args.tiles_x) * TH;
         const int tx0 = (tile % args.tiles_x) * kTW;
-        const int nxt = tile + gridDim.x;
-        if (nxt < args.n_tiles)
+        const int nxt = tile + t_step;
+        if (nxt < t_end)
             stage_tile<S::RROWS, RP, S::NT>(buf ? Rbuf0 : Rbuf1, args, (nxt / args.tiles_x) * TH,
                                             (nxt % args.tiles_x) * kTW, vec);
         cp_async_commit();
@@ -600,7 +603,6 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
     if (MODE == kModeGrad) {
         if (since_flush > 0) flush();
         __syncthreads();
-        double *out = args.partials + (size_t)blockIdx.x * S::NP;
         // rows with one owner warp (w, qb < nq(w)); the RM shared rows summed
         // over the warps' copies in a fixed order
         for (int i = tid; i < MK * MK; i += S::NT) {
@@ -630,6 +632,16 @@ __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
             out[tid == 0 ? 0 : MK * MK + tid] = t;
         }
     }
+}
+
+template <int MK, int NW, int QF, int PF, int SPLIT, int MODE>
+__global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
+    if (args.done_flag != nullptr && *((volatile const int *)args.done_flag) != 0) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    process_tiles<MK, NW, QF, PF, SPLIT, MODE>(
+        args, smem, blockIdx.x, args.n_tiles, gridDim.x,
+        MODE == kModeGrad ? args.partials + (size_t)blockIdx.x * EvalShape<MK, NW, QF, SPLIT>::NP
+                          : nullptr);
 }
 
 }  // namespace dia

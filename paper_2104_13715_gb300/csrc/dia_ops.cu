@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "dia_eval.cuh"
 #include "dia_ops.cuh"
 
 namespace dia {
@@ -133,6 +134,7 @@ __device__ void finish(const StepArgs &a, int status, int reason) {
         st->L_sum = st->L * st->ndata;
         __threadfence();
         st->done = 1;
+        if (a.n_done) atomicAdd(a.n_done, 1);
     }
 }
 
@@ -246,10 +248,11 @@ __device__ int line_search_decide(FitState *st, double Lt, double gdt, double &n
     return kActContinue;
 }
 
-__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+// One optimiser step of one fit (the whole CTA): reads the reduced sums of
+// the last evaluation, updates the FP64 state and writes the next trial K.
+__device__ void step_body(const StepArgs &a, StepShared &sm) {
     FitState *st = a.st;
     if (*((volatile int *)&st->done) != 0) return;
-    __shared__ StepShared sm;
     const OptBuffers &b = a.b;
     const OptParams &p = a.p;
     const int n = a.n, tid = threadIdx.x;
@@ -453,6 +456,37 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
     start_line_search(a, sm);
 }
 
+__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+    __shared__ StepShared sm;
+    step_body(a, sm);
+}
+
+// Batched step: CTA p reduces pair p's chunk partials (fixed order) and runs
+// its optimiser step.  CTA 0 first resets the evaluation work queues.
+__global__ void __launch_bounds__(kStepThreads)
+    step_batch_kernel(const StepArgs *args, const BatchRed *red, const double *partials,
+                      int *queue_counters, int n_counters) {
+    if (blockIdx.x == 0 && threadIdx.x < n_counters) queue_counters[threadIdx.x] = 0;
+    const StepArgs a = args[blockIdx.x];
+    if (*((volatile int *)&a.st->done) != 0) return;
+    const BatchRed r = red[blockIdx.x];
+    for (int k = threadIdx.x; k < r.np; k += kStepThreads) {
+        double t = 0.0;
+        for (int c = 0; c < r.n_chunks; ++c) t += partials[r.part_off + (long long)c * r.np + k];
+        r.red[k] = t;
+    }
+    __syncthreads();
+    __shared__ StepShared sm;
+    step_body(a, sm);
+}
+
+cudaError_t launch_step_batch(const StepArgs *args, const BatchRed *red, const double *partials,
+                              int npairs, int *queue_counters, int n_counters, cudaStream_t s) {
+    step_batch_kernel<<<npairs, kStepThreads, 0, s>>>(args, red, partials, queue_counters,
+                                                      n_counters);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(const StepArgs &a, cudaStream_t s) {
     step_kernel<<<1, kStepThreads, 0, s>>>(a);
     return cudaGetLastError();
@@ -461,9 +495,9 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s) {
 // ----------------------------------------------------------------------------
 // Initialisation: K box-car (1/m^2) or a normalised Gaussian (Sec. 2.8, Sec. 5.1),
 // B0 = median of the unmasked valid target pixels; or theta already in place.
-__global__ void init_kernel(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int mode,
-                            double sigma, const SelectState *sel, int start_phase) {
-    __shared__ double sh[kStepThreads / 32];
+__device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int mode,
+                          double sigma, double median, int degenerate, int start_phase,
+                          double *sh) {
     const int n = mk * mk + 1, tid = threadIdx.x, h = mk / 2;
     if (mode == 0 || mode == 1) {
         double w = 0.0;
@@ -478,7 +512,7 @@ __global__ void init_kernel(FitState *st, OptBuffers b, float *Kpad, int mk, int
         }
         w = block_sum(w, sh);
         for (int k = tid; k < n - 1; k += kStepThreads) b.theta[k] /= w;
-        if (tid == 0) b.theta[n - 1] = sel->median;
+        if (tid == 0) b.theta[n - 1] = median;
     }
     __syncthreads();
     for (int k = tid; k < n; k += kStepThreads) {
@@ -494,14 +528,22 @@ __global__ void init_kernel(FitState *st, OptBuffers b, float *Kpad, int mk, int
         z.b1t = 1.0;
         z.b2t = 1.0;
         z.phase = start_phase;
-        z.median = sel ? sel->median : 0.0;
-        if (sel && sel->degenerate) {
+        z.median = median;
+        if (degenerate) {
             z.status = 6; /* DIA_ERR_DEGENERATE */
+            z.reason = kStopDegenerate;
             z.phase = kPhaseDone;
             z.done = 1;
         }
         *st = z;
     }
+}
+
+__global__ void init_kernel(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int mode,
+                            double sigma, const SelectState *sel, int start_phase) {
+    __shared__ double sh[kStepThreads / 32];
+    init_body(st, b, Kpad, mk, kp, mode, sigma, sel ? sel->median : 0.0,
+              sel ? sel->degenerate : 0, start_phase, sh);
 }
 
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,
@@ -629,6 +671,112 @@ cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int
             select_kernel<<<1, 1024, 0, s>>>(hist, sel, slot, pass);
         }
     median_finish_kernel<<<1, 32, 0, s>>>(sel);
+    return cudaGetLastError();
+}
+
+// Median of the unmasked valid target pixels of one pair by one CTA: the
+// same three-pass radix select over order-preserving keys, with the
+// histogram in shared memory, for the two middle ranks.
+__device__ void cta_median(const EvalArgs &ea, int h, unsigned *hist, double *out_median,
+                           int *out_degenerate) {
+    __shared__ unsigned long long s_count;
+    __shared__ uint32_t s_rank[2], s_prefix[2];
+    const int Hv = ea.H - 2 * h, Wv = ea.W - 2 * h;
+    const long long total = (long long)Hv * Wv;
+    for (int slot = 0; slot < 2; ++slot) {
+        for (int pass = 0; pass < 3; ++pass) {
+            for (int i = threadIdx.x; i < kBins; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            const uint32_t pre = (pass == 0) ? 0u : s_prefix[slot];
+            for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+                const int y = (int)(i / Wv), x = (int)(i - (long long)y * Wv);
+                const size_t off = (size_t)(y + h) * ea.ld + (x + h);
+                if (ea.mask && ea.mask[off] == 0) continue;
+                const uint32_t k = float_key(ea.I[off]);
+                uint32_t bin;
+                if (pass == 0) {
+                    bin = k >> 21;
+                } else if (pass == 1) {
+                    if ((k >> 21) != (pre >> 21)) continue;
+                    bin = (k >> 10) & 0x7ffu;
+                } else {
+                    if ((k >> 10) != (pre >> 10)) continue;
+                    bin = k & 0x3ffu;
+                }
+                atomicAdd(&hist[bin], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (pass == 0 && slot == 0) {
+                    unsigned long long tot = 0;
+                    for (int i = 0; i < kBins; ++i) tot += hist[i];
+                    s_count = tot;
+                    s_rank[0] = tot ? (uint32_t)((tot - 1) / 2) : 0u;
+                    s_rank[1] = tot ? (uint32_t)(tot / 2) : 0u;
+                }
+                const int shift = (pass == 0) ? 21 : (pass == 1 ? 10 : 0);
+                const int nb = (pass == 2) ? 1024 : 2048;
+                const uint32_t k = s_rank[slot];
+                unsigned long long cum = 0;
+                int bin = nb - 1;
+                for (int i = 0; i < nb; ++i) {
+                    if (cum + hist[i] > k) {
+                        bin = i;
+                        break;
+                    }
+                    cum += hist[i];
+                }
+                s_rank[slot] = (uint32_t)(k - cum);
+                s_prefix[slot] = (pass == 0 ? 0u : s_prefix[slot]) | ((uint32_t)bin << shift);
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        *out_degenerate = (s_count == 0);
+        *out_median = s_count ? 0.5 * ((double)key_float(s_prefix[0]) + (double)key_float(s_prefix[1]))
+                              : 0.0;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kStepThreads)
+    init_batch_kernel(const StepArgs *args, const EvalArgs *eas, int mode, double sigma,
+                      int start_phase) {
+    __shared__ unsigned hist[kBins];
+    __shared__ double sh[kStepThreads / 32];
+    __shared__ double s_med;
+    __shared__ int s_deg;
+    const StepArgs a = args[blockIdx.x];
+    const EvalArgs ea = eas[blockIdx.x];
+    if (mode != 2) {
+        cta_median(ea, a.mk / 2, hist, &s_med, &s_deg);
+    } else if (threadIdx.x == 0) {
+        s_med = 0.0;
+        s_deg = 0;
+    }
+    __syncthreads();
+    init_body(a.st, a.b, a.Kpad, a.mk, a.kp, mode, sigma, s_med, s_deg, start_phase, sh);
+    if (threadIdx.x == 0 && s_deg && a.n_done) atomicAdd(a.n_done, 1);   // finished at once
+}
+
+cudaError_t launch_init_batch(const StepArgs *args, const EvalArgs *eas, int npairs, int init_mode,
+                              double init_sigma, int start_phase, cudaStream_t s) {
+    init_batch_kernel<<<npairs, kStepThreads, 0, s>>>(args, eas, init_mode, init_sigma,
+                                                      start_phase);
+    return cudaGetLastError();
+}
+
+__global__ void pack_batch_kernel(const StepArgs *args, const long long *theta_off,
+                                  double *theta_out) {
+    const StepArgs a = args[blockIdx.x];
+    for (int k = threadIdx.x; k < a.n; k += blockDim.x)
+        theta_out[theta_off[blockIdx.x] + k] = a.b.theta[k];
+}
+
+cudaError_t launch_pack_batch(const StepArgs *args, const long long *theta_off, double *theta_out,
+                              int npairs, cudaStream_t s) {
+    pack_batch_kernel<<<npairs, 256, 0, s>>>(args, theta_off, theta_out);
     return cudaGetLastError();
 }
 

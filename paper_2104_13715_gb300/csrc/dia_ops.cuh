@@ -59,6 +59,7 @@ struct StepArgs {
     float *Kpad;         // float32 copy of the trial theta for the next evaluation
     int n, mk, kp;
     OptParams p;
+    int *n_done;         // nullable: incremented once when the fit finishes (batched fits)
 };
 
 // Order-preserving map float -> uint32 (for the radix-select median).
@@ -80,6 +81,15 @@ struct SelectState {
     double median;
 };
 
+// Batched fits: the partial sums of pair p's work items (chunks of its
+// tiles) sit at part_off + c * np for c < n_chunks; the step kernel of pair p
+// sums them in chunk order into red.
+struct BatchRed {
+    long long part_off;
+    int n_chunks, np;
+    double *red;
+};
+
 // host launchers (dia_ops.cu)
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
                           cudaStream_t s);
@@ -97,5 +107,13 @@ cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int
                           uint32_t *hist, SelectState *sel, int grid, cudaStream_t s);
 cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, float *K_out,
                                 float *b0_out, cudaStream_t s);
+// batched: one CTA per pair
+cudaError_t launch_step_batch(const StepArgs *args, const BatchRed *red, const double *partials,
+                              int npairs, int *queue_counters, int n_counters, cudaStream_t s);
+struct EvalArgs;
+cudaError_t launch_init_batch(const StepArgs *args, const struct EvalArgs *eas, int npairs,
+                              int init_mode, double init_sigma, int start_phase, cudaStream_t s);
+cudaError_t launch_pack_batch(const StepArgs *args, const long long *theta_off, double *theta_out,
+                              int npairs, cudaStream_t s);
 
 }  // namespace dia

@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("clip_passes", ctypes.c_int32), ("clip_kappa", ctypes.c_float),
                 ("init", ctypes.c_int32), ("init_sigma", ctypes.c_double),
                 ("theta0", ctypes.c_void_p), ("graph_iters", ctypes.c_int32),
-                ("timeout_s", ctypes.c_double), ("stall_iters", ctypes.c_int32)]
+                ("timeout_s", ctypes.c_double), ("stall_iters", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
 
 
 class FitInfo(ctypes.Structure):
@@ -83,6 +84,10 @@ _SIGS = {
     "dia_loss_grad_noalloc": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p]),
+    "dia_batch_workspace_size": (ctypes.c_size_t, [_P(Pair), ctypes.c_int32, _P(Opts)]),
+    "dia_fit_batch": (ctypes.c_int32, [_P(Pair), ctypes.c_int32, _P(LossSpec), _P(Opts),
+                                       ctypes.c_void_p, ctypes.c_void_p, _P(FitInfo),
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "dia_fit": (ctypes.c_int32, [_P(Pair), _P(LossSpec), _P(Opts), ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, _P(FitInfo), ctypes.c_void_p, ctypes.c_size_t,
@@ -296,6 +301,45 @@ def fit(R, I, m, spec: LossSpec, opts: Opts = None, mask=None, var=None, flat=No
     if check and st not in (DIA_OK, DIA_ERR_MAXITER):
         raise DiaError(st, "dia_fit")
     return dict(theta=theta, K=K, b0=b0, diff=diff, mask=mk, info=info.as_dict(), status=st)
+
+
+def fit_batch(items, spec: LossSpec, opts: Opts = None, want_diff=False, ws=None, stream=None):
+    """dia_fit_batch over a list of dicts {R, I, m, mask?, var?, flat?} of device
+    tensors.  Returns dict(thetas=[float64 tensors], diffs=[...] or None,
+    infos=[dict], status)."""
+    n = len(items)
+    pairs = (Pair * n)()
+    keep = []
+    for i, it in enumerate(items):
+        p, k = make_pair(it["R"], it["I"], it["m"], it.get("mask"), it.get("var"), it.get("flat"))
+        if p.mem != MEM_DEVICE:
+            raise ValueError("fit_batch takes device tensors")
+        pairs[i] = p
+        keep.append(k)
+    opts = opts if opts is not None else default_opts()
+    dev = items[0]["R"].device
+    need = lib.dia_batch_workspace_size(pairs, n, ctypes.byref(opts))
+    if need == 0:
+        raise DiaError(DIA_ERR_ARG, "dia_batch_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    sizes = [it["m"] * it["m"] + 1 for it in items]
+    theta = torch.empty(sum(sizes), dtype=torch.float64, device=dev)
+    diffs = None
+    dptr = None
+    if want_diff:
+        diffs = [torch.empty((it["R"].shape[0] - 2 * (it["m"] // 2),
+                              it["R"].shape[1] - 2 * (it["m"] // 2)), dtype=torch.float32,
+                             device=dev) for it in items]
+        dptr = (ctypes.c_void_p * n)(*[d.data_ptr() for d in diffs])
+    infos = (FitInfo * n)()
+    st = lib.dia_fit_batch(pairs, n, ctypes.byref(spec), ctypes.byref(opts), _ptr(theta),
+                           dptr, infos, _ptr(ws), ws.numel(), _stream(stream))
+    if st not in (DIA_OK, DIA_ERR_MAXITER):
+        raise DiaError(st, "dia_fit_batch")
+    thetas = list(torch.split(theta, sizes))
+    return dict(thetas=thetas, diffs=diffs, infos=[f.as_dict() for f in infos], status=st,
+                ws=ws)
 
 
 class DiaLossGrad(torch.autograd.Function):

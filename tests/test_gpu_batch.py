@@ -1,0 +1,84 @@
+"""Batched fits (dia_fit_batch): many pairs of uneven sizes and kernel sides in
+one persistent launch per iteration, each pair checked against the FP64
+oracle's normal-equation optimum and against the same pair fitted alone."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_13715_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2104_13715_gb300 import native
+    return native
+
+
+def _check(theta, ref, sky):
+    ek = np.max(np.abs(theta[:-1] - ref[:-1])) / abs(ref[:-1].sum())
+    eb = abs(theta[-1] - ref[-1]) / sky
+    assert ek <= TOL and eb <= TOL, (ek, eb)
+
+
+def _pairs(n, seed, side=(64, 200), m_range=(7, 25)):
+    specs = synth.batch_specs(n, seed, side=side, m_range=m_range)
+    return [synth.make_pair(s, 1000 * seed + k) for k, s in enumerate(specs)]
+
+
+def _dev(d):
+    dev = torch.device("cuda")
+    return dict(R=torch.from_numpy(d["R"]).to(dev), I=torch.from_numpy(d["I"]).to(dev), m=d["m"])
+
+
+def test_batch_matches_oracle_and_single_fits(nat):
+    ds = _pairs(14, seed=1)
+    assert len({nat_m for nat_m in (d["m"] for d in ds)}) >= 4     # several kernel sides
+    spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
+    out = nat.fit_batch([_dev(d) for d in ds], spec, nat.default_opts(timeout_s=120.0),
+                        want_diff=True)
+    for k, d in enumerate(ds):
+        th = out["thetas"][k].cpu().numpy()
+        ref = oracle.normal_solve(d["R"], d["I"], d["m"])
+        sky = float(np.median(d["I"]))
+        _check(th, ref, sky)
+        assert out["infos"][k]["status"] == 0
+        D = out["diffs"][k].cpu().numpy()
+        Do = oracle.diff_image(d["R"], d["I"], d["m"], th)
+        assert np.max(np.abs(D - Do)) <= 1e-5 * np.max(np.abs(d["I"]))
+    # the same pairs one at a time through the plain (non-graph) single-pair path
+    plain = nat.default_opts(use_graph=0)
+    for k in (0, 5, 9):
+        d = ds[k]
+        o = nat.fit(_dev(d)["R"], _dev(d)["I"], d["m"], spec, plain)
+        _check(o["theta"].cpu().numpy(), oracle.normal_solve(d["R"], d["I"], d["m"]),
+               float(np.median(d["I"])))
+
+
+def test_batch_with_degenerate_pair(nat):
+    ds = _pairs(4, seed=2, side=(64, 96), m_range=(7, 11))
+    items = [_dev(d) for d in ds]
+    items[2]["mask"] = torch.zeros_like(items[2]["R"], dtype=torch.uint8)
+    spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
+    out = nat.fit_batch(items, spec, nat.default_opts(timeout_s=120.0))
+    assert out["infos"][2]["status"] == nat.DIA_ERR_DEGENERATE
+    for k in (0, 1, 3):
+        d = ds[k]
+        _check(out["thetas"][k].cpu().numpy(), oracle.normal_solve(d["R"], d["I"], d["m"]),
+               float(np.median(d["I"])))
+
+
+def test_batch_nonlinear_loss(nat):
+    """CCD negative log-likelihood in a batch: each pair at its FP64 Newton optimum."""
+    ds = _pairs(5, seed=3, side=(80, 150), m_range=(7, 15))
+    spec_d = dict(rho="gauss", noise="ccd", sigma0=5.0, gain=1.0, var_floor=1e-6)
+    out = nat.fit_batch([_dev(d) for d in ds], nat.loss_spec(**spec_d),
+                        nat.default_opts(timeout_s=120.0))
+    for k, d in enumerate(ds):
+        th = out["thetas"][k].cpu().numpy()
+        ref = oracle.newton(d["R"], d["I"], d["m"], th,
+                            oracle.LossSpec("gauss", "ccd", sigma0=5.0, gain=1.0))
+        _check(th, ref, float(np.median(d["I"])))
