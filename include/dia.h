@@ -52,7 +52,7 @@ extern "C" {
 #endif
 
 #define DIA_MAX_M 31           /* largest odd kernel side of the fused kernels */
-#define DIA_ABI_VERSION 1
+#define DIA_ABI_VERSION 2
 
 typedef enum {
     DIA_OK = 0,
@@ -117,7 +117,7 @@ typedef struct {
     double adam_eps;           /* Adam epsilon (1e-8) */
     double switch_tol;         /* |dL/L| between Adam steps that hands over to L-BFGS (1e-6) */
     int32_t max_adam_iters;    /* Adam step cap (5000) */
-    int32_t history;           /* L-BFGS memory (100, at most 128) */
+    int32_t history;           /* L-BFGS memory (20, at most 128) */
     double rel_tol;            /* if > 0: stop when |dL/L| between L-BFGS steps < rel_tol
                                   (0 = off: the loss is flat along ill-conditioned kernel
                                   directions, so this test can stop far from the optimum) */
@@ -134,9 +134,17 @@ typedef struct {
     int32_t graph_iters;       /* optimiser iterations per CUDA-graph launch (16) */
     double timeout_s;          /* host polling limit per fit (600 s) */
     int32_t stall_iters;       /* limit of numerical precision: stop when max|dL/dtheta| has
-                                  not halved over this many accepted L-BFGS steps (250) */
+                                  not halved over this many loss+gradient evaluations of
+                                  the L-BFGS phase (60) */
     int32_t use_graph;         /* 1: replay optimiser iterations from a CUDA graph (default);
                                   0: launch them one by one (the plain form) */
+    int32_t precond;           /* L-BFGS initial inverse Hessian: 1 = block-Toeplitz
+                                  preconditioner from the weighted autocorrelation of R
+                                  (default), 0 = diagonal */
+    int32_t stall_iters_diag;  /* stall_iters when L-BFGS runs with the diagonal
+                                  preconditioner (precond = 0, or the block-Toeplitz
+                                  factorisation failed), which converges far more slowly
+                                  (1000) */
 } dia_opts;
 
 typedef struct {
@@ -152,6 +160,8 @@ typedef struct {
                                   (precision limit), 4 line search, 5 max iterations,
                                   6 max evaluations, 7 non-finite, 8 degenerate */
     int64_t kernel_launches;   /* CUDA kernels this call launched (graph nodes included) */
+    int32_t precond_used;      /* 1: L-BFGS ran with the block-Toeplitz preconditioner
+                                  (asked for and factored), 0: with the diagonal one */
 } dia_fit_info;
 
 /* Human-readable status name (static string). */

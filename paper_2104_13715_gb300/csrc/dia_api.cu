@@ -1,4 +1,5 @@
 // C ABI of the DIA kernel-fit library (declarations and contract in include/dia.h).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -36,7 +37,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
     size_t state, sel, hist, red, partials, theta, trial, grad, glo, m1, m2, dir, S, Y, rho, ahist,
-        pdiag, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
+        pdiag, pc_C, pc_A, pc_B, pc_R, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
         total;
     int G, n_tiles, tiles_x, np, n, kp;
 };
@@ -84,6 +85,10 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
     L.rho = take(8 * kHistMax);
     L.ahist = take(8 * kHistMax);
     L.pdiag = take(n8);
+    L.pc_C = take((size_t)(m * (2 * m - 1) + 2) * 8);
+    L.pc_A = take((size_t)L.n * L.n * 4);
+    L.pc_B = take((size_t)L.n * L.n * 4);
+    L.pc_R = take((size_t)std::min(Hv, 1024) * std::min(Wv, 1024) * 4);
     L.kpad = take((size_t)(m * ki.kp + 4) * 4);
     const size_t plane = (size_t)H * (mem == DIA_MEM_HOST ? W : ld);
     L.mask = clip ? take(plane) : 0;
@@ -273,6 +278,8 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     c.ob.rho = (double *)(c.ws + c.L.rho);
     c.ob.ahist = (double *)(c.ws + c.L.ahist);
     c.ob.pdiag = (double *)(c.ws + c.L.pdiag);
+    c.ob.Xl = nullptr;
+    c.ob.XT = nullptr;
     return DIA_OK;
 }
 
@@ -362,9 +369,10 @@ void fill_opts_default(dia_opts *o) {
     o->adam_eps = 1e-8;
     o->switch_tol = 1e-6;
     o->max_adam_iters = 5000;
-    o->history = 100;
+    o->history = 20;
     o->rel_tol = 0.0;
-    o->stall_iters = 250;
+    o->stall_iters = 60;
+    o->stall_iters_diag = 1000;
     o->grad_tol = 1e-7;
     o->max_lbfgs_iters = 3000;
     o->max_evals = 20000;
@@ -376,6 +384,7 @@ void fill_opts_default(dia_opts *o) {
     o->graph_iters = 16;
     o->timeout_s = 600.0;
     o->use_graph = 1;
+    o->precond = 1;
 }
 
 }  // namespace
@@ -486,7 +495,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         fill_opts_default(&opts);
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.clip_passes < 0 || opts.max_adam_iters < 0 ||
-        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.init < 0 || opts.init > 2 ||
+        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.init < 0 || opts.init > 2 ||
         (opts.init == 2 && !opts.theta0) || (opts.init == 1 && !(opts.init_sigma > 0.0)) ||
         !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
@@ -528,6 +537,42 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         launches += kMedianLaunches + 1;
     }
 
+    // block-Toeplitz preconditioner of L-BFGS from the zero-padded weighted
+    // autocorrelation of R over a centred window of at most 1024 x 1024 valid
+    // pixels
+    {
+        const int Hv = H - 2 * h, Wv = W - 2 * h;
+        if (opts.precond) {
+            PrecondArgs pa;
+            memset(&pa, 0, sizeof(pa));
+            pa.R = c.dp.ref;
+            pa.I = c.dp.img;
+            pa.mask = c.ea.mask;
+            pa.var = c.dp.var;
+            pa.flat = c.dp.flat;
+            pa.H = H;
+            pa.W = W;
+            pa.ld = ld;
+            pa.m = m;
+            const int sy = std::min(Hv, 1024), sx = std::min(Wv, 1024);
+            pa.y0 = (Hv - sy) / 2;
+            pa.y1 = pa.y0 + sy;
+            pa.x0 = (Wv - sx) / 2;
+            pa.x1 = pa.x0 + sx;
+            pa.Rt = (float *)(c.ws + c.L.pc_R);
+            pa.lp = c.ea.lp;
+            pa.C = (double *)(c.ws + c.L.pc_C);
+            pa.A = (float *)(c.ws + c.L.pc_A);
+            pa.B = (float *)(c.ws + c.L.pc_B);
+            pa.st = c.st;
+            pa.eps = 1e-5;
+            DIA_CK(launch_precond(pa, s));
+            launches += 3;
+            c.ob.Xl = (const float *)(c.ws + c.L.pc_B);
+            c.ob.XT = (const float *)(c.ws + c.L.pc_A);
+        }
+    }
+
     EvalArgs ea = c.ea;
     ea.done_flag = &c.st->done;
     StepArgs sa;
@@ -552,6 +597,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     sa.p.max_lbfgs = opts.max_lbfgs_iters;
     sa.p.max_evals = opts.max_evals;
     sa.p.stall_iters = opts.stall_iters;
+    sa.p.stall_iters_diag = opts.stall_iters_diag;
 
     cudaGraphExec_t gx = nullptr;
     if (opts.use_graph) {
@@ -641,6 +687,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         info->b0 = th[n - 1];
         info->reason = hs.reason;
         info->kernel_launches = launches;
+        info->precond_used = (opts.precond && hs.pc_ok) ? 1 : 0;
     } else {
         DIA_CK(cudaStreamSynchronize(s));
     }

@@ -39,21 +39,23 @@ size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct PairPlan {
     int m, n, np, tiles_x, n_tiles, n_chunks;
+    int y0, y1, x0, x1;   // preconditioner window (valid-region coordinates)
     size_t st_off, red_off, vec_off, hist_off, kpad_off;
+    size_t pc_c_off, pc_a_off, pc_b_off, pc_r_off;   // preconditioner buffers (if enabled)
     long long part_off, theta_off;
 };
 
 struct BatchPlan {
     std::vector<PairPlan> pp;
     std::vector<BatchItem> items;
-    size_t off_hdr, off_eas, off_mks, off_items, off_sa, off_red, off_thoff, off_pairs, off_parts,
-        total;
+    size_t off_hdr, off_eas, off_mks, off_items, off_sa, off_red, off_thoff, off_pas, off_pairs,
+        off_parts, total;
     long long total_parts;
     int history;
     int gbeg[5];   // items of kernel-side group g: [gbeg[g], gbeg[g+1])
 };
 
-dia_status plan_batch(const dia_pair *pairs, int npairs, int history, BatchPlan &P) {
+dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precond, BatchPlan &P) {
     if (!pairs || npairs <= 0) return DIA_ERR_ARG;
     P.pp.resize(npairs);
     P.history = history;
@@ -87,6 +89,24 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, BatchPlan 
         per = al(per + (size_t)q.n * 8 * (8 + 2 * (size_t)history) + 2 * (size_t)history * 8);
         q.kpad_off = per;
         per = al(per + (size_t)(p.m * round4(p.m) + 4) * 4);
+        // block-Toeplitz preconditioner: autocorrelation, two n x n float32
+        // matrices, sqrt(w) R over a centred window of at most 1024^2 pixels
+        const int sy = std::min(Hv, 1024), sx = std::min(Wv, 1024);
+        q.y0 = (Hv - sy) / 2;
+        q.y1 = q.y0 + sy;
+        q.x0 = (Wv - sx) / 2;
+        q.x1 = q.x0 + sx;
+        q.pc_c_off = q.pc_a_off = q.pc_b_off = q.pc_r_off = 0;
+        if (precond) {
+            q.pc_c_off = per;
+            per = al(per + (size_t)(p.m * (2 * p.m - 1) + 2) * 8);
+            q.pc_a_off = per;
+            per = al(per + (size_t)q.n * q.n * 4);
+            q.pc_b_off = per;
+            per = al(per + (size_t)q.n * q.n * 4);
+            q.pc_r_off = per;
+            per = al(per + (size_t)sy * sx * 4);
+        }
         q.hist_off = 0;
         for (int c = 0; c < q.n_chunks; ++c) {
             BatchItem it;
@@ -126,6 +146,8 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, BatchPlan 
     o = al(o + sizeof(BatchRed) * npairs);
     P.off_thoff = o;
     o = al(o + sizeof(long long) * npairs);
+    P.off_pas = o;
+    o = al(o + (precond ? sizeof(PrecondArgs) * npairs : 0));
     P.off_pairs = o;
     o = al(o + per);
     P.off_parts = o;
@@ -167,7 +189,7 @@ extern "C" size_t dia_batch_workspace_size(const dia_pair *pairs, int32_t npairs
         dia_opts_default(&o);
     if (o.history < 1 || o.history > kHistMax) return 0;
     BatchPlan P;
-    if (plan_batch(pairs, npairs, o.history, P) != DIA_OK) return 0;
+    if (plan_batch(pairs, npairs, o.history, o.precond, P) != DIA_OK) return 0;
     return P.total;
 }
 
@@ -184,7 +206,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     if (!loss || npairs <= 0) return DIA_ERR_ARG;
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.max_adam_iters < 0 || opts.max_evals < 1 ||
-        opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.init < 0 || opts.init > 1 ||
+        opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.init < 0 || opts.init > 1 ||
         (opts.init == 1 && !(opts.init_sigma > 0.0)) || !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
     if (opts.clip_passes != 0) return DIA_ERR_UNSUPPORTED;
@@ -199,7 +221,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         if (loss->var_model == DIA_VAR_FIXED && !pairs[i].var && !(loss->var_scalar > 0.f))
             return DIA_ERR_ARG;
     BatchPlan P;
-    dia_status rc = plan_batch(pairs, npairs, opts.history, P);
+    dia_status rc = plan_batch(pairs, npairs, opts.history, opts.precond, P);
     if (rc != DIA_OK) return rc;
     if (!workspace || workspace_bytes < P.total || ((uintptr_t)workspace & 255) != 0)
         return DIA_ERR_WORKSPACE;
@@ -214,6 +236,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     StepArgs *d_sa = (StepArgs *)(ws + P.off_sa);
     BatchRed *d_red = (BatchRed *)(ws + P.off_red);
     long long *d_thoff = (long long *)(ws + P.off_thoff);
+    PrecondArgs *d_pas = (PrecondArgs *)(ws + P.off_pas);
     char *pairs_base = ws + P.off_pairs;
     double *d_parts = (double *)(ws + P.off_parts);
 
@@ -223,6 +246,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     std::vector<StepArgs> sas(npairs);
     std::vector<BatchRed> reds(npairs);
     std::vector<long long> thoff(npairs);
+    std::vector<PrecondArgs> pas(opts.precond ? npairs : 0);
     LossParams lp;
     lp.rho = loss->rho;
     lp.var_model = loss->var_model;
@@ -275,6 +299,32 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         sa.b.Y = vec + 8 * n + (size_t)H * n;
         sa.b.rho = vec + 8 * n + 2 * (size_t)H * n;
         sa.b.ahist = sa.b.rho + H;
+        if (opts.precond) {
+            PrecondArgs &pa = pas[i];
+            memset(&pa, 0, sizeof(pa));
+            pa.R = p.ref;
+            pa.I = p.img;
+            pa.mask = p.mask;
+            pa.var = p.var;
+            pa.flat = p.flat;
+            pa.H = p.H;
+            pa.W = p.W;
+            pa.ld = p.ld;
+            pa.m = p.m;
+            pa.y0 = q.y0;
+            pa.y1 = q.y1;
+            pa.x0 = q.x0;
+            pa.x1 = q.x1;
+            pa.lp = lp;
+            pa.Rt = (float *)(pb + q.pc_r_off);
+            pa.C = (double *)(pb + q.pc_c_off);
+            pa.A = (float *)(pb + q.pc_a_off);
+            pa.B = (float *)(pb + q.pc_b_off);
+            pa.st = st;
+            pa.eps = 1e-5;
+            sa.b.Xl = pa.B;
+            sa.b.XT = pa.A;
+        }
         sa.red = (const double *)(pb + q.red_off);
         sa.Kpad = (float *)(pb + q.kpad_off);
         sa.n = n;
@@ -293,6 +343,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         sa.p.max_lbfgs = opts.max_lbfgs_iters;
         sa.p.max_evals = opts.max_evals;
         sa.p.stall_iters = opts.stall_iters;
+        sa.p.stall_iters_diag = opts.stall_iters_diag;
         sa.n_done = hdr + 2;
         BatchRed &r = reds[i];
         r.part_off = q.part_off;
@@ -310,6 +361,9 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     DB_CK(cudaMemcpyAsync(d_red, reds.data(), sizeof(BatchRed) * npairs, cudaMemcpyHostToDevice, s));
     DB_CK(cudaMemcpyAsync(d_thoff, thoff.data(), sizeof(long long) * npairs,
                           cudaMemcpyHostToDevice, s));
+    if (opts.precond)
+        DB_CK(cudaMemcpyAsync(d_pas, pas.data(), sizeof(PrecondArgs) * npairs,
+                              cudaMemcpyHostToDevice, s));
 
     // kernel configuration: one persistent kernel per kernel-side group present
     int dev = 0, sms = 1;
@@ -339,6 +393,8 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     // initialisation: per-pair median and theta (Sec. 2.8)
     const int start_phase = opts.max_adam_iters > 0 ? kPhaseAdam : kPhaseLbfgsStart;
     DB_CK(launch_init_batch(d_sa, d_eas, npairs, opts.init, opts.init_sigma, start_phase, s));
+    // per-pair block-Toeplitz preconditioners (after init, which clears the state)
+    if (opts.precond) DB_CK(launch_precond_batch(d_pas, pas.data(), npairs, s));
 
     // the iteration graph (cached per workspace / batch shape / settings); the
     // group kernels are parallel branches, joined before the optimiser step
@@ -404,7 +460,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     const auto t0 = std::chrono::steady_clock::now();
     int status = DIA_OK;
     int done_host = 0;
-    long long launches = 1;
+    long long launches = 1 + (opts.precond ? 3 : 0);   // init (+ preconditioner)
     for (;;) {
         DB_CK(cudaGraphLaunch(gx, s));
         launches += (long long)(n_groups + 1) * opts.graph_iters;
@@ -450,6 +506,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
             f.grad_inf = hs[i].grad_inf;
             f.reason = hs[i].reason;
             f.kernel_launches = launches;
+            f.precond_used = (opts.precond && hs[i].pc_ok) ? 1 : 0;
         }
     } else {
         DB_CK(cudaStreamSynchronize(s));

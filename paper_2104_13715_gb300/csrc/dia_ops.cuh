@@ -1,15 +1,19 @@
 // Small kernels around the fused evaluation: the float64 cross-CTA reduction,
-// the on-device optimiser (Adam, then L-BFGS with a strong-Wolfe line search,
-// Sec. 2.3 and Sec. 2.8), initialisation (box-car or Gaussian kernel, B0 =
+// the on-device optimiser (Adam, then L-BFGS with a Wolfe / approximate-Wolfe
+// line search and a block-Toeplitz preconditioner, Sec. 2.3 and Sec. 2.8),
+// initialisation (box-car or Gaussian kernel, B0 =
 // median of the target, Sec. 2.8) and output packing.
 #pragma once
 
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dia_eval.cuh"
+
 namespace dia {
 
 constexpr int kHistMax = 128;  // largest L-BFGS memory
+constexpr int kPcMaxN = 31 * 31 + 1;   // largest preconditioned theta (m <= 31)
 
 enum Phase { kPhaseAdam = 0, kPhaseLbfgs = 1, kPhaseLbfgsStart = 2, kPhaseDone = 3 };
 
@@ -27,6 +31,8 @@ struct FitState {
     int status;      // dia_status of the pass
     int it_adam, it_lbfgs, evals;
     int ls_evals, hist_len, hist_head, ls_restarts, stall, reason;
+    int pc_ok;       // 1: the block-Toeplitz preconditioner is factored and used
+    int ev_best;     // evals when max|g| last halved (stall detection)
     double ndata;    // unmasked valid pixels of the last evaluation
     double L;        // scaled loss (L_sum / N) at the accepted theta
     double L_sum;    // unscaled loss at the accepted theta
@@ -43,13 +49,16 @@ struct FitState {
 struct OptParams {
     double lr_kernel, lr_b0, beta1, beta2, adam_eps, switch_tol;
     double rel_tol, grad_tol;
-    int max_adam, history, max_lbfgs, max_evals, stall_iters;
+    int max_adam, history, max_lbfgs, max_evals, stall_iters, stall_iters_diag;
 };
 
 // Float64 vectors of the optimiser (n = m*m + 1 each, S and Y are history x n;
 // pdiag is the diagonal preconditioner, an approximate inverse Hessian diagonal).
 struct OptBuffers {
     double *theta, *trial, *grad, *glo, *m1, *m2, *dir, *S, *Y, *rho, *ahist, *pdiag;
+    // block-Toeplitz preconditioner (nullable): X = L^-1 for T = L L^T, row
+    // major, and its transpose; used when FitState::pc_ok is set
+    const float *Xl, *XT;
 };
 
 struct StepArgs {
@@ -90,6 +99,26 @@ struct BatchRed {
     double *red;
 };
 
+// Block-Toeplitz preconditioner input: Rt = sqrt(w) R[p + c] over a window
+// of valid pixels p (zero outside it), w_p = mask / (pixel variance at M = I);
+// C[dr][dc + m - 1] = sum_p Rt[p] Rt[p + (dr, dc)] (the zero-padded, i.e.
+// biased, autocorrelation; dr in [0, m), dc in [-(m-1), m-1]), then
+// sum_p Rt[p] and sum_p w_p.  With these, T is exactly the Gram matrix of the
+// shifted copies of Rt and a constant, hence positive semidefinite.
+struct PrecondArgs {
+    const float *R, *I;
+    const uint8_t *mask;
+    const float *var, *flat;
+    int H, W, ld, m;
+    int y0, y1, x0, x1;   // window of valid-region coordinates
+    LossParams lp;
+    float *Rt;            // (y1 - y0) x (x1 - x0) scratch
+    double *C;            // m * (2m - 1) + 2
+    float *A, *B;         // n x n each (n = m*m + 1): on return X^T and X = L^-1
+    FitState *st;         // receives pc_ok
+    double eps;           // relative diagonal regularisation of T
+};
+
 // host launchers (dia_ops.cu)
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
                           cudaStream_t s);
@@ -97,6 +126,10 @@ cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, float *Kpad, c
 cudaError_t launch_emit_loss_grad(const double *red, int mk, double *loss, double *grad,
                                   cudaStream_t s);
 cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_precond(const PrecondArgs &pa, cudaStream_t s);
+// d_pas: device array of npairs descriptors; h_pas: the same on the host
+cudaError_t launch_precond_batch(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
+                                 cudaStream_t s);
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,
                         double init_sigma, const SelectState *sel, int start_phase,
                         cudaStream_t s);
@@ -110,8 +143,7 @@ cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, 
 // batched: one CTA per pair
 cudaError_t launch_step_batch(const StepArgs *args, const BatchRed *red, const double *partials,
                               int npairs, int *queue_counters, int n_counters, cudaStream_t s);
-struct EvalArgs;
-cudaError_t launch_init_batch(const StepArgs *args, const struct EvalArgs *eas, int npairs,
+cudaError_t launch_init_batch(const StepArgs *args, const EvalArgs *eas, int npairs,
                               int init_mode, double init_sigma, int start_phase, cudaStream_t s);
 cudaError_t launch_pack_batch(const StepArgs *args, const long long *theta_off, double *theta_out,
                               int npairs, cudaStream_t s);

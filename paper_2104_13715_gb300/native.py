@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
                 ("init", ctypes.c_int32), ("init_sigma", ctypes.c_double),
                 ("theta0", ctypes.c_void_p), ("graph_iters", ctypes.c_int32),
                 ("timeout_s", ctypes.c_double), ("stall_iters", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("stall_iters_diag", ctypes.c_int32)]
 
 
 class FitInfo(ctypes.Structure):
@@ -58,7 +59,8 @@ class FitInfo(ctypes.Structure):
                 ("clip_passes_done", ctypes.c_int32), ("ndata", ctypes.c_int64),
                 ("loss", ctypes.c_double), ("grad_inf", ctypes.c_double),
                 ("scale", ctypes.c_double), ("b0", ctypes.c_double),
-                ("reason", ctypes.c_int32), ("kernel_launches", ctypes.c_int64)]
+                ("reason", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+                ("precond_used", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +97,9 @@ _SIGS = {
 }
 
 
+ABI_VERSION = 2   # the struct layouts below match include/dia.h of this version
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -105,6 +110,9 @@ def _load():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
+    if lib.dia_abi_version() != ABI_VERSION:
+        raise ImportError(f"{LIB_PATH} has ABI version {lib.dia_abi_version()}, this binding "
+                          f"expects {ABI_VERSION}: rebuild it with __graft_entry__.build()")
     return lib
 
 

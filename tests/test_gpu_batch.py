@@ -34,13 +34,16 @@ def _dev(d):
     return dict(R=torch.from_numpy(d["R"]).to(dev), I=torch.from_numpy(d["I"]).to(dev), m=d["m"])
 
 
-def test_batch_matches_oracle_and_single_fits(nat):
+@pytest.mark.parametrize("precond", [1, 0])
+def test_batch_matches_oracle_and_single_fits(nat, precond):
     ds = _pairs(14, seed=1)
     assert len({nat_m for nat_m in (d["m"] for d in ds)}) >= 4     # several kernel sides
     spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
-    out = nat.fit_batch([_dev(d) for d in ds], spec, nat.default_opts(timeout_s=120.0),
-                        want_diff=True)
+    opts = (nat.default_opts(timeout_s=120.0) if precond else
+            nat.default_opts(timeout_s=120.0, precond=0, history=100))
+    out = nat.fit_batch([_dev(d) for d in ds], spec, opts, want_diff=True)
     for k, d in enumerate(ds):
+        assert out["infos"][k]["precond_used"] == precond
         th = out["thetas"][k].cpu().numpy()
         ref = oracle.normal_solve(d["R"], d["I"], d["m"])
         sky = float(np.median(d["I"]))

@@ -1,0 +1,100 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark uses: where the oracle can afford it, against its FP64 optimum;
+otherwise on sampled outputs and on properties that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_13715_gb300 import synth
+from tests._helpers import ospec, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2104_13715_gb300 import native
+    return native
+
+
+def _lk(d):
+    return {k: v for k, v in d["loss"].items()
+            if k in ("rho", "noise", "sigma0", "gain", "excess", "huber_c", "var", "var_floor")}
+
+
+def _ospec(d):
+    lk = _lk(d)
+    if lk.get("noise", "fixed") == "fixed":
+        lk.pop("sigma0", None)
+        lk.pop("gain", None)
+    return ospec(lk)
+
+
+def _dev(d):
+    dev = torch.device("cuda")
+    t = lambda a, dt=torch.float32: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    return t(d["R"]), t(d["I"]), t(d.get("mask"), torch.uint8), t(d.get("var"))
+
+
+@pytest.fixture(scope="module")
+def c3():
+    return synth.workload("ccd4096_m25_cauchy_clip3", seed=0)
+
+
+def test_4096_m25_gradient_and_sampled_difference(nat, c3):
+    """4096^2, m = 25, Cauchy loss with mask and variance map: the fused
+    kernel's loss and gradient at the box-car start against the full FP64
+    oracle, and the difference image on 2000 sampled pixels."""
+    d = c3
+    m = d["m"]
+    R, I, mask, var = _dev(d)
+    th = np.full(m * m + 1, 1.0 / (m * m))
+    th[-1] = float(np.median(d["I"]))
+    L, g = nat.loss_grad(R, I, m, torch.from_numpy(th), nat.loss_spec(**_lk(d)), mask=mask, var=var)
+    Lo, go = oracle.loss_grad(d["R"], d["I"], m, th, _ospec(d), mask=d["mask"], var=d["var"])
+    assert L.item() == pytest.approx(Lo, rel=1e-5)
+    assert rel_inf(g.cpu().numpy(), go) <= 1e-5
+    D = nat.diff_image(R, I, m, torch.from_numpy(th)).cpu().numpy()
+    rng = np.random.default_rng(0)
+    h = m // 2
+    K = th[:-1].reshape(m, m)
+    for _ in range(2000):
+        y, x = rng.integers(0, D.shape[0]), rng.integers(0, D.shape[1])
+        Mo = float(np.sum(K * d["R"][y:y + m, x:x + m].astype(np.float64))) + th[-1]
+        assert abs(D[y, x] - (d["I"][y + h, x + h] - Mo)) <= 1e-5 * max(1.0, abs(Mo))
+
+
+def test_4096_m25_fit_is_stationary_for_the_oracle(nat, c3):
+    """The bench fit (Cauchy, 3 clipped refits): at the returned theta and
+    mask the FP64 oracle's gradient is tiny compared with its value at the
+    box-car start, and the mask only loses pixels."""
+    d = c3
+    m = d["m"]
+    R, I, mask, var = _dev(d)
+    opts = nat.default_opts(clip_passes=3, clip_kappa=5.0)
+    out = nat.fit(R, I, m, nat.loss_spec(**_lk(d)), opts, mask=mask, var=var, want_mask=True)
+    th = out["theta"].cpu().numpy()
+    mk = out["mask"].cpu().numpy()
+    assert np.all(mk <= d["mask"])
+    th0 = np.full(m * m + 1, 1.0 / (m * m))
+    th0[-1] = float(np.median(d["I"]))
+    _, g = oracle.loss_grad(d["R"], d["I"], m, th, _ospec(d), mask=mk, var=d["var"])
+    _, g0 = oracle.loss_grad(d["R"], d["I"], m, th0, _ospec(d), mask=mk, var=d["var"])
+    assert np.max(np.abs(g)) <= 1e-6 * np.max(np.abs(g0))
+    assert abs(th[:-1].sum() - 1.0) < 0.01          # injected photometric scale P = 1
+
+
+def test_1024_m19_ccd_nll_fit_matches_oracle_newton(nat):
+    """1024^2, m = 19, CCD NLL (sigma0 = 6, G = 1.5): L-BFGS to convergence vs
+    the FP64 Newton optimum (exact Hessian) from the GPU result."""
+    d = synth.workload("ccd1024_m19_nll", seed=0)
+    m = d["m"]
+    R, I, mask, var = _dev(d)
+    out = nat.fit(R, I, m, nat.loss_spec(**_lk(d)))
+    th = out["theta"].cpu().numpy()
+    ref = oracle.newton(d["R"], d["I"], m, th, _ospec(d))
+    sky = float(np.median(d["I"]))
+    ek = np.max(np.abs(th[:-1] - ref[:-1])) / abs(ref[:-1].sum())
+    eb = abs(th[-1] - ref[-1]) / sky
+    assert ek <= 1e-4 and eb <= 1e-4, (ek, eb)
