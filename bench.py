@@ -232,7 +232,8 @@ def _config(args, d):
             "masked_frac": None if d.get("mask") is None else float(1 - d["mask"].mean()),
             "seeds": [args.seed + r for r in range(_env_int("WORLD_SIZE", 1))],
             "l2": f"inputs larger than L2 ({by / 2**20:.0f} MiB > {L2_BYTES / 2**20:.0f} MiB)",
-            "init": "box-car K, B0 = median(I) (Sec. 2.8)", "optimizer": "Adam -> L-BFGS"}
+            "init": "box-car K, B0 = median(I) (Sec. 2.8)",
+            "optimizer": "Adam -> L-BFGS (block-Toeplitz preconditioned, library defaults)"}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -407,7 +408,8 @@ def run_ours(args, rank, world, local_rank):
             "fits_per_s": fits_per_s,
             "evals_per_fit": evals_all / (args.steps * world),
             "fit_info": {k: last.get(k) for k in ("status", "adam_iters", "lbfgs_iters", "evals",
-                                                  "clip_passes_done", "reason", "ndata")},
+                                                  "clip_passes_done", "reason", "ndata",
+                                                  "precond_used")},
             "gpu_launches": launches * world,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "oracle_check": err,
@@ -528,7 +530,7 @@ def run_kernel_only(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,

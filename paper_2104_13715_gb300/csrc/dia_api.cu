@@ -36,8 +36,8 @@ constexpr int kMaxGrid = 1024;   // CTAs of the fused kernel (partials are sized
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t state, sel, hist, red, partials, theta, trial, grad, glo, m1, m2, dir, S, Y, rho, ahist,
-        pdiag, pc_C, pc_A, pc_B, pc_R, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
+    size_t state, sel, hist, red, partials, theta, trial, grad, glo, m1, m2, dir, pg, S, Y, PY, SY,
+        YPY, pdiag, pc_args, pc_C, pc_A64, pc_X64, pc_P, pc_R, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
         total;
     int G, n_tiles, tiles_x, np, n, kp;
 };
@@ -80,14 +80,20 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
     L.m1 = take(n8);
     L.m2 = take(n8);
     L.dir = take(n8);
+    L.pg = take(n8);
     L.S = take(n8 * kHistMax);
     L.Y = take(n8 * kHistMax);
-    L.rho = take(8 * kHistMax);
-    L.ahist = take(8 * kHistMax);
+    L.PY = take(n8 * kHistMax);
+    L.SY = take((size_t)kHistMax * kHistMax * 8);
+    L.YPY = take((size_t)kHistMax * kHistMax * 8);
     L.pdiag = take(n8);
+    // block-Toeplitz preconditioner: descriptor, autocorrelation, float64
+    // factor and inverse (padded to 32), P, sqrt(w) R over the window
+    L.pc_args = take(sizeof(PrecondArgs));
     L.pc_C = take((size_t)(m * (2 * m - 1) + 2) * 8);
-    L.pc_A = take((size_t)L.n * L.n * 4);
-    L.pc_B = take((size_t)L.n * L.n * 4);
+    L.pc_A64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
+    L.pc_X64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
+    L.pc_P = take((size_t)L.n * pc_ldp(L.n) * 4);
     L.pc_R = take((size_t)std::min(Hv, 1024) * std::min(Wv, 1024) * 4);
     L.kpad = take((size_t)(m * ki.kp + 4) * 4);
     const size_t plane = (size_t)H * (mem == DIA_MEM_HOST ? W : ld);
@@ -273,13 +279,15 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     c.ob.m1 = (double *)(c.ws + c.L.m1);
     c.ob.m2 = (double *)(c.ws + c.L.m2);
     c.ob.dir = (double *)(c.ws + c.L.dir);
+    c.ob.pg = (double *)(c.ws + c.L.pg);
     c.ob.S = (double *)(c.ws + c.L.S);
     c.ob.Y = (double *)(c.ws + c.L.Y);
-    c.ob.rho = (double *)(c.ws + c.L.rho);
-    c.ob.ahist = (double *)(c.ws + c.L.ahist);
+    c.ob.PY = (double *)(c.ws + c.L.PY);
+    c.ob.SY = (double *)(c.ws + c.L.SY);
+    c.ob.YPY = (double *)(c.ws + c.L.YPY);
     c.ob.pdiag = (double *)(c.ws + c.L.pdiag);
-    c.ob.Xl = nullptr;
-    c.ob.XT = nullptr;
+    c.ob.P = nullptr;
+    c.ob.ldp = pc_ldp(c.L.n);
     return DIA_OK;
 }
 
@@ -562,14 +570,17 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             pa.Rt = (float *)(c.ws + c.L.pc_R);
             pa.lp = c.ea.lp;
             pa.C = (double *)(c.ws + c.L.pc_C);
-            pa.A = (float *)(c.ws + c.L.pc_A);
-            pa.B = (float *)(c.ws + c.L.pc_B);
+            pa.A64 = (double *)(c.ws + c.L.pc_A64);
+            pa.X64 = (double *)(c.ws + c.L.pc_X64);
+            pa.P = (float *)(c.ws + c.L.pc_P);
+            pa.ldp = pc_ldp(n);
             pa.st = c.st;
-            pa.eps = 1e-5;
-            DIA_CK(launch_precond(pa, s));
-            launches += 3;
-            c.ob.Xl = (const float *)(c.ws + c.L.pc_B);
-            c.ob.XT = (const float *)(c.ws + c.L.pc_A);
+            pa.eps = 1e-6;
+            PrecondArgs *d_pa = (PrecondArgs *)(c.ws + c.L.pc_args);
+            DIA_CK(cudaMemcpyAsync(d_pa, &pa, sizeof(pa), cudaMemcpyHostToDevice, s));
+            DIA_CK(launch_precond(d_pa, &pa, 1, s));
+            launches += precond_launches(m);
+            c.ob.P = pa.P;
         }
     }
 
@@ -625,7 +636,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             } else {
                 for (int i = 0; i < opts.graph_iters; ++i) DIA_CK(enqueue_iteration(c, ea, sa, s));
             }
-            launches += 3LL * opts.graph_iters;
+            launches += (2LL + kStepLaunches) * opts.graph_iters;
             DIA_CK(cudaMemcpyAsync(&hs, c.st, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
             DIA_CK(cudaStreamSynchronize(s));
             if (hs.done) break;

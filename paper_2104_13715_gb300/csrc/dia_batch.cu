@@ -41,7 +41,7 @@ struct PairPlan {
     int m, n, np, tiles_x, n_tiles, n_chunks;
     int y0, y1, x0, x1;   // preconditioner window (valid-region coordinates)
     size_t st_off, red_off, vec_off, hist_off, kpad_off;
-    size_t pc_c_off, pc_a_off, pc_b_off, pc_r_off;   // preconditioner buffers (if enabled)
+    size_t pc_c_off, pc_a_off, pc_x_off, pc_p_off, pc_r_off;   // preconditioner (if enabled)
     long long part_off, theta_off;
 };
 
@@ -80,13 +80,15 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
         parts += (long long)q.n_chunks * q.np;
         q.theta_off = thoff;
         thoff += q.n;
-        // per-pair region: FitState, reduced sums, 8 vectors + S/Y history, Kpad
+        // per-pair region: FitState, reduced sums, 9 vectors + S/Y/PY history,
+        // S'Y and Y'PY, Kpad
         q.st_off = per;
         per = al(per + sizeof(FitState));
         q.red_off = per;
         per = al(per + (size_t)q.np * 8);
         q.vec_off = per;
-        per = al(per + (size_t)q.n * 8 * (8 + 2 * (size_t)history) + 2 * (size_t)history * 8);
+        per = al(per + (size_t)q.n * 8 * (9 + 3 * (size_t)history) +
+                 2 * (size_t)history * history * 8);
         q.kpad_off = per;
         per = al(per + (size_t)(p.m * round4(p.m) + 4) * 4);
         // block-Toeplitz preconditioner: autocorrelation, two n x n float32
@@ -96,14 +98,17 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
         q.y1 = q.y0 + sy;
         q.x0 = (Wv - sx) / 2;
         q.x1 = q.x0 + sx;
-        q.pc_c_off = q.pc_a_off = q.pc_b_off = q.pc_r_off = 0;
+        q.pc_c_off = q.pc_a_off = q.pc_x_off = q.pc_p_off = q.pc_r_off = 0;
         if (precond) {
+            const size_t np2 = (size_t)pc_np(q.n) * pc_np(q.n);
             q.pc_c_off = per;
             per = al(per + (size_t)(p.m * (2 * p.m - 1) + 2) * 8);
             q.pc_a_off = per;
-            per = al(per + (size_t)q.n * q.n * 4);
-            q.pc_b_off = per;
-            per = al(per + (size_t)q.n * q.n * 4);
+            per = al(per + np2 * 8);
+            q.pc_x_off = per;
+            per = al(per + np2 * 8);
+            q.pc_p_off = per;
+            per = al(per + (size_t)q.n * pc_ldp(q.n) * 4);
             q.pc_r_off = per;
             per = al(per + (size_t)sy * sx * 4);
         }
@@ -257,6 +262,9 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     lp.var_scalar = loss->var_scalar;
     lp.var_floor = loss->var_floor;
     const int H = opts.history;
+    int max_m = 1;
+    for (int i = 0; i < npairs; ++i) max_m = std::max(max_m, pairs[i].m);
+    const int max_n = max_m * max_m + 1;
     for (int i = 0; i < npairs; ++i) {
         const dia_pair &p = pairs[i];
         const PairPlan &q = P.pp[i];
@@ -295,10 +303,14 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         sa.b.m2 = vec + 5 * n;
         sa.b.dir = vec + 6 * n;
         sa.b.pdiag = vec + 7 * n;
-        sa.b.S = vec + 8 * n;
-        sa.b.Y = vec + 8 * n + (size_t)H * n;
-        sa.b.rho = vec + 8 * n + 2 * (size_t)H * n;
-        sa.b.ahist = sa.b.rho + H;
+        sa.b.pg = vec + 8 * n;
+        sa.b.S = vec + 9 * n;
+        sa.b.Y = sa.b.S + (size_t)H * n;
+        sa.b.PY = sa.b.Y + (size_t)H * n;
+        sa.b.SY = sa.b.PY + (size_t)H * n;
+        sa.b.YPY = sa.b.SY + (size_t)H * H;
+        sa.b.P = nullptr;
+        sa.b.ldp = pc_ldp(n);
         if (opts.precond) {
             PrecondArgs &pa = pas[i];
             memset(&pa, 0, sizeof(pa));
@@ -318,12 +330,13 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
             pa.lp = lp;
             pa.Rt = (float *)(pb + q.pc_r_off);
             pa.C = (double *)(pb + q.pc_c_off);
-            pa.A = (float *)(pb + q.pc_a_off);
-            pa.B = (float *)(pb + q.pc_b_off);
+            pa.A64 = (double *)(pb + q.pc_a_off);
+            pa.X64 = (double *)(pb + q.pc_x_off);
+            pa.P = (float *)(pb + q.pc_p_off);
+            pa.ldp = pc_ldp(n);
             pa.st = st;
-            pa.eps = 1e-5;
-            sa.b.Xl = pa.B;
-            sa.b.XT = pa.A;
+            pa.eps = 1e-6;
+            sa.b.P = pa.P;
         }
         sa.red = (const double *)(pb + q.red_off);
         sa.Kpad = (float *)(pb + q.kpad_off);
@@ -394,7 +407,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     const int start_phase = opts.max_adam_iters > 0 ? kPhaseAdam : kPhaseLbfgsStart;
     DB_CK(launch_init_batch(d_sa, d_eas, npairs, opts.init, opts.init_sigma, start_phase, s));
     // per-pair block-Toeplitz preconditioners (after init, which clears the state)
-    if (opts.precond) DB_CK(launch_precond_batch(d_pas, pas.data(), npairs, s));
+    if (opts.precond) DB_CK(launch_precond(d_pas, pas.data(), npairs, s));
 
     // the iteration graph (cached per workspace / batch shape / settings); the
     // group kernels are parallel branches, joined before the optimiser step
@@ -406,6 +419,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     app(n_it, sizeof n_it);
     app(grid, sizeof grid);
     app(&opts.graph_iters, sizeof opts.graph_iters);
+    app(&max_n, sizeof max_n);
     cudaGraphExec_t gx = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_bmu);
@@ -435,7 +449,8 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
                     if (e == cudaSuccess) e = cudaEventRecord(evj[g], side[g]);
                     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, evj[g], 0);
                 }
-                if (e == cudaSuccess) e = launch_step_batch(d_sa, d_red, d_parts, npairs, hdr + 4, 4, cs);
+                if (e == cudaSuccess)
+                    e = launch_step_batch(d_sa, d_red, d_parts, npairs, max_n, hdr + 4, 4, cs);
             }
             cudaGraph_t gr = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
@@ -460,10 +475,10 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     const auto t0 = std::chrono::steady_clock::now();
     int status = DIA_OK;
     int done_host = 0;
-    long long launches = 1 + (opts.precond ? 3 : 0);   // init (+ preconditioner)
+    long long launches = 1 + (opts.precond ? precond_launches(max_m) : 0);   // init (+ preconditioner)
     for (;;) {
         DB_CK(cudaGraphLaunch(gx, s));
-        launches += (long long)(n_groups + 1) * opts.graph_iters;
+        launches += (long long)(n_groups + kStepLaunches) * opts.graph_iters;
         DB_CK(cudaMemcpyAsync(&done_host, hdr + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
         DB_CK(cudaStreamSynchronize(s));
         if (done_host >= npairs) break;

@@ -109,11 +109,25 @@ enum { kActContinue = 0, kActAcceptTrial = 1, kActAcceptLo = 2, kActFail = 3 };
 
 struct StepShared {
     double red[kStepThreads / 32];
-    double gt[1024];     // scaled gradient at the trial point
-    float pt[1024];      // preconditioner intermediate
+    double gt[1024];          // scaled gradient at the trial point
+    double v[4][kHistMax];    // compact-form vectors over the history
     int act, finish_status, copy_glo;
     double new_alpha;
 };
+
+// x . y over n entries by one warp (every lane gets the sum).
+__device__ __forceinline__ double warp_dot(const double *x, const double *y, int n) {
+    double s = 0.0;
+    for (int k = threadIdx.x & 31; k < n; k += 32) s = fma(x[k], y[k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// History slot of chronological entry c (0 = oldest) of hl entries ending before head.
+__device__ __forceinline__ int hist_slot(int c, int hl, int head, int H) {
+    return (head - hl + c + 2 * H) % H;
+}
 
 __device__ void set_trial(const StepArgs &a, double alpha) {
     const OptBuffers &b = a.b;
@@ -151,79 +165,117 @@ __device__ void update_precond(const StepArgs &a) {
         a.b.pdiag[k] = N * ((k == a.n - 1) ? pb : pk);   // the loss is scaled by 1/N
 }
 
-// out = P v for the preconditioner P: the block-Toeplitz X^T X (float32
-// matrix, warp per row) when factored, else the diagonal pdiag.  out may
-// alias v.
-__device__ void apply_pc(const StepArgs &a, StepShared &sm, const double *v, double *out) {
-    const int n = a.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int NWS = kStepThreads / 32;
-    if (a.st->pc_ok && a.b.Xl) {
-        for (int k = tid; k < n; k += kStepThreads) sm.pt[k] = (float)v[k];
-        __syncthreads();
-        float *t = reinterpret_cast<float *>(sm.gt);   // X v (gt is free here)
-        for (int i = warp; i < n; i += NWS) {
-            const float *row = a.b.Xl + (size_t)i * n;
-            float acc = 0.f;
-            for (int k = lane; k <= i; k += 32) acc = fmaf(row[k], sm.pt[k], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) t[i] = acc;
-        }
-        __syncthreads();
-        for (int j = warp; j < n; j += NWS) {
-            const float *row = a.b.XT + (size_t)j * n;
-            float acc = 0.f;
-            for (int i = j + lane; i < n; i += 32) acc = fmaf(row[i], t[i], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) out[j] = (double)acc;
-        }
-        __syncthreads();
-    } else {
-        for (int k = tid; k < n; k += kStepThreads) out[k] = a.b.pdiag[k] * v[k];
-        __syncthreads();
+// A new L-BFGS direction is needed at the accepted point: P g (and P y_new
+// when a curvature pair was just stored in slot `slot`) are computed by the
+// multi-CTA preconditioner kernel, then direction_body finishes the step.
+__device__ void request_direction(const StepArgs &a, int slot) {
+    if (threadIdx.x == 0) {
+        a.st->need_pc = slot >= 0 ? 2 : 1;
+        a.st->pc_slot = slot;
     }
 }
 
-// New L-BFGS direction by the two-loop recursion (Nocedal & Wright Alg. 7.4)
-// with the initial inverse Hessian tau * P (P the preconditioner), tau =
-// s'y / y'Py of the newest pair, and the start of its line search.
-__device__ void start_line_search(const StepArgs &a, StepShared &sm) {
+// The direction half of the step (one CTA): new row of y'Py, the compact
+// representation of the L-BFGS inverse Hessian (Byrd, Nocedal & Schnabel
+// 1994, Theorem 2.2) with H0 = tau P, tau = s'y / y'Py of the newest pair,
+//   H g = tau P g + S p1 + tau (PY) p2,  u = R^-1 S'g,  p2 = -u,
+//   p1 = R^-T ((D + tau Y'PY) u - tau (PY)'g),
+// R the upper triangle of S'Y and D its diagonal (chronological order); then
+// the start of the line search at alpha = 1 (Sec. 2.8).
+__device__ void direction_body(const StepArgs &a, StepShared &sm) {
     FitState *st = a.st;
+    if (*((volatile int *)&st->done) != 0) return;
+    const int need = st->need_pc;
+    if (need == 0) return;
     const OptBuffers &b = a.b;
-    const int n = a.n, tid = threadIdx.x, H = a.p.history;
-    const int hl = st->hist_len, head = st->hist_head;
-    for (int k = tid; k < n; k += kStepThreads) b.dir[k] = b.grad[k];   // q = g
-    __syncthreads();
-    for (int j = 0; j < hl; ++j) {                                       // newest -> oldest
-        const int i = (head - 1 - j + H) % H;
-        const double al = b.rho[i] * dot(b.S + (size_t)i * n, b.dir, n, sm.red);
-        if (tid == 0) b.ahist[i] = al;
-        for (int k = tid; k < n; k += kStepThreads) b.dir[k] -= al * b.Y[(size_t)i * n + k];
+    const int n = a.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, H = a.p.history;
+    constexpr int NWS = kStepThreads / 32;
+    int hl = st->hist_len;
+    const int head = st->hist_head;
+    if (need == 2) {   // row and column of y_new' P y_j
+        const int sn = st->pc_slot;
+        const double *py = b.PY + (size_t)sn * n;
+        for (int c = warp; c < hl; c += NWS) {
+            const int j = hist_slot(c, hl, head, H);
+            const double v = warp_dot(py, b.Y + (size_t)j * n, n);
+            if (lane == 0) {
+                b.YPY[(size_t)sn * H + j] = v;
+                b.YPY[(size_t)j * H + sn] = v;
+            }
+        }
         __syncthreads();
     }
     double tau = 1.0;
     if (hl > 0) {
-        const int i = (head - 1 + H) % H;
-        const double sy = 1.0 / b.rho[i];
-        apply_pc(a, sm, b.Y + (size_t)i * n, b.glo);      // glo as scratch: P y
-        const double ypy = dot(b.Y + (size_t)i * n, b.glo, n, sm.red);
-        tau = sy / ypy;
+        const int nw = hist_slot(hl - 1, hl, head, H);
+        tau = b.SY[(size_t)nw * H + nw] / b.YPY[(size_t)nw * H + nw];
+        if (!(tau > 0.0) || !isfinite(tau)) tau = 1.0;
     }
-    apply_pc(a, sm, b.dir, b.dir);
-    for (int k = tid; k < n; k += kStepThreads) b.dir[k] *= tau;
+    // a_c = s_c . g, b_c = tau (P y_c) . g
+    for (int t = warp; t < 2 * hl; t += NWS) {
+        const int c = t < hl ? t : t - hl;
+        const int j = hist_slot(c, hl, head, H);
+        const double v = warp_dot(t < hl ? b.S + (size_t)j * n : b.PY + (size_t)j * n, b.grad, n);
+        if (lane == 0) sm.v[t < hl ? 0 : 1][c] = t < hl ? v : tau * v;
+    }
     __syncthreads();
-    for (int j = hl - 1; j >= 0; --j) {                                  // oldest -> newest
-        const int i = (head - 1 - j + H) % H;
-        const double be = b.rho[i] * dot(b.Y + (size_t)i * n, b.dir, n, sm.red);
-        const double al = b.ahist[i];
-        for (int k = tid; k < n; k += kStepThreads) b.dir[k] += (al - be) * b.S[(size_t)i * n + k];
-        __syncthreads();
+    if (warp == 0 && hl > 0) {
+        double *A = sm.v[0], *B = sm.v[1], *U = sm.v[2], *T = sm.v[3];
+        auto R = [&](int c1, int c2) {   // s_c1 . y_c2 (chronological indices)
+            return b.SY[(size_t)hist_slot(c1, hl, head, H) * H + hist_slot(c2, hl, head, H)];
+        };
+        // U = R^-1 A (back substitution, column sweep; A is the accumulator)
+        for (int c = hl - 1; c >= 0; --c) {
+            const double uc = A[c] / R(c, c);
+            __syncwarp();
+            if (lane == 0) U[c] = uc;
+            for (int r = lane; r < c; r += 32) A[r] -= R(r, c) * uc;
+            __syncwarp();
+        }
+        // T = D U + tau Y'PY U
+        for (int r = lane; r < hl; r += 32) {
+            const int jr = hist_slot(r, hl, head, H);
+            double t = R(r, r) * U[r];
+            for (int c = 0; c < hl; ++c)
+                t += tau * b.YPY[(size_t)jr * H + hist_slot(c, hl, head, H)] * U[c];
+            T[r] = t;
+        }
+        __syncwarp();
+        // T <- R^-T T, B <- R^-T B (forward substitution, column sweep, in place)
+        for (int c = 0; c < hl; ++c) {
+            const double d = R(c, c);
+            const double tc = T[c] / d, bc = B[c] / d;
+            __syncwarp();
+            if (lane == 0) {
+                T[c] = tc;
+                B[c] = bc;
+            }
+            for (int r = c + 1 + lane; r < hl; r += 32) {
+                const double rc = R(c, r);
+                T[r] -= rc * tc;
+                B[r] -= rc * bc;
+            }
+            __syncwarp();
+        }
+        // p1 = T - B (in T), p2 = -U (in U)
+        for (int r = lane; r < hl; r += 32) {
+            T[r] -= B[r];
+            U[r] = -U[r];
+        }
     }
-    for (int k = tid; k < n; k += kStepThreads) b.dir[k] = -b.dir[k];
+    __syncthreads();
+    for (int k = tid; k < n; k += kStepThreads) {
+        double hg = tau * b.pg[k];
+        for (int c = 0; c < hl; ++c) {
+            const int j = hist_slot(c, hl, head, H);
+            hg += sm.v[3][c] * b.S[(size_t)j * n + k] + tau * sm.v[2][c] * b.PY[(size_t)j * n + k];
+        }
+        b.dir[k] = -hg;
+    }
     __syncthreads();
     double gd0 = dot(b.grad, b.dir, n, sm.red);
     if (!(gd0 < 0.0) || !isfinite(gd0)) {          // not a descent direction: preconditioned SD
-        apply_pc(a, sm, b.grad, b.dir);
-        for (int k = tid; k < n; k += kStepThreads) b.dir[k] = -b.dir[k];
+        for (int k = tid; k < n; k += kStepThreads) b.dir[k] = -b.pg[k];
         __syncthreads();
         gd0 = dot(b.grad, b.dir, n, sm.red);
         if (tid == 0) st->hist_len = 0;
@@ -237,6 +289,7 @@ __device__ void start_line_search(const StepArgs &a, StepShared &sm) {
         st->gd_lo = gd0;
         st->hi = -1.0;
         st->ls_evals = 0;
+        st->need_pc = 0;
     }
     __syncthreads();
     set_trial(a, 1.0);
@@ -246,7 +299,7 @@ __device__ void start_line_search(const StepArgs &a, StepShared &sm) {
 // Toeplitz preconditioned iteration reaches its float32 floor within tens of
 // evaluations, the diagonally preconditioned one needs far more.
 __device__ __forceinline__ int stall_limit(const StepArgs &a) {
-    return (a.st->pc_ok && a.b.Xl) ? a.p.stall_iters : a.p.stall_iters_diag;
+    return (a.st->pc_ok && a.b.P) ? a.p.stall_iters : a.p.stall_iters_diag;
 }
 
 // Line-search decision for the trial alpha (thread 0).  Wolfe conditions, or
@@ -379,7 +432,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
             finish(a, 0, kStopGradTol);
             return;
         }
-        start_line_search(a, sm);
+        request_direction(a, -1);
         return;
     }
 
@@ -427,7 +480,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
         }
         __syncthreads();
         if (sm.finish_status < 0)
-            start_line_search(a, sm);
+            request_direction(a, -1);
         else
             finish(a, sm.finish_status, sm.act);
         return;
@@ -438,7 +491,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
     const double aacc = use_trial ? st->alpha : st->lo;
     const double Lacc = use_trial ? Lt : st->L_lo;
     const double *gacc = use_trial ? sm.gt : b.glo;
-    const int H = p.history, head = st->hist_head;
+    const int H = p.history, head = st->hist_head, hl0 = st->hist_len;
     double *Sn = b.S + (size_t)head * n, *Yn = b.Y + (size_t)head * n;
     for (int k = tid; k < n; k += kStepThreads) {
         Sn[k] = aacc * b.dir[k];
@@ -455,13 +508,12 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
     }
     const double ginf = block_max(mx, sm.red);
     if (use_trial) update_precond(a);
+    const bool keep = sy > 1e-12 * yy && sy > 0.0;   // curvature pair kept only if y's > 0
+    const int hl = keep ? min(hl0 + 1, H) : hl0, hd = keep ? (head + 1) % H : head;
     if (tid == 0) {
         const double Lold = st->L;
-        if (sy > 1e-12 * yy && sy > 0.0) {   // curvature pair kept only if y's > 0
-            b.rho[head] = 1.0 / sy;
-            st->hist_head = (head + 1) % H;
-            st->hist_len = min(st->hist_len + 1, H);
-        }
+        st->hist_head = hd;
+        st->hist_len = hl;
         st->L = Lacc;
         st->L_sum = Lacc * N;
         st->grad_inf = ginf;
@@ -497,12 +549,34 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
         finish(a, sm.finish_status, sm.act);
         return;
     }
-    start_line_search(a, sm);
+    if (keep) {   // s_new . y_j and s_j . y_new over the history, the new pair included
+        const int warp = tid >> 5, lane = tid & 31;
+        constexpr int NWS = kStepThreads / 32;
+        for (int t = warp; t < 2 * hl; t += NWS) {
+            const int c = t < hl ? t : t - hl;
+            const int j = hist_slot(c, hl, hd, H);
+            const double v = t < hl ? warp_dot(Sn, b.Y + (size_t)j * n, n)
+                                    : warp_dot(b.S + (size_t)j * n, Yn, n);
+            if (lane == 0) {
+                if (t < hl)
+                    b.SY[(size_t)head * H + j] = v;
+                else
+                    b.SY[(size_t)j * H + head] = v;
+            }
+        }
+        __syncthreads();
+    }
+    request_direction(a, keep ? head : -1);
 }
 
 __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
     __shared__ StepShared sm;
     step_body(a, sm);
+}
+
+__global__ void __launch_bounds__(kStepThreads) direction_kernel(const StepArgs a) {
+    __shared__ StepShared sm;
+    direction_body(a, sm);
 }
 
 // Batched step: CTA p reduces pair p's chunk partials (fixed order) and runs
@@ -524,228 +598,28 @@ __global__ void __launch_bounds__(kStepThreads)
     step_body(a, sm);
 }
 
+__global__ void __launch_bounds__(kStepThreads) direction_batch_kernel(const StepArgs *args) {
+    __shared__ StepShared sm;
+    const StepArgs a = args[blockIdx.x];
+    direction_body(a, sm);
+}
+
 cudaError_t launch_step_batch(const StepArgs *args, const BatchRed *red, const double *partials,
-                              int npairs, int *queue_counters, int n_counters, cudaStream_t s) {
+                              int npairs, int max_n, int *queue_counters, int n_counters,
+                              cudaStream_t s) {
     step_batch_kernel<<<npairs, kStepThreads, 0, s>>>(args, red, partials, queue_counters,
                                                       n_counters);
-    return cudaGetLastError();
-}
-
-// ----------------------------------------------------------------------------
-// Block-Toeplitz preconditioner.  For kernel pixels u = (a, b), v = (a', b')
-// the Gauss-Newton Hessian sum_p w_p R[p+u] R[p+v] is, up to the image border
-// and the variation of w, the weighted autocorrelation of R at lag v - u.
-// Built from the zero-padded autocorrelation of sqrt(w) R it is a Gram matrix
-// (positive semidefinite), and the preconditioned Hessian is well conditioned
-// (condition number about 4 on a 128 x 128, m = 11 pair, against 2e5 with a
-// diagonal preconditioner).
-
-// Weight of image pixel q (offset in the pitched image): mask / variance at M = I.
-__device__ __forceinline__ float pc_weight(const PrecondArgs &a, size_t q) {
-    float v;
-    if (a.lp.var_model == 0) {
-        v = a.var ? a.var[q] : a.lp.var_scalar;
-    } else {
-        const float F = a.flat ? a.flat[q] : 1.f, Iv = fmaxf(a.I[q], 0.f);
-        v = a.lp.var_model == 1 ? a.lp.s0sq / (F * F) + Iv * a.lp.inv_gain / F
-                                : a.lp.excess * Iv * a.lp.inv_gain / F;
-        v = fmaxf(v, a.lp.var_floor);
-    }
-    return (a.mask && a.mask[q] == 0) ? 0.f : 1.0f / v;
-}
-
-// Rt over the window, grid-stride over blocks [blk, nblk).
-__device__ void rtilde_body(const PrecondArgs &a, int blk, int nblk) {
-    const int h = a.m / 2, wx = a.x1 - a.x0;
-    const long long total = (long long)(a.y1 - a.y0) * wx;
-    for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)nblk * blockDim.x) {
-        const int py = a.y0 + (int)(i / wx), px = a.x0 + (int)(i % wx);
-        const size_t q = (size_t)(py + h) * a.ld + (px + h);   // pixel p + c of the image
-        a.Rt[i] = sqrtf(pc_weight(a, q)) * a.R[q];
-    }
-}
-
-// One lag (lag < m(2m-1)) of the zero-padded autocorrelation of Rt, or, for
-// lag == m(2m-1), the sums of Rt and of w; the whole block takes part.
-__device__ void autocorr_body(const PrecondArgs &a, int lag, double *sh) {
-    const int m = a.m, h = m / 2, L = 2 * m - 1, nl = m * L;
-    const int wy = a.y1 - a.y0, wx = a.x1 - a.x0;
-    double tot = 0.0, tot_w = 0.0;
-    float acc = 0.f, acc_w = 0.f;   // float32 over <= 4096 terms per thread, then float64
-    int cnt = 0;
-    if (lag < nl) {
-        const int dr = lag / L, dc = lag % L - (m - 1);
-        const int ny = wy - dr, xa = dc < 0 ? -dc : 0, nx = wx - (dc < 0 ? -dc : dc);
-        const long long total = (ny > 0 && nx > 0) ? (long long)ny * nx : 0;
-        for (long long i = threadIdx.x; i < total; i += blockDim.x) {
-            const int y = (int)(i / nx), x = xa + (int)(i % nx);
-            acc = fmaf(a.Rt[(size_t)y * wx + x], a.Rt[(size_t)(y + dr) * wx + (x + dc)], acc);
-            if (++cnt == 4096) {
-                tot += acc;
-                acc = 0.f;
-                cnt = 0;
-            }
-        }
-    } else {
-        const long long total = (long long)wy * wx;
-        for (long long i = threadIdx.x; i < total; i += blockDim.x) {
-            acc += a.Rt[i];
-            const int py = a.y0 + (int)(i / wx), px = a.x0 + (int)(i % wx);
-            acc_w += pc_weight(a, (size_t)(py + h) * a.ld + (px + h));
-            if (++cnt == 4096) {
-                tot += acc;
-                tot_w += acc_w;
-                acc = acc_w = 0.f;
-                cnt = 0;
-            }
-        }
-    }
-    tot = block_sum(tot + acc, sh);
-    tot_w = block_sum(tot_w + acc_w, sh);
-    if (threadIdx.x == 0) {
-        if (lag < nl) {
-            a.C[lag] = tot;
-        } else {
-            a.C[nl] = tot;         // sum Rt
-            a.C[nl + 1] = tot_w;   // sum w
-        }
-    }
-}
-
-// The whole block: T (n x n, float32) from the autocorrelation, divided by
-// the window's pixel count so that T^-1 approximates the inverse Hessian of
-// the loss per pixel (the optimiser's scaled loss), relative diagonal
-// regularisation eps, Cholesky T = L L^T in place (A), X = L^-1 (B), X^T (A).
-// Sets st->pc_ok when every pivot is positive.
-__device__ void precond_build_body(const PrecondArgs &a, float *colk, int *s_bad) {
-    const int m = a.m, n = m * m + 1, L = 2 * m - 1, nl = m * L, tid = threadIdx.x,
-              nt = blockDim.x;
-    const int wy = a.y1 - a.y0, wx = a.x1 - a.x0;
-    const double *C = a.C;
-    float *A = a.A, *B = a.B;
-    const double npx = (double)wy * wx;
-    // border: the constant vector sqrt(mean w) over the window dilated by m - 1
-    const double wbar = C[nl + 1] / npx;
-    if (tid == 0) *s_bad = 0;
-    for (int e = tid; e < n * n; e += nt) {
-        const int u = e / n, v = e % n;
-        double t;
-        if (u == n - 1 && v == n - 1) {
-            t = wbar * (double)(wy + m - 1) * (double)(wx + m - 1);
-        } else if (u == n - 1 || v == n - 1) {
-            t = sqrt(wbar) * C[nl];
-        } else {
-            int dr = v / m - u / m, dc = v % m - u % m;
-            if (dr < 0 || (dr == 0 && dc < 0)) {
-                dr = -dr;
-                dc = -dc;
-            }
-            t = C[dr * L + dc + (m - 1)];
-        }
-        if (u == v) t *= (1.0 + a.eps);
-        A[e] = (float)(t / npx);
-    }
-    __syncthreads();
-    // right-looking Cholesky (lower triangle)
-    for (int k = 0; k < n; ++k) {
-        if (tid == 0) {
-            const float d = A[(size_t)k * n + k];
-            if (!(d > 0.f)) *s_bad = 1;
-            A[(size_t)k * n + k] = d > 0.f ? sqrtf(d) : 1.f;
-        }
-        __syncthreads();
-        const float dk = A[(size_t)k * n + k];
-        for (int i = k + 1 + tid; i < n; i += nt) {
-            const float l = A[(size_t)i * n + k] / dk;
-            A[(size_t)i * n + k] = l;
-            colk[i] = l;
-        }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < n; i += nt) {
-            const float li = colk[i];
-            float *row = A + (size_t)i * n;
-            for (int j = k + 1; j <= i; ++j) row[j] -= li * colk[j];
-        }
-        __syncthreads();
-    }
-    // X = L^-1, one column per thread (forward substitution)
-    for (int j = tid; j < n; j += nt) {
-        for (int i = 0; i < j; ++i) B[(size_t)i * n + j] = 0.f;
-        for (int i = j; i < n; ++i) {
-            float s = (i == j) ? 1.f : 0.f;
-            const float *Li = A + (size_t)i * n;
-            for (int k = j; k < i; ++k) s -= Li[k] * B[(size_t)k * n + j];
-            B[(size_t)i * n + j] = s / Li[i];
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < n * n; e += nt) {
-        const int u = e / n, v = e % n;
-        A[e] = B[(size_t)v * n + u];
-    }
-    __syncthreads();
-    if (tid == 0) a.st->pc_ok = *s_bad ? 0 : 1;
-    __syncthreads();
-}
-
-__global__ void rtilde_kernel(const PrecondArgs a) { rtilde_body(a, blockIdx.x, gridDim.x); }
-
-__global__ void __launch_bounds__(256) autocorr_kernel(const PrecondArgs a) {
-    __shared__ double sh[8];
-    autocorr_body(a, blockIdx.x, sh);
-}
-
-__global__ void __launch_bounds__(1024) precond_build_kernel(const PrecondArgs a) {
-    __shared__ float colk[kPcMaxN];
-    __shared__ int s_bad;
-    precond_build_body(a, colk, &s_bad);
-}
-
-// Batched forms: blockIdx.y (rtilde, autocorr) or blockIdx.x (build) strides
-// over the pairs; pairs with fewer lags than the grid skip the extra blocks.
-__global__ void rtilde_batch_kernel(const PrecondArgs *pas, int npairs) {
-    for (int p = blockIdx.y; p < npairs; p += gridDim.y) rtilde_body(pas[p], blockIdx.x, gridDim.x);
-}
-
-__global__ void __launch_bounds__(256) autocorr_batch_kernel(const PrecondArgs *pas, int npairs) {
-    __shared__ double sh[8];
-    for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
-        const int m = pas[p].m;
-        if ((int)blockIdx.x <= m * (2 * m - 1)) autocorr_body(pas[p], blockIdx.x, sh);
-    }
-}
-
-__global__ void __launch_bounds__(1024) precond_build_batch_kernel(const PrecondArgs *pas,
-                                                                    int npairs) {
-    __shared__ float colk[kPcMaxN];
-    __shared__ int s_bad;
-    for (int p = blockIdx.x; p < npairs; p += gridDim.x) precond_build_body(pas[p], colk, &s_bad);
-}
-
-cudaError_t launch_precond(const PrecondArgs &pa, cudaStream_t s) {
-    if (pa.m * pa.m + 1 > kPcMaxN) return cudaErrorInvalidValue;
-    const int nl = pa.m * (2 * pa.m - 1);
-    rtilde_kernel<<<256, 256, 0, s>>>(pa);
-    autocorr_kernel<<<nl + 1, 256, 0, s>>>(pa);
-    precond_build_kernel<<<1, 1024, 0, s>>>(pa);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_precond_batch(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
-                                 cudaStream_t s) {
-    int max_m = 1;
-    for (int i = 0; i < npairs; ++i) max_m = max(max_m, h_pas[i].m);
-    if (max_m * max_m + 1 > kPcMaxN || npairs < 1) return cudaErrorInvalidValue;
-    const unsigned gy = (unsigned)min(npairs, 65535);
-    rtilde_batch_kernel<<<dim3(16, gy), 256, 0, s>>>(d_pas, npairs);
-    autocorr_batch_kernel<<<dim3(max_m * (2 * max_m - 1) + 1, gy), 256, 0, s>>>(d_pas, npairs);
-    precond_build_batch_kernel<<<min(npairs, 65535), 1024, 0, s>>>(d_pas, npairs);
+    cudaError_t e = launch_pc_apply_batch(args, npairs, max_n, s);
+    if (e != cudaSuccess) return e;
+    direction_batch_kernel<<<npairs, kStepThreads, 0, s>>>(args);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step(const StepArgs &a, cudaStream_t s) {
     step_kernel<<<1, kStepThreads, 0, s>>>(a);
+    cudaError_t e = launch_pc_apply(a, s);
+    if (e != cudaSuccess) return e;
+    direction_kernel<<<1, kStepThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -825,6 +699,7 @@ __global__ void restart_kernel(FitState *st, float *Kpad, OptBuffers b, int mk, 
         st->hist_len = 0;
         st->hist_head = 0;
         st->ls_restarts = 0;
+        st->need_pc = 0;
     }
 }
 

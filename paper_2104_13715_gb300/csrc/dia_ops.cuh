@@ -33,6 +33,8 @@ struct FitState {
     int ls_evals, hist_len, hist_head, ls_restarts, stall, reason;
     int pc_ok;       // 1: the block-Toeplitz preconditioner is factored and used
     int ev_best;     // evals when max|g| last halved (stall detection)
+    int need_pc;     // new L-BFGS direction pending: 1 needs P g, 2 also P y_new
+    int pc_slot;     // history slot of y_new (need_pc == 2)
     double ndata;    // unmasked valid pixels of the last evaluation
     double L;        // scaled loss (L_sum / N) at the accepted theta
     double L_sum;    // unscaled loss at the accepted theta
@@ -52,13 +54,19 @@ struct OptParams {
     int max_adam, history, max_lbfgs, max_evals, stall_iters, stall_iters_diag;
 };
 
-// Float64 vectors of the optimiser (n = m*m + 1 each, S and Y are history x n;
-// pdiag is the diagonal preconditioner, an approximate inverse Hessian diagonal).
+// Float64 vectors of the optimiser (n = m*m + 1 each).  L-BFGS history in
+// slots of a ring of `history` entries: S, Y and PY = P y are history x n;
+// SY[i][j] = s_i.y_j and YPY[i][j] = y_i.P y_j are history x history (the
+// compact representation of Byrd, Nocedal & Schnabel 1994).  pg = P g for the
+// current gradient; pdiag is the diagonal preconditioner, an approximate
+// inverse Hessian diagonal.
 struct OptBuffers {
-    double *theta, *trial, *grad, *glo, *m1, *m2, *dir, *S, *Y, *rho, *ahist, *pdiag;
-    // block-Toeplitz preconditioner (nullable): X = L^-1 for T = L L^T, row
-    // major, and its transpose; used when FitState::pc_ok is set
-    const float *Xl, *XT;
+    double *theta, *trial, *grad, *glo, *m1, *m2, *dir, *pg, *pdiag;
+    double *S, *Y, *PY, *SY, *YPY;
+    // block-Toeplitz preconditioner (nullable): P = T^-1, n x n float32, row
+    // pitch ldp (a multiple of 4); used when FitState::pc_ok is set
+    const float *P;
+    int ldp;
 };
 
 struct StepArgs {
@@ -114,10 +122,17 @@ struct PrecondArgs {
     LossParams lp;
     float *Rt;            // (y1 - y0) x (x1 - x0) scratch
     double *C;            // m * (2m - 1) + 2
-    float *A, *B;         // n x n each (n = m*m + 1): on return X^T and X = L^-1
+    double *A64;          // np x np (np = n rounded up to 32): T, then its Cholesky factor
+    double *X64;          // np x np: the inverse of the factor
+    float *P;             // n x ldp: T^-1, the preconditioner
+    int ldp;
     FitState *st;         // receives pc_ok
     double eps;           // relative diagonal regularisation of T
 };
+
+constexpr int kPcB = 32;   // block size of the preconditioner factorisation
+__host__ __device__ inline int pc_np(int n) { return (n + kPcB - 1) / kPcB * kPcB; }
+__host__ __device__ inline int pc_ldp(int n) { return (n + 3) & ~3; }
 
 // host launchers (dia_ops.cu)
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
@@ -125,11 +140,17 @@ cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, co
 cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, float *Kpad, cudaStream_t s);
 cudaError_t launch_emit_loss_grad(const double *red, int mk, double *loss, double *grad,
                                   cudaStream_t s);
+// One optimiser step: the line-search / history half (one CTA), P g and
+// P y_new (many CTAs), the direction half (one CTA).
+constexpr int kStepLaunches = 3;
 cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
-cudaError_t launch_precond(const PrecondArgs &pa, cudaStream_t s);
 // d_pas: device array of npairs descriptors; h_pas: the same on the host
-cudaError_t launch_precond_batch(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
-                                 cudaStream_t s);
+cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
+                           cudaStream_t s);
+int precond_launches(int max_m);   // kernels one launch_precond call enqueues
+// P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
+cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_pc_apply_batch(const StepArgs *args, int npairs, int max_n, cudaStream_t s);
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,
                         double init_sigma, const SelectState *sel, int start_phase,
                         cudaStream_t s);
@@ -140,9 +161,11 @@ cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int
                           uint32_t *hist, SelectState *sel, int grid, cudaStream_t s);
 cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, float *K_out,
                                 float *b0_out, cudaStream_t s);
-// batched: one CTA per pair
+// batched: one CTA per pair for the two optimiser halves (kStepLaunches
+// kernels in all); max_n = the largest m*m + 1 of the batch
 cudaError_t launch_step_batch(const StepArgs *args, const BatchRed *red, const double *partials,
-                              int npairs, int *queue_counters, int n_counters, cudaStream_t s);
+                              int npairs, int max_n, int *queue_counters, int n_counters,
+                              cudaStream_t s);
 cudaError_t launch_init_batch(const StepArgs *args, const EvalArgs *eas, int npairs,
                               int init_mode, double init_sigma, int start_phase, cudaStream_t s);
 cudaError_t launch_pack_batch(const StepArgs *args, const long long *theta_off, double *theta_out,
