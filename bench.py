@@ -447,9 +447,13 @@ def run_batch(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     evals = 0
+    launches = 0
+    flops = 0.0
     for _ in range(args.steps):
         out = nat.fit_batch(items, spec, opts, ws=ws, stream=stream)
         evals += sum(f["evals"] for f in out["infos"])
+        launches += out["infos"][0]["kernel_launches"]   # per call, the same in every info
+        flops += sum(4.0 * d["m"] ** 2 * f["ndata"] * f["evals"] for d, f in zip(ds, out["infos"]))
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop() if sampler else None
@@ -472,6 +476,19 @@ def run_batch(args, rank, world, local_rank):
         t[mode] = len(sub) / (time.perf_counter() - t0)
     npx = sum((d["R"].shape[0] - 2 * (d["m"] // 2)) * (d["R"].shape[1] - 2 * (d["m"] // 2))
               for d in ds)
+    peaks, src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tf = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": achieved / peak_tf, "traffic": None,
+            "kernel": "dia::eval_batch_kernel (fused evaluations of all pairs, graph nodes)",
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({src} peaks file)",
+            "algorithmic": "sum over pairs and evaluations of 4*m^2 flop x unmasked valid px",
+            "note": "lower bound: divided by the whole timed region (optimiser steps, "
+                    "preconditioner builds and host polling included); the evaluation "
+                    "kernels run inside CUDA graphs and are not timed alone"}
     line = {"metric": METRIC, "value": fits_s, "unit": "pair fits/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -481,6 +498,7 @@ def run_batch(args, rank, world, local_rank):
                                  int(max(d["R"].shape[0] for d in ds))],
                        "m": sorted({d["m"] for d in ds}), "loss": "gauss", "variance": "fixed"},
             "evals_per_s": evals / (ms / 1e3), "pairs_converged": ok,
+            "gpu_launches": launches, "roofline": roof,
             "subset_fits_per_s": {"pairs": len(sub), **t,
                                   "batch_over_single_plain": t["batch"] / t["single_plain"]},
             "clocks": clocks}

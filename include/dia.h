@@ -135,7 +135,7 @@ typedef struct {
     double timeout_s;          /* host polling limit per fit (600 s) */
     int32_t stall_iters;       /* limit of numerical precision: stop when max|dL/dtheta| has
                                   not halved over this many loss+gradient evaluations of
-                                  the L-BFGS phase (60) */
+                                  the L-BFGS phase (30) */
     int32_t use_graph;         /* 1: replay optimiser iterations from a CUDA graph (default);
                                   0: launch them one by one (the plain form) */
     int32_t precond;           /* L-BFGS initial inverse Hessian: 1 = block-Toeplitz
@@ -145,6 +145,9 @@ typedef struct {
                                   preconditioner (precond = 0, or the block-Toeplitz
                                   factorisation failed), which converges far more slowly
                                   (1000) */
+    int32_t max_ls_evals;      /* evaluations one line search may take before it gives up
+                                  (restart from preconditioned steepest descent, twice at
+                                  most, then stop) (12) */
 } dia_opts;
 
 typedef struct {

@@ -379,8 +379,9 @@ void fill_opts_default(dia_opts *o) {
     o->max_adam_iters = 5000;
     o->history = 20;
     o->rel_tol = 0.0;
-    o->stall_iters = 60;
+    o->stall_iters = 30;
     o->stall_iters_diag = 1000;
+    o->max_ls_evals = 12;
     o->grad_tol = 1e-7;
     o->max_lbfgs_iters = 3000;
     o->max_evals = 20000;
@@ -503,7 +504,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         fill_opts_default(&opts);
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.clip_passes < 0 || opts.max_adam_iters < 0 ||
-        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.init < 0 || opts.init > 2 ||
+        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 || opts.init < 0 || opts.init > 2 ||
         (opts.init == 2 && !opts.theta0) || (opts.init == 1 && !(opts.init_sigma > 0.0)) ||
         !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
@@ -609,6 +610,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     sa.p.max_evals = opts.max_evals;
     sa.p.stall_iters = opts.stall_iters;
     sa.p.stall_iters_diag = opts.stall_iters_diag;
+    sa.p.max_ls = opts.max_ls_evals;
 
     cudaGraphExec_t gx = nullptr;
     if (opts.use_graph) {

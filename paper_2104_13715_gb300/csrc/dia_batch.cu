@@ -211,7 +211,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     if (!loss || npairs <= 0) return DIA_ERR_ARG;
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.max_adam_iters < 0 || opts.max_evals < 1 ||
-        opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.init < 0 || opts.init > 1 ||
+        opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 || opts.init < 0 || opts.init > 1 ||
         (opts.init == 1 && !(opts.init_sigma > 0.0)) || !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
     if (opts.clip_passes != 0) return DIA_ERR_UNSUPPORTED;
@@ -357,6 +357,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         sa.p.max_evals = opts.max_evals;
         sa.p.stall_iters = opts.stall_iters;
         sa.p.stall_iters_diag = opts.stall_iters_diag;
+        sa.p.max_ls = opts.max_ls_evals;
         sa.n_done = hdr + 2;
         BatchRed &r = reds[i];
         r.part_off = q.part_off;

@@ -306,7 +306,8 @@ __device__ __forceinline__ int stall_limit(const StepArgs &a) {
 // the approximate Wolfe conditions of Hager & Zhang (2005), which rely on the
 // float64 directional derivative when loss differences fall below the
 // float32 pixel-rounding level; brackets are updated on the sign of phi'.
-__device__ int line_search_decide(FitState *st, double Lt, double gdt, double &na, int &copy_glo) {
+__device__ int line_search_decide(FitState *st, double Lt, double gdt, int max_ls, double &na,
+                                  int &copy_glo) {
     const double al = st->alpha, L0 = st->L, gd0 = st->gd0;
     const double delta = 0.1, sigma = 0.9, eps_f = 1e-6 * fabs(L0);
     copy_glo = 0;
@@ -333,7 +334,7 @@ __device__ int line_search_decide(FitState *st, double Lt, double gdt, double &n
     }
     st->ls_evals += 1;
     const bool collapsed = st->hi >= 0.0 && (st->hi - st->lo) <= 1e-13 * fmax(1.0, st->lo);
-    if (st->ls_evals >= 30 || collapsed || na > 1e10) {
+    if (st->ls_evals >= max_ls || collapsed || na > 1e10) {
         return (st->lo > 0.0) ? kActAcceptLo : kActFail;
     }
     return kActContinue;
@@ -441,7 +442,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
     if (tid == 0) {
         double na = st->alpha;
         int copy_glo = 0;
-        int act = line_search_decide(st, Lt, gdt, na, copy_glo);
+        int act = line_search_decide(st, Lt, gdt, p.max_ls, na, copy_glo);
         if (act == kActContinue && st->evals >= p.max_evals) act = (st->lo > 0.0) ? kActAcceptLo : kActFail;
         sm.act = act;
         sm.copy_glo = copy_glo;

@@ -51,7 +51,7 @@ struct FitState {
 struct OptParams {
     double lr_kernel, lr_b0, beta1, beta2, adam_eps, switch_tol;
     double rel_tol, grad_tol;
-    int max_adam, history, max_lbfgs, max_evals, stall_iters, stall_iters_diag;
+    int max_adam, history, max_lbfgs, max_evals, stall_iters, stall_iters_diag, max_ls;
 };
 
 // Float64 vectors of the optimiser (n = m*m + 1 each).  L-BFGS history in

@@ -46,6 +46,9 @@ def test_default_opts_are_the_paper_values(native):
     assert o.switch_tol == 1e-6           # Sec. 2.8
     assert o.clip_kappa == 5.0            # Sec. 4.2
     assert o.grad_tol == 1e-7             # Sec. 2.8
+    # preconditioned L-BFGS settings (not in the paper; chosen by measurement)
+    assert (o.precond, o.history, o.stall_iters, o.stall_iters_diag, o.max_ls_evals) == \
+        (1, 20, 30, 1000, 12)
 
 
 @pytest.mark.parametrize("H,W,ld,m,ok", [(128, 128, 128, 11, True), (10, 10, 10, 11, False),
