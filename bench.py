@@ -41,7 +41,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2104_13715_gb300 import synth  # noqa: E402
+from paper_2104_13715_gb300 import shard, synth  # noqa: E402
 
 METRIC = ("pair fits/s and loss+grad evals/s (4096², m=25) vs plain FP32; "
           "err vs FP64 oracle")
@@ -421,16 +421,27 @@ def run_ours(args, rank, world, local_rank):
 BATCH_WORKLOAD = "batch512_m7to21_chi2"
 
 
+def _batch_costs(ds):
+    return [shard.pair_cost(d["R"].shape[0], d["R"].shape[1], d["m"]) for d in ds]
+
+
 def run_batch(args, rank, world, local_rank):
     """Batched fits of 512 stamp pairs (side ~ U{64..512}, odd m ~ U{7..21},
     fixed-variance chi^2): pair fits/s of the batched graph-captured form,
     and, on a same-pairs subset, batched vs one pair at a time (plain
-    non-graph form, and graph form)."""
+    non-graph form, and graph form).  Under torchrun the 512 pairs are split
+    across ranks by cost (strong scaling); each rank fits its share in one
+    batched call, with no collective on the data path."""
     import torch
     from paper_2104_13715_gb300 import native as nat
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    ds = synth.batch(args.batch_pairs, seed=args.seed + rank)
+    ds_all = synth.batch(args.batch_pairs, seed=args.seed)
+    mine = shard.partition_by_cost(_batch_costs(ds_all), world)[rank]
+    ds = [ds_all[k] for k in mine]
     items = [dict(R=torch.from_numpy(d["R"]).to(dev), I=torch.from_numpy(d["I"]).to(dev),
                   m=d["m"]) for d in ds]
     spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
@@ -444,6 +455,9 @@ def run_batch(args, rank, world, local_rank):
     sampler = ClockSampler(local_rank) if local_rank == 0 else None
     if sampler:
         sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     evals = 0
@@ -456,54 +470,100 @@ def run_batch(args, rank, world, local_rank):
         flops += sum(4.0 * d["m"] ** 2 * f["ndata"] * f["evals"] for d, f in zip(ds, out["infos"]))
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1)
-    fits_s = args.steps * len(items) / (ms / 1e3)
-    ok = sum(f["status"] == 0 for f in out["infos"])
-    # same-pairs subset: batched vs one at a time
-    sub = items[:args.subset]
-    t = {}
-    for mode in ("batch", "single_plain", "single_graph"):
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        if mode == "batch":
-            nat.fit_batch(sub, spec, opts, stream=stream)
-        else:
-            o = nat.default_opts(use_graph=1 if mode == "single_graph" else 0, timeout_s=900.0)
-            for it in sub:
-                nat.fit(it["R"], it["I"], it["m"], spec, o, want_diff=False, stream=stream)
-        torch.cuda.synchronize(dev)
-        t[mode] = len(sub) / (time.perf_counter() - t0)
+    ms_own = e0.elapsed_time(e1)
+    ok_own = sum(f["status"] == 0 for f in out["infos"])
+    ms, pairs_all = shard.reduce_max_sum(ms_own, args.steps * len(items), device=dev)
+    _, evals_all = shard.reduce_max_sum(0.0, evals, device=dev)
+    _, ok = shard.reduce_max_sum(0.0, ok_own, device=dev)
+    _, launches_all = shard.reduce_max_sum(0.0, launches, device=dev)
+    _, flops_all = shard.reduce_max_sum(0.0, flops, device=dev)
+    fits_s = pairs_all / (ms / 1e3)
+    # same-pairs subset: batched vs one at a time (single GPU only)
+    t = None
+    if world == 1:
+        sub = items[:args.subset]
+        t = {}
+        for mode in ("batch", "single_plain", "single_graph"):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            if mode == "batch":
+                nat.fit_batch(sub, spec, opts, stream=stream)
+            else:
+                o = nat.default_opts(use_graph=1 if mode == "single_graph" else 0, timeout_s=900.0)
+                for it in sub:
+                    nat.fit(it["R"], it["I"], it["m"], spec, o, want_diff=False, stream=stream)
+            torch.cuda.synchronize(dev)
+            t[mode] = len(sub) / (time.perf_counter() - t0)
+        t = {"pairs": len(sub), **t, "batch_over_single_plain": t["batch"] / t["single_plain"]}
     npx = sum((d["R"].shape[0] - 2 * (d["m"] // 2)) * (d["R"].shape[1] - 2 * (d["m"] // 2))
-              for d in ds)
+              for d in ds_all)
     peaks, src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tf = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = flops / (ms / 1e3) / 1e12
+    achieved = flops_all / world / (ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
             "frac": achieved / peak_tf, "traffic": None,
             "kernel": "dia::eval_batch_kernel (fused evaluations of all pairs, graph nodes)",
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({src} peaks file)",
             "algorithmic": "sum over pairs and evaluations of 4*m^2 flop x unmasked valid px",
-            "note": "lower bound: divided by the whole timed region (optimiser steps, "
+            "note": "per GPU, lower bound: divided by the whole timed region (optimiser steps, "
                     "preconditioner builds and host polling included); the evaluation "
                     "kernels run inside CUDA graphs and are not timed alone"}
     line = {"metric": METRIC, "value": fits_s, "unit": "pair fits/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "pairs": len(items), "valid_px": npx,
-                       "sides": [int(min(d["R"].shape[0] for d in ds)),
-                                 int(max(d["R"].shape[0] for d in ds))],
-                       "m": sorted({d["m"] for d in ds}), "loss": "gauss", "variance": "fixed"},
-            "evals_per_s": evals / (ms / 1e3), "pairs_converged": ok,
-            "gpu_launches": launches, "roofline": roof,
-            "subset_fits_per_s": {"pairs": len(sub), **t,
-                                  "batch_over_single_plain": t["batch"] / t["single_plain"]},
-            "clocks": clocks}
+            "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "pairs": len(ds_all), "valid_px": npx,
+                       "sides": [int(min(d["R"].shape[0] for d in ds_all)),
+                                 int(max(d["R"].shape[0] for d in ds_all))],
+                       "m": sorted({d["m"] for d in ds_all}), "loss": "gauss",
+                       "variance": "fixed",
+                       "sharding": "pairs split across ranks by cost, no collective"},
+            "evals_per_s": evals_all / (ms / 1e3), "pairs_converged": int(ok),
+            "gpu_launches": int(launches_all), "roofline": roof,
+            "subset_fits_per_s": t, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_reference_batch(args, rank, world):
+    """The FP64 oracle on the batch workload: pairs fitted one after another
+    by the normal-equation solve (the chi^2 optimum), a bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    ds = synth.batch(args.batch_pairs, seed=args.seed)
+    rates, k, sample_pairs = [], 0, 0
+    budget = max(args.ref_budget / max(args.steps + args.warmup, 1), 1.0)
+    for i in range(args.warmup + args.steps):
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget or n == 0:
+            d = ds[k % len(ds)]
+            oracle.normal_solve(d["R"], d["I"], d["m"])
+            k += 1
+            n += 1
+        if i >= args.warmup:
+            rates.append(n / (time.perf_counter() - t0))
+            sample_pairs += n
+    value = float(np.mean(rates))
+    cores = os.cpu_count() or 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pair fits/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "pairs": len(ds)},
+        "cpu_baseline": {"value": value, "unit": "pair fits/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample_pairs} pairs of the batch (in order) fitted by the "
+                                   f"oracle's FP64 normal-equation solve, ~{budget:.0f} s per step"},
+        "e2e": {"value": value, "unit": "pair fits/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_kernel_only(args):
@@ -569,14 +629,12 @@ def main():
     if args.kernel_only:
         run_kernel_only(args)
         return
-    if args.workload == BATCH_WORKLOAD:
-        run_batch(args, _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0))
-        return
-    world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local_rank = _env_int("LOCAL_RANK", 0)
+    rank, world, local_rank = shard.rank_env()
     if args.impl == "reference":
-        run_reference(args, rank, world)
+        if args.workload == BATCH_WORKLOAD:
+            run_reference_batch(args, rank, world)
+        else:
+            run_reference(args, rank, world)
         return
     if world > 1:
         import torch
@@ -584,12 +642,14 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == BATCH_WORKLOAD:
+            run_batch(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
-
 
 if __name__ == "__main__":
     main()

@@ -37,7 +37,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
     size_t state, sel, hist, red, partials, theta, trial, grad, glo, m1, m2, dir, pg, S, Y, PY, SY,
-        YPY, pdiag, pc_args, pc_C, pc_A64, pc_X64, pc_P, pc_R, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
+        YPY, pdiag, pc_args, pc_part, pc_A64, pc_X64, pc_P, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
         total;
     int G, n_tiles, tiles_x, np, n, kp;
 };
@@ -87,14 +87,15 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
     L.SY = take((size_t)kHistMax * kHistMax * 8);
     L.YPY = take((size_t)kHistMax * kHistMax * 8);
     L.pdiag = take(n8);
-    // block-Toeplitz preconditioner: descriptor, autocorrelation, float64
-    // factor and inverse (padded to 32), P, sqrt(w) R over the window
+    // preconditioner: descriptor, chunk partials of the Gauss-Newton Hessian,
+    // its float64 factor and inverse (padded to 64), P
     L.pc_args = take(sizeof(PrecondArgs));
-    L.pc_C = take((size_t)(m * (2 * m - 1) + 2) * 8);
+    int wy0, wy1, wx0, wx1, chunks;
+    precond_window(H, W, m, true, &wy0, &wy1, &wx0, &wx1, &chunks);
+    L.pc_part = take(chunks > 1 ? (size_t)chunks * gn_blocks(L.n) * kGnT * kGnT * 8 : 0);
     L.pc_A64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
     L.pc_X64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
     L.pc_P = take((size_t)L.n * pc_ldp(L.n) * 4);
-    L.pc_R = take((size_t)std::min(Hv, 1024) * std::min(Wv, 1024) * 4);
     L.kpad = take((size_t)(m * ki.kp + 4) * 4);
     const size_t plane = (size_t)H * (mem == DIA_MEM_HOST ? W : ld);
     L.mask = clip ? take(plane) : 0;
@@ -563,14 +564,9 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             pa.W = W;
             pa.ld = ld;
             pa.m = m;
-            const int sy = std::min(Hv, 1024), sx = std::min(Wv, 1024);
-            pa.y0 = (Hv - sy) / 2;
-            pa.y1 = pa.y0 + sy;
-            pa.x0 = (Wv - sx) / 2;
-            pa.x1 = pa.x0 + sx;
-            pa.Rt = (float *)(c.ws + c.L.pc_R);
+            precond_window(H, W, m, true, &pa.y0, &pa.y1, &pa.x0, &pa.x1, &pa.gn_chunks);
             pa.lp = c.ea.lp;
-            pa.C = (double *)(c.ws + c.L.pc_C);
+            pa.part = (double *)(c.ws + c.L.pc_part);
             pa.A64 = (double *)(c.ws + c.L.pc_A64);
             pa.X64 = (double *)(c.ws + c.L.pc_X64);
             pa.P = (float *)(c.ws + c.L.pc_P);

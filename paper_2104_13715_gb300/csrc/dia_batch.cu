@@ -41,7 +41,7 @@ struct PairPlan {
     int m, n, np, tiles_x, n_tiles, n_chunks;
     int y0, y1, x0, x1;   // preconditioner window (valid-region coordinates)
     size_t st_off, red_off, vec_off, hist_off, kpad_off;
-    size_t pc_c_off, pc_a_off, pc_x_off, pc_p_off, pc_r_off;   // preconditioner (if enabled)
+    size_t pc_a_off, pc_x_off, pc_p_off;   // preconditioner (if enabled)
     long long part_off, theta_off;
 };
 
@@ -91,26 +91,19 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
                  2 * (size_t)history * history * 8);
         q.kpad_off = per;
         per = al(per + (size_t)(p.m * round4(p.m) + 4) * 4);
-        // block-Toeplitz preconditioner: autocorrelation, two n x n float32
-        // matrices, sqrt(w) R over a centred window of at most 1024^2 pixels
-        const int sy = std::min(Hv, 1024), sx = std::min(Wv, 1024);
-        q.y0 = (Hv - sy) / 2;
-        q.y1 = q.y0 + sy;
-        q.x0 = (Wv - sx) / 2;
-        q.x1 = q.x0 + sx;
-        q.pc_c_off = q.pc_a_off = q.pc_x_off = q.pc_p_off = q.pc_r_off = 0;
+        // preconditioner: float64 Gauss-Newton Hessian (factored in place) and
+        // inverse factor, padded to 64, and P; one pixel chunk per pair
+        int chunks = 1;
+        precond_window(p.H, p.W, p.m, false, &q.y0, &q.y1, &q.x0, &q.x1, &chunks);
+        q.pc_a_off = q.pc_x_off = q.pc_p_off = 0;
         if (precond) {
             const size_t np2 = (size_t)pc_np(q.n) * pc_np(q.n);
-            q.pc_c_off = per;
-            per = al(per + (size_t)(p.m * (2 * p.m - 1) + 2) * 8);
             q.pc_a_off = per;
             per = al(per + np2 * 8);
             q.pc_x_off = per;
             per = al(per + np2 * 8);
             q.pc_p_off = per;
             per = al(per + (size_t)q.n * pc_ldp(q.n) * 4);
-            q.pc_r_off = per;
-            per = al(per + (size_t)sy * sx * 4);
         }
         q.hist_off = 0;
         for (int c = 0; c < q.n_chunks; ++c) {
@@ -328,8 +321,8 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
             pa.x0 = q.x0;
             pa.x1 = q.x1;
             pa.lp = lp;
-            pa.Rt = (float *)(pb + q.pc_r_off);
-            pa.C = (double *)(pb + q.pc_c_off);
+            pa.part = nullptr;
+            pa.gn_chunks = 1;
             pa.A64 = (double *)(pb + q.pc_a_off);
             pa.X64 = (double *)(pb + q.pc_x_off);
             pa.P = (float *)(pb + q.pc_p_off);

@@ -107,12 +107,10 @@ struct BatchRed {
     double *red;
 };
 
-// Block-Toeplitz preconditioner input: Rt = sqrt(w) R[p + c] over a window
-// of valid pixels p (zero outside it), w_p = mask / (pixel variance at M = I);
-// C[dr][dc + m - 1] = sum_p Rt[p] Rt[p + (dr, dc)] (the zero-padded, i.e.
-// biased, autocorrelation; dr in [0, m), dc in [-(m-1), m-1]), then
-// sum_p Rt[p] and sum_p w_p.  With these, T is exactly the Gram matrix of the
-// shifted copies of Rt and a constant, hence positive semidefinite.
+// Preconditioner of L-BFGS: the Gauss-Newton Hessian of the per-pixel loss
+// over a window of valid pixels p (valid-region coordinates [y0, y1) x
+// [x0, x1)), H = sum_p w_p phi_p phi_p^T / N_window with phi_p = [R window of
+// p, 1] and w_p = mask / (pixel variance at M = I); then P = H^-1.
 struct PrecondArgs {
     const float *R, *I;
     const uint8_t *mask;
@@ -120,19 +118,31 @@ struct PrecondArgs {
     int H, W, ld, m;
     int y0, y1, x0, x1;   // window of valid-region coordinates
     LossParams lp;
-    float *Rt;            // (y1 - y0) x (x1 - x0) scratch
-    double *C;            // m * (2m - 1) + 2
-    double *A64;          // np x np (np = n rounded up to 32): T, then its Cholesky factor
+    double *part;         // gn_chunks x gn_blocks(n) x 64 x 64 partial sums (gn_chunks > 1)
+    int gn_chunks;        // pixel chunks the Hessian sum is split into
+    double *A64;          // np x np (np = n rounded up to 64): H, then its Cholesky factor
     double *X64;          // np x np: the inverse of the factor
-    float *P;             // n x ldp: T^-1, the preconditioner
+    float *P;             // n x ldp: H^-1, the preconditioner
     int ldp;
     FitState *st;         // receives pc_ok
-    double eps;           // relative diagonal regularisation of T
+    double eps;           // relative diagonal regularisation of H
 };
 
-constexpr int kPcB = 32;   // block size of the preconditioner factorisation
-__host__ __device__ inline int pc_np(int n) { return (n + kPcB - 1) / kPcB * kPcB; }
+constexpr int kPcB = 32;    // block size of the factorisation
+constexpr int kGnT = 64;    // block size of the Hessian sum
+constexpr int kGnChunk = 16384;   // pixels per chunk of the Hessian sum
+__host__ __device__ inline int pc_np(int n) { return (n + kGnT - 1) / kGnT * kGnT; }
 __host__ __device__ inline int pc_ldp(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline int gn_tiles(int n) { return (n + kGnT - 1) / kGnT; }
+__host__ __device__ inline int gn_blocks(int n) { return gn_tiles(n) * (gn_tiles(n) + 1) / 2; }
+// Window side for a kernel of n parameters: about 1.2e11 / n^2 pixels (a few
+// ms of FP32 work), between 256^2 and 1024^2.
+inline int pc_window_side(int n) {
+    double s = 0.0;
+    const double t = 1.2e11 / ((double)n * n);
+    while ((s + 32.0) * (s + 32.0) <= t) s += 32.0;
+    return s < 256.0 ? 256 : (s > 1024.0 ? 1024 : (int)s);
+}
 
 // host launchers (dia_ops.cu)
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
@@ -148,6 +158,8 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
                            cudaStream_t s);
 int precond_launches(int max_m);   // kernels one launch_precond call enqueues
+void precond_window(int H, int W, int m, bool single, int *y0, int *y1, int *x0, int *x1,
+                    int *chunks);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_pc_apply_batch(const StepArgs *args, int npairs, int max_n, cudaStream_t s);

@@ -1,27 +1,27 @@
-// Block-Toeplitz preconditioner of L-BFGS, built once per fit, and its
-// application P v inside every optimiser step.
+// Preconditioner of L-BFGS, built once per fit, and its application P v
+// inside every optimiser step.
 //
-// For kernel pixels u = (a, b), v = (a', b') the Gauss-Newton Hessian of the
-// loss, sum_p w_p R[p+u] R[p+v], is, up to the image border and the variation
-// of w, the weighted autocorrelation of R at lag v - u.  Built from the
-// zero-padded autocorrelation of Rt = sqrt(w) R over a window it is exactly
-// the Gram matrix of the shifted copies of Rt (and of a constant, for B0),
-// hence positive semidefinite; the preconditioned Hessian is well
-// conditioned (condition number about 4 on a 128 x 128, m = 11 pair, against
-// 2e5 with a diagonal preconditioner).
+// P is the inverse of the Gauss-Newton Hessian of the per-pixel loss over a
+// window of valid pixels, H = sum_p w_p phi_p phi_p^T / N_window, with
+// phi_p = [R window of p (Eq. 2), 1] and w_p = mask / (variance at M = I):
+// for the fixed-variance chi^2 this is the exact Hessian (on the window), for
+// the other losses its Gauss-Newton part.  As a Gram matrix it is positive
+// semidefinite; the window keeps its cost to a few ms (pc_window_side).
 //
 // Build, every launch over all pairs of a batch (blockIdx.y, or blockIdx.x
 // for one-CTA-per-pair kernels):
-//   rtilde      Rt over the window;
-//   autocorr    one CTA per row lag dr: sum over row pairs (y, y + dr) held
-//               in shared memory, every column lag at once;
-//   fill        T (np x np, float64, padded with the identity), scaled by
-//               the window's pixel count (the optimiser's loss is per pixel);
+//   gn          64 x 64 blocks of the upper triangle of H, one pixel chunk per
+//               CTA: phi of 32 pixels gathered into shared memory, a 4 x 4
+//               register block per thread, float32 sums flushed to float64
+//               every 512 pixels;
+//   fill        chunks summed in a fixed order, scaled, the lower triangle
+//               mirrored, the padding set to the identity (np = n rounded up
+//               to 64);
 //   per block column K of 32: chol_diag (factor the diagonal block, invert
 //               it), chol_panel (L_IK = A_IK L_KK^-T), chol_update
 //               (A_IJ -= L_IK L_JK^T);
 //   per block diagonal d: trtri (X_IJ = -X_II sum_T L_IT X_TJ), X = L^-1;
-//   gram        P = X^T X = T^-1 (float32, symmetric).
+//   gram        P = X^T X = H^-1 (float32, symmetric).
 // pc_ok is cleared when a pivot is not positive (the diagonal preconditioner
 // is used instead).
 #include <cmath>
@@ -35,19 +35,7 @@ namespace {
 
 constexpr int kB = kPcB;
 
-__device__ __forceinline__ double block_sum256(double v, double *sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    return t;
-}
-
-// Weight of image pixel q (offset in the pitched image): mask / variance at M = I.
+// Weight of target pixel q (offset in the pitched image): mask / variance at M = I.
 __device__ __forceinline__ float pc_weight(const PrecondArgs &a, size_t q) {
     float v;
     if (a.lp.var_model == 0) {
@@ -61,121 +49,162 @@ __device__ __forceinline__ float pc_weight(const PrecondArgs &a, size_t q) {
     return (a.mask && a.mask[q] == 0) ? 0.f : 1.0f / v;
 }
 
-__global__ void rtilde_kernel(const PrecondArgs *pas, int npairs) {
-    for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
-        const PrecondArgs &a = pas[p];
-        const int h = a.m / 2, wx = a.x1 - a.x0;
-        const long long total = (long long)(a.y1 - a.y0) * wx;
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-             i += (long long)gridDim.x * blockDim.x) {
-            const int py = a.y0 + (int)(i / wx), px = a.x0 + (int)(i % wx);
-            const size_t q = (size_t)(py + h) * a.ld + (px + h);   // pixel p + c of the image
-            a.Rt[i] = sqrtf(pc_weight(a, q)) * a.R[q];
-        }
-    }
+constexpr int kGnThreads = 256;
+constexpr int kGnKB = 32;          // pixels per shared-memory batch
+constexpr int kGnFlush = 16;       // batches per float64 flush (512 pixels)
+
+__host__ __device__ inline long long window_px(const PrecondArgs &a) {
+    return (long long)(a.y1 - a.y0) * (a.x1 - a.x0);
 }
 
-// Block dr < m: C[dr][dc + m - 1] for every dc in [-(m-1), m-1].  Thread t
-// takes column lag t % L over the t / L-th chunk of the columns; row pairs are
-// staged in shared memory; float32 per row, float64 across rows.
-// Block dr == m: sum of Rt and sum of w over the window.
-constexpr int kAcThreads = 256;
-constexpr int kAcMaxW = 1024;
+// Block b of the upper triangle (row-major over U <= V) of nt x nt tiles.
+__device__ __forceinline__ void gn_block(int b, int nt, int &U, int &V) {
+    U = 0;
+    while (b >= nt - U) {
+        b -= nt - U;
+        ++U;
+    }
+    V = U + b;
+}
 
-__global__ void __launch_bounds__(kAcThreads) autocorr_kernel(const PrecondArgs *pas, int npairs) {
-    __shared__ float ra[kAcMaxW], rb[kAcMaxW];
-    __shared__ double part[kAcThreads];
-    __shared__ double sh[kAcThreads / 32];
+__global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, int npairs) {
+    __shared__ __align__(16) float sA[kGnKB][kGnT], sB[kGnKB][kGnT];
+    __shared__ int offU[kGnT], offV[kGnT];
+    __shared__ long long sBase[kGnKB];
+    __shared__ float sW[kGnKB];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int m = a.m, h = m / 2, L = 2 * m - 1, nl = m * L;
-        const int wy = a.y1 - a.y0, wx = a.x1 - a.x0;
-        const int dr = blockIdx.x;
-        if (dr > m) continue;
-        if (dr == m) {
-            double tot = 0.0, tot_w = 0.0;
-            for (int y = 0; y < wy; ++y) {
-                float acc = 0.f, acc_w = 0.f;
-                for (int x = threadIdx.x; x < wx; x += blockDim.x) {
-                    acc += a.Rt[(size_t)y * wx + x];
-                    acc_w += pc_weight(a, (size_t)(a.y0 + y + h) * a.ld + (a.x0 + x + h));
+        const int m = a.m, n = m * m + 1, h = m / 2, ld = a.ld, nt = gn_tiles(n);
+        const int wx = a.x1 - a.x0;
+        const long long npx = window_px(a);
+        const int nch = a.gn_chunks, nblk = gn_blocks(n);
+        if ((int)blockIdx.x >= nblk * nch) continue;
+        const int b = blockIdx.x / nch, chunk = blockIdx.x % nch;
+        int U, V;
+        gn_block(b, nt, U, V);
+        __syncthreads();   // shared memory of the previous pair
+        // offset of phi_u in R relative to the window pixel's R[py][px];
+        // -1: the constant of B0, -2: padding (zero)
+        if (tid < 2 * kGnT) {
+            const int u = (tid < kGnT ? U : V) * kGnT + (tid & (kGnT - 1));
+            const int o = u < n - 1 ? (u / m) * ld + u % m : (u == n - 1 ? -1 : -2);
+            if (tid < kGnT) offU[tid] = o; else offV[tid - kGnT] = o;
+        }
+        float acc[4][4];
+        double acc64[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                acc[i][j] = 0.f;
+                acc64[i][j] = 0.0;
+            }
+        const long long k0 = (long long)chunk * ((npx + nch - 1) / nch);
+        const long long k1 = min(npx, k0 + (npx + nch - 1) / nch);
+        int nb = 0;
+        for (long long kb = k0; kb < k1; kb += kGnKB) {
+            __syncthreads();
+            if (tid < kGnKB) {
+                const long long k = kb + tid;
+                if (k < k1) {
+                    const int py = a.y0 + (int)(k / wx), px = a.x0 + (int)(k % wx);
+                    sBase[tid] = (long long)py * ld + px;
+                    sW[tid] = pc_weight(a, (size_t)(py + h) * ld + (px + h));
+                } else {
+                    sBase[tid] = -1;
+                    sW[tid] = 0.f;
                 }
-                tot += acc;
-                tot_w += acc_w;
-            }
-            tot = block_sum256(tot, sh);
-            tot_w = block_sum256(tot_w, sh);
-            if (threadIdx.x == 0) {
-                a.C[nl] = tot;
-                a.C[nl + 1] = tot_w;
             }
             __syncthreads();
-            continue;
-        }
-        const int nch = kAcThreads / L;
-        const int t = threadIdx.x, li = t % L, ch = t / L;
-        const int dc = li - (m - 1);
-        const int xa = dc < 0 ? -dc : 0, nx = wx - (dc < 0 ? -dc : dc);
-        const int per = nx > 0 ? (nx + nch - 1) / nch : 0;
-        const int xb = xa + ch * per, xe = min(xa + nx, xb + per);
-        double acc = 0.0;
-        for (int y = 0; y + dr < wy; ++y) {
-            __syncthreads();
-            for (int x = t; x < wx; x += kAcThreads) {
-                ra[x] = a.Rt[(size_t)y * wx + x];
-                rb[x] = a.Rt[(size_t)(y + dr) * wx + x];
+            for (int e = tid; e < kGnKB * kGnT; e += kGnThreads) {
+                const int kk = e / kGnT, ul = e % kGnT;
+                const long long base = sBase[kk];
+                float va = 0.f, vb = 0.f;
+                if (base >= 0) {
+                    const int ou = offU[ul], ov = offV[ul];
+                    va = ou >= 0 ? a.R[base + ou] : (ou == -1 ? 1.f : 0.f);
+                    vb = ov >= 0 ? a.R[base + ov] : (ov == -1 ? 1.f : 0.f);
+                }
+                sA[kk][ul] = sW[kk] * va;
+                sB[kk][ul] = vb;
             }
             __syncthreads();
-            if (ch < nch) {
-                float s = 0.f;
-                for (int x = xb; x < xe; ++x) s = fmaf(ra[x], rb[x + dc], s);
-                acc += s;
+#pragma unroll 8
+            for (int kk = 0; kk < kGnKB; ++kk) {
+                const float4 av = *reinterpret_cast<const float4 *>(&sA[kk][ty * 4]);
+                const float4 bv = *reinterpret_cast<const float4 *>(&sB[kk][tx * 4]);
+                const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+            }
+            if (++nb == kGnFlush) {
+                nb = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        acc64[i][j] += acc[i][j];
+                        acc[i][j] = 0.f;
+                    }
             }
         }
-        part[t] = (ch < nch) ? acc : 0.0;
-        __syncthreads();
-        if (t < L) {
-            double c = 0.0;
-            for (int k = 0; k < nch; ++k) c += part[k * L + t];
-            a.C[dr * L + t] = c;
-        }
-        __syncthreads();
+        const double inv = 1.0 / (double)npx;
+        const int np = pc_np(n);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const double v = acc64[i][j] + acc[i][j];
+                const int il = ty * 4 + i, jl = tx * 4 + j;
+                if (nch > 1) {
+                    a.part[((size_t)chunk * nblk + b) * (kGnT * kGnT) + il * kGnT + jl] = v;
+                } else {   // final values of the upper blocks, in place
+                    const int u = U * kGnT + il, w = V * kGnT + jl;
+                    double t;
+                    if (u >= n || w >= n)
+                        t = (u == w) ? 1.0 : 0.0;
+                    else
+                        t = v * inv * ((u == w) ? 1.0 + a.eps : 1.0);
+                    a.A64[(size_t)u * np + w] = t;
+                }
+            }
     }
 }
 
-// T (padded to np with the identity) into A64, X64 zeroed, pc_ok set.
+// H from the chunk partials (fixed order) or, with one chunk, the lower
+// blocks mirrored from the upper ones; X64 and P zeroed; pc_ok set.
 __global__ void fill_kernel(const PrecondArgs *pas, int npairs) {
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int m = a.m, n = m * m + 1, np = pc_np(n), L = 2 * m - 1, nl = m * L;
-        const int wy = a.y1 - a.y0, wx = a.x1 - a.x0;
-        const double npx = (double)wy * wx;
-        const double wbar = a.C[nl + 1] / npx;   // mean weight over the window
+        const int n = a.m * a.m + 1, np = pc_np(n), nt = gn_tiles(n), nblk = gn_blocks(n);
+        const int nch = a.gn_chunks;
+        const double inv = 1.0 / (double)window_px(a);
         for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)np * np;
              e += (long long)gridDim.x * blockDim.x) {
-            const int u = (int)(e / np), v = (int)(e % np);
+            const int u = (int)(e / np), w = (int)(e % np);
+            const int Tu = u / kGnT, Tw = w / kGnT;
+            a.X64[e] = 0.0;
+            if (nch == 1) {
+                if (Tu > Tw) a.A64[e] = a.A64[(size_t)w * np + u];
+                continue;
+            }
+            // block (min, max) of the upper triangle and the entry within it
+            const int U = min(Tu, Tw), V = max(Tu, Tw);
+            const int il = (Tu <= Tw ? u : w) - U * kGnT, jl = (Tu <= Tw ? w : u) - V * kGnT;
+            const int b = U * nt - U * (U - 1) / 2 + (V - U);
             double t;
-            if (u >= n || v >= n) {
-                t = (u == v) ? 1.0 : 0.0;
+            if (u >= n || w >= n) {
+                t = (u == w) ? 1.0 : 0.0;
             } else {
-                if (u == n - 1 && v == n - 1) {
-                    // the constant sqrt(wbar) over the window dilated by m - 1
-                    t = wbar * (double)(wy + m - 1) * (double)(wx + m - 1);
-                } else if (u == n - 1 || v == n - 1) {
-                    t = sqrt(wbar) * a.C[nl];
-                } else {
-                    int dr = v / m - u / m, dc = v % m - u % m;
-                    if (dr < 0 || (dr == 0 && dc < 0)) {
-                        dr = -dr;
-                        dc = -dc;
-                    }
-                    t = a.C[dr * L + dc + (m - 1)];
-                }
-                if (u == v) t *= (1.0 + a.eps);
-                t /= npx;
+                double s = 0.0;
+                for (int c = 0; c < nch; ++c)
+                    s += a.part[((size_t)c * nblk + b) * (kGnT * kGnT) + il * kGnT + jl];
+                t = s * inv * ((u == w) ? 1.0 + a.eps : 1.0);
             }
             a.A64[e] = t;
-            a.X64[e] = 0.0;
         }
         // P, including the pitch padding that P v reads (times zero)
         for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * a.ldp;
@@ -413,18 +442,20 @@ __global__ void __launch_bounds__(kPaThreads) pc_apply_batch_kernel(const StepAr
 cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
                            cudaStream_t s) {
     if (npairs < 1) return cudaErrorInvalidValue;
-    int max_m = 1;
+    int max_m = 1, gn_grid = 1;
     for (int i = 0; i < npairs; ++i) {
         const PrecondArgs &a = h_pas[i];
-        if (a.m * a.m + 1 > kPcMaxN || a.x1 - a.x0 > kAcMaxW || a.x1 <= a.x0 || a.y1 <= a.y0 ||
-            a.ldp < a.m * a.m + 1 || (a.ldp & 3) != 0)
+        const int n = a.m * a.m + 1;
+        if (n > kPcMaxN || a.x1 <= a.x0 || a.y1 <= a.y0 || a.ldp < n || (a.ldp & 3) != 0 ||
+            a.gn_chunks < 1 || (a.gn_chunks > 1 && !a.part) ||
+            (long long)a.gn_chunks > window_px(a))
             return cudaErrorInvalidValue;
         max_m = max(max_m, a.m);
+        gn_grid = max(gn_grid, gn_blocks(n) * a.gn_chunks);
     }
     const int max_n = max_m * max_m + 1, nb = pc_np(max_n) / kB;
     const unsigned gy = (unsigned)min(npairs, 65535);
-    rtilde_kernel<<<dim3(npairs == 1 ? 256 : 16, gy), 256, 0, s>>>(d_pas, npairs);
-    autocorr_kernel<<<dim3(max_m + 1, gy), kAcThreads, 0, s>>>(d_pas, npairs);
+    gn_kernel<<<dim3(gn_grid, gy), kGnThreads, 0, s>>>(d_pas, npairs);
     fill_kernel<<<dim3(npairs == 1 ? 64 : 8, gy), 256, 0, s>>>(d_pas, npairs);
     for (int K = 0; K < nb; ++K) {
         chol_diag_kernel<<<min(npairs, 65535), 1024, 0, s>>>(d_pas, npairs, K);
@@ -441,7 +472,22 @@ cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, i
 
 int precond_launches(int max_m) {
     const int nb = pc_np(max_m * max_m + 1) / kB;
-    return 3 + nb + 2 * (nb - 1) + (nb - 1) + 1;
+    return 2 + nb + 2 * (nb - 1) + (nb - 1) + 1;
+}
+
+// Window (centred, side pc_window_side) and chunk count of a pair's
+// Hessian sum; chunks > 1 only for a single pair (a batch has parallelism
+// across its pairs).
+void precond_window(int H, int W, int m, bool single, int *y0, int *y1, int *x0, int *x1,
+                    int *chunks) {
+    const int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h, side = pc_window_side(m * m + 1);
+    const int sy = min(Hv, side), sx = min(Wv, side);
+    *y0 = (Hv - sy) / 2;
+    *y1 = *y0 + sy;
+    *x0 = (Wv - sx) / 2;
+    *x1 = *x0 + sx;
+    const long long px = (long long)sy * sx;
+    *chunks = single ? (int)min(64LL, (px + kGnChunk - 1) / kGnChunk) : 1;
 }
 
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s) {
