@@ -232,7 +232,7 @@ def _config(args, d):
             "masked_frac": None if d.get("mask") is None else float(1 - d["mask"].mean()),
             "seeds": [args.seed + r for r in range(_env_int("WORLD_SIZE", 1))],
             "l2": f"inputs larger than L2 ({by / 2**20:.0f} MiB > {L2_BYTES / 2**20:.0f} MiB)",
-            "init": "box-car K, B0 = median(I) (Sec. 2.8)",
+            "init": "box-car K, B0 = median(I) (Sec. 2.9)",
             "optimizer": "Adam -> L-BFGS (block-Toeplitz preconditioned, library defaults)"}
 
 
@@ -344,6 +344,25 @@ def run_ours(args, rank, world, local_rank):
             "algorithmic": f"4*m^2 flop x {npx} unmasked valid px = {flops / 1e9:.2f} GFLOP per launch",
             "eval_ms": t_eval * 1e3}
 
+    # the same fit without the Adam phase (preconditioned L-BFGS from the start)
+    o_off = nat.default_opts(clip_passes=opts.clip_passes, clip_kappa=opts.clip_kappa,
+                             max_adam_iters=0)
+    step_off = lambda: nat.fit(R, I, m, spec, o_off, mask=mask, var=var, ws=ws, stream=stream,
+                               want_diff=True)
+    step_off()
+    torch.cuda.synchronize(dev)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_off, ev_off = max(1, min(args.steps, 3)), 0
+    a0.record(stream)
+    for _ in range(n_off):
+        ev_off += step_off()["info"]["evals"]
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_off = a0.elapsed_time(a1)
+    adam_off = {"fits_per_s": n_off / (ms_off / 1e3), "evals_per_fit": ev_off / n_off,
+                "what": "same fits with max_adam_iters = 0 (the library default keeps the "
+                        "paper's Adam phase)"}
+
     # e2e: the same fits with the pair in pinned host memory (library stages it)
     e2e = None
     if not args.no_e2e:
@@ -407,6 +426,7 @@ def run_ours(args, rank, world, local_rank):
                        "tile_variant": tuned.get("variant")},
             "fits_per_s": fits_per_s,
             "evals_per_fit": evals_all / (args.steps * world),
+            "adam_off": adam_off,
             "fit_info": {k: last.get(k) for k in ("status", "adam_iters", "lbfgs_iters", "evals",
                                                   "clip_passes_done", "reason", "ndata",
                                                   "precond_used")},
@@ -481,6 +501,18 @@ def run_batch(args, rank, world, local_rank):
     _, launches_all = shard.reduce_max_sum(0.0, launches, device=dev)
     _, flops_all = shard.reduce_max_sum(0.0, flops, device=dev)
     fits_s = pairs_all / (ms / 1e3)
+    # the same batch without the Adam phase
+    o_off = nat.default_opts(timeout_s=900.0, max_adam_iters=0)
+    nat.fit_batch(items, spec, o_off, ws=ws, stream=stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    out_off = nat.fit_batch(items, spec, o_off, ws=ws, stream=stream)
+    torch.cuda.synchronize(dev)
+    adam_off = {"fits_per_s_rank0": len(items) / (time.perf_counter() - t0),
+                "evals_per_pair": float(np.mean([f["evals"] for f in out_off["infos"]])),
+                "converged": int(sum(f["status"] == 0 for f in out_off["infos"])),
+                "what": "same pairs with max_adam_iters = 0 (the library default keeps the "
+                        "paper's Adam phase)"}
     # same-pairs subset: batched vs one at a time (single GPU only)
     t = None
     if world == 1:
@@ -525,7 +557,7 @@ def run_batch(args, rank, world, local_rank):
                        "sharding": "pairs split across ranks by cost, no collective"},
             "evals_per_s": evals_all / (ms / 1e3), "pairs_converged": int(ok),
             "gpu_launches": int(launches_all), "roofline": roof,
-            "subset_fits_per_s": t, "clocks": clocks}
+            "subset_fits_per_s": t, "adam_off": adam_off, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -7,8 +7,8 @@
  *     M_ij = sum_{l,m} K_lm R_(i+l)(j+m) + B0                 (Sec. 2.1, Eq. 2)
  *
  * to a target image I by minimising a per-pixel negative log-likelihood
- * (Sec. 2.3, Eq. 7; Sec. 2.4, Eq. 11) with Adam followed by L-BFGS
- * (Sec. 2.3, Sec. 2.8).  Every step of the fit runs in this library's own
+ * (Sec. 2.3, Eq. 8; Sec. 2.4, Eq. 13) with Adam followed by L-BFGS
+ * (Sec. 2.3, Sec. 2.9).  Every step of the fit runs in this library's own
  * CUDA kernels on one GPU.
  *
  * Conventions shared by every entry point
@@ -69,16 +69,16 @@ typedef enum {
 
 /* Loss shape rho(z) of the pixel residual z = (I - M)/sigma. */
 typedef enum {
-    DIA_RHO_GAUSS = 0,         /* z^2/2                        (Eq. 7)  */
-    DIA_RHO_HUBER = 1,         /* Huber with threshold c       (Eq. 10) */
+    DIA_RHO_GAUSS = 0,         /* z^2/2                        (Eq. 8)  */
+    DIA_RHO_HUBER = 1,         /* Huber with threshold c       (Eq. 12) */
     DIA_RHO_CAUCHY = 2         /* ln(1 + z^2), the Student-t nu=1 drop-in (Sec. 2.4) */
 } dia_rho;
 
 /* Pixel variance sigma^2. */
 typedef enum {
     DIA_VAR_FIXED = 0,         /* var map, else var_scalar; ln sigma dropped (constant) */
-    DIA_VAR_CCD = 1,           /* sigma0^2/F^2 + M/(G F)       (Eq. 5) */
-    DIA_VAR_EMCCD = 2          /* E M/(G F), G = G_total       (Eq. 6) */
+    DIA_VAR_CCD = 1,           /* sigma0^2/F^2 + M/(G F)       (Eq. 6) */
+    DIA_VAR_EMCCD = 2          /* E M/(G F), G = G_total       (Eq. 7) */
 } dia_var_model;
 
 typedef struct {
@@ -97,7 +97,7 @@ typedef enum { DIA_MEM_DEVICE = 0, DIA_MEM_HOST = 1 } dia_mem;
 
 /* One reference/target pair. */
 typedef struct {
-    const float *ref;          /* R, H x W pitch ld (background-subtracted, Sec. 2.8) */
+    const float *ref;          /* R, H x W pitch ld (background-subtracted, Sec. 2.9) */
     const float *img;          /* I, H x W pitch ld */
     const uint8_t *mask;       /* nullable: every pixel used */
     const float *var;          /* nullable: fixed variance map (DIA_VAR_FIXED) */
@@ -108,7 +108,7 @@ typedef struct {
                                   outputs of the call live */
 } dia_pair;
 
-/* Optimiser settings (Sec. 2.8).  dia_opts_default() fills the paper's
+/* Optimiser settings (Sec. 2.9).  dia_opts_default() fills the paper's
  * values; a NULL dia_opts* means those defaults. */
 typedef struct {
     double lr_kernel;          /* Adam learning rate of the kernel pixels (1e-3) */
@@ -128,7 +128,7 @@ typedef struct {
     float clip_kappa;          /* clip |z| > kappa (5, Sec. 4.2) */
     int32_t init;              /* 0: box-car K = 1/m^2, 1: Gaussian of init_sigma,
                                   2: theta0; B0 = median of the unmasked valid I
-                                  for 0 and 1 (Sec. 2.8) */
+                                  for 0 and 1 (Sec. 2.9) */
     double init_sigma;         /* Gaussian init width phi_K (px) */
     const double *theta0;      /* HOST pointer, n entries, used when init == 2 */
     int32_t graph_iters;       /* optimiser iterations per CUDA-graph launch (16) */
@@ -203,7 +203,7 @@ dia_status dia_kernel_variant_desc(int32_t m, int32_t variant, int32_t *warps,
  * covers every tile variant of m. */
 size_t dia_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m, int32_t clip, int32_t mem);
 
-/* One loss + gradient evaluation at theta (Sec. 2.3, Eq. 7 / Eq. 11).
+/* One loss + gradient evaluation at theta (Sec. 2.3, Eq. 8 / Eq. 13).
  *   theta     device float64[n]  (read; the kernel works in float32 pixels)
  *   loss_out  device float64[1]  L = sum over unmasked valid pixels
  *   grad_out  device float64[n]  dL/dtheta, same layout as theta
@@ -221,7 +221,7 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss,
 dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff_out,
                           void *workspace, size_t workspace_bytes, void *stream);
 
-/* Fit theta = [K, B0] (Sec. 2.9 algorithm): initialise, Adam until the
+/* Fit theta = [K, B0] (Sec. 2.10 algorithm): initialise, Adam until the
  * relative loss change drops below switch_tol, then L-BFGS with a
  * strong-Wolfe line search until rel_tol / grad_tol; optionally clip
  * |z| > kappa and refit clip_passes times.  Each optimiser iteration is one
@@ -288,6 +288,43 @@ dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs, const dia_loss_s
 dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss_spec *loss,
                                  const double *theta, double *loss_out, double *grad_out,
                                  void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Observed Fisher information and covariance (Sec. 2.5, Eq. 15 and 16).
+ *
+ * F = d^2 L / d theta^2 at theta, L the loss of dia_loss_grad (for the
+ * Gaussian loss with a fixed or model-dependent variance this is the negative
+ * log-likelihood up to constants, so F is the observed Fisher information; for
+ * Huber and Cauchy it is the Hessian of that loss).  M is linear in theta, so
+ * F = sum_p l''(M_p) phi_p phi_p^T over every unmasked valid pixel, with
+ * phi_p = [R window of p, 1]; float32 per-pixel terms, float64 sums (every 32
+ * pixels), n = m*m + 1.  The covariance estimate is F^-1 at the fitted theta
+ * (Eq. 16); its diagonal square roots are the Cramer-Rao bounds (Eq. 17).
+ * Sec. 2.5 asks that the covariance be checked: F is tested for positive
+ * definiteness by a float64 Cholesky factorisation (for a symmetric matrix
+ * this is the same as every eigenvalue > 0, and then the determinant is > 0).
+ */
+typedef struct {
+    int32_t positive_definite; /* 1: F (and so F^-1) is positive definite; 0: the
+                                  warning flag of Sec. 2.5 -- cov_out is NaN */
+    int32_t n;                 /* m*m + 1 */
+    double log_det;            /* ln det F (valid when positive_definite) */
+    double min_pivot;          /* smallest pivot of the Cholesky factorisation */
+    int64_t ndata;             /* unmasked valid pixels summed */
+} dia_fisher_info;
+
+/* Workspace bytes of dia_fisher for this image and kernel side (0 if invalid). */
+size_t dia_fisher_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m);
+
+/* pair: DIA_MEM_DEVICE images; theta: DEVICE pointer, n doubles (e.g. the
+ * theta_out of dia_fit); F_out, cov_out: nullable DEVICE pointers to n x n
+ * row-major doubles (at least one of them, or info, should be given); info:
+ * nullable HOST pointer, filled after the stream is synchronised (the call is
+ * then synchronous).  Errors: DIA_ERR_ARG (bad pair, loss or pointers),
+ * DIA_ERR_WORKSPACE, DIA_ERR_UNSUPPORTED (m > DIA_MAX_M), DIA_ERR_CUDA. */
+dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
+                      double *F_out, double *cov_out, dia_fisher_info *info, void *workspace,
+                      size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

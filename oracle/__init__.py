@@ -8,8 +8,8 @@ loads it and shares no code with it: the direct loops live in ``dia_oracle.c``
 Pieces (each cites the passage it follows):
 
 * :func:`model`, :func:`loss_grad`, :func:`pixel_terms` -- the image model
-  (Sec. 2.1, Eq. 2), the noise models (Eq. 5, Eq. 6) and the loss (Eq. 7,
-  Eq. 11 with the Huber rho of Eq. 10 or a Cauchy rho as the Student-t drop-in
+  (Sec. 2.1, Eq. 2), the noise models (Eq. 6, Eq. 7) and the loss (Eq. 8,
+  Eq. 13 with the Huber rho of Eq. 12 or a Cauchy rho as the Student-t drop-in
   named in Sec. 2.4), by direct loops in FP64.
 * :func:`gram`, :func:`normal_solve` -- the Bramich (2008) normal equations
   for the fixed-variance chi^2 (Sec. 1 and Sec. 2.1): A = sum w phi phi^T,
@@ -87,7 +87,7 @@ def _load():
 @dataclass
 class LossSpec:
     """Loss choice: rho in {gauss, huber, cauchy}, variance model in
-    {fixed, ccd, emccd} (Eq. 5, Eq. 6), and their constants."""
+    {fixed, ccd, emccd} (Eq. 6, Eq. 7), and their constants."""
     rho: str = "gauss"
     noise: str = "fixed"
     sigma0: float = 0.0        # read noise (image units), CCD model
@@ -172,7 +172,7 @@ def pixel_terms(I, M, m, spec: LossSpec, mask=None, var=None, flat=None):
 
 def loss_grad(R, I, m, theta, spec: LossSpec = None, mask=None, var=None, flat=None,
               nthreads: int = 0):
-    """FP64 loss L(theta) and gradient dL/dtheta (Eq. 7 / Eq. 11, summed over the
+    """FP64 loss L(theta) and gradient dL/dtheta (Eq. 8 / Eq. 13, summed over the
     unmasked valid pixels).  Returns (L, grad[m*m+1])."""
     spec = spec or LossSpec()
     R = _d(R)

@@ -12,10 +12,10 @@
  *                   with centred offsets l,m in [-h, h], kernel side 2h+1,
  *                   defined only where the whole kernel footprint lies
  *                   inside R, i.e. i,j in [h, N-h)                     (Sec. 2.1, N_data)
- *   pixel variance  fixed map / CCD  s0^2/F^2 + M/(G F)                (Sec. 2.1, Eq. 5)
- *                   EMCCD  E M/(G_tot F)                                (Sec. 2.1, Eq. 6)
- *   pixel loss      rho(z) + ln(sigma), z = (I - M)/sigma               (Sec. 2.3, Eq. 7;
- *                   rho = z^2/2 (Gaussian), Huber (Sec. 2.4, Eq. 10),   Sec. 2.4, Eq. 11)
+ *   pixel variance  fixed map / CCD  s0^2/F^2 + M/(G F)                (Sec. 2.1, Eq. 6)
+ *                   EMCCD  E M/(G_tot F)                                (Sec. 2.1, Eq. 7)
+ *   pixel loss      rho(z) + ln(sigma), z = (I - M)/sigma               (Sec. 2.3, Eq. 8;
+ *                   rho = z^2/2 (Gaussian), Huber (Sec. 2.4, Eq. 12),   Sec. 2.4, Eq. 13)
  *                   Cauchy ln(1+z^2) (a Student-t drop-in, Sec. 2.4)
  *   total loss      L = sum over unmasked valid pixels
  *   gradient        dL/dK_lm = sum_p dl/dM_p R_(p+lm),  dL/dB0 = sum_p dl/dM_p

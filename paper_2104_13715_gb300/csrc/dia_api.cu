@@ -531,7 +531,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     }
     c.ea.clip_kappa = opts.clip_kappa;
 
-    // initial theta (Sec. 2.8)
+    // initial theta (Sec. 2.9)
     const int start_phase = opts.max_adam_iters > 0 ? kPhaseAdam : kPhaseLbfgsStart;
     long long launches = 0;   // kernels this call launches (graph nodes included)
     if (opts.init == 2) {
@@ -573,6 +573,8 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             pa.ldp = pc_ldp(n);
             pa.st = c.st;
             pa.eps = 1e-6;
+            pa.scale = 1.0 / ((double)(pa.y1 - pa.y0) * (pa.x1 - pa.x0));
+            pa.flush = kGnFlushPc;
             PrecondArgs *d_pa = (PrecondArgs *)(c.ws + c.L.pc_args);
             DIA_CK(cudaMemcpyAsync(d_pa, &pa, sizeof(pa), cudaMemcpyHostToDevice, s));
             DIA_CK(launch_precond(d_pa, &pa, 1, s));
@@ -701,6 +703,126 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         DIA_CK(cudaStreamSynchronize(s));
     }
     return (dia_status)status;
+}
+
+// ---------------------------------------------------------------- Fisher
+// Workspace of dia_fisher after the evaluation workspace: state, descriptor,
+// two result doubles, the per-pixel curvature (valid region), the chunk
+// partials of the sum and the float64 factor and inverse.
+struct FisherLayout {
+    size_t base, st, args, res, w, part, A, X, total;
+    int chunks;
+};
+
+static bool fisher_layout(int H, int W, int ld, int m, FisherLayout &F) {
+    F.base = dia_workspace_size(H, W, ld, m, 0, DIA_MEM_DEVICE);
+    if (F.base == 0) return false;
+    const int h = m / 2, n = m * m + 1;
+    const long long npx = (long long)(H - 2 * h) * (W - 2 * h);
+    F.chunks = (int)std::min(64LL, (npx + kGnChunk - 1) / kGnChunk);
+    size_t o = align_up(F.base);
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    F.st = take(sizeof(FitState));
+    F.args = take(sizeof(PrecondArgs));
+    F.res = take(3 * sizeof(double));
+    F.w = take((size_t)npx * 4);
+    F.part = take(F.chunks > 1 ? (size_t)F.chunks * gn_blocks(n) * kGnT * kGnT * 8 : 0);
+    F.A = take((size_t)pc_np(n) * pc_np(n) * 8);
+    F.X = take((size_t)pc_np(n) * pc_np(n) * 8);
+    F.total = o;
+    return true;
+}
+
+size_t dia_fisher_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m) {
+    FisherLayout F;
+    return fisher_layout(H, W, ld, m, F) ? F.total : 0;
+}
+
+dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
+                      double *F_out, double *cov_out, dia_fisher_info *info, void *workspace,
+                      size_t workspace_bytes, void *stream) {
+    if (!pair || pair->mem != DIA_MEM_DEVICE || !loss || !theta) return DIA_ERR_ARG;
+    if (!F_out && !cov_out && !info) return DIA_ERR_ARG;
+    FisherLayout FL;
+    if (!dims_ok(pair->H, pair->W, pair->ld, pair->m)) return DIA_ERR_ARG;
+    if (pair->m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
+    if (!fisher_layout(pair->H, pair->W, pair->ld, pair->m, FL)) return DIA_ERR_ARG;
+    if (!workspace || workspace_bytes < FL.total) return DIA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    dia_status rc = setup(pair, loss, 0, workspace, FL.base, s, c);
+    if (rc != DIA_OK) return rc;
+    const int m = pair->m, n = m * m + 1, h = m / 2, np = pc_np(n);
+    const int Hv = pair->H - 2 * h, Wv = pair->W - 2 * h;
+    char *ws = (char *)workspace;
+    float *w = (float *)(ws + FL.w);
+    FitState *st = (FitState *)(ws + FL.st);
+    double *res = (double *)(ws + FL.res);
+
+    // curvature l''(M_p) at theta: D = I - M from the forward pass, then l''
+    DIA_CK(launch_prep_kpad(theta, m, c.ki.kp, c.kpad, s));
+    EvalArgs ea = c.ea;
+    ea.diff_out = w;
+    DIA_CK(launch_eval(c.ki, kModeForward, ea, c.grid, s));
+    DIA_CK(cudaMemsetAsync(res, 0, 3 * sizeof(double), s));
+    DIA_CK(launch_fisher_weights(c.ea, w, (unsigned long long *)(res + 2), s));
+
+    // F = sum_p l'' phi phi^T over the valid region, its factor and inverse
+    PrecondArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.R = c.dp.ref;
+    pa.I = c.dp.img;
+    pa.mask = c.ea.mask;
+    pa.var = c.dp.var;
+    pa.flat = c.dp.flat;
+    pa.H = pair->H;
+    pa.W = pair->W;
+    pa.ld = pair->ld;
+    pa.m = m;
+    pa.y0 = 0;
+    pa.y1 = Hv;
+    pa.x0 = 0;
+    pa.x1 = Wv;
+    pa.lp = c.ea.lp;
+    pa.part = (double *)(ws + FL.part);
+    pa.gn_chunks = FL.chunks;
+    pa.A64 = (double *)(ws + FL.A);
+    pa.X64 = (double *)(ws + FL.X);
+    pa.P = nullptr;
+    pa.ldp = pc_ldp(n);
+    pa.st = st;
+    pa.eps = 0.0;
+    pa.scale = 1.0;
+    pa.flush = 1;   // float64 every 32 pixels: F^-1 needs ~1e-9 relative sums
+    pa.wmap = w;
+    pa.wmap_ld = Wv;
+    pa.F_out = F_out;
+    pa.cov_out = cov_out;
+    PrecondArgs *d_pa = (PrecondArgs *)(ws + FL.args);
+    DIA_CK(cudaMemcpyAsync(d_pa, &pa, sizeof(pa), cudaMemcpyHostToDevice, s));
+    DIA_CK(launch_precond(d_pa, &pa, 1, s));
+    DIA_CK(launch_fisher_finish(pa.A64, n, np, res, s));
+
+    int pd = 0;
+    double r[3] = {0.0, 0.0, 0.0};
+    DIA_CK(cudaMemcpyAsync(&pd, &st->pc_ok, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DIA_CK(cudaMemcpyAsync(r, res, sizeof(r), cudaMemcpyDeviceToHost, s));
+    DIA_CK(cudaStreamSynchronize(s));
+    if (!pd && cov_out) DIA_CK(cudaMemsetAsync(cov_out, 0xFF, (size_t)n * n * 8, s));   // NaN
+    if (info) {
+        unsigned long long cnt = 0;
+        memcpy(&cnt, &r[2], sizeof(cnt));
+        info->positive_definite = pd;
+        info->n = n;
+        info->log_det = pd ? r[0] : NAN;
+        info->min_pivot = r[1];
+        info->ndata = (int64_t)cnt;
+    }
+    return DIA_OK;
 }
 
 }  // extern "C"

@@ -329,6 +329,8 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
             pa.ldp = pc_ldp(n);
             pa.st = st;
             pa.eps = 1e-6;
+            pa.scale = 1.0 / ((double)(pa.y1 - pa.y0) * (pa.x1 - pa.x0));
+            pa.flush = kGnFlushPc;
             sa.b.P = pa.P;
         }
         sa.red = (const double *)(pb + q.red_off);
@@ -397,7 +399,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
                                 kBatchSmem, st);
     };
 
-    // initialisation: per-pair median and theta (Sec. 2.8)
+    // initialisation: per-pair median and theta (Sec. 2.9)
     const int start_phase = opts.max_adam_iters > 0 ? kPhaseAdam : kPhaseLbfgsStart;
     DB_CK(launch_init_batch(d_sa, d_eas, npairs, opts.init, opts.init_sigma, start_phase, s));
     // per-pair block-Toeplitz preconditioners (after init, which clears the state)

@@ -3,9 +3,9 @@
 //
 // Model (Sec. 2.1, Eq. 2): for an output pixel p = (y, x) of the valid region,
 //   M_p = sum_{a,b} K[a][b] R[y+a][x+b] + B0        (valid-region coordinates)
-// Loss (Sec. 2.3 Eq. 7, Sec. 2.4 Eq. 10-11): l_p = rho(z_p) + ln sigma_p with
+// Loss (Sec. 2.3 Eq. 8, Sec. 2.4 Eq. 12-13): l_p = rho(z_p) + ln sigma_p with
 // z = (I - M)/sigma and sigma^2 from the fixed map or the CCD / EMCCD models
-// (Eq. 5, Eq. 6).  Gradient: dL/dK[a][b] = sum_p g_p R[y+a][x+b],
+// (Eq. 6, Eq. 7).  Gradient: dL/dK[a][b] = sum_p g_p R[y+a][x+b],
 // dL/dB0 = sum_p g_p with g_p = dl_p/dM_p.
 //
 // One CTA owns a TH x TW tile of output pixels at a time (persistent loop over

@@ -181,7 +181,7 @@ __device__ void request_direction(const StepArgs &a, int slot) {
 //   H g = tau P g + S p1 + tau (PY) p2,  u = R^-1 S'g,  p2 = -u,
 //   p1 = R^-T ((D + tau Y'PY) u - tau (PY)'g),
 // R the upper triangle of S'Y and D its diagonal (chronological order); then
-// the start of the line search at alpha = 1 (Sec. 2.8).
+// the start of the line search at alpha = 1 (Sec. 2.9).
 __device__ void direction_body(const StepArgs &a, StepShared &sm) {
     FitState *st = a.st;
     if (*((volatile int *)&st->done) != 0) return;
@@ -283,7 +283,7 @@ __device__ void direction_body(const StepArgs &a, StepShared &sm) {
     for (int k = tid; k < n; k += kStepThreads) b.glo[k] = b.grad[k];
     if (tid == 0) {
         st->gd0 = gd0;
-        st->alpha = 1.0;   // L-BFGS learning rate 1 (Sec. 2.8)
+        st->alpha = 1.0;   // L-BFGS learning rate 1 (Sec. 2.9)
         st->lo = 0.0;
         st->L_lo = st->L;
         st->gd_lo = gd0;
@@ -377,7 +377,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
         const bool sw = (st->it_adam > 0 && fabs(Lt - st->L_prev) <= p.switch_tol * fabs(st->L_prev)) ||
                         st->it_adam >= p.max_adam;
         if (!sw) {
-            // Adam step (Kingma & Ba), per-parameter learning rates (Sec. 2.8)
+            // Adam step (Kingma & Ba), per-parameter learning rates (Sec. 2.9)
             const double b1t = st->b1t * p.beta1, b2t = st->b2t * p.beta2;
             const double bc1 = 1.0 - b1t, bc2 = 1.0 - b2t;
             for (int k = tid; k < n; k += kStepThreads) {
@@ -525,7 +525,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
             st->ev_best = st->evals;
         }
         st->stall = st->evals - st->ev_best;
-        // Convergence (Sec. 2.8): every |dL/dtheta| below grad_tol, or the
+        // Convergence (Sec. 2.9): every |dL/dtheta| below grad_tol, or the
         // limit of numerical precision: max|g| has not halved over the last
         // stall_iters evaluations (float32 pixel rounding sets a floor on the
         // gradient; once there, line searches fail and spend many
@@ -625,7 +625,7 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------------------------
-// Initialisation: K box-car (1/m^2) or a normalised Gaussian (Sec. 2.8, Sec. 5.1),
+// Initialisation: K box-car (1/m^2) or a normalised Gaussian (Sec. 2.9, Sec. 5.1),
 // B0 = median of the unmasked valid target pixels; or theta already in place.
 __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int mode,
                           double sigma, double median, int degenerate, int start_phase,

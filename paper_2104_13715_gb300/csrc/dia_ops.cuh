@@ -1,8 +1,8 @@
 // Small kernels around the fused evaluation: the float64 cross-CTA reduction,
 // the on-device optimiser (Adam, then L-BFGS with a Wolfe / approximate-Wolfe
-// line search and a block-Toeplitz preconditioner, Sec. 2.3 and Sec. 2.8),
+// line search and a block-Toeplitz preconditioner, Sec. 2.3 and Sec. 2.9),
 // initialisation (box-car or Gaussian kernel, B0 =
-// median of the target, Sec. 2.8) and output packing.
+// median of the target, Sec. 2.9) and output packing.
 #pragma once
 
 #include <cstdint>
@@ -126,11 +126,19 @@ struct PrecondArgs {
     int ldp;
     FitState *st;         // receives pc_ok
     double eps;           // relative diagonal regularisation of H
+    double scale;         // H is scaled by this (1 / window pixels for the preconditioner)
+    int flush;            // shared-memory batches of 32 px per float64 flush
+    int wmap_ld;
+    const float *wmap;    // nullable: per-pixel weights (valid-region coordinates, pitch
+                          // wmap_ld) instead of mask / variance
+    double *F_out;        // nullable: n x n float64 copy of H (before factorisation)
+    double *cov_out;      // nullable: n x n float64 H^-1 (then P is not written)
 };
 
 constexpr int kPcB = 32;    // block size of the factorisation
 constexpr int kGnT = 64;    // block size of the Hessian sum
 constexpr int kGnChunk = 16384;   // pixels per chunk of the Hessian sum
+constexpr int kGnFlushPc = 16;    // 32-px batches per float64 flush for the preconditioner
 __host__ __device__ inline int pc_np(int n) { return (n + kGnT - 1) / kGnT * kGnT; }
 __host__ __device__ inline int pc_ldp(int n) { return (n + 3) & ~3; }
 __host__ __device__ inline int gn_tiles(int n) { return (n + kGnT - 1) / kGnT; }
@@ -158,6 +166,12 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
                            cudaStream_t s);
 int precond_launches(int max_m);   // kernels one launch_precond call enqueues
+// Observed Fisher information (dia_fisher.cu): w[p] <- d2l/dM2 at M = I - D for
+// the valid pixels (D = the difference image held in w on entry; 0 where masked)
+cudaError_t launch_fisher_weights(const EvalArgs &ea, float *w, unsigned long long *count,
+                                  cudaStream_t s);
+// res[0] = log det H, res[1] = smallest pivot of its Cholesky factor (squared)
+cudaError_t launch_fisher_finish(const double *A64, int n, int np, double *res, cudaStream_t s);
 void precond_window(int H, int W, int m, bool single, int *y0, int *y1, int *x0, int *x1,
                     int *chunks);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)

@@ -51,7 +51,6 @@ __device__ __forceinline__ float pc_weight(const PrecondArgs &a, size_t q) {
 
 constexpr int kGnThreads = 256;
 constexpr int kGnKB = 32;          // pixels per shared-memory batch
-constexpr int kGnFlush = 16;       // batches per float64 flush (512 pixels)
 
 __host__ __device__ inline long long window_px(const PrecondArgs &a) {
     return (long long)(a.y1 - a.y0) * (a.x1 - a.x0);
@@ -110,7 +109,8 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
                 if (k < k1) {
                     const int py = a.y0 + (int)(k / wx), px = a.x0 + (int)(k % wx);
                     sBase[tid] = (long long)py * ld + px;
-                    sW[tid] = pc_weight(a, (size_t)(py + h) * ld + (px + h));
+                    sW[tid] = a.wmap ? a.wmap[(size_t)py * a.wmap_ld + px]
+                                     : pc_weight(a, (size_t)(py + h) * ld + (px + h));
                 } else {
                     sBase[tid] = -1;
                     sW[tid] = 0.f;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
             }
-            if (++nb == kGnFlush) {
+            if (++nb == a.flush) {
                 nb = 0;
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
                     }
             }
         }
-        const double inv = 1.0 / (double)npx;
+        const double inv = a.scale;
         const int np = pc_np(n);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -181,19 +181,22 @@ __global__ void fill_kernel(const PrecondArgs *pas, int npairs) {
         const PrecondArgs &a = pas[p];
         const int n = a.m * a.m + 1, np = pc_np(n), nt = gn_tiles(n), nblk = gn_blocks(n);
         const int nch = a.gn_chunks;
-        const double inv = 1.0 / (double)window_px(a);
+        const double inv = a.scale;
         for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)np * np;
              e += (long long)gridDim.x * blockDim.x) {
             const int u = (int)(e / np), w = (int)(e % np);
-            const int Tu = u / kGnT, Tw = w / kGnT;
+            // every entry from the upper one (a, b), a <= b, so that H is exactly
+            // symmetric (the two triangles of a diagonal block are rounded differently)
+            const int ea = min(u, w), eb = max(u, w);
             a.X64[e] = 0.0;
             if (nch == 1) {
-                if (Tu > Tw) a.A64[e] = a.A64[(size_t)w * np + u];
+                const double t = a.A64[(size_t)ea * np + eb];
+                if (u > w) a.A64[e] = t;
+                if (a.F_out && u < n && w < n) a.F_out[(size_t)u * n + w] = t;
                 continue;
             }
-            // block (min, max) of the upper triangle and the entry within it
-            const int U = min(Tu, Tw), V = max(Tu, Tw);
-            const int il = (Tu <= Tw ? u : w) - U * kGnT, jl = (Tu <= Tw ? w : u) - V * kGnT;
+            const int U = ea / kGnT, V = eb / kGnT;
+            const int il = ea - U * kGnT, jl = eb - V * kGnT;
             const int b = U * nt - U * (U - 1) / 2 + (V - U);
             double t;
             if (u >= n || w >= n) {
@@ -203,13 +206,15 @@ __global__ void fill_kernel(const PrecondArgs *pas, int npairs) {
                 for (int c = 0; c < nch; ++c)
                     s += a.part[((size_t)c * nblk + b) * (kGnT * kGnT) + il * kGnT + jl];
                 t = s * inv * ((u == w) ? 1.0 + a.eps : 1.0);
+                if (a.F_out) a.F_out[(size_t)u * n + w] = t;
             }
             a.A64[e] = t;
         }
         // P, including the pitch padding that P v reads (times zero)
-        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * a.ldp;
-             e += (long long)gridDim.x * blockDim.x)
-            a.P[e] = 0.f;
+        if (a.P)
+            for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+                 e < (long long)n * a.ldp; e += (long long)gridDim.x * blockDim.x)
+                a.P[e] = 0.f;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.st->pc_ok = 1;
     }
 }
@@ -358,8 +363,13 @@ __global__ void __launch_bounds__(1024) gram_kernel(const PrecondArgs *pas, int 
         }
         const int r = I * kB + ty, c = J * kB + tx;
         if (r < n && c < n) {
-            a.P[(size_t)r * a.ldp + c] = (float)s;
-            a.P[(size_t)c * a.ldp + r] = (float)s;
+            if (a.cov_out) {
+                a.cov_out[(size_t)r * n + c] = s;
+                a.cov_out[(size_t)c * n + r] = s;
+            } else if (a.P) {
+                a.P[(size_t)r * a.ldp + c] = (float)s;
+                a.P[(size_t)c * a.ldp + r] = (float)s;
+            }
         }
     }
 }
@@ -447,7 +457,7 @@ cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, i
         const PrecondArgs &a = h_pas[i];
         const int n = a.m * a.m + 1;
         if (n > kPcMaxN || a.x1 <= a.x0 || a.y1 <= a.y0 || a.ldp < n || (a.ldp & 3) != 0 ||
-            a.gn_chunks < 1 || (a.gn_chunks > 1 && !a.part) ||
+            a.gn_chunks < 1 || (a.gn_chunks > 1 && !a.part) || a.flush < 1 ||
             (long long)a.gn_chunks > window_px(a))
             return cudaErrorInvalidValue;
         max_m = max(max_m, a.m);

@@ -53,6 +53,15 @@ class Opts(ctypes.Structure):
                 ("stall_iters_diag", ctypes.c_int32), ("max_ls_evals", ctypes.c_int32)]
 
 
+class FisherInfo(ctypes.Structure):
+    _fields_ = [("positive_definite", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("log_det", ctypes.c_double), ("min_pivot", ctypes.c_double),
+                ("ndata", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class FitInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("adam_iters", ctypes.c_int32),
                 ("lbfgs_iters", ctypes.c_int32), ("evals", ctypes.c_int32),
@@ -87,6 +96,10 @@ _SIGS = {
                                                ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p]),
     "dia_batch_workspace_size": (ctypes.c_size_t, [_P(Pair), ctypes.c_int32, _P(Opts)]),
+    "dia_fisher_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 4),
+    "dia_fisher": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, _P(FisherInfo), ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p]),
     "dia_fit_batch": (ctypes.c_int32, [_P(Pair), ctypes.c_int32, _P(LossSpec), _P(Opts),
                                        ctypes.c_void_p, ctypes.c_void_p, _P(FitInfo),
                                        ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -238,6 +251,30 @@ def loss_grad(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, ws
                            _ptr(grad), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "dia_loss_grad")
     return loss, grad
+
+
+def fisher(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, want_F=True,
+           want_cov=True, stream=None):
+    """dia_fisher: observed Fisher information F (the Hessian of the loss at
+    theta, Sec. 2.5) and the covariance estimate F^-1.  Returns dict(F, cov,
+    info) with n x n float64 device tensors (None where not asked for; cov is
+    NaN when F is not positive definite)."""
+    pair, keep = make_pair(R, I, m, mask, var, flat)
+    if not R.is_cuda:
+        raise ValueError("fisher takes device tensors")
+    n = m * m + 1
+    theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
+    nb = lib.dia_fisher_workspace_size(R.shape[0], R.shape[1], R.stride(0), m)
+    if nb == 0:
+        raise DiaError(DIA_ERR_ARG, "dia_fisher_workspace_size")
+    ws = torch.empty(nb, dtype=torch.uint8, device=R.device)
+    F = torch.empty((n, n), dtype=torch.float64, device=R.device) if want_F else None
+    cov = torch.empty((n, n), dtype=torch.float64, device=R.device) if want_cov else None
+    info = FisherInfo()
+    st = lib.dia_fisher(ctypes.byref(pair), ctypes.byref(spec), _ptr(theta), _ptr(F), _ptr(cov),
+                        ctypes.byref(info), _ptr(ws), nb, _stream(stream))
+    _check(st, "dia_fisher")
+    return {"F": F, "cov": cov, "info": info.as_dict()}
 
 
 def loss_grad_noalloc(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None,

@@ -10,7 +10,7 @@ independent image pairs):
 * one large image (not run on a GPU here: every call has one GPU): the valid
   region splits into row bands, each band holding its rows plus the (m - 1)
   reference rows below them that its pixels read; the loss and gradient are
-  sums over pixels (Eq. 7), so the bands' partial sums add up to the whole,
+  sums over pixels (Eq. 8), so the bands' partial sums add up to the whole,
   and an evaluation would need one all-reduce of m^2 + 5 float64 values.
 
 Everything here runs with the gloo backend on CPU as well as with NCCL.

@@ -4,16 +4,16 @@ This module renders inputs only: star fields with pixel-integrated Gaussian
 PSFs, sky, Poisson and read noise, masks and outliers.  It contains none of the
 fit's arithmetic (no convolution with a kernel, no loss): the target is rendered
 directly with the PSF width phi_I^2 = phi_R^2 + phi_K^2 that a Gaussian kernel of
-width phi_K produces (Sec. 3.1 step viii, Eq. 15), its stars scaled by the
+width phi_K produces (Sec. 3.1 step viii, Eq. 24), its stars scaled by the
 photometric factor P and its sky set to P*S_R + B0.
 
 The recipe follows the paper's simulated-image procedure (Sec. 3.1): uniform
 sub-pixel star positions, a symmetric Gaussian PSF, a constant sky, a reference
-with 10x less pixel variance than the target (Eq. 12-13), and a target with
-variance sigma0^2 + I/G (Eq. 16-17).  The named workloads below set the
+with 10x less pixel variance than the target (Eq. 22-23), and a target with
+variance sigma0^2 + I/G (Eq. 25-26).  The named workloads below set the
 parameters (image side, star count, flux law, PSF widths, kernel side, loss).
 The reference handed to the fit is background-subtracted by its median, as the
-paper always does (Sec. 2.8).
+paper always does (Sec. 2.9).
 """
 from __future__ import annotations
 
@@ -58,7 +58,7 @@ def render_stars(shape, xs, ys, fluxes, sigma, chunk: int = 20000) -> np.ndarray
 
 def add_noise(img, rng, gain: float, read: float, var_scale: float = 1.0) -> np.ndarray:
     """Poisson photon noise at gain G (e-/ADU) plus Gaussian read noise, with the
-    total variance scaled by `var_scale` (0.1 for the stacked reference, Eq. 12)."""
+    total variance scaled by `var_scale` (0.1 for the stacked reference, Eq. 22)."""
     if var_scale == 1.0:
         e = rng.poisson(np.maximum(img, 0.0) * gain).astype(np.float64) / gain
         return e + rng.normal(0.0, read, img.shape)
@@ -82,7 +82,7 @@ class PairSpec:
     shift: tuple = (0.0, 0.0)        # sub-pixel shift of the target (dx, dy)
     gain: float = 1.0
     read: float = 5.0
-    ref_noise: bool = True           # reference with 10x less variance (Eq. 12-13)
+    ref_noise: bool = True           # reference with 10x less variance (Eq. 22-23)
     mask_frac: float = 0.0           # Bernoulli fraction of bad (masked) pixels
     cosmic_frac: float = 0.0         # unmasked outliers, +U(1e3, 1e4)
     loss: dict = field(default_factory=dict)

@@ -29,7 +29,7 @@ def field(H, W, m, seed, n_per_px=0.002, sky=100.0, sigma_k=1.2, scale=1.1, b0=3
 
 
 def theta_start(m, I, rng=None, jitter=0.0):
-    """Box-car start (Sec. 2.8) with B0 = median(I); optional positive jitter
+    """Box-car start (Sec. 2.9) with B0 = median(I); optional positive jitter
     so that the point is generic."""
     th = np.full(m * m + 1, 1.0 / (m * m))
     if rng is not None and jitter:

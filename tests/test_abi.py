@@ -42,10 +42,10 @@ def test_status_strings_and_version(native):
 
 def test_default_opts_are_the_paper_values(native):
     o = native.default_opts()
-    assert o.lr_kernel == 1e-3            # Sec. 2.8
-    assert o.switch_tol == 1e-6           # Sec. 2.8
+    assert o.lr_kernel == 1e-3            # Sec. 2.9
+    assert o.switch_tol == 1e-6           # Sec. 2.9
     assert o.clip_kappa == 5.0            # Sec. 4.2
-    assert o.grad_tol == 1e-7             # Sec. 2.8
+    assert o.grad_tol == 1e-7             # Sec. 2.9
     # preconditioned L-BFGS settings (not in the paper; chosen by measurement)
     assert (o.precond, o.history, o.stall_iters, o.stall_iters_diag, o.max_ls_evals) == \
         (1, 20, 30, 1000, 12)

@@ -1,6 +1,6 @@
 """Multi-process host logic on CPU (gloo, world size 2): the row-band split of
 one image (its partial sums add up to the whole-image loss and gradient of
-the FP64 oracle, Eq. 7 being a sum over pixels), the cost-balanced split of
+the FP64 oracle, Eq. 8 being a sum over pixels), the cost-balanced split of
 a batch, and the max-over-ranks timing reduction of the benchmark."""
 import os
 import socket

@@ -81,7 +81,7 @@ def test_gauss_fixed_loss_is_gaussian_nll_minus_constants():
     w = _valid(mask, m) != 0
     sd = np.sqrt(_valid(var, m))
     nll = -stats.norm.logpdf(_valid(I, m), loc=M, scale=sd)
-    # Eq. 1 minus the sigma-only constants: 1/2 chi^2 over the unmasked pixels
+    # Eq. 4 minus the sigma-only constants: 1/2 chi^2 over the unmasked pixels
     ref = np.sum((nll - np.log(sd) - 0.5 * math.log(2 * math.pi))[w])
     assert L == pytest.approx(ref, rel=1e-12)
 
@@ -97,9 +97,9 @@ def test_model_dependent_nll_is_gaussian_logpdf(noise):
     M = _scipy_model(R, th, m)
     F = _valid(flat, m)
     if noise == "ccd":
-        v = 16.0 / F ** 2 + M / (1.7 * F)          # Eq. 5
+        v = 16.0 / F ** 2 + M / (1.7 * F)          # Eq. 6
     else:
-        v = 2.0 * M / (1.7 * F)                     # Eq. 6
+        v = 2.0 * M / (1.7 * F)                     # Eq. 7
     ref = -np.sum(stats.norm.logpdf(_valid(I, m), loc=M, scale=np.sqrt(v)))
     ref -= M.size * 0.5 * math.log(2 * math.pi)
     assert L == pytest.approx(ref, rel=1e-12)
@@ -115,7 +115,7 @@ def test_huber_loss_matches_scipy_huber():
     v = 9.0 + M / 2.0
     z = (_valid(I, m) - M) / np.sqrt(v)
     assert np.any(np.abs(z) > c) and np.any(np.abs(z) < c)
-    ref = np.sum(special.huber(c, z)) + np.sum(0.5 * np.log(v))   # Eq. 11 without Q
+    ref = np.sum(special.huber(c, z)) + np.sum(0.5 * np.log(v))   # Eq. 13 without Q
     assert L == pytest.approx(ref, rel=1e-12)
 
 
@@ -354,11 +354,11 @@ def test_mfv_of_weighted_fit_matches_paper_b08_value():
                            flux_law="paper")
         d = synth.make_pair(p, seed)
         I_nl = d["I_noiseless"].astype(np.float64)
-        var = 25.0 + I_nl                      # Eq. 16, the true pixel variance
+        var = 25.0 + I_nl                      # Eq. 25, the true pixel variance
         th = oracle.normal_solve(d["R"], d["I"], 19, var=var)
         eps = oracle.diff_image(d["R"], d["I"], 19, th) / np.sqrt(_valid(var, 19))
         assert eps.size == GOLD["ndata_142_m19"]["value"]
-        vals.append(np.var(eps, ddof=1))        # MFV (Eq. 20)
+        vals.append(np.var(eps, ddof=1))        # MFV (Eq. 30)
     med = float(np.median(vals))
     assert gold["median"] - 3 * (gold["median"] - gold["p16"]) < med < \
         gold["median"] + 3 * (gold["p84"] - gold["median"])
