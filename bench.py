@@ -124,14 +124,22 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def kernel_source_sha():
+    """Hash of the fused kernel's source and of its m = 25 tile variants."""
+    h = hashlib.sha256()
+    for f in ("dia_eval.cuh", "dia_eval_m25.cu"):
+        with open(os.path.join(ROOT, "paper_2104_13715_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_record():
     """DRAM bytes per launch of the fused kernel from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "fused_eval_m25_4096.md")
-    src = os.path.join(ROOT, "paper_2104_13715_gb300", "csrc", "dia_eval.cuh")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha()
     rec = {}
     for line in open(path):
         if ":" in line and line.strip().startswith("- "):

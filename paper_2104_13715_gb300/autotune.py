@@ -6,6 +6,7 @@ fastest for that kernel side; results are cached in a JSON file keyed by GPU
 name, kernel side and image size, so later runs skip the timing."""
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 import threading
@@ -20,7 +21,11 @@ _lock = threading.Lock()
 
 
 def _key(m, H, W, dev):
-    return f"{torch.cuda.get_device_name(dev)}|m={m}|{H}x{W}"
+    # the variant table's shapes are part of the key: a rebuilt library with a
+    # different table must not reuse indices tuned for the old one
+    table = [tuple(nat.kernel_variant_desc(m, v).values()) for v in range(nat.kernel_variants(m))]
+    sig = hashlib.sha256(repr(table).encode()).hexdigest()[:12]
+    return f"{torch.cuda.get_device_name(dev)}|m={m}|{H}x{W}|{sig}"
 
 
 def _load():

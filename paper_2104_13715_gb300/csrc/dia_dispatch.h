@@ -9,7 +9,7 @@ namespace dia {
 constexpr int kMaxKernelSide = 31;
 
 struct KernelInfo {
-    int mk, variant, nw, qf, minb, th, nt, smem, np, kp;
+    int mk, variant, nw, qf, minb, th, nt, smem, np, kp, f2;
     const void *fn[2];   // [kModeGrad], [kModeForward]
 };
 

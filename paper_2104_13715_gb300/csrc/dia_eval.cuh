@@ -239,7 +239,7 @@ __device__ __forceinline__ int halving_index(int lane, int j) {
 // SPLIT selects how the backward's kernel rows are shared among the warps:
 // 0 = whole rows, ceil(MK/NW) or floor(MK/NW) per warp; 1 = MK = NW*KF + RM
 // with KF whole rows per warp and the RM last rows split by tile-row slices.
-template <int MK, int NW, int QF, int SPLIT>
+template <int MK, int NW, int QF, int SPLIT, int F2 = 0>
 struct EvalShape {
     static constexpr int TH = NW * QF;
     static constexpr int RROWS = TH + MK - 1;
@@ -272,7 +272,10 @@ struct EvalShape {
     static constexpr int NK = QB * MK;
     static constexpr int OFF_KS = OFF_D + SZ_D;
     static constexpr int SZ_KS = NW * 2 * NK * 4;
-    static constexpr int SMEM = OFF_KS + SZ_KS;
+    // F2: float2 pairs (K[a][b], K[a-1][b]) for the paired forward
+    static constexpr int OFF_K2 = (OFF_KS + SZ_KS + 15) & ~15;
+    static constexpr int SZ_K2 = (F2 & 1) ? MK * KP * 8 : 0;
+    static constexpr int SMEM = OFF_K2 + SZ_K2;
 };
 
 // Backward rows: dk[OFF+qb][b] += sum_rr sum_p g[y][x+p] R[r0+rr][x+b+p] with
@@ -335,14 +338,69 @@ __device__ __forceinline__ void bwd_rows(const float *rrow, const float *g0, con
     }
 }
 
+// Paired backward (F2): whole kernel rows 2j and 2j+1 of this warp share one
+// packed FMA, dkp[j * MK + b] = (dk[2j][b], dk[2j+1][b]) += (g[y][x+p],
+// g[y-1][x+p]) * R[r0+rr][x+b+p] with y = rr - 2j.  Same FMA order per
+// accumulator as bwd_row.
+template <int MK, int NP2, int RWIN>
+__device__ __forceinline__ void bwd_row2(const float (&win)[RWIN], const float *g0, int rr,
+                                         float2 (&dkp)[NP2 * MK]) {
+    float4 ga[NP2], gb[NP2];
+#pragma unroll
+    for (int j = 0; j < NP2; ++j) {
+        ga[j] = *reinterpret_cast<const float4 *>(g0 + (rr - 2 * j) * kTW);
+        gb[j] = *reinterpret_cast<const float4 *>(g0 + (rr - 2 * j - 1) * kTW);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+#pragma unroll
+        for (int j = 0; j < NP2; ++j) {
+            const float2 gv = p == 0 ? make_float2(ga[j].x, gb[j].x)
+                            : p == 1 ? make_float2(ga[j].y, gb[j].y)
+                            : p == 2 ? make_float2(ga[j].z, gb[j].z)
+                                     : make_float2(ga[j].w, gb[j].w);
+#pragma unroll
+            for (int b = 0; b < MK; ++b)
+                dkp[j * MK + b] = __ffma2_rn(gv, make_float2(win[b + p], win[b + p]), dkp[j * MK + b]);
+        }
+    }
+}
+
+template <int MK, int NP2, int RP, int RWIN, int PF>
+__device__ __forceinline__ void bwd_rows2(const float *rrow, const float *g0, int n_rr,
+                                          float2 (&dkp)[NP2 * MK]) {
+    if (PF) {
+        float wa[RWIN], wb[RWIN];
+        load_win<RWIN>(wa, rrow);
+#pragma unroll 1
+        for (int rr = 0; rr < n_rr; rr += 2) {
+            const bool two = rr + 1 < n_rr;
+            if (two) load_win<RWIN>(wb, rrow + (rr + 1) * RP);
+            bwd_row2<MK, NP2, RWIN>(wa, g0, rr, dkp);
+            if (two) {
+                if (rr + 2 < n_rr) load_win<RWIN>(wa, rrow + (rr + 2) * RP);
+                bwd_row2<MK, NP2, RWIN>(wb, g0, rr + 1, dkp);
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int rr = 0; rr < n_rr; ++rr) {
+            float win[RWIN];
+            load_win<RWIN>(win, rrow + rr * RP);
+            bwd_row2<MK, NP2, RWIN>(win, g0, rr, dkp);
+        }
+    }
+}
+
 // The fused pass over tiles t_begin, t_begin + t_step, ... < t_end of one
 // pair; the CTA's partial sums (m*m + 5 float64) go to `out`.  Called by
 // the single-pair kernel (tiles strided over the grid) and by the batched
 // kernel (a contiguous tile range of one pair per work item).
-template <int MK, int NW, int QF, int PF, int SPLIT, int MODE>
+template <int MK, int NW, int QF, int PF, int SPLIT, int MODE, int F2 = 0>
 __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned char *smem, int t_begin,
                                               int t_end, int t_step, double *out) {
-    using S = EvalShape<MK, NW, QF, SPLIT>;
+    using S = EvalShape<MK, NW, QF, SPLIT, F2>;
+    static_assert(!(F2 & 1) || QF % 2 == 0, "the paired forward pairs output rows");
     constexpr int TH = S::TH, RP = S::RP, RWIN = S::RWIN, KP = S::KP, QB = S::QB;
     constexpr int H2 = MK / 2;
 
@@ -356,6 +414,13 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int i = tid; i < MK * KP + 4; i += S::NT) Ks[i] = args.Kpad[i];
+    float2 *K2 = reinterpret_cast<float2 *>(smem + S::OFF_K2);   // F2 only
+    if constexpr ((F2 & 1) != 0) {
+        for (int i = tid; i < MK * KP; i += S::NT) {
+            const int a = i / KP;
+            K2[i] = make_float2(args.Kpad[i], a > 0 ? args.Kpad[i - KP] : 0.f);
+        }
+    }
     if (MODE == kModeGrad) {
         for (int i = tid; i < 5 * NW; i += S::NT) acc64[i] = 0.0;
         for (int i = tid; i < NW * 2 * S::NK; i += S::NT) kahan[i] = 0.f;
@@ -451,7 +516,49 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
                 }
             }
         };
-        if (PF) {
+        if constexpr ((F2 & 1) != 0) {
+            // output rows paired (2i, 2i+1): kernel rows a = r - 2i and a - 1 in one
+            // packed FMA per column b, the R value broadcast to both halves
+            float2 accp[QF / 2][4];
+#pragma unroll
+            for (int i = 0; i < QF / 2; ++i)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) accp[i][p] = make_float2(0.f, 0.f);
+            const float4 *K24 = reinterpret_cast<const float4 *>(K2);
+#pragma unroll 1
+            for (int r = QF - 1; r <= MK - 1; ++r) {
+                float win[RWIN];
+                load_win<RWIN>(win, rbase + r * RP);
+#pragma unroll
+                for (int b2 = 0; b2 < KP / 2; ++b2) {
+                    float4 kk[QF / 2];
+#pragma unroll
+                    for (int i = 0; i < QF / 2; ++i) kk[i] = K24[((r - 2 * i) * KP) / 2 + b2];
+#pragma unroll
+                    for (int bb = 0; bb < 2; ++bb) {
+                        const int b = 2 * b2 + bb;
+                        if (b < MK) {
+#pragma unroll
+                            for (int i = 0; i < QF / 2; ++i) {
+                                const float2 kv = bb == 0 ? make_float2(kk[i].x, kk[i].y)
+                                                          : make_float2(kk[i].z, kk[i].w);
+#pragma unroll
+                                for (int p = 0; p < 4; ++p)
+                                    accp[i][p] = __ffma2_rn(kv, make_float2(win[p + b], win[p + b]),
+                                                            accp[i][p]);
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < QF / 2; ++i)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    acc[2 * i][p] = accp[i][p].x;
+                    acc[2 * i + 1][p] = accp[i][p].y;
+                }
+        } else if constexpr (PF != 0) {
             // the next row's window is loaded while the current one is used
             float wa[RWIN], wb[RWIN];
             if (QF - 1 <= MK - 1) load_win<RWIN>(wa, rbase + (QF - 1) * RP);
@@ -559,7 +666,27 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
 #pragma unroll
         for (int i = 0; i < NK; ++i) dk[i] = 0.f;
         const float *gzero = gs + 4 * lane;   // a zero row above the g tile
-        if (KF > 0 && nq == KF)
+        bool whole_done = false;
+        if constexpr ((F2 & 2) != 0 && KF > 0 && KF % 2 == 0) {
+          if (nq == KF) {
+            whole_done = true;
+            constexpr int NP2 = KF / 2;
+            float2 dkp[NP2 * MK];
+#pragma unroll
+            for (int i = 0; i < NP2 * MK; ++i) dkp[i] = make_float2(0.f, 0.f);
+            bwd_rows2<MK, NP2, RP, RWIN, PF>(Rs + a_lo * RP + 4 * lane, gt + 4 * lane, TH + KF - 1,
+                                             dkp);
+#pragma unroll
+            for (int j = 0; j < NP2; ++j)
+#pragma unroll
+                for (int b = 0; b < MK; ++b) {
+                    dk[(2 * j) * MK + b] = dkp[j * MK + b].x;
+                    dk[(2 * j + 1) * MK + b] = dkp[j * MK + b].y;
+                }
+          }
+        }
+        if (whole_done) {
+        } else if (KF > 0 && nq == KF)
             bwd_rows<MK, QB, 0, (KF > 0 ? KF : 1), RP, RWIN, false, TH, PF>(
                 Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 1, dk);
         else if (KF > 1 && nq == KF - 1)   // SPLIT 0: the warps with one row fewer
@@ -634,13 +761,13 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     }
 }
 
-template <int MK, int NW, int QF, int PF, int SPLIT, int MODE>
+template <int MK, int NW, int QF, int PF, int SPLIT, int MODE, int F2 = 0>
 __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
     if (args.done_flag != nullptr && *((volatile const int *)args.done_flag) != 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    process_tiles<MK, NW, QF, PF, SPLIT, MODE>(
+    process_tiles<MK, NW, QF, PF, SPLIT, MODE, F2>(
         args, smem, blockIdx.x, args.n_tiles, gridDim.x,
-        MODE == kModeGrad ? args.partials + (size_t)blockIdx.x * EvalShape<MK, NW, QF, SPLIT>::NP
+        MODE == kModeGrad ? args.partials + (size_t)blockIdx.x * EvalShape<MK, NW, QF, SPLIT, F2>::NP
                           : nullptr);
 }
 

@@ -1,5 +1,5 @@
 // Fused evaluation kernels for kernel sides [31] (generated by gen_instances.py)
 #include "dia_eval_inst.cuh"
 
-DIA_EVAL_INST(31, 0, 8, 4, 0, 0)
-DIA_EVAL_INST(31, 1, 8, 4, 1, 0)
+DIA_EVAL_INST(31, 0, 8, 4, 0, 0, 0)
+DIA_EVAL_INST(31, 1, 8, 4, 1, 0, 0)

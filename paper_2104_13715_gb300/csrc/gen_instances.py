@@ -7,20 +7,23 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel side -> list of tile variants (NW warps, QF output rows per warp in the
 # forward pass, PF = 1 to load the next R-row window while the current one is used,
 # SPLIT = backward row split: 0 whole rows ceil/floor per warp, 1 equal work
-# with the MK % NW last rows split by tile-row slices).
+# with the MK % NW last rows split by tile-row slices, F2 = packed float2 FMAs:
+# bit 0 pairs output rows in the forward, bit 1 pairs kernel rows in the
+# backward when a warp owns an even number of whole rows; 0 if omitted).
 # Variant 0 is the default; the autotuner may pick another at run time.
 VARIANTS = {
     1: [(8, 8, 0, 0)], 3: [(8, 8, 0, 0)], 5: [(8, 8, 0, 0)],
-    7: [(8, 4, 0, 0), (8, 8, 0, 0)],
-    9: [(8, 4, 0, 1), (8, 8, 0, 1)],
-    11: [(8, 4, 1, 1), (8, 4, 0, 1), (12, 4, 0, 0)],
-    13: [(12, 4, 1, 1), (12, 4, 0, 1), (13, 4, 0, 0)],
-    15: [(12, 4, 1, 1), (12, 4, 0, 1)],
-    17: [(8, 4, 0, 1), (8, 4, 1, 1)],
-    19: [(8, 4, 1, 1), (8, 4, 0, 1), (10, 4, 0, 0)],
-    21: [(8, 4, 0, 0), (8, 4, 1, 0), (7, 4, 0, 0)],
-    23: [(8, 4, 0, 0), (8, 4, 1, 0)],
-    25: [(12, 4, 0, 1), (12, 4, 1, 1), (13, 4, 0, 0), (12, 2, 0, 1)],
+    7: [(8, 4, 0, 0), (8, 8, 0, 0), (8, 4, 0, 0, 1)],
+    9: [(8, 4, 0, 1), (8, 8, 0, 1), (8, 4, 0, 1, 1)],
+    11: [(8, 4, 0, 1, 1), (8, 4, 1, 1), (8, 4, 0, 1), (12, 4, 0, 0)],
+    13: [(12, 4, 1, 1), (12, 4, 0, 1), (13, 4, 0, 0), (12, 4, 1, 1, 1)],
+    15: [(12, 4, 1, 1), (12, 4, 0, 1), (12, 4, 1, 1, 1)],
+    17: [(8, 4, 0, 1), (8, 4, 1, 1), (8, 4, 1, 1, 1)],
+    19: [(8, 4, 1, 1), (8, 4, 0, 1), (10, 4, 0, 0), (8, 4, 1, 1, 1), (8, 4, 0, 1, 1)],
+    21: [(8, 4, 0, 0, 1), (8, 4, 0, 0), (8, 4, 1, 0), (7, 4, 0, 0)],
+    23: [(8, 4, 0, 0), (8, 4, 1, 0), (8, 4, 1, 0, 1)],
+    25: [(12, 4, 1, 1, 1), (12, 4, 0, 1), (12, 4, 1, 1), (13, 4, 0, 0), (12, 2, 0, 1),
+         (12, 4, 0, 1, 1), (12, 4, 1, 1, 3)],
     27: [(9, 4, 0, 0), (9, 4, 1, 0)],
     29: [(10, 4, 0, 0), (10, 4, 1, 0)],
     31: [(8, 4, 0, 0), (8, 4, 1, 0)],
@@ -36,8 +39,10 @@ def main():
         lines = [f"// Fused evaluation kernels for kernel sides {grp} (generated by gen_instances.py)",
                  '#include "dia_eval_inst.cuh"', ""]
         for mk in grp:
-            for v, (nw, qf, mb, sp) in enumerate(VARIANTS[mk]):
-                lines.append(f"DIA_EVAL_INST({mk}, {v}, {nw}, {qf}, {mb}, {sp})")
+            for v, t in enumerate(VARIANTS[mk]):
+                nw, qf, mb, sp = t[:4]
+                f2 = t[4] if len(t) > 4 else 0
+                lines.append(f"DIA_EVAL_INST({mk}, {v}, {nw}, {qf}, {mb}, {sp}, {f2})")
         with open(os.path.join(HERE, f"dia_eval_m{grp[0]:02d}.cu"), "w") as fh:
             fh.write("\n".join(lines) + "\n")
     decl, cases = [], []

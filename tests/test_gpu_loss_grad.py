@@ -156,3 +156,26 @@ def test_autograd_function_central_difference(nat):
     assert fd == pytest.approx(float(g @ v), rel=1e-3)
     _, go = oracle.loss_grad(d["R"], d["I"], m, th.detach().cpu().numpy(), ospec(SPECS["gauss-ccd"]))
     assert rel_inf(g.cpu().numpy(), go) <= TOL_G
+
+
+# (scalar variant, packed-float2 variant) of the same tile shape, from the
+# VARIANTS table of paper_2104_13715_gb300/csrc/gen_instances.py
+F2_TWINS = {25: [(2, 0), (1, 5), (2, 6)], 19: [(0, 3), (1, 4)], 11: [(2, 0)], 21: [(1, 0)],
+            7: [(0, 2)], 9: [(0, 2)], 13: [(0, 3)], 15: [(0, 2)], 17: [(1, 2)], 23: [(1, 2)]}
+
+
+@pytest.mark.parametrize("m", sorted(F2_TWINS))
+def test_packed_fma_variants_are_bitwise_equal(nat, m):
+    """__ffma2_rn performs the same correctly rounded FMAs in the same order as
+    the scalar path, so the loss and gradient are identical bit for bit."""
+    d = field(150, 260, m, seed=90 + m)
+    th = theta_start(m, d["I"], np.random.default_rng(m), jitter=0.3)
+    try:
+        for a, b in F2_TWINS[m]:
+            nat.select_kernel_variant(m, a)
+            La, ga = _run(nat, d, m, th, SPECS["cauchy-emccd"])
+            nat.select_kernel_variant(m, b)
+            Lb, gb = _run(nat, d, m, th, SPECS["cauchy-emccd"])
+            assert La == Lb and np.array_equal(ga, gb), (m, a, b)
+    finally:
+        nat.select_kernel_variant(m, 0)
