@@ -606,6 +606,64 @@ def run_reference_batch(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_precision_study(args):
+    """Fifth configuration: the FP32 fused path with float64 cross-block
+    accumulation against the pure-float32 accumulation form, on the 2048^2
+    high-dynamic-range field (m = 21, CCD negative log-likelihood).  For each
+    form: fit, then K, B0 and difference-image errors against the FP64
+    oracle's Newton optimum (polished from the float64 form's theta), and the
+    gradient error at a fixed non-stationary theta."""
+    import torch
+    import oracle
+    from paper_2104_13715_gb300 import native as nat
+    name = "hdr2048_m21_nll"
+    d = synth.workload(name, seed=args.seed, size=args.size)
+    m = d["m"]
+    dev = torch.device("cuda", 0)
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    R, I = up(d["R"]), up(d["I"])
+    spec = nat.loss_spec(**_loss_kw(d))
+    ospec = _oracle_spec(d)
+    th_start = np.full(m * m + 1, 1.0 / (m * m))
+    th_start[-1] = float(np.median(d["I"]))
+    rng = np.random.default_rng(1)
+    th_start[:-1] *= 1.0 + 0.3 * rng.uniform(-1, 1, m * m)
+    _, g_or = oracle.loss_grad(d["R"], d["I"], m, th_start, ospec)
+    forms = {}
+    for mode, label in ((nat.ACCUM_FP64, "fp32_pixels_fp64_accumulation"),
+                        (nat.ACCUM_FP32, "pure_fp32_accumulation")):
+        nat.set_accumulation(mode)
+        try:
+            _, g = nat.loss_grad(R, I, m, torch.from_numpy(th_start), spec)
+            out = nat.fit(R, I, m, spec, nat.default_opts())
+        finally:
+            nat.set_accumulation(nat.ACCUM_FP64)
+        forms[label] = {"theta": out["theta"].cpu().numpy(), "diff": out["diff"].cpu().numpy(),
+                        "info": out["info"],
+                        "grad_err": float(np.max(np.abs(g.cpu().numpy() - g_or)) /
+                                          np.max(np.abs(g_or)))}
+    t0 = time.perf_counter()
+    ref = oracle.newton(d["R"], d["I"], m, forms["fp32_pixels_fp64_accumulation"]["theta"], ospec)
+    t_or = time.perf_counter() - t0
+    D_ref = oracle.diff_image(d["R"], d["I"], m, ref)
+    sky = float(np.median(d["I"]))
+    res = {}
+    for label, f in forms.items():
+        th = f["theta"]
+        res[label] = {
+            "K_err_rel_sumK": float(np.max(np.abs(th[:-1] - ref[:-1])) / abs(ref[:-1].sum())),
+            "B0_err_rel_sky": float(abs(th[-1] - ref[-1]) / sky),
+            "diff_err_rel_maxI": float(np.max(np.abs(f["diff"] - D_ref)) / np.max(np.abs(d["I"]))),
+            "grad_err_rel_at_start": f["grad_err"],
+            "evals": f["info"]["evals"], "reason": f["info"]["reason"]}
+    res["tensor_core_split_tf32_form"] = "not built (see DESIGN.md)"
+    print(json.dumps({"precision_study": name, "H": d["R"].shape[0], "W": d["R"].shape[1],
+                      "m": m, "loss": "gauss", "variance": "ccd", "results": res,
+                      "oracle": f"FP64 Newton polish from the float64-accumulation fit, "
+                                f"{t_or:.1f} s on {os.cpu_count()} host cores",
+                      "tolerances": {"K": 1e-4, "B0": 1e-4, "grad": 1e-5}}), flush=True)
+
+
 def run_kernel_only(args):
     """W + K back-to-back fused evaluations (dia_loss_grad) of the workload at
     the box-car start: the driver of the ncu captures of the fused kernel."""
@@ -665,7 +723,12 @@ def main():
                     help="time the fused loss+gradient kernel alone (ncu driver)")
     ap.add_argument("--size", type=int, default=None, help="image side override (--kernel-only)")
     ap.add_argument("--variant", type=int, default=None, help="tile variant (--kernel-only)")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="float64 vs float32 accumulation on the 2048^2 HDR field")
     args = ap.parse_args()
+    if args.precision_study:
+        run_precision_study(args)
+        return
     if args.kernel_only:
         run_kernel_only(args)
         return

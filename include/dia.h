@@ -189,6 +189,22 @@ dia_status dia_opts_default(dia_opts *opts);
  * selected one); output pointers are nullable host pointers.  Results of all
  * variants agree up to the order of float32 tile sums. */
 int32_t dia_kernel_variants(int32_t m);
+
+/* Accumulation of the per-pixel loss and gradient terms (the benchmark spec precision
+ * item; the fifth benchmark configuration compares the two forms):
+ *   DIA_ACCUM_FP64 (default) -- float32 per-lane runs of at most 4096 pixels,
+ *     Kahan-compensated float32 per tile run for dL/dK, float64 across tiles,
+ *     warps and CTAs;
+ *   DIA_ACCUM_FP32 -- float32 everywhere without compensation, a comparison
+ *     form for the precision study, not for production.
+ * Process-wide; applies to dia_loss_grad and dia_fit from the next call on
+ * (not to dia_fit_batch or dia_loss_grad_noalloc); the optimiser's own
+ * arithmetic stays float64.  Not safe to change while another host thread
+ * launches work. */
+#define DIA_ACCUM_FP64 0
+#define DIA_ACCUM_FP32 1
+dia_status dia_set_accumulation(int32_t mode);
+int32_t dia_get_accumulation(void);
 dia_status dia_select_kernel_variant(int32_t m, int32_t variant);
 dia_status dia_kernel_variant_desc(int32_t m, int32_t variant, int32_t *warps,
                                    int32_t *rows_per_warp, int32_t *tile_rows,

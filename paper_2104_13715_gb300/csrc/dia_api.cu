@@ -1,4 +1,5 @@
 // C ABI of the DIA kernel-fit library (declarations and contract in include/dia.h).
+#include <atomic>
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -20,6 +21,8 @@ using namespace dia;
 namespace {
 
 thread_local int g_last_cuda = 0;
+// accumulation form of the single-pair entries (dia_set_accumulation)
+std::atomic<int> g_accumulation{DIA_ACCUM_FP64};
 
 #define DIA_CK(expr)                               \
     do {                                           \
@@ -270,6 +273,7 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     a.partials = c.partials;
     a.clip_kappa = 5.0f;
     if (loss) a.lp = to_params(loss);
+    a.acc32 = g_accumulation.load() == DIA_ACCUM_FP32 ? 1 : 0;
     c.red = (double *)(c.ws + c.L.red);
     c.st = (FitState *)(c.ws + c.L.state);
     c.sel = (SelectState *)(c.ws + c.L.sel);
@@ -322,7 +326,7 @@ void append(std::string &k, const T &v) {
 cudaError_t enqueue_iteration(const Ctx &c, const EvalArgs &ea, const StepArgs &sa, cudaStream_t s) {
     cudaError_t e = launch_eval(c.ki, kModeGrad, ea, c.grid, s);
     if (e != cudaSuccess) return e;
-    e = launch_reduce(c.partials, c.grid, c.L.np, c.red, &c.st->done, s);
+    e = launch_reduce(c.partials, c.grid, c.L.np, c.red, &c.st->done, s, ea.acc32);
     if (e != cudaSuccess) return e;
     return launch_step(sa, s);
 }
@@ -419,6 +423,14 @@ const char *dia_status_str(int32_t s) {
 
 int32_t dia_abi_version(void) { return DIA_ABI_VERSION; }
 
+dia_status dia_set_accumulation(int32_t mode) {
+    if (mode != DIA_ACCUM_FP64 && mode != DIA_ACCUM_FP32) return DIA_ERR_ARG;
+    g_accumulation.store(mode);
+    return DIA_OK;
+}
+
+int32_t dia_get_accumulation(void) { return g_accumulation.load(); }
+
 int32_t dia_last_cuda_error(void) { return g_last_cuda; }
 
 int32_t dia_kernel_variants(int32_t m) {
@@ -472,7 +484,7 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss, const 
     if (rc != DIA_OK) return rc;
     DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.kpad, s));
     DIA_CK(launch_eval(c.ki, kModeGrad, c.ea, c.grid, s));
-    DIA_CK(launch_reduce(c.partials, c.grid, c.L.np, c.red, nullptr, s));
+    DIA_CK(launch_reduce(c.partials, c.grid, c.L.np, c.red, nullptr, s, c.ea.acc32));
     DIA_CK(launch_emit_loss_grad(c.red, pair->m, loss_out, grad_out, s));
     return DIA_OK;
 }

@@ -68,6 +68,8 @@ struct EvalArgs {
     float clip_kappa;
     const int *done_flag;  // nullable: nonzero -> return at once
     LossParams lp;
+    int acc32;             // nonzero: float32 accumulation everywhere, no compensation
+                           // (the comparison form of the precision study)
 };
 
 __host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
@@ -447,11 +449,19 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
         const float k = warp_sum(ksum), kr = warp_sum(kr2sum);
         if (lane == 0) {
             double *w5 = acc64 + 5 * warp;
-            w5[0] += (double)l;
-            w5[1] += (double)g;
-            w5[2] += (double)c;
-            w5[3] += (double)kr;
-            w5[4] += (double)k;
+            if (args.acc32) {   // float32 running sums (kept in the float64 slots)
+                w5[0] = (double)((float)w5[0] + l);
+                w5[1] = (double)((float)w5[1] + g);
+                w5[2] = (double)((float)w5[2] + c);
+                w5[3] = (double)((float)w5[3] + kr);
+                w5[4] = (double)((float)w5[4] + k);
+            } else {
+                w5[0] += (double)l;
+                w5[1] += (double)g;
+                w5[2] += (double)c;
+                w5[3] += (double)kr;
+                w5[4] += (double)k;
+            }
         }
         lsum = gsum = cnt = ksum = kr2sum = 0.f;
     };
@@ -712,10 +722,14 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
                 const int ix = kidx[j];
                 if (ix >= 0) {
                     float *sm = ksum_w + ix, *cm = ksum_w + NK + ix;
-                    const float y = w5[j] - *cm;
-                    const float t = *sm + y;
-                    *cm = (t - *sm) - y;
-                    *sm = t;
+                    if (args.acc32) {
+                        *sm += w5[j];
+                    } else {
+                        const float y = w5[j] - *cm;
+                        const float t = *sm + y;
+                        *cm = (t - *sm) - y;
+                        *sm = t;
+                    }
                 }
             }
         }
@@ -745,18 +759,25 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
                 t = (double)kw[qb * MK + b] - (double)kw[NK + qb * MK + b];
             } else {
                 const int qb = KF + (a - (MK - RM));
+                float t32 = 0.f;
                 for (int w = 0; w < NW; ++w) {
                     const float *kw = kahan + w * 2 * NK;
                     t += (double)kw[qb * MK + b] - (double)kw[NK + qb * MK + b];
+                    t32 += kw[qb * MK + b];
                 }
+                if (args.acc32) t = (double)t32;
             }
             out[1 + i] = t;
         }
         if (tid < 5) {
             // tid 0: loss, 1: dB0, 2: pixel count, 3: sum kappa R^2, 4: sum kappa
             double t = 0.0;
-            for (int w = 0; w < NW; ++w) t += acc64[5 * w + tid];
-            out[tid == 0 ? 0 : MK * MK + tid] = t;
+            float t32 = 0.f;
+            for (int w = 0; w < NW; ++w) {
+                t += acc64[5 * w + tid];
+                t32 += (float)acc64[5 * w + tid];
+            }
+            out[tid == 0 ? 0 : MK * MK + tid] = args.acc32 ? (double)t32 : t;
         }
     }
 }

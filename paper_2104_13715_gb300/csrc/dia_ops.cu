@@ -10,29 +10,39 @@ namespace dia {
 // ----------------------------------------------------------------------------
 // Float64 sum of the per-CTA partials in a fixed order (bitwise repeatable).
 // Block b handles entries [32b, 32b+32); its 8 warps take every 8th CTA row.
+// acc32: the same sums in float32 (the comparison form of the precision study).
 __global__ void __launch_bounds__(256) reduce_kernel(const double *__restrict__ partials, int G,
                                                      int NP, double *__restrict__ out,
-                                                     const int *done) {
+                                                     const int *done, int acc32) {
     if (done != nullptr && *((volatile const int *)done) != 0) return;
     __shared__ double sh[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + lane;
     double s = 0.0;
+    float s32 = 0.f;
     if (e < NP)
-        for (int g = warp; g < G; g += 8) s += partials[(size_t)g * NP + e];
-    sh[warp][lane] = s;
+        for (int g = warp; g < G; g += 8) {
+            const double v = partials[(size_t)g * NP + e];
+            s += v;
+            s32 += (float)v;
+        }
+    sh[warp][lane] = acc32 ? (double)s32 : s;
     __syncthreads();
     if (warp == 0 && e < NP) {
         double t = 0.0;
+        float t32 = 0.f;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) t += sh[w][lane];
-        out[e] = t;
+        for (int w = 0; w < 8; ++w) {
+            t += sh[w][lane];
+            t32 += (float)sh[w][lane];
+        }
+        out[e] = acc32 ? (double)t32 : t;
     }
 }
 
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
-                          cudaStream_t s) {
-    reduce_kernel<<<(NP + 31) / 32, 256, 0, s>>>(partials, G, NP, out, done);
+                          cudaStream_t s, int acc32) {
+    reduce_kernel<<<(NP + 31) / 32, 256, 0, s>>>(partials, G, NP, out, done, acc32);
     return cudaGetLastError();
 }
 

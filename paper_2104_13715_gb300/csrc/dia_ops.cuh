@@ -154,7 +154,7 @@ inline int pc_window_side(int n) {
 
 // host launchers (dia_ops.cu)
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
-                          cudaStream_t s);
+                          cudaStream_t s, int acc32 = 0);
 cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, float *Kpad, cudaStream_t s);
 cudaError_t launch_emit_loss_grad(const double *red, int mk, double *loss, double *grad,
                                   cudaStream_t s);

@@ -97,6 +97,8 @@ _SIGS = {
                                                ctypes.c_void_p]),
     "dia_batch_workspace_size": (ctypes.c_size_t, [_P(Pair), ctypes.c_int32, _P(Opts)]),
     "dia_fisher_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 4),
+    "dia_set_accumulation": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_get_accumulation": (ctypes.c_int32, []),
     "dia_fisher": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, _P(FisherInfo), ctypes.c_void_p,
                                     ctypes.c_size_t, ctypes.c_void_p]),
@@ -147,6 +149,18 @@ def _check(status, what):
 
 def status_str(s: int) -> str:
     return lib.dia_status_str(s).decode()
+
+
+ACCUM_FP64, ACCUM_FP32 = 0, 1
+
+
+def set_accumulation(mode: int) -> None:
+    """dia_set_accumulation: ACCUM_FP64 (default) or ACCUM_FP32 (comparison form)."""
+    _check(lib.dia_set_accumulation(int(mode)), "dia_set_accumulation")
+
+
+def get_accumulation() -> int:
+    return lib.dia_get_accumulation()
 
 
 def kernel_variants(m: int) -> int:
