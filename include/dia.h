@@ -161,7 +161,9 @@ typedef struct {
     double b0;                 /* fitted B0 */
     int32_t reason;            /* why the last pass stopped: 1 grad_tol, 2 rel_tol, 3 stall
                                   (precision limit), 4 line search, 5 max iterations,
-                                  6 max evaluations, 7 non-finite, 8 degenerate */
+                                  6 max evaluations, 7 non-finite, 8 degenerate, 9 a
+                                  refit reached (within 3x) the max|dL/dtheta| floor of
+                                  an earlier pass of the same fit */
     int64_t kernel_launches;   /* CUDA kernels this call launched (graph nodes included) */
     int32_t precond_used;      /* 1: L-BFGS ran with the block-Toeplitz preconditioner
                                   (asked for and factored), 0: with the diagonal one */

@@ -446,7 +446,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
                     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, evj[g], 0);
                 }
                 if (e == cudaSuccess)
-                    e = launch_step_batch(d_sa, d_red, d_parts, npairs, max_n, hdr + 4, 4, cs);
+                    e = launch_step_batch(d_sa, d_red, d_parts, npairs, hdr + 4, 4, cs);
             }
             cudaGraph_t gr = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
@@ -474,7 +474,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     long long launches = 1 + (opts.precond ? precond_launches(max_m) : 0);   // init (+ preconditioner)
     for (;;) {
         DB_CK(cudaGraphLaunch(gx, s));
-        launches += (long long)(n_groups + kStepLaunches) * opts.graph_iters;
+        launches += (long long)(n_groups + kStepLaunchesBatch) * opts.graph_iters;
         DB_CK(cudaMemcpyAsync(&done_host, hdr + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
         DB_CK(cudaStreamSynchronize(s));
         if (done_host >= npairs) break;

@@ -155,6 +155,8 @@ __device__ void finish(const StepArgs &a, int status, int reason) {
     if (threadIdx.x == 0) {
         st->status = status;
         st->reason = reason;
+        // the float32 floor of max|g| found by this pass serves the refits
+        if (reason == kStopStall || reason == kStopLineSearch) st->ginf_floor = st->ginf_best;
         st->phase = kPhaseDone;
         st->L_sum = st->L * st->ndata;
         __threadfence();
@@ -305,6 +307,15 @@ __device__ void direction_body(const StepArgs &a, StepShared &sm) {
     set_trial(a, 1.0);
 }
 
+// A refit (sigma-clip pass) is at the limit of numerical precision once max|g|
+// is within kFloorFactor of the floor an earlier pass of the same fit reached
+// (same images, same float32 arithmetic, nearly the same theta), so it need
+// not spend stall_iters evaluations finding that floor again.
+constexpr double kFloorFactor = 3.0;
+__device__ __forceinline__ bool at_floor(const FitState *st, double ginf) {
+    return st->ginf_floor > 0.0 && ginf <= kFloorFactor * st->ginf_floor;
+}
+
 // Evaluations without a halving of max|g| that end the pass: the block-
 // Toeplitz preconditioned iteration reaches its float32 floor within tens of
 // evaluations, the diagonally preconditioned one needs far more.
@@ -443,6 +454,10 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
             finish(a, 0, kStopGradTol);
             return;
         }
+        if (at_floor(st, ginf)) {
+            finish(a, 0, kStopFloor);
+            return;
+        }
         request_direction(a, -1);
         return;
     }
@@ -545,6 +560,8 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
         sm.act = kStopNone;
         if (ginf < p.grad_tol) {
             sm.finish_status = 0; sm.act = kStopGradTol;
+        } else if (at_floor(st, ginf)) {
+            sm.finish_status = 0; sm.act = kStopFloor;
         } else if (p.rel_tol > 0.0 && fabs(Lold - Lacc) < p.rel_tol * fabs(Lacc)) {
             sm.finish_status = 0; sm.act = kStopRelTol;
         } else if (st->stall >= stall_limit(a)) {
@@ -609,19 +626,22 @@ __global__ void __launch_bounds__(kStepThreads)
     step_body(a, sm);
 }
 
+// Batched direction: the CTA of pair p applies P itself (one CTA holds a
+// pair's P v easily; a grid of row blocks x pairs would mostly find nothing
+// to do), then finishes the step.
 __global__ void __launch_bounds__(kStepThreads) direction_batch_kernel(const StepArgs *args) {
     __shared__ StepShared sm;
+    __shared__ __align__(16) float ws[2 * kPaW];
     const StepArgs a = args[blockIdx.x];
+    pc_apply_body(a, 0, 1, ws);
+    __syncthreads();
     direction_body(a, sm);
 }
 
 cudaError_t launch_step_batch(const StepArgs *args, const BatchRed *red, const double *partials,
-                              int npairs, int max_n, int *queue_counters, int n_counters,
-                              cudaStream_t s) {
+                              int npairs, int *queue_counters, int n_counters, cudaStream_t s) {
     step_batch_kernel<<<npairs, kStepThreads, 0, s>>>(args, red, partials, queue_counters,
                                                       n_counters);
-    cudaError_t e = launch_pc_apply_batch(args, npairs, max_n, s);
-    if (e != cudaSuccess) return e;
     direction_batch_kernel<<<npairs, kStepThreads, 0, s>>>(args);
     return cudaGetLastError();
 }

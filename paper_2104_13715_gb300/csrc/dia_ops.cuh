@@ -20,7 +20,8 @@ enum Phase { kPhaseAdam = 0, kPhaseLbfgs = 1, kPhaseLbfgsStart = 2, kPhaseDone =
 // Why a fit pass stopped (FitState::reason, dia_fit_info::reason).
 enum StopReason {
     kStopNone = 0, kStopGradTol = 1, kStopRelTol = 2, kStopStall = 3, kStopLineSearch = 4,
-    kStopMaxIter = 5, kStopMaxEvals = 6, kStopNonfinite = 7, kStopDegenerate = 8
+    kStopMaxIter = 5, kStopMaxEvals = 6, kStopNonfinite = 7, kStopDegenerate = 8,
+    kStopFloor = 9
 };
 
 // Optimiser state, float64, resident in the caller's workspace.  The first
@@ -46,6 +47,7 @@ struct FitState {
     double lo, L_lo, gd_lo, hi, L_hi, gd_hi;  // line-search bracket (hi < 0: none yet)
     double b1t, b2t; // Adam beta powers
     double median;   // B0 initialisation
+    double ginf_floor; // best max|g| of the last pass that ended at the precision limit (0: none)
 };
 
 struct OptParams {
@@ -152,6 +154,65 @@ inline int pc_window_side(int n) {
     return s < 256.0 ? 256 : (s > 1024.0 ? 1024 : (int)s);
 }
 
+// ---------------------------------------------------------------- P v
+// For a fit with a direction pending: pg = P g, and PY[slot] = P y_new when
+// need_pc == 2.  P is applied as a dense float32 matrix (warp per row; rows
+// strided over CTAs blk of nblk), or, without the factorisation, as the
+// diagonal pdiag.  Block size kPaThreads.
+constexpr int kPaThreads = 256;
+constexpr int kPaRowsPerCta = kPaThreads / 32;
+constexpr int kPaW = (kPcMaxN + 7) & ~3;   // staged vector length (16-byte multiple)
+
+__device__ __forceinline__ void pc_apply_body(const StepArgs &a, int blk, int nblk, float *ws) {
+    const FitState *st = a.st;
+    if (*((volatile const int *)&st->done) != 0) return;
+    const int need = *((volatile const int *)&st->need_pc);
+    if (need == 0) return;
+    const OptBuffers &b = a.b;
+    const int n = a.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int slot = st->pc_slot;
+    const double *yv = need == 2 ? b.Y + (size_t)slot * n : nullptr;
+    double *pyv = need == 2 ? b.PY + (size_t)slot * n : nullptr;
+    if (!(st->pc_ok && b.P)) {
+        for (int k = blk * kPaThreads + tid; k < n; k += nblk * kPaThreads) {
+            b.pg[k] = b.pdiag[k] * b.grad[k];
+            if (yv) pyv[k] = b.pdiag[k] * yv[k];
+        }
+        return;
+    }
+    const int ldp = b.ldp;
+    float *g = ws, *y = ws + kPaW;
+    for (int k = tid; k < ldp; k += kPaThreads) {
+        g[k] = k < n ? (float)b.grad[k] : 0.f;
+        y[k] = (yv && k < n) ? (float)yv[k] : 0.f;
+    }
+    __syncthreads();
+    for (int r = blk * kPaRowsPerCta + warp; r < n; r += nblk * kPaRowsPerCta) {
+        const float4 *row = reinterpret_cast<const float4 *>(b.P + (size_t)r * ldp);
+        const float4 *g4 = reinterpret_cast<const float4 *>(g);
+        const float4 *y4 = reinterpret_cast<const float4 *>(y);
+        float s0 = 0.f, s1 = 0.f;
+        for (int k = lane; k < ldp / 4; k += 32) {
+            const float4 pv = row[k], gv = g4[k];
+            s0 = fmaf(pv.x, gv.x, fmaf(pv.y, gv.y, fmaf(pv.z, gv.z, fmaf(pv.w, gv.w, s0))));
+            if (yv) {
+                const float4 yw = y4[k];
+                s1 = fmaf(pv.x, yw.x, fmaf(pv.y, yw.y, fmaf(pv.z, yw.z, fmaf(pv.w, yw.w, s1))));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (lane == 0) {
+            b.pg[r] = (double)s0;
+            if (yv) pyv[r] = (double)s1;
+        }
+    }
+}
+
+
 // host launchers (dia_ops.cu)
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
                           cudaStream_t s, int acc32 = 0);
@@ -176,7 +237,6 @@ void precond_window(int H, int W, int m, bool single, int *y0, int *y1, int *x0,
                     int *chunks);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
-cudaError_t launch_pc_apply_batch(const StepArgs *args, int npairs, int max_n, cudaStream_t s);
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,
                         double init_sigma, const SelectState *sel, int start_phase,
                         cudaStream_t s);
@@ -187,11 +247,11 @@ cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int
                           uint32_t *hist, SelectState *sel, int grid, cudaStream_t s);
 cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, float *K_out,
                                 float *b0_out, cudaStream_t s);
-// batched: one CTA per pair for the two optimiser halves (kStepLaunches
-// kernels in all); max_n = the largest m*m + 1 of the batch
+// batched: one CTA per pair for the two optimiser halves, P v inside the
+// second (kStepLaunchesBatch kernels)
+constexpr int kStepLaunchesBatch = 2;
 cudaError_t launch_step_batch(const StepArgs *args, const BatchRed *red, const double *partials,
-                              int npairs, int max_n, int *queue_counters, int n_counters,
-                              cudaStream_t s);
+                              int npairs, int *queue_counters, int n_counters, cudaStream_t s);
 cudaError_t launch_init_batch(const StepArgs *args, const EvalArgs *eas, int npairs,
                               int init_mode, double init_sigma, int start_phase, cudaStream_t s);
 cudaError_t launch_pack_batch(const StepArgs *args, const long long *theta_off, double *theta_out,

@@ -378,73 +378,9 @@ __global__ void __launch_bounds__(1024) gram_kernel(const PrecondArgs *pas, int 
 // For a fit with a direction pending: pg = P g, and PY[slot] = P y_new when
 // need_pc == 2.  P is applied as a dense float32 matrix (warp per row, rows
 // over the CTAs), or, without the factorisation, as the diagonal pdiag.
-constexpr int kPaThreads = 256;
-constexpr int kPaRowsPerCta = kPaThreads / 32;
-constexpr int kPaW = (kPcMaxN + 7) & ~3;   // staged vector length (16-byte multiple)
-
-__device__ void pc_apply_body(const StepArgs &a, int blk, int nblk, float *ws) {
-    const FitState *st = a.st;
-    if (*((volatile const int *)&st->done) != 0) return;
-    const int need = *((volatile const int *)&st->need_pc);
-    if (need == 0) return;
-    const OptBuffers &b = a.b;
-    const int n = a.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int slot = st->pc_slot;
-    const double *yv = need == 2 ? b.Y + (size_t)slot * n : nullptr;
-    double *pyv = need == 2 ? b.PY + (size_t)slot * n : nullptr;
-    if (!(st->pc_ok && b.P)) {
-        for (int k = blk * kPaThreads + tid; k < n; k += nblk * kPaThreads) {
-            b.pg[k] = b.pdiag[k] * b.grad[k];
-            if (yv) pyv[k] = b.pdiag[k] * yv[k];
-        }
-        return;
-    }
-    const int ldp = b.ldp;
-    float *g = ws, *y = ws + kPaW;
-    for (int k = tid; k < ldp; k += kPaThreads) {
-        g[k] = k < n ? (float)b.grad[k] : 0.f;
-        y[k] = (yv && k < n) ? (float)yv[k] : 0.f;
-    }
-    __syncthreads();
-    for (int r = blk * kPaRowsPerCta + warp; r < n; r += nblk * kPaRowsPerCta) {
-        const float4 *row = reinterpret_cast<const float4 *>(b.P + (size_t)r * ldp);
-        const float4 *g4 = reinterpret_cast<const float4 *>(g);
-        const float4 *y4 = reinterpret_cast<const float4 *>(y);
-        float s0 = 0.f, s1 = 0.f;
-        for (int k = lane; k < ldp / 4; k += 32) {
-            const float4 pv = row[k], gv = g4[k];
-            s0 = fmaf(pv.x, gv.x, fmaf(pv.y, gv.y, fmaf(pv.z, gv.z, fmaf(pv.w, gv.w, s0))));
-            if (yv) {
-                const float4 yw = y4[k];
-                s1 = fmaf(pv.x, yw.x, fmaf(pv.y, yw.y, fmaf(pv.z, yw.z, fmaf(pv.w, yw.w, s1))));
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        }
-        if (lane == 0) {
-            b.pg[r] = (double)s0;
-            if (yv) pyv[r] = (double)s1;
-        }
-    }
-}
-
 __global__ void __launch_bounds__(kPaThreads) pc_apply_kernel(const StepArgs a) {
     __shared__ __align__(16) float ws[2 * kPaW];
     pc_apply_body(a, blockIdx.x, gridDim.x, ws);
-}
-
-__global__ void __launch_bounds__(kPaThreads) pc_apply_batch_kernel(const StepArgs *args,
-                                                                    int npairs) {
-    __shared__ __align__(16) float ws[2 * kPaW];
-    for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
-        __syncthreads();
-        const StepArgs a = args[p];
-        if ((int)blockIdx.x * kPaRowsPerCta >= a.n) continue;
-        pc_apply_body(a, blockIdx.x, gridDim.x, ws);
-    }
 }
 
 }  // namespace
@@ -506,11 +442,5 @@ cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_pc_apply_batch(const StepArgs *args, int npairs, int max_n, cudaStream_t s) {
-    const int grid = (max_n + kPaRowsPerCta - 1) / kPaRowsPerCta;
-    pc_apply_batch_kernel<<<dim3(grid, (unsigned)min(npairs, 65535)), kPaThreads, 0, s>>>(args,
-                                                                                         npairs);
-    return cudaGetLastError();
-}
 
 }  // namespace dia
