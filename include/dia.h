@@ -148,6 +148,10 @@ typedef struct {
     int32_t max_ls_evals;      /* evaluations one line search may take before it gives up
                                   (restart from preconditioned steepest descent, twice at
                                   most, then stop) (12) */
+    int32_t precond_window;    /* side of the centred window of target pixels whose
+                                  Gauss-Newton Hessian is the preconditioner; 0 = automatic
+                                  (about sqrt(1.2e11) / n, between 256 and 1024; 544 at
+                                  m = 25) (0) */
 } dia_opts;
 
 typedef struct {

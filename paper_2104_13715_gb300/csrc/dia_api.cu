@@ -43,6 +43,7 @@ struct Layout {
         YPY, pdiag, pc_args, pc_part, pc_A64, pc_X64, pc_P, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
         total;
     int G, n_tiles, tiles_x, np, n, kp;
+    int pc_chunks;   // chunk partials the preconditioner's Hessian sum may use
 };
 
 bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInfo &ki, Layout &L) {
@@ -94,7 +95,8 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
     // its float64 factor and inverse (padded to 64), P
     L.pc_args = take(sizeof(PrecondArgs));
     int wy0, wy1, wx0, wx1, chunks;
-    precond_window(H, W, m, true, &wy0, &wy1, &wx0, &wx1, &chunks);
+    precond_window(H, W, m, true, 0, &wy0, &wy1, &wx0, &wx1, &chunks);
+    L.pc_chunks = chunks;
     L.pc_part = take(chunks > 1 ? (size_t)chunks * gn_blocks(L.n) * kGnT * kGnT * 8 : 0);
     L.pc_A64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
     L.pc_X64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
@@ -387,6 +389,7 @@ void fill_opts_default(dia_opts *o) {
     o->stall_iters = 30;
     o->stall_iters_diag = 1000;
     o->max_ls_evals = 12;
+    o->precond_window = 0;
     o->grad_tol = 1e-7;
     o->max_lbfgs_iters = 3000;
     o->max_evals = 20000;
@@ -517,7 +520,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         fill_opts_default(&opts);
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.clip_passes < 0 || opts.max_adam_iters < 0 ||
-        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 || opts.init < 0 || opts.init > 2 ||
+        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 || opts.precond_window < 0 || opts.init < 0 || opts.init > 2 ||
         (opts.init == 2 && !opts.theta0) || (opts.init == 1 && !(opts.init_sigma > 0.0)) ||
         !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
@@ -576,7 +579,9 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             pa.W = W;
             pa.ld = ld;
             pa.m = m;
-            precond_window(H, W, m, true, &pa.y0, &pa.y1, &pa.x0, &pa.x1, &pa.gn_chunks);
+            precond_window(H, W, m, true, opts.precond_window, &pa.y0, &pa.y1, &pa.x0, &pa.x1,
+                           &pa.gn_chunks);
+            pa.gn_chunks = std::min(pa.gn_chunks, c.L.pc_chunks);   // the workspace's partials
             pa.lp = c.ea.lp;
             pa.part = (double *)(c.ws + c.L.pc_part);
             pa.A64 = (double *)(c.ws + c.L.pc_A64);

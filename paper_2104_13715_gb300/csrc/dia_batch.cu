@@ -55,7 +55,8 @@ struct BatchPlan {
     int gbeg[5];   // items of kernel-side group g: [gbeg[g], gbeg[g+1])
 };
 
-dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precond, BatchPlan &P) {
+dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precond, int pc_side,
+                      BatchPlan &P) {
     if (!pairs || npairs <= 0) return DIA_ERR_ARG;
     P.pp.resize(npairs);
     P.history = history;
@@ -94,7 +95,7 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
         // preconditioner: float64 Gauss-Newton Hessian (factored in place) and
         // inverse factor, padded to 64, and P; one pixel chunk per pair
         int chunks = 1;
-        precond_window(p.H, p.W, p.m, false, &q.y0, &q.y1, &q.x0, &q.x1, &chunks);
+        precond_window(p.H, p.W, p.m, false, pc_side, &q.y0, &q.y1, &q.x0, &q.x1, &chunks);
         q.pc_a_off = q.pc_x_off = q.pc_p_off = 0;
         if (precond) {
             const size_t np2 = (size_t)pc_np(q.n) * pc_np(q.n);
@@ -187,7 +188,7 @@ extern "C" size_t dia_batch_workspace_size(const dia_pair *pairs, int32_t npairs
         dia_opts_default(&o);
     if (o.history < 1 || o.history > kHistMax) return 0;
     BatchPlan P;
-    if (plan_batch(pairs, npairs, o.history, o.precond, P) != DIA_OK) return 0;
+    if (plan_batch(pairs, npairs, o.history, o.precond, o.precond_window, P) != DIA_OK) return 0;
     return P.total;
 }
 
@@ -204,7 +205,8 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     if (!loss || npairs <= 0) return DIA_ERR_ARG;
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.max_adam_iters < 0 || opts.max_evals < 1 ||
-        opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 || opts.init < 0 || opts.init > 1 ||
+        opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 ||
+        opts.precond_window < 0 || opts.init < 0 || opts.init > 1 ||
         (opts.init == 1 && !(opts.init_sigma > 0.0)) || !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
     if (opts.clip_passes != 0) return DIA_ERR_UNSUPPORTED;
@@ -219,7 +221,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         if (loss->var_model == DIA_VAR_FIXED && !pairs[i].var && !(loss->var_scalar > 0.f))
             return DIA_ERR_ARG;
     BatchPlan P;
-    dia_status rc = plan_batch(pairs, npairs, opts.history, opts.precond, P);
+    dia_status rc = plan_batch(pairs, npairs, opts.history, opts.precond, opts.precond_window, P);
     if (rc != DIA_OK) return rc;
     if (!workspace || workspace_bytes < P.total || ((uintptr_t)workspace & 255) != 0)
         return DIA_ERR_WORKSPACE;

@@ -9,7 +9,7 @@ namespace dia {
 constexpr int kBW = 8;             // warps per CTA of the batched kernel
 constexpr int kBQF = 4;            // output rows per warp in the forward pass
 constexpr int kBTH = kBW * kBQF;   // tile rows
-constexpr int kChunkTiles = 8;     // tiles per work item
+constexpr int kChunkTiles = 2;     // tiles per work item
 
 // per kernel side: prefetch flag and backward split of the batched kernel
 #define DIA_BATCH_SIDES(X)                                                                    \

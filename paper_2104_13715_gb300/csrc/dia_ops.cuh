@@ -233,8 +233,8 @@ cudaError_t launch_fisher_weights(const EvalArgs &ea, float *w, unsigned long lo
                                   cudaStream_t s);
 // res[0] = log det H, res[1] = smallest pivot of its Cholesky factor (squared)
 cudaError_t launch_fisher_finish(const double *A64, int n, int np, double *res, cudaStream_t s);
-void precond_window(int H, int W, int m, bool single, int *y0, int *y1, int *x0, int *x1,
-                    int *chunks);
+void precond_window(int H, int W, int m, bool single, int side, int *y0, int *y1, int *x0,
+                    int *x1, int *chunks);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,

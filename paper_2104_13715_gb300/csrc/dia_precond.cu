@@ -424,9 +424,10 @@ int precond_launches(int max_m) {
 // Window (centred, side pc_window_side) and chunk count of a pair's
 // Hessian sum; chunks > 1 only for a single pair (a batch has parallelism
 // across its pairs).
-void precond_window(int H, int W, int m, bool single, int *y0, int *y1, int *x0, int *x1,
-                    int *chunks) {
-    const int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h, side = pc_window_side(m * m + 1);
+void precond_window(int H, int W, int m, bool single, int side_opt, int *y0, int *y1, int *x0,
+                    int *x1, int *chunks) {
+    const int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h;
+    const int side = side_opt > 0 ? side_opt : pc_window_side(m * m + 1);
     const int sy = min(Hv, side), sx = min(Wv, side);
     *y0 = (Hv - sy) / 2;
     *y1 = *y0 + sy;

@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
                 ("theta0", ctypes.c_void_p), ("graph_iters", ctypes.c_int32),
                 ("timeout_s", ctypes.c_double), ("stall_iters", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("stall_iters_diag", ctypes.c_int32), ("max_ls_evals", ctypes.c_int32)]
+                ("stall_iters_diag", ctypes.c_int32), ("max_ls_evals", ctypes.c_int32),
+                ("precond_window", ctypes.c_int32)]
 
 
 class FisherInfo(ctypes.Structure):
