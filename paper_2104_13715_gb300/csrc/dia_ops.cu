@@ -146,6 +146,8 @@ __device__ void set_trial(const StepArgs &a, double alpha) {
     write_kpad(b.trial, a.mk, a.kp, a.Kpad, threadIdx.x, kStepThreads);
 }
 
+constexpr double kNoProgress = 1e-2;   // see finish()
+
 // Finish the pass: theta is the answer; the next evaluation (if any) sees it.
 __device__ void finish(const StepArgs &a, int status, int reason) {
     FitState *st = a.st;
@@ -153,10 +155,17 @@ __device__ void finish(const StepArgs &a, int status, int reason) {
     __syncthreads();
     write_kpad(a.b.theta, a.mk, a.kp, a.Kpad, threadIdx.x, kStepThreads);
     if (threadIdx.x == 0) {
+        // a pass that stops for lack of progress is at the limit of numerical
+        // precision only if max|g| came down by orders of magnitude from the
+        // fit's start (measured floors are ~1e-6 of it); otherwise it failed
+        if (status == 0 && (reason == kStopStall || reason == kStopLineSearch) &&
+            !st->from_theta0 && st->ginf_first > 0.0 && st->ginf_best > kNoProgress * st->ginf_first)
+            status = 5; /* DIA_ERR_LINESEARCH */
         st->status = status;
         st->reason = reason;
         // the float32 floor of max|g| found by this pass serves the refits
-        if (reason == kStopStall || reason == kStopLineSearch) st->ginf_floor = st->ginf_best;
+        if (status == 0 && (reason == kStopStall || reason == kStopLineSearch))
+            st->ginf_floor = st->ginf_best;
         st->phase = kPhaseDone;
         st->L_sum = st->L * st->ndata;
         __threadfence();
@@ -293,9 +302,20 @@ __device__ void direction_body(const StepArgs &a, StepShared &sm) {
         if (tid == 0) st->hist_len = 0;
     }
     for (int k = tid; k < n; k += kStepThreads) b.glo[k] = b.grad[k];
+    // L-BFGS learning rate 1 (Sec. 2.9).  Without curvature pairs the step is
+    // the preconditioner's Gauss-Newton step, whose model can be far off where
+    // the variance depends on M and the residuals are large: the first trial
+    // is then capped so that its predicted decrease is at most 4 |L| (the
+    // loss), and scaled down further after a failed search (alpha0)
+    double a_init = 1.0;
+    if (st->hist_len == 0) {
+        const double L = st->L;
+        if (L > 0.0 && -gd0 > 4.0 * L) a_init = 4.0 * L / -gd0;
+        a_init *= st->alpha0 > 0.0 ? st->alpha0 : 1.0;
+    }
     if (tid == 0) {
         st->gd0 = gd0;
-        st->alpha = 1.0;   // L-BFGS learning rate 1 (Sec. 2.9)
+        st->alpha = a_init;
         st->lo = 0.0;
         st->L_lo = st->L;
         st->gd_lo = gd0;
@@ -304,7 +324,7 @@ __device__ void direction_body(const StepArgs &a, StepShared &sm) {
         st->need_pc = 0;
     }
     __syncthreads();
-    set_trial(a, 1.0);
+    set_trial(a, a_init);
 }
 
 // A refit (sigma-clip pass) is at the limit of numerical precision once max|g|
@@ -377,6 +397,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
     }
     const double invN = 1.0 / N;
     const double Lt = a.red[0] * invN;
+    const bool first_eval = *((volatile int *)&st->evals) == 0;   // read before the update below
     bool bad = !isfinite(Lt);
     for (int k = tid; k < n; k += kStepThreads) {
         const double g = a.red[1 + k] * invN;
@@ -391,6 +412,12 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
     if (nbad) {
         finish(a, 3 /* DIA_ERR_NONFINITE */, kStopNonfinite);
         return;
+    }
+    if (first_eval) {   // the scale against which progress is judged (finish())
+        double mx = 0.0;
+        for (int k = tid; k < n; k += kStepThreads) mx = fmax(mx, fabs(sm.gt[k]));
+        const double g0 = block_max(mx, sm.red);
+        if (tid == 0) st->ginf_first = g0;
     }
 
     int phase = st->phase;
@@ -497,7 +524,10 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
             } else if (st->stall >= stall_limit(a) && st->it_lbfgs > 0) {
                 sm.finish_status = 0;
                 sm.act = kStopStall;
-            } else if (st->hist_len > 0 && st->ls_restarts < 2) {
+            } else if (st->ls_restarts < 2) {
+                // restart from preconditioned steepest descent; a search that
+                // already had no history retries with a 100x shorter first step
+                if (st->hist_len == 0) st->alpha0 = (st->alpha0 > 0.0 ? st->alpha0 : 1.0) * 0.01;
                 st->hist_len = 0;
                 st->ls_restarts += 1;
             } else {
@@ -545,6 +575,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
         st->grad_inf = ginf;
         st->it_lbfgs += 1;
         st->ls_restarts = 0;
+        st->alpha0 = 1.0;
         if (ginf < 0.5 * st->ginf_best) {
             st->ginf_best = ginf;
             st->ev_best = st->evals;
@@ -691,6 +722,8 @@ __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int k
         z.b2t = 1.0;
         z.phase = start_phase;
         z.median = median;
+        z.from_theta0 = (mode == 2) ? 1 : 0;
+        z.alpha0 = 1.0;
         if (degenerate) {
             z.status = 6; /* DIA_ERR_DEGENERATE */
             z.reason = kStopDegenerate;

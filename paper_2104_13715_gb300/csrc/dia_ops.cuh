@@ -36,6 +36,7 @@ struct FitState {
     int ev_best;     // evals when max|g| last halved (stall detection)
     int need_pc;     // new L-BFGS direction pending: 1 needs P g, 2 also P y_new
     int pc_slot;     // history slot of y_new (need_pc == 2)
+    int from_theta0; // 1: the fit started from the caller's theta (no progress test)
     double ndata;    // unmasked valid pixels of the last evaluation
     double L;        // scaled loss (L_sum / N) at the accepted theta
     double L_sum;    // unscaled loss at the accepted theta
@@ -48,6 +49,8 @@ struct FitState {
     double b1t, b2t; // Adam beta powers
     double median;   // B0 initialisation
     double ginf_floor; // best max|g| of the last pass that ended at the precision limit (0: none)
+    double ginf_first; // max|g| of the fit's first evaluation
+    double alpha0;     // scale of the first trial step of a search without history (restarts)
 };
 
 struct OptParams {

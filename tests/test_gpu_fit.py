@@ -188,3 +188,21 @@ def test_host_buffers_end_to_end(nat):
     _check(out["theta"].numpy(), ref, float(np.median(d["I"])))
     dev = _fit(nat, d, m, d["loss"])
     assert np.array_equal(dev["theta"].cpu().numpy(), out["theta"].numpy())
+
+
+def test_lbfgs_from_the_boxcar_start_with_model_dependent_variance(nat):
+    """Without the Adam phase L-BFGS starts at the box-car kernel, where the
+    CCD likelihood's curvature is far from the preconditioner's Gauss-Newton
+    model (large residuals): the capped first step must still reach the FP64
+    optimum rather than stop early, at any preconditioner window."""
+    d = synth.workload("ccd1024_m19_nll", seed=2, size=384)
+    m, spec = d["m"], d["loss"]
+    keys = {k: v for k, v in spec.items() if k in ("rho", "noise", "sigma0", "gain", "var_floor")}
+    ref = None
+    for win in (0, 256, 160):
+        out = _fit(nat, d, m, keys, nat.default_opts(max_adam_iters=0, precond_window=win))
+        th = out["theta"].cpu().numpy()
+        assert out["info"]["status"] == 0 and out["info"]["adam_iters"] == 0
+        if ref is None:
+            ref = oracle.newton(d["R"], d["I"], m, th, ospec(keys))
+        _check(th, ref, float(np.median(d["I"])))
