@@ -340,7 +340,14 @@ __device__ __forceinline__ bool at_floor(const FitState *st, double ginf) {
 // Toeplitz preconditioned iteration reaches its float32 floor within tens of
 // evaluations, the diagonally preconditioned one needs far more.
 __device__ __forceinline__ int stall_limit(const StepArgs &a) {
-    return (a.st->pc_ok && a.b.P) ? a.p.stall_iters : a.p.stall_iters_diag;
+    const FitState *st = a.st;
+    int lim = (st->pc_ok && a.b.P) ? a.p.stall_iters : a.p.stall_iters_diag;
+    // far above any float32 floor (max|g| not yet down to kNoProgress of the
+    // fit's first gradient, e.g. a redescending loss started far from the
+    // optimum) a stall is slow progress, not the precision limit
+    if (!st->from_theta0 && st->ginf_first > 0.0 && st->ginf_best > kNoProgress * st->ginf_first)
+        lim = max(lim, a.p.stall_iters_diag);
+    return lim;
 }
 
 // Line-search decision for the trial alpha (thread 0).  Wolfe conditions, or

@@ -206,3 +206,20 @@ def test_lbfgs_from_the_boxcar_start_with_model_dependent_variance(nat):
         if ref is None:
             ref = oracle.newton(d["R"], d["I"], m, th, ospec(keys))
         _check(th, ref, float(np.median(d["I"])))
+
+
+@pytest.mark.parametrize("name", ["gauss-emccd", "huber-ccd", "huber-fixed", "cauchy-emccd"])
+@pytest.mark.parametrize("adam", [5000, 0])
+def test_every_loss_fits_to_the_oracle_optimum(nat, name, adam):
+    """Each loss x variance model, with the paper's Adam phase and without:
+    the fitted theta is the FP64 oracle's (local) optimum, found by Newton
+    steps from it (Cauchy is not convex; without Adam its start is slow and
+    the stall budget stays long until max|g| is well below its start)."""
+    m = 9
+    d = field(150, 140, m, seed=31)
+    spec = SPECS[name]
+    out = _fit(nat, d, m, spec, nat.default_opts(max_adam_iters=adam))
+    th = out["theta"].cpu().numpy()
+    assert out["info"]["status"] == 0
+    ref = oracle.newton(d["R"], d["I"], m, th, ospec(spec))
+    _check(th, ref, float(np.median(d["I"])))
