@@ -340,60 +340,6 @@ __device__ __forceinline__ void bwd_rows(const float *rrow, const float *g0, con
     }
 }
 
-// Paired backward (F2): whole kernel rows 2j and 2j+1 of this warp share one
-// packed FMA, dkp[j * MK + b] = (dk[2j][b], dk[2j+1][b]) += (g[y][x+p],
-// g[y-1][x+p]) * R[r0+rr][x+b+p] with y = rr - 2j.  Same FMA order per
-// accumulator as bwd_row.
-template <int MK, int NP2, int RWIN>
-__device__ __forceinline__ void bwd_row2(const float (&win)[RWIN], const float *g0, int rr,
-                                         float2 (&dkp)[NP2 * MK]) {
-    float4 ga[NP2], gb[NP2];
-#pragma unroll
-    for (int j = 0; j < NP2; ++j) {
-        ga[j] = *reinterpret_cast<const float4 *>(g0 + (rr - 2 * j) * kTW);
-        gb[j] = *reinterpret_cast<const float4 *>(g0 + (rr - 2 * j - 1) * kTW);
-    }
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-#pragma unroll
-        for (int j = 0; j < NP2; ++j) {
-            const float2 gv = p == 0 ? make_float2(ga[j].x, gb[j].x)
-                            : p == 1 ? make_float2(ga[j].y, gb[j].y)
-                            : p == 2 ? make_float2(ga[j].z, gb[j].z)
-                                     : make_float2(ga[j].w, gb[j].w);
-#pragma unroll
-            for (int b = 0; b < MK; ++b)
-                dkp[j * MK + b] = __ffma2_rn(gv, make_float2(win[b + p], win[b + p]), dkp[j * MK + b]);
-        }
-    }
-}
-
-template <int MK, int NP2, int RP, int RWIN, int PF>
-__device__ __forceinline__ void bwd_rows2(const float *rrow, const float *g0, int n_rr,
-                                          float2 (&dkp)[NP2 * MK]) {
-    if (PF) {
-        float wa[RWIN], wb[RWIN];
-        load_win<RWIN>(wa, rrow);
-#pragma unroll 1
-        for (int rr = 0; rr < n_rr; rr += 2) {
-            const bool two = rr + 1 < n_rr;
-            if (two) load_win<RWIN>(wb, rrow + (rr + 1) * RP);
-            bwd_row2<MK, NP2, RWIN>(wa, g0, rr, dkp);
-            if (two) {
-                if (rr + 2 < n_rr) load_win<RWIN>(wa, rrow + (rr + 2) * RP);
-                bwd_row2<MK, NP2, RWIN>(wb, g0, rr + 1, dkp);
-            }
-        }
-    } else {
-#pragma unroll 1
-        for (int rr = 0; rr < n_rr; ++rr) {
-            float win[RWIN];
-            load_win<RWIN>(win, rrow + rr * RP);
-            bwd_row2<MK, NP2, RWIN>(win, g0, rr, dkp);
-        }
-    }
-}
-
 // The fused pass over tiles t_begin, t_begin + t_step, ... < t_end of one
 // pair; the CTA's partial sums (m*m + 5 float64) go to `out`.  Called by
 // the single-pair kernel (tiles strided over the grid) and by the batched
@@ -676,27 +622,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
 #pragma unroll
         for (int i = 0; i < NK; ++i) dk[i] = 0.f;
         const float *gzero = gs + 4 * lane;   // a zero row above the g tile
-        bool whole_done = false;
-        if constexpr ((F2 & 2) != 0 && KF > 0 && KF % 2 == 0) {
-          if (nq == KF) {
-            whole_done = true;
-            constexpr int NP2 = KF / 2;
-            float2 dkp[NP2 * MK];
-#pragma unroll
-            for (int i = 0; i < NP2 * MK; ++i) dkp[i] = make_float2(0.f, 0.f);
-            bwd_rows2<MK, NP2, RP, RWIN, PF>(Rs + a_lo * RP + 4 * lane, gt + 4 * lane, TH + KF - 1,
-                                             dkp);
-#pragma unroll
-            for (int j = 0; j < NP2; ++j)
-#pragma unroll
-                for (int b = 0; b < MK; ++b) {
-                    dk[(2 * j) * MK + b] = dkp[j * MK + b].x;
-                    dk[(2 * j + 1) * MK + b] = dkp[j * MK + b].y;
-                }
-          }
-        }
-        if (whole_done) {
-        } else if (KF > 0 && nq == KF)
+        if (KF > 0 && nq == KF)
             bwd_rows<MK, QB, 0, (KF > 0 ? KF : 1), RP, RWIN, false, TH, PF>(
                 Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 1, dk);
         else if (KF > 1 && nq == KF - 1)   // SPLIT 0: the warps with one row fewer

@@ -7,4 +7,4 @@ DIA_EVAL_INST(25, 2, 12, 4, 1, 1, 0)
 DIA_EVAL_INST(25, 3, 13, 4, 0, 0, 0)
 DIA_EVAL_INST(25, 4, 12, 2, 0, 1, 0)
 DIA_EVAL_INST(25, 5, 12, 4, 0, 1, 1)
-DIA_EVAL_INST(25, 6, 12, 4, 1, 1, 3)
+DIA_EVAL_INST(25, 6, 13, 4, 0, 0, 1)

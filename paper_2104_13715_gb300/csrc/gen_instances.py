@@ -7,9 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel side -> list of tile variants (NW warps, QF output rows per warp in the
 # forward pass, PF = 1 to load the next R-row window while the current one is used,
 # SPLIT = backward row split: 0 whole rows ceil/floor per warp, 1 equal work
-# with the MK % NW last rows split by tile-row slices, F2 = packed float2 FMAs:
-# bit 0 pairs output rows in the forward, bit 1 pairs kernel rows in the
-# backward when a warp owns an even number of whole rows; 0 if omitted).
+# with the MK % NW last rows split by tile-row slices, F2 = 1 for packed float2
+# FMAs pairing output rows in the forward; 0 if omitted).
 # Variant 0 is the default; the autotuner may pick another at run time.
 VARIANTS = {
     1: [(8, 8, 0, 0)], 3: [(8, 8, 0, 0)], 5: [(8, 8, 0, 0)],
@@ -23,7 +22,7 @@ VARIANTS = {
     21: [(8, 4, 0, 0, 1), (8, 4, 0, 0), (8, 4, 1, 0), (7, 4, 0, 0)],
     23: [(8, 4, 0, 0), (8, 4, 1, 0), (8, 4, 1, 0, 1)],
     25: [(12, 4, 1, 1, 1), (12, 4, 0, 1), (12, 4, 1, 1), (13, 4, 0, 0), (12, 2, 0, 1),
-         (12, 4, 0, 1, 1), (12, 4, 1, 1, 3)],
+         (12, 4, 0, 1, 1), (13, 4, 0, 0, 1)],
     27: [(9, 4, 0, 0), (9, 4, 1, 0)],
     29: [(10, 4, 0, 0), (10, 4, 1, 0)],
     31: [(8, 4, 0, 0), (8, 4, 1, 0)],
