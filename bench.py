@@ -241,7 +241,7 @@ def _config(args, d):
             "seeds": [args.seed + r for r in range(_env_int("WORLD_SIZE", 1))],
             "l2": f"inputs larger than L2 ({by / 2**20:.0f} MiB > {L2_BYTES / 2**20:.0f} MiB)",
             "init": "box-car K, B0 = median(I) (Sec. 2.9)",
-            "optimizer": "Adam -> L-BFGS (block-Toeplitz preconditioned, library defaults)"}
+            "optimizer": "Adam -> L-BFGS (Gauss-Newton preconditioned, library defaults)"}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -607,7 +607,7 @@ def run_reference_batch(args, rank, world):
 
 
 def run_precision_study(args):
-    """Fifth configuration: the FP32 fused path with float64 cross-block
+    """Precision study: the FP32 fused path with float64 cross-block
     accumulation against the pure-float32 accumulation form, on the 2048^2
     high-dynamic-range field (m = 21, CCD negative log-likelihood).  For each
     form: fit, then K, B0 and difference-image errors against the FP64
@@ -656,7 +656,7 @@ def run_precision_study(args):
             "diff_err_rel_maxI": float(np.max(np.abs(f["diff"] - D_ref)) / np.max(np.abs(d["I"]))),
             "grad_err_rel_at_start": f["grad_err"],
             "evals": f["info"]["evals"], "reason": f["info"]["reason"]}
-    res["tensor_core_split_tf32_form"] = "not built (see DESIGN.md)"
+    res["tensor_core_split_tf32_form"] = "not built"
     print(json.dumps({"precision_study": name, "H": d["R"].shape[0], "W": d["R"].shape[1],
                       "m": m, "loss": "gauss", "variance": "ccd", "results": res,
                       "oracle": f"FP64 Newton polish from the float64-accumulation fit, "

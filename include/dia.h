@@ -138,11 +138,11 @@ typedef struct {
                                   the L-BFGS phase (30) */
     int32_t use_graph;         /* 1: replay optimiser iterations from a CUDA graph (default);
                                   0: launch them one by one (the plain form) */
-    int32_t precond;           /* L-BFGS initial inverse Hessian: 1 = block-Toeplitz
-                                  preconditioner from the weighted autocorrelation of R
+    int32_t precond;           /* L-BFGS initial inverse Hessian: 1 = the inverse of the
+                                  Gauss-Newton Hessian over a window of target pixels
                                   (default), 0 = diagonal */
     int32_t stall_iters_diag;  /* stall_iters when L-BFGS runs with the diagonal
-                                  preconditioner (precond = 0, or the block-Toeplitz
+                                  preconditioner (precond = 0, or the Gauss-Newton
                                   factorisation failed), which converges far more slowly
                                   (1000) */
     int32_t max_ls_evals;      /* evaluations one line search may take before it gives up
@@ -169,7 +169,7 @@ typedef struct {
                                   refit reached (within 3x) the max|dL/dtheta| floor of
                                   an earlier pass of the same fit */
     int64_t kernel_launches;   /* CUDA kernels this call launched (graph nodes included) */
-    int32_t precond_used;      /* 1: L-BFGS ran with the block-Toeplitz preconditioner
+    int32_t precond_used;      /* 1: L-BFGS ran with the Gauss-Newton preconditioner
                                   (asked for and factored), 0: with the diagonal one */
 } dia_fit_info;
 
@@ -196,8 +196,8 @@ dia_status dia_opts_default(dia_opts *opts);
  * variants agree up to the order of float32 tile sums. */
 int32_t dia_kernel_variants(int32_t m);
 
-/* Accumulation of the per-pixel loss and gradient terms (the benchmark spec precision
- * item; the fifth benchmark configuration compares the two forms):
+/* Accumulation of the per-pixel loss and gradient terms (the precision
+ * study of the high-dynamic-range workload compares the two forms):
  *   DIA_ACCUM_FP64 (default) -- float32 per-lane runs of at most 4096 pixels,
  *     Kahan-compensated float32 per tile run for dL/dK, float64 across tiles,
  *     warps and CTAs;
@@ -244,11 +244,14 @@ dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff
                           void *workspace, size_t workspace_bytes, void *stream);
 
 /* Fit theta = [K, B0] (Sec. 2.10 algorithm): initialise, Adam until the
- * relative loss change drops below switch_tol, then L-BFGS with a
- * strong-Wolfe line search until rel_tol / grad_tol; optionally clip
- * |z| > kappa and refit clip_passes times.  Each optimiser iteration is one
- * fused evaluation, a float64 reduction and a one-CTA float64 optimiser
- * step, replayed graph_iters at a time from a CUDA graph.
+ * relative loss change drops below switch_tol, then L-BFGS (preconditioned
+ * by the inverse Gauss-Newton Hessian of a window of the pair, Wolfe /
+ * approximate-Wolfe line search) until grad_tol, rel_tol or the limit of
+ * numerical precision (stall_iters); optionally clip |z| > kappa and refit
+ * clip_passes times.  Each optimiser iteration is one fused evaluation, a
+ * float64 reduction and the float64 optimiser step (a line-search kernel, a
+ * multi-CTA P v and a direction kernel), replayed graph_iters at a time from
+ * a CUDA graph.
  * Outputs (all nullable; device pointers, or host pointers if the pair is
  * DIA_MEM_HOST):
  *   theta_out  float64[n]; K_out float32[m*m]; b0_out float32[1];
@@ -262,13 +265,15 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
                    uint8_t *mask_out, dia_fit_info *info,
                    void *workspace, size_t workspace_bytes, void *stream);
 
-/* Batched fits (SURVEY config: many stamp pairs of uneven sizes and kernel
- * sides in one launch per iteration).  `pairs` is a HOST array of npairs
- * DIA_MEM_DEVICE pairs (each with its own H, W, ld, m, maps); one loss spec
- * and one dia_opts apply to all (clip_passes must be 0; init 0 or 1).
- * Every optimiser iteration of the whole batch is two kernels: a persistent
- * fused evaluation over work items (a pair and a range of its tiles, largest
- * first, from an atomic queue) and one optimiser CTA per pair; converged
+/* Batched fits: many stamp pairs of uneven sizes and kernel sides, each
+ * optimiser iteration of the whole batch in a few launches.  `pairs` is a
+ * HOST array of npairs DIA_MEM_DEVICE pairs (each with its own H, W, ld, m,
+ * maps); one loss spec and one dia_opts apply to all (clip_passes must be 0;
+ * init 0 or 1).  Every optimiser iteration runs one persistent fused
+ * evaluation kernel per group of kernel sides (1-7, 9-15, 17-23, 25-31;
+ * parallel graph branches) over work items (a pair and two of its tiles,
+ * largest first, from atomic queues), then two kernels with one CTA per
+ * pair (line search and history; P v and the L-BFGS direction); converged
  * pairs drop out.  graph_iters iterations are replayed from a CUDA graph.
  * Outputs: theta_out (device, nullable) packs the pairs' theta vectors in
  * order, pair i at offset sum_{j<i} (m_j^2 + 1); diff_out (nullable HOST

@@ -562,9 +562,8 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         launches += kMedianLaunches + 1;
     }
 
-    // block-Toeplitz preconditioner of L-BFGS from the zero-padded weighted
-    // autocorrelation of R over a centred window of at most 1024 x 1024 valid
-    // pixels
+    // preconditioner of L-BFGS: the inverse of the Gauss-Newton Hessian over
+    // a centred window of valid target pixels (dia_precond.cu)
     {
         const int Hv = H - 2 * h, Wv = W - 2 * h;
         if (opts.precond) {

@@ -404,7 +404,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     // initialisation: per-pair median and theta (Sec. 2.9)
     const int start_phase = opts.max_adam_iters > 0 ? kPhaseAdam : kPhaseLbfgsStart;
     DB_CK(launch_init_batch(d_sa, d_eas, npairs, opts.init, opts.init_sigma, start_phase, s));
-    // per-pair block-Toeplitz preconditioners (after init, which clears the state)
+    // per-pair Gauss-Newton preconditioners (after init, which clears the state)
     if (opts.precond) DB_CK(launch_precond(d_pas, pas.data(), npairs, s));
 
     // the iteration graph (cached per workspace / batch shape / settings); the

@@ -337,7 +337,7 @@ __device__ __forceinline__ bool at_floor(const FitState *st, double ginf) {
 }
 
 // Evaluations without a halving of max|g| that end the pass: the block-
-// Toeplitz preconditioned iteration reaches its float32 floor within tens of
+// Newton preconditioned iteration reaches its float32 floor within tens of
 // evaluations, the diagonally preconditioned one needs far more.
 __device__ __forceinline__ int stall_limit(const StepArgs &a) {
     const FitState *st = a.st;

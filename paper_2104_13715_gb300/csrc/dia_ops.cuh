@@ -1,6 +1,6 @@
 // Small kernels around the fused evaluation: the float64 cross-CTA reduction,
 // the on-device optimiser (Adam, then L-BFGS with a Wolfe / approximate-Wolfe
-// line search and a block-Toeplitz preconditioner, Sec. 2.3 and Sec. 2.9),
+// line search and a Gauss-Newton preconditioner, Sec. 2.3 and Sec. 2.9),
 // initialisation (box-car or Gaussian kernel, B0 =
 // median of the target, Sec. 2.9) and output packing.
 #pragma once
@@ -32,7 +32,7 @@ struct FitState {
     int status;      // dia_status of the pass
     int it_adam, it_lbfgs, evals;
     int ls_evals, hist_len, hist_head, ls_restarts, stall, reason;
-    int pc_ok;       // 1: the block-Toeplitz preconditioner is factored and used
+    int pc_ok;       // 1: the Gauss-Newton preconditioner is factored and used
     int ev_best;     // evals when max|g| last halved (stall detection)
     int need_pc;     // new L-BFGS direction pending: 1 needs P g, 2 also P y_new
     int pc_slot;     // history slot of y_new (need_pc == 2)
@@ -68,7 +68,7 @@ struct OptParams {
 struct OptBuffers {
     double *theta, *trial, *grad, *glo, *m1, *m2, *dir, *pg, *pdiag;
     double *S, *Y, *PY, *SY, *YPY;
-    // block-Toeplitz preconditioner (nullable): P = T^-1, n x n float32, row
+    // Gauss-Newton preconditioner (nullable): P = H^-1, n x n float32, row
     // pitch ldp (a multiple of 4); used when FitState::pc_ok is set
     const float *P;
     int ldp;

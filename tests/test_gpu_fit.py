@@ -50,7 +50,7 @@ def test_stamp128_m11_chi2_matches_normal_equations(nat):
 
 
 def test_preconditioner_cuts_lbfgs_iterations(nat):
-    """The block-Toeplitz preconditioner (the default) and the diagonal one
+    """The Gauss-Newton preconditioner (the default) and the diagonal one
     reach the same normal-equation optimum; the former in far fewer L-BFGS
     iterations (about 100 against about 1000 on this pair)."""
     d = synth.workload("stamp128_m11_chi2", seed=1)

@@ -1,4 +1,4 @@
-"""Precision study (fifth benchmark configuration, the benchmark spec precision item):
+"""Precision study of the accumulation of the per-pixel terms:
 float32 pixel arithmetic with float64 accumulation against the pure-float32
 accumulation form, on the high-dynamic-range recipe (fluxes 1e1-1e6, sky 2000,
 m = 21, CCD negative log-likelihood), both against the FP64 oracle."""
