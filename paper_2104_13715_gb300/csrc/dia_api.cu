@@ -11,6 +11,8 @@
 #include <string>
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dia.h"
 #include "dia_dispatch.h"
 #include "dia_eval.cuh"
@@ -21,6 +23,14 @@ using namespace dia;
 namespace {
 
 thread_local int g_last_cuda = 0;
+
+// NVTX range for profilers (a no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 // accumulation form of the single-pair entries (dia_set_accumulation)
 std::atomic<int> g_accumulation{DIA_ACCUM_FP64};
 
@@ -513,6 +523,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
                    double *theta_out, float *K_out, float *b0_out, float *diff_out,
                    uint8_t *mask_out, dia_fit_info *info, void *workspace,
                    size_t workspace_bytes, void *stream) {
+    NvtxRange range_fit("dia_fit");
     dia_opts opts;
     if (opts_in)
         opts = *opts_in;
@@ -567,6 +578,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     {
         const int Hv = H - 2 * h, Wv = W - 2 * h;
         if (opts.precond) {
+            NvtxRange range_pc("dia_fit preconditioner");
             PrecondArgs pa;
             memset(&pa, 0, sizeof(pa));
             pa.R = c.dp.ref;
@@ -637,6 +649,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     memset(&hs, 0, sizeof(hs));
     int status = DIA_OK, passes_done = 0;
     for (int pass = 0; pass <= opts.clip_passes; ++pass) {
+        NvtxRange range_pass(pass == 0 ? "dia_fit pass" : "dia_fit clip pass");
         if (pass > 0) {
             // clip |z| > kappa at the current theta, then refit from it
             EvalArgs ca = c.ea;

@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dia.h"
 #include "dia_batch.cuh"
 #include "dia_ops.cuh"
@@ -197,6 +199,10 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
                                     double *theta_out, float *const *diff_out,
                                     dia_fit_info *infos, void *workspace,
                                     size_t workspace_bytes, void *stream) {
+    nvtxRangePushA("dia_fit_batch");
+    struct PopOnExit {
+        ~PopOnExit() { nvtxRangePop(); }
+    } pop_on_exit;
     dia_opts opts;
     if (opts_in)
         opts = *opts_in;

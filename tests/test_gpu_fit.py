@@ -223,3 +223,42 @@ def test_every_loss_fits_to_the_oracle_optimum(nat, name, adam):
     assert out["info"]["status"] == 0
     ref = oracle.newton(d["R"], d["I"], m, th, ospec(spec))
     _check(th, ref, float(np.median(d["I"])))
+
+
+def test_noiseless_transforms_reach_float32_precision(nat):
+    """Sec. 3.4 tests (i)-(iv) -- identity, Gaussian phi_K = 1.5, +1 px shift,
+    +1/2 px bicubic shift (no pre-filtering) -- with the fractional errors of P
+    and B0 held to ten times the float32 values the paper prints (golden)."""
+    import json
+    import os
+    from scipy import ndimage
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "paper_values.json")))["noiseless_fp32_eps"]
+    p = synth.PairSpec(size=(150, 150), n_stars=60, m=1, fwhm_ref=2.5, kernel_sigma=0.0,
+                       sky=100.0, ref_noise=True, flux_law="paper")
+    Rbig = synth.make_pair(p, 4)["R"].astype(np.float64)
+    R = Rbig[4:-4, 4:-4]
+    B0 = 25.0
+    yy, xx = np.mgrid[-5:6, -5:6]
+    G = np.exp(-(xx ** 2 + yy ** 2) / (2 * 1.5 ** 2))
+    G /= G.sum()
+    cases = {
+        "identity": (R + B0, 9),
+        "gaussian": (None, 11),
+        "shift1": (None, 9),
+        "bicubic_half": (ndimage.shift(Rbig, (0.5, 0.5), order=3, prefilter=False)[4:-4, 4:-4]
+                         + B0, 9),
+    }
+    Ig = np.full_like(R, B0)
+    Ig[5:-5, 5:-5] = signal.correlate2d(R, G, mode="valid") + B0
+    cases["gaussian"] = (Ig, 11)
+    Is = np.full_like(R, B0)
+    Is[1:, 1:] += R[:-1, :-1]
+    cases["shift1"] = (Is, 9)
+    for name, (I, m) in cases.items():
+        d = dict(R=R.astype(np.float32), I=I.astype(np.float32))
+        th = _fit(nat, d, m, SPECS["gauss-fixed"])["theta"].cpu().numpy()
+        eps_p = abs(th[:-1].sum() - 1.0)
+        eps_b = abs(th[-1] - B0) / B0
+        assert eps_p <= 10 * gold["eps_P_max"] and eps_b <= 10 * gold["eps_B0_max"], \
+            (name, eps_p, eps_b)
