@@ -14,6 +14,10 @@ Pieces (each cites the passage it follows):
 * :func:`gram`, :func:`normal_solve` -- the Bramich (2008) normal equations
   for the fixed-variance chi^2 (Sec. 1 and Sec. 2.1): A = sum w phi phi^T,
   b = sum w phi I with phi_p = [R window of p, 1], solved by Cholesky.
+* :func:`laplacian`, :func:`penalty` -- the kernel regulariser of Sec. 2.7
+  (Eq. 20, Eq. 21): lam * N_data * theta^T L^T L theta with L the Laplacian of
+  the kernel-pixel graph (4-connectivity); loss_grad, normal_solve, hessian
+  and newton take it through ``reg_lambda``.
 * :func:`newton` -- for the losses that are not quadratic in theta: Newton
   steps with the exact Hessian sum_p l''(M_p) phi_p phi_p^T (M is linear in
   theta), Levenberg damping where it is not positive definite, backtracking
@@ -132,6 +136,34 @@ def n_params(m: int) -> int:
     return m * m + 1
 
 
+def laplacian(m: int) -> np.ndarray:
+    """Laplacian matrix of the kernel-pixel graph (Sec. 2.7, Eq. 21), of size
+    (m*m + 1) x (m*m + 1): L[u, u] = number of kernel pixels adjacent to u,
+    L[u, v] = -1 for adjacent u, v (sharing an edge: 4-connectivity), zero in
+    the B0 row and column."""
+    n = n_params(m)
+    L = np.zeros((n, n))
+    for a in range(m):
+        for b in range(m):
+            u = a * m + b
+            for da, db in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                aa, bb = a + da, b + db
+                if 0 <= aa < m and 0 <= bb < m:
+                    L[u, aa * m + bb] = -1.0
+                    L[u, u] += 1.0
+    return L
+
+
+def penalty(theta, m, lam, n_data):
+    """The regulariser of Eq. 20, lam * N_data * theta^T L^T L theta, with its
+    gradient and Hessian (L of Eq. 21)."""
+    L = laplacian(m)
+    LtL = L.T @ L
+    th = np.asarray(theta, dtype=np.float64)
+    c = lam * n_data
+    return c * th @ LtL @ th, 2.0 * c * LtL @ th, 2.0 * c * LtL
+
+
 def ndata(shape, m, mask=None) -> int:
     """Valid, unmasked pixel count N_data = (N - 2h)^2 without a mask (Sec. 2.1)."""
     H, W = shape
@@ -171,9 +203,10 @@ def pixel_terms(I, M, m, spec: LossSpec, mask=None, var=None, flat=None):
 
 
 def loss_grad(R, I, m, theta, spec: LossSpec = None, mask=None, var=None, flat=None,
-              nthreads: int = 0):
+              nthreads: int = 0, reg_lambda: float = 0.0):
     """FP64 loss L(theta) and gradient dL/dtheta (Eq. 8 / Eq. 13, summed over the
-    unmasked valid pixels).  Returns (L, grad[m*m+1])."""
+    unmasked valid pixels; with reg_lambda > 0, plus the regulariser of Eq. 20).
+    Returns (L, grad[m*m+1])."""
     spec = spec or LossSpec()
     R = _d(R)
     I = _d(I)
@@ -191,6 +224,9 @@ def loss_grad(R, I, m, theta, spec: LossSpec = None, mask=None, var=None, flat=N
                                   _ptr(loss), _ptr(grad), nthreads)
     if rc:
         raise ValueError(f"oracle_loss_grad failed ({rc})")
+    if reg_lambda:
+        pv, pg, _ = penalty(th, m, reg_lambda, ndata(R.shape, m, mask))
+        return float(loss[0]) + pv, grad + pg
     return float(loss[0]), grad
 
 
@@ -236,9 +272,12 @@ def _valid(a, m):
     return a[h:a.shape[0] - h, h:a.shape[1] - h]
 
 
-def normal_solve(R, I, m, mask=None, var=None, var_scalar: float = 1.0):
+def normal_solve(R, I, m, mask=None, var=None, var_scalar: float = 1.0,
+                 reg_lambda: float = 0.0):
     """B08 linear least squares for the fixed-variance chi^2: solve A theta = b
-    by Cholesky (Sec. 1; Sec. 2.1 'fixed estimates for sigma')."""
+    by Cholesky (Sec. 1; Sec. 2.1 'fixed estimates for sigma').  With
+    reg_lambda > 0 the minimum of chi^2/2 + the regulariser of Eq. 20:
+    (A + 2 lam N_data L^T L) theta = b."""
     R = _d(R)
     I = _d(I)
     H, W = _shape(R, m)
@@ -247,6 +286,8 @@ def normal_solve(R, I, m, mask=None, var=None, var_scalar: float = 1.0):
     if mask is not None:
         w = w * (_valid(np.asarray(mask), m) != 0)
     A, b = gram(R, m, w, w * Iv)
+    if reg_lambda:
+        A = A + penalty(np.zeros(n_params(m)), m, reg_lambda, ndata(R.shape, m, mask))[2]
     try:
         L = np.linalg.cholesky(A)
     except np.linalg.LinAlgError as e:
@@ -255,24 +296,30 @@ def normal_solve(R, I, m, mask=None, var=None, var_scalar: float = 1.0):
     return np.linalg.solve(L.T, y)
 
 
-def hessian(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None):
-    """Exact Hessian sum_p l''(M_p) phi_p phi_p^T (M is linear in theta)."""
+def hessian(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None,
+            reg_lambda: float = 0.0):
+    """Exact Hessian sum_p l''(M_p) phi_p phi_p^T (M is linear in theta), plus
+    that of the regulariser of Eq. 20 when reg_lambda > 0."""
     M = model(R, theta, m)
     _, _, d2, _ = pixel_terms(I, M, m, spec, mask, var, flat)
-    return gram(R, m, d2)
+    Hm = gram(R, m, d2)
+    if reg_lambda:
+        Hm = Hm + penalty(theta, m, reg_lambda, ndata(np.shape(R), m, mask))[2]
+    return Hm
 
 
 def newton(R, I, m, theta0, spec: LossSpec, mask=None, var=None, flat=None,
-           max_iter: int = 50, rtol: float = 1e-13, verbose: bool = False):
+           max_iter: int = 50, rtol: float = 1e-13, verbose: bool = False,
+           reg_lambda: float = 0.0):
     """Damped Newton iteration on the FP64 loss to its stationary point.
 
     Step: solve (H + lam diag(H)) d = -g with lam = 0 unless H is not positive
     definite; backtrack on the loss (Armijo, c = 1e-4).  Stops when the step is
     below rtol relative to theta or the loss no longer decreases."""
     th = _d(theta0).copy()
-    L, g = loss_grad(R, I, m, th, spec, mask, var, flat)
+    L, g = loss_grad(R, I, m, th, spec, mask, var, flat, reg_lambda=reg_lambda)
     for it in range(max_iter):
-        Hm = hessian(R, I, m, th, spec, mask, var, flat)
+        Hm = hessian(R, I, m, th, spec, mask, var, flat, reg_lambda=reg_lambda)
         dH = np.diag(Hm).copy()
         if np.all(dH == 0):
             raise Degenerate("zero Hessian")
@@ -289,7 +336,7 @@ def newton(R, I, m, theta0, spec: LossSpec, mask=None, var=None, flat=None,
         t = 1.0
         slope = float(g @ d)
         while True:
-            Lt, gt = loss_grad(R, I, m, th + t * d, spec, mask, var, flat)
+            Lt, gt = loss_grad(R, I, m, th + t * d, spec, mask, var, flat, reg_lambda=reg_lambda)
             if Lt <= L + 1e-4 * t * slope or t < 1e-12:
                 break
             t *= 0.5

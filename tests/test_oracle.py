@@ -362,3 +362,105 @@ def test_mfv_of_weighted_fit_matches_paper_b08_value():
     med = float(np.median(vals))
     assert gold["median"] - 3 * (gold["median"] - gold["p16"]) < med < \
         gold["median"] + 3 * (gold["p84"] - gold["median"])
+
+
+# --------------------------------------------------- regulariser (Sec. 2.7)
+def _field(H, W, m, seed):
+    """A star-field pair: I = R (*) K_true + B0 + noise, the valid region filled."""
+    rng = np.random.default_rng(seed)
+    R = _star_ref((H, W), 12, 1.5, rng) + 100.0
+    yy, xx = np.mgrid[0:m, 0:m] - m // 2
+    K = np.exp(-(xx ** 2 + yy ** 2) / (2 * 1.2 ** 2))
+    K /= K.sum()
+    th = np.append(K.ravel(), 30.0)
+    I = np.full((H, W), 130.0)
+    h = m // 2
+    I[h:H - h, h:W - h] = _scipy_model(R, th, m) + rng.normal(0, 2.0, (H - 2 * h, W - 2 * h))
+    return {"R": R, "I": I, "theta": th}
+
+
+def test_laplacian_structure_and_quadratic_surface():
+    """Eq. 21: symmetric, rows summing to zero (a constant kernel is not
+    penalised), degree 2/3/4 at corners/edges/interior, B0 row and column zero;
+    for the surface K[a, b] = a^2 + b^2 the discrete Laplacian is 4, so
+    (L theta)_u = -4 at every interior pixel."""
+    m = 5
+    L = oracle.laplacian(m)
+    n = m * m + 1
+    assert L.shape == (n, n) and np.array_equal(L, L.T)
+    assert np.allclose(L.sum(axis=1), 0.0)
+    assert np.all(L[-1] == 0) and np.all(L[:, -1] == 0)
+    deg = np.diag(L)[:-1].reshape(m, m)
+    assert deg[0, 0] == 2 and deg[0, 2] == 3 and deg[2, 2] == 4
+    a, b = np.mgrid[0:m, 0:m]
+    th = np.append((a ** 2 + b ** 2).astype(float).ravel(), 7.0)
+    Lth = (L @ th)[:-1].reshape(m, m)
+    assert np.allclose(Lth[1:-1, 1:-1], -4.0)
+    assert np.all(np.linalg.eigvalsh(L) > -1e-12)
+
+
+def test_regularised_gradient_and_hessian_central_differences():
+    m = 5
+    d = _field(40, 36, m, seed=8)
+    spec = oracle.LossSpec(rho="gauss", noise="ccd", sigma0=4.0, gain=1.3, var_floor=1e-6)
+    rng = np.random.default_rng(8)
+    th = np.full(m * m + 1, 1.0 / (m * m)) * (1 + 0.2 * rng.uniform(-1, 1, m * m + 1))
+    th[-1] = float(np.median(d["I"]))
+    lam = 3.0
+    L0, g = oracle.loss_grad(d["R"], d["I"], m, th, spec, reg_lambda=lam)
+    H = oracle.hessian(d["R"], d["I"], m, th, spec, reg_lambda=lam)
+    for k in (0, 7, 12, m * m):
+        e = np.zeros_like(th)
+        e[k] = 1e-4 * max(1.0, abs(th[k]))
+        Lp, gp = oracle.loss_grad(d["R"], d["I"], m, th + e, spec, reg_lambda=lam)
+        Lm, gm = oracle.loss_grad(d["R"], d["I"], m, th - e, spec, reg_lambda=lam)
+        assert (Lp - Lm) / (2 * e[k]) == pytest.approx(g[k], rel=1e-6, abs=1e-6 * np.max(np.abs(g)))
+        np.testing.assert_allclose((gp - gm) / (2 * e[k]), H[:, k], rtol=1e-5,
+                                   atol=1e-6 * np.max(np.abs(H)))
+
+
+def test_regularised_normal_solve_is_stationary_and_smoother():
+    """The regularised chi^2 minimum has zero regularised gradient, and a larger
+    lam gives a kernel with a smaller Laplacian norm and a larger chi^2."""
+    m = 7
+    d = _field(60, 56, m, seed=9)
+    spec = oracle.LossSpec()
+    L = oracle.laplacian(m)
+    prev = None
+    for lam in (0.0, 1.0, 100.0):
+        th = oracle.normal_solve(d["R"], d["I"], m, reg_lambda=lam)
+        _, g = oracle.loss_grad(d["R"], d["I"], m, th, spec, reg_lambda=lam)
+        scale = np.max(np.abs(oracle.loss_grad(d["R"], d["I"], m, np.zeros_like(th), spec)[1]))
+        assert np.max(np.abs(g)) <= 1e-9 * scale
+        rough = float(np.sum((L @ th) ** 2))
+        chi2 = oracle.loss(d["R"], d["I"], m, th, spec)
+        if prev is not None:
+            assert rough < prev[0] and chi2 > prev[1]
+        prev = (rough, chi2)
+
+
+def test_penalty_is_the_squared_graph_laplacian_of_the_kernel_surface():
+    """Eq. 20 written with array shifts instead of the matrix: (L theta)_u is
+    the sum over the edge-neighbours v of u of (K_u - K_v); the penalty is
+    lam * N_data * sum_u (L theta)_u^2 and B0 does not enter it."""
+    m, lam, n_data = 6, 0.7, 1234
+    rng = np.random.default_rng(5)
+    K = rng.normal(size=(m, m))
+    Lk = np.zeros((m, m))
+    Lk[1:, :] += K[1:, :] - K[:-1, :]
+    Lk[:-1, :] += K[:-1, :] - K[1:, :]
+    Lk[:, 1:] += K[:, 1:] - K[:, :-1]
+    Lk[:, :-1] += K[:, :-1] - K[:, 1:]
+    th = np.append(K.ravel(), 99.0)
+    v, g, Hp = oracle.penalty(th, m, lam, n_data)
+    assert v == pytest.approx(lam * n_data * np.sum(Lk ** 2), rel=1e-12)
+    assert g[-1] == 0 and np.all(Hp[-1] == 0)
+    th2 = th.copy()
+    th2[:-1] += 3.0              # a constant kernel offset is not penalised
+    assert oracle.penalty(th2, m, lam, n_data)[0] == pytest.approx(v, rel=1e-12)
+    d = _field(30, 28, 5, seed=2)
+    t = d["theta"]
+    L1, g1 = oracle.loss_grad(d["R"], d["I"], 5, t, reg_lambda=2.0)
+    L0, g0 = oracle.loss_grad(d["R"], d["I"], 5, t)
+    pv, pg, _ = oracle.penalty(t, 5, 2.0, oracle.ndata((30, 28), 5))
+    assert L1 - L0 == pytest.approx(pv, rel=1e-9) and np.allclose(g1 - g0, pg, rtol=1e-9)
