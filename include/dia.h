@@ -52,7 +52,7 @@ extern "C" {
 #endif
 
 #define DIA_MAX_M 31           /* largest odd kernel side of the fused kernels */
-#define DIA_ABI_VERSION 2
+#define DIA_ABI_VERSION 3
 
 typedef enum {
     DIA_OK = 0,
@@ -152,6 +152,11 @@ typedef struct {
                                   Gauss-Newton Hessian is the preconditioner; 0 = automatic
                                   (about sqrt(1.2e11) / n, between 256 and 1024; 544 at
                                   m = 25) (0) */
+    double reg_lambda;         /* lambda of the kernel regulariser of Sec. 2.7 (Eq. 20):
+                                  minimise L0 + lambda N_data theta^T L^T L theta, L the
+                                  Laplacian of the kernel-pixel graph (Eq. 21, kernel
+                                  pixels sharing an edge are adjacent; B0 is not
+                                  penalised); 0 = off (0) */
 } dia_opts;
 
 typedef struct {
@@ -159,7 +164,8 @@ typedef struct {
     int32_t adam_iters, lbfgs_iters, evals;
     int32_t clip_passes_done;
     int64_t ndata;             /* unmasked valid pixels at the end (N_data) */
-    double loss;               /* final loss, sum over pixels (float64) */
+    double loss;               /* final objective, sum over pixels (float64; with
+                                  reg_lambda > 0 the regulariser of Eq. 20 included) */
     double grad_inf;           /* max |dL/dtheta| / N_data at the end */
     double scale;              /* photometric scale P = sum K (Eq. 3) */
     double b0;                 /* fitted B0 */

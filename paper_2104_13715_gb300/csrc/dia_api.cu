@@ -400,6 +400,7 @@ void fill_opts_default(dia_opts *o) {
     o->stall_iters_diag = 1000;
     o->max_ls_evals = 12;
     o->precond_window = 0;
+    o->reg_lambda = 0.0;
     o->grad_tol = 1e-7;
     o->max_lbfgs_iters = 3000;
     o->max_evals = 20000;
@@ -531,7 +532,8 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         fill_opts_default(&opts);
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.clip_passes < 0 || opts.max_adam_iters < 0 ||
-        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 || opts.precond_window < 0 || opts.init < 0 || opts.init > 2 ||
+        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 || opts.precond_window < 0 ||
+        !(opts.reg_lambda >= 0.0) || !std::isfinite(opts.reg_lambda) || opts.init < 0 || opts.init > 2 ||
         (opts.init == 2 && !opts.theta0) || (opts.init == 1 && !(opts.init_sigma > 0.0)) ||
         !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
@@ -601,6 +603,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             pa.ldp = pc_ldp(n);
             pa.st = c.st;
             pa.eps = 1e-6;
+            pa.reg2 = 2.0 * opts.reg_lambda;
             pa.scale = 1.0 / ((double)(pa.y1 - pa.y0) * (pa.x1 - pa.x0));
             pa.flush = kGnFlushPc;
             PrecondArgs *d_pa = (PrecondArgs *)(c.ws + c.L.pc_args);
@@ -637,6 +640,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     sa.p.stall_iters = opts.stall_iters;
     sa.p.stall_iters_diag = opts.stall_iters_diag;
     sa.p.max_ls = opts.max_ls_evals;
+    sa.p.reg_lambda = opts.reg_lambda;
 
     cudaGraphExec_t gx = nullptr;
     if (opts.use_graph) {

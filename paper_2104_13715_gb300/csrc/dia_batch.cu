@@ -212,6 +212,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.max_adam_iters < 0 || opts.max_evals < 1 ||
         opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 ||
+        !(opts.reg_lambda >= 0.0) || !std::isfinite(opts.reg_lambda) ||
         opts.precond_window < 0 || opts.init < 0 || opts.init > 1 ||
         (opts.init == 1 && !(opts.init_sigma > 0.0)) || !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
@@ -337,6 +338,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
             pa.ldp = pc_ldp(n);
             pa.st = st;
             pa.eps = 1e-6;
+            pa.reg2 = 2.0 * opts.reg_lambda;
             pa.scale = 1.0 / ((double)(pa.y1 - pa.y0) * (pa.x1 - pa.x0));
             pa.flush = kGnFlushPc;
             sa.b.P = pa.P;
@@ -361,6 +363,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         sa.p.stall_iters = opts.stall_iters;
         sa.p.stall_iters_diag = opts.stall_iters_diag;
         sa.p.max_ls = opts.max_ls_evals;
+        sa.p.reg_lambda = opts.reg_lambda;
         sa.n_done = hdr + 2;
         BatchRed &r = reds[i];
         r.part_off = q.part_off;

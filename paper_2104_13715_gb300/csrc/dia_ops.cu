@@ -120,6 +120,7 @@ enum { kActContinue = 0, kActAcceptTrial = 1, kActAcceptLo = 2, kActFail = 3 };
 struct StepShared {
     double red[kStepThreads / 32];
     double gt[1024];          // scaled gradient at the trial point
+    double lt[1024];          // L theta of the regulariser (kernel pixels)
     double v[4][kHistMax];    // compact-form vectors over the history
     int act, finish_status, copy_glo;
     double new_alpha;
@@ -174,6 +175,37 @@ __device__ void finish(const StepArgs &a, int status, int reason) {
     }
 }
 
+// Graph Laplacian of the kernel surface (Eq. 21) applied to x at kernel pixel
+// k = r * mk + c: sum over its edge neighbours j of (x_k - x_j).
+__device__ __forceinline__ double lap_apply(const double *x, int k, int mk) {
+    const int r = k / mk, c = k - r * mk;
+    const double t = x[k];
+    double v = 0.0;
+    if (r > 0) v += t - x[k - mk];
+    if (r < mk - 1) v += t - x[k + mk];
+    if (c > 0) v += t - x[k - 1];
+    if (c < mk - 1) v += t - x[k + 1];
+    return v;
+}
+
+// Regulariser of Eq. 20 at the evaluated point (trial), in the optimiser's
+// 1/N_data scale: returns lambda |L theta|^2 and adds 2 lambda L^T L theta
+// (L symmetric) to the scaled gradient sm.gt.  B0 is not penalised.
+__device__ double add_penalty(const StepArgs &a, StepShared &sm) {
+    const int mk = a.mk, nk = mk * mk;
+    const double lam = a.p.reg_lambda;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nk; k += kStepThreads) {
+        const double v = lap_apply(a.b.trial, k, mk);
+        sm.lt[k] = v;
+        s += v * v;
+    }
+    const double pen = block_sum(s, sm.red);   // also orders the sm.lt writes
+    for (int k = threadIdx.x; k < nk; k += kStepThreads) sm.gt[k] += 2.0 * lam * lap_apply(sm.lt, k, mk);
+    __syncthreads();
+    return lam * pen;
+}
+
 // Diagonal preconditioner from the curvature sums of the last evaluation:
 // kernel pixels ~ 1/sum(kappa R^2), B0 ~ 1/sum(kappa) (Gauss-Newton diagonal
 // with the kernel-pixel entries approximated by the centre pixel).
@@ -182,8 +214,18 @@ __device__ void update_precond(const StepArgs &a) {
     const double pk = (dk > 0.0 && isfinite(dk)) ? 1.0 / dk : 1.0;
     const double pb = (db > 0.0 && isfinite(db)) ? 1.0 / db : 1.0;
     const double N = a.red[a.n + 1];
-    for (int k = threadIdx.x; k < a.n; k += kStepThreads)
-        a.b.pdiag[k] = N * ((k == a.n - 1) ? pb : pk);   // the loss is scaled by 1/N
+    const int mk = a.mk;
+    for (int k = threadIdx.x; k < a.n; k += kStepThreads) {
+        double p = N * ((k == a.n - 1) ? pb : pk);   // the loss is scaled by 1/N
+        if (a.p.reg_lambda > 0.0 && k < a.n - 1) {
+            // plus the regulariser's diagonal 2 lambda (L^T L)_kk = 2 lambda d (d + 1),
+            // d the number of edge neighbours of kernel pixel k
+            const int r = k / mk, c = k - r * mk;
+            const int d = (r > 0) + (r < mk - 1) + (c > 0) + (c < mk - 1);
+            p = 1.0 / (1.0 / p + 2.0 * a.p.reg_lambda * d * (d + 1));
+        }
+        a.b.pdiag[k] = p;
+    }
 }
 
 // A new L-BFGS direction is needed at the accepted point: P g (and P y_new
@@ -403,14 +445,15 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
         return;
     }
     const double invN = 1.0 / N;
-    const double Lt = a.red[0] * invN;
+    double Lt = a.red[0] * invN;
     const bool first_eval = *((volatile int *)&st->evals) == 0;   // read before the update below
-    bool bad = !isfinite(Lt);
-    for (int k = tid; k < n; k += kStepThreads) {
-        const double g = a.red[1 + k] * invN;
-        sm.gt[k] = g;
-        bad |= !isfinite(g);
+    for (int k = tid; k < n; k += kStepThreads) sm.gt[k] = a.red[1 + k] * invN;
+    if (p.reg_lambda > 0.0) {
+        __syncthreads();
+        Lt += add_penalty(a, sm);
     }
+    bool bad = !isfinite(Lt);
+    for (int k = tid; k < n; k += kStepThreads) bad |= !isfinite(sm.gt[k]);
     const int nbad = __syncthreads_or(bad);
     if (tid == 0) {
         st->evals += 1;

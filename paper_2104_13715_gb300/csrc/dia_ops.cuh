@@ -56,6 +56,7 @@ struct FitState {
 struct OptParams {
     double lr_kernel, lr_b0, beta1, beta2, adam_eps, switch_tol;
     double rel_tol, grad_tol;
+    double reg_lambda;   // kernel regulariser of Eq. 20 (0 = off)
     int max_adam, history, max_lbfgs, max_evals, stall_iters, stall_iters_diag, max_ls;
 };
 
@@ -131,6 +132,7 @@ struct PrecondArgs {
     int ldp;
     FitState *st;         // receives pc_ok
     double eps;           // relative diagonal regularisation of H
+    double reg2;          // 2 lambda: H += 2 lambda L^T L, the regulariser of Eq. 20 (0 = off)
     double scale;         // H is scaled by this (1 / window pixels for the preconditioner)
     int flush;            // shared-memory batches of 32 px per float64 flush
     int wmap_ld;

@@ -66,6 +66,30 @@ __device__ __forceinline__ void gn_block(int b, int nt, int &U, int &V) {
     V = U + b;
 }
 
+// Entry (u, v) of the Laplacian of the kernel-pixel graph (Eq. 21): the number
+// of edge neighbours on the diagonal, -1 for pixels sharing an edge.
+__device__ __forceinline__ int lap_entry(int u, int v, int mk) {
+    const int ru = u / mk, cu = u - ru * mk;
+    if (u == v) return (ru > 0) + (ru < mk - 1) + (cu > 0) + (cu < mk - 1);
+    const int rv = v / mk, cv = v - rv * mk;
+    return (abs(ru - rv) + abs(cu - cv) == 1) ? -1 : 0;
+}
+
+// 2 lambda (L^T L)_uv, the Hessian of the regulariser of Eq. 20 in the
+// optimiser's 1/N_data scale; (L^T L)_uv = sum over k in {u} and the
+// neighbours of u of L_uk L_kv (L symmetric).  Zero for B0.
+__device__ __forceinline__ double reg_hess(const PrecondArgs &a, int u, int v) {
+    const int mk = a.m, nk = mk * mk;
+    if (a.reg2 == 0.0 || u >= nk || v >= nk) return 0.0;
+    const int r = u / mk, c = u - r * mk;
+    int s = lap_entry(u, u, mk) * lap_entry(u, v, mk);
+    if (r > 0) s -= lap_entry(u - mk, v, mk);
+    if (r < mk - 1) s -= lap_entry(u + mk, v, mk);
+    if (c > 0) s -= lap_entry(u - 1, v, mk);
+    if (c < mk - 1) s -= lap_entry(u + 1, v, mk);
+    return a.reg2 * s;
+}
+
 __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, int npairs) {
     __shared__ __align__(16) float sA[kGnKB][kGnT], sB[kGnKB][kGnT];
     __shared__ int offU[kGnT], offV[kGnT];
@@ -167,7 +191,7 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
                     if (u >= n || w >= n)
                         t = (u == w) ? 1.0 : 0.0;
                     else
-                        t = v * inv * ((u == w) ? 1.0 + a.eps : 1.0);
+                        t = v * inv * ((u == w) ? 1.0 + a.eps : 1.0) + reg_hess(a, u, w);
                     a.A64[(size_t)u * np + w] = t;
                 }
             }
@@ -205,7 +229,7 @@ __global__ void fill_kernel(const PrecondArgs *pas, int npairs) {
                 double s = 0.0;
                 for (int c = 0; c < nch; ++c)
                     s += a.part[((size_t)c * nblk + b) * (kGnT * kGnT) + il * kGnT + jl];
-                t = s * inv * ((u == w) ? 1.0 + a.eps : 1.0);
+                t = s * inv * ((u == w) ? 1.0 + a.eps : 1.0) + reg_hess(a, u, w);
                 if (a.F_out) a.F_out[(size_t)u * n + w] = t;
             }
             a.A64[e] = t;

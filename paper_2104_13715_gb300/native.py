@@ -51,7 +51,7 @@ class Opts(ctypes.Structure):
                 ("timeout_s", ctypes.c_double), ("stall_iters", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("stall_iters_diag", ctypes.c_int32), ("max_ls_evals", ctypes.c_int32),
-                ("precond_window", ctypes.c_int32)]
+                ("precond_window", ctypes.c_int32), ("reg_lambda", ctypes.c_double)]
 
 
 class FisherInfo(ctypes.Structure):
@@ -113,7 +113,7 @@ _SIGS = {
 }
 
 
-ABI_VERSION = 2   # the struct layouts below match include/dia.h of this version
+ABI_VERSION = 3   # the struct layouts below match include/dia.h of this version
 
 
 def _load():
