@@ -13,7 +13,11 @@ Pieces (each cites the passage it follows):
   named in Sec. 2.4), by direct loops in FP64.
 * :func:`gram`, :func:`normal_solve` -- the Bramich (2008) normal equations
   for the fixed-variance chi^2 (Sec. 1 and Sec. 2.1): A = sum w phi phi^T,
-  b = sum w phi I with phi_p = [R window of p, 1], solved by Cholesky.
+  b = sum w phi I with phi_p = [R window of p, background basis at p], solved
+  by Cholesky.
+* :func:`background_basis` -- the polynomial background of Sec. 2.6 (Eq. 18)
+  in the normalised coordinates of Eq. 19; degree 0 is the constant B0.  Every
+  function taking theta reads the degree from its length, m*m + (d+1)(d+2)/2.
 * :func:`laplacian`, :func:`penalty` -- the kernel regulariser of Sec. 2.7
   (Eq. 20, Eq. 21): lam * N_data * theta^T L^T L theta with L the Laplacian of
   the kernel-pixel graph (4-connectivity); loss_grad, normal_solve, hessian
@@ -26,7 +30,11 @@ Pieces (each cites the passage it follows):
   difference image I - M and the kappa-sigma clipping of B08 (Sec. 2.4,
   Sec. 4.2).
 
-Conventions: theta = [K row-major over (row offset, column offset), B0];
+Conventions: theta = [K row-major over (row offset, column offset), b] with b
+= [B0] or the coefficients b_00, b_01, ..., b_0d, b_10, ..., b_d0 of Eq. 18 (the
+power of xi running fastest); eta = (x - x_c)/N_x, xi = (y - y_c)/N_y with x
+the column and y the row of the full image, x_c = (W - 1)/2, y_c = (H - 1)/2,
+N_x = W, N_y = H;
 ``K[a, b]`` multiplies ``R[i - h + a, j - h + b]`` for the target pixel
 (i, j), with h = m // 2, so ``a = b = h`` is the kernel centre and a +1 pixel
 shift of the target in x and y gives a delta at ``a = b = h - 1`` (Sec. 3.4
@@ -74,12 +82,12 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         up = ctypes.POINTER(ctypes.c_uint8)
         i = ctypes.c_int
-        lib.oracle_model.argtypes = [dp, i, i, i, i, dp, dp, i]
+        lib.oracle_model.argtypes = [dp, i, i, i, i, i, dp, dp, i]
         lib.oracle_model.restype = i
         lib.oracle_pixel_terms.argtypes = [dp, up, dp, dp, i, i, i, i, dp, dp,
                                            dp, dp, dp, dp]
         lib.oracle_pixel_terms.restype = i
-        lib.oracle_loss_grad.argtypes = [dp, dp, up, dp, dp, i, i, i, i, dp, dp,
+        lib.oracle_loss_grad.argtypes = [dp, dp, up, dp, dp, i, i, i, i, i, dp, dp,
                                          dp, dp, i]
         lib.oracle_loss_grad.restype = i
         lib.oracle_ndata.argtypes = [up, i, i, i, i]
@@ -132,16 +140,48 @@ def _shape(R, m):
     return H, W
 
 
-def n_params(m: int) -> int:
-    return m * m + 1
+def n_background(deg: int) -> int:
+    """Coefficients of the degree-d polynomial of Eq. 18: (d+1)(d+2)/2."""
+    return (deg + 1) * (deg + 2) // 2
 
 
-def laplacian(m: int) -> np.ndarray:
+def n_params(m: int, deg: int = 0) -> int:
+    return m * m + n_background(deg)
+
+
+def degree_of(theta, m) -> int:
+    """Background degree implied by len(theta) = m*m + (d+1)(d+2)/2."""
+    nb = len(theta) - m * m
+    for d in range(10):
+        if n_background(d) == nb:
+            return d
+    raise ValueError(f"theta of length {len(theta)} fits no background degree for m={m}")
+
+
+def background_basis(shape, m, deg):
+    """The basis eta^p xi^q of Eq. 18 over the valid region, shape (Hv, Wv,
+    (d+1)(d+2)/2), in the coefficient order of theta; eta, xi of Eq. 19 on the
+    full image's pixel grid (column x, row y), centred at ((W-1)/2, (H-1)/2)
+    and scaled by W and H."""
+    H, W = shape
+    h = m // 2
+    y = np.arange(h, H - h, dtype=np.float64)
+    x = np.arange(h, W - h, dtype=np.float64)
+    xi = (y - 0.5 * (H - 1)) / H
+    eta = (x - 0.5 * (W - 1)) / W
+    cols = []
+    for p in range(deg + 1):
+        for q in range(deg - p + 1):
+            cols.append(np.outer(xi ** q, eta ** p))
+    return np.stack(cols, axis=-1)
+
+
+def laplacian(m: int, deg: int = 0) -> np.ndarray:
     """Laplacian matrix of the kernel-pixel graph (Sec. 2.7, Eq. 21), of size
-    (m*m + 1) x (m*m + 1): L[u, u] = number of kernel pixels adjacent to u,
+    n_params(m, deg) square: L[u, u] = number of kernel pixels adjacent to u,
     L[u, v] = -1 for adjacent u, v (sharing an edge: 4-connectivity), zero in
-    the B0 row and column."""
-    n = n_params(m)
+    the rows and columns of the background coefficients."""
+    n = n_params(m, deg)
     L = np.zeros((n, n))
     for a in range(m):
         for b in range(m):
@@ -157,9 +197,9 @@ def laplacian(m: int) -> np.ndarray:
 def penalty(theta, m, lam, n_data):
     """The regulariser of Eq. 20, lam * N_data * theta^T L^T L theta, with its
     gradient and Hessian (L of Eq. 21)."""
-    L = laplacian(m)
-    LtL = L.T @ L
     th = np.asarray(theta, dtype=np.float64)
+    L = laplacian(m, degree_of(th, m))
+    LtL = L.T @ L
     c = lam * n_data
     return c * th @ LtL @ th, 2.0 * c * LtL @ th, 2.0 * c * LtL
 
@@ -172,13 +212,15 @@ def ndata(shape, m, mask=None) -> int:
 
 
 def model(R, theta, m, nthreads: int = 0) -> np.ndarray:
-    """Model image M = R (x) K + B0 over the valid region (Eq. 2)."""
+    """Model image M = R (x) K + B over the valid region (Eq. 2; B the constant
+    B0 or the polynomial of Eq. 18, by the length of theta)."""
     R = _d(R)
     H, W = _shape(R, m)
     th = _d(theta)
     h = m // 2
     out = np.empty((H - 2 * h, W - 2 * h), dtype=np.float64)
-    rc = _load().oracle_model(_ptr(R), H, W, W, m, _ptr(th), _ptr(out), nthreads)
+    rc = _load().oracle_model(_ptr(R), H, W, W, m, degree_of(th, m), _ptr(th), _ptr(out),
+                              nthreads)
     if rc:
         raise ValueError("oracle_model: bad arguments")
     return out
@@ -206,21 +248,21 @@ def loss_grad(R, I, m, theta, spec: LossSpec = None, mask=None, var=None, flat=N
               nthreads: int = 0, reg_lambda: float = 0.0):
     """FP64 loss L(theta) and gradient dL/dtheta (Eq. 8 / Eq. 13, summed over the
     unmasked valid pixels; with reg_lambda > 0, plus the regulariser of Eq. 20).
-    Returns (L, grad[m*m+1])."""
+    Returns (L, grad[len(theta)])."""
     spec = spec or LossSpec()
     R = _d(R)
     I = _d(I)
     H, W = _shape(R, m)
     assert I.shape == R.shape
     th = _d(theta)
-    assert th.shape == (n_params(m),)
+    deg = degree_of(th, m)
     loss = np.zeros(1)
-    grad = np.zeros(n_params(m))
+    grad = np.zeros(n_params(m, deg))
     mk = _u8(mask)
     vv = _d(var)
     ff = _d(flat)
     rc = _load().oracle_loss_grad(_ptr(R), _ptr(I), _ptr(mk, ctypes.c_uint8), _ptr(vv),
-                                  _ptr(ff), H, W, W, m, _ptr(spec.params()), _ptr(th),
+                                  _ptr(ff), H, W, W, m, deg, _ptr(spec.params()), _ptr(th),
                                   _ptr(loss), _ptr(grad), nthreads)
     if rc:
         raise ValueError(f"oracle_loss_grad failed ({rc})")
@@ -238,24 +280,27 @@ def _windows(R, m):
     return np.lib.stride_tricks.sliding_window_view(R, (m, m))
 
 
-def gram(R, m, weights, rhs=None, block_rows: int = 64):
+def gram(R, m, weights, rhs=None, block_rows: int = 64, deg: int = 0):
     """A = sum_p w_p phi_p phi_p^T and (optionally) b = sum_p rhs_p phi_p, where
-    phi_p = [R window of valid pixel p (m*m, row-major), 1].  ``weights`` and
-    ``rhs`` are arrays over the valid region.  This is the B08 normal matrix
-    when w = 1/sigma^2 and rhs = I/sigma^2 (Sec. 1)."""
+    phi_p = [R window of valid pixel p (m*m, row-major), background basis at p
+    (Eq. 18; [1] for degree 0)].  ``weights`` and ``rhs`` are arrays over the
+    valid region.  This is the B08 normal matrix when w = 1/sigma^2 and
+    rhs = I/sigma^2 (Sec. 1)."""
     R = _d(R)
     H, W = _shape(R, m)
     h = m // 2
     Hv, Wv = H - 2 * h, W - 2 * h
-    n = n_params(m)
+    n = n_params(m, deg)
+    nk = m * m
+    basis = background_basis((H, W), m, deg)
     win = _windows(R, m)
     A = np.zeros((n, n))
     b = np.zeros(n) if rhs is not None else None
     for y0 in range(0, Hv, block_rows):
         y1 = min(Hv, y0 + block_rows)
         phi = np.empty(((y1 - y0) * Wv, n))
-        phi[:, : n - 1] = win[y0:y1].reshape(-1, m * m)
-        phi[:, n - 1] = 1.0
+        phi[:, :nk] = win[y0:y1].reshape(-1, m * m)
+        phi[:, nk:] = basis[y0:y1].reshape(-1, n - nk)
         w = np.asarray(weights[y0:y1], dtype=np.float64).reshape(-1)
         A += (phi * w[:, None]).T @ phi
         if rhs is not None:
@@ -273,7 +318,7 @@ def _valid(a, m):
 
 
 def normal_solve(R, I, m, mask=None, var=None, var_scalar: float = 1.0,
-                 reg_lambda: float = 0.0):
+                 reg_lambda: float = 0.0, deg: int = 0):
     """B08 linear least squares for the fixed-variance chi^2: solve A theta = b
     by Cholesky (Sec. 1; Sec. 2.1 'fixed estimates for sigma').  With
     reg_lambda > 0 the minimum of chi^2/2 + the regulariser of Eq. 20:
@@ -285,9 +330,9 @@ def normal_solve(R, I, m, mask=None, var=None, var_scalar: float = 1.0,
     w = np.ones_like(Iv) / var_scalar if var is None else 1.0 / _valid(_d(var), m)
     if mask is not None:
         w = w * (_valid(np.asarray(mask), m) != 0)
-    A, b = gram(R, m, w, w * Iv)
+    A, b = gram(R, m, w, w * Iv, deg=deg)
     if reg_lambda:
-        A = A + penalty(np.zeros(n_params(m)), m, reg_lambda, ndata(R.shape, m, mask))[2]
+        A = A + penalty(np.zeros(n_params(m, deg)), m, reg_lambda, ndata(R.shape, m, mask))[2]
     try:
         L = np.linalg.cholesky(A)
     except np.linalg.LinAlgError as e:
@@ -302,7 +347,7 @@ def hessian(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None,
     that of the regulariser of Eq. 20 when reg_lambda > 0."""
     M = model(R, theta, m)
     _, _, d2, _ = pixel_terms(I, M, m, spec, mask, var, flat)
-    Hm = gram(R, m, d2)
+    Hm = gram(R, m, d2, deg=degree_of(theta, m))
     if reg_lambda:
         Hm = Hm + penalty(theta, m, reg_lambda, ndata(np.shape(R), m, mask))[2]
     return Hm
@@ -352,16 +397,19 @@ def newton(R, I, m, theta0, spec: LossSpec, mask=None, var=None, flat=None,
 
 
 def fit(R, I, m, spec: LossSpec = None, mask=None, var=None, flat=None,
-        theta0=None, max_iter: int = 50):
+        theta0=None, max_iter: int = 50, deg: int = 0):
     """The minimiser of the loss.  Fixed-variance Gaussian: the B08 normal
     solve.  Otherwise: Newton from theta0 (default: the normal solve with the
-    scalar variance, which is the B08 first iteration)."""
+    scalar variance, which is the B08 first iteration).  ``deg``: background
+    degree (Eq. 18) when theta0 is not given."""
     spec = spec or LossSpec()
+    if theta0 is not None:
+        deg = degree_of(theta0, m)
     if spec.rho == "gauss" and spec.noise == "fixed":
-        return normal_solve(R, I, m, mask, var, spec.var)
+        return normal_solve(R, I, m, mask, var, spec.var, deg=deg)
     if theta0 is None:
         theta0 = normal_solve(R, I, m, mask, var if spec.noise == "fixed" else None,
-                              spec.var if spec.noise == "fixed" else 1.0)
+                              spec.var if spec.noise == "fixed" else 1.0, deg=deg)
     return newton(R, I, m, theta0, spec, mask, var, flat, max_iter=max_iter)
 
 
@@ -387,10 +435,10 @@ def sigma_clip(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None,
 
 
 def fit_clipped(R, I, m, spec: LossSpec, mask=None, var=None, flat=None,
-                passes: int = 3, kappa: float = 5.0, theta0=None):
+                passes: int = 3, kappa: float = 5.0, theta0=None, deg: int = 0):
     """Fit, then `passes` times: clip at kappa and refit from the current theta.
     Returns (theta, mask)."""
-    th = fit(R, I, m, spec, mask, var, flat, theta0)
+    th = fit(R, I, m, spec, mask, var, flat, theta0, deg=deg)
     mk = None if mask is None else np.array(mask, np.uint8)
     for _ in range(passes):
         mk = sigma_clip(R, I, m, th, spec, mk, var, flat, kappa)

@@ -8,21 +8,28 @@
  *
  * What it computes, by direct nested loops in double precision:
  *
- *   model image     M_ij = sum_{l,m} K_lm R_(i+l)(j+m) + B0           (Sec. 2.1, Eq. 2)
+ *   model image     M_ij = sum_{l,m} K_lm R_(i+l)(j+m) + B_ij         (Sec. 2.1, Eq. 2)
  *                   with centred offsets l,m in [-h, h], kernel side 2h+1,
  *                   defined only where the whole kernel footprint lies
  *                   inside R, i.e. i,j in [h, N-h)                     (Sec. 2.1, N_data)
+ *   background      B_ij = B0 (degree 0), or the polynomial of degree d
+ *                   B = sum_{p=0..d} sum_{q=0..d-p} b_pq eta^p xi^q     (Sec. 2.6, Eq. 18)
+ *                   eta = (j - x_c)/N_x, xi = (i - y_c)/N_y            (Sec. 2.6, Eq. 19)
+ *                   with x = column j, y = row i of the full image,
+ *                   x_c = (W-1)/2, y_c = (H-1)/2, N_x = W, N_y = H
  *   pixel variance  fixed map / CCD  s0^2/F^2 + M/(G F)                (Sec. 2.1, Eq. 6)
  *                   EMCCD  E M/(G_tot F)                                (Sec. 2.1, Eq. 7)
  *   pixel loss      rho(z) + ln(sigma), z = (I - M)/sigma               (Sec. 2.3, Eq. 8;
  *                   rho = z^2/2 (Gaussian), Huber (Sec. 2.4, Eq. 12),   Sec. 2.4, Eq. 13)
  *                   Cauchy ln(1+z^2) (a Student-t drop-in, Sec. 2.4)
  *   total loss      L = sum over unmasked valid pixels
- *   gradient        dL/dK_lm = sum_p dl/dM_p R_(p+lm),  dL/dB0 = sum_p dl/dM_p
+ *   gradient        dL/dK_lm = sum_p dl/dM_p R_(p+lm),  dL/db_pq = sum_p dl/dM_p eta^p xi^q
  *
  * The per-pixel curvature d2l/dM2 is exported too: because M is linear in
- * theta = [K, B0], the Hessian of L is sum_p (d2l/dM2)_p phi_p phi_p^T with
- * phi_p = [R window of p, 1]; the Python side forms that product.
+ * theta = [K, b], the Hessian of L is sum_p (d2l/dM2)_p phi_p phi_p^T with
+ * phi_p = [R window of p, background basis at p]; the Python side forms that
+ * product.  theta holds K row-major, then b_00, b_01, ..., b_0d, b_10, ...,
+ * b_d0 (q fastest, the order of the double sum of Eq. 18).
  *
  * Readings of points the paper leaves open (the same ones the CUDA path takes):
  *   - with a fixed variance the ln(sigma) term is a constant and is dropped;
@@ -137,19 +144,38 @@ static void pixel_terms(const spec_t *s, double I, double M, double vmap, double
     if (zout) *zout = z;
 }
 
-static double model_at(const double *R, int ld, int m, const double *theta, int i, int j)
+/* Number of background coefficients of degree d: (d+1)(d+2)/2. */
+static int n_background(int deg) { return (deg + 1) * (deg + 2) / 2; }
+
+/* Background basis functions eta^p xi^q at full-image pixel (i, j), in the
+ * coefficient order (Eq. 18, Eq. 19). */
+static void background_basis(int deg, int H, int W, int i, int j, double *phi)
+{
+    double eta = (j - 0.5 * (W - 1)) / (double)W;
+    double xi = (i - 0.5 * (H - 1)) / (double)H;
+    int k = 0;
+    for (int p = 0; p <= deg; ++p)
+        for (int q = 0; q <= deg - p; ++q)
+            phi[k++] = pow(eta, p) * pow(xi, q);
+}
+
+static double model_at(const double *R, int H, int W, int ld, int m, int deg,
+                       const double *theta, int i, int j)
 {
     int h = m / 2;
-    double acc = 0.0;
+    double acc = 0.0, phi[64];
     for (int a = 0; a < m; ++a)
         for (int b = 0; b < m; ++b)
             acc += theta[a * m + b] * R[(size_t)(i - h + a) * ld + (j - h + b)];
-    return acc + theta[m * m];
+    background_basis(deg, H, W, i, j, phi);
+    for (int k = 0; k < n_background(deg); ++k) acc += theta[m * m + k] * phi[k];
+    return acc;
 }
 
 static int check_args(int H, int W, int ld, int m)
 {
     if (m < 1 || (m % 2) == 0) return -1;
+    if (W < 1 || H < 1) return -1;
     if (H < m || W < m || ld < W) return -1;
     return 0;
 }
@@ -164,16 +190,16 @@ static void set_threads(int nthreads)
 }
 
 /* M over the valid region, row-major (H-2h) x (W-2h). */
-int oracle_model(const double *R, int H, int W, int ld, int m, const double *theta,
+int oracle_model(const double *R, int H, int W, int ld, int m, int deg, const double *theta,
                  double *M_out, int nthreads)
 {
-    if (check_args(H, W, ld, m)) return -1;
+    if (check_args(H, W, ld, m) || deg < 0 || deg > 9) return -1;
     int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h;
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int y = 0; y < Hv; ++y)
         for (int x = 0; x < Wv; ++x)
-            M_out[(size_t)y * Wv + x] = model_at(R, ld, m, theta, y + h, x + h);
+            M_out[(size_t)y * Wv + x] = model_at(R, H, W, ld, m, deg, theta, y + h, x + h);
     return 0;
 }
 
@@ -208,15 +234,16 @@ int oracle_pixel_terms(const double *I, const uint8_t *mask, const double *var,
     return 0;
 }
 
-/* Loss and gradient (m*m + 1 entries: K row-major, then B0) at theta. */
+/* Loss and gradient (m*m + (d+1)(d+2)/2 entries: K row-major, then the
+ * background coefficients) at theta. */
 int oracle_loss_grad(const double *R, const double *I, const uint8_t *mask,
                      const double *var, const double *flat, int H, int W, int ld, int m,
-                     const double *params, const double *theta, double *loss_out,
+                     int deg, const double *params, const double *theta, double *loss_out,
                      double *grad_out, int nthreads)
 {
-    if (check_args(H, W, ld, m)) return -1;
+    if (check_args(H, W, ld, m) || deg < 0 || deg > 9) return -1;
     spec_t s = read_spec(params);
-    int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h, n = m * m + 1;
+    int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h, nbg = n_background(deg), n = m * m + nbg;
     double *row_loss = (double *)calloc((size_t)Hv, sizeof(double));
     double *row_grad = (double *)calloc((size_t)Hv * n, sizeof(double));
     if (!row_loss || !row_grad) {
@@ -234,7 +261,7 @@ int oracle_loss_grad(const double *R, const double *I, const uint8_t *mask,
             int j = x + h;
             size_t q = (size_t)i * ld + j;
             if (mask && mask[q] == 0) continue;
-            double M = model_at(R, ld, m, theta, i, j);
+            double M = model_at(R, H, W, ld, m, deg, theta, i, j), phi[64];
             double e, g1;
             double vm = var ? var[q] : s.var_scalar;
             double F = flat ? flat[q] : 1.0;
@@ -243,7 +270,8 @@ int oracle_loss_grad(const double *R, const double *I, const uint8_t *mask,
             for (int a = 0; a < m; ++a)
                 for (int b = 0; b < m; ++b)
                     gr[a * m + b] += g1 * R[(size_t)(i - h + a) * ld + (j - h + b)];
-            gr[m * m] += g1;
+            background_basis(deg, H, W, i, j, phi);
+            for (int k = 0; k < nbg; ++k) gr[m * m + k] += g1 * phi[k];
         }
         row_loss[y] = ls;
     }

@@ -464,3 +464,95 @@ def test_penalty_is_the_squared_graph_laplacian_of_the_kernel_surface():
     L0, g0 = oracle.loss_grad(d["R"], d["I"], 5, t)
     pv, pg, _ = oracle.penalty(t, 5, 2.0, oracle.ndata((30, 28), 5))
     assert L1 - L0 == pytest.approx(pv, rel=1e-9) and np.allclose(g1 - g0, pg, rtol=1e-9)
+
+
+# ------------------------------------------- polynomial background (Sec. 2.6)
+def test_background_basis_values_by_hand():
+    """Eq. 18-19 at hand-worked pixels of a 9 x 13 image (m = 3, d = 2): the
+    image centre (row 4, column 6) has eta = xi = 0; the first valid pixel
+    (row 1, column 1) has eta = (1 - 6)/13, xi = (1 - 4)/9; the coefficient
+    order is b_00, b_01, b_02, b_10, b_11, b_20 (power of xi fastest)."""
+    Bs = oracle.background_basis((9, 13), 3, 2)
+    assert Bs.shape == (7, 11, 6)
+    np.testing.assert_allclose(Bs[3, 5], [1, 0, 0, 0, 0, 0], atol=0)
+    eta, xi = -5.0 / 13.0, -1.0 / 3.0
+    np.testing.assert_allclose(Bs[0, 0], [1, xi, xi * xi, eta, eta * xi, eta * eta],
+                               rtol=1e-15)
+    assert oracle.n_background(0) == 1 and oracle.n_background(3) == 10
+    assert oracle.degree_of(np.zeros(9 + 6), 3) == 2
+    with pytest.raises(ValueError):
+        oracle.degree_of(np.zeros(9 + 5), 3)
+
+
+def _poly_image(H, W, m, coef, deg):
+    """Eq. 18 written directly over the valid region (row y, column x)."""
+    h = m // 2
+    y, x = np.mgrid[h:H - h, h:W - h].astype(float)
+    eta, xi = (x - (W - 1) / 2) / W, (y - (H - 1) / 2) / H
+    out = np.zeros_like(x)
+    k = 0
+    for p in range(deg + 1):
+        for q in range(deg - p + 1):
+            out += coef[k] * eta ** p * xi ** q
+            k += 1
+    return out
+
+
+@pytest.mark.parametrize("deg", [0, 1, 3])
+def test_model_is_correlation_plus_polynomial(deg):
+    rng = np.random.default_rng(12 + deg)
+    H, W, m = 17, 21, 5
+    R = rng.normal(size=(H, W))
+    nb = oracle.n_background(deg)
+    th = rng.normal(size=m * m + nb)
+    M = oracle.model(R, th, m)
+    ref = _scipy_model(np.asarray(R), np.append(th[:m * m], 0.0), m) + \
+        _poly_image(H, W, m, th[m * m:], deg)
+    np.testing.assert_allclose(M, ref, rtol=0, atol=1e-12)
+
+
+def test_polynomial_background_gradient_and_hessian_central_differences():
+    m, deg = 5, 2
+    d = _field(40, 44, m, seed=13)
+    spec = oracle.LossSpec(rho="huber", noise="ccd", sigma0=4.0, gain=1.3, var_floor=1e-6)
+    rng = np.random.default_rng(13)
+    th = np.concatenate([np.full(m * m, 1.0 / (m * m)), [float(np.median(d["I"])), 3.0, -2.0,
+                                                         5.0, 1.5, -4.0]])
+    th[:m * m] *= 1 + 0.2 * rng.uniform(-1, 1, m * m)
+    L0, g = oracle.loss_grad(d["R"], d["I"], m, th, spec)
+    H = oracle.hessian(d["R"], d["I"], m, th, spec)
+    assert g.shape == (m * m + 6,) and H.shape == (m * m + 6, m * m + 6)
+    for k in (3, m * m, m * m + 1, m * m + 3, m * m + 5):
+        e = np.zeros_like(th)
+        e[k] = 1e-4 * max(1.0, abs(th[k]))
+        Lp, gp = oracle.loss_grad(d["R"], d["I"], m, th + e, spec)
+        Lm, gm = oracle.loss_grad(d["R"], d["I"], m, th - e, spec)
+        assert (Lp - Lm) / (2 * e[k]) == pytest.approx(g[k], rel=1e-6, abs=1e-6 * np.max(np.abs(g)))
+        np.testing.assert_allclose((gp - gm) / (2 * e[k]), H[:, k], rtol=1e-5,
+                                   atol=1e-6 * np.max(np.abs(H)))
+
+
+@pytest.mark.parametrize("deg", [1, 2, 3])
+def test_normal_solve_recovers_an_injected_polynomial_background(deg):
+    """Noiseless target I = R (x) K + B(x, y), B a degree-d polynomial written
+    from Eq. 18 in the test: the normal solve of degree d returns K and every
+    coefficient; a degree-0 fit of the same pair cannot."""
+    rng = np.random.default_rng(20 + deg)
+    H, W, m = 48, 52, 5
+    R = _star_ref((H, W), 15, 1.4, rng) + 50.0
+    yy, xx = np.mgrid[0:m, 0:m] - m // 2
+    K = np.exp(-(xx ** 2 + yy ** 2) / 2.0)
+    K *= 1.3 / K.sum()
+    nb = oracle.n_background(deg)
+    coef = rng.uniform(-40, 40, nb)
+    coef[0] = 25.0
+    I = np.zeros((H, W))
+    h = m // 2
+    I[h:H - h, h:W - h] = _scipy_model(R, np.append(K.ravel(), 0.0), m) + \
+        _poly_image(H, W, m, coef, deg)
+    th = oracle.normal_solve(R, I, m, deg=deg)
+    np.testing.assert_allclose(th[:m * m], K.ravel(), rtol=0, atol=1e-9)
+    np.testing.assert_allclose(th[m * m:], coef, rtol=0, atol=1e-7 * np.max(np.abs(coef)))
+    th0 = oracle.normal_solve(R, I, m)
+    assert np.max(np.abs(oracle.diff_image(R, I, m, th0))) > 1e-3
+    assert np.max(np.abs(oracle.diff_image(R, I, m, th))) < 1e-8
