@@ -4,7 +4,9 @@
  * The library fits the model image of Bramich (2008) as used by PyTorchDIA
  * (arXiv 2104.13715):
  *
- *     M_ij = sum_{l,m} K_lm R_(i+l)(j+m) + B0                 (Sec. 2.1, Eq. 2)
+ *     M_ij = sum_{l,m} K_lm R_(i+l)(j+m) + B_ij               (Sec. 2.1, Eq. 2)
+ *
+ * with a constant background B_ij = B0 or the polynomial of Sec. 2.6 (Eq. 18)
  *
  * to a target image I by minimising a per-pixel negative log-likelihood
  * (Sec. 2.3, Eq. 8; Sec. 2.4, Eq. 13) with Adam followed by L-BFGS
@@ -25,7 +27,15 @@
  *   loss (Sec. 2.1: the convolution is undefined within half a kernel width
  *   of the edge); the difference image covers exactly that region,
  *   (H-2h) x (W-2h), row-major, dense, its (0,0) at pixel (h, h).
- * theta: float64 vector of n = m*m + 1 entries: K row-major, then B0.
+ * Background: a pair's bg_degree d (0 <= d <= DIA_MAX_BG_DEGREE) selects
+ *   B = sum_{p=0..d} sum_{q=0..d-p} b_pq eta^p xi^q (Eq. 18) with the
+ *   normalised coordinates of Eq. 19, eta = (x - x_c)/N_x, xi = (y - y_c)/N_y:
+ *   x = column j and y = row i of the full image, x_c = (W-1)/2,
+ *   y_c = (H-1)/2, N_x = W, N_y = H.  d = 0 is the constant B0 = b_00.
+ * theta: float64 vector of n = m*m + (d+1)(d+2)/2 entries: K row-major, then
+ *   b_00, b_01, ..., b_0d, b_10, ..., b_d0 (power of xi fastest, the order of
+ *   the double sum of Eq. 18); n = m*m + 1 (K, then B0) for d = 0.  b_00 is the
+ *   background at the image centre.
  * Mask: nonzero = use the pixel, 0 = masked.  The mask refers to target
  *   pixels; a bad reference pixel must be masked (dilated by h) by the caller.
  * Memory: unless a pair says DIA_MEM_HOST, every pointer is a DEVICE pointer
@@ -52,6 +62,7 @@ extern "C" {
 #endif
 
 #define DIA_MAX_M 31           /* largest odd kernel side of the fused kernels */
+#define DIA_MAX_BG_DEGREE 4    /* largest degree of the polynomial background */
 #define DIA_ABI_VERSION 3
 
 typedef enum {
@@ -106,13 +117,16 @@ typedef struct {
     int32_t m;                 /* odd kernel side */
     int32_t mem;               /* dia_mem: where the pointers above AND the
                                   outputs of the call live */
+    int32_t bg_degree;         /* degree d of the background polynomial (Eq. 18);
+                                  0 = constant B0 */
 } dia_pair;
 
 /* Optimiser settings (Sec. 2.9).  dia_opts_default() fills the paper's
  * values; a NULL dia_opts* means those defaults. */
 typedef struct {
     double lr_kernel;          /* Adam learning rate of the kernel pixels (1e-3) */
-    double lr_b0;              /* Adam learning rate of B0 (10; the paper uses 1, 10 or 100) */
+    double lr_b0;              /* Adam learning rate of B0 and of the other background
+                                  coefficients (10; the paper uses 1, 10 or 100) */
     double beta1, beta2;       /* Adam moment decays (0.9, 0.999) */
     double adam_eps;           /* Adam epsilon (1e-8) */
     double switch_tol;         /* |dL/L| between Adam steps that hands over to L-BFGS (1e-6) */
@@ -128,7 +142,8 @@ typedef struct {
     float clip_kappa;          /* clip |z| > kappa (5, Sec. 4.2) */
     int32_t init;              /* 0: box-car K = 1/m^2, 1: Gaussian of init_sigma,
                                   2: theta0; B0 = median of the unmasked valid I
-                                  for 0 and 1 (Sec. 2.9) */
+                                  for 0 and 1 (Sec. 2.9), the other background
+                                  coefficients 0 */
     double init_sigma;         /* Gaussian init width phi_K (px) */
     const double *theta0;      /* HOST pointer, n entries, used when init == 2 */
     int32_t graph_iters;       /* optimiser iterations per CUDA-graph launch (16) */
@@ -168,7 +183,7 @@ typedef struct {
                                   reg_lambda > 0 the regulariser of Eq. 20 included) */
     double grad_inf;           /* max |dL/dtheta| / N_data at the end */
     double scale;              /* photometric scale P = sum K (Eq. 3) */
-    double b0;                 /* fitted B0 */
+    double b0;                 /* fitted B0 (b_00: the background at the image centre) */
     int32_t reason;            /* why the last pass stopped: 1 grad_tol, 2 rel_tol, 3 stall
                                   (precision limit), 4 line search, 5 max iterations,
                                   6 max evaluations, 7 non-finite, 8 degenerate, 9 a
@@ -249,7 +264,7 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss,
 dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff_out,
                           void *workspace, size_t workspace_bytes, void *stream);
 
-/* Fit theta = [K, B0] (Sec. 2.10 algorithm): initialise, Adam until the
+/* Fit theta = [K, background] (Sec. 2.10 algorithm): initialise, Adam until the
  * relative loss change drops below switch_tol, then L-BFGS (preconditioned
  * by the inverse Gauss-Newton Hessian of a window of the pair, Wolfe /
  * approximate-Wolfe line search) until grad_tol, rel_tol or the limit of
@@ -260,7 +275,7 @@ dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff
  * a CUDA graph.
  * Outputs (all nullable; device pointers, or host pointers if the pair is
  * DIA_MEM_HOST):
- *   theta_out  float64[n]; K_out float32[m*m]; b0_out float32[1];
+ *   theta_out  float64[n]; K_out float32[m*m]; b0_out float32[1] (b_00);
  *   diff_out   float32 (H-2h) x (W-2h) difference image at the final theta;
  *   mask_out   uint8 H x W final mask (input mask with clipped pixels zeroed).
  * info (HOST, nullable) receives counters, final loss, P = sum K, B0.
@@ -282,8 +297,9 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
  * pair (line search and history; P v and the L-BFGS direction); converged
  * pairs drop out.  graph_iters iterations are replayed from a CUDA graph.
  * Outputs: theta_out (device, nullable) packs the pairs' theta vectors in
- * order, pair i at offset sum_{j<i} (m_j^2 + 1); diff_out (nullable HOST
- * array of npairs device pointers, entries nullable) receives each pair's
+ * order, pair i at offset sum_{j<i} n_j with n_j = m_j^2 + (d_j+1)(d_j+2)/2
+ * (d_j its bg_degree); diff_out (nullable HOST array of npairs device
+ * pointers, entries nullable) receives each pair's
  * difference image; infos (nullable HOST array of npairs) the per-pair
  * counters and status.  Returns DIA_OK, or the first error; per-pair fit
  * statuses are in infos.  The workspace (256-byte aligned device memory) is
@@ -330,8 +346,8 @@ dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss_spec *loss
  * log-likelihood up to constants, so F is the observed Fisher information; for
  * Huber and Cauchy it is the Hessian of that loss).  M is linear in theta, so
  * F = sum_p l''(M_p) phi_p phi_p^T over every unmasked valid pixel, with
- * phi_p = [R window of p, 1]; float32 per-pixel terms, float64 sums (every 32
- * pixels), n = m*m + 1.  The covariance estimate is F^-1 at the fitted theta
+ * phi_p = [R window of p, background basis at p]; float32 per-pixel terms,
+ * float64 sums (every 32 pixels), n = m*m + (d+1)(d+2)/2.  The covariance estimate is F^-1 at the fitted theta
  * (Eq. 16); its diagonal square roots are the Cramer-Rao bounds (Eq. 17).
  * Sec. 2.5 asks that the covariance be checked: F is tested for positive
  * definiteness by a float64 Cholesky factorisation (for a symmetric matrix
@@ -340,13 +356,14 @@ dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss_spec *loss
 typedef struct {
     int32_t positive_definite; /* 1: F (and so F^-1) is positive definite; 0: the
                                   warning flag of Sec. 2.5 -- cov_out is NaN */
-    int32_t n;                 /* m*m + 1 */
+    int32_t n;                 /* m*m + (d+1)(d+2)/2 */
     double log_det;            /* ln det F (valid when positive_definite) */
     double min_pivot;          /* smallest pivot of the Cholesky factorisation */
     int64_t ndata;             /* unmasked valid pixels summed */
 } dia_fisher_info;
 
-/* Workspace bytes of dia_fisher for this image and kernel side (0 if invalid). */
+/* Workspace bytes of dia_fisher for this image and kernel side, any
+ * background degree (0 if invalid). */
 size_t dia_fisher_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m);
 
 /* pair: DIA_MEM_DEVICE images; theta: DEVICE pointer, n doubles (e.g. the

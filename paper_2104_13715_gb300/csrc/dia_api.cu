@@ -73,7 +73,7 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
     }
     L.G = max_tiles < kMaxGrid ? max_tiles : kMaxGrid;
     L.np = ki.np;
-    L.n = m * m + 1;
+    L.n = m * m + kBgMax;   // capacity: the largest background
     L.kp = ki.kp;
     const size_t n8 = (size_t)L.n * 8;
     size_t o = 0;
@@ -111,7 +111,7 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
     L.pc_A64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
     L.pc_X64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
     L.pc_P = take((size_t)L.n * pc_ldp(L.n) * 4);
-    L.kpad = take((size_t)(m * ki.kp + 4) * 4);
+    L.kpad = take((size_t)(m * ki.kp + kBgMax + 1) * 4);
     const size_t plane = (size_t)H * (mem == DIA_MEM_HOST ? W : ld);
     L.mask = clip ? take(plane) : 0;
     if (mem == DIA_MEM_HOST) {
@@ -121,7 +121,7 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
         L.stage_flat = take(plane * 4);
         L.stage_mask = take(plane);
         L.stage_diff = take((size_t)Hv * Wv * 4);
-        L.stage_out = take((size_t)(m * m + 1) * 4);
+        L.stage_out = take((size_t)(m * m + kBgMax) * 4);
     } else {
         L.stage_R = L.stage_I = L.stage_var = L.stage_flat = L.stage_mask = L.stage_diff =
             L.stage_out = 0;
@@ -142,6 +142,7 @@ dia_status check_pair(const dia_pair *p) {
     if (p->mem != DIA_MEM_DEVICE && p->mem != DIA_MEM_HOST) return DIA_ERR_ARG;
     if (!dims_ok(p->H, p->W, p->ld, p->m)) return DIA_ERR_ARG;
     if (p->m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
+    if (p->bg_degree < 0 || p->bg_degree > DIA_MAX_BG_DEGREE) return DIA_ERR_ARG;
     return DIA_OK;
 }
 
@@ -213,6 +214,7 @@ struct Ctx {
     OptBuffers ob;
     float *kpad;
     double *red, *partials;
+    int nb;         // background coefficients of the pair
 };
 
 dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void *workspace,
@@ -286,6 +288,8 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     a.clip_kappa = 5.0f;
     if (loss) a.lp = to_params(loss);
     a.acc32 = g_accumulation.load() == DIA_ACCUM_FP32 ? 1 : 0;
+    set_background(a, pair->bg_degree, H, W, h);
+    c.nb = n_background(pair->bg_degree);
     c.red = (double *)(c.ws + c.L.red);
     c.st = (FitState *)(c.ws + c.L.state);
     c.sel = (SelectState *)(c.ws + c.L.sel);
@@ -304,7 +308,7 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     c.ob.YPY = (double *)(c.ws + c.L.YPY);
     c.ob.pdiag = (double *)(c.ws + c.L.pdiag);
     c.ob.P = nullptr;
-    c.ob.ldp = pc_ldp(c.L.n);
+    c.ob.ldp = pc_ldp(pair->m * pair->m + c.nb);
     return DIA_OK;
 }
 
@@ -496,10 +500,10 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss, const 
     Ctx c;
     dia_status rc = setup(pair, loss, 0, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
-    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.kpad, s));
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
     DIA_CK(launch_eval(c.ki, kModeGrad, c.ea, c.grid, s));
     DIA_CK(launch_reduce(c.partials, c.grid, c.L.np, c.red, nullptr, s, c.ea.acc32));
-    DIA_CK(launch_emit_loss_grad(c.red, pair->m, loss_out, grad_out, s));
+    DIA_CK(launch_emit_loss_grad(c.red, pair->m, c.nb, loss_out, grad_out, s));
     return DIA_OK;
 }
 
@@ -513,7 +517,7 @@ dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff
     ls.var_scalar = 1.f;
     dia_status rc = setup(pair, &ls, 0, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
-    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.kpad, s));
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
     EvalArgs ea = c.ea;
     ea.diff_out = diff_out;
     DIA_CK(launch_eval(c.ki, kModeForward, ea, c.grid, s));
@@ -543,7 +547,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     Ctx c;
     dia_status rc = setup(pair, loss, clip, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
-    const int m = pair->m, n = m * m + 1, h = m / 2;
+    const int m = pair->m, nk = m * m, n = nk + c.nb, h = m / 2;
     const int H = c.dp.H, W = c.dp.W, ld = c.dp.ld;
     const bool host = pair->mem == DIA_MEM_HOST;
 
@@ -564,14 +568,14 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     long long launches = 0;   // kernels this call launches (graph nodes included)
     if (opts.init == 2) {
         DIA_CK(cudaMemcpyAsync(c.ob.theta, opts.theta0, (size_t)n * 8, cudaMemcpyHostToDevice, s));
-        DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, 2, 0.0, nullptr, start_phase, s));
+        DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, c.nb, 2, 0.0, nullptr, start_phase, s));
         launches += 1;
     } else {
         int mgrid = device_sms() * 4;
         DIA_CK(launch_median(c.dp.img, c.ea.mask, H, W, ld, m, (uint32_t *)(c.ws + c.L.hist),
                              c.sel, mgrid, s));
-        DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, opts.init, opts.init_sigma, c.sel,
-                           start_phase, s));
+        DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, c.nb, opts.init, opts.init_sigma,
+                           c.sel, start_phase, s));
         launches += kMedianLaunches + 1;
     }
 
@@ -604,12 +608,17 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             pa.st = c.st;
             pa.eps = 1e-6;
             pa.reg2 = 2.0 * opts.reg_lambda;
+            pa.nbg = c.nb;
+            pa.eta0 = c.ea.eta0;
+            pa.eta_s = c.ea.eta_s;
+            pa.xi0 = c.ea.xi0;
+            pa.xi_s = c.ea.xi_s;
             pa.scale = 1.0 / ((double)(pa.y1 - pa.y0) * (pa.x1 - pa.x0));
             pa.flush = kGnFlushPc;
             PrecondArgs *d_pa = (PrecondArgs *)(c.ws + c.L.pc_args);
             DIA_CK(cudaMemcpyAsync(d_pa, &pa, sizeof(pa), cudaMemcpyHostToDevice, s));
             DIA_CK(launch_precond(d_pa, &pa, 1, s));
-            launches += precond_launches(m);
+            launches += precond_launches(n);
             c.ob.P = pa.P;
         }
     }
@@ -659,7 +668,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             EvalArgs ca = c.ea;
             ca.mask_out = wmask;
             DIA_CK(launch_eval(c.ki, kModeForward, ca, c.grid, s));
-            DIA_CK(launch_restart(c.st, c.kpad, c.ob, m, c.ki.kp, s));
+            DIA_CK(launch_restart(c.st, c.kpad, c.ob, m, c.ki.kp, c.nb, s));
             launches += 2;
             passes_done = pass;
         }
@@ -699,7 +708,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     }
     if (host) {
         float *kst = (float *)(c.ws + c.L.stage_out);
-        DIA_CK(launch_pack_outputs(c.ob.theta, m, nullptr, kst, kst + m * m, s));
+        DIA_CK(launch_pack_outputs(c.ob.theta, m, c.nb, nullptr, kst, kst + m * m, s));
         launches += 1;
         if (theta_out)
             DIA_CK(cudaMemcpyAsync(theta_out, c.ob.theta, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -708,17 +717,17 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         if (mask_out)
             DIA_CK(cudaMemcpy2DAsync(mask_out, pair->ld, wmask, W, W, H, cudaMemcpyDeviceToHost, s));
     } else {
-        DIA_CK(launch_pack_outputs(c.ob.theta, m, theta_out, K_out, b0_out, s));
+        DIA_CK(launch_pack_outputs(c.ob.theta, m, c.nb, theta_out, K_out, b0_out, s));
         launches += 1;
         if (mask_out)
             DIA_CK(cudaMemcpyAsync(mask_out, wmask, (size_t)H * ld, cudaMemcpyDeviceToDevice, s));
     }
     if (info) {
-        double th[DIA_MAX_M * DIA_MAX_M + 1];
+        double th[DIA_MAX_M * DIA_MAX_M + kBgMax];
         DIA_CK(cudaMemcpyAsync(th, c.ob.theta, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
         DIA_CK(cudaStreamSynchronize(s));
         double P = 0.0;
-        for (int k = 0; k < n - 1; ++k) P += th[k];
+        for (int k = 0; k < nk; ++k) P += th[k];
         info->status = status;
         info->adam_iters = hs.it_adam;
         info->lbfgs_iters = hs.it_lbfgs;
@@ -728,7 +737,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         info->loss = hs.L_sum;
         info->grad_inf = hs.grad_inf;
         info->scale = P;
-        info->b0 = th[n - 1];
+        info->b0 = th[nk];
         info->reason = hs.reason;
         info->kernel_launches = launches;
         info->precond_used = (opts.precond && hs.pc_ok) ? 1 : 0;
@@ -750,7 +759,7 @@ struct FisherLayout {
 static bool fisher_layout(int H, int W, int ld, int m, FisherLayout &F) {
     F.base = dia_workspace_size(H, W, ld, m, 0, DIA_MEM_DEVICE);
     if (F.base == 0) return false;
-    const int h = m / 2, n = m * m + 1;
+    const int h = m / 2, n = m * m + kBgMax;   // any background degree
     const long long npx = (long long)(H - 2 * h) * (W - 2 * h);
     F.chunks = (int)std::min(64LL, (npx + kGnChunk - 1) / kGnChunk);
     size_t o = align_up(F.base);
@@ -789,7 +798,7 @@ dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const dou
     Ctx c;
     dia_status rc = setup(pair, loss, 0, workspace, FL.base, s, c);
     if (rc != DIA_OK) return rc;
-    const int m = pair->m, n = m * m + 1, h = m / 2, np = pc_np(n);
+    const int m = pair->m, n = m * m + c.nb, h = m / 2, np = pc_np(n);
     const int Hv = pair->H - 2 * h, Wv = pair->W - 2 * h;
     char *ws = (char *)workspace;
     float *w = (float *)(ws + FL.w);
@@ -797,7 +806,7 @@ dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const dou
     double *res = (double *)(ws + FL.res);
 
     // curvature l''(M_p) at theta: D = I - M from the forward pass, then l''
-    DIA_CK(launch_prep_kpad(theta, m, c.ki.kp, c.kpad, s));
+    DIA_CK(launch_prep_kpad(theta, m, c.ki.kp, c.nb, c.kpad, s));
     EvalArgs ea = c.ea;
     ea.diff_out = w;
     DIA_CK(launch_eval(c.ki, kModeForward, ea, c.grid, s));
@@ -829,6 +838,11 @@ dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const dou
     pa.ldp = pc_ldp(n);
     pa.st = st;
     pa.eps = 0.0;
+    pa.nbg = c.nb;
+    pa.eta0 = c.ea.eta0;
+    pa.eta_s = c.ea.eta_s;
+    pa.xi0 = c.ea.xi0;
+    pa.xi_s = c.ea.xi_s;
     pa.scale = 1.0;
     pa.flush = 1;   // float64 every 32 pixels: F^-1 needs ~1e-9 relative sums
     pa.wmap = w;

@@ -71,9 +71,10 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
             p.m > p.W)
             return DIA_ERR_ARG;
         if (p.m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
+        if (p.bg_degree < 0 || p.bg_degree > DIA_MAX_BG_DEGREE) return DIA_ERR_ARG;
         PairPlan &q = P.pp[i];
         q.m = p.m;
-        q.n = p.m * p.m + 1;
+        q.n = p.m * p.m + n_background(p.bg_degree);
         q.np = np_of(p.m);
         const int h = p.m / 2, Hv = p.H - 2 * h, Wv = p.W - 2 * h;
         q.tiles_x = (Wv + kTW - 1) / kTW;
@@ -93,7 +94,7 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
         per = al(per + (size_t)q.n * 8 * (9 + 3 * (size_t)history) +
                  2 * (size_t)history * history * 8);
         q.kpad_off = per;
-        per = al(per + (size_t)(p.m * round4(p.m) + 4) * 4);
+        per = al(per + (size_t)(p.m * round4(p.m) + kBgMax + 1) * 4);
         // preconditioner: float64 Gauss-Newton Hessian (factored in place) and
         // inverse factor, padded to 64, and P; one pixel chunk per pair
         int chunks = 1;
@@ -264,9 +265,8 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     lp.var_scalar = loss->var_scalar;
     lp.var_floor = loss->var_floor;
     const int H = opts.history;
-    int max_m = 1;
-    for (int i = 0; i < npairs; ++i) max_m = std::max(max_m, pairs[i].m);
-    const int max_n = max_m * max_m + 1;
+    int max_n = 1;
+    for (int i = 0; i < npairs; ++i) max_n = std::max(max_n, P.pp[i].n);
     for (int i = 0; i < npairs; ++i) {
         const dia_pair &p = pairs[i];
         const PairPlan &q = P.pp[i];
@@ -293,6 +293,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         a.clip_kappa = opts.clip_kappa;
         a.done_flag = &st->done;
         a.lp = lp;
+        set_background(a, p.bg_degree, p.H, p.W, h);
         mks[i] = p.m;
         StepArgs &sa = sas[i];
         memset(&sa, 0, sizeof(sa));
@@ -339,6 +340,11 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
             pa.st = st;
             pa.eps = 1e-6;
             pa.reg2 = 2.0 * opts.reg_lambda;
+            pa.nbg = n - p.m * p.m;
+            pa.eta0 = a.eta0;
+            pa.eta_s = a.eta_s;
+            pa.xi0 = a.xi0;
+            pa.xi_s = a.xi_s;
             pa.scale = 1.0 / ((double)(pa.y1 - pa.y0) * (pa.x1 - pa.x0));
             pa.flush = kGnFlushPc;
             sa.b.P = pa.P;
@@ -427,6 +433,11 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     app(grid, sizeof grid);
     app(&opts.graph_iters, sizeof opts.graph_iters);
     app(&max_n, sizeof max_n);
+    // the captured kernels take pointers into the workspace at these offsets
+    const size_t offs[] = {P.off_hdr, P.off_eas,   P.off_mks,   P.off_items, P.off_sa,
+                           P.off_red, P.off_thoff, P.off_pas,   P.off_pairs, P.off_parts};
+    app(offs, sizeof offs);
+    app(P.gbeg, sizeof P.gbeg);
     cudaGraphExec_t gx = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_bmu);
@@ -482,7 +493,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     const auto t0 = std::chrono::steady_clock::now();
     int status = DIA_OK;
     int done_host = 0;
-    long long launches = 1 + (opts.precond ? precond_launches(max_m) : 0);   // init (+ preconditioner)
+    long long launches = 1 + (opts.precond ? precond_launches(max_n) : 0);   // init (+ preconditioner)
     for (;;) {
         DB_CK(cudaGraphLaunch(gx, s));
         launches += (long long)(n_groups + kStepLaunchesBatch) * opts.graph_iters;

@@ -2,11 +2,14 @@
 // kernel/background gradient in one pass over the image (sm_103a).
 //
 // Model (Sec. 2.1, Eq. 2): for an output pixel p = (y, x) of the valid region,
-//   M_p = sum_{a,b} K[a][b] R[y+a][x+b] + B0        (valid-region coordinates)
+//   M_p = sum_{a,b} K[a][b] R[y+a][x+b] + B_p       (valid-region coordinates)
+// with B_p = B0, or the polynomial of Sec. 2.6 (Eq. 18) in the normalised
+// coordinates of Eq. 19 (eta along x, xi along y):
+//   B_p = sum_{i<=d} c_i(xi) eta^i,  c_i(xi) = sum_{j<=d-i} b_ij xi^j.
 // Loss (Sec. 2.3 Eq. 8, Sec. 2.4 Eq. 12-13): l_p = rho(z_p) + ln sigma_p with
 // z = (I - M)/sigma and sigma^2 from the fixed map or the CCD / EMCCD models
 // (Eq. 6, Eq. 7).  Gradient: dL/dK[a][b] = sum_p g_p R[y+a][x+b],
-// dL/dB0 = sum_p g_p with g_p = dl_p/dM_p.
+// dL/db_ij = sum_p g_p eta_p^i xi_p^j with g_p = dl_p/dM_p (dL/dB0 = sum_p g_p).
 //
 // One CTA owns a TH x TW tile of output pixels at a time (persistent loop over
 // tiles).  Per tile:
@@ -27,9 +30,12 @@
 //      halving butterfly and added to per-warp Kahan-compensated float32
 //      shared accumulators; loss sums: per-lane float32 over <= 4096 pixels,
 //      then float64.  Everything is combined in float64 at the end.
-// At the end each CTA writes m*m + 5 float64 partials (loss, dK, dB0, pixel
-// count, and two curvature sums for the optimiser's diagonal preconditioner);
-// a separate kernel sums them in a fixed order.
+// At the end each CTA writes m*m + kBgMax + 4 float64 partials (loss, dK, the
+// kBgMax background slots, pixel count, and two curvature sums for the
+// optimiser's diagonal preconditioner); a separate kernel sums them in a fixed
+// order.  With a polynomial background the moments sum_p g eta^i xi^j of a
+// tile are taken from the shared g tile after the epilogue (float32 over one
+// tile and warp, then float64).
 #pragma once
 
 #include <cstdint>
@@ -38,6 +44,26 @@
 namespace dia {
 
 constexpr int kTW = 128;  // tile width: 32 lanes x 4 pixels
+
+// Polynomial background (Eq. 18): degree <= kBgMaxDeg, kBgMax coefficient
+// slots b_00, b_01, ..., b_0d, b_10, ... (power of xi fastest) after K.
+constexpr int kBgMaxDeg = 4;
+constexpr int kBgMax = (kBgMaxDeg + 1) * (kBgMaxDeg + 2) / 2;
+__host__ __device__ constexpr int n_background(int deg) { return (deg + 1) * (deg + 2) / 2; }
+// degree whose coefficient count is nb (nb = n_background(d) for some d <= kBgMaxDeg)
+__host__ __device__ inline int bg_degree_of(int nb) {
+    int d = 0;
+    while (d < kBgMaxDeg && n_background(d) < nb) ++d;
+    return d;
+}
+// layout of the reduced vector / per-CTA partials: [0] loss, [1, nk] dK,
+// [nk+1, nk+kBgMax] background coefficients, then pixel count, sum kappa R^2,
+// sum kappa
+__host__ __device__ constexpr int red_count(int nk) { return nk + kBgMax + 1; }
+__host__ __device__ constexpr int red_size(int nk) { return nk + kBgMax + 4; }
+// float64 per-warp accumulators: loss, dB0, count, kR^2, k, then the moments of
+// the background coefficients 1 .. kBgMax-1
+constexpr int kAccW = 5 + kBgMax - 1;
 
 enum EvalMode { kModeGrad = 0, kModeForward = 1 };
 
@@ -61,8 +87,9 @@ struct EvalArgs {
     int H, W, ld;
     int Hv, Wv;            // valid region
     int tiles_x, n_tiles;
-    const float *Kpad;     // m rows of KP floats (zero padded), then B0
-    double *partials;      // [gridDim.x][m*m + 5]
+    const float *Kpad;     // m rows of KP floats (zero padded), then kBgMax + 1
+                           // background slots (b_00 first)
+    double *partials;      // [gridDim.x][red_size(m*m)]
     float *diff_out;       // forward mode: D = I - M over the valid region (nullable)
     uint8_t *mask_out;     // forward mode: clip |z| > kappa (nullable)
     float clip_kappa;
@@ -70,9 +97,23 @@ struct EvalArgs {
     LossParams lp;
     int acc32;             // nonzero: float32 accumulation everywhere, no compensation
                            // (the comparison form of the precision study)
+    int bg_deg;            // background degree (0: constant B0)
+    float eta0, eta_s;     // eta = eta0 + eta_s * x for valid-region column x (Eq. 19)
+    float xi0, xi_s;       // xi = xi0 + xi_s * y for valid-region row y
 };
 
 __host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
+
+// Background of degree deg for an H x W image with kernel half-width h: the
+// Eq. 19 coordinates of valid-region pixel (y, x), i.e. full-image pixel
+// (y + h, x + h): eta = (x + h - (W-1)/2) / W, xi = (y + h - (H-1)/2) / H.
+inline void set_background(EvalArgs &a, int deg, int H, int W, int h) {
+    a.bg_deg = deg;
+    a.eta_s = (float)(1.0 / W);
+    a.eta0 = (float)((h - 0.5 * (W - 1)) / W);
+    a.xi_s = (float)(1.0 / H);
+    a.xi0 = (float)((h - 0.5 * (H - 1)) / H);
+}
 
 // Pixel loss and g = dl/dM (float32).  Returns the loss; writes g, z and a
 // non-negative curvature weight kappa ~ d2l/dM2 (Gauss-Newton / IRLS weight
@@ -254,7 +295,7 @@ struct EvalShape {
     static constexpr int KF = SPLIT ? MK / NW : (MK + NW - 1) / NW;
     static constexpr int RM = SPLIT ? MK % NW : 0;
     static constexpr int QB = KF + RM;                   // dK rows held per lane
-    static constexpr int NP = MK * MK + 5;               // partials per CTA
+    static constexpr int NP = red_size(MK * MK);         // partials per CTA
     static constexpr int NT = NW * 32;
     // shared memory layout (bytes)
     static constexpr int OFF_R = 0;
@@ -266,10 +307,10 @@ struct EvalShape {
     static constexpr int FLUSH = (4096 / (4 * TH)) > 0 ? (4096 / (4 * TH)) : 1;
     static constexpr int SZ_G = (TH + 2 * GPAD) * kTW * 4;
     static constexpr int OFF_K = OFF_G + SZ_G;
-    static constexpr int SZ_K = (MK * KP + 4) * 4;
+    static constexpr int SZ_K = (MK * KP + kBgMax + 1) * 4;
     static constexpr int OFF_D = (OFF_K + SZ_K + 15) & ~15;
-    // float64 per-warp {loss, dB0, count, kR^2, k}
-    static constexpr int SZ_D = 5 * NW * 8;
+    // float64 per-warp {loss, dB0, count, kR^2, k, background moments}
+    static constexpr int SZ_D = kAccW * NW * 8;
     // float32 Kahan pairs (sum, compensation) of each warp's QB x MK dK rows
     static constexpr int NK = QB * MK;
     static constexpr int OFF_KS = OFF_D + SZ_D;
@@ -277,8 +318,71 @@ struct EvalShape {
     // F2: float2 pairs (K[a][b], K[a-1][b]) for the paired forward
     static constexpr int OFF_K2 = (OFF_KS + SZ_KS + 15) & ~15;
     static constexpr int SZ_K2 = (F2 & 1) ? MK * KP * 8 : 0;
-    static constexpr int SMEM = OFF_K2 + SZ_K2;
+    // background: c_i(xi) of each tile row (8 floats per row)
+    static constexpr int OFF_BG = OFF_K2 + SZ_K2;
+    static constexpr int SZ_BG = TH * 8 * 4;
+    static constexpr int SMEM = OFF_BG + SZ_BG;
 };
+
+// Moments sum_p g_p eta^i xi^j of the background coefficients (Eq. 18)
+// over this warp's QF rows of the g tile (out-of-range and masked pixels hold
+// g = 0): float32 per lane over its 4 pixels of each row, summed over the warp,
+// added by lane 0 to the warp's float64 slots w[5 + c - 1], c the coefficient
+// index for the pair's degree d (c = 0, dL/dB0, is summed in the epilogue).
+// All kBgMax moments of the largest degree are formed in registers (fixed
+// indices) and those with i + j <= d kept.
+template <int QF>
+__device__ __forceinline__ void bg_moments(const EvalArgs &args, const float *gt, int ty0, int tx0,
+                                           double *w, int warp, int lane) {
+    float mom[kBgMax];
+#pragma unroll
+    for (int k = 0; k < kBgMax; ++k) mom[k] = 0.f;
+#pragma unroll
+    for (int q = 0; q < QF; ++q) {
+        const int yl = warp * QF + q;
+        const float xi = fmaf((float)(ty0 + yl), args.xi_s, args.xi0);
+        float sx[kBgMaxDeg + 1];   // sum over the lane's pixels of g eta^i
+#pragma unroll
+        for (int i = 0; i <= kBgMaxDeg; ++i) sx[i] = 0.f;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int xl = 4 * lane + p;
+            const float g = gt[yl * kTW + xl];
+            const float eta = fmaf((float)(tx0 + xl), args.eta_s, args.eta0);
+            float e = g;
+#pragma unroll
+            for (int i = 0; i <= kBgMaxDeg; ++i) {
+                sx[i] += e;
+                e *= eta;
+            }
+        }
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i <= kBgMaxDeg; ++i) {
+            float t = sx[i];
+#pragma unroll
+            for (int j = 0; j <= kBgMaxDeg - i; ++j) {
+                mom[k++] += t;
+                t *= xi;
+            }
+        }
+    }
+    const int d = args.bg_deg;
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i <= kBgMaxDeg; ++i) {
+#pragma unroll
+        for (int j = 0; j <= kBgMaxDeg - i; ++j, ++k) {
+            if (k == 0) continue;
+            const float v = warp_sum(mom[k]);
+            if (lane == 0 && i + j <= d) {
+                const int c = i * (d + 1) - i * (i - 1) / 2 + j;   // index for degree d
+                double *slot = w + 5 + c - 1;
+                *slot = args.acc32 ? (double)((float)*slot + v) : *slot + (double)v;
+            }
+        }
+    }
+}
 
 // Backward rows: dk[OFF+qb][b] += sum_rr sum_p g[y][x+p] R[r0+rr][x+b+p] with
 // y = y0 + rr - qb, for NQ kernel rows.  Whole-tile rows (SLICE = false)
@@ -356,12 +460,13 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     float *Rbuf1 = Rbuf0 + S::RROWS * RP;
     float *gs = reinterpret_cast<float *>(smem + S::OFF_G);
     float *Ks = reinterpret_cast<float *>(smem + S::OFF_K);
-    double *acc64 = reinterpret_cast<double *>(smem + S::OFF_D);  // per warp {loss, dB0, count, kR2, k}
+    double *acc64 = reinterpret_cast<double *>(smem + S::OFF_D);  // per warp, kAccW each
+    float *bgrow = reinterpret_cast<float *>(smem + S::OFF_BG);     // c_i(xi) per tile row
     float *kahan = reinterpret_cast<float *>(smem + S::OFF_KS);    // per warp [NK sums | NK comps]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int i = tid; i < MK * KP + 4; i += S::NT) Ks[i] = args.Kpad[i];
+    for (int i = tid; i < MK * KP + kBgMax + 1; i += S::NT) Ks[i] = args.Kpad[i];
     float2 *K2 = reinterpret_cast<float2 *>(smem + S::OFF_K2);   // F2 only
     if constexpr ((F2 & 1) != 0) {
         for (int i = tid; i < MK * KP; i += S::NT) {
@@ -370,7 +475,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
         }
     }
     if (MODE == kModeGrad) {
-        for (int i = tid; i < 5 * NW; i += S::NT) acc64[i] = 0.0;
+        for (int i = tid; i < kAccW * NW; i += S::NT) acc64[i] = 0.0;
         for (int i = tid; i < NW * 2 * S::NK; i += S::NT) kahan[i] = 0.f;
         for (int i = tid; i < S::GPAD * kTW; i += S::NT) {
             gs[i] = 0.f;
@@ -394,7 +499,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
         const float l = warp_sum(lsum), g = warp_sum(gsum), c = warp_sum(cnt);
         const float k = warp_sum(ksum), kr = warp_sum(kr2sum);
         if (lane == 0) {
-            double *w5 = acc64 + 5 * warp;
+            double *w5 = acc64 + kAccW * warp;
             if (args.acc32) {   // float32 running sums (kept in the float64 slots)
                 w5[0] = (double)((float)w5[0] + l);
                 w5[1] = (double)((float)w5[1] + g);
@@ -436,6 +541,22 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             stage_tile<S::RROWS, RP, S::NT>(buf ? Rbuf0 : Rbuf1, args, (nxt / args.tiles_x) * TH,
                                             (nxt % args.tiles_x) * kTW, vec);
         cp_async_commit();
+        if (args.bg_deg > 0) {
+            // c_i(xi) = sum_j b_ij xi^j of each tile row (Eq. 18), by Horner in xi
+            for (int r = tid; r < TH; r += S::NT) {
+                const float xi = fmaf((float)(ty0 + r), args.xi_s, args.xi0);
+                int k = MK * KP;
+                for (int i = 0; i <= kBgMaxDeg; ++i) {
+                    float c = 0.f;
+                    if (i <= args.bg_deg) {
+                        const int nj = args.bg_deg - i;
+                        for (int j = nj; j >= 0; --j) c = fmaf(c, xi, Ks[k + j]);
+                        k += nj + 1;
+                    }
+                    bgrow[r * 8 + i] = c;
+                }
+            }
+        }
         cp_async_wait<1>();   // this tile's copies have landed
         __syncthreads();
         const float *Rs = buf ? Rbuf1 : Rbuf0;
@@ -587,7 +708,14 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
                 if (y < args.Hv && x < args.Wv) {
                     const size_t off = (size_t)(y + H2) * args.ld + (x + H2);
                     const bool use = (args.mask == nullptr) || (args.mask[off] != 0);
-                    const float M = acc[q][p] + B0;
+                    float Bp = B0;
+                    if (args.bg_deg > 0) {   // Horner in eta over the row's c_i
+                        const float eta = fmaf((float)x, args.eta_s, args.eta0);
+                        const float *c = bgrow + yl * 8;
+                        Bp = c[args.bg_deg];
+                        for (int i = args.bg_deg - 1; i >= 0; --i) Bp = fmaf(Bp, eta, c[i]);
+                    }
+                    const float M = acc[q][p] + Bp;
                     const float Iv = __ldg(args.I + off);
                     const float vm = args.var ? __ldg(args.var + off) : args.lp.var_scalar;
                     const float F = args.flat ? __ldg(args.flat + off) : 1.0f;
@@ -616,6 +744,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             continue;
         }
         __syncthreads();  // g tile complete
+        if (args.bg_deg > 0) bg_moments<QF>(args, gt, ty0, tx0, acc64 + kAccW * warp, warp, lane);
 
         // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b]
         float dk[NK];
@@ -695,15 +824,20 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             }
             out[1 + i] = t;
         }
-        if (tid < 5) {
-            // tid 0: loss, 1: dB0, 2: pixel count, 3: sum kappa R^2, 4: sum kappa
+        if (tid < kAccW) {
+            // tid 0: loss, 1: dB0, 2: pixel count, 3: sum kappa R^2, 4: sum kappa,
+            // 5 + c: background coefficient 1 + c
             double t = 0.0;
             float t32 = 0.f;
             for (int w = 0; w < NW; ++w) {
-                t += acc64[5 * w + tid];
-                t32 += (float)acc64[5 * w + tid];
+                t += acc64[kAccW * w + tid];
+                t32 += (float)acc64[kAccW * w + tid];
             }
-            out[tid == 0 ? 0 : MK * MK + tid] = args.acc32 ? (double)t32 : t;
+            const int o = tid == 0  ? 0
+                          : tid == 1 ? MK * MK + 1
+                          : tid < 5  ? red_count(MK * MK) + tid - 2
+                                     : MK * MK + 1 + (tid - 4);
+            out[o] = args.acc32 ? (double)t32 : t;
         }
     }
 }

@@ -26,8 +26,8 @@ namespace {
 using namespace dia;
 
 constexpr size_t kScratchBytes = DIA_NOALLOC_SCRATCH_BYTES;
-constexpr size_t kKpadOff = 0;                       // (31*32 + 4) floats
-constexpr size_t kRedOff = 4096;                     // up to 966 doubles
+constexpr size_t kKpadOff = 0;                       // (31*32 + kBgMax + 1) floats
+constexpr size_t kRedOff = 4096;                     // up to 31*31 + kBgMax + 4 doubles
 constexpr size_t kPartOff = 16384;                   // per-CTA partials
 constexpr int kMaxDevices = 64;
 
@@ -87,6 +87,7 @@ extern "C" dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss
     const int H = pair->H, W = pair->W, ld = pair->ld, m = pair->m;
     if (H <= 0 || W <= 0 || ld < W || m < 1 || (m & 1) == 0 || m > H || m > W) return DIA_ERR_ARG;
     if (m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
+    if (pair->bg_degree < 0 || pair->bg_degree > DIA_MAX_BG_DEGREE) return DIA_ERR_ARG;
     if (loss->rho < 0 || loss->rho > 2 || loss->var_model < 0 || loss->var_model > 2)
         return DIA_ERR_ARG;
     if (loss->var_model == DIA_VAR_FIXED) {
@@ -102,7 +103,7 @@ extern "C" dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss
     const size_t part_bytes_per_cta = (size_t)ki.np * sizeof(double);
     const size_t max_ctas = (kScratchBytes - kPartOff) / part_bytes_per_cta;
     // sizes the fixed scratch cannot hold are refused (cannot happen for m <= DIA_MAX_M)
-    if ((size_t)(m * ki.kp + 4) * 4 > kRedOff - kKpadOff || (size_t)ki.np * 8 > kPartOff - kRedOff ||
+    if ((size_t)(m * ki.kp + kBgMax + 1) * 4 > kRedOff - kKpadOff || (size_t)ki.np * 8 > kPartOff - kRedOff ||
         max_ctas < 1)
         return DIA_ERR_WORKSPACE;
 
@@ -152,13 +153,15 @@ extern "C" dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss
     a.lp.huber_c = loss->huber_c;
     a.lp.var_scalar = loss->var_scalar;
     a.lp.var_floor = loss->var_floor;
+    set_background(a, pair->bg_degree, H, W, h);
+    const int nb = n_background(pair->bg_degree);
 
     // Every CTA writes all of its partials and the reduction writes every
     // reduced entry, so nothing left in the array by an earlier call is read.
-    NA_CK(launch_prep_kpad(theta, m, ki.kp, kpad, s));
+    NA_CK(launch_prep_kpad(theta, m, ki.kp, nb, kpad, s));
     void *params[] = {(void *)&a};
     NA_CK(cudaLaunchKernel(ki.fn[kModeGrad], dim3((unsigned)grid), dim3(ki.nt), params, ki.smem, s));
     NA_CK(launch_reduce(partials, (int)grid, ki.np, red, nullptr, s));
-    NA_CK(launch_emit_loss_grad(red, m, loss_out, grad_out, s));
+    NA_CK(launch_emit_loss_grad(red, m, nb, loss_out, grad_out, s));
     return DIA_OK;
 }

@@ -46,36 +46,36 @@ cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, co
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ void write_kpad(const double *th, int mk, int kp, float *Kpad, int tid,
-                                           int nt) {
+// float32 copy of theta for the fused kernel: m rows of kp floats (zero
+// padded), then the nb background coefficients and zeros up to kBgMax + 1.
+__device__ __forceinline__ void write_kpad(const double *th, int mk, int kp, int nb, float *Kpad,
+                                           int tid, int nt) {
     for (int i = tid; i < mk * kp; i += nt) {
         const int a = i / kp, b = i - a * kp;
         Kpad[i] = (b < mk) ? (float)th[a * mk + b] : 0.f;
     }
-    if (tid == 0) {
-        Kpad[mk * kp] = (float)th[mk * mk];
-        Kpad[mk * kp + 1] = Kpad[mk * kp + 2] = Kpad[mk * kp + 3] = 0.f;
-    }
+    for (int i = tid; i < kBgMax + 1; i += nt) Kpad[mk * kp + i] = (i < nb) ? (float)th[mk * mk + i] : 0.f;
 }
 
-__global__ void prep_kpad_kernel(const double *theta, int mk, int kp, float *Kpad) {
-    write_kpad(theta, mk, kp, Kpad, threadIdx.x, blockDim.x);
+__global__ void prep_kpad_kernel(const double *theta, int mk, int kp, int nb, float *Kpad) {
+    write_kpad(theta, mk, kp, nb, Kpad, threadIdx.x, blockDim.x);
 }
 
-cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, float *Kpad, cudaStream_t s) {
-    prep_kpad_kernel<<<1, 256, 0, s>>>(theta, mk, kp, Kpad);
+cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, int nb, float *Kpad,
+                             cudaStream_t s) {
+    prep_kpad_kernel<<<1, 256, 0, s>>>(theta, mk, kp, nb, Kpad);
     return cudaGetLastError();
 }
 
-__global__ void emit_kernel(const double *red, int mk, double *loss, double *grad) {
-    const int n = mk * mk + 1;
+__global__ void emit_kernel(const double *red, int mk, int nb, double *loss, double *grad) {
+    const int n = mk * mk + nb;
     for (int k = threadIdx.x; k < n; k += blockDim.x) grad[k] = red[1 + k];
     if (threadIdx.x == 0) *loss = red[0];
 }
 
-cudaError_t launch_emit_loss_grad(const double *red, int mk, double *loss, double *grad,
+cudaError_t launch_emit_loss_grad(const double *red, int mk, int nb, double *loss, double *grad,
                                   cudaStream_t s) {
-    emit_kernel<<<1, 256, 0, s>>>(red, mk, loss, grad);
+    emit_kernel<<<1, 256, 0, s>>>(red, mk, nb, loss, grad);
     return cudaGetLastError();
 }
 
@@ -144,7 +144,7 @@ __device__ void set_trial(const StepArgs &a, double alpha) {
     const OptBuffers &b = a.b;
     for (int k = threadIdx.x; k < a.n; k += kStepThreads) b.trial[k] = b.theta[k] + alpha * b.dir[k];
     __syncthreads();
-    write_kpad(b.trial, a.mk, a.kp, a.Kpad, threadIdx.x, kStepThreads);
+    write_kpad(b.trial, a.mk, a.kp, a.n - a.mk * a.mk, a.Kpad, threadIdx.x, kStepThreads);
 }
 
 constexpr double kNoProgress = 1e-2;   // see finish()
@@ -154,7 +154,7 @@ __device__ void finish(const StepArgs &a, int status, int reason) {
     FitState *st = a.st;
     for (int k = threadIdx.x; k < a.n; k += kStepThreads) a.b.trial[k] = a.b.theta[k];
     __syncthreads();
-    write_kpad(a.b.theta, a.mk, a.kp, a.Kpad, threadIdx.x, kStepThreads);
+    write_kpad(a.b.theta, a.mk, a.kp, a.n - a.mk * a.mk, a.Kpad, threadIdx.x, kStepThreads);
     if (threadIdx.x == 0) {
         // a pass that stops for lack of progress is at the limit of numerical
         // precision only if max|g| came down by orders of magnitude from the
@@ -208,16 +208,28 @@ __device__ double add_penalty(const StepArgs &a, StepShared &sm) {
 
 // Diagonal preconditioner from the curvature sums of the last evaluation:
 // kernel pixels ~ 1/sum(kappa R^2), B0 ~ 1/sum(kappa) (Gauss-Newton diagonal
-// with the kernel-pixel entries approximated by the centre pixel).
+// with the kernel-pixel entries approximated by the centre pixel); background
+// coefficient b_ij ~ 1/(sum(kappa) E[eta^2i] E[xi^2j]) with eta, xi taken as
+// uniform on [-1/2, 1/2] (E[eta^2i] = 4^-i / (2i + 1)).
 __device__ void update_precond(const StepArgs &a) {
-    const double dk = a.red[a.n + 2], db = a.red[a.n + 3];
+    const int mk = a.mk, nk = mk * mk, deg = bg_degree_of(a.n - nk);
+    const double dk = a.red[red_count(nk) + 1], db = a.red[red_count(nk) + 2];
     const double pk = (dk > 0.0 && isfinite(dk)) ? 1.0 / dk : 1.0;
     const double pb = (db > 0.0 && isfinite(db)) ? 1.0 / db : 1.0;
-    const double N = a.red[a.n + 1];
-    const int mk = a.mk;
+    const double N = a.red[red_count(nk)];
     for (int k = threadIdx.x; k < a.n; k += kStepThreads) {
-        double p = N * ((k == a.n - 1) ? pb : pk);   // the loss is scaled by 1/N
-        if (a.p.reg_lambda > 0.0 && k < a.n - 1) {
+        double p = N * ((k >= nk) ? pb : pk);   // the loss is scaled by 1/N
+        if (k > nk) {
+            int c = k - nk, i = 0;
+            while (c > deg - i) {   // (i, j) of coefficient c
+                c -= deg - i + 1;
+                ++i;
+            }
+            const int j = c;
+            p *= (double)(2 * i + 1) * (double)(1 << (2 * i)) * (double)(2 * j + 1) *
+                 (double)(1 << (2 * j));
+        }
+        if (a.p.reg_lambda > 0.0 && k < nk) {
             // plus the regulariser's diagonal 2 lambda (L^T L)_kk = 2 lambda d (d + 1),
             // d the number of edge neighbours of kernel pixel k
             const int r = k / mk, c = k - r * mk;
@@ -439,7 +451,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
     const OptParams &p = a.p;
     const int n = a.n, tid = threadIdx.x;
 
-    const double N = a.red[n + 1];
+    const double N = a.red[red_count(a.mk * a.mk)];
     if (!(N > 0.0)) {
         finish(a, 6 /* DIA_ERR_DEGENERATE */, kStopDegenerate);
         return;
@@ -484,13 +496,13 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
                 const double m2 = p.beta2 * b.m2[k] + (1.0 - p.beta2) * g * g;
                 b.m1[k] = m1;
                 b.m2[k] = m2;
-                const double lr = (k == n - 1) ? p.lr_b0 : p.lr_kernel;
+                const double lr = (k >= a.mk * a.mk) ? p.lr_b0 : p.lr_kernel;
                 const double th = b.theta[k] - lr * (m1 / bc1) / (sqrt(m2 / bc2) + p.adam_eps);
                 b.theta[k] = th;
                 b.trial[k] = th;
             }
             __syncthreads();
-            write_kpad(b.trial, a.mk, a.kp, a.Kpad, tid, kStepThreads);
+            write_kpad(b.trial, a.mk, a.kp, n - a.mk * a.mk, a.Kpad, tid, kStepThreads);
             if (tid == 0) {
                 st->b1t = b1t;
                 st->b2t = b2t;
@@ -738,13 +750,13 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s) {
 // ----------------------------------------------------------------------------
 // Initialisation: K box-car (1/m^2) or a normalised Gaussian (Sec. 2.9, Sec. 5.1),
 // B0 = median of the unmasked valid target pixels; or theta already in place.
-__device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int mode,
-                          double sigma, double median, int degenerate, int start_phase,
-                          double *sh) {
-    const int n = mk * mk + 1, tid = threadIdx.x, h = mk / 2;
+__device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,
+                          int mode, double sigma, double median, int degenerate,
+                          int start_phase, double *sh) {
+    const int nk = mk * mk, n = nk + nb, tid = threadIdx.x, h = mk / 2;
     if (mode == 0 || mode == 1) {
         double w = 0.0;
-        for (int k = tid; k < n - 1; k += kStepThreads) {
+        for (int k = tid; k < nk; k += kStepThreads) {
             double v = 1.0;
             if (mode == 1) {
                 const int a = k / mk - h, c = k % mk - h;
@@ -754,8 +766,9 @@ __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int k
             w += v;
         }
         w = block_sum(w, sh);
-        for (int k = tid; k < n - 1; k += kStepThreads) b.theta[k] /= w;
-        if (tid == 0) b.theta[n - 1] = median;
+        for (int k = tid; k < nk; k += kStepThreads) b.theta[k] /= w;
+        // B0 = median (Sec. 2.9); a polynomial background starts flat
+        for (int k = nk + tid; k < n; k += kStepThreads) b.theta[k] = (k == nk) ? median : 0.0;
     }
     __syncthreads();
     for (int k = tid; k < n; k += kStepThreads) {
@@ -764,7 +777,7 @@ __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int k
         b.m2[k] = 0.0;
     }
     __syncthreads();
-    write_kpad(b.theta, mk, kp, Kpad, tid, kStepThreads);
+    write_kpad(b.theta, mk, kp, nb, Kpad, tid, kStepThreads);
     if (tid == 0) {
         FitState z;
         memset(&z, 0, sizeof(z));
@@ -784,28 +797,28 @@ __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int k
     }
 }
 
-__global__ void init_kernel(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int mode,
-                            double sigma, const SelectState *sel, int start_phase) {
+__global__ void init_kernel(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,
+                            int mode, double sigma, const SelectState *sel, int start_phase) {
     __shared__ double sh[kStepThreads / 32];
-    init_body(st, b, Kpad, mk, kp, mode, sigma, sel ? sel->median : 0.0,
+    init_body(st, b, Kpad, mk, kp, nb, mode, sigma, sel ? sel->median : 0.0,
               sel ? sel->degenerate : 0, start_phase, sh);
 }
 
-cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,
-                        double init_sigma, const SelectState *sel, int start_phase,
-                        cudaStream_t s) {
-    init_kernel<<<1, kStepThreads, 0, s>>>(st, b, Kpad, mk, kp, init_mode, init_sigma, sel,
+cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,
+                        int init_mode, double init_sigma, const SelectState *sel,
+                        int start_phase, cudaStream_t s) {
+    init_kernel<<<1, kStepThreads, 0, s>>>(st, b, Kpad, mk, kp, nb, init_mode, init_sigma, sel,
                                            start_phase);
     return cudaGetLastError();
 }
 
 // Restart the optimiser from the accepted theta (refit after clipping): the
 // next evaluation at theta starts L-BFGS afresh.
-__global__ void restart_kernel(FitState *st, float *Kpad, OptBuffers b, int mk, int kp) {
-    const int n = mk * mk + 1;
+__global__ void restart_kernel(FitState *st, float *Kpad, OptBuffers b, int mk, int kp, int nb) {
+    const int n = mk * mk + nb;
     for (int k = threadIdx.x; k < n; k += blockDim.x) b.trial[k] = b.theta[k];
     __syncthreads();
-    write_kpad(b.theta, mk, kp, Kpad, threadIdx.x, blockDim.x);
+    write_kpad(b.theta, mk, kp, nb, Kpad, threadIdx.x, blockDim.x);
     if (threadIdx.x == 0) {
         st->done = 0;
         st->phase = kPhaseLbfgsStart;
@@ -817,9 +830,9 @@ __global__ void restart_kernel(FitState *st, float *Kpad, OptBuffers b, int mk, 
     }
 }
 
-cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp,
+cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp, int nb,
                            cudaStream_t s) {
-    restart_kernel<<<1, 256, 0, s>>>(st, Kpad, b, mk, kp);
+    restart_kernel<<<1, 256, 0, s>>>(st, Kpad, b, mk, kp, nb);
     return cudaGetLastError();
 }
 
@@ -1002,7 +1015,8 @@ __global__ void __launch_bounds__(kStepThreads)
         s_deg = 0;
     }
     __syncthreads();
-    init_body(a.st, a.b, a.Kpad, a.mk, a.kp, mode, sigma, s_med, s_deg, start_phase, sh);
+    init_body(a.st, a.b, a.Kpad, a.mk, a.kp, a.n - a.mk * a.mk, mode, sigma, s_med, s_deg,
+              start_phase, sh);
     if (threadIdx.x == 0 && s_deg && a.n_done) atomicAdd(a.n_done, 1);   // finished at once
 }
 
@@ -1026,19 +1040,19 @@ cudaError_t launch_pack_batch(const StepArgs *args, const long long *theta_off, 
     return cudaGetLastError();
 }
 
-__global__ void pack_kernel(const double *theta, int mk, double *theta_out, float *K_out,
+__global__ void pack_kernel(const double *theta, int mk, int nb, double *theta_out, float *K_out,
                             float *b0_out) {
-    const int n = mk * mk + 1;
+    const int nk = mk * mk, n = nk + nb;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         if (theta_out) theta_out[k] = theta[k];
-        if (K_out && k < n - 1) K_out[k] = (float)theta[k];
+        if (K_out && k < nk) K_out[k] = (float)theta[k];
     }
-    if (threadIdx.x == 0 && b0_out) *b0_out = (float)theta[n - 1];
+    if (threadIdx.x == 0 && b0_out) *b0_out = (float)theta[nk];
 }
 
-cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, float *K_out,
-                                float *b0_out, cudaStream_t s) {
-    pack_kernel<<<1, 256, 0, s>>>(theta, mk, theta_out, K_out, b0_out);
+cudaError_t launch_pack_outputs(const double *theta, int mk, int nb, double *theta_out,
+                                float *K_out, float *b0_out, cudaStream_t s) {
+    pack_kernel<<<1, 256, 0, s>>>(theta, mk, nb, theta_out, K_out, b0_out);
     return cudaGetLastError();
 }
 

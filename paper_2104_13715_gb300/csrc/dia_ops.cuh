@@ -13,7 +13,7 @@
 namespace dia {
 
 constexpr int kHistMax = 128;  // largest L-BFGS memory
-constexpr int kPcMaxN = 31 * 31 + 1;   // largest preconditioned theta (m <= 31)
+constexpr int kPcMaxN = 31 * 31 + kBgMax;   // largest theta (m <= 31, largest background)
 
 enum Phase { kPhaseAdam = 0, kPhaseLbfgs = 1, kPhaseLbfgsStart = 2, kPhaseDone = 3 };
 
@@ -133,6 +133,8 @@ struct PrecondArgs {
     FitState *st;         // receives pc_ok
     double eps;           // relative diagonal regularisation of H
     double reg2;          // 2 lambda: H += 2 lambda L^T L, the regulariser of Eq. 20 (0 = off)
+    int nbg;              // background coefficients (1: the constant B0)
+    float eta0, eta_s, xi0, xi_s;   // Eq. 19 coordinates of valid-region pixels (EvalArgs)
     double scale;         // H is scaled by this (1 / window pixels for the preconditioner)
     int flush;            // shared-memory batches of 32 px per float64 flush
     int wmap_ld;
@@ -147,6 +149,7 @@ constexpr int kGnT = 64;    // block size of the Hessian sum
 constexpr int kGnChunk = 16384;   // pixels per chunk of the Hessian sum
 constexpr int kGnFlushPc = 16;    // 32-px batches per float64 flush for the preconditioner
 __host__ __device__ inline int pc_np(int n) { return (n + kGnT - 1) / kGnT * kGnT; }
+__host__ __device__ inline int pc_n(const PrecondArgs &a) { return a.m * a.m + a.nbg; }
 __host__ __device__ inline int pc_ldp(int n) { return (n + 3) & ~3; }
 __host__ __device__ inline int gn_tiles(int n) { return (n + kGnT - 1) / kGnT; }
 __host__ __device__ inline int gn_blocks(int n) { return gn_tiles(n) * (gn_tiles(n) + 1) / 2; }
@@ -221,8 +224,10 @@ __device__ __forceinline__ void pc_apply_body(const StepArgs &a, int blk, int nb
 // host launchers (dia_ops.cu)
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
                           cudaStream_t s, int acc32 = 0);
-cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, float *Kpad, cudaStream_t s);
-cudaError_t launch_emit_loss_grad(const double *red, int mk, double *loss, double *grad,
+// nb: background coefficients of the pair (1 for the constant B0)
+cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, int nb, float *Kpad,
+                             cudaStream_t s);
+cudaError_t launch_emit_loss_grad(const double *red, int mk, int nb, double *loss, double *grad,
                                   cudaStream_t s);
 // One optimiser step: the line-search / history half (one CTA), P g and
 // P y_new (many CTAs), the direction half (one CTA).
@@ -231,7 +236,7 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
 // d_pas: device array of npairs descriptors; h_pas: the same on the host
 cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
                            cudaStream_t s);
-int precond_launches(int max_m);   // kernels one launch_precond call enqueues
+int precond_launches(int max_n);   // kernels one launch_precond call enqueues (largest n)
 // Observed Fisher information (dia_fisher.cu): w[p] <- d2l/dM2 at M = I - D for
 // the valid pixels (D = the difference image held in w on entry; 0 where masked)
 cudaError_t launch_fisher_weights(const EvalArgs &ea, float *w, unsigned long long *count,
@@ -242,16 +247,16 @@ void precond_window(int H, int W, int m, bool single, int side, int *y0, int *y1
                     int *x1, int *chunks);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
-cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int init_mode,
-                        double init_sigma, const SelectState *sel, int start_phase,
-                        cudaStream_t s);
-cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp,
+cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,
+                        int init_mode, double init_sigma, const SelectState *sel,
+                        int start_phase, cudaStream_t s);
+cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp, int nb,
                            cudaStream_t s);
 constexpr int kMedianLaunches = 14;   // kernels launch_median enqueues
 cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int ld, int mk,
                           uint32_t *hist, SelectState *sel, int grid, cudaStream_t s);
-cudaError_t launch_pack_outputs(const double *theta, int mk, double *theta_out, float *K_out,
-                                float *b0_out, cudaStream_t s);
+cudaError_t launch_pack_outputs(const double *theta, int mk, int nb, double *theta_out,
+                                float *K_out, float *b0_out, cudaStream_t s);
 // batched: one CTA per pair for the two optimiser halves, P v inside the
 // second (kStepLaunchesBatch kernels)
 constexpr int kStepLaunchesBatch = 2;

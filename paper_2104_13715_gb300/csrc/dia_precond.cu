@@ -3,7 +3,8 @@
 //
 // P is the inverse of the Gauss-Newton Hessian of the per-pixel loss over a
 // window of valid pixels, H = sum_p w_p phi_p phi_p^T / N_window, with
-// phi_p = [R window of p (Eq. 2), 1] and w_p = mask / (variance at M = I):
+// phi_p = [R window of p (Eq. 2), background basis at p (Eq. 18; 1 for B0)]
+// and w_p = mask / (variance at M = I):
 // for the fixed-variance chi^2 this is the exact Hessian (on the window), for
 // the other losses its Gauss-Newton part.  As a Gram matrix it is positive
 // semidefinite; the window keeps its cost to a few ms (pc_window_side).
@@ -51,6 +52,7 @@ __device__ __forceinline__ float pc_weight(const PrecondArgs &a, size_t q) {
 
 constexpr int kGnThreads = 256;
 constexpr int kGnKB = 32;          // pixels per shared-memory batch
+constexpr int kPadCol = -1000;     // column code of the zero padding beyond n
 
 __host__ __device__ inline long long window_px(const PrecondArgs &a) {
     return (long long)(a.y1 - a.y0) * (a.x1 - a.x0);
@@ -95,10 +97,12 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
     __shared__ int offU[kGnT], offV[kGnT];
     __shared__ long long sBase[kGnKB];
     __shared__ float sW[kGnKB];
+    __shared__ float sBg[kGnKB][kBgMax];   // background basis eta^i xi^j of each pixel
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int m = a.m, n = m * m + 1, h = m / 2, ld = a.ld, nt = gn_tiles(n);
+        const int m = a.m, nk = m * m, n = pc_n(a), h = m / 2, ld = a.ld, nt = gn_tiles(n);
+        const int deg = bg_degree_of(a.nbg);
         const int wx = a.x1 - a.x0;
         const long long npx = window_px(a);
         const int nch = a.gn_chunks, nblk = gn_blocks(n);
@@ -108,10 +112,10 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
         gn_block(b, nt, U, V);
         __syncthreads();   // shared memory of the previous pair
         // offset of phi_u in R relative to the window pixel's R[py][px];
-        // -1: the constant of B0, -2: padding (zero)
+        // -1 - c: background basis function c, kPadCol: padding (zero)
         if (tid < 2 * kGnT) {
             const int u = (tid < kGnT ? U : V) * kGnT + (tid & (kGnT - 1));
-            const int o = u < n - 1 ? (u / m) * ld + u % m : (u == n - 1 ? -1 : -2);
+            const int o = u < nk ? (u / m) * ld + u % m : (u < n ? -1 - (u - nk) : kPadCol);
             if (tid < kGnT) offU[tid] = o; else offV[tid - kGnT] = o;
         }
         float acc[4][4];
@@ -135,6 +139,19 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
                     sBase[tid] = (long long)py * ld + px;
                     sW[tid] = a.wmap ? a.wmap[(size_t)py * a.wmap_ld + px]
                                      : pc_weight(a, (size_t)(py + h) * ld + (px + h));
+                    // basis of Eq. 18 in the coefficient order (power of xi fastest)
+                    const float eta = fmaf((float)px, a.eta_s, a.eta0);
+                    const float xi = fmaf((float)py, a.xi_s, a.xi0);
+                    int c = 0;
+                    float ep = 1.f;
+                    for (int i = 0; i <= deg; ++i) {
+                        float t = ep;
+                        for (int j = 0; j <= deg - i; ++j) {
+                            sBg[tid][c++] = t;
+                            t *= xi;
+                        }
+                        ep *= eta;
+                    }
                 } else {
                     sBase[tid] = -1;
                     sW[tid] = 0.f;
@@ -147,8 +164,8 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
                 float va = 0.f, vb = 0.f;
                 if (base >= 0) {
                     const int ou = offU[ul], ov = offV[ul];
-                    va = ou >= 0 ? a.R[base + ou] : (ou == -1 ? 1.f : 0.f);
-                    vb = ov >= 0 ? a.R[base + ov] : (ov == -1 ? 1.f : 0.f);
+                    va = ou >= 0 ? a.R[base + ou] : (ou > kPadCol ? sBg[kk][-1 - ou] : 0.f);
+                    vb = ov >= 0 ? a.R[base + ov] : (ov > kPadCol ? sBg[kk][-1 - ov] : 0.f);
                 }
                 sA[kk][ul] = sW[kk] * va;
                 sB[kk][ul] = vb;
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
 __global__ void fill_kernel(const PrecondArgs *pas, int npairs) {
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int n = a.m * a.m + 1, np = pc_np(n), nt = gn_tiles(n), nblk = gn_blocks(n);
+        const int n = pc_n(a), np = pc_np(n), nt = gn_tiles(n), nblk = gn_blocks(n);
         const int nch = a.gn_chunks;
         const double inv = a.scale;
         for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)np * np;
@@ -256,7 +273,7 @@ __global__ void __launch_bounds__(1024) chol_diag_kernel(const PrecondArgs *pas,
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
         const PrecondArgs &a = pas[p];
-        const int np = pc_np(a.m * a.m + 1);
+        const int np = pc_np(pc_n(a));
         if (K >= np / kB) continue;
         __syncthreads();
         if (threadIdx.x == 0) bad = 0;
@@ -302,7 +319,7 @@ __global__ void __launch_bounds__(1024) chol_panel_kernel(const PrecondArgs *pas
     const int I = K + 1 + blockIdx.x;
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int np = pc_np(a.m * a.m + 1);
+        const int np = pc_np(pc_n(a));
         if (I >= np / kB) continue;
         __syncthreads();
         load_tile(a.A64, np, I, K, As);
@@ -321,7 +338,7 @@ __global__ void __launch_bounds__(1024) chol_update_kernel(const PrecondArgs *pa
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int np = pc_np(a.m * a.m + 1), nb = np / kB, r = nb - K - 1;
+        const int np = pc_np(pc_n(a)), nb = np / kB, r = nb - K - 1;
         if (r <= 0 || (int)blockIdx.x >= r * r) continue;
         const int I = K + 1 + blockIdx.x / r, J = K + 1 + blockIdx.x % r;
         if (J > I) continue;
@@ -344,7 +361,7 @@ __global__ void __launch_bounds__(1024) trtri_kernel(const PrecondArgs *pas, int
     const int J = blockIdx.x, I = J + d;
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int np = pc_np(a.m * a.m + 1);
+        const int np = pc_np(pc_n(a));
         if (I >= np / kB) continue;
         double y = 0.0;
         for (int T = J; T < I; ++T) {
@@ -372,7 +389,7 @@ __global__ void __launch_bounds__(1024) gram_kernel(const PrecondArgs *pas, int 
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int n = a.m * a.m + 1, np = pc_np(n), nb = np / kB;
+        const int n = pc_n(a), np = pc_np(n), nb = np / kB;
         if ((int)blockIdx.x >= nb * nb) continue;
         const int I = blockIdx.x / nb, J = blockIdx.x % nb;
         if (J > I) continue;
@@ -412,18 +429,18 @@ __global__ void __launch_bounds__(kPaThreads) pc_apply_kernel(const StepArgs a) 
 cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, int npairs,
                            cudaStream_t s) {
     if (npairs < 1) return cudaErrorInvalidValue;
-    int max_m = 1, gn_grid = 1;
+    int max_n = 1, gn_grid = 1;
     for (int i = 0; i < npairs; ++i) {
         const PrecondArgs &a = h_pas[i];
-        const int n = a.m * a.m + 1;
-        if (n > kPcMaxN || a.x1 <= a.x0 || a.y1 <= a.y0 || a.ldp < n || (a.ldp & 3) != 0 ||
+        const int n = pc_n(a);
+        if (a.nbg < 1 || a.nbg > kBgMax || n > kPcMaxN || a.x1 <= a.x0 || a.y1 <= a.y0 || a.ldp < n || (a.ldp & 3) != 0 ||
             a.gn_chunks < 1 || (a.gn_chunks > 1 && !a.part) || a.flush < 1 ||
             (long long)a.gn_chunks > window_px(a))
             return cudaErrorInvalidValue;
-        max_m = max(max_m, a.m);
+        max_n = max(max_n, n);
         gn_grid = max(gn_grid, gn_blocks(n) * a.gn_chunks);
     }
-    const int max_n = max_m * max_m + 1, nb = pc_np(max_n) / kB;
+    const int nb = pc_np(max_n) / kB;
     const unsigned gy = (unsigned)min(npairs, 65535);
     gn_kernel<<<dim3(gn_grid, gy), kGnThreads, 0, s>>>(d_pas, npairs);
     fill_kernel<<<dim3(npairs == 1 ? 64 : 8, gy), 256, 0, s>>>(d_pas, npairs);
@@ -440,8 +457,8 @@ cudaError_t launch_precond(const PrecondArgs *d_pas, const PrecondArgs *h_pas, i
     return cudaGetLastError();
 }
 
-int precond_launches(int max_m) {
-    const int nb = pc_np(max_m * max_m + 1) / kB;
+int precond_launches(int max_n) {
+    const int nb = pc_np(max_n) / kB;
     return 2 + nb + 2 * (nb - 1) + (nb - 1) + 1;
 }
 

@@ -35,7 +35,7 @@ class Pair(ctypes.Structure):
     _fields_ = [("ref", ctypes.c_void_p), ("img", ctypes.c_void_p), ("mask", ctypes.c_void_p),
                 ("var", ctypes.c_void_p), ("flat", ctypes.c_void_p),
                 ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("ld", ctypes.c_int32),
-                ("m", ctypes.c_int32), ("mem", ctypes.c_int32)]
+                ("m", ctypes.c_int32), ("mem", ctypes.c_int32), ("bg_degree", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):
@@ -212,7 +212,13 @@ def _img(t, H, W, name, dtype=torch.float32):
     return t
 
 
-def make_pair(R, I, m, mask=None, var=None, flat=None):
+def n_params(m, bg_degree=0):
+    """Entries of theta: m*m kernel pixels and (d+1)(d+2)/2 background
+    coefficients (Eq. 18; 1 = the constant B0)."""
+    return m * m + (bg_degree + 1) * (bg_degree + 2) // 2
+
+
+def make_pair(R, I, m, mask=None, var=None, flat=None, bg_degree=0):
     """dia_pair over torch tensors (all on one CUDA device, or all on the host
     in pinned or pageable memory).  Returns (pair, keep-alive list)."""
     H, W = R.shape
@@ -232,7 +238,7 @@ def make_pair(R, I, m, mask=None, var=None, flat=None):
     p = Pair(R.data_ptr(), I.data_ptr(), mask.data_ptr() if mask is not None else None,
              var.data_ptr() if var is not None else None,
              flat.data_ptr() if flat is not None else None, H, W, ld, m,
-             MEM_HOST if host else MEM_DEVICE)
+             MEM_HOST if host else MEM_DEVICE, bg_degree)
     return p, [R, I, mask, var, flat]
 
 
@@ -250,13 +256,13 @@ def workspace(H, W, m, ld=None, clip=False, host=False, device=None) -> torch.Te
 
 
 def loss_grad(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, ws=None,
-              stream=None):
+              stream=None, bg_degree=0):
     """One fused evaluation on the device: returns (loss[1], grad[n]) float64 tensors."""
-    pair, keep = make_pair(R, I, m, mask, var, flat)
+    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
     if not R.is_cuda:
         raise ValueError("loss_grad takes device tensors")
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
-    n = m * m + 1
+    n = n_params(m, bg_degree)
     if theta.numel() != n:
         raise ValueError(f"theta must have {n} entries")
     ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
@@ -269,15 +275,15 @@ def loss_grad(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, ws
 
 
 def fisher(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, want_F=True,
-           want_cov=True, stream=None):
+           want_cov=True, stream=None, bg_degree=0):
     """dia_fisher: observed Fisher information F (the Hessian of the loss at
     theta, Sec. 2.5) and the covariance estimate F^-1.  Returns dict(F, cov,
     info) with n x n float64 device tensors (None where not asked for; cov is
     NaN when F is not positive definite)."""
-    pair, keep = make_pair(R, I, m, mask, var, flat)
+    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
     if not R.is_cuda:
         raise ValueError("fisher takes device tensors")
-    n = m * m + 1
+    n = n_params(m, bg_degree)
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
     nb = lib.dia_fisher_workspace_size(R.shape[0], R.shape[1], R.stride(0), m)
     if nb == 0:
@@ -293,15 +299,15 @@ def fisher(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, want_
 
 
 def loss_grad_noalloc(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None,
-                      stream=None):
+                      stream=None, bg_degree=0):
     """dia_loss_grad_noalloc: the same evaluation without a workspace (the
     library's fixed device scratch array is used instead).  Returns
     (loss[1], grad[n]) float64 tensors."""
-    pair, keep = make_pair(R, I, m, mask, var, flat)
+    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
     if not R.is_cuda:
         raise ValueError("loss_grad_noalloc takes device tensors")
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
-    n = m * m + 1
+    n = n_params(m, bg_degree)
     if theta.numel() != n:
         raise ValueError(f"theta must have {n} entries")
     loss = torch.empty(1, dtype=torch.float64, device=R.device)
@@ -312,8 +318,8 @@ def loss_grad_noalloc(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=
     return loss, grad
 
 
-def diff_image(R, I, m, theta, ws=None, stream=None):
-    pair, keep = make_pair(R, I, m)
+def diff_image(R, I, m, theta, ws=None, stream=None, bg_degree=0):
+    pair, keep = make_pair(R, I, m, bg_degree=bg_degree)
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
     ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
     h = m // 2
@@ -324,11 +330,13 @@ def diff_image(R, I, m, theta, ws=None, stream=None):
 
 
 def fit(R, I, m, spec: LossSpec, opts: Opts = None, mask=None, var=None, flat=None,
-        theta0=None, want_diff=True, want_mask=False, ws=None, stream=None, check=True):
+        theta0=None, want_diff=True, want_mask=False, ws=None, stream=None, check=True,
+        bg_degree=0):
     """dia_fit.  Tensors on one CUDA device, or all on the host (the library
     then stages them through the workspace and returns host tensors).
+    ``bg_degree``: degree of the polynomial background (Eq. 18).
     Returns dict(theta, K, b0, diff, mask, info)."""
-    pair, keep = make_pair(R, I, m, mask, var, flat)
+    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
     host = pair.mem == MEM_HOST
     dev = R.device
     opts = opts if opts is not None else default_opts()
@@ -342,7 +350,9 @@ def fit(R, I, m, spec: LossSpec, opts: Opts = None, mask=None, var=None, flat=No
     if ws is None:
         ws = workspace(pair.H, pair.W, m, pair.ld, clip, host,
                        device=None if host else dev)
-    n = m * m + 1
+    n = n_params(m, bg_degree)
+    if th0 is not None and th0.size != n:
+        raise ValueError(f"theta0 must have {n} entries")
     h = m // 2
     kw = dict(device=dev)
     if host:
@@ -364,14 +374,15 @@ def fit(R, I, m, spec: LossSpec, opts: Opts = None, mask=None, var=None, flat=No
 
 
 def fit_batch(items, spec: LossSpec, opts: Opts = None, want_diff=False, ws=None, stream=None):
-    """dia_fit_batch over a list of dicts {R, I, m, mask?, var?, flat?} of device
-    tensors.  Returns dict(thetas=[float64 tensors], diffs=[...] or None,
-    infos=[dict], status)."""
+    """dia_fit_batch over a list of dicts {R, I, m, mask?, var?, flat?,
+    bg_degree?} of device tensors.  Returns dict(thetas=[float64 tensors],
+    diffs=[...] or None, infos=[dict], status)."""
     n = len(items)
     pairs = (Pair * n)()
     keep = []
     for i, it in enumerate(items):
-        p, k = make_pair(it["R"], it["I"], it["m"], it.get("mask"), it.get("var"), it.get("flat"))
+        p, k = make_pair(it["R"], it["I"], it["m"], it.get("mask"), it.get("var"), it.get("flat"),
+                         it.get("bg_degree", 0))
         if p.mem != MEM_DEVICE:
             raise ValueError("fit_batch takes device tensors")
         pairs[i] = p
@@ -383,7 +394,7 @@ def fit_batch(items, spec: LossSpec, opts: Opts = None, want_diff=False, ws=None
         raise DiaError(DIA_ERR_ARG, "dia_batch_workspace_size")
     if ws is None or ws.numel() < need:
         ws = torch.empty(need, dtype=torch.uint8, device=dev)
-    sizes = [it["m"] * it["m"] + 1 for it in items]
+    sizes = [n_params(it["m"], it.get("bg_degree", 0)) for it in items]
     theta = torch.empty(sum(sizes), dtype=torch.float64, device=dev)
     diffs = None
     dptr = None
@@ -406,20 +417,21 @@ class DiaLossGrad(torch.autograd.Function):
     """L(theta) with the hand-written fused backward (Sec. 2.3).
 
     forward runs one fused pass that returns the loss and keeps only the
-    gradient vector (m*m + 1 float64 values): no model image or other
+    gradient vector (len(theta) float64 values): no model image or other
     activation is stored; backward scales that gradient by grad_output."""
 
     @staticmethod
-    def forward(ctx, theta, R, I, m, spec, mask=None, var=None, flat=None):
-        loss, grad = loss_grad(R, I, m, theta.detach(), spec, mask, var, flat)
+    def forward(ctx, theta, R, I, m, spec, mask=None, var=None, flat=None, bg_degree=0):
+        loss, grad = loss_grad(R, I, m, theta.detach(), spec, mask, var, flat,
+                               bg_degree=bg_degree)
         ctx.save_for_backward(grad)
         return loss.reshape(()).to(theta.dtype)
 
     @staticmethod
     def backward(ctx, gout):
         (grad,) = ctx.saved_tensors
-        return (gout * grad).to(gout.dtype), None, None, None, None, None, None, None
+        return (gout * grad).to(gout.dtype), None, None, None, None, None, None, None, None
 
 
-def dia_loss(theta, R, I, m, spec, mask=None, var=None, flat=None):
-    return DiaLossGrad.apply(theta, R, I, m, spec, mask, var, flat)
+def dia_loss(theta, R, I, m, spec, mask=None, var=None, flat=None, bg_degree=0):
+    return DiaLossGrad.apply(theta, R, I, m, spec, mask, var, flat, bg_degree)

@@ -77,6 +77,14 @@ def test_arguments_rejected_before_any_launch(native):
     p = native.Pair(1, 2, None, None, None, 16, 16, 16, 3, 0)
     assert native.lib.dia_loss_grad(ctypes.byref(p), ctypes.byref(bad), 1, 1, 1, None, 0,
                                     None) == native.DIA_ERR_ARG
+    # background degree outside [0, DIA_MAX_BG_DEGREE] (Eq. 18)
+    for deg in (-1, 5):
+        pd = native.Pair(1, 2, None, None, None, 16, 16, 16, 3, 0, deg)
+        assert native.lib.dia_loss_grad(ctypes.byref(pd), ctypes.byref(spec), 1, 1, 1, 256,
+                                        1 << 30, None) == native.DIA_ERR_ARG
+        assert native.lib.dia_loss_grad_noalloc(ctypes.byref(pd), ctypes.byref(spec), 1, 1, 1,
+                                                None) == native.DIA_ERR_ARG
+    assert native.n_params(5, 0) == 26 and native.n_params(5, 2) == 31
     # workspace too small
     assert native.lib.dia_loss_grad(ctypes.byref(p), ctypes.byref(spec), 1, 1, 1, 256, 8,
                                     None) == native.DIA_ERR_WORKSPACE
