@@ -226,6 +226,10 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
         if (rc != DIA_OK) return rc;
     }
     if (!kernel_info(pair->m, &c.ki)) return DIA_ERR_UNSUPPORTED;
+    if (pair->bg_degree > 0) {   // the kernels with the polynomial background
+        c.ki.fn[kModeGrad] = c.ki.fn_bg[kModeGrad];
+        c.ki.fn[kModeForward] = c.ki.fn_bg[kModeForward];
+    }
     make_layout(pair->H, pair->W, pair->ld, pair->m, clip, pair->mem, c.ki, c.L);
     if (!workspace || ws_bytes < c.L.total || ((uintptr_t)workspace % kAlign) != 0)
         return DIA_ERR_WORKSPACE;

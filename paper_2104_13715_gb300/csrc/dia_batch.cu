@@ -265,8 +265,11 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     lp.var_scalar = loss->var_scalar;
     lp.var_floor = loss->var_floor;
     const int H = opts.history;
-    int max_n = 1;
-    for (int i = 0; i < npairs; ++i) max_n = std::max(max_n, P.pp[i].n);
+    int max_n = 1, bg = 0;   // bg: some pair has a polynomial background
+    for (int i = 0; i < npairs; ++i) {
+        max_n = std::max(max_n, P.pp[i].n);
+        bg |= pairs[i].bg_degree > 0;
+    }
     for (int i = 0; i < npairs; ++i) {
         const dia_pair &p = pairs[i];
         const PairPlan &q = P.pp[i];
@@ -402,17 +405,17 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         g_items[g] = d_items + P.gbeg[g];
         if (n_it[g] == 0) continue;
         for (int mode = 0; mode < 2; ++mode)
-            DB_CK(cudaFuncSetAttribute(batch_kernel_ptr(g, mode),
+            DB_CK(cudaFuncSetAttribute(batch_kernel_ptr(g, mode, bg),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem));
         int occ = 1;
-        DB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(g, kModeGrad),
+        DB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(g, kModeGrad, bg),
                                                             kBW * 32, kBatchSmem));
         grid[g] = std::min(n_it[g], sms * (occ < 1 ? 1 : occ));
     }
     auto launch_group = [&](int g, int mode, int *counter, cudaStream_t st) -> cudaError_t {
         void *params[] = {(void *)&d_eas, (void *)&d_mks, (void *)&g_items[g], (void *)&n_it[g],
                           (void *)&counter, (void *)&d_parts};
-        return cudaLaunchKernel(batch_kernel_ptr(g, mode), dim3(grid[g]), dim3(kBW * 32), params,
+        return cudaLaunchKernel(batch_kernel_ptr(g, mode, bg), dim3(grid[g]), dim3(kBW * 32), params,
                                 kBatchSmem, st);
     };
 
@@ -433,6 +436,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     app(grid, sizeof grid);
     app(&opts.graph_iters, sizeof opts.graph_iters);
     app(&max_n, sizeof max_n);
+    app(&bg, sizeof bg);
     // the captured kernels take pointers into the workspace at these offsets
     const size_t offs[] = {P.off_hdr, P.off_eas,   P.off_mks,   P.off_items, P.off_sa,
                            P.off_red, P.off_thoff, P.off_pas,   P.off_pairs, P.off_parts};

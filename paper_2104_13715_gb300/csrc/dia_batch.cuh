@@ -38,7 +38,8 @@ struct BatchItem {
 // 3 = {25,27,29,31}.
 __host__ __device__ constexpr int batch_group(int mk) { return mk <= 7 ? 0 : mk <= 15 ? 1 : mk <= 23 ? 2 : 3; }
 
-template <int GROUP, int MODE>
+// BG = 1: pairs may have a polynomial background (EvalArgs::bg_deg > 0)
+template <int GROUP, int MODE, int BG = 0>
 __global__ void __launch_bounds__(kBW * 32, 1)
     eval_batch_kernel(const EvalArgs *eas, const int *mks, const BatchItem *items, int n_items,
                       int *counter, double *partials) {
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(kBW * 32, 1)
 #define DIA_CASE(MKV, PFV, SPV)                                                              \
     case MKV:                                                                                \
         if constexpr (batch_group(MKV) == GROUP)                                             \
-            process_tiles<MKV, kBW, kBQF, PFV, SPV, MODE>(s_ea, smem, item.t0, item.t1, 1, out); \
+            process_tiles<MKV, kBW, kBQF, PFV, SPV, MODE, 0, BG>(s_ea, smem, item.t0, item.t1, 1, out); \
         break;
                 DIA_BATCH_SIDES(DIA_CASE)
 #undef DIA_CASE
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kBW * 32, 1)
     }
 }
 
-// kernel pointers of a group (defined in dia_batch_gN.cu)
-const void *batch_kernel_ptr(int group, int mode);
+// kernel pointers of a group (defined in dia_batch_gN.cu, dia_batch_gN_bg.cu)
+const void *batch_kernel_ptr(int group, int mode, int bg);
 
 }  // namespace dia

@@ -1,0 +1,9 @@
+// Batched evaluation kernels of kernel-side group 2, polynomial background.
+#include "dia_batch.cuh"
+
+namespace dia {
+const void *batch_kernel_ptr_bg_2(int mode) {
+    return mode == kModeGrad ? (const void *)&eval_batch_kernel<2, kModeGrad, 1>
+                             : (const void *)&eval_batch_kernel<2, kModeForward, 1>;
+}
+}  // namespace dia

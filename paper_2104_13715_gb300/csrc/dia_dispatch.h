@@ -10,7 +10,8 @@ constexpr int kMaxKernelSide = 31;
 
 struct KernelInfo {
     int mk, variant, nw, qf, minb, th, nt, smem, np, kp, f2;
-    const void *fn[2];   // [kModeGrad], [kModeForward]
+    const void *fn[2];      // [kModeGrad], [kModeForward]: constant background B0
+    const void *fn_bg[2];   // the same with the polynomial background (Eq. 18)
 };
 
 // Kernel of side mk (odd, 1..31) in its currently selected tile variant.

@@ -448,7 +448,9 @@ __device__ __forceinline__ void bwd_rows(const float *rrow, const float *g0, con
 // pair; the CTA's partial sums (m*m + 5 float64) go to `out`.  Called by
 // the single-pair kernel (tiles strided over the grid) and by the batched
 // kernel (a contiguous tile range of one pair per work item).
-template <int MK, int NW, int QF, int PF, int SPLIT, int MODE, int F2 = 0>
+// BG = 1: the kernel also handles a polynomial background (args.bg_deg > 0);
+// BG = 0 kernels take the constant B0 only.
+template <int MK, int NW, int QF, int PF, int SPLIT, int MODE, int F2 = 0, int BG = 0>
 __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned char *smem, int t_begin,
                                               int t_end, int t_step, double *out) {
     using S = EvalShape<MK, NW, QF, SPLIT, F2>;
@@ -484,7 +486,10 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     }
     float *gt = gs + S::GPAD * kTW;   // g tile row 0
     __syncthreads();
-    const float B0 = Ks[MK * KP];
+    const bool poly = BG && args.bg_deg > 0;
+    // the constant background, added in the epilogue; a polynomial one is added
+    // to the accumulators before it
+    const float B0 = poly ? 0.f : Ks[MK * KP];
 
     constexpr int KF = S::KF, RM = S::RM;
     // whole-tile kernel rows of this warp: [a_lo, a_lo + nq)
@@ -541,7 +546,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             stage_tile<S::RROWS, RP, S::NT>(buf ? Rbuf0 : Rbuf1, args, (nxt / args.tiles_x) * TH,
                                             (nxt % args.tiles_x) * kTW, vec);
         cp_async_commit();
-        if (args.bg_deg > 0) {
+        if (poly) {
             // c_i(xi) = sum_j b_ij xi^j of each tile row (Eq. 18), by Horner in xi
             for (int r = tid; r < TH; r += S::NT) {
                 const float xi = fmaf((float)(ty0 + r), args.xi_s, args.xi0);
@@ -695,7 +700,21 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             }
         }
 
-        // ---- 3. epilogue: loss terms, g -> shared tile
+        // ---- 3. epilogue: loss terms, g -> shared tile (a polynomial background
+        // first: B = sum_i c_i eta^i by Horner over the row's c_i)
+        if (poly) {
+#pragma unroll
+            for (int q = 0; q < QF; ++q) {
+                const float *c = bgrow + (warp * QF + q) * 8;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float eta = fmaf((float)(tx0 + 4 * lane + p), args.eta_s, args.eta0);
+                    float b = c[args.bg_deg];
+                    for (int i = args.bg_deg - 1; i >= 0; --i) b = fmaf(b, eta, c[i]);
+                    acc[q][p] += b;
+                }
+            }
+        }
 #pragma unroll
         for (int q = 0; q < QF; ++q) {
             const int yl = warp * QF + q;
@@ -708,14 +727,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
                 if (y < args.Hv && x < args.Wv) {
                     const size_t off = (size_t)(y + H2) * args.ld + (x + H2);
                     const bool use = (args.mask == nullptr) || (args.mask[off] != 0);
-                    float Bp = B0;
-                    if (args.bg_deg > 0) {   // Horner in eta over the row's c_i
-                        const float eta = fmaf((float)x, args.eta_s, args.eta0);
-                        const float *c = bgrow + yl * 8;
-                        Bp = c[args.bg_deg];
-                        for (int i = args.bg_deg - 1; i >= 0; --i) Bp = fmaf(Bp, eta, c[i]);
-                    }
-                    const float M = acc[q][p] + Bp;
+                    const float M = acc[q][p] + B0;
                     const float Iv = __ldg(args.I + off);
                     const float vm = args.var ? __ldg(args.var + off) : args.lp.var_scalar;
                     const float F = args.flat ? __ldg(args.flat + off) : 1.0f;
@@ -744,7 +756,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             continue;
         }
         __syncthreads();  // g tile complete
-        if (args.bg_deg > 0) bg_moments<QF>(args, gt, ty0, tx0, acc64 + kAccW * warp, warp, lane);
+        if (poly) bg_moments<QF>(args, gt, ty0, tx0, acc64 + kAccW * warp, warp, lane);
 
         // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b]
         float dk[NK];
@@ -842,11 +854,11 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     }
 }
 
-template <int MK, int NW, int QF, int PF, int SPLIT, int MODE, int F2 = 0>
+template <int MK, int NW, int QF, int PF, int SPLIT, int MODE, int F2 = 0, int BG = 0>
 __global__ void __launch_bounds__(NW * 32, 1) eval_kernel(const EvalArgs args) {
     if (args.done_flag != nullptr && *((volatile const int *)args.done_flag) != 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    process_tiles<MK, NW, QF, PF, SPLIT, MODE, F2>(
+    process_tiles<MK, NW, QF, PF, SPLIT, MODE, F2, BG>(
         args, smem, blockIdx.x, args.n_tiles, gridDim.x,
         MODE == kModeGrad ? args.partials + (size_t)blockIdx.x * EvalShape<MK, NW, QF, SPLIT, F2>::NP
                           : nullptr);

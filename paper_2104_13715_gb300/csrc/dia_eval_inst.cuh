@@ -22,6 +22,9 @@
         o->kp = S::KP;                                                                         \
         o->fn[kModeGrad] = (const void *)&eval_kernel<MKV, NWV, QFV, MBV, SPV, kModeGrad, F2V>;     \
         o->fn[kModeForward] = (const void *)&eval_kernel<MKV, NWV, QFV, MBV, SPV, kModeForward, F2V>; \
+        o->fn_bg[kModeGrad] = (const void *)&eval_kernel<MKV, NWV, QFV, MBV, SPV, kModeGrad, F2V, 1>; \
+        o->fn_bg[kModeForward] =                                                               \
+            (const void *)&eval_kernel<MKV, NWV, QFV, MBV, SPV, kModeForward, F2V, 1>;         \
         return true;                                                                           \
     }                                                                                          \
     }

@@ -15,6 +15,8 @@
 // the address is looked up once per device with cudaGetSymbolAddress.
 #include <cstring>
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "../../include/dia.h"
 #include "dia_dispatch.h"
@@ -35,7 +37,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
-bool g_attr_set[kMaxDevices][DIA_MAX_M + 1][2] = {};
+std::set<std::pair<int, const void *>> g_attr_set;   // (device, kernel) with the smem attribute
 
 // Device address of the scratch array for the current device (looked up on
 // the first call on that device, with the device current).
@@ -61,11 +63,11 @@ cudaError_t set_smem_attr(const KernelInfo &ki, int *occ) {
     if (e != cudaSuccess) return e;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_attr_set[dev][ki.mk][0]) {
+        if (!g_attr_set.count({dev, ki.fn[kModeGrad]})) {
             e = cudaFuncSetAttribute(ki.fn[kModeGrad], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      ki.smem);
             if (e != cudaSuccess) return e;
-            g_attr_set[dev][ki.mk][0] = true;
+            g_attr_set.insert({dev, ki.fn[kModeGrad]});
         }
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, ki.fn[kModeGrad], ki.nt, ki.smem);
@@ -100,6 +102,10 @@ extern "C" dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss
 
     KernelInfo ki;
     if (!kernel_info(m, &ki)) return DIA_ERR_UNSUPPORTED;
+    if (pair->bg_degree > 0) {   // the kernels with the polynomial background
+        ki.fn[kModeGrad] = ki.fn_bg[kModeGrad];
+        ki.fn[kModeForward] = ki.fn_bg[kModeForward];
+    }
     const size_t part_bytes_per_cta = (size_t)ki.np * sizeof(double);
     const size_t max_ctas = (kScratchBytes - kPartOff) / part_bytes_per_cta;
     // sizes the fixed scratch cannot hold are refused (cannot happen for m <= DIA_MAX_M)
