@@ -318,38 +318,71 @@ struct EvalShape {
     // F2: float2 pairs (K[a][b], K[a-1][b]) for the paired forward
     static constexpr int OFF_K2 = (OFF_KS + SZ_KS + 15) & ~15;
     static constexpr int SZ_K2 = (F2 & 1) ? MK * KP * 8 : 0;
-    // background: c_i(xi) of each tile row (8 floats per row)
-    static constexpr int OFF_BG = OFF_K2 + SZ_K2;
-    static constexpr int SZ_BG = TH * 8 * 4;
-    static constexpr int SMEM = OFF_BG + SZ_BG;
+    static constexpr int SMEM = OFF_K2 + SZ_K2;
 };
 
+// Polynomial background (Eq. 18) of the tile's TH x kTW pixels, written to
+// B_out (pitch kTW): each thread takes one row segment of 16 pixels, forms the
+// row's c_i(xi) = sum_j b_ij xi^j by Horner in xi and then B = sum_i c_i eta^i
+// by Horner in eta.  b: the coefficients in theta order (float32).  Kept out of
+// line so that the tile loop's code stays as compact as without a background.
+struct BgCoords {
+    int deg;
+    float eta0, eta_s, xi0, xi_s;
+};
+
+static __device__ __noinline__ void bg_tile(const BgCoords bc, const float *b, float *B_out, int TH,
+                                     int ty0, int tx0, int tid, int nt) {
+    const int d = bc.deg;
+    for (int e = tid; e < TH * (kTW / 16); e += nt) {
+        const int r = e / (kTW / 16), x0 = (e % (kTW / 16)) * 16;
+        const float xi = fmaf((float)(ty0 + r), bc.xi_s, bc.xi0);
+        float c[kBgMaxDeg + 1];
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i <= kBgMaxDeg; ++i) {
+            c[i] = 0.f;
+            if (i <= d) {
+                for (int j = d - i; j >= 0; --j) c[i] = fmaf(c[i], xi, b[k + j]);
+                k += d - i + 1;
+            }
+        }
+        float *out = B_out + r * kTW + x0;
+#pragma unroll 4
+        for (int p = 0; p < 16; ++p) {
+            const float eta = fmaf((float)(tx0 + x0 + p), bc.eta_s, bc.eta0);
+            float v = c[kBgMaxDeg];
+#pragma unroll
+            for (int i = kBgMaxDeg - 1; i >= 0; --i) v = fmaf(v, eta, c[i]);
+            out[p] = v;
+        }
+    }
+}
+
 // Moments sum_p g_p eta^i xi^j of the background coefficients (Eq. 18)
-// over this warp's QF rows of the g tile (out-of-range and masked pixels hold
+// over this warp's qf rows of the g tile (out-of-range and masked pixels hold
 // g = 0): float32 per lane over its 4 pixels of each row, summed over the warp,
 // added by lane 0 to the warp's float64 slots w[5 + c - 1], c the coefficient
 // index for the pair's degree d (c = 0, dL/dB0, is summed in the epilogue).
 // All kBgMax moments of the largest degree are formed in registers (fixed
-// indices) and those with i + j <= d kept.
-template <int QF>
-__device__ __forceinline__ void bg_moments(const EvalArgs &args, const float *gt, int ty0, int tx0,
-                                           double *w, int warp, int lane) {
+// indices) and those with i + j <= d kept.  Out of line, like bg_tile.
+static __device__ __noinline__ void bg_moments(const BgCoords bc, int acc32, const float *gt, int qf,
+                                        int ty0, int tx0, double *w, int warp, int lane) {
     float mom[kBgMax];
 #pragma unroll
     for (int k = 0; k < kBgMax; ++k) mom[k] = 0.f;
-#pragma unroll
-    for (int q = 0; q < QF; ++q) {
-        const int yl = warp * QF + q;
-        const float xi = fmaf((float)(ty0 + yl), args.xi_s, args.xi0);
+    for (int q = 0; q < qf; ++q) {
+        const int yl = warp * qf + q;
+        const float xi = fmaf((float)(ty0 + yl), bc.xi_s, bc.xi0);
+        const float4 g4 = *reinterpret_cast<const float4 *>(gt + yl * kTW + 4 * lane);
+        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
         float sx[kBgMaxDeg + 1];   // sum over the lane's pixels of g eta^i
 #pragma unroll
         for (int i = 0; i <= kBgMaxDeg; ++i) sx[i] = 0.f;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-            const int xl = 4 * lane + p;
-            const float g = gt[yl * kTW + xl];
-            const float eta = fmaf((float)(tx0 + xl), args.eta_s, args.eta0);
-            float e = g;
+            const float eta = fmaf((float)(tx0 + 4 * lane + p), bc.eta_s, bc.eta0);
+            float e = gv[p];
 #pragma unroll
             for (int i = 0; i <= kBgMaxDeg; ++i) {
                 sx[i] += e;
@@ -367,7 +400,7 @@ __device__ __forceinline__ void bg_moments(const EvalArgs &args, const float *gt
             }
         }
     }
-    const int d = args.bg_deg;
+    const int d = bc.deg;
     int k = 0;
 #pragma unroll
     for (int i = 0; i <= kBgMaxDeg; ++i) {
@@ -378,7 +411,7 @@ __device__ __forceinline__ void bg_moments(const EvalArgs &args, const float *gt
             if (lane == 0 && i + j <= d) {
                 const int c = i * (d + 1) - i * (i - 1) / 2 + j;   // index for degree d
                 double *slot = w + 5 + c - 1;
-                *slot = args.acc32 ? (double)((float)*slot + v) : *slot + (double)v;
+                *slot = acc32 ? (double)((float)*slot + v) : *slot + (double)v;
             }
         }
     }
@@ -463,7 +496,6 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     float *gs = reinterpret_cast<float *>(smem + S::OFF_G);
     float *Ks = reinterpret_cast<float *>(smem + S::OFF_K);
     double *acc64 = reinterpret_cast<double *>(smem + S::OFF_D);  // per warp, kAccW each
-    float *bgrow = reinterpret_cast<float *>(smem + S::OFF_BG);     // c_i(xi) per tile row
     float *kahan = reinterpret_cast<float *>(smem + S::OFF_KS);    // per warp [NK sums | NK comps]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -487,6 +519,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     float *gt = gs + S::GPAD * kTW;   // g tile row 0
     __syncthreads();
     const bool poly = BG && args.bg_deg > 0;
+    const BgCoords bc = {args.bg_deg, args.eta0, args.eta_s, args.xi0, args.xi_s};
     // the constant background, added in the epilogue; a polynomial one is added
     // to the accumulators before it
     const float B0 = poly ? 0.f : Ks[MK * KP];
@@ -546,22 +579,9 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             stage_tile<S::RROWS, RP, S::NT>(buf ? Rbuf0 : Rbuf1, args, (nxt / args.tiles_x) * TH,
                                             (nxt % args.tiles_x) * kTW, vec);
         cp_async_commit();
-        if (poly) {
-            // c_i(xi) = sum_j b_ij xi^j of each tile row (Eq. 18), by Horner in xi
-            for (int r = tid; r < TH; r += S::NT) {
-                const float xi = fmaf((float)(ty0 + r), args.xi_s, args.xi0);
-                int k = MK * KP;
-                for (int i = 0; i <= kBgMaxDeg; ++i) {
-                    float c = 0.f;
-                    if (i <= args.bg_deg) {
-                        const int nj = args.bg_deg - i;
-                        for (int j = nj; j >= 0; --j) c = fmaf(c, xi, Ks[k + j]);
-                        k += nj + 1;
-                    }
-                    bgrow[r * 8 + i] = c;
-                }
-            }
-        }
+        // a polynomial background: B over the tile into the g tile's rows (the
+        // epilogue reads it back before writing g there)
+        if (poly) bg_tile(bc, Ks + MK * KP, gt, TH, ty0, tx0, tid, S::NT);
         cp_async_wait<1>();   // this tile's copies have landed
         __syncthreads();
         const float *Rs = buf ? Rbuf1 : Rbuf0;
@@ -700,21 +720,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             }
         }
 
-        // ---- 3. epilogue: loss terms, g -> shared tile (a polynomial background
-        // first: B = sum_i c_i eta^i by Horner over the row's c_i)
-        if (poly) {
-#pragma unroll
-            for (int q = 0; q < QF; ++q) {
-                const float *c = bgrow + (warp * QF + q) * 8;
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const float eta = fmaf((float)(tx0 + 4 * lane + p), args.eta_s, args.eta0);
-                    float b = c[args.bg_deg];
-                    for (int i = args.bg_deg - 1; i >= 0; --i) b = fmaf(b, eta, c[i]);
-                    acc[q][p] += b;
-                }
-            }
-        }
+        // ---- 3. epilogue: loss terms, g -> shared tile
 #pragma unroll
         for (int q = 0; q < QF; ++q) {
             const int yl = warp * QF + q;
@@ -727,7 +733,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
                 if (y < args.Hv && x < args.Wv) {
                     const size_t off = (size_t)(y + H2) * args.ld + (x + H2);
                     const bool use = (args.mask == nullptr) || (args.mask[off] != 0);
-                    const float M = acc[q][p] + B0;
+                    const float M = acc[q][p] + (poly ? gt[yl * kTW + xl] : B0);
                     const float Iv = __ldg(args.I + off);
                     const float vm = args.var ? __ldg(args.var + off) : args.lp.var_scalar;
                     const float F = args.flat ? __ldg(args.flat + off) : 1.0f;
@@ -756,7 +762,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             continue;
         }
         __syncthreads();  // g tile complete
-        if (poly) bg_moments<QF>(args, gt, ty0, tx0, acc64 + kAccW * warp, warp, lane);
+        if (poly) bg_moments(bc, args.acc32, gt, QF, ty0, tx0, acc64 + kAccW * warp, warp, lane);
 
         // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b]
         float dk[NK];
