@@ -209,3 +209,73 @@ def batch_specs(n_pairs: int = 512, seed: int = 0, side=(64, 512), m_range=(7, 2
 def batch(n_pairs: int = 512, seed: int = 0, **kw) -> list:
     return [make_pair(s, 100_000 * (seed + 1) + k)
             for k, s in enumerate(batch_specs(n_pairs, seed, **kw))]
+
+
+# ---------------------------------------------------------------------------
+# The simulated pairs of the paper's accuracy study (Sec. 3.2, after the S10
+# set of Bramich et al. 2016): 142 x 142 pixels, Gaussian PSFs and kernel,
+# CCD noise with sigma0 = 5 ADU, G = 1, a reference with ten times less
+# variance.  Star profiles are pixel-integrated unit Gaussians (the paper says
+# only "normalised"); the target noise is Gaussian with the noise map of the
+# noiseless target (the paper's step x).
+# ---------------------------------------------------------------------------
+S10_SIZE = 142
+S10_M = 19
+S10_SIGMA0 = 5.0
+S10_SNR_EDGES = (8.0, 40.0, 200.0, 1000.0)   # SNR regimes 1, 2, 3 of the accuracy study
+
+
+def s10_pair(seed: int, size: int = S10_SIZE) -> dict:
+    """One simulated reference/target pair (Sec. 3.2 steps i-x).  Returns the
+    background-subtracted float32 reference, the float32 target, the noiseless
+    target, its noise map sigma_I, phi_R, phi_K, SNR_I and the regime labels
+    (SNR regime 1-3 or 0 outside, sampling regime 0-3 = i-iv)."""
+    rng = np.random.default_rng(seed)
+    H = W = size
+    phi_r = rng.uniform(0.5, 2.5)                         # (i)
+    lg_rho = rng.uniform(0.0, 3.0)                         # (ii) per 100 x 100 px
+    n = max(1, int(round(10 ** lg_rho * H * W / 1e4)))
+    xs = rng.uniform(-0.5, W - 0.5, n)
+    ys = rng.uniform(-0.5, H - 0.5, n)
+    u = rng.uniform(1e-9, 10 ** -4.5, n)                   # (iii) F^-3/2 uniform
+    fl = u ** (-2.0 / 3.0)
+    b = int(np.argmax(fl))                                 # brightest star to the centre
+    xs[b], ys[b] = 0.5 * (W - 1), 0.5 * (H - 1)
+    s_r = rng.uniform(10.0, 1000.0)                        # (v)
+    R_nl = s_r + render_stars((H, W), xs, ys, fl, phi_r)   # (iv)
+    sig_r = math.sqrt(0.1) * np.sqrt(S10_SIGMA0 ** 2 + R_nl)          # (vi)
+    R = R_nl + rng.normal(0.0, 1.0, (H, W)) * sig_r       # (vii)
+    phi_k = rng.uniform(0.5, 2.5)                          # (viii)
+    phi_i = math.sqrt(phi_r * phi_r + phi_k * phi_k)
+    s_i = rng.uniform(10.0, 1000.0)
+    dx, dy = rng.uniform(-0.5, 0.5, 2)
+    I_nl = s_i + render_stars((H, W), xs + dx, ys + dy, fl, phi_i)
+    sig_i = np.sqrt(S10_SIGMA0 ** 2 + I_nl)               # (ix)
+    I = I_nl + rng.normal(0.0, 1.0, (H, W)) * sig_i       # (x)
+    snr = float(np.sum(I_nl - s_i) / math.sqrt(float(np.sum(sig_i ** 2))))
+    e = S10_SNR_EDGES
+    snr_regime = 1 if e[0] < snr < e[1] else 2 if e[1] < snr < e[2] else 3 if e[2] < snr < e[3] else 0
+    samp = (0 if phi_k > 1 else 1) if phi_r > 1 else (2 if phi_k > 1 else 3)
+    sky_ref = float(np.median(R))
+    return dict(R=(R - sky_ref).astype(np.float32), I=I.astype(np.float32), I_noiseless=I_nl,
+                sigma_I=sig_i, phi_r=phi_r, phi_k=phi_k, snr=snr, snr_regime=snr_regime,
+                sampling=samp, m=S10_M, seed=seed)
+
+
+def s10_metrics(d: dict, theta, diff) -> dict:
+    """Fit-quality metrics of the accuracy study (Sec. 3.3) for one fitted
+    pair: P = sum K (Eq. 3), MSE of M against the noiseless target, and the
+    mean and variance (MFB, MFV) of the normalised residuals (I - M)/sigma_I
+    over the N_data valid pixels.  theta, diff: the fit's float64 theta and
+    float32 difference image (valid region)."""
+    m = d["m"]
+    h = m // 2
+    th = np.asarray(theta, np.float64)
+    D = np.asarray(diff, np.float64)
+    v = (slice(h, d["I"].shape[0] - h), slice(h, d["I"].shape[1] - h))
+    I = d["I"][v].astype(np.float64)
+    M = I - D
+    eps = D / d["sigma_I"][v]
+    mfb = float(eps.mean())
+    return dict(P=float(th[:m * m].sum()), MSE=float(np.mean((M - d["I_noiseless"][v]) ** 2)),
+                MFB=mfb, MFV=float(np.sum((eps - mfb) ** 2) / (eps.size - 1)))
