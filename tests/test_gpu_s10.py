@@ -45,15 +45,26 @@ def _bins(rows):
     return {k: v for k, v in b.items() if len(v) >= MIN_BIN}
 
 
-@pytest.mark.parametrize("metric", ["P", "MFV", "MSE"])
-def test_medians_match_the_paper(study, metric):
+@pytest.mark.parametrize("metric,ours_key", [("P", "P"), ("MFV", "MFV"), ("MSE", "MSE_noisy")])
+def test_medians_match_the_paper(study, metric, ours_key):
+    """The paper's tabulated MSE (about 530-630, the mean pixel variance of the
+    target) follows the mean squared residual against the noisy target, not
+    the noiseless-target definition printed beside it (which gives ~15-30 for
+    these fits): the table is compared with that quantity."""
     bins = _bins(study)
     assert len(bins) >= 3, {k: len(v) for k, v in bins.items()}
     for (snr, samp), mets in bins.items():
         med, lo, hi = TABLE[metric][str(snr)][samp]
         se = 1.2533 * 0.5 * (lo + hi) / np.sqrt(len(mets))
-        ours = float(np.median([x[metric] for x in mets]))
+        ours = float(np.median([x[ours_key] for x in mets]))
         assert abs(ours - med) <= 3.0 * se, (metric, snr, samp, len(mets), ours, med, se)
+
+
+def test_mse_against_the_noiseless_target_is_far_below_the_noise(study):
+    """The printed definition of MSE (model against the noiseless target) is a
+    small fraction of the pixel variance for every fit."""
+    for _, _, met in study:
+        assert met["MSE"] < 0.2 * met["MSE_noisy"]
 
 
 def test_mfv_below_one_by_the_fitted_parameters(study):
