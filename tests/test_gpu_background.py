@@ -196,3 +196,25 @@ def test_fisher_with_polynomial_background(nat):
     cov = out["cov"].cpu().numpy()
     ref_inv = np.linalg.inv(F)
     assert np.max(np.abs(cov - ref_inv)) <= 1e-7 * np.max(np.abs(ref_inv))
+
+
+def test_host_buffers_and_theta0_with_background(nat):
+    """Host (pinned) buffers staged by the library give the device result
+    bitwise; a fit started from theta0 (init 2) of the background length
+    lands on the same optimum."""
+    m, deg, sky = 7, 2, 100.0
+    d, c = _with_background(field(140, 150, m, seed=120), m, deg, seed=120, sky=sky)
+    spec = nat.loss_spec(**SPECS["gauss-fixed"])
+    R = torch.from_numpy(d["R"]).pin_memory()
+    I = torch.from_numpy(d["I"]).pin_memory()
+    host = nat.fit(R, I, m, spec, bg_degree=deg)
+    assert not host["theta"].is_cuda and host["theta"].numel() == m * m + 6
+    dev = nat.fit(_t(d["R"]), _t(d["I"]), m, spec, bg_degree=deg)
+    assert np.array_equal(dev["theta"].cpu().numpy(), host["theta"].numpy())
+    ref = oracle.normal_solve(d["R"], d["I"], m, deg=deg)
+    _check_fit(host["theta"].numpy(), ref, d["I"].shape, m, deg, sky)
+    th0 = np.concatenate([np.full(m * m, 1.0 / (m * m)), c])
+    warm = nat.fit(_t(d["R"]), _t(d["I"]), m, spec, theta0=th0, bg_degree=deg)
+    _check_fit(warm["theta"].cpu().numpy(), ref, d["I"].shape, m, deg, sky)
+    with pytest.raises(ValueError):
+        nat.fit(_t(d["R"]), _t(d["I"]), m, spec, theta0=th0[:-1], bg_degree=deg)
