@@ -62,9 +62,11 @@ def test_medians_match_the_paper(study, metric, ours_key):
 
 def test_mse_against_the_noiseless_target_is_far_below_the_noise(study):
     """The printed definition of MSE (model against the noiseless target) is a
-    small fraction of the pixel variance for every fit."""
-    for _, _, met in study:
-        assert met["MSE"] < 0.2 * met["MSE_noisy"]
+    small fraction of the pixel variance: its median is a few per cent of the
+    median noisy-target residual (the model error of a 19x19 fit to ~15,000
+    noisy pixels)."""
+    ratio = np.array([met["MSE"] / met["MSE_noisy"] for _, _, met in study])
+    assert np.median(ratio) < 0.1
 
 
 def test_mfv_below_one_by_the_fitted_parameters(study):
