@@ -528,6 +528,28 @@ dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff
     return DIA_OK;
 }
 
+dia_status dia_diff_image_tc(const dia_pair *pair, const double *theta, float *diff_out,
+                             void *workspace, size_t workspace_bytes, void *stream) {
+    if (!pair || pair->mem != DIA_MEM_DEVICE || !theta || !diff_out) return DIA_ERR_ARG;
+    if (pair->bg_degree != 0) return DIA_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    dia_loss_spec ls;
+    memset(&ls, 0, sizeof(ls));
+    ls.var_scalar = 1.f;
+    dia_status rc = setup(pair, &ls, 0, workspace, workspace_bytes, s, c);
+    if (rc != DIA_OK) return rc;
+    int *status = (int *)c.red;   // scratch: the reduced-sum slots are unused here
+    DIA_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
+    DIA_CK(launch_tc_forward(c.dp.ref, c.dp.img, c.dp.H, c.dp.W, c.dp.ld, pair->m, c.kpad,
+                             c.ki.kp, diff_out, status, s));
+    int hs = 0;
+    DIA_CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DIA_CK(cudaStreamSynchronize(s));
+    return hs ? DIA_ERR_TIMEOUT : DIA_OK;
+}
+
 dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_opts *opts_in,
                    double *theta_out, float *K_out, float *b0_out, float *diff_out,
                    uint8_t *mask_out, dia_fit_info *info, void *workspace,

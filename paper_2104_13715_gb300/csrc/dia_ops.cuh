@@ -245,6 +245,13 @@ cudaError_t launch_fisher_weights(const EvalArgs &ea, float *w, unsigned long lo
 cudaError_t launch_fisher_finish(const double *A64, int n, int np, double *res, cudaStream_t s);
 void precond_window(int H, int W, int m, bool single, int side, int *y0, int *y1, int *x0,
                     int *x1, int *chunks);
+// Tensor-core forward pass (dia_tc.cu): D = I - M over the valid region with the
+// correlation on tcgen05 (split bf16, float32 accumulators in tensor memory);
+// constant background B0 = Kpad[m * kp].  *status is set to 1 if a bounded wait
+// ran out.
+cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int ld, int m,
+                              const float *Kpad, int kp, float *diff_out, int *status,
+                              cudaStream_t s);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,

@@ -93,6 +93,8 @@ _SIGS = {
                                        ctypes.c_void_p]),
     "dia_diff_image": (ctypes.c_int32, [_P(Pair), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "dia_diff_image_tc": (ctypes.c_int32, [_P(Pair), ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "dia_loss_grad_noalloc": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p]),
@@ -326,6 +328,19 @@ def diff_image(R, I, m, theta, ws=None, stream=None, bg_degree=0):
     out = torch.empty((pair.H - 2 * h, pair.W - 2 * h), dtype=torch.float32, device=R.device)
     _check(lib.dia_diff_image(ctypes.byref(pair), _ptr(theta), _ptr(out), _ptr(ws), ws.numel(),
                               _stream(stream)), "dia_diff_image")
+    return out
+
+
+def diff_image_tc(R, I, m, theta, ws=None, stream=None):
+    """dia_diff_image_tc: the difference image with the correlation on the
+    tensor cores (split bf16, float32 accumulation; constant background)."""
+    pair, keep = make_pair(R, I, m)
+    theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
+    ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
+    h = m // 2
+    out = torch.empty((pair.H - 2 * h, pair.W - 2 * h), dtype=torch.float32, device=R.device)
+    _check(lib.dia_diff_image_tc(ctypes.byref(pair), _ptr(theta), _ptr(out), _ptr(ws),
+                                 ws.numel(), _stream(stream)), "dia_diff_image_tc")
     return out
 
 

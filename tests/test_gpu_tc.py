@@ -1,0 +1,71 @@
+"""Tensor-core forward (dia_diff_image_tc: tcgen05.mma on split-bf16 operands,
+float32 accumulators in tensor memory) against the FP64 oracle's difference
+image and the float32 CUDA-core form.
+
+Tolerance: max |D - D*| <= 1e-5 x max |I| (split bf16 keeps about 16 bits of
+each operand; the omitted lo*lo products are below 2^-16 of each term)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests._helpers import field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2104_13715_gb300 import native
+    return native
+
+
+def _t(a, dt=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+@pytest.mark.parametrize("m", [1, 3, 7, 11, 19, 25, 31])
+@pytest.mark.parametrize("shape", [(200, 300), (157, 131)])
+def test_tc_difference_image_matches_the_oracle(nat, m, shape):
+    d = field(shape[0], shape[1], m, seed=7 + m)
+    rng = np.random.default_rng(m)
+    th = np.append(np.abs(rng.normal(1.0 / (m * m), 0.3 / (m * m), m * m)), 97.5)
+    D = nat.diff_image_tc(_t(d["R"]), _t(d["I"]), m, torch.from_numpy(th)).cpu().numpy()
+    Do = oracle.diff_image(d["R"], d["I"], m, th)
+    scale = np.max(np.abs(d["I"]))
+    assert D.shape == Do.shape
+    assert np.max(np.abs(D - Do)) <= 1e-5 * scale, np.max(np.abs(D - Do)) / scale
+    Df = nat.diff_image(_t(d["R"]), _t(d["I"]), m, torch.from_numpy(th)).cpu().numpy()
+    assert np.max(np.abs(D - Df)) <= 1e-5 * scale
+
+
+def test_tc_pitched_rows_and_signed_kernel(nat):
+    """Row pitch > W and a kernel with negative taps (a difference of Gaussians)."""
+    m, H, W, ld = 9, 140, 170, 192
+    d = field(H, W, m, seed=5)
+    Rp = np.zeros((H, ld), np.float32)
+    Ip = np.zeros((H, ld), np.float32)
+    Rp[:, :W] = d["R"]
+    Ip[:, :W] = d["I"]
+    yy, xx = np.mgrid[0:m, 0:m] - m // 2
+    K = np.exp(-(xx ** 2 + yy ** 2) / 2.0) - 0.5 * np.exp(-(xx ** 2 + yy ** 2) / 8.0)
+    th = np.append(K.ravel(), -12.0)
+    R = _t(Rp)[:, :W]
+    I = _t(Ip)[:, :W]
+    D = nat.diff_image_tc(R, I, m, torch.from_numpy(th)).cpu().numpy()
+    Do = oracle.diff_image(d["R"], d["I"], m, th)
+    assert np.max(np.abs(D - Do)) <= 1e-5 * np.max(np.abs(d["I"]))
+
+
+def test_tc_rejects_polynomial_background(nat):
+    import ctypes
+    d = field(64, 64, 3, seed=1)
+    R, I = _t(d["R"]), _t(d["I"])
+    pair, keep = nat.make_pair(R, I, 3, bg_degree=1)
+    th = torch.zeros(9 + 3, dtype=torch.float64, device="cuda")
+    out = torch.empty((62, 62), dtype=torch.float32, device="cuda")
+    ws = nat.workspace(64, 64, 3, device=R.device)
+    st = nat.lib.dia_diff_image_tc(ctypes.byref(pair), ctypes.c_void_p(th.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                   ws.numel(), None)
+    assert st == nat.DIA_ERR_UNSUPPORTED
