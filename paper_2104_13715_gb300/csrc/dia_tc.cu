@@ -51,6 +51,7 @@ constexpr int kTcThreads = kTcProducers + 32;
 constexpr long long kTcWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
 
 struct TcSmem {
+    float f[kTcYT][kTcXT];                        // next tile's R window (cp.async)
     __nv_bfloat16 t[2][2][kTcYC][kTcXT][8];       // [buffer][hi|lo][y / 8][x][y % 8]
     __nv_bfloat16 zk[2][kTcMaxM][kTcKC * 64];     // [hi|lo][b][c][t][e]
     uint64_t tfull[2];    // T buffer staged (128 producer arrivals)
@@ -58,7 +59,8 @@ struct TcSmem {
     uint64_t afull[2];    // accumulators final (tcgen05.commit)
     uint64_t aempty[2];   // accumulators read back (128 producer arrivals)
     uint32_t tslot;
-    int abort;
+    int mma_abort;        // set by the MMA warp when a wait of its own ran out
+    int prod_abort;       // set by a producer (read by the MMA warp's waits)
 };
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
@@ -96,21 +98,56 @@ __device__ __forceinline__ void tc_commit(uint64_t *b) {
                  :: "r"(su32(b)));
 }
 
-// Wait for the phase with parity `ph`; false after kTcWaitCycles or once any
-// thread of the CTA has aborted (then this one aborts too).
-__device__ __forceinline__ bool tc_wait(TcSmem &S, uint64_t *bar, uint32_t ph) {
+// Wait for the phase with parity `ph`; false after kTcWaitCycles or once the
+// other role has aborted (*other != 0).
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t ph, const int *other) {
     const long long t0 = clock64();
-    volatile int *ab = &S.abort;
+    const volatile int *ab = other;
     for (;;) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(su32(bar)), "r"(ph));
         if (done) return true;
-        if (*ab != 0 || clock64() - t0 > kTcWaitCycles) {
-            *ab = 1;
-            return false;
+        if (*ab != 0 || clock64() - t0 > kTcWaitCycles) return false;
+    }
+}
+
+// Barrier 1 over the 128 producer threads with an OR reduction of `fail`: every
+// producer gets the same answer, so they all leave the pipeline together.
+__device__ __forceinline__ bool producers_any(bool fail) {
+    uint32_t any;
+    asm volatile("{\n\t.reg .pred q, p;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(any) : "r"((uint32_t)fail), "n"(kTcProducers) : "memory");
+    return any != 0;
+}
+
+// cp.async of the R window of the tile at (y0, x0) into f (zeros outside the
+// image and past the window rows a kernel tap reaches); 16-byte copies when
+// rows are 16-byte aligned
+__device__ __forceinline__ void tc_prefetch(float (*f)[kTcXT], const float *R, int H, int W,
+                                            int ld, int y0, int x0, int ylim, bool vec) {
+    if (vec) {
+        for (int i = threadIdx.x; i < kTcYT * (kTcXT / 4); i += kTcProducers) {
+            const int yy = i / (kTcXT / 4), c4 = i % (kTcXT / 4);
+            const int gy = y0 + yy, gx = x0 + 4 * c4;
+            int bytes = 0;
+            const float *src = R;
+            if (yy < ylim && gy < H && gx < W) {
+                bytes = (W - gx >= 4) ? 16 : 4 * (W - gx);
+                src = R + (size_t)gy * ld + gx;
+            }
+            cp_async16(&f[yy][4 * c4], src, bytes);
+        }
+    } else {
+        for (int i = threadIdx.x; i < kTcYT * kTcXT; i += kTcProducers) {
+            const int yy = i / kTcXT, x = i % kTcXT;
+            const int gy = y0 + yy, gx = x0 + x;
+            const bool in = yy < ylim && gy < H && gx < W;
+            cp_async4(&f[yy][x], in ? R + (size_t)gy * ld + gx : R, in ? 4 : 0);
         }
     }
+    cp_async_commit();
 }
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
@@ -148,7 +185,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs 
             mbar_init(&S.aempty[i], kTcProducers);
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
-        S.abort = 0;
+        S.mma_abort = 0;
+        S.prod_abort = 0;
     }
     // Zk_b[c][t][e] = K[8c + t + e - (NO - 1)][b] (0 outside the kernel)
     for (int i = tid; i < m * kTcKC * 64; i += kTcThreads) {
@@ -176,8 +214,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs 
             int k = 0;
             for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++k) {
                 const int buf = k & 1;
-                if (!tc_wait(S, &S.tfull[buf], (uint32_t)((k >> 1) & 1))) break;
-                if (k >= 2 && !tc_wait(S, &S.aempty[buf], (uint32_t)(((k - 2) >> 1) & 1))) break;
+                if (!tc_wait(&S.tfull[buf], (uint32_t)((k >> 1) & 1), &S.prod_abort) ||
+                    (k >= 2 &&
+                     !tc_wait(&S.aempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.prod_abort))) {
+                    *reinterpret_cast<volatile int *>(&S.mma_abort) = 1;
+                    atomicExch(a.status, 1);
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t acc = tmem + (uint32_t)(buf * kTcNO);
                 for (int b = 0; b < m; ++b) {
@@ -197,9 +240,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs 
         }
         __syncwarp();
     } else {
+        // returns false if the accumulators did not arrive
         auto epilogue = [&](int kk, int tile) {
             const int buf = kk & 1;
-            bool ok = tc_wait(S, &S.afull[buf], (uint32_t)((kk >> 1) & 1));
+            bool ok = tc_wait(&S.afull[buf], (uint32_t)((kk >> 1) & 1), &S.mma_abort);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -232,45 +276,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs 
             }
             return true;
         };
-        bool ok = true;
-        int k = 0, prev = -1;
+        const bool vec = ((a.ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.R) & 15) == 0);
         const int ylim = kTcNO + m - 1;   // window rows with a nonzero kernel weight
-        for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++k) {
+        auto origin = [&](int tile, int &y0, int &x0) {
+            y0 = (tile / a.tiles_x) * kTcNO;
+            x0 = (tile % a.tiles_x) * kTcW;
+        };
+        int y0, x0;
+        if ((int)blockIdx.x < a.n_tiles) {
+            origin(blockIdx.x, y0, x0);
+            tc_prefetch(S.f, a.R, a.H, a.W, a.ld, y0, x0, ylim, vec);
+        }
+        bool fail = false;
+        int k = 0, prev = -1;
+        for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++k) {
             const int buf = k & 1;
-            const int y0 = (tile / a.tiles_x) * kTcNO, x0 = (tile % a.tiles_x) * kTcW;
-            if (k >= 2 && !tc_wait(S, &S.tempty[buf], (uint32_t)(((k - 2) >> 1) & 1))) {
-                ok = false;
+            // the window has landed (each thread's own copies, then everyone's)
+            cp_async_wait<0>();
+            if (k >= 2 && !fail)
+                fail = !tc_wait(&S.tempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.mma_abort);
+            if (producers_any(fail)) {
+                fail = true;
                 break;
             }
-            // T[buf][.][yc][x][e] = R[y0 + 8 yc + e][x0 + x] (0 outside the image or
-            // past the last window row a kernel tap reaches)
+            // T[buf][.][yc][x][e] = split(f[8 yc + e][x])
 #pragma unroll 2
             for (int u = tid; u < kTcYC * kTcXT; u += kTcProducers) {
                 const int yc = u / kTcXT, x = u % kTcXT;
-                const int gx = x0 + x;
-                float f[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int yy = 8 * yc + e, gy = y0 + yy;
-                    f[e] = (yy < ylim && gy < a.H && gx < a.W) ? __ldg(a.R + (size_t)gy * a.ld + gx) : 0.f;
-                }
                 __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) split_bf16(f[e], hi[e], lo[e]);
+                for (int e = 0; e < 8; ++e) split_bf16(S.f[8 * yc + e][x], hi[e], lo[e]);
                 *reinterpret_cast<uint4 *>(&S.t[buf][0][yc][x][0]) = *reinterpret_cast<const uint4 *>(hi);
                 *reinterpret_cast<uint4 *>(&S.t[buf][1][yc][x][0]) = *reinterpret_cast<const uint4 *>(lo);
             }
             asm volatile("fence.proxy.async.shared::cta;");
             mbar_arrive(&S.tfull[buf]);
-            if (prev >= 0) ok = epilogue(k - 1, prev);
+            // every producer has read f: request the next tile's window
+            if (producers_any(fail)) {
+                fail = true;
+                break;
+            }
+            if (tile + (int)gridDim.x < a.n_tiles) {
+                origin(tile + gridDim.x, y0, x0);
+                tc_prefetch(S.f, a.R, a.H, a.W, a.ld, y0, x0, ylim, vec);
+            }
+            if (prev >= 0 && !epilogue(k - 1, prev)) fail = true;
             prev = tile;
         }
-        if (ok && prev >= 0) ok = epilogue(k - 1, prev);
-        if (!ok && tid == 0) atomicExch(a.status, 1);
+        if (!fail && prev >= 0 && !epilogue(k - 1, prev)) fail = true;
+        cp_async_wait<0>();
+        if (fail) {
+            *reinterpret_cast<volatile int *>(&S.prod_abort) = 1;
+            if (lane == 0) atomicExch(a.status, 1);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (S.abort && tid == 0) atomicExch(a.status, 1);
     if (warp == 4)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64));
 }
