@@ -718,6 +718,45 @@ def run_s10_study(args):
           flush=True)
 
 
+def run_tc_forward(args):
+    """The forward pass alone, two ways: the difference image D = I - M of the
+    workload at the box-car kernel through dia_diff_image (float32 CUDA cores)
+    and dia_diff_image_tc (tcgen05 tensor cores, split bf16), W + K calls each,
+    CUDA events around the K calls (each call includes its small prep kernel;
+    the tensor-core call also reads back its status word)."""
+    import torch
+    from paper_2104_13715_gb300 import native as nat
+    d = synth.workload(args.workload, seed=args.seed, size=args.size)
+    m = d["m"]
+    dev = torch.device("cuda", 0)
+    R = torch.from_numpy(d["R"]).to(dev)
+    I = torch.from_numpy(d["I"]).to(dev)
+    th = torch.full((m * m + 1,), 1.0 / (m * m), dtype=torch.float64)
+    th[-1] = float(np.median(d["I"]))
+    ws = nat.workspace(R.shape[0], R.shape[1], m, device=dev)
+    H, W = R.shape
+    h = m // 2
+    npx = (H - 2 * h) * (W - 2 * h)
+    res = {}
+    outs = {}
+    for name, fn in (("fp32_cuda_cores", nat.diff_image), ("tensor_cores_split_bf16", nat.diff_image_tc)):
+        for _ in range(args.warmup):
+            outs[name] = fn(R, I, m, th, ws=ws)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            outs[name] = fn(R, I, m, th, ws=ws)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        res[name] = {"ms": ms, "tflops_useful": 2.0 * m * m * npx / ms / 1e9}
+    diff = (outs["tensor_cores_split_bf16"] - outs["fp32_cuda_cores"]).abs().max().item()
+    print(json.dumps({"tc_forward": args.workload, "H": H, "W": W, "m": m, "results": res,
+                      "max_abs_diff_rel_maxI": diff / I.abs().max().item(),
+                      "useful": "2 m^2 flop per valid pixel"}), flush=True)
+
+
 def run_kernel_only(args):
     """W + K back-to-back fused evaluations (dia_loss_grad) of the workload at
     the box-car start: the driver of the ncu captures of the fused kernel."""
@@ -777,6 +816,8 @@ def main():
                     help="time the fused loss+gradient kernel alone (ncu driver)")
     ap.add_argument("--size", type=int, default=None, help="image side override (--kernel-only)")
     ap.add_argument("--variant", type=int, default=None, help="tile variant (--kernel-only)")
+    ap.add_argument("--tc-forward", action="store_true",
+                    help="time the forward pass on CUDA cores and on tensor cores")
     ap.add_argument("--s10-study", type=int, default=0,
                     help="run the simulated-image accuracy study with this many simulations")
     ap.add_argument("--precision-study", action="store_true",
@@ -784,6 +825,9 @@ def main():
     args = ap.parse_args()
     if args.s10_study:
         run_s10_study(args)
+        return
+    if args.tc_forward:
+        run_tc_forward(args)
         return
     if args.precision_study:
         run_precision_study(args)
