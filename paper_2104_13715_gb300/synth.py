@@ -259,7 +259,8 @@ def s10_pair(seed: int, size: int = S10_SIZE) -> dict:
     sky_ref = float(np.median(R))
     return dict(R=(R - sky_ref).astype(np.float32), I=I.astype(np.float32), I_noiseless=I_nl,
                 sigma_I=sig_i, phi_r=phi_r, phi_k=phi_k, snr=snr, snr_regime=snr_regime,
-                sampling=samp, m=S10_M, seed=seed)
+                sampling=samp, m=S10_M, seed=seed, sky_r=s_r, sky_i=s_i,
+                R_noiseless=R_nl)
 
 
 def s10_metrics(d: dict, theta, diff) -> dict:
