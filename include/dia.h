@@ -265,14 +265,15 @@ dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff
                           void *workspace, size_t workspace_bytes, void *stream);
 
 /* The same difference image with the correlation on the tensor cores
- * (tcgen05.mma, sm_103a): per output tile of 32 rows x 128 columns and per R
- * row, a 128 x 32 x 32 product of the R row's Hankel matrix with a window of
- * the row-reversed kernel accumulates M - B0 in tensor memory; R and K are
- * split into bf16 high and low parts and the three products hi*hi, hi*lo, lo*hi
- * are summed in float32 (relative error of M about 1e-6 against 1e-7 for the
- * float32 CUDA-core form).  Constant background only (bg_degree 0, else
- * DIA_ERR_UNSUPPORTED).  Synchronous: waits on `stream` and returns
- * DIA_ERR_TIMEOUT if a kernel wait ran out (the kernel bounds its waits). */
+ * (tcgen05.mma, sm_103a): per output tile of 32 rows x 128 columns and per
+ * kernel column b, a 128 x 32 x 64 product of the tile's R window (shifted by
+ * b columns) with a Hankel matrix of kernel column b accumulates M - B0 in
+ * tensor memory; R and K are split into bf16 high and low parts and the three
+ * products hi*hi, hi*lo, lo*hi are summed in float32 (each term of M within
+ * 3 x 2^-16 of its magnitude, against 2^-24 for the float32 CUDA-core form).
+ * Constant background only (bg_degree 0, else DIA_ERR_UNSUPPORTED); m <= 31.
+ * Synchronous: waits on `stream` and returns DIA_ERR_TIMEOUT if a kernel wait
+ * ran out (the kernel bounds every wait). */
 dia_status dia_diff_image_tc(const dia_pair *pair, const double *theta, float *diff_out,
                              void *workspace, size_t workspace_bytes, void *stream);
 
