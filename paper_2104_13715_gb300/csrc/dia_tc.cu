@@ -22,15 +22,21 @@
 // three products hi*hi + hi*lo + lo*hi are accumulated in float32 (the omitted
 // lo*lo term is below 2^-16 of each product).
 //
-// Persistent CTAs (one per SM), warp-specialised: warps 0-3 stage tile k's R
-// window into T[k & 1] (signalled on tfull) and, one tile behind, read the
+// Persistent CTAs (one per SM), warp-specialised: the R window of the next
+// tile arrives by TMA (cp.async.bulk.tensor, 2-D tiled map, zero fill outside
+// the image; cp.async when the rows are not 16-byte aligned); warps 0-3 split
+// tile k's window into T[k & 1] (signalled on tfull) and, one tile behind, read the
 // accumulators of the previous tile from tensor memory and write D = I - M
 // (signalled on aempty); warp 4 owns the tensor memory (two 32-column
 // accumulators) and, on one lane, issues each tile's m x (K steps) x 3 MMAs and
 // commits them to tempty (T buffer free) and afull (accumulators ready).  Every
 // wait is bounded and any failed wait aborts the whole CTA.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 
 #include "../../include/dia.h"
 #include "dia_ops.cuh"
@@ -58,6 +64,7 @@ struct TcSmem {
     uint64_t tempty[2];   // T buffer read by its MMAs (tcgen05.commit)
     uint64_t afull[2];    // accumulators final (tcgen05.commit)
     uint64_t aempty[2];   // accumulators read back (128 producer arrivals)
+    uint64_t wfull;       // the TMA window copy landed (1 arrival + 40960 bytes)
     uint32_t tslot;
     int mma_abort;        // set by the MMA warp when a wait of its own ran out
     int prod_abort;       // set by a producer (read by the MMA warp's waits)
@@ -163,9 +170,25 @@ struct TcArgs {
     int kp;
     float *diff_out;     // (Hv x Wv) D = I - M
     int *status;         // set to 1 if a wait ran out
+    int use_tma;         // 1: the window by TMA through `tmap`
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs a) {
+constexpr uint32_t kTcWindowBytes = kTcYT * kTcXT * 4;
+
+// one elected thread: the window of the tile at (y0, x0) into f by TMA
+__device__ __forceinline__ void tc_tma_window(TcSmem &S, const CUtensorMap *tmap, int y0, int x0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(su32(&S.wfull)), "r"(kTcWindowBytes) : "memory");
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(su32(&S.f[0][0])), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x0), "r"(y0),
+                    "r"(su32(&S.wfull))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_forward_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -184,6 +207,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs 
             mbar_init(&S.afull[i], 1);
             mbar_init(&S.aempty[i], kTcProducers);
         }
+        mbar_init(&S.wfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         S.mma_abort = 0;
         S.prod_abort = 0;
@@ -283,16 +307,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs 
             x0 = (tile % a.tiles_x) * kTcW;
         };
         int y0, x0;
+        int tma_issued = 0;   // TMA windows requested (thread 0), each consumed in order
         if ((int)blockIdx.x < a.n_tiles) {
             origin(blockIdx.x, y0, x0);
-            tc_prefetch(S.f, a.R, a.H, a.W, a.ld, y0, x0, ylim, vec);
+            if (a.use_tma) {
+                if (tid == 0) tc_tma_window(S, &tmap, y0, x0);
+                tma_issued = 1;
+            } else {
+                tc_prefetch(S.f, a.R, a.H, a.W, a.ld, y0, x0, ylim, vec);
+            }
         }
         bool fail = false;
         int k = 0, prev = -1;
         for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++k) {
             const int buf = k & 1;
-            // the window has landed (each thread's own copies, then everyone's)
-            cp_async_wait<0>();
+            // the window has landed (TMA: the transaction count of wfull; cp.async:
+            // each thread's own copies, then everyone's at the barrier)
+            if (a.use_tma)
+                fail = fail || !tc_wait(&S.wfull, (uint32_t)(k & 1), &S.mma_abort);
+            else
+                cp_async_wait<0>();
             if (k >= 2 && !fail)
                 fail = !tc_wait(&S.tempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.mma_abort);
             if (producers_any(fail)) {
@@ -318,13 +352,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs 
             }
             if (tile + (int)gridDim.x < a.n_tiles) {
                 origin(tile + gridDim.x, y0, x0);
-                tc_prefetch(S.f, a.R, a.H, a.W, a.ld, y0, x0, ylim, vec);
+                if (a.use_tma) {
+                    if (tid == 0) tc_tma_window(S, &tmap, y0, x0);
+                    ++tma_issued;
+                } else {
+                    tc_prefetch(S.f, a.R, a.H, a.W, a.ld, y0, x0, ylim, vec);
+                }
             }
             if (prev >= 0 && !epilogue(k - 1, prev)) fail = true;
             prev = tile;
         }
         if (!fail && prev >= 0 && !epilogue(k - 1, prev)) fail = true;
         cp_async_wait<0>();
+        // after a failure, the last window requested must land (or its wait run
+        // out) before the CTA's shared memory is released
+        if (fail && a.use_tma && tid == 0 && tma_issued > 0) {
+            const int never = 0;
+            tc_wait(&S.wfull, (uint32_t)((tma_issued - 1) & 1), &never);
+        }
         if (fail) {
             *reinterpret_cast<volatile int *>(&S.prod_abort) = 1;
             if (lane == 0) atomicExch(a.status, 1);
@@ -340,10 +385,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_forward_kernel(const TcArgs 
 
 int tc_smem_bytes() { return (int)sizeof(TcSmem); }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to
+// the driver library); nullptr if unavailable
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
 cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int ld, int m,
                               const float *Kpad, int kp, float *diff_out, int *status,
                               cudaStream_t s) {
     if (m < 1 || m > kTcMaxM || (m & 1) == 0) return cudaErrorInvalidValue;
+    // 2-D tiled map of R (x innermost): 160 x 64 float boxes, zero fill outside;
+    // needs a 16-byte aligned base and row pitch
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    int use_tma = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (enc && (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(R) % 16) == 0) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)W, (cuuint64_t)H};
+        const cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)kTcXT, (cuuint32_t)kTcYT};
+        const cuuint32_t estride[2] = {1, 1};
+        if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(R), gdim, gstride,
+                box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            use_tma = 1;
+    }
     TcArgs a;
     a.R = R;
     a.I = I;
@@ -359,6 +436,7 @@ cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int 
     a.kp = kp;
     a.diff_out = diff_out;
     a.status = status;
+    a.use_tma = use_tma;
     int dev = 0, sms = 1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -368,7 +446,7 @@ cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int 
     e = cudaFuncSetAttribute(tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int grid = a.n_tiles < sms ? a.n_tiles : sms;
-    tc_forward_kernel<<<grid, kTcThreads, smem, s>>>(a);
+    tc_forward_kernel<<<grid, kTcThreads, smem, s>>>(a, tmap);
     return cudaGetLastError();
 }
 
