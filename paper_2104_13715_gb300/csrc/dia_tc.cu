@@ -27,11 +27,9 @@
 // the image; cp.async when the rows are not 16-byte aligned); warps 0-3 split
 // tile k's window into T[k & 1] (signalled on tfull) and, one tile behind, read the
 // accumulators of the previous tile from tensor memory and write D = I - M
-// (signalled on aempty); warp 4 owns the tensor memory (per tile in flight four
-// 32-column accumulators that consecutive MMAs rotate over, so that the chain of
-// small MMAs does not wait on its own results; the epilogue sums them) and, on
-// one lane, issues each tile's m x (K steps) x 3 MMAs and commits them to tempty
-// (T buffer free) and afull (accumulators ready).  Every
+// (signalled on aempty); warp 4 owns the tensor memory (two 32-column
+// accumulators) and, on one lane, issues each tile's m x (K steps) x 3 MMAs and
+// commits them to tempty (T buffer free) and afull (accumulators ready).  Every
 // wait is bounded and any failed wait aborts the whole CTA.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -54,8 +52,6 @@ constexpr int kTcYT = 64;                  // R window rows (NO + m - 1 <= 64)
 constexpr int kTcYC = kTcYT / 8;           // 8-row chunks of the window
 constexpr int kTcKC = 12;                  // 16-byte chunks of one Zk_b (>= (NO + YT) / 8 + 1)
 constexpr int kTcMaxM = 31;
-constexpr int kTcNAcc = 4;                 // accumulators per tile, MMAs rotate over them
-constexpr int kTcTmemCols = 2 * kTcNAcc * kTcNO;   // two tiles in flight
 constexpr int kTcProducers = 128;          // warps 0-3
 constexpr int kTcThreads = kTcProducers + 32;
 constexpr long long kTcWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
@@ -201,7 +197,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(su32(&S.tslot)), "r"(kTcTmemCols));
+                     :: "r"(su32(&S.tslot)), "r"(64));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -250,23 +246,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                // consecutive MMAs go to different accumulators so that they do not
-                // wait on one another's results; the epilogue sums the kTcNAcc partials
-                const uint32_t acc0 = tmem + (uint32_t)(buf * kTcNAcc * kTcNO);
-                int j = 0;
-                auto mma = [&](uint64_t ad, uint64_t bd) {
-                    tc_mma(acc0 + (uint32_t)((j % kTcNAcc) * kTcNO), ad, bd, idesc, j >= kTcNAcc);
-                    ++j;
-                };
+                const uint32_t acc = tmem + (uint32_t)(buf * kTcNO);
                 for (int b = 0; b < m; ++b) {
                     const uint64_t tb = dt0 + ((buf * kTbuf + b * 16) >> 4);
                     const uint64_t zb = dz0 + ((b * kZb) >> 4);
                     for (int ks = 0; ks < nks; ++ks) {
                         const uint64_t ahi = tb + ((2 * ks * kTcXT * 16) >> 4), alo = ahi + (kTsplit >> 4);
                         const uint64_t bhi = zb + ((2 * ks * 128) >> 4), blo = bhi + (kZsplit >> 4);
-                        mma(ahi, bhi);
-                        mma(ahi, blo);
-                        mma(alo, bhi);
+                        tc_mma(acc, ahi, bhi, idesc, (b > 0 || ks > 0) ? 1 : 0);
+                        tc_mma(acc, ahi, blo, idesc, 1);
+                        tc_mma(acc, alo, bhi, idesc, 1);
                     }
                 }
                 tc_commit(&S.tempty[buf]);
@@ -282,28 +271,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            float sum[kTcNO];
-#pragma unroll
-            for (int i = 0; i < kTcNO; ++i) sum[i] = 0.f;
-#pragma unroll
-            for (int q = 0; q < kTcNAcc; ++q) {
-                uint32_t v[kTcNO];
-                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) +
-                                    (uint32_t)((buf * kTcNAcc + q) * kTcNO);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-                               "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                               "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]),
-                               "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                             : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                for (int i = 0; i < kTcNO; ++i) sum[i] += __uint_as_float(v[i]);
-            }
+            uint32_t v[kTcNO];
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * kTcNO);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                           "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                           "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+                           "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                           "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]),
+                           "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                         : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(&S.aempty[buf]);
             const int y0 = (tile / a.tiles_x) * kTcNO, x0 = (tile % a.tiles_x) * kTcW;
@@ -314,7 +294,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int y = y0 + kTcNO - 1 - ip;
                     if (y < a.Hv) {
                         const float Iv = __ldg(a.I + (size_t)(y + h) * a.ld + (x + h));
-                        a.diff_out[(size_t)y * a.Wv + x] = Iv - (sum[ip] + B0);
+                        a.diff_out[(size_t)y * a.Wv + x] = Iv - (__uint_as_float(v[ip]) + B0);
                     }
                 }
             }
@@ -398,8 +378,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 4)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                     :: "r"(tmem), "r"(kTcTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64));
 }
 
 }  // namespace
