@@ -387,7 +387,7 @@ int tc_smem_bytes() { return (int)sizeof(TcSmem); }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to
 // the driver library); nullptr if unavailable
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     std::call_once(once, [] {
