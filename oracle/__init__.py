@@ -22,6 +22,10 @@ Pieces (each cites the passage it follows):
   (Eq. 20, Eq. 21): lam * N_data * theta^T L^T L theta with L the Laplacian of
   the kernel-pixel graph (4-connectivity); loss_grad, normal_solve, hessian
   and newton take it through ``reg_lambda``.
+* :func:`svk_model`, :func:`svk_loss_grad`, :func:`svk_normal_solve` -- a
+  spatially varying kernel (each kernel pixel a polynomial of degree dk in the
+  coordinates of Eq. 19, the Bramich et al. 2013 form the paper cites in
+  Sec. 1), in numpy for small images.
 * :func:`newton` -- for the losses that are not quadratic in theta: Newton
   steps with the exact Hessian sum_p l''(M_p) phi_p phi_p^T (M is linear in
   theta), Levenberg damping where it is not positive definite, backtracking
@@ -444,3 +448,85 @@ def fit_clipped(R, I, m, spec: LossSpec, mask=None, var=None, flat=None,
         mk = sigma_clip(R, I, m, th, spec, mk, var, flat, kappa)
         th = fit(R, I, m, spec, mk, var, flat, theta0=th)
     return th, mk
+
+
+# ---------------------------------------------------------------------------
+# Spatially varying kernel.  The paper mentions this extension of DIA (Sec. 1,
+# citing Alard 2000 and Bramich et al. 2013) without implementing it; the
+# reading taken here is the Bramich et al. form: every kernel pixel varies over
+# the image as a polynomial of degree dk in the normalised coordinates of
+# Eq. 19,
+#     K_ab(x, y) = sum_{p+q <= dk} K_pq[a][b] eta^p xi^q,
+# evaluated at the output pixel, so that
+#     M = sum_pq eta^p xi^q (R (x) K_pq) + B(x, y)
+# stays linear in theta = [K_00, K_01, ..., K_dk0 (m*m each, the coefficient
+# order of Eq. 18), background coefficients].  dk = 0 is the constant kernel.
+# Plain numpy over the valid region (small images only).
+# ---------------------------------------------------------------------------
+def svk_split(theta, m, dk):
+    """(list of the n_background(dk) kernel coefficient arrays m x m, background
+    coefficients) of a spatially varying kernel theta."""
+    th = np.asarray(theta, dtype=np.float64)
+    nk = n_background(dk)
+    ks = [th[c * m * m:(c + 1) * m * m].reshape(m, m) for c in range(nk)]
+    bg = th[nk * m * m:]
+    degree_of(np.concatenate([np.zeros(m * m), bg]), m)   # validates the background length
+    return ks, bg
+
+
+def svk_model(R, theta, m, dk) -> np.ndarray:
+    """Model image with the spatially varying kernel over the valid region."""
+    R = _d(R)
+    H, W = _shape(R, m)
+    ks, bg = svk_split(theta, m, dk)
+    win = _windows(R, m)                          # (Hv, Wv, m, m): R[y + a][x + b]
+    phi = background_basis((H, W), m, dk)         # (Hv, Wv, nk): eta^p xi^q
+    M = np.zeros(win.shape[:2])
+    for c, K in enumerate(ks):
+        M += phi[..., c] * np.einsum("yxab,ab->yx", win, K)
+    B = background_basis((H, W), m, degree_of(np.concatenate([np.zeros(m * m), bg]), m))
+    return M + B @ bg
+
+
+def svk_loss_grad(R, I, m, theta, dk, spec: LossSpec = None, mask=None, var=None, flat=None):
+    """FP64 loss and gradient for the spatially varying kernel: the per-pixel
+    terms of Eq. 8 / Eq. 13 at M = svk_model, dL/dK_pq[a][b] = sum_p g_p eta^p
+    xi^q R[y + a][x + b], dL/db = sum_p g_p (background basis)."""
+    spec = spec or LossSpec()
+    R = _d(R)
+    H, W = _shape(R, m)
+    M = svk_model(R, theta, m, dk)
+    ell, g, _, _ = pixel_terms(I, M, m, spec, mask, var, flat)
+    win = _windows(R, m)
+    phi = background_basis((H, W), m, dk)
+    ks, bg = svk_split(theta, m, dk)
+    grads = [np.einsum("yx,yxab->ab", g * phi[..., c], win).ravel() for c in range(len(ks))]
+    B = background_basis((H, W), m, degree_of(np.concatenate([np.zeros(m * m), bg]), m))
+    grads.append(np.einsum("yx,yxk->k", g, B))
+    return float(np.sum(ell)), np.concatenate(grads)
+
+
+def svk_normal_solve(R, I, m, dk, deg: int = 0, mask=None, var=None, var_scalar: float = 1.0):
+    """The fixed-variance chi^2 minimum for the spatially varying kernel: the
+    design row of pixel p is [eta^p xi^q R window of p for each (p, q), background
+    basis at p]; A = sum w phi phi^T, b = sum w phi I, solved by Cholesky."""
+    R = _d(R)
+    I = _d(I)
+    H, W = _shape(R, m)
+    Iv = _valid(I, m)
+    w = np.ones_like(Iv) / var_scalar if var is None else 1.0 / _valid(_d(var), m)
+    if mask is not None:
+        w = w * (_valid(np.asarray(mask), m) != 0)
+    win = _windows(R, m).reshape(Iv.shape[0], Iv.shape[1], m * m)
+    phi = background_basis((H, W), m, dk)
+    B = background_basis((H, W), m, deg)
+    cols = [phi[..., c:c + 1] * win for c in range(phi.shape[-1])] + [B]
+    X = np.concatenate(cols, axis=-1).reshape(-1, phi.shape[-1] * m * m + B.shape[-1])
+    wv = w.reshape(-1)
+    A = (X * wv[:, None]).T @ X
+    b = X.T @ (wv * Iv.reshape(-1))
+    try:
+        L = np.linalg.cholesky(A)
+    except np.linalg.LinAlgError as e:
+        raise Degenerate(str(e))
+    return np.linalg.solve(L.T, np.linalg.solve(L, b))

@@ -556,3 +556,95 @@ def test_normal_solve_recovers_an_injected_polynomial_background(deg):
     th0 = oracle.normal_solve(R, I, m)
     assert np.max(np.abs(oracle.diff_image(R, I, m, th0))) > 1e-3
     assert np.max(np.abs(oracle.diff_image(R, I, m, th))) < 1e-8
+
+
+# ------------------------------------------- spatially varying kernel (Sec. 1)
+def _svk_direct(R, Ks, bg, m, dk, deg):
+    """M by the definition, pixel by pixel: K_ab(x, y) = sum_c K_c[a][b] eta^p xi^q,
+    then the correlation of that kernel with R, plus the background."""
+    H, W = R.shape
+    h = m // 2
+    out = np.zeros((H - 2 * h, W - 2 * h))
+    for y in range(H - 2 * h):
+        for x in range(W - 2 * h):
+            eta, xi = (x + h - (W - 1) / 2) / W, (y + h - (H - 1) / 2) / H
+            Kxy = np.zeros((m, m))
+            c = 0
+            for p in range(dk + 1):
+                for q in range(dk - p + 1):
+                    Kxy += Ks[c] * eta ** p * xi ** q
+                    c += 1
+            B = 0.0
+            c = 0
+            for p in range(deg + 1):
+                for q in range(deg - p + 1):
+                    B += bg[c] * eta ** p * xi ** q
+                    c += 1
+            out[y, x] = np.sum(Kxy * R[y:y + m, x:x + m]) + B
+    return out
+
+
+@pytest.mark.parametrize("dk,deg", [(0, 0), (1, 0), (2, 1)])
+def test_svk_model_is_the_pixel_by_pixel_definition(dk, deg):
+    rng = np.random.default_rng(30 + dk)
+    H, W, m = 17, 19, 5
+    R = rng.normal(size=(H, W))
+    nk, nb = oracle.n_background(dk), oracle.n_background(deg)
+    th = rng.normal(size=nk * m * m + nb)
+    Ks = [th[c * m * m:(c + 1) * m * m].reshape(m, m) for c in range(nk)]
+    ref = _svk_direct(R, Ks, th[nk * m * m:], m, dk, deg)
+    np.testing.assert_allclose(oracle.svk_model(R, th, m, dk), ref, rtol=0, atol=1e-12)
+
+
+def test_svk_degree_zero_is_the_constant_kernel():
+    m, deg = 5, 1
+    d = _field(40, 44, m, seed=31)
+    spec = oracle.LossSpec(rho="huber", noise="ccd", sigma0=4.0, gain=1.3, var_floor=1e-6)
+    th = np.concatenate([d["theta"][:-1], [30.0, 2.0, -3.0]])
+    np.testing.assert_allclose(oracle.svk_model(d["R"], th, m, 0), oracle.model(d["R"], th, m),
+                               rtol=0, atol=1e-10)
+    L1, g1 = oracle.svk_loss_grad(d["R"], d["I"], m, th, 0, spec)
+    L0, g0 = oracle.loss_grad(d["R"], d["I"], m, th, spec)
+    assert L1 == pytest.approx(L0, rel=1e-12)
+    np.testing.assert_allclose(g1, g0, rtol=1e-9, atol=1e-9 * np.max(np.abs(g0)))
+    np.testing.assert_allclose(oracle.svk_normal_solve(d["R"], d["I"], m, 0, deg=deg),
+                               oracle.normal_solve(d["R"], d["I"], m, deg=deg), rtol=1e-8, atol=1e-10)
+
+
+def test_svk_gradient_central_differences():
+    m, dk = 5, 1
+    d = _field(36, 40, m, seed=32)
+    spec = oracle.LossSpec(rho="gauss", noise="ccd", sigma0=4.0, gain=1.3, var_floor=1e-6)
+    rng = np.random.default_rng(32)
+    K0 = d["theta"][:-1]
+    th = np.concatenate([K0, 0.02 * rng.normal(size=m * m), 0.02 * rng.normal(size=m * m), [30.0]])
+    L0, g = oracle.svk_loss_grad(d["R"], d["I"], m, th, dk, spec)
+    for k in (3, m * m + 7, 2 * m * m + 12, 3 * m * m):
+        e = np.zeros_like(th)
+        e[k] = 1e-5 * max(1.0, abs(th[k]))   # the difference error falls as the step squared
+        Lp, _ = oracle.svk_loss_grad(d["R"], d["I"], m, th + e, dk, spec)
+        Lm, _ = oracle.svk_loss_grad(d["R"], d["I"], m, th - e, dk, spec)
+        assert (Lp - Lm) / (2 * e[k]) == pytest.approx(g[k], rel=1e-6, abs=1e-6 * np.max(np.abs(g)))
+
+
+def test_svk_normal_solve_recovers_an_injected_varying_kernel():
+    """Noiseless target made pixel by pixel from a kernel whose width and centre
+    drift linearly across the field (dk = 1) plus a tilted background: the dk = 1
+    solve returns every coefficient; the constant-kernel solve cannot fit it."""
+    rng = np.random.default_rng(33)
+    H, W, m, dk, deg = 44, 48, 5, 1, 1
+    R = _star_ref((H, W), 25, 1.3, rng) + 40.0
+    yy, xx = np.mgrid[0:m, 0:m] - m // 2
+    G = np.exp(-(xx ** 2 + yy ** 2) / 2.0)
+    K00 = G / G.sum()
+    K01 = 0.3 * (np.roll(K00, 1, axis=0) - K00)     # drift along y
+    K10 = 0.2 * (K00 * (xx ** 2 - 1.0))             # width change along x
+    bg = np.array([20.0, 3.0, -5.0])
+    I = np.zeros((H, W))
+    h = m // 2
+    I[h:H - h, h:W - h] = _svk_direct(R, [K00, K01, K10], bg, m, dk, deg)
+    th = oracle.svk_normal_solve(R, I, m, dk, deg=deg)
+    truth = np.concatenate([K00.ravel(), K01.ravel(), K10.ravel(), bg])
+    np.testing.assert_allclose(th, truth, rtol=0, atol=1e-8)
+    th0 = oracle.svk_normal_solve(R, I, m, 0, deg=deg)
+    assert np.max(np.abs(oracle.svk_model(R, th0, m, 0) - _valid(I, m))) > 1e-3
