@@ -406,12 +406,14 @@ cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int 
                               cudaStream_t s) {
     if (m < 1 || m > kTcMaxM || (m & 1) == 0) return cudaErrorInvalidValue;
     // 2-D tiled map of R (x innermost): 160 x 64 float boxes, zero fill outside;
-    // needs a 16-byte aligned base and row pitch
+    // needs a 16-byte aligned base and row pitch; images smaller than one box
+    // take the cp.async path
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof(tmap));
     int use_tma = 0;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (enc && (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(R) % 16) == 0) {
+    if (enc && (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(R) % 16) == 0 && W >= kTcXT &&
+        H >= kTcYT) {
         const cuuint64_t gdim[2] = {(cuuint64_t)W, (cuuint64_t)H};
         const cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
         const cuuint32_t box[2] = {(cuuint32_t)kTcXT, (cuuint32_t)kTcYT};

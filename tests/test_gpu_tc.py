@@ -35,7 +35,7 @@ def _bound(d, m, th):
 
 
 @pytest.mark.parametrize("m", [1, 3, 7, 11, 19, 25, 31])
-@pytest.mark.parametrize("shape", [(200, 300), (157, 131)])
+@pytest.mark.parametrize("shape", [(200, 300), (157, 131), (48, 64)])
 def test_tc_difference_image_matches_the_oracle(nat, m, shape):
     d = field(shape[0], shape[1], m, seed=7 + m)
     rng = np.random.default_rng(m)
