@@ -24,7 +24,8 @@
 //
 // Persistent CTAs (one per SM), warp-specialised: the R window of the next
 // tile arrives by TMA (cp.async.bulk.tensor, 2-D tiled map, zero fill outside
-// the image; cp.async when the rows are not 16-byte aligned); warps 0-3 split
+// the image; cp.async when the rows are not 16-byte aligned or the image is
+// smaller than one 160 x 64 box); warps 0-3 split
 // tile k's window into T[k & 1] (signalled on tfull) and, one tile behind, read the
 // accumulators of the previous tile from tensor memory and write D = I - M
 // (signalled on aempty); warp 4 owns the tensor memory (two 32-column
