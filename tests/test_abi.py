@@ -91,3 +91,24 @@ def test_arguments_rejected_before_any_launch(native):
     o = native.default_opts(history=0)
     assert native.lib.dia_fit(ctypes.byref(p), ctypes.byref(spec), ctypes.byref(o), None, None,
                               None, None, None, None, None, 0, None) == native.DIA_ERR_ARG
+
+
+def test_model_extension_defaults_and_batch_validation(native):
+    """The regulariser is off and the background constant by default (the
+    paper's fits, Sec. 3.3, use neither); the batch planner sizes each pair's
+    theta as m*m + (d+1)(d+2)/2 and rejects a degree outside [0, 4] before
+    anything runs (host-only calls)."""
+    o = native.default_opts()
+    assert o.reg_lambda == 0.0
+    pair = native.Pair(1, 2, None, None, None, 64, 64, 64, 5, 0)
+    assert pair.bg_degree == 0
+    pairs = (native.Pair * 2)(native.Pair(1, 2, None, None, None, 64, 64, 64, 5, 0, 0),
+                              native.Pair(1, 2, None, None, None, 80, 72, 72, 7, 0, 2))
+    n_ok = native.lib.dia_batch_workspace_size(pairs, 2, ctypes.byref(o))
+    assert n_ok > 0
+    pairs[1].bg_degree = 4
+    assert native.lib.dia_batch_workspace_size(pairs, 2, ctypes.byref(o)) >= n_ok
+    pairs[1].bg_degree = 5
+    assert native.lib.dia_batch_workspace_size(pairs, 2, ctypes.byref(o)) == 0
+    pairs[1].bg_degree = -1
+    assert native.lib.dia_batch_workspace_size(pairs, 2, ctypes.byref(o)) == 0
