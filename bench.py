@@ -791,9 +791,13 @@ def run_kernel_only(args):
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     h = m // 2
     npx = int(d["mask"][h:H - h, h:W - h].sum()) if d.get("mask") is not None else (H - 2 * h) * (W - 2 * h)
+    # bytes every evaluation must read: R and I, and the mask / variance map if
+    # given (4 + 4 + 1 + 4 per pixel of the image)
+    nbytes = H * W * (8 + (1 if d.get("mask") is not None else 0) + (4 if d.get("var") is not None else 0))
     print(json.dumps({"kernel_only": args.workload, "H": H, "W": W, "m": m,
                       "variant": nat.kernel_variant_desc(m), "ms_per_eval": ms,
-                      "tflops_algorithmic": 4.0 * m * m * npx / ms / 1e9}), flush=True)
+                      "tflops_algorithmic": 4.0 * m * m * npx / ms / 1e9,
+                      "gbs_algorithmic": nbytes / ms / 1e6, "bytes_algorithmic": nbytes}), flush=True)
 
 
 def main():

@@ -163,6 +163,16 @@ WORKLOADS = {
         mask_frac=0.02, cosmic_frac=0.001,
         loss=dict(rho="cauchy", noise="fixed", var_map="target", sigma0=5.0, gain=1.0,
                   clip_passes=3, kappa=5.0)),
+    # 4096^2 field with small kernels (3x3, 5x5), fixed-variance chi^2: the
+    # memory-bound end of the fused kernel (a few flop per byte)
+    "ccd4096_m3_chi2": PairSpec(
+        size=(4096, 4096), n_stars=60000, m=3, fwhm_ref=2.0, kernel_sigma=0.5,
+        scale=1.0, b0=20.0, sky=100.0, read=5.0, gain=1.0,
+        loss=dict(rho="gauss", noise="fixed", var=1.0)),
+    "ccd4096_m5_chi2": PairSpec(
+        size=(4096, 4096), n_stars=60000, m=5, fwhm_ref=2.0, kernel_sigma=0.8,
+        scale=1.0, b0=20.0, sky=100.0, read=5.0, gain=1.0,
+        loss=dict(rho="gauss", noise="fixed", var=1.0)),
     # 2048^2 high-dynamic-range field, 21x21 kernel, CCD NLL
     "hdr2048_m21_nll": PairSpec(
         size=(2048, 2048), n_stars=15000, m=21, fwhm_ref=2.0,
