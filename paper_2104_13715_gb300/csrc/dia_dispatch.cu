@@ -7,8 +7,17 @@
 namespace dia {
 
 bool kernel_info_1_0(KernelInfo *o);
+bool kernel_info_1_1(KernelInfo *o);
+bool kernel_info_1_2(KernelInfo *o);
+bool kernel_info_1_3(KernelInfo *o);
 bool kernel_info_3_0(KernelInfo *o);
+bool kernel_info_3_1(KernelInfo *o);
+bool kernel_info_3_2(KernelInfo *o);
+bool kernel_info_3_3(KernelInfo *o);
 bool kernel_info_5_0(KernelInfo *o);
+bool kernel_info_5_1(KernelInfo *o);
+bool kernel_info_5_2(KernelInfo *o);
+bool kernel_info_5_3(KernelInfo *o);
 bool kernel_info_7_0(KernelInfo *o);
 bool kernel_info_7_1(KernelInfo *o);
 bool kernel_info_7_2(KernelInfo *o);
@@ -61,9 +70,9 @@ std::atomic<int> g_selected[kMaxKernelSide + 1];
 
 int kernel_variants(int mk) {
     switch (mk) {
-        case 1: return 1;
-        case 3: return 1;
-        case 5: return 1;
+        case 1: return 4;
+        case 3: return 4;
+        case 5: return 4;
         case 7: return 3;
         case 9: return 3;
         case 11: return 4;
@@ -84,11 +93,11 @@ int kernel_variants(int mk) {
 bool kernel_info_variant(int mk, int v, KernelInfo *o) {
     switch (mk) {
         case 1:
-            switch (v) { case 0: return kernel_info_1_0(o); default: return false; }
+            switch (v) { case 0: return kernel_info_1_0(o); case 1: return kernel_info_1_1(o); case 2: return kernel_info_1_2(o); case 3: return kernel_info_1_3(o); default: return false; }
         case 3:
-            switch (v) { case 0: return kernel_info_3_0(o); default: return false; }
+            switch (v) { case 0: return kernel_info_3_0(o); case 1: return kernel_info_3_1(o); case 2: return kernel_info_3_2(o); case 3: return kernel_info_3_3(o); default: return false; }
         case 5:
-            switch (v) { case 0: return kernel_info_5_0(o); default: return false; }
+            switch (v) { case 0: return kernel_info_5_0(o); case 1: return kernel_info_5_1(o); case 2: return kernel_info_5_2(o); case 3: return kernel_info_5_3(o); default: return false; }
         case 7:
             switch (v) { case 0: return kernel_info_7_0(o); case 1: return kernel_info_7_1(o); case 2: return kernel_info_7_2(o); default: return false; }
         case 9:
