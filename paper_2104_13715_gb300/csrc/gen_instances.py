@@ -11,9 +11,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # FMAs pairing output rows in the forward; 0 if omitted).
 # Variant 0 is the default; the autotuner may pick another at run time.
 VARIANTS = {
-    1: [(8, 8, 0, 0), (8, 2, 0, 0), (8, 4, 0, 0), (4, 4, 0, 0)],
-    3: [(8, 8, 0, 0), (8, 2, 0, 0), (8, 4, 0, 0), (4, 4, 0, 0)],
-    5: [(8, 8, 0, 0), (8, 2, 0, 0), (8, 4, 0, 0), (4, 4, 0, 0)],
+    1: [(8, 4, 0, 0), (8, 2, 0, 0), (8, 8, 0, 0), (4, 4, 0, 0)],
+    3: [(8, 4, 0, 0), (8, 2, 0, 0), (8, 8, 0, 0), (4, 4, 0, 0)],
+    5: [(8, 2, 0, 0), (8, 4, 0, 0), (8, 8, 0, 0), (4, 4, 0, 0)],
     7: [(8, 4, 0, 0), (8, 8, 0, 0), (8, 4, 0, 0, 1)],
     9: [(8, 4, 0, 1), (8, 8, 0, 1), (8, 4, 0, 1, 1)],
     11: [(8, 4, 0, 1, 1), (8, 4, 1, 1), (8, 4, 0, 1), (12, 4, 0, 0)],
