@@ -475,7 +475,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
         finish(a, 3 /* DIA_ERR_NONFINITE */, kStopNonfinite);
         return;
     }
-    if (first_eval) {   // the scale against which progress is judged (finish())
+    if (first_eval) {   // the scale against which progress is measured (finish())
         double mx = 0.0;
         for (int k = tid; k < n; k += kStepThreads) mx = fmax(mx, fabs(sm.gt[k]));
         const double g0 = block_max(mx, sm.red);
