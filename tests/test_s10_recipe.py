@@ -85,3 +85,24 @@ def test_metrics_definitions():
     assert met["MFB"] == pytest.approx(eps.mean(), abs=1e-6)
     assert met["MFV"] == pytest.approx(eps.var(ddof=1), rel=1e-6)
     assert met["MSE_noisy"] == pytest.approx(np.mean(D * D), rel=1e-9)
+
+
+def test_regime_populations_follow_the_paper_counts():
+    """The paper prints how its 71,569 simulations fall into the 3 SNR x 4
+    sampling bins (Sec. 3.3 table).  The recipe's draws fall into the bins in
+    the same proportions: each bin's share within 4 binomial standard errors
+    (1,500 draws)."""
+    import json
+    import os
+    table = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "s10_table.json")))
+    counts = {(int(r), s): n for r, row in table["N_sim"].items() for s, n in enumerate(row)}
+    total = sum(counts.values())
+    draws = [synth.s10_pair(seed) for seed in range(1500)]
+    inside = [(d["snr_regime"], d["sampling"]) for d in draws if d["snr_regime"] > 0]
+    n = len(inside)
+    assert n > 900
+    for key, c in counts.items():
+        p = c / total
+        got = sum(1 for k in inside if k == key) / n
+        se = math.sqrt(p * (1 - p) / n)
+        assert abs(got - p) <= 4 * se + 1e-3, (key, got, p)
