@@ -22,7 +22,8 @@ Pieces (each cites the passage it follows):
   (Eq. 20, Eq. 21): lam * N_data * theta^T L^T L theta with L the Laplacian of
   the kernel-pixel graph (4-connectivity); loss_grad, normal_solve, hessian
   and newton take it through ``reg_lambda``.
-* :func:`svk_model`, :func:`svk_loss_grad`, :func:`svk_normal_solve` -- a
+* :func:`svk_model`, :func:`svk_loss_grad`, :func:`svk_normal_solve`,
+  :func:`svk_hessian`, :func:`svk_newton` -- a
   spatially varying kernel (each kernel pixel a polynomial of degree dk in the
   coordinates of Eq. 19, the Bramich et al. 2013 form the paper cites in
   Sec. 1), in numpy for small images.
@@ -530,3 +531,58 @@ def svk_normal_solve(R, I, m, dk, deg: int = 0, mask=None, var=None, var_scalar:
     except np.linalg.LinAlgError as e:
         raise Degenerate(str(e))
     return np.linalg.solve(L.T, np.linalg.solve(L, b))
+
+
+def svk_hessian(R, I, m, theta, dk, spec: LossSpec, mask=None, var=None, flat=None):
+    """Exact Hessian of the spatially varying kernel's loss: sum_p l''(M_p)
+    phi_p phi_p^T with phi_p the design row of svk_normal_solve (M is linear in
+    theta)."""
+    R = _d(R)
+    H, W = _shape(R, m)
+    M = svk_model(R, theta, m, dk)
+    _, _, d2, _ = pixel_terms(I, M, m, spec, mask, var, flat)
+    ks, bg = svk_split(theta, m, dk)
+    deg = degree_of(np.concatenate([np.zeros(m * m), bg]), m)
+    win = _windows(R, m).reshape(M.shape[0], M.shape[1], m * m)
+    phi = background_basis((H, W), m, dk)
+    B = background_basis((H, W), m, deg)
+    cols = [phi[..., c:c + 1] * win for c in range(phi.shape[-1])] + [B]
+    X = np.concatenate(cols, axis=-1).reshape(-1, phi.shape[-1] * m * m + B.shape[-1])
+    return (X * d2.reshape(-1)[:, None]).T @ X
+
+
+def svk_newton(R, I, m, theta0, dk, spec: LossSpec, mask=None, var=None, flat=None,
+               max_iter: int = 50, rtol: float = 1e-13):
+    """Damped Newton on the spatially varying kernel's FP64 loss (the steps of
+    :func:`newton`: Levenberg damping where the Hessian is not positive
+    definite, Armijo backtracking)."""
+    th = _d(theta0).copy()
+    L, g = svk_loss_grad(R, I, m, th, dk, spec, mask, var, flat)
+    for _ in range(max_iter):
+        Hm = svk_hessian(R, I, m, th, dk, spec, mask, var, flat)
+        dH = np.diag(Hm).copy()
+        if np.all(dH == 0):
+            raise Degenerate("zero Hessian")
+        lam = 0.0
+        while True:
+            try:
+                Lc = np.linalg.cholesky(Hm + lam * np.diag(np.abs(dH) + 1e-300))
+                break
+            except np.linalg.LinAlgError:
+                lam = 1e-6 if lam == 0.0 else lam * 10.0
+                if lam > 1e12:
+                    raise Degenerate("Hessian not positive definite")
+        d = -np.linalg.solve(Lc.T, np.linalg.solve(Lc, g))
+        t, slope = 1.0, float(g @ d)
+        while True:
+            Lt, gt = svk_loss_grad(R, I, m, th + t * d, dk, spec, mask, var, flat)
+            if Lt <= L + 1e-4 * t * slope or t < 1e-12:
+                break
+            t *= 0.5
+        step = t * d
+        th = th + step
+        dec = L - Lt
+        L, g = Lt, gt
+        if np.max(np.abs(step)) <= rtol * (1.0 + np.max(np.abs(th))) or dec <= 0.0:
+            break
+    return th

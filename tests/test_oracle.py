@@ -648,3 +648,30 @@ def test_svk_normal_solve_recovers_an_injected_varying_kernel():
     np.testing.assert_allclose(th, truth, rtol=0, atol=1e-8)
     th0 = oracle.svk_normal_solve(R, I, m, 0, deg=deg)
     assert np.max(np.abs(oracle.svk_model(R, th0, m, 0) - _valid(I, m))) > 1e-3
+
+
+def test_svk_hessian_and_newton():
+    """The spatially varying kernel's Hessian is the central difference of its
+    gradient; Newton lands on the normal solve for chi^2 and on a stationary
+    point of the CCD likelihood."""
+    m, dk = 5, 1
+    d = _field(36, 40, m, seed=34)
+    spec = oracle.LossSpec(rho="gauss", noise="ccd", sigma0=4.0, gain=1.3, var_floor=1e-6)
+    rng = np.random.default_rng(34)
+    th = np.concatenate([d["theta"][:-1], 0.02 * rng.normal(size=2 * m * m), [30.0]])
+    Hm = oracle.svk_hessian(d["R"], d["I"], m, th, dk, spec)
+    for k in (2, m * m + 4, 2 * m * m + 9, 3 * m * m):
+        e = np.zeros_like(th)
+        e[k] = 1e-5 * max(1.0, abs(th[k]))
+        _, gp = oracle.svk_loss_grad(d["R"], d["I"], m, th + e, dk, spec)
+        _, gm = oracle.svk_loss_grad(d["R"], d["I"], m, th - e, dk, spec)
+        np.testing.assert_allclose((gp - gm) / (2 * e[k]), Hm[:, k], rtol=1e-5,
+                                   atol=1e-6 * np.max(np.abs(Hm)))
+    chi2 = oracle.LossSpec()
+    ref = oracle.svk_normal_solve(d["R"], d["I"], m, dk)
+    got = oracle.svk_newton(d["R"], d["I"], m, th, dk, chi2)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-8 * np.max(np.abs(ref)))
+    tn = oracle.svk_newton(d["R"], d["I"], m, ref, dk, spec)
+    _, g = oracle.svk_loss_grad(d["R"], d["I"], m, tn, dk, spec)
+    _, g0 = oracle.svk_loss_grad(d["R"], d["I"], m, th, dk, spec)
+    assert np.max(np.abs(g)) <= 1e-9 * np.max(np.abs(g0))
