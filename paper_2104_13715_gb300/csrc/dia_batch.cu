@@ -21,6 +21,7 @@
 
 #include "../../include/dia.h"
 #include "dia_batch.cuh"
+#include "dia_checks.h"
 #include "dia_ops.cuh"
 
 namespace dia {
@@ -66,12 +67,9 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
     size_t per = 0;
     for (int i = 0; i < npairs; ++i) {
         const dia_pair &p = pairs[i];
-        if (!p.ref || !p.img || p.mem != DIA_MEM_DEVICE) return DIA_ERR_ARG;
-        if (p.H <= 0 || p.W <= 0 || p.ld < p.W || p.m < 1 || (p.m & 1) == 0 || p.m > p.H ||
-            p.m > p.W)
-            return DIA_ERR_ARG;
-        if (p.m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
-        if (p.bg_degree < 0 || p.bg_degree > DIA_MAX_BG_DEGREE) return DIA_ERR_ARG;
+        if (p.mem != DIA_MEM_DEVICE) return DIA_ERR_ARG;
+        const dia_status rc = check_pair(&p);
+        if (rc != DIA_OK) return rc;
         PairPlan &q = P.pp[i];
         q.m = p.m;
         q.n = p.m * p.m + n_background(p.bg_degree);
@@ -209,7 +207,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         opts = *opts_in;
     else
         dia_opts_default(&opts);
-    if (!loss || npairs <= 0) return DIA_ERR_ARG;
+    if (!loss || !pairs || npairs <= 0) return DIA_ERR_ARG;
     if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
         opts.graph_iters > 1024 || opts.max_adam_iters < 0 || opts.max_evals < 1 ||
         opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 ||
@@ -218,16 +216,10 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         (opts.init == 1 && !(opts.init_sigma > 0.0)) || !(opts.timeout_s > 0.0))
         return DIA_ERR_ARG;
     if (opts.clip_passes != 0) return DIA_ERR_UNSUPPORTED;
-    if (loss->rho < 0 || loss->rho > 2 || loss->var_model < 0 || loss->var_model > 2)
-        return DIA_ERR_ARG;
-    if (loss->var_model != DIA_VAR_FIXED &&
-        (!(loss->gain > 0.f) || !(loss->var_floor > 0.f) ||
-         (loss->var_model == DIA_VAR_EMCCD && !(loss->excess > 0.f))))
-        return DIA_ERR_ARG;
-    if (loss->rho == DIA_RHO_HUBER && !(loss->huber_c > 0.f)) return DIA_ERR_ARG;
-    for (int i = 0; i < npairs; ++i)
-        if (loss->var_model == DIA_VAR_FIXED && !pairs[i].var && !(loss->var_scalar > 0.f))
-            return DIA_ERR_ARG;
+    for (int i = 0; i < npairs; ++i) {
+        const dia_status lrc = check_loss(loss, &pairs[i]);
+        if (lrc != DIA_OK) return lrc;
+    }
     BatchPlan P;
     dia_status rc = plan_batch(pairs, npairs, opts.history, opts.precond, opts.precond_window, P);
     if (rc != DIA_OK) return rc;
@@ -255,15 +247,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     std::vector<BatchRed> reds(npairs);
     std::vector<long long> thoff(npairs);
     std::vector<PrecondArgs> pas(opts.precond ? npairs : 0);
-    LossParams lp;
-    lp.rho = loss->rho;
-    lp.var_model = loss->var_model;
-    lp.s0sq = loss->sigma0 * loss->sigma0;
-    lp.inv_gain = (loss->gain > 0.f) ? 1.0f / loss->gain : 1.0f;
-    lp.excess = loss->excess;
-    lp.huber_c = loss->huber_c;
-    lp.var_scalar = loss->var_scalar;
-    lp.var_floor = loss->var_floor;
+    const LossParams lp = to_params(loss);
     const int H = opts.history;
     int max_n = 1, bg = 0;   // bg: some pair has a polynomial background
     for (int i = 0; i < npairs; ++i) {

@@ -19,6 +19,7 @@
 #include <utility>
 
 #include "../../include/dia.h"
+#include "dia_checks.h"
 #include "dia_dispatch.h"
 #include "dia_eval.cuh"
 #include "dia_ops.cuh"
@@ -86,19 +87,11 @@ extern "C" dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss
     if (!pair || !loss || !theta || !loss_out || !grad_out || !pair->ref || !pair->img)
         return DIA_ERR_ARG;
     if (pair->mem != DIA_MEM_DEVICE) return DIA_ERR_ARG;
+    dia_status rc = check_pair(pair);
+    if (rc != DIA_OK) return rc;
+    rc = check_loss(loss, pair);
+    if (rc != DIA_OK) return rc;
     const int H = pair->H, W = pair->W, ld = pair->ld, m = pair->m;
-    if (H <= 0 || W <= 0 || ld < W || m < 1 || (m & 1) == 0 || m > H || m > W) return DIA_ERR_ARG;
-    if (m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
-    if (pair->bg_degree < 0 || pair->bg_degree > DIA_MAX_BG_DEGREE) return DIA_ERR_ARG;
-    if (loss->rho < 0 || loss->rho > 2 || loss->var_model < 0 || loss->var_model > 2)
-        return DIA_ERR_ARG;
-    if (loss->var_model == DIA_VAR_FIXED) {
-        if (!pair->var && !(loss->var_scalar > 0.f)) return DIA_ERR_ARG;
-    } else if (!(loss->gain > 0.f) || !(loss->var_floor > 0.f) ||
-               (loss->var_model == DIA_VAR_EMCCD && !(loss->excess > 0.f))) {
-        return DIA_ERR_ARG;
-    }
-    if (loss->rho == DIA_RHO_HUBER && !(loss->huber_c > 0.f)) return DIA_ERR_ARG;
 
     KernelInfo ki;
     if (!kernel_info(m, &ki)) return DIA_ERR_UNSUPPORTED;
@@ -151,14 +144,7 @@ extern "C" dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss
     a.Kpad = kpad;
     a.partials = partials;
     a.clip_kappa = 5.0f;
-    a.lp.rho = loss->rho;
-    a.lp.var_model = loss->var_model;
-    a.lp.s0sq = loss->sigma0 * loss->sigma0;
-    a.lp.inv_gain = (loss->gain > 0.f) ? 1.0f / loss->gain : 1.0f;
-    a.lp.excess = loss->excess;
-    a.lp.huber_c = loss->huber_c;
-    a.lp.var_scalar = loss->var_scalar;
-    a.lp.var_floor = loss->var_floor;
+    a.lp = to_params(loss);
     set_background(a, pair->bg_degree, H, W, h);
     const int nb = n_background(pair->bg_degree);
 

@@ -112,3 +112,23 @@ def test_model_extension_defaults_and_batch_validation(native):
     assert native.lib.dia_batch_workspace_size(pairs, 2, ctypes.byref(o)) == 0
     pairs[1].bg_degree = -1
     assert native.lib.dia_batch_workspace_size(pairs, 2, ctypes.byref(o)) == 0
+
+
+def test_batch_entry_validates_before_launching(native):
+    """dia_fit_batch: no pairs, a bad loss for one pair, or clipping requested
+    give status codes without any device work (host-only)."""
+    spec = native.loss_spec()
+    o = native.default_opts()
+    assert native.lib.dia_fit_batch(None, 2, ctypes.byref(spec), ctypes.byref(o), None, None,
+                                    None, None, 0, None) == native.DIA_ERR_ARG
+    pairs = (native.Pair * 2)(native.Pair(1, 2, None, None, None, 64, 64, 64, 5, 0),
+                              native.Pair(1, 2, None, None, None, 64, 64, 64, 5, 0))
+    bad = native.loss_spec(noise="ccd", gain=0.0)
+    assert native.lib.dia_fit_batch(pairs, 2, ctypes.byref(bad), ctypes.byref(o), None, None,
+                                    None, None, 0, None) == native.DIA_ERR_ARG
+    clip = native.default_opts(clip_passes=1)
+    assert native.lib.dia_fit_batch(pairs, 2, ctypes.byref(spec), ctypes.byref(clip), None, None,
+                                    None, None, 0, None) == native.DIA_ERR_UNSUPPORTED
+    big = (native.Pair * 1)(native.Pair(1, 2, None, None, None, 64, 64, 64, 33, 0))
+    assert native.lib.dia_fit_batch(big, 1, ctypes.byref(spec), ctypes.byref(o), None, None,
+                                    None, None, 0, None) == native.DIA_ERR_UNSUPPORTED
