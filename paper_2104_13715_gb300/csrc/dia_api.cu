@@ -519,13 +519,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         opts = *opts_in;
     else
         fill_opts_default(&opts);
-    if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
-        opts.graph_iters > 1024 || opts.clip_passes < 0 || opts.max_adam_iters < 0 ||
-        opts.max_evals < 1 || opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 || opts.precond_window < 0 ||
-        !(opts.reg_lambda >= 0.0) || !std::isfinite(opts.reg_lambda) || opts.init < 0 || opts.init > 2 ||
-        (opts.init == 2 && !opts.theta0) || (opts.init == 1 && !(opts.init_sigma > 0.0)) ||
-        !(opts.timeout_s > 0.0))
-        return DIA_ERR_ARG;
+    if (check_opts(opts, 2) != DIA_OK) return DIA_ERR_ARG;
     if (!pair || !loss) return DIA_ERR_ARG;
     const int clip = opts.clip_passes > 0 || mask_out != nullptr;
     cudaStream_t s = (cudaStream_t)stream;

@@ -208,13 +208,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     else
         dia_opts_default(&opts);
     if (!loss || !pairs || npairs <= 0) return DIA_ERR_ARG;
-    if (opts.history < 1 || opts.history > kHistMax || opts.graph_iters < 1 ||
-        opts.graph_iters > 1024 || opts.max_adam_iters < 0 || opts.max_evals < 1 ||
-        opts.max_lbfgs_iters < 1 || opts.stall_iters < 1 || opts.stall_iters_diag < 1 || opts.max_ls_evals < 2 ||
-        !(opts.reg_lambda >= 0.0) || !std::isfinite(opts.reg_lambda) ||
-        opts.precond_window < 0 || opts.init < 0 || opts.init > 1 ||
-        (opts.init == 1 && !(opts.init_sigma > 0.0)) || !(opts.timeout_s > 0.0))
-        return DIA_ERR_ARG;
+    if (check_opts(opts, 1) != DIA_OK) return DIA_ERR_ARG;   // no theta0 for a batch
     if (opts.clip_passes != 0) return DIA_ERR_UNSUPPORTED;
     for (int i = 0; i < npairs; ++i) {
         const dia_status lrc = check_loss(loss, &pairs[i]);

@@ -1,5 +1,8 @@
 // Argument checks and loss-parameter conversion shared by every entry point.
+#include <cmath>
+
 #include "dia_checks.h"
+#include "dia_ops.cuh"
 
 namespace dia {
 
@@ -30,6 +33,17 @@ dia_status check_loss(const dia_loss_spec *l, const dia_pair *p) {
     }
     if (l->rho == DIA_RHO_HUBER && !(l->huber_c > 0.f)) return DIA_ERR_ARG;
     return DIA_OK;
+}
+
+dia_status check_opts(const dia_opts &o, int max_init) {
+    const bool ok = o.history >= 1 && o.history <= kHistMax && o.graph_iters >= 1 &&
+                    o.graph_iters <= 1024 && o.clip_passes >= 0 && o.max_adam_iters >= 0 &&
+                    o.max_evals >= 1 && o.max_lbfgs_iters >= 1 && o.stall_iters >= 1 &&
+                    o.stall_iters_diag >= 1 && o.max_ls_evals >= 2 && o.precond_window >= 0 &&
+                    o.reg_lambda >= 0.0 && std::isfinite(o.reg_lambda) && o.init >= 0 &&
+                    o.init <= max_init && !(o.init == 2 && !o.theta0) &&
+                    !(o.init == 1 && !(o.init_sigma > 0.0)) && o.timeout_s > 0.0;
+    return ok ? DIA_OK : DIA_ERR_ARG;
 }
 
 LossParams to_params(const dia_loss_spec *l) {

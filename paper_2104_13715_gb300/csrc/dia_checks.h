@@ -16,6 +16,9 @@ dia_status check_pair(const dia_pair *p);
 // a loss of a known kind with the parameters its variance model needs (p: the
 // pair it applies to, for the fixed-variance map)
 dia_status check_loss(const dia_loss_spec *l, const dia_pair *p);
+// optimiser settings within their documented ranges (include/dia.h); init
+// modes up to max_init (2 = theta0, which must then be given)
+dia_status check_opts(const dia_opts &o, int max_init);
 // the float32 parameters the fused kernel reads
 LossParams to_params(const dia_loss_spec *l);
 
