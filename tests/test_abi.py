@@ -132,3 +132,22 @@ def test_batch_entry_validates_before_launching(native):
     big = (native.Pair * 1)(native.Pair(1, 2, None, None, None, 64, 64, 64, 33, 0))
     assert native.lib.dia_fit_batch(big, 1, ctypes.byref(spec), ctypes.byref(o), None, None,
                                     None, None, 0, None) == native.DIA_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("field,value", [("history", 0), ("history", 129), ("graph_iters", 0),
+                                         ("max_ls_evals", 1), ("timeout_s", 0.0),
+                                         ("reg_lambda", -1.0), ("reg_lambda", float("nan")),
+                                         ("init", 3), ("init", 2), ("clip_passes", -1),
+                                         ("precond_window", -5)])
+def test_out_of_range_options_are_rejected_on_the_host(native, field, value):
+    """Every entry validates dia_opts before any launch (init 2 without theta0
+    included); the batch entry takes no theta0, so init 2 is refused there too."""
+    spec = native.loss_spec()
+    p = native.Pair(1, 2, None, None, None, 64, 64, 64, 5, 0)
+    o = native.default_opts()
+    setattr(o, field, value)
+    assert native.lib.dia_fit(ctypes.byref(p), ctypes.byref(spec), ctypes.byref(o), None, None,
+                              None, None, None, None, None, 0, None) == native.DIA_ERR_ARG
+    pairs = (native.Pair * 1)(p)
+    assert native.lib.dia_fit_batch(pairs, 1, ctypes.byref(spec), ctypes.byref(o), None, None,
+                                    None, None, 0, None) == native.DIA_ERR_ARG
