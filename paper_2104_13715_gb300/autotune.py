@@ -15,8 +15,13 @@ import torch
 
 from . import native as nat
 
-CACHE = os.environ.get("DIA_TUNING_CACHE",
-                       os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning.json"))
+def _default_cache():
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "dia_gb300", "tuning.json")
+
+
+# the cache lives outside the package (a user cache directory, or DIA_TUNING_CACHE)
+CACHE = os.environ.get("DIA_TUNING_CACHE") or _default_cache()
 _lock = threading.Lock()
 
 
@@ -28,29 +33,33 @@ def _key(m, H, W, dev):
     return f"{torch.cuda.get_device_name(dev)}|m={m}|{H}x{W}|{sig}"
 
 
-def _load():
+def _load(path):
     try:
-        with open(CACHE) as f:
+        with open(path) as f:
             return json.load(f)
     except (OSError, ValueError):
         return {}
 
 
-def _save(d):
-    tmp = CACHE + f".{os.getpid()}.tmp"
+def _save(d, path):
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
     with open(tmp, "w") as f:
         json.dump(d, f, indent=1, sort_keys=True)
-    os.replace(tmp, CACHE)
+    os.replace(tmp, path)
 
 
-def tune(R, I, m, spec, mask=None, var=None, flat=None, reps=5, use_cache=True, stream=None):
-    """Select (and return) the fastest tile variant for this pair's shape."""
+def tune(R, I, m, spec, mask=None, var=None, flat=None, reps=5, use_cache=True, stream=None,
+         cache_path=None):
+    """Select (and return) the fastest tile variant for this pair's shape.
+    ``cache_path``: the JSON cache file (default: CACHE)."""
+    path = cache_path or CACHE
     H, W = R.shape
     dev = R.device
     key = _key(m, H, W, dev)
     nvar = nat.kernel_variants(m)
     with _lock:
-        cache = _load() if use_cache else {}
+        cache = _load(path) if use_cache else {}
         if key in cache and cache[key]["variant"] < nvar:
             nat.select_kernel_variant(m, cache[key]["variant"])
             return cache[key]
@@ -77,7 +86,7 @@ def tune(R, I, m, spec, mask=None, var=None, flat=None, reps=5, use_cache=True, 
     nat.select_kernel_variant(m, best)
     rec = {"variant": best, "times_ms": times, "desc": nat.kernel_variant_desc(m, best)}
     with _lock:
-        cache = _load()
+        cache = _load(path)
         cache[key] = rec
-        _save(cache)
+        _save(cache, path)
     return rec

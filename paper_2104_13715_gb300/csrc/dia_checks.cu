@@ -35,7 +35,22 @@ dia_status check_loss(const dia_loss_spec *l, const dia_pair *p) {
     return DIA_OK;
 }
 
+namespace {
+bool pos_finite(double v) { return std::isfinite(v) && v > 0.0; }
+bool nonneg_finite(double v) { return std::isfinite(v) && v >= 0.0; }
+}  // namespace
+
 dia_status check_opts(const dia_opts &o, int max_init) {
+    // Adam (Sec. 2.3): decays in [0, 1) (beta = 1 divides by zero in the bias
+    // correction), positive finite rates and epsilon; finite non-negative
+    // stopping tolerances; a positive finite clip threshold when clipping
+    // (NaN would clip nothing, 0 every pixel)
+    const bool adam_ok = o.beta1 >= 0.0 && o.beta1 < 1.0 && o.beta2 >= 0.0 && o.beta2 < 1.0 &&
+                         pos_finite(o.lr_kernel) && pos_finite(o.lr_b0) && pos_finite(o.adam_eps);
+    const bool tol_ok = nonneg_finite(o.switch_tol) && nonneg_finite(o.rel_tol) &&
+                        nonneg_finite(o.grad_tol);
+    const bool clip_ok = o.clip_passes == 0 || (std::isfinite(o.clip_kappa) && o.clip_kappa > 0.f);
+    if (!adam_ok || !tol_ok || !clip_ok) return DIA_ERR_ARG;
     const bool ok = o.history >= 1 && o.history <= kHistMax && o.graph_iters >= 1 &&
                     o.graph_iters <= 1024 && o.clip_passes >= 0 && o.max_adam_iters >= 0 &&
                     o.max_evals >= 1 && o.max_lbfgs_iters >= 1 && o.stall_iters >= 1 &&

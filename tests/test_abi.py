@@ -138,7 +138,12 @@ def test_batch_entry_validates_before_launching(native):
                                          ("max_ls_evals", 1), ("timeout_s", 0.0),
                                          ("reg_lambda", -1.0), ("reg_lambda", float("nan")),
                                          ("init", 3), ("init", 2), ("clip_passes", -1),
-                                         ("precond_window", -5)])
+                                         ("precond_window", -5), ("beta1", 1.0),
+                                         ("beta1", -0.1), ("beta2", 1.0),
+                                         ("lr_kernel", 0.0), ("lr_b0", -1.0),
+                                         ("lr_kernel", float("inf")), ("adam_eps", 0.0),
+                                         ("grad_tol", float("nan")), ("switch_tol", -1.0),
+                                         ("rel_tol", float("inf"))])
 def test_out_of_range_options_are_rejected_on_the_host(native, field, value):
     """Every entry validates dia_opts before any launch (init 2 without theta0
     included); the batch entry takes no theta0, so init 2 is refused there too."""
@@ -151,3 +156,15 @@ def test_out_of_range_options_are_rejected_on_the_host(native, field, value):
     pairs = (native.Pair * 1)(p)
     assert native.lib.dia_fit_batch(pairs, 1, ctypes.byref(spec), ctypes.byref(o), None, None,
                                     None, None, 0, None) == native.DIA_ERR_ARG
+
+
+@pytest.mark.parametrize("kappa", [0.0, -1.0, float("nan"), float("inf")])
+def test_clip_threshold_is_checked_when_clipping(native, kappa):
+    """A clip threshold that is not positive and finite is refused when the fit
+    clips (NaN would clip nothing, 0 every pixel); without clipping it is unused."""
+    spec = native.loss_spec()
+    p = native.Pair(1, 2, None, None, None, 64, 64, 64, 5, 0)
+    o = native.default_opts(clip_passes=2)
+    o.clip_kappa = kappa
+    assert native.lib.dia_fit(ctypes.byref(p), ctypes.byref(spec), ctypes.byref(o), None, None,
+                              None, None, None, None, None, 0, None) == native.DIA_ERR_ARG
