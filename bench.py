@@ -133,24 +133,20 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_record():
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "fused_eval_m25_4096.md")
-    if not os.path.exists(path):
-        return None
-    sha = kernel_source_sha()
-    rec = {}
-    for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            rec[k.strip()] = v.strip()
-    if rec.get("kernel_source_sha256_16") != sha:
-        return None
+def _traffic_record(name="fused_eval_m25_4096"):
+    """DRAM bytes per launch of the fused kernel from the committed ncu record
+    (profiles/<name>.json, written from the same capture as the summary
+    beside it), if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", name + ".json")
     try:
-        return float(rec["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
+    if rec.get("kernel_source_sha256_16") != kernel_source_sha():
+        return None
+    v = rec.get("dram_bytes_per_launch")
+    return float(v) if isinstance(v, (int, float)) else None
 
 
 def _loss_kw(d):
@@ -177,54 +173,92 @@ def _crop(d, side):
     return out
 
 
-def oracle_rate(d, budget_s=15.0, crop=1024, max_evals=50):
-    """FP64 oracle loss+gradient evaluations per second on a crop of the pair,
-    scaled to the full valid pixel count.  Returns (rate, cores, sample)."""
+def cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def _theta_boxcar(d):
+    m = d["m"]
+    th = np.full(m * m + 1, 1.0 / (m * m))
+    th[-1] = float(np.median(d["I"]))
+    return th
+
+
+def oracle_evals(d, n, nthreads=0):
+    """Run n FP64 oracle loss+gradient evaluations of the whole pair at the
+    box-car start; returns the seconds taken."""
     import oracle
     m = d["m"]
-    c = _crop(d, min(crop, d["R"].shape[0]))
     spec = _oracle_spec(d)
-    th = np.full(m * m + 1, 1.0 / (m * m))
-    th[-1] = float(np.median(c["I"]))
-    cores = os.cpu_count() or 1
-    n = 0
+    th = _theta_boxcar(d)
     t0 = time.perf_counter()
-    while True:
-        oracle.loss_grad(c["R"], c["I"], m, th, spec, mask=c.get("mask"), var=c.get("var"),
-                         nthreads=cores)
+    for _ in range(n):
+        oracle.loss_grad(d["R"], d["I"], m, th, spec, mask=d.get("mask"), var=d.get("var"),
+                         nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(d, budget_s=15.0, max_evals=50):
+    """FP64 oracle loss+gradient evaluations per second on the whole pair
+    (all host cores), as many as fit in budget_s (at least one), plus a
+    single-thread figure from one evaluation of a 1024^2 crop scaled by valid
+    pixel count.  Returns (rate, cores, sample, extra)."""
+    cores = os.cpu_count() or 1
+    n, dt = 0, 0.0
+    while n < max_evals and (n == 0 or dt < budget_s):
+        dt += oracle_evals(d, 1, nthreads=cores)
         n += 1
-        if time.perf_counter() - t0 >= budget_s or n >= max_evals:
-            break
-    dt = time.perf_counter() - t0
-    h = m // 2
-    px_s = (c["R"].shape[0] - 2 * h) * (c["R"].shape[1] - 2 * h)
+    h = d["m"] // 2
     px_f = (d["R"].shape[0] - 2 * h) * (d["R"].shape[1] - 2 * h)
-    rate = n / dt * px_s / px_f
-    sample = (f"{n} FP64 loss+gradient evaluations of the oracle on a {c['R'].shape[0]}x"
-              f"{c['R'].shape[1]} crop ({px_s} valid px) in {dt:.1f} s, scaled by valid pixel "
-              f"count to {d['R'].shape[0]}x{d['R'].shape[1]} ({px_f} px)")
-    return rate, cores, sample
+    c = _crop(d, min(1024, d["R"].shape[0]))
+    px_c = (c["R"].shape[0] - 2 * h) * (c["R"].shape[1] - 2 * h)
+    t1 = oracle_evals(c, 1, nthreads=1)
+    extra = {"cpu_model": cpu_model(),
+             "single_thread_evals_per_s": px_c / px_f / t1,
+             "single_thread_sample": f"one evaluation of a {c['R'].shape[0]}x{c['R'].shape[1]} "
+                                     f"crop ({px_c} valid px) on one thread in {t1:.2f} s, "
+                                     f"scaled by valid pixel count"}
+    sample = (f"{n} FP64 loss+gradient evaluations of the oracle on the whole "
+              f"{d['R'].shape[0]}x{d['R'].shape[1]} pair ({px_f} valid px) at the box-car "
+              f"start in {dt:.1f} s on {cores} threads")
+    return n / dt, cores, sample, extra
 
 
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank, world):
+    """The FP64 oracle as it stands, on the same pair: one whole-pair
+    loss+gradient evaluation per step on all host cores."""
     if rank != 0:
         return
     d = synth.workload(args.workload, seed=args.seed)
-    rates = []
-    for i in range(args.warmup + args.steps):
-        r, cores, sample = oracle_rate(d, budget_s=args.ref_budget, max_evals=1)
-        if i >= args.warmup:
-            rates.append(r)
-    value = float(np.mean(rates))
+    cores = os.cpu_count() or 1
+    oracle_evals(d, args.warmup, nthreads=cores)
+    dt = oracle_evals(d, args.steps, nthreads=cores)
+    value = args.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(args, d),
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                         "sample": sample + " (one evaluation per step)"},
+                         "sample": f"one FP64 loss+gradient evaluation of the whole "
+                                   f"{d['R'].shape[0]}x{d['R'].shape[1]} pair per step, "
+                                   f"{cores} threads", "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -244,6 +278,96 @@ def _config(args, d):
             "optimizer": "Adam -> L-BFGS (Gauss-Newton preconditioned, library defaults)"}
 
 
+def oracle_check(nat, d, R, I, m, spec, opts, mask, var, ws, stream, out_plain, th_init):
+    """K, B0 and difference-image errors of the fit against the FP64 oracle's
+    optimum theta*: theta* = theta_gpu + one Newton step with the oracle's
+    exact FP64 Hessian, on the mask the fit itself returned (its clip
+    decisions, taken in float32, are the fit's; the oracle optimises on that
+    mask).  Also the oracle's max|dL/dtheta| at theta_gpu and at theta*,
+    relative to the box-car start."""
+    import oracle
+    out = nat.fit(R, I, m, spec, opts, mask=mask, var=var, ws=ws, stream=stream,
+                  want_diff=True, want_mask=opts.clip_passes > 0)
+    th = out["theta"].cpu().numpy()
+    fmask = out["mask"].cpu().numpy() if opts.clip_passes > 0 else d.get("mask")
+    spec_o = _oracle_spec(d)
+    kw = dict(mask=fmask, var=d.get("var"))
+    t0 = time.perf_counter()
+    ref = oracle.newton(d["R"], d["I"], m, th, spec_o, max_iter=1, **kw)
+    t_newton = time.perf_counter() - t0
+    _, g_fit = oracle.loss_grad(d["R"], d["I"], m, th, spec_o, **kw)
+    _, g_ref = oracle.loss_grad(d["R"], d["I"], m, ref, spec_o, **kw)
+    _, g_ini = oracle.loss_grad(d["R"], d["I"], m, th_init, spec_o, **kw)
+    D_ref = oracle.diff_image(d["R"], d["I"], m, ref)
+    D = out["diff"].cpu().numpy()
+    h = m // 2
+    sky = float(np.median(d["I"]))
+    vv = d.get("var")
+    sig_med = float(np.sqrt(np.median(vv[h:-h, h:-h]))) if vv is not None else float(
+        np.sqrt(_loss_kw(d).get("var", 1.0)))
+    sumK = abs(ref[:-1].sum())
+    th_pl = out_plain["theta"].cpu().numpy()
+    gi = np.max(np.abs(g_ini))
+    return {"err_K": float(np.max(np.abs(th[:-1] - ref[:-1])) / sumK),
+            "err_B0": float(abs(th[-1] - ref[-1]) / sky),
+            "err_D": float(np.max(np.abs(D - D_ref)) / sig_med),
+            "err_D_rel_maxI": float(np.max(np.abs(D - D_ref)) / np.max(np.abs(d["I"]))),
+            "plain_K_err_rel_sumK": float(np.max(np.abs(th_pl[:-1] - ref[:-1])) / sumK),
+            "oracle_grad_ratio": float(np.max(np.abs(g_fit)) / gi),
+            "oracle_grad_ratio_polished": float(np.max(np.abs(g_ref)) / gi),
+            "P": float(th[:-1].sum()), "B0": float(th[-1]),
+            "tolerances": {"err_K": 1e-4, "err_B0": 1e-4},
+            "what": "err_K = max|K - K*| / |sum K*|, err_B0 = |B0 - B0*| / median(I), "
+                    "err_D = max|D - D*| / sigma_median, theta* = theta_gpu + one FP64 "
+                    f"Newton step of the oracle on the fit's final mask ({t_newton:.0f} s on "
+                    f"{os.cpu_count()} host cores)"}
+
+
+def batch_subset(nat, dev, stream, n, seed):
+    """The first n pairs of the batch workload fitted three ways: batched
+    (one dia_fit_batch call, graph-captured), one at a time in the plain form
+    (no graph) and one at a time with the graph; fits/s of each and the max
+    K error (relative to sum K*) against the oracle's normal-equation solve."""
+    import oracle
+    import torch
+    ds = synth.batch(n, seed=seed)
+    items = [dict(R=torch.from_numpy(x["R"]).to(dev), I=torch.from_numpy(x["I"]).to(dev),
+                  m=x["m"]) for x in ds]
+    spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
+    refs = [oracle.normal_solve(x["R"], x["I"], x["m"]) for x in ds]
+
+    def kerr(thetas):
+        return float(max(np.max(np.abs(t[:-1] - r[:-1])) / abs(r[:-1].sum())
+                         for t, r in zip(thetas, refs)))
+
+    res = {"pairs": n}
+    opts = nat.default_opts(timeout_s=900.0)
+    nat.fit_batch(items, spec, opts, stream=stream)   # warm-up (graph capture)
+    for mode in ("batch", "single_plain", "single_graph"):
+        o = nat.default_opts(use_graph=0 if mode == "single_plain" else 1, timeout_s=900.0)
+        if mode != "batch":
+            nat.fit(items[0]["R"], items[0]["I"], items[0]["m"], spec, o, want_diff=False,
+                    stream=stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        if mode == "batch":
+            thetas = [t.cpu().numpy() for t in nat.fit_batch(items, spec, opts,
+                                                             stream=stream)["thetas"]]
+        else:
+            thetas = [nat.fit(it["R"], it["I"], it["m"], spec, o, want_diff=False,
+                              stream=stream)["theta"] for it in items]
+            torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if mode != "batch":
+            thetas = [t.cpu().numpy() for t in thetas]
+        res[mode] = {"fits_per_s": n / dt, "K_err_rel_sumK": kerr(thetas)}
+    res["batch_over_single_plain"] = res["batch"]["fits_per_s"] / res["single_plain"]["fits_per_s"]
+    res["what"] = ("first pairs of the batch recipe (side 64-512, m 7-21, chi^2): batched vs "
+                   "one at a time plain (no graph) and with the graph; host wall clock "
+                   "around each; K error against the oracle's normal-equation solve")
+    return res
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2104_13715_gb300 import native as nat
@@ -261,8 +385,9 @@ def run_ours(args, rank, world, local_rank):
     # CPU baseline first (rank 0, N=1 only), before the GPU is busy
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, cores, sample = oracle_rate(d, budget_s=args.ref_budget)
-        cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample}
+        r, cores, sample, extra = oracle_rate(d, budget_s=args.ref_budget)
+        cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
+               **extra}
 
     def up(a, dt):
         return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
@@ -405,23 +530,39 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": ev2 / (ms2 / 1000.0), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "fits_per_s": n2 * world / (ms2 / 1000.0)}
 
-    # error vs the FP64 oracle at the fitted theta: relative stationarity
+    # the plain form: the same fit with every optimiser iteration launched one
+    # by one (no CUDA graph), one pair at a time
+    o_plain = nat.default_opts(clip_passes=opts.clip_passes, clip_kappa=opts.clip_kappa,
+                               use_graph=0)
+    nat.fit(R, I, m, spec, o_plain, mask=mask, var=var, ws=ws, stream=stream, want_diff=True)
+    torch.cuda.synchronize(dev)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_pl, ev_pl = max(1, min(args.steps, 3)), 0
+    p0.record(stream)
+    for _ in range(n_pl):
+        out_pl = nat.fit(R, I, m, spec, o_plain, mask=mask, var=var, ws=ws, stream=stream,
+                         want_diff=True)
+        ev_pl += out_pl["info"]["evals"]
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_pl = p0.elapsed_time(p1)
+    plain = {"value": ev_pl / (ms_pl / 1e3), "unit": "evals/s",
+             "fits_per_s": n_pl / (ms_pl / 1e3), "evals_per_fit": ev_pl / n_pl,
+             "what": "the same fit, optimiser iterations launched one by one (use_graph = 0)"}
+
+    # error vs the FP64 oracle: one Newton step (exact FP64 Hessian) from the
+    # fitted theta on the fit's own final mask gives the oracle's optimum
+    # theta* to second order; K, B0 and D are compared with it (outside the
+    # timed region)
     err = None
     if rank == 0 and not args.no_oracle_check:
-        import oracle
-        th = out["theta"].cpu().numpy() if hasattr(out["theta"], "cpu") else np.asarray(out["theta"])
-        mk = out["mask"]
-        spec_o = _oracle_spec(d)
-        fmask = d.get("mask")
-        if opts.clip_passes > 0:
-            fmask = nat.fit(R, I, m, spec, opts, mask=mask, var=var, ws=ws, stream=stream,
-                            want_diff=False, want_mask=True)["mask"].cpu().numpy()
-        th_init = th0.cpu().numpy()
-        _, g_fit = oracle.loss_grad(d["R"], d["I"], m, th, spec_o, mask=fmask, var=d.get("var"))
-        _, g_ini = oracle.loss_grad(d["R"], d["I"], m, th_init, spec_o, mask=fmask, var=d.get("var"))
-        err = {"oracle_grad_ratio": float(np.max(np.abs(g_fit)) / np.max(np.abs(g_ini))),
-               "P": float(th[:-1].sum()), "B0": float(th[-1]),
-               "what": "max|dL/dtheta| of the FP64 oracle at the fitted theta / at the box-car start"}
+        err = oracle_check(nat, d, R, I, m, spec, opts, mask, var, ws, stream, out_pl,
+                           th0.cpu().numpy())
+        plain["K_err_rel_sumK"] = err.pop("plain_K_err_rel_sumK", None)
+
+    batch_sub = None
+    if rank == 0 and world == 1 and args.subset > 0 and not args.no_batch_subset:
+        batch_sub = batch_subset(nat, dev, stream, args.subset, args.seed)
 
     if rank == 0:
         last = infos[-1] if infos else {}
@@ -430,9 +571,10 @@ def run_ours(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**_config(args, d), "tile": nat.kernel_variant_desc(m),
-                       "tile_variant": tuned.get("variant")},
+            "config": _config(args, d),
+            "kernel_tile": {**nat.kernel_variant_desc(m), "variant": tuned.get("variant")},
             "fits_per_s": fits_per_s,
+            "vs_plain": value / plain["value"], "plain": plain, "batch_subset": batch_sub,
             "evals_per_fit": evals_all / (args.steps * world),
             "adam_off": adam_off,
             "fit_info": {k: last.get(k) for k in ("status", "adam_iters", "lbfgs_iters", "evals",
@@ -816,6 +958,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-batch-subset", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the fused loss+gradient kernel alone (ncu driver)")
     ap.add_argument("--size", type=int, default=None, help="image side override (--kernel-only)")

@@ -97,6 +97,8 @@ def _load():
         lib.oracle_loss_grad.restype = i
         lib.oracle_ndata.argtypes = [up, i, i, i, i]
         lib.oracle_ndata.restype = ctypes.c_longlong
+        lib.oracle_design_rows.argtypes = [dp, i, i, i, i, i, i, i, dp, i, dp, dp, i]
+        lib.oracle_design_rows.restype = i
         _lib = lib
         return lib
 
@@ -285,31 +287,39 @@ def _windows(R, m):
     return np.lib.stride_tricks.sliding_window_view(R, (m, m))
 
 
-def gram(R, m, weights, rhs=None, block_rows: int = 64, deg: int = 0):
+def gram(R, m, weights, rhs=None, block_rows: int = 0, deg: int = 0):
     """A = sum_p w_p phi_p phi_p^T and (optionally) b = sum_p rhs_p phi_p, where
     phi_p = [R window of valid pixel p (m*m, row-major), background basis at p
     (Eq. 18; [1] for degree 0)].  ``weights`` and ``rhs`` are arrays over the
     valid region.  This is the B08 normal matrix when w = 1/sigma^2 and
-    rhs = I/sigma^2 (Sec. 1)."""
+    rhs = I/sigma^2 (Sec. 1).  The rows phi_p and w_p phi_p of a block of image
+    rows are laid out by ``oracle_design_rows`` (C, threaded copy) and the
+    block's sum is one matrix product; blocks (about 2^25 doubles each unless
+    ``block_rows`` is given) are added in row order."""
     R = _d(R)
     H, W = _shape(R, m)
     h = m // 2
     Hv, Wv = H - 2 * h, W - 2 * h
     n = n_params(m, deg)
-    nk = m * m
-    basis = background_basis((H, W), m, deg)
-    win = _windows(R, m)
+    w_all = np.ascontiguousarray(weights, dtype=np.float64)
+    assert w_all.shape == (Hv, Wv)
+    if block_rows <= 0:
+        block_rows = max(1, (1 << 25) // (Wv * n))
+    lib = _load()
     A = np.zeros((n, n))
     b = np.zeros(n) if rhs is not None else None
+    phi = np.empty((min(block_rows, Hv) * Wv, n))
+    phiw = np.empty_like(phi)
     for y0 in range(0, Hv, block_rows):
         y1 = min(Hv, y0 + block_rows)
-        phi = np.empty(((y1 - y0) * Wv, n))
-        phi[:, :nk] = win[y0:y1].reshape(-1, m * m)
-        phi[:, nk:] = basis[y0:y1].reshape(-1, n - nk)
-        w = np.asarray(weights[y0:y1], dtype=np.float64).reshape(-1)
-        A += (phi * w[:, None]).T @ phi
+        k = (y1 - y0) * Wv
+        rc = lib.oracle_design_rows(_ptr(R), H, W, W, m, deg, y0, y1, _ptr(w_all), Wv,
+                                    _ptr(phi), _ptr(phiw), 0)
+        if rc:
+            raise ValueError("oracle_design_rows: bad arguments")
+        A += phiw[:k].T @ phi[:k]
         if rhs is not None:
-            b += phi.T @ np.asarray(rhs[y0:y1], dtype=np.float64).reshape(-1)
+            b += phi[:k].T @ np.asarray(rhs[y0:y1], dtype=np.float64).reshape(-1)
     return (A, b) if rhs is not None else A
 
 

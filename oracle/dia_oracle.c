@@ -298,3 +298,37 @@ long long oracle_ndata(const uint8_t *mask, int H, int W, int ld, int m)
             n += mask ? (mask[(size_t)i * ld + j] != 0) : 1;
     return n;
 }
+
+/* Design rows of the linear model for the valid-region rows [y0, y1): for
+ * each valid pixel p, phi_p = [R window of p (m*m, row-major), background
+ * basis at p] (Eq. 2, Eq. 18), written row after row into phi (n columns,
+ * n = m*m + (d+1)(d+2)/2); if w is given (valid-region map of pitch ldw),
+ * also w_p phi_p into phiw.  The Python side forms the normal matrix or the
+ * Hessian sum_p w_p phi_p phi_p^T from these blocks with one matrix product;
+ * this routine only lays the rows out (a parallel copy, no sums). */
+int oracle_design_rows(const double *R, int H, int W, int ld, int m, int deg, int y0, int y1,
+                       const double *w, int ldw, double *phi, double *phiw, int nthreads)
+{
+    if (check_args(H, W, ld, m) || deg < 0 || deg > 9) return -1;
+    int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h;
+    if (y0 < 0 || y1 > Hv || y0 > y1) return -1;
+    int nb = n_background(deg), n = m * m + nb;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = y0; y < y1; ++y) {
+        for (int x = 0; x < Wv; ++x) {
+            double *row = phi + ((size_t)(y - y0) * Wv + x) * n;
+            for (int a = 0; a < m; ++a) {
+                const double *rr = R + (size_t)(y + a) * ld + x;
+                for (int b = 0; b < m; ++b) row[a * m + b] = rr[b];
+            }
+            background_basis(deg, H, W, y + h, x + h, row + m * m);
+            if (w && phiw) {
+                double wp = w[(size_t)y * ldw + x];
+                double *rw = phiw + ((size_t)(y - y0) * Wv + x) * n;
+                for (int k = 0; k < n; ++k) rw[k] = wp * row[k];
+            }
+        }
+    }
+    return 0;
+}
