@@ -446,20 +446,16 @@ def run_ours(args, rank, world, local_rank):
     value = evals_all / (ms_max / 1000.0)
     fits_per_s = args.steps * world / (ms_max / 1000.0)
 
-    # roofline of the fused evaluation kernel: dia_loss_grad alone, events on the stream
+    # roofline of the fused evaluation kernel: its launches alone, each bracketed
+    # by CUDA events on the stream, L2 overwritten before each (dia_time_eval)
     th0 = torch.full((m * m + 1,), 1.0 / (m * m), dtype=torch.float64, device=dev)
     th0[-1] = float(np.median(d["I"]))
-    for _ in range(3):
-        nat.loss_grad(R, I, m, th0, spec, mask=mask, var=var, ws=ws, stream=stream)
-    torch.cuda.synchronize(dev)
-    k_ev = args.kernel_evals
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(k_ev):
-        nat.loss_grad(R, I, m, th0, spec, mask=mask, var=var, ws=ws, stream=stream)
-    f1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_eval = f0.elapsed_time(f1) / k_ev / 1000.0
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    nat.time_eval(R, I, m, th0, spec, mask=mask, var=var, reps=3, flush=flush, ws=ws,
+                  stream=stream)
+    t_eval = nat.time_eval(R, I, m, th0, spec, mask=mask, var=var, reps=args.kernel_evals,
+                           flush=flush, ws=ws, stream=stream) / 1000.0
+    del flush
     npx = int(d["mask"][h:H - h, h:W - h].sum()) if d.get("mask") is not None else (H - 2 * h) * (W - 2 * h)
     flops = 4.0 * m * m * npx
     peaks, src = _peaks()
@@ -475,7 +471,10 @@ def run_ours(args, rank, world, local_rank):
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (max SM clock, "
                           f"{src} peaks file); FP32 FMA pipe",
             "algorithmic": f"4*m^2 flop x {npx} unmasked valid px = {flops / 1e9:.2f} GFLOP per launch",
-            "eval_ms": t_eval * 1e3}
+            "eval_ms": t_eval * 1e3,
+            "timing": f"dia_time_eval: mean of {args.kernel_evals} launches, each between CUDA "
+                      f"events on the launching stream after overwriting {2 * L2_BYTES >> 20} MiB "
+                      f"(L2 flushed)"}
 
     # the same fit without the Adam phase (preconditioned L-BFGS from the start)
     o_off = nat.default_opts(clip_passes=opts.clip_passes, clip_kappa=opts.clip_kappa,
@@ -900,8 +899,12 @@ def run_tc_forward(args):
 
 
 def run_kernel_only(args):
-    """W + K back-to-back fused evaluations (dia_loss_grad) of the workload at
-    the box-car start: the driver of the ncu captures of the fused kernel."""
+    """The fused loss+gradient kernel of the workload at the box-car start:
+    its launches alone (dia_time_eval: CUDA events around each launch on the
+    stream, L2 overwritten before each), and whole dia_loss_grad calls
+    (preparation, kernel, reduction) back to back; the driver of the ncu
+    captures of the fused kernel.  Reports algorithmic GB/s and TFLOP/s and
+    their fractions of the measured HBM copy and of the FP32 pipe."""
     import torch
     from paper_2104_13715_gb300 import native as nat
     d = synth.workload(args.workload, seed=args.seed, size=args.size)
@@ -917,10 +920,17 @@ def run_kernel_only(args):
     spec = nat.loss_spec(**_loss_kw(d))
     if args.variant is not None:
         nat.select_kernel_variant(m, args.variant)
+    if args.tiled:
+        nat.set_small_kernel(False)
     ws = nat.workspace(H, W, m, device=dev)
     th = torch.full((m * m + 1,), 1.0 / (m * m), dtype=torch.float64, device=dev)
     th[-1] = float(np.median(d["I"]))
     s = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    nat.time_eval(R, I, m, th, spec, mask=mask, var=var, reps=args.warmup, flush=flush, ws=ws,
+                  stream=s)
+    ms_k = nat.time_eval(R, I, m, th, spec, mask=mask, var=var, reps=args.steps, flush=flush,
+                         ws=ws, stream=s)
     for _ in range(args.warmup):
         nat.loss_grad(R, I, m, th, spec, mask=mask, var=var, ws=ws, stream=s)
     torch.cuda.synchronize(dev)
@@ -930,16 +940,27 @@ def run_kernel_only(args):
         nat.loss_grad(R, I, m, th, spec, mask=mask, var=var, ws=ws, stream=s)
     e1.record(s)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    ms_call = e0.elapsed_time(e1) / max(args.steps, 1)
     h = m // 2
     npx = int(d["mask"][h:H - h, h:W - h].sum()) if d.get("mask") is not None else (H - 2 * h) * (W - 2 * h)
     # bytes every evaluation must read: R and I, and the mask / variance map if
     # given (4 + 4 + 1 + 4 per pixel of the image)
     nbytes = H * W * (8 + (1 if d.get("mask") is not None else 0) + (4 if d.get("var") is not None else 0))
+    flops = 4.0 * m * m * npx
+    peaks, src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tf = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    gbs = nbytes / ms_k / 1e6
+    tfl = flops / ms_k / 1e9
     print(json.dumps({"kernel_only": args.workload, "H": H, "W": W, "m": m,
-                      "variant": nat.kernel_variant_desc(m), "ms_per_eval": ms,
-                      "tflops_algorithmic": 4.0 * m * m * npx / ms / 1e9,
-                      "gbs_algorithmic": nbytes / ms / 1e6, "bytes_algorithmic": nbytes}), flush=True)
+                      "form": "tiled" if (args.tiled or m > 5) else "streaming small-kernel",
+                      "variant": nat.kernel_variant_desc(m), "ms_per_launch": ms_k,
+                      "ms_per_call": ms_call,
+                      "gbs_algorithmic": gbs, "hbm_frac": gbs / float(peaks["hbm_gbs"]),
+                      "tflops_algorithmic": tfl, "fp32_frac": tfl / peak_tf,
+                      "bytes_algorithmic": nbytes, "flops_algorithmic": flops,
+                      "peaks": f"{peaks['hbm_gbs']} GB/s HBM copy, {peak_tf:.1f} TFLOP/s FP32 "
+                               f"({src})"}), flush=True)
 
 
 def main():
@@ -963,6 +984,9 @@ def main():
                     help="time the fused loss+gradient kernel alone (ncu driver)")
     ap.add_argument("--size", type=int, default=None, help="image side override (--kernel-only)")
     ap.add_argument("--variant", type=int, default=None, help="tile variant (--kernel-only)")
+    ap.add_argument("--tiled", action="store_true",
+                    help="the tiled kernel even where the streaming small-kernel form applies "
+                         "(--kernel-only)")
     ap.add_argument("--tc-forward", action="store_true",
                     help="time the forward pass on CUDA cores and on tensor cores")
     ap.add_argument("--s10-study", type=int, default=0,

@@ -232,6 +232,21 @@ int32_t dia_kernel_variants(int32_t m);
 #define DIA_ACCUM_FP32 1
 dia_status dia_set_accumulation(int32_t mode);
 int32_t dia_get_accumulation(void);
+/* Streaming form of the fused evaluation for small kernels (m = 1, 3, 5: the
+ * memory-bound end of the kernel-size sweep of Sec. 5.3, where each pixel
+ * costs 2 m^2 FMAs against 8-17 bytes of input).  Enabled (1, default), the
+ * gradient-mode evaluations of dia_loss_grad and dia_fit use it whenever it
+ * applies: m <= 5, constant background, DIA_ACCUM_FP64, 16-byte aligned
+ * images with a row pitch that is a multiple of 4 floats (of 16 bytes when a
+ * mask is given; dia_fit's clipping mask has the pair's pitch); otherwise,
+ * and with 0, the tiled kernel runs.  Each warp streams a strip of rows
+ * through a private shared-memory ring (cp.async) and keeps the R window in
+ * registers; per-lane float32 sums over one strip (at most 4096 pixels),
+ * float64 across lanes, warps and CTAs.  Process-wide; not safe to change
+ * while another host thread launches work.  Returns DIA_ERR_ARG unless
+ * enable is 0 or 1. */
+dia_status dia_set_small_kernel(int32_t enable);
+int32_t dia_get_small_kernel(void);
 dia_status dia_select_kernel_variant(int32_t m, int32_t variant);
 dia_status dia_kernel_variant_desc(int32_t m, int32_t variant, int32_t *warps,
                                    int32_t *rows_per_warp, int32_t *tile_rows,
@@ -257,6 +272,21 @@ size_t dia_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m, int32_t c
  * Asynchronous on `stream`. */
 dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss,
                          const double *theta, double *loss_out, double *grad_out,
+                         void *workspace, size_t workspace_bytes, void *stream);
+
+/* Device time of the fused evaluation kernel alone (the gradient-mode
+ * launch dia_loss_grad makes: the streaming small-kernel form or the tiled
+ * kernel, as dia_set_small_kernel and the pair decide), for roofline figures
+ * and the tile autotuner.  The float32 copy of theta is prepared once, then
+ * `reps` launches are each bracketed by CUDA events on `stream`; if
+ * flush_bytes > 0, flush_buf (device, flush_bytes; make it larger than the
+ * L2 cache) is overwritten before every launch so each one reads its inputs
+ * from HBM.  *ms_out (HOST) receives the mean milliseconds per launch.  The
+ * partial sums are left in the workspace (no reduction runs).  Synchronous.
+ * Errors: DIA_ERR_ARG (reps outside 1..100000, flush_bytes without a buffer,
+ * bad pair or loss), DIA_ERR_WORKSPACE, DIA_ERR_CUDA. */
+dia_status dia_time_eval(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
+                         int32_t reps, void *flush_buf, size_t flush_bytes, float *ms_out,
                          void *workspace, size_t workspace_bytes, void *stream);
 
 /* Difference image D = I - M over the valid region (Sec. 1) for theta

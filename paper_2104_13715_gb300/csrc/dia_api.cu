@@ -18,6 +18,7 @@
 #include "dia_dispatch.h"
 #include "dia_eval.cuh"
 #include "dia_ops.cuh"
+#include "dia_small.h"
 
 using namespace dia;
 
@@ -34,6 +35,8 @@ struct NvtxRange {
 };
 // accumulation form of the single-pair entries (dia_set_accumulation)
 std::atomic<int> g_accumulation{DIA_ACCUM_FP64};
+// streaming small-kernel evaluation for m <= 5 (dia_set_small_kernel)
+std::atomic<int> g_small_kernel{1};
 
 #define DIA_CK(expr)                               \
     do {                                           \
@@ -174,7 +177,30 @@ struct Ctx {
     float *kpad;
     double *red, *partials;
     int nb;         // background coefficients of the pair
+    int small_grid; // > 0: gradient-mode evaluations use the small-kernel form on this grid
 };
+
+// Picks the streaming small-kernel form (dia_small.cu) for the gradient-mode
+// evaluations of these arguments when it applies (m <= 5, constant
+// background, float64 accumulation, aligned images) and is enabled.
+cudaError_t choose_small(Ctx &c, const EvalArgs &ea) {
+    c.small_grid = 0;
+    if (!g_small_kernel.load() || !small_kernel_ok(ea, c.dp.m)) return cudaSuccess;
+    int occ = 1;
+    cudaError_t e = small_kernel_prepare(ea, c.dp.m, &occ);
+    if (e != cudaSuccess) return e;
+    long long g = (long long)device_sms() * (occ < 1 ? 1 : occ);
+    if (g > c.L.G) g = c.L.G;
+    c.small_grid = (int)g;
+    return cudaSuccess;
+}
+
+cudaError_t launch_grad(const Ctx &c, const EvalArgs &ea, cudaStream_t s) {
+    if (c.small_grid > 0) return launch_eval_small(ea, c.dp.m, c.ki.kp, c.L.np, c.small_grid, s);
+    return launch_eval(c.ki, kModeGrad, ea, c.grid, s);
+}
+
+int grad_grid(const Ctx &c) { return c.small_grid > 0 ? c.small_grid : c.grid; }
 
 dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void *workspace,
                  size_t ws_bytes, cudaStream_t s, Ctx &c) {
@@ -272,6 +298,7 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     c.ob.pdiag = (double *)(c.ws + c.L.pdiag);
     c.ob.P = nullptr;
     c.ob.ldp = pc_ldp(pair->m * pair->m + c.nb);
+    DIA_CK(choose_small(c, c.ea));
     return DIA_OK;
 }
 
@@ -303,9 +330,9 @@ void append(std::string &k, const T &v) {
 
 // One optimiser iteration = fused evaluation, float64 reduction, optimiser step.
 cudaError_t enqueue_iteration(const Ctx &c, const EvalArgs &ea, const StepArgs &sa, cudaStream_t s) {
-    cudaError_t e = launch_eval(c.ki, kModeGrad, ea, c.grid, s);
+    cudaError_t e = launch_grad(c, ea, s);
     if (e != cudaSuccess) return e;
-    e = launch_reduce(c.partials, c.grid, c.L.np, c.red, &c.st->done, s, ea.acc32);
+    e = launch_reduce(c.partials, grad_grid(c), c.L.np, c.red, &c.st->done, s, ea.acc32);
     if (e != cudaSuccess) return e;
     return launch_step(sa, s);
 }
@@ -320,6 +347,7 @@ dia_status get_graph(const Ctx &c, const EvalArgs &ea, const StepArgs &sa, int i
     append(key, sa);
     append(key, iters);
     append(key, c.grid);
+    append(key, c.small_grid);
     append(key, c.ki);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it)
@@ -412,6 +440,14 @@ dia_status dia_set_accumulation(int32_t mode) {
 
 int32_t dia_get_accumulation(void) { return g_accumulation.load(); }
 
+dia_status dia_set_small_kernel(int32_t enable) {
+    if (enable != 0 && enable != 1) return DIA_ERR_ARG;
+    g_small_kernel.store(enable);
+    return DIA_OK;
+}
+
+int32_t dia_get_small_kernel(void) { return g_small_kernel.load(); }
+
 int32_t dia_last_cuda_error(void) { return g_last_cuda; }
 
 int32_t dia_kernel_variants(int32_t m) {
@@ -464,9 +500,41 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss, const 
     dia_status rc = setup(pair, loss, 0, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
     DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
-    DIA_CK(launch_eval(c.ki, kModeGrad, c.ea, c.grid, s));
-    DIA_CK(launch_reduce(c.partials, c.grid, c.L.np, c.red, nullptr, s, c.ea.acc32));
+    DIA_CK(launch_grad(c, c.ea, s));
+    DIA_CK(launch_reduce(c.partials, grad_grid(c), c.L.np, c.red, nullptr, s, c.ea.acc32));
     DIA_CK(launch_emit_loss_grad(c.red, pair->m, c.nb, loss_out, grad_out, s));
+    return DIA_OK;
+}
+
+dia_status dia_time_eval(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
+                         int32_t reps, void *flush_buf, size_t flush_bytes, float *ms_out,
+                         void *workspace, size_t workspace_bytes, void *stream) {
+    if (!pair || pair->mem != DIA_MEM_DEVICE || !loss || !theta || !ms_out || reps < 1 ||
+        reps > 100000 || (flush_bytes > 0 && !flush_buf))
+        return DIA_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    dia_status rc = setup(pair, loss, 0, workspace, workspace_bytes, s, c);
+    if (rc != DIA_OK) return rc;
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DIA_CK(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    float total = 0.f;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        if (flush_bytes > 0) e = cudaMemsetAsync(flush_buf, r & 1, flush_bytes, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch_grad(c, c.ea, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        total += ms;
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    DIA_CK(e);
+    *ms_out = total / (float)reps;
     return DIA_OK;
 }
 
@@ -539,6 +607,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         else
             DIA_CK(cudaMemsetAsync(wmask, 1, (size_t)H * ld, s));
         c.ea.mask = wmask;
+        DIA_CK(choose_small(c, c.ea));   // the working mask has the pair's pitch
     }
     c.ea.clip_kappa = opts.clip_kappa;
 

@@ -101,6 +101,12 @@ _SIGS = {
     "dia_batch_workspace_size": (ctypes.c_size_t, [_P(Pair), ctypes.c_int32, _P(Opts)]),
     "dia_fisher_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 4),
     "dia_set_accumulation": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_set_small_kernel": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_time_eval": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_float), ctypes.c_void_p,
+                                       ctypes.c_size_t, ctypes.c_void_p]),
+    "dia_get_small_kernel": (ctypes.c_int32, []),
     "dia_get_accumulation": (ctypes.c_int32, []),
     "dia_fisher": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, _P(FisherInfo), ctypes.c_void_p,
@@ -160,6 +166,16 @@ ACCUM_FP64, ACCUM_FP32 = 0, 1
 def set_accumulation(mode: int) -> None:
     """dia_set_accumulation: ACCUM_FP64 (default) or ACCUM_FP32 (comparison form)."""
     _check(lib.dia_set_accumulation(int(mode)), "dia_set_accumulation")
+
+
+def set_small_kernel(enable: bool) -> None:
+    """dia_set_small_kernel: the streaming small-kernel evaluation (m <= 5)
+    on (default) or off (the tiled kernel for every m)."""
+    _check(lib.dia_set_small_kernel(1 if enable else 0), "dia_set_small_kernel")
+
+
+def get_small_kernel() -> bool:
+    return bool(lib.dia_get_small_kernel())
 
 
 def get_accumulation() -> int:
@@ -274,6 +290,22 @@ def loss_grad(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, ws
                            _ptr(grad), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "dia_loss_grad")
     return loss, grad
+
+
+def time_eval(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, reps=20,
+              flush=None, ws=None, stream=None, bg_degree=0) -> float:
+    """dia_time_eval: mean device milliseconds of the fused evaluation kernel
+    alone over `reps` launches (CUDA events on the stream), each after
+    overwriting the uint8 device tensor `flush` (if given) to evict L2."""
+    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
+    theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
+    ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
+    ms = ctypes.c_float(0.0)
+    st = lib.dia_time_eval(ctypes.byref(pair), ctypes.byref(spec), _ptr(theta), int(reps),
+                           _ptr(flush), 0 if flush is None else flush.numel(), ctypes.byref(ms),
+                           _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "dia_time_eval")
+    return float(ms.value)
 
 
 def fisher(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, want_F=True,
