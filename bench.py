@@ -473,8 +473,8 @@ def run_ours(args, rank, world, local_rank):
             "algorithmic": f"4*m^2 flop x {npx} unmasked valid px = {flops / 1e9:.2f} GFLOP per launch",
             "eval_ms": t_eval * 1e3,
             "timing": f"dia_time_eval: mean of {args.kernel_evals} launches, each between CUDA "
-                      f"events on the launching stream after overwriting {2 * L2_BYTES >> 20} MiB "
-                      f"(L2 flushed)"}
+                      f"events on the launching stream after reading {2 * L2_BYTES >> 20} MiB "
+                      f"through L2 (L2 flushed, no dirty lines)"}
 
     # the same fit without the Adam phase (preconditioned L-BFGS from the start)
     o_off = nat.default_opts(clip_passes=opts.clip_passes, clip_kappa=opts.clip_kappa,
@@ -963,6 +963,56 @@ def run_kernel_only(args):
                                f"({src})"}), flush=True)
 
 
+def run_m_sweep(args):
+    """The kernel-size sweep of the paper's speed tests (Sec. 5.3, a 1000^2
+    crop fitted with kernels of increasing size): a 1000^2 field (lg rho = 1.5
+    per 100^2 px, phi_R = 1, phi_K = 1.5, sky 100, the Sec. 5.2 recipe) fitted
+    with the fixed-variance chi^2 for every odd m in 3..31.  Per m: the fused
+    evaluation kernel alone (dia_time_eval, L2 flushed before each launch) in
+    algorithmic TFLOP/s and GB/s against the FP32 pipe and the measured HBM
+    copy, and one full fit (dia_fit, Adam then L-BFGS) in ms with its
+    evaluation count."""
+    import torch
+    from paper_2104_13715_gb300 import native as nat
+    dev = torch.device("cuda", 0)
+    peaks, src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tf = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    rows = []
+    for m in range(3, 32, 2):
+        spec_p = synth.PairSpec(size=(1000, 1000), n_stars=int(round(10 ** 1.5 * 100)), m=m,
+                                fwhm_ref=2.0 * math.sqrt(2 * math.log(2.0)), kernel_sigma=1.5,
+                                sky=100.0, flux_law="paper", read=5.0, gain=1.0)
+        d = synth.make_pair(spec_p, args.seed + m)
+        R = torch.from_numpy(d["R"]).to(dev)
+        I = torch.from_numpy(d["I"]).to(dev)
+        spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
+        th = torch.full((m * m + 1,), 1.0 / (m * m), dtype=torch.float64, device=dev)
+        th[-1] = float(np.median(d["I"]))
+        ws = nat.workspace(1000, 1000, m, device=dev)
+        nat.time_eval(R, I, m, th, spec, reps=3, flush=flush, ws=ws)
+        ms = nat.time_eval(R, I, m, th, spec, reps=args.steps, flush=flush, ws=ws)
+        h = m // 2
+        npx = (1000 - 2 * h) ** 2
+        tfl = 4.0 * m * m * npx / ms / 1e9
+        gbs = 1000 * 1000 * 8 / ms / 1e6
+        nat.fit(R, I, m, spec, want_diff=False)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = nat.fit(R, I, m, spec, want_diff=False)
+        torch.cuda.synchronize(dev)
+        fit_ms = (time.perf_counter() - t0) * 1e3
+        rows.append({"m": m, "eval_ms": ms, "tflops": tfl, "fp32_frac": tfl / peak_tf,
+                     "gbs": gbs, "hbm_frac": gbs / float(peaks["hbm_gbs"]),
+                     "form": "streaming small-kernel" if m <= 5 else "tiled",
+                     "fit_ms": fit_ms, "fit_evals": out["info"]["evals"],
+                     "fit_status": out["info"]["status"]})
+    print(json.dumps({"m_sweep": "1000x1000 chi^2, Sec. 5.3 recipe", "rows": rows,
+                      "peaks": f"{peaks['hbm_gbs']} GB/s HBM copy, {peak_tf:.1f} TFLOP/s FP32 "
+                               f"({src})"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -993,7 +1043,12 @@ def main():
                     help="run the simulated-image accuracy study with this many simulations")
     ap.add_argument("--precision-study", action="store_true",
                     help="float64 vs float32 accumulation on the 2048^2 HDR field")
+    ap.add_argument("--m-sweep", action="store_true",
+                    help="kernel-size sweep m = 3..31 on a 1000^2 field (Sec. 5.3)")
     args = ap.parse_args()
+    if args.m_sweep:
+        run_m_sweep(args)
+        return
     if args.s10_study:
         run_s10_study(args)
         return

@@ -36,6 +36,14 @@
  *   b_00, b_01, ..., b_0d, b_10, ..., b_d0 (power of xi fastest, the order of
  *   the double sum of Eq. 18); n = m*m + 1 (K, then B0) for d = 0.  b_00 is the
  *   background at the image centre.
+ * Spatially varying kernel: a pair's kernel_degree dk (0 <= dk <=
+ *   DIA_MAX_KERNEL_DEGREE) makes every kernel pixel a polynomial of degree dk
+ *   in the same coordinates, K_ab(x, y) = sum_{p+q<=dk} K_pq[a][b] eta^p xi^q,
+ *   evaluated at the output pixel (the extension Sec. 1 cites, in the Bramich
+ *   et al. 2013 form); theta then holds nc = (dk+1)(dk+2)/2 kernels of m*m
+ *   (K_00, K_01, ..., K_dk0, the order of Eq. 18) before the background
+ *   coefficients: n = nc*m*m + (d+1)(d+2)/2.  K_00 is the kernel at the image
+ *   centre.  dk = 0 is the constant kernel.
  * Mask: nonzero = use the pixel, 0 = masked.  The mask refers to target
  *   pixels; a bad reference pixel must be masked (dilated by h) by the caller.
  * Memory: unless a pair says DIA_MEM_HOST, every pointer is a DEVICE pointer
@@ -63,7 +71,8 @@ extern "C" {
 
 #define DIA_MAX_M 31           /* largest odd kernel side of the fused kernels */
 #define DIA_MAX_BG_DEGREE 4    /* largest degree of the polynomial background */
-#define DIA_ABI_VERSION 3
+#define DIA_MAX_KERNEL_DEGREE 2 /* largest degree of a spatially varying kernel */
+#define DIA_ABI_VERSION 4
 
 typedef enum {
     DIA_OK = 0,
@@ -119,6 +128,11 @@ typedef struct {
                                   outputs of the call live */
     int32_t bg_degree;         /* degree d of the background polynomial (Eq. 18);
                                   0 = constant B0 */
+    int32_t kernel_degree;     /* degree dk of a spatially varying kernel (0 = one
+                                  kernel for the whole image); dia_loss_grad,
+                                  dia_diff_image, dia_fit and dia_fisher take dk > 0
+                                  (with reg_lambda = 0); the other entries return
+                                  DIA_ERR_UNSUPPORTED */
 } dia_pair;
 
 /* Optimiser settings (Sec. 2.9).  dia_opts_default() fills the paper's
@@ -261,6 +275,11 @@ dia_status dia_kernel_variant_desc(int32_t m, int32_t variant, int32_t *warps,
  * covers every tile variant of m. */
 size_t dia_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m, int32_t clip, int32_t mem);
 
+/* The same for a whole pair description (its H, W, ld, m, mem and
+ * kernel_degree); the only size query for pairs with kernel_degree > 0.
+ * Returns 0 for an invalid pair. */
+size_t dia_pair_workspace_size(const dia_pair *pair, int32_t clip);
+
 /* One loss + gradient evaluation at theta (Sec. 2.3, Eq. 8 / Eq. 13).
  *   theta     device float64[n]  (read; the kernel works in float32 pixels)
  *   loss_out  device float64[1]  L = sum over unmasked valid pixels
@@ -279,9 +298,10 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss,
  * kernel, as dia_set_small_kernel and the pair decide), for roofline figures
  * and the tile autotuner.  The float32 copy of theta is prepared once, then
  * `reps` launches are each bracketed by CUDA events on `stream`; if
- * flush_bytes > 0, flush_buf (device, flush_bytes; make it larger than the
- * L2 cache) is overwritten before every launch so each one reads its inputs
- * from HBM.  *ms_out (HOST) receives the mean milliseconds per launch.  The
+ * flush_bytes > 0, flush_buf (device, 16-byte aligned, flush_bytes; make it
+ * larger than the L2 cache; its contents are only read) is read through L2
+ * before every launch, so each launch reads its inputs from HBM and finds no
+ * dirty lines to write back.  *ms_out (HOST) receives the mean milliseconds per launch.  The
  * partial sums are left in the workspace (no reduction runs).  Synchronous.
  * Errors: DIA_ERR_ARG (reps outside 1..100000, flush_bytes without a buffer,
  * bad pair or loss), DIA_ERR_WORKSPACE, DIA_ERR_CUDA. */
@@ -306,6 +326,15 @@ dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff
  * ran out (the kernel bounds every wait). */
 dia_status dia_diff_image_tc(const dia_pair *pair, const double *theta, float *diff_out,
                              void *workspace, size_t workspace_bytes, void *stream);
+
+/* Limit, in SM clock cycles, of each pipeline wait of dia_diff_image_tc's
+ * kernel (an mbarrier wait of a producer or MMA role); 0 restores the default
+ * (2e9 cycles, about one second).  A wait that runs out aborts every role of
+ * the CTA: in-flight copies and MMAs are drained (with the default limit),
+ * tensor memory is released and the call returns DIA_ERR_TIMEOUT; the next
+ * call runs normally.  For exercising that failure path (a short limit makes
+ * a wait run out on a healthy GPU); process-wide.  DIA_ERR_ARG if cycles < 0. */
+dia_status dia_set_tc_wait_cycles(int64_t cycles);
 
 /* Fit theta = [K, background] (Sec. 2.10 algorithm): initialise, Adam until the
  * relative loss change drops below switch_tol, then L-BFGS (preconditioned
@@ -408,6 +437,8 @@ typedef struct {
 /* Workspace bytes of dia_fisher for this image and kernel side, any
  * background degree (0 if invalid). */
 size_t dia_fisher_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m);
+/* The same for a pair description (any kernel_degree; 0 if invalid). */
+size_t dia_pair_fisher_workspace_size(const dia_pair *pair);
 
 /* pair: DIA_MEM_DEVICE images; theta: DEVICE pointer, n doubles (e.g. the
  * theta_out of dia_fit); F_out, cov_out: nullable DEVICE pointers to n x n

@@ -19,6 +19,7 @@
 #include "dia_eval.cuh"
 #include "dia_ops.cuh"
 #include "dia_small.h"
+#include "dia_svk.h"
 
 using namespace dia;
 
@@ -37,6 +38,8 @@ struct NvtxRange {
 std::atomic<int> g_accumulation{DIA_ACCUM_FP64};
 // streaming small-kernel evaluation for m <= 5 (dia_set_small_kernel)
 std::atomic<int> g_small_kernel{1};
+// limit of the tensor-core kernel's pipeline waits (dia_set_tc_wait_cycles; 0 = default)
+std::atomic<long long> g_tc_wait_cycles{0};
 
 #define DIA_CK(expr)                               \
     do {                                           \
@@ -60,14 +63,40 @@ struct Layout {
     int pc_chunks;   // chunk partials the preconditioner's Hessian sum may use
 };
 
-bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInfo &ki, Layout &L) {
+// Preconditioner window of a spatially varying kernel: the whole valid region
+// (the coefficient kernels are only told apart by the variation of eta^p xi^q
+// across the image), chunked only while the chunk partials stay small.
+void svk_precond_window(int H, int W, int m, int n, int *y0, int *y1, int *x0, int *x1,
+                        int *chunks) {
+    const int h = m / 2;
+    *y0 = 0;
+    *y1 = H - 2 * h;
+    *x0 = 0;
+    *x1 = W - 2 * h;
+    const long long px = (long long)(*y1) * (*x1);
+    int c = (int)std::min(64LL, (px + kGnChunk - 1) / kGnChunk);
+    const int cap = std::max(1, 1024 / gn_blocks(n));   // about 1024 CTAs of the sum in all
+    *chunks = std::max(1, std::min(c, cap));
+}
+
+// kernel coefficient sets of a spatially varying kernel of degree kdeg (1: constant)
+int n_coef_of(int kdeg) { return n_background(kdeg); }
+
+bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInfo &ki, Layout &L,
+                 int kdeg = 0) {
     const int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h;
+    const int nc = n_coef_of(kdeg);
     L.tiles_x = (Wv + kTW - 1) / kTW;
     const int tiles_y = (Hv + ki.th - 1) / ki.th;
     L.n_tiles = L.tiles_x * tiles_y;
     // partial slots for the tile variant with the most tiles, so that one
-    // workspace serves whichever variant is selected
+    // workspace serves whichever variant is selected (and the tiling of the
+    // spatially varying kernel's evaluation)
     int max_tiles = L.n_tiles;
+    if (kdeg > 0) {
+        const int t = L.tiles_x * ((Hv + svk_tile_rows() - 1) / svk_tile_rows());
+        if (t > max_tiles) max_tiles = t;
+    }
     for (int v = 0; v < kernel_variants(m); ++v) {
         KernelInfo kv;
         if (kernel_info_variant(m, v, &kv)) {
@@ -76,8 +105,8 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
         }
     }
     L.G = max_tiles < kMaxGrid ? max_tiles : kMaxGrid;
-    L.np = ki.np;
-    L.n = m * m + kBgMax;   // capacity: the largest background
+    L.np = kdeg > 0 ? red_size(nc * m * m) : ki.np;
+    L.n = nc * m * m + kBgMax;   // capacity: the largest background
     L.kp = ki.kp;
     const size_t n8 = (size_t)L.n * 8;
     size_t o = 0;
@@ -110,12 +139,13 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
     L.pc_args = take(sizeof(PrecondArgs));
     int wy0, wy1, wx0, wx1, chunks;
     precond_window(H, W, m, true, 0, &wy0, &wy1, &wx0, &wx1, &chunks);
+    if (kdeg > 0) svk_precond_window(H, W, m, L.n, &wy0, &wy1, &wx0, &wx1, &chunks);
     L.pc_chunks = chunks;
     L.pc_part = take(chunks > 1 ? (size_t)chunks * gn_blocks(L.n) * kGnT * kGnT * 8 : 0);
     L.pc_A64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
     L.pc_X64 = take((size_t)pc_np(L.n) * pc_np(L.n) * 8);
     L.pc_P = take((size_t)L.n * pc_ldp(L.n) * 4);
-    L.kpad = take((size_t)(m * ki.kp + kBgMax + 1) * 4);
+    L.kpad = take((size_t)(nc * m * ki.kp + kBgMax + 1) * 4);
     const size_t plane = (size_t)H * (mem == DIA_MEM_HOST ? W : ld);
     L.mask = clip ? take(plane) : 0;
     if (mem == DIA_MEM_HOST) {
@@ -178,6 +208,9 @@ struct Ctx {
     double *red, *partials;
     int nb;         // background coefficients of the pair
     int small_grid; // > 0: gradient-mode evaluations use the small-kernel form on this grid
+    int kdeg, nc;   // spatially varying kernel: degree and coefficient kernels (0, 1: constant)
+    SvkArgs sv;
+    int svk_grid;   // grid of the spatially varying kernel's evaluations
 };
 
 // Picks the streaming small-kernel form (dia_small.cu) for the gradient-mode
@@ -185,7 +218,7 @@ struct Ctx {
 // background, float64 accumulation, aligned images) and is enabled.
 cudaError_t choose_small(Ctx &c, const EvalArgs &ea) {
     c.small_grid = 0;
-    if (!g_small_kernel.load() || !small_kernel_ok(ea, c.dp.m)) return cudaSuccess;
+    if (c.kdeg > 0 || !g_small_kernel.load() || !small_kernel_ok(ea, c.dp.m)) return cudaSuccess;
     int occ = 1;
     cudaError_t e = small_kernel_prepare(ea, c.dp.m, &occ);
     if (e != cudaSuccess) return e;
@@ -196,11 +229,20 @@ cudaError_t choose_small(Ctx &c, const EvalArgs &ea) {
 }
 
 cudaError_t launch_grad(const Ctx &c, const EvalArgs &ea, cudaStream_t s) {
+    if (c.kdeg > 0) return launch_eval_svk(ea, c.sv, c.dp.m, kModeGrad, c.svk_grid, s);
     if (c.small_grid > 0) return launch_eval_small(ea, c.dp.m, c.ki.kp, c.L.np, c.small_grid, s);
     return launch_eval(c.ki, kModeGrad, ea, c.grid, s);
 }
 
-int grad_grid(const Ctx &c) { return c.small_grid > 0 ? c.small_grid : c.grid; }
+// forward mode: difference image and / or clip mask
+cudaError_t launch_fwd(const Ctx &c, const EvalArgs &ea, cudaStream_t s) {
+    if (c.kdeg > 0) return launch_eval_svk(ea, c.sv, c.dp.m, kModeForward, c.svk_grid, s);
+    return launch_eval(c.ki, kModeForward, ea, c.grid, s);
+}
+
+int grad_grid(const Ctx &c) {
+    return c.kdeg > 0 ? c.svk_grid : (c.small_grid > 0 ? c.small_grid : c.grid);
+}
 
 dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void *workspace,
                  size_t ws_bytes, cudaStream_t s, Ctx &c) {
@@ -215,7 +257,10 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
         c.ki.fn[kModeGrad] = c.ki.fn_bg[kModeGrad];
         c.ki.fn[kModeForward] = c.ki.fn_bg[kModeForward];
     }
-    make_layout(pair->H, pair->W, pair->ld, pair->m, clip, pair->mem, c.ki, c.L);
+    c.kdeg = pair->kernel_degree;
+    c.nc = n_coef_of(c.kdeg);
+    if (c.nc * pair->m * pair->m + n_background(pair->bg_degree) > kMaxN) return DIA_ERR_UNSUPPORTED;
+    make_layout(pair->H, pair->W, pair->ld, pair->m, clip, pair->mem, c.ki, c.L, c.kdeg);
     if (!workspace || ws_bytes < c.L.total || ((uintptr_t)workspace % kAlign) != 0)
         return DIA_ERR_WORKSPACE;
     c.ws = (char *)workspace;
@@ -254,6 +299,21 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     long long g = (long long)device_sms() * occ;
     if (g > c.L.G) g = c.L.G;
     c.grid = (int)g;
+    c.svk_grid = 0;
+    memset(&c.sv, 0, sizeof(c.sv));
+    if (c.kdeg > 0) {
+        int occ3 = 1, smem3 = 0;
+        DIA_CK(svk_prepare(pair->m, &occ3, &smem3));
+        const int h0 = pair->m / 2;
+        const int svk_tiles = c.L.tiles_x * ((pair->H - 2 * h0 + svk_tile_rows() - 1) / svk_tile_rows());
+        long long g3 = (long long)device_sms() * (occ3 < 1 ? 1 : occ3);
+        if (g3 > svk_tiles) g3 = svk_tiles;
+        if (g3 > c.L.G) g3 = c.L.G;
+        c.svk_grid = (int)g3;
+        c.sv.kdeg = c.kdeg;
+        c.sv.nc = c.nc;
+        c.sv.np = c.L.np;
+    }
 
     const int h = pair->m / 2;
     EvalArgs &a = c.ea;
@@ -270,6 +330,8 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     a.Wv = W - 2 * h;
     a.tiles_x = c.L.tiles_x;
     a.n_tiles = c.L.n_tiles;
+    if (c.kdeg > 0)   // the spatially varying kernel's own tiling
+        a.n_tiles = c.L.tiles_x * ((a.Hv + svk_tile_rows() - 1) / svk_tile_rows());
     c.kpad = (float *)(c.ws + c.L.kpad);
     a.Kpad = c.kpad;
     c.partials = (double *)(c.ws + c.L.partials);
@@ -297,7 +359,7 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     c.ob.YPY = (double *)(c.ws + c.L.YPY);
     c.ob.pdiag = (double *)(c.ws + c.L.pdiag);
     c.ob.P = nullptr;
-    c.ob.ldp = pc_ldp(pair->m * pair->m + c.nb);
+    c.ob.ldp = pc_ldp(c.nc * pair->m * pair->m + c.nb);
     DIA_CK(choose_small(c, c.ea));
     return DIA_OK;
 }
@@ -348,6 +410,8 @@ dia_status get_graph(const Ctx &c, const EvalArgs &ea, const StepArgs &sa, int i
     append(key, iters);
     append(key, c.grid);
     append(key, c.small_grid);
+    append(key, c.svk_grid);
+    append(key, c.sv);
     append(key, c.ki);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it)
@@ -448,6 +512,12 @@ dia_status dia_set_small_kernel(int32_t enable) {
 
 int32_t dia_get_small_kernel(void) { return g_small_kernel.load(); }
 
+dia_status dia_set_tc_wait_cycles(int64_t cycles) {
+    if (cycles < 0) return DIA_ERR_ARG;
+    g_tc_wait_cycles.store((long long)cycles);
+    return DIA_OK;
+}
+
 int32_t dia_last_cuda_error(void) { return g_last_cuda; }
 
 int32_t dia_kernel_variants(int32_t m) {
@@ -490,6 +560,18 @@ size_t dia_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m, int32_t c
     return L.total;
 }
 
+size_t dia_pair_workspace_size(const dia_pair *pair, int32_t clip) {
+    if (!pair || !dims_ok(pair->H, pair->W, pair->ld, pair->m) || pair->m > DIA_MAX_M) return 0;
+    if (pair->mem != DIA_MEM_DEVICE && pair->mem != DIA_MEM_HOST) return 0;
+    if (pair->kernel_degree < 0 || pair->kernel_degree > DIA_MAX_KERNEL_DEGREE) return 0;
+    KernelInfo ki;
+    if (!kernel_info(pair->m, &ki)) return 0;
+    Layout L;
+    make_layout(pair->H, pair->W, pair->ld, pair->m, clip != 0, pair->mem, ki, L,
+                pair->kernel_degree);
+    return L.total;
+}
+
 dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
                          double *loss_out, double *grad_out, void *workspace,
                          size_t workspace_bytes, void *stream) {
@@ -499,30 +581,51 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss, const 
     Ctx c;
     dia_status rc = setup(pair, loss, 0, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
-    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s, c.nc));
     DIA_CK(launch_grad(c, c.ea, s));
     DIA_CK(launch_reduce(c.partials, grad_grid(c), c.L.np, c.red, nullptr, s, c.ea.acc32));
-    DIA_CK(launch_emit_loss_grad(c.red, pair->m, c.nb, loss_out, grad_out, s));
+    DIA_CK(launch_emit_loss_grad(c.red, pair->m, c.nb, loss_out, grad_out, s, c.nc));
     return DIA_OK;
 }
+
+namespace {
+// Reads `n` bytes (16-byte aligned, n a multiple of 16) so that the L2 cache
+// holds them instead of the previous contents; clean lines only (no
+// write-backs during the next kernel).  Writes nothing in practice: the
+// store is taken only if the folded sum equals a value the data never gives.
+__global__ void l2_flush_read_kernel(const uint4 *p, size_t n16, unsigned *sink) {
+    unsigned acc = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldcg(p + i);
+        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x9e3779b9u && sink) *sink = acc;
+}
+}  // namespace
 
 dia_status dia_time_eval(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
                          int32_t reps, void *flush_buf, size_t flush_bytes, float *ms_out,
                          void *workspace, size_t workspace_bytes, void *stream) {
     if (!pair || pair->mem != DIA_MEM_DEVICE || !loss || !theta || !ms_out || reps < 1 ||
-        reps > 100000 || (flush_bytes > 0 && !flush_buf))
+        reps > 100000 || (flush_bytes > 0 && !flush_buf) ||
+        ((uintptr_t)flush_buf & 15) != 0)
         return DIA_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     Ctx c;
     dia_status rc = setup(pair, loss, 0, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
-    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s, c.nc));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     DIA_CK(cudaEventCreate(&e0));
     cudaError_t e = cudaEventCreate(&e1);
     float total = 0.f;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-        if (flush_bytes > 0) e = cudaMemsetAsync(flush_buf, r & 1, flush_bytes, s);
+        if (flush_bytes >= 16) {
+            l2_flush_read_kernel<<<device_sms() * 8, 256, 0, s>>>((const uint4 *)flush_buf,
+                                                                  flush_bytes / 16, nullptr);
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         if (e == cudaSuccess) e = launch_grad(c, c.ea, s);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
@@ -548,17 +651,17 @@ dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff
     ls.var_scalar = 1.f;
     dia_status rc = setup(pair, &ls, 0, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
-    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
+    DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s, c.nc));
     EvalArgs ea = c.ea;
     ea.diff_out = diff_out;
-    DIA_CK(launch_eval(c.ki, kModeForward, ea, c.grid, s));
+    DIA_CK(launch_fwd(c, ea, s));
     return DIA_OK;
 }
 
 dia_status dia_diff_image_tc(const dia_pair *pair, const double *theta, float *diff_out,
                              void *workspace, size_t workspace_bytes, void *stream) {
     if (!pair || pair->mem != DIA_MEM_DEVICE || !theta || !diff_out) return DIA_ERR_ARG;
-    if (pair->bg_degree != 0) return DIA_ERR_UNSUPPORTED;
+    if (pair->bg_degree != 0 || pair->kernel_degree != 0) return DIA_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     Ctx c;
     dia_loss_spec ls;
@@ -570,7 +673,7 @@ dia_status dia_diff_image_tc(const dia_pair *pair, const double *theta, float *d
     DIA_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
     DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
     DIA_CK(launch_tc_forward(c.dp.ref, c.dp.img, c.dp.H, c.dp.W, c.dp.ld, pair->m, c.kpad,
-                             c.ki.kp, diff_out, status, s));
+                             c.ki.kp, diff_out, status, s, g_tc_wait_cycles.load()));
     int hs = 0;
     DIA_CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     DIA_CK(cudaStreamSynchronize(s));
@@ -589,12 +692,14 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         fill_opts_default(&opts);
     if (check_opts(opts, 2) != DIA_OK) return DIA_ERR_ARG;
     if (!pair || !loss) return DIA_ERR_ARG;
+    // the regulariser of Eq. 20 is defined for one kernel
+    if (pair->kernel_degree > 0 && opts.reg_lambda > 0.0) return DIA_ERR_UNSUPPORTED;
     const int clip = opts.clip_passes > 0 || mask_out != nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     Ctx c;
     dia_status rc = setup(pair, loss, clip, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
-    const int m = pair->m, nk = m * m, n = nk + c.nb, h = m / 2;
+    const int m = pair->m, nk = m * m, n = c.nc * nk + c.nb, h = m / 2;
     const int H = c.dp.H, W = c.dp.W, ld = c.dp.ld;
     const bool host = pair->mem == DIA_MEM_HOST;
 
@@ -616,14 +721,15 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     long long launches = 0;   // kernels this call launches (graph nodes included)
     if (opts.init == 2) {
         DIA_CK(cudaMemcpyAsync(c.ob.theta, opts.theta0, (size_t)n * 8, cudaMemcpyHostToDevice, s));
-        DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, c.nb, 2, 0.0, nullptr, start_phase, s));
+        DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, c.nb, 2, 0.0, nullptr, start_phase, s,
+                           c.nc));
         launches += 1;
     } else {
         int mgrid = device_sms() * 4;
         DIA_CK(launch_median(c.dp.img, c.ea.mask, H, W, ld, m, (uint32_t *)(c.ws + c.L.hist),
                              c.sel, mgrid, s));
         DIA_CK(launch_init(c.st, c.ob, c.kpad, m, c.ki.kp, c.nb, opts.init, opts.init_sigma,
-                           c.sel, start_phase, s));
+                           c.sel, start_phase, s, c.nc));
         launches += kMedianLaunches + 1;
     }
 
@@ -646,6 +752,9 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             pa.m = m;
             precond_window(H, W, m, true, opts.precond_window, &pa.y0, &pa.y1, &pa.x0, &pa.x1,
                            &pa.gn_chunks);
+            if (c.kdeg > 0)
+                svk_precond_window(H, W, m, c.L.n, &pa.y0, &pa.y1, &pa.x0, &pa.x1, &pa.gn_chunks);
+            pa.kdeg = c.kdeg;
             pa.gn_chunks = std::min(pa.gn_chunks, c.L.pc_chunks);   // the workspace's partials
             pa.lp = c.ea.lp;
             pa.part = (double *)(c.ws + c.L.pc_part);
@@ -682,6 +791,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     sa.n = n;
     sa.mk = m;
     sa.kp = c.ki.kp;
+    sa.nc = c.nc;
     sa.p.lr_kernel = opts.lr_kernel;
     sa.p.lr_b0 = opts.lr_b0;
     sa.p.beta1 = opts.beta1;
@@ -715,8 +825,8 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             // clip |z| > kappa at the current theta, then refit from it
             EvalArgs ca = c.ea;
             ca.mask_out = wmask;
-            DIA_CK(launch_eval(c.ki, kModeForward, ca, c.grid, s));
-            DIA_CK(launch_restart(c.st, c.kpad, c.ob, m, c.ki.kp, c.nb, s));
+            DIA_CK(launch_fwd(c, ca, s));
+            DIA_CK(launch_restart(c.st, c.kpad, c.ob, m, c.ki.kp, c.nb, s, c.nc));
             launches += 2;
             passes_done = pass;
         }
@@ -748,7 +858,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     if (diff_out) {
         EvalArgs da = c.ea;
         da.diff_out = host ? (float *)(c.ws + c.L.stage_diff) : diff_out;
-        DIA_CK(launch_eval(c.ki, kModeForward, da, c.grid, s));
+        DIA_CK(launch_fwd(c, da, s));
         launches += 1;
         if (host)
             DIA_CK(cudaMemcpyAsync(diff_out, da.diff_out, (size_t)(H - 2 * h) * (W - 2 * h) * 4,
@@ -756,7 +866,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     }
     if (host) {
         float *kst = (float *)(c.ws + c.L.stage_out);
-        DIA_CK(launch_pack_outputs(c.ob.theta, m, c.nb, nullptr, kst, kst + m * m, s));
+        DIA_CK(launch_pack_outputs(c.ob.theta, m, c.nb, nullptr, kst, kst + m * m, s, c.nc));
         launches += 1;
         if (theta_out)
             DIA_CK(cudaMemcpyAsync(theta_out, c.ob.theta, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -765,13 +875,13 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         if (mask_out)
             DIA_CK(cudaMemcpy2DAsync(mask_out, pair->ld, wmask, W, W, H, cudaMemcpyDeviceToHost, s));
     } else {
-        DIA_CK(launch_pack_outputs(c.ob.theta, m, c.nb, theta_out, K_out, b0_out, s));
+        DIA_CK(launch_pack_outputs(c.ob.theta, m, c.nb, theta_out, K_out, b0_out, s, c.nc));
         launches += 1;
         if (mask_out)
             DIA_CK(cudaMemcpyAsync(mask_out, wmask, (size_t)H * ld, cudaMemcpyDeviceToDevice, s));
     }
     if (info) {
-        double th[DIA_MAX_M * DIA_MAX_M + kBgMax];
+        double th[kMaxN];
         DIA_CK(cudaMemcpyAsync(th, c.ob.theta, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
         DIA_CK(cudaStreamSynchronize(s));
         double P = 0.0;
@@ -785,7 +895,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
         info->loss = hs.L_sum;
         info->grad_inf = hs.grad_inf;
         info->scale = P;
-        info->b0 = th[nk];
+        info->b0 = th[c.nc * nk];
         info->reason = hs.reason;
         info->kernel_launches = launches;
         info->precond_used = (opts.precond && hs.pc_ok) ? 1 : 0;
@@ -804,10 +914,18 @@ struct FisherLayout {
     int chunks;
 };
 
-static bool fisher_layout(int H, int W, int ld, int m, FisherLayout &F) {
-    F.base = dia_workspace_size(H, W, ld, m, 0, DIA_MEM_DEVICE);
+static bool fisher_layout(int H, int W, int ld, int m, int kdeg, FisherLayout &F) {
+    dia_pair q;
+    memset(&q, 0, sizeof(q));
+    q.H = H;
+    q.W = W;
+    q.ld = ld;
+    q.m = m;
+    q.mem = DIA_MEM_DEVICE;
+    q.kernel_degree = kdeg;
+    F.base = dia_pair_workspace_size(&q, 0);
     if (F.base == 0) return false;
-    const int h = m / 2, n = m * m + kBgMax;   // any background degree
+    const int h = m / 2, n = n_coef_of(kdeg) * m * m + kBgMax;   // any background degree
     const long long npx = (long long)(H - 2 * h) * (W - 2 * h);
     F.chunks = (int)std::min(64LL, (npx + kGnChunk - 1) / kGnChunk);
     size_t o = align_up(F.base);
@@ -829,7 +947,13 @@ static bool fisher_layout(int H, int W, int ld, int m, FisherLayout &F) {
 
 size_t dia_fisher_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m) {
     FisherLayout F;
-    return fisher_layout(H, W, ld, m, F) ? F.total : 0;
+    return fisher_layout(H, W, ld, m, 0, F) ? F.total : 0;
+}
+
+size_t dia_pair_fisher_workspace_size(const dia_pair *pair) {
+    if (!pair || pair->kernel_degree < 0 || pair->kernel_degree > DIA_MAX_KERNEL_DEGREE) return 0;
+    FisherLayout F;
+    return fisher_layout(pair->H, pair->W, pair->ld, pair->m, pair->kernel_degree, F) ? F.total : 0;
 }
 
 dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
@@ -840,13 +964,15 @@ dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const dou
     FisherLayout FL;
     if (!dims_ok(pair->H, pair->W, pair->ld, pair->m)) return DIA_ERR_ARG;
     if (pair->m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
-    if (!fisher_layout(pair->H, pair->W, pair->ld, pair->m, FL)) return DIA_ERR_ARG;
+    if (pair->kernel_degree < 0 || pair->kernel_degree > DIA_MAX_KERNEL_DEGREE) return DIA_ERR_ARG;
+    if (!fisher_layout(pair->H, pair->W, pair->ld, pair->m, pair->kernel_degree, FL))
+        return DIA_ERR_ARG;
     if (!workspace || workspace_bytes < FL.total) return DIA_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     Ctx c;
     dia_status rc = setup(pair, loss, 0, workspace, FL.base, s, c);
     if (rc != DIA_OK) return rc;
-    const int m = pair->m, n = m * m + c.nb, h = m / 2, np = pc_np(n);
+    const int m = pair->m, n = c.nc * m * m + c.nb, h = m / 2, np = pc_np(n);
     const int Hv = pair->H - 2 * h, Wv = pair->W - 2 * h;
     char *ws = (char *)workspace;
     float *w = (float *)(ws + FL.w);
@@ -854,10 +980,10 @@ dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const dou
     double *res = (double *)(ws + FL.res);
 
     // curvature l''(M_p) at theta: D = I - M from the forward pass, then l''
-    DIA_CK(launch_prep_kpad(theta, m, c.ki.kp, c.nb, c.kpad, s));
+    DIA_CK(launch_prep_kpad(theta, m, c.ki.kp, c.nb, c.kpad, s, c.nc));
     EvalArgs ea = c.ea;
     ea.diff_out = w;
-    DIA_CK(launch_eval(c.ki, kModeForward, ea, c.grid, s));
+    DIA_CK(launch_fwd(c, ea, s));
     DIA_CK(cudaMemsetAsync(res, 0, 3 * sizeof(double), s));
     DIA_CK(launch_fisher_weights(c.ea, w, (unsigned long long *)(res + 2), s));
 
@@ -887,6 +1013,7 @@ dia_status dia_fisher(const dia_pair *pair, const dia_loss_spec *loss, const dou
     pa.st = st;
     pa.eps = 0.0;
     pa.nbg = c.nb;
+    pa.kdeg = c.kdeg;
     pa.eta0 = c.ea.eta0;
     pa.eta_s = c.ea.eta_s;
     pa.xi0 = c.ea.xi0;

@@ -70,6 +70,7 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
         if (p.mem != DIA_MEM_DEVICE) return DIA_ERR_ARG;
         const dia_status rc = check_pair(&p);
         if (rc != DIA_OK) return rc;
+        if (p.kernel_degree != 0) return DIA_ERR_UNSUPPORTED;   // one kernel per pair only
         PairPlan &q = P.pp[i];
         q.m = p.m;
         q.n = p.m * p.m + n_background(p.bg_degree);

@@ -19,6 +19,7 @@ dia_status check_pair(const dia_pair *p) {
     if (!dims_ok(p->H, p->W, p->ld, p->m)) return DIA_ERR_ARG;
     if (p->m > DIA_MAX_M) return DIA_ERR_UNSUPPORTED;
     if (p->bg_degree < 0 || p->bg_degree > DIA_MAX_BG_DEGREE) return DIA_ERR_ARG;
+    if (p->kernel_degree < 0 || p->kernel_degree > DIA_MAX_KERNEL_DEGREE) return DIA_ERR_ARG;
     return DIA_OK;
 }
 

@@ -89,6 +89,7 @@ extern "C" dia_status dia_loss_grad_noalloc(const dia_pair *pair, const dia_loss
     if (pair->mem != DIA_MEM_DEVICE) return DIA_ERR_ARG;
     dia_status rc = check_pair(pair);
     if (rc != DIA_OK) return rc;
+    if (pair->kernel_degree != 0) return DIA_ERR_UNSUPPORTED;   // one kernel per image only
     rc = check_loss(loss, pair);
     if (rc != DIA_OK) return rc;
     const int H = pair->H, W = pair->W, ld = pair->ld, m = pair->m;

@@ -46,36 +46,45 @@ cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, co
     return cudaGetLastError();
 }
 
-// float32 copy of theta for the fused kernel: m rows of kp floats (zero
-// padded), then the nb background coefficients and zeros up to kBgMax + 1.
+// float32 copy of theta for the fused kernels: nc blocks (one per kernel
+// coefficient of a spatially varying kernel, nc = 1 otherwise) of m rows of kp
+// floats (zero padded), then the nb background coefficients and zeros up to
+// kBgMax + 1.
 __device__ __forceinline__ void write_kpad(const double *th, int mk, int kp, int nb, float *Kpad,
-                                           int tid, int nt) {
-    for (int i = tid; i < mk * kp; i += nt) {
-        const int a = i / kp, b = i - a * kp;
-        Kpad[i] = (b < mk) ? (float)th[a * mk + b] : 0.f;
+                                           int tid, int nt, int nc = 1) {
+    const int blk = mk * kp;
+    for (int i = tid; i < nc * blk; i += nt) {
+        const int c = i / blk, r = i - c * blk;
+        const int a = r / kp, b = r - a * kp;
+        Kpad[i] = (b < mk) ? (float)th[(c * mk + a) * mk + b] : 0.f;
     }
-    for (int i = tid; i < kBgMax + 1; i += nt) Kpad[mk * kp + i] = (i < nb) ? (float)th[mk * mk + i] : 0.f;
+    for (int i = tid; i < kBgMax + 1; i += nt)
+        Kpad[nc * blk + i] = (i < nb) ? (float)th[nc * mk * mk + i] : 0.f;
 }
 
-__global__ void prep_kpad_kernel(const double *theta, int mk, int kp, int nb, float *Kpad) {
-    write_kpad(theta, mk, kp, nb, Kpad, threadIdx.x, blockDim.x);
+// kernel coefficient sets of a fit (a spatially varying kernel has several)
+__host__ __device__ inline int n_coef(const StepArgs &a) { return a.nc > 1 ? a.nc : 1; }
+__host__ __device__ inline int n_kpar(const StepArgs &a) { return n_coef(a) * a.mk * a.mk; }
+
+__global__ void prep_kpad_kernel(const double *theta, int mk, int kp, int nb, float *Kpad, int nc) {
+    write_kpad(theta, mk, kp, nb, Kpad, threadIdx.x, blockDim.x, nc);
 }
 
 cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, int nb, float *Kpad,
-                             cudaStream_t s) {
-    prep_kpad_kernel<<<1, 256, 0, s>>>(theta, mk, kp, nb, Kpad);
+                             cudaStream_t s, int nc) {
+    prep_kpad_kernel<<<1, 256, 0, s>>>(theta, mk, kp, nb, Kpad, nc);
     return cudaGetLastError();
 }
 
-__global__ void emit_kernel(const double *red, int mk, int nb, double *loss, double *grad) {
-    const int n = mk * mk + nb;
+__global__ void emit_kernel(const double *red, int nk, int nb, double *loss, double *grad) {
+    const int n = nk + nb;
     for (int k = threadIdx.x; k < n; k += blockDim.x) grad[k] = red[1 + k];
     if (threadIdx.x == 0) *loss = red[0];
 }
 
 cudaError_t launch_emit_loss_grad(const double *red, int mk, int nb, double *loss, double *grad,
-                                  cudaStream_t s) {
-    emit_kernel<<<1, 256, 0, s>>>(red, mk, nb, loss, grad);
+                                  cudaStream_t s, int nc) {
+    emit_kernel<<<1, 256, 0, s>>>(red, nc * mk * mk, nb, loss, grad);
     return cudaGetLastError();
 }
 
@@ -144,7 +153,7 @@ __device__ void set_trial(const StepArgs &a, double alpha) {
     const OptBuffers &b = a.b;
     for (int k = threadIdx.x; k < a.n; k += kStepThreads) b.trial[k] = b.theta[k] + alpha * b.dir[k];
     __syncthreads();
-    write_kpad(b.trial, a.mk, a.kp, a.n - a.mk * a.mk, a.Kpad, threadIdx.x, kStepThreads);
+    write_kpad(b.trial, a.mk, a.kp, a.n - n_kpar(a), a.Kpad, threadIdx.x, kStepThreads, n_coef(a));
 }
 
 constexpr double kNoProgress = 1e-2;   // see finish()
@@ -154,7 +163,8 @@ __device__ void finish(const StepArgs &a, int status, int reason) {
     FitState *st = a.st;
     for (int k = threadIdx.x; k < a.n; k += kStepThreads) a.b.trial[k] = a.b.theta[k];
     __syncthreads();
-    write_kpad(a.b.theta, a.mk, a.kp, a.n - a.mk * a.mk, a.Kpad, threadIdx.x, kStepThreads);
+    write_kpad(a.b.theta, a.mk, a.kp, a.n - n_kpar(a), a.Kpad, threadIdx.x, kStepThreads,
+               n_coef(a));
     if (threadIdx.x == 0) {
         // a pass that stops for lack of progress is at the limit of numerical
         // precision only if max|g| came down by orders of magnitude from the
@@ -212,13 +222,26 @@ __device__ double add_penalty(const StepArgs &a, StepShared &sm) {
 // coefficient b_ij ~ 1/(sum(kappa) E[eta^2i] E[xi^2j]) with eta, xi taken as
 // uniform on [-1/2, 1/2] (E[eta^2i] = 4^-i / (2i + 1)).
 __device__ void update_precond(const StepArgs &a) {
-    const int mk = a.mk, nk = mk * mk, deg = bg_degree_of(a.n - nk);
+    const int mk = a.mk, nk = n_kpar(a), deg = bg_degree_of(a.n - nk);
+    const int kdeg = bg_degree_of(n_coef(a));   // degree of a spatially varying kernel
     const double dk = a.red[red_count(nk) + 1], db = a.red[red_count(nk) + 2];
     const double pk = (dk > 0.0 && isfinite(dk)) ? 1.0 / dk : 1.0;
     const double pb = (db > 0.0 && isfinite(db)) ? 1.0 / db : 1.0;
     const double N = a.red[red_count(nk)];
     for (int k = threadIdx.x; k < a.n; k += kStepThreads) {
         double p = N * ((k >= nk) ? pb : pk);   // the loss is scaled by 1/N
+        if (k < nk && k >= mk * mk) {
+            // coefficient kernel c of a spatially varying kernel: its pixels are
+            // scaled like the background coefficient of the same (i, j)
+            int c = k / (mk * mk), i = 0;
+            while (c > kdeg - i) {
+                c -= kdeg - i + 1;
+                ++i;
+            }
+            const int j = c;
+            p *= (double)(2 * i + 1) * (double)(1 << (2 * i)) * (double)(2 * j + 1) *
+                 (double)(1 << (2 * j));
+        }
         if (k > nk) {
             int c = k - nk, i = 0;
             while (c > deg - i) {   // (i, j) of coefficient c
@@ -451,7 +474,7 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
     const OptParams &p = a.p;
     const int n = a.n, tid = threadIdx.x;
 
-    const double N = a.red[red_count(a.mk * a.mk)];
+    const double N = a.red[red_count(n_kpar(a))];
     if (!(N > 0.0)) {
         finish(a, 6 /* DIA_ERR_DEGENERATE */, kStopDegenerate);
         return;
@@ -496,13 +519,13 @@ __device__ void step_body(const StepArgs &a, StepShared &sm) {
                 const double m2 = p.beta2 * b.m2[k] + (1.0 - p.beta2) * g * g;
                 b.m1[k] = m1;
                 b.m2[k] = m2;
-                const double lr = (k >= a.mk * a.mk) ? p.lr_b0 : p.lr_kernel;
+                const double lr = (k >= n_kpar(a)) ? p.lr_b0 : p.lr_kernel;
                 const double th = b.theta[k] - lr * (m1 / bc1) / (sqrt(m2 / bc2) + p.adam_eps);
                 b.theta[k] = th;
                 b.trial[k] = th;
             }
             __syncthreads();
-            write_kpad(b.trial, a.mk, a.kp, n - a.mk * a.mk, a.Kpad, tid, kStepThreads);
+            write_kpad(b.trial, a.mk, a.kp, n - n_kpar(a), a.Kpad, tid, kStepThreads, n_coef(a));
             if (tid == 0) {
                 st->b1t = b1t;
                 st->b2t = b2t;
@@ -752,8 +775,10 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s) {
 // B0 = median of the unmasked valid target pixels; or theta already in place.
 __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,
                           int mode, double sigma, double median, int degenerate,
-                          int start_phase, double *sh) {
-    const int nk = mk * mk, n = nk + nb, tid = threadIdx.x, h = mk / 2;
+                          int start_phase, double *sh, int nc = 1) {
+    // the constant part K_00 starts as the box-car / Gaussian kernel, the
+    // other coefficient kernels of a spatially varying kernel at zero
+    const int nk = mk * mk, nkt = nc * nk, n = nkt + nb, tid = threadIdx.x, h = mk / 2;
     if (mode == 0 || mode == 1) {
         double w = 0.0;
         for (int k = tid; k < nk; k += kStepThreads) {
@@ -767,8 +792,9 @@ __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int k
         }
         w = block_sum(w, sh);
         for (int k = tid; k < nk; k += kStepThreads) b.theta[k] /= w;
+        for (int k = nk + tid; k < nkt; k += kStepThreads) b.theta[k] = 0.0;
         // B0 = median (Sec. 2.9); a polynomial background starts flat
-        for (int k = nk + tid; k < n; k += kStepThreads) b.theta[k] = (k == nk) ? median : 0.0;
+        for (int k = nkt + tid; k < n; k += kStepThreads) b.theta[k] = (k == nkt) ? median : 0.0;
     }
     __syncthreads();
     for (int k = tid; k < n; k += kStepThreads) {
@@ -777,7 +803,7 @@ __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int k
         b.m2[k] = 0.0;
     }
     __syncthreads();
-    write_kpad(b.theta, mk, kp, nb, Kpad, tid, kStepThreads);
+    write_kpad(b.theta, mk, kp, nb, Kpad, tid, kStepThreads, nc);
     if (tid == 0) {
         FitState z;
         memset(&z, 0, sizeof(z));
@@ -798,27 +824,29 @@ __device__ void init_body(FitState *st, OptBuffers b, float *Kpad, int mk, int k
 }
 
 __global__ void init_kernel(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,
-                            int mode, double sigma, const SelectState *sel, int start_phase) {
+                            int mode, double sigma, const SelectState *sel, int start_phase,
+                            int nc) {
     __shared__ double sh[kStepThreads / 32];
     init_body(st, b, Kpad, mk, kp, nb, mode, sigma, sel ? sel->median : 0.0,
-              sel ? sel->degenerate : 0, start_phase, sh);
+              sel ? sel->degenerate : 0, start_phase, sh, nc);
 }
 
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,
                         int init_mode, double init_sigma, const SelectState *sel,
-                        int start_phase, cudaStream_t s) {
+                        int start_phase, cudaStream_t s, int nc) {
     init_kernel<<<1, kStepThreads, 0, s>>>(st, b, Kpad, mk, kp, nb, init_mode, init_sigma, sel,
-                                           start_phase);
+                                           start_phase, nc);
     return cudaGetLastError();
 }
 
 // Restart the optimiser from the accepted theta (refit after clipping): the
 // next evaluation at theta starts L-BFGS afresh.
-__global__ void restart_kernel(FitState *st, float *Kpad, OptBuffers b, int mk, int kp, int nb) {
-    const int n = mk * mk + nb;
+__global__ void restart_kernel(FitState *st, float *Kpad, OptBuffers b, int mk, int kp, int nb,
+                               int nc) {
+    const int n = nc * mk * mk + nb;
     for (int k = threadIdx.x; k < n; k += blockDim.x) b.trial[k] = b.theta[k];
     __syncthreads();
-    write_kpad(b.theta, mk, kp, nb, Kpad, threadIdx.x, blockDim.x);
+    write_kpad(b.theta, mk, kp, nb, Kpad, threadIdx.x, blockDim.x, nc);
     if (threadIdx.x == 0) {
         st->done = 0;
         st->phase = kPhaseLbfgsStart;
@@ -831,8 +859,8 @@ __global__ void restart_kernel(FitState *st, float *Kpad, OptBuffers b, int mk, 
 }
 
 cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp, int nb,
-                           cudaStream_t s) {
-    restart_kernel<<<1, 256, 0, s>>>(st, Kpad, b, mk, kp, nb);
+                           cudaStream_t s, int nc) {
+    restart_kernel<<<1, 256, 0, s>>>(st, Kpad, b, mk, kp, nb, nc);
     return cudaGetLastError();
 }
 
@@ -1040,19 +1068,21 @@ cudaError_t launch_pack_batch(const StepArgs *args, const long long *theta_off, 
     return cudaGetLastError();
 }
 
+// K_out: the constant kernel (K_00, the kernel at the image centre, for a
+// spatially varying one); b0_out: b_00
 __global__ void pack_kernel(const double *theta, int mk, int nb, double *theta_out, float *K_out,
-                            float *b0_out) {
-    const int nk = mk * mk, n = nk + nb;
+                            float *b0_out, int nc) {
+    const int nk = mk * mk, nkt = nc * nk, n = nkt + nb;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         if (theta_out) theta_out[k] = theta[k];
         if (K_out && k < nk) K_out[k] = (float)theta[k];
     }
-    if (threadIdx.x == 0 && b0_out) *b0_out = (float)theta[nk];
+    if (threadIdx.x == 0 && b0_out) *b0_out = (float)theta[nkt];
 }
 
 cudaError_t launch_pack_outputs(const double *theta, int mk, int nb, double *theta_out,
-                                float *K_out, float *b0_out, cudaStream_t s) {
-    pack_kernel<<<1, 256, 0, s>>>(theta, mk, nb, theta_out, K_out, b0_out);
+                                float *K_out, float *b0_out, cudaStream_t s, int nc) {
+    pack_kernel<<<1, 256, 0, s>>>(theta, mk, nb, theta_out, K_out, b0_out, nc);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,10 @@
 namespace dia {
 
 constexpr int kHistMax = 128;  // largest L-BFGS memory
-constexpr int kPcMaxN = 31 * 31 + kBgMax;   // largest theta (m <= 31, largest background)
+// largest theta of a fit: m <= 31 with the largest background (976), and a
+// spatially varying kernel whose nc m^2 + background coefficients fit
+constexpr int kMaxN = 1024;
+constexpr int kPcMaxN = kMaxN;
 
 enum Phase { kPhaseAdam = 0, kPhaseLbfgs = 1, kPhaseLbfgsStart = 2, kPhaseDone = 3 };
 
@@ -83,6 +86,7 @@ struct StepArgs {
     int n, mk, kp;
     OptParams p;
     int *n_done;         // nullable: incremented once when the fit finishes (batched fits)
+    int nc;              // kernel coefficient sets (a spatially varying kernel; 0 or 1: one)
 };
 
 // Order-preserving map float -> uint32 (for the radix-select median).
@@ -134,6 +138,8 @@ struct PrecondArgs {
     double eps;           // relative diagonal regularisation of H
     double reg2;          // 2 lambda: H += 2 lambda L^T L, the regulariser of Eq. 20 (0 = off)
     int nbg;              // background coefficients (1: the constant B0)
+    int kdeg;             // degree of a spatially varying kernel (0: one kernel); its
+                          // design columns are eta^p xi^q R windows (Eq. 19 coordinates)
     float eta0, eta_s, xi0, xi_s;   // Eq. 19 coordinates of valid-region pixels (EvalArgs)
     double scale;         // H is scaled by this (1 / window pixels for the preconditioner)
     int flush;            // shared-memory batches of 32 px per float64 flush
@@ -149,7 +155,9 @@ constexpr int kGnT = 64;    // block size of the Hessian sum
 constexpr int kGnChunk = 16384;   // pixels per chunk of the Hessian sum
 constexpr int kGnFlushPc = 16;    // 32-px batches per float64 flush for the preconditioner
 __host__ __device__ inline int pc_np(int n) { return (n + kGnT - 1) / kGnT * kGnT; }
-__host__ __device__ inline int pc_n(const PrecondArgs &a) { return a.m * a.m + a.nbg; }
+__host__ __device__ inline int pc_n(const PrecondArgs &a) {
+    return n_background(a.kdeg) * a.m * a.m + a.nbg;
+}
 __host__ __device__ inline int pc_ldp(int n) { return (n + 3) & ~3; }
 __host__ __device__ inline int gn_tiles(int n) { return (n + kGnT - 1) / kGnT; }
 __host__ __device__ inline int gn_blocks(int n) { return gn_tiles(n) * (gn_tiles(n) + 1) / 2; }
@@ -225,10 +233,11 @@ __device__ __forceinline__ void pc_apply_body(const StepArgs &a, int blk, int nb
 cudaError_t launch_reduce(const double *partials, int G, int NP, double *out, const int *done,
                           cudaStream_t s, int acc32 = 0);
 // nb: background coefficients of the pair (1 for the constant B0)
+// nc: kernel coefficient sets (spatially varying kernel), 1 otherwise
 cudaError_t launch_prep_kpad(const double *theta, int mk, int kp, int nb, float *Kpad,
-                             cudaStream_t s);
+                             cudaStream_t s, int nc = 1);
 cudaError_t launch_emit_loss_grad(const double *red, int mk, int nb, double *loss, double *grad,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int nc = 1);
 // One optimiser step: the line-search / history half (one CTA), P g and
 // P y_new (many CTAs), the direction half (one CTA).
 constexpr int kStepLaunches = 3;
@@ -249,21 +258,22 @@ void precond_window(int H, int W, int m, bool single, int side, int *y0, int *y1
 // correlation on tcgen05 (split bf16, float32 accumulators in tensor memory);
 // constant background B0 = Kpad[m * kp].  *status is set to 1 if a bounded wait
 // ran out.
+// wait_cycles: limit of each pipeline wait (0: about one second)
 cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int ld, int m,
                               const float *Kpad, int kp, float *diff_out, int *status,
-                              cudaStream_t s);
+                              cudaStream_t s, long long wait_cycles = 0);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,
                         int init_mode, double init_sigma, const SelectState *sel,
-                        int start_phase, cudaStream_t s);
+                        int start_phase, cudaStream_t s, int nc = 1);
 cudaError_t launch_restart(FitState *st, float *Kpad, OptBuffers b, int mk, int kp, int nb,
-                           cudaStream_t s);
+                           cudaStream_t s, int nc = 1);
 constexpr int kMedianLaunches = 14;   // kernels launch_median enqueues
 cudaError_t launch_median(const float *I, const uint8_t *mask, int H, int W, int ld, int mk,
                           uint32_t *hist, SelectState *sel, int grid, cudaStream_t s);
 cudaError_t launch_pack_outputs(const double *theta, int mk, int nb, double *theta_out,
-                                float *K_out, float *b0_out, cudaStream_t s);
+                                float *K_out, float *b0_out, cudaStream_t s, int nc = 1);
 // batched: one CTA per pair for the two optimiser halves, P v inside the
 // second (kStepLaunchesBatch kernels)
 constexpr int kStepLaunchesBatch = 2;

@@ -98,11 +98,14 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
     __shared__ long long sBase[kGnKB];
     __shared__ float sW[kGnKB];
     __shared__ float sBg[kGnKB][kBgMax];   // background basis eta^i xi^j of each pixel
+    __shared__ float sKb[kGnKB][6];        // basis of a spatially varying kernel (degree <= 2)
+    __shared__ unsigned char cU[kGnT], cV[kGnT];   // coefficient kernel of column u, v
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
-        const int m = a.m, nk = m * m, n = pc_n(a), h = m / 2, ld = a.ld, nt = gn_tiles(n);
-        const int deg = bg_degree_of(a.nbg);
+        const int m = a.m, nk1 = m * m, nk = n_background(a.kdeg) * nk1, n = pc_n(a), h = m / 2,
+                  ld = a.ld, nt = gn_tiles(n);
+        const int deg = bg_degree_of(a.nbg), kdeg = a.kdeg;
         const int wx = a.x1 - a.x0;
         const long long npx = window_px(a);
         const int nch = a.gn_chunks, nblk = gn_blocks(n);
@@ -115,8 +118,16 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
         // -1 - c: background basis function c, kPadCol: padding (zero)
         if (tid < 2 * kGnT) {
             const int u = (tid < kGnT ? U : V) * kGnT + (tid & (kGnT - 1));
-            const int o = u < nk ? (u / m) * ld + u % m : (u < n ? -1 - (u - nk) : kPadCol);
-            if (tid < kGnT) offU[tid] = o; else offV[tid - kGnT] = o;
+            const int uk = u % nk1;   // kernel pixel of a kernel column
+            const int o = u < nk ? (uk / m) * ld + uk % m : (u < n ? -1 - (u - nk) : kPadCol);
+            const unsigned char cc = (unsigned char)(u < nk ? u / nk1 : 0);
+            if (tid < kGnT) {
+                offU[tid] = o;
+                cU[tid] = cc;
+            } else {
+                offV[tid - kGnT] = o;
+                cV[tid - kGnT] = cc;
+            }
         }
         float acc[4][4];
         double acc64[4][4];
@@ -152,6 +163,17 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
                         }
                         ep *= eta;
                     }
+                    // the same basis for the coefficient kernels (degree kdeg)
+                    c = 0;
+                    ep = 1.f;
+                    for (int i = 0; i <= kdeg; ++i) {
+                        float t = ep;
+                        for (int j = 0; j <= kdeg - i; ++j) {
+                            sKb[tid][c++] = t;
+                            t *= xi;
+                        }
+                        ep *= eta;
+                    }
                 } else {
                     sBase[tid] = -1;
                     sW[tid] = 0.f;
@@ -166,6 +188,10 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
                     const int ou = offU[ul], ov = offV[ul];
                     va = ou >= 0 ? a.R[base + ou] : (ou > kPadCol ? sBg[kk][-1 - ou] : 0.f);
                     vb = ov >= 0 ? a.R[base + ov] : (ov > kPadCol ? sBg[kk][-1 - ov] : 0.f);
+                    if (kdeg > 0) {   // column of coefficient kernel c: eta^p xi^q R
+                        if (ou >= 0) va *= sKb[kk][cU[ul]];
+                        if (ov >= 0) vb *= sKb[kk][cV[ul]];
+                    }
                 }
                 sA[kk][ul] = sW[kk] * va;
                 sB[kk][ul] = vb;

@@ -19,10 +19,12 @@
 //     ring (the row loop is unrolled by m so ring slots are compile-time); the
 //     forward sum, g = dl/dM, and the m^2 weight-gradient FMAs of each pixel run
 //     on the same registers (M is never stored, no g tile);
-//   * sums: float32 per lane over one strip (<= 4 S <= 4096 pixels), then a halving
-//     butterfly over the warp and float64 per lane; one CTA-wide float64 sum at
-//     the end gives the same per-CTA partials as the tiled kernel (loss, dK,
-//     dB0, pixel count, curvature sums), reduced by the same fixed-order kernel.
+//   * sums: float32 per lane over one strip (<= 64 rows, <= 256 pixels; for
+//     m <= 3 in two levels, per m-row chunk then per strip), then a float64
+//     halving butterfly over the warp and float64 per lane across strips; one
+//     CTA-wide float64 sum at the end gives the same per-CTA partials as the
+//     tiled kernel (loss, dK, dB0, pixel count, curvature sums), reduced by the
+//     same fixed-order kernel.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -48,51 +50,99 @@ __device__ __forceinline__ void cpa16(void *dst, const void *src, int bytes) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes));
 }
+// the same, issued only where `pred` holds (a predicated instruction, no branch)
+__device__ __forceinline__ void cpa16_if(void *dst, const void *src, int bytes, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+                 "@p cp.async.cg.shared.global [%0], [%1], 16, %2;\n\t}\n"
+                 ::"r"(d), "l"(src), "r"(bytes), "r"((int)pred));
+}
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cpa_wait_depth() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kSDepth - 1));
 }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
+// The halving warp reduction of dia_eval.cuh on float64 values.
+template <int N, int O>
+__device__ __forceinline__ void halve_d(const double *v, double *w, bool up) {
+    constexpr int H = (N + 1) / 2;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const double lo = v[i];
+        const double hi = (i + H < N) ? v[i + H] : 0.0;
+        const double keep = up ? hi : lo;
+        const double send = up ? lo : hi;
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+
 struct SlotLayout {
     int off_I, off_var, off_flat, off_mask, bytes;
 };
 
-// Stage slot t of the strip (R row i0 - h + t; target-side rows of output
-// row i0 + t - 2h when that row lies in the strip) into `slot`.
-template <int MK>
-__device__ __forceinline__ void stage_slot(unsigned char *slot, const SlotLayout &sl,
-                                           const EvalArgs &a, int cb, int i0, int i1, int t,
-                                           int lane) {
+// Per-lane copy plan of one strip (row independent): the R chunk of the
+// lane's own columns (chunk lane + 1 of the slot's 34) and, for lanes 0 and
+// 1, the halo chunks 0 and 33; the target-side chunk (columns cb + 4 lane)
+// and, for lanes 0-7, a 16-byte mask chunk.  Byte counts below 16 zero-fill.
+struct StripCopy {
+    int rx1, rb1;   // R column and bytes of chunk lane + 1
+    int rc2, rx2, rb2;   // chunk index (0 or 33), column and bytes (lanes 0, 1)
+    int ix, ib;     // target-side column and bytes
+    int mx, mb;     // mask column and bytes (lanes 0-7)
+};
+
+__device__ __forceinline__ StripCopy strip_copy(const EvalArgs &a, int cb, int lane) {
+    StripCopy c;
+    c.rx1 = cb + 4 * lane;
+    c.rb1 = (c.rx1 < a.W) ? ((a.W - c.rx1 >= 4) ? 16 : 4 * (a.W - c.rx1)) : 0;
+    if (c.rb1 == 0) c.rx1 = 0;
+    c.rc2 = lane == 0 ? 0 : 33;
+    c.rx2 = cb - 4 + 4 * c.rc2;
+    c.rb2 = (lane < 2 && c.rx2 >= 0 && c.rx2 < a.W) ? ((a.W - c.rx2 >= 4) ? 16 : 4 * (a.W - c.rx2)) : 0;
+    if (c.rb2 == 0) c.rx2 = 0;
+    c.ix = c.rx1;
+    c.ib = c.rb1;
+    c.mx = cb + 16 * lane;
+    c.mb = (lane < 8 && c.mx < a.W) ? ((a.W - c.mx >= 16) ? 16 : (a.W - c.mx)) : 0;
+    if (c.mb == 0) c.mx = 0;
+    return c;
+}
+
+// Running source pointers of one strip's staging: the next R row to stage
+// (chunk lane + 1 and the halo chunk of lanes 0, 1) and the next target-side
+// row (advanced by one row pitch per staged slot).
+struct StripPtr {
+    const float *r1, *r2, *ti, *tv, *tf;
+    const uint8_t *tm;
+};
+
+// Stage the next slot (R row i0 - h + t, and the target-side rows of output
+// row i0 + t - 2h once t >= 2h) into `slot` and advance the pointers.
+template <int MK, int FAST>
+__device__ __forceinline__ void stage_next(unsigned char *slot, const SlotLayout &sl,
+                                           const StripCopy &cp, StripPtr &sp, size_t ld, int t,
+                                           int lane, bool hv, bool hf, bool hm) {
     constexpr int h = MK / 2;
-    const int rr = i0 - h + t;                 // R row (in [0, H) while t < i1 - i0 + 2h)
-    const int io = i0 + t - 2 * h;             // output row of the target-side rows
-    if (rr >= i1 + h) return;                  // past the strip: nothing to stage
     float *Rs = reinterpret_cast<float *>(slot);
-    // R: 34 chunks of 4 floats from column cb - 4
-    for (int c = lane; c < 34; c += 32) {
-        const int gx = cb - 4 + 4 * c;
-        int bytes = 0;
-        const float *src = a.R;
-        if (gx >= 0 && gx < a.W) {
-            bytes = (a.W - gx >= 4) ? 16 : 4 * (a.W - gx);
-            src = a.R + (size_t)rr * a.ld + gx;
-        }
-        cpa16(Rs + 4 * c, src, bytes);
+    cpa16(Rs + 4 * (lane + 1), sp.r1, cp.rb1);
+    cpa16_if(Rs + 4 * cp.rc2, sp.r2, cp.rb2, lane < 2);
+    sp.r1 += ld;
+    sp.r2 += ld;
+    if (t < 2 * h) return;                              // no output row yet
+    cpa16(slot + sl.off_I + 16 * lane, sp.ti, cp.ib);
+    sp.ti += ld;
+    if (!FAST && hv) {
+        cpa16(slot + sl.off_var + 16 * lane, sp.tv, cp.ib);
+        sp.tv += ld;
     }
-    if (io < i0) return;
-    const int gx = cb + 4 * lane;
-    const bool in = gx < a.W;
-    const int bytes = in ? ((a.W - gx >= 4) ? 16 : 4 * (a.W - gx)) : 0;
-    const size_t off = (size_t)io * a.ld + (in ? gx : 0);
-    cpa16(slot + sl.off_I + 16 * lane, a.I + off, bytes);
-    if (a.var) cpa16(slot + sl.off_var + 16 * lane, a.var + off, bytes);
-    if (a.flat) cpa16(slot + sl.off_flat + 16 * lane, a.flat + off, bytes);
-    if (a.mask && lane < 8) {
-        const int mx = cb + 16 * lane;
-        const bool min_ = mx < a.W;
-        const int mb = min_ ? ((a.W - mx >= 16) ? 16 : (a.W - mx)) : 0;
-        cpa16(slot + sl.off_mask + 16 * lane, a.mask + (size_t)io * a.ld + (min_ ? mx : 0), mb);
+    if (!FAST && hf) {
+        cpa16(slot + sl.off_flat + 16 * lane, sp.tf, cp.ib);
+        sp.tf += ld;
+    }
+    if (hm) {
+        cpa16_if(slot + sl.off_mask + 16 * lane, sp.tm, cp.mb, lane < 8);
+        sp.tm += ld;
     }
 }
 
@@ -116,12 +166,55 @@ __device__ __forceinline__ void read_window(const float *Rs, int lane, float (&w
     }
 }
 
-template <int MK>
-__global__ void __launch_bounds__(kSNT, 2) eval_small_kernel(const EvalArgs a, const SmallGeom g) {
+// Pixel terms with a fixed scalar variance: 1/v and its square root are the
+// same for every pixel, so they are formed once per thread (the same float32
+// operations as pixel_loss, hoisted: identical results).
+__device__ __forceinline__ float pixel_loss_scalar(const LossParams &lp, float inv_v, float inv_s,
+                                                   float I, float M, float &g, float &kappa) {
+    const float r = I - M;
+    const float z = r * inv_s;
+    const float dz = -inv_s;
+    float rho, rho1, wz;
+    if (lp.rho == 0) {
+        rho = 0.5f * z * z;
+        rho1 = z;
+        wz = 1.f;
+    } else if (lp.rho == 1) {
+        const float c = lp.huber_c, az = fabsf(z);
+        if (az <= c) {
+            rho = 0.5f * z * z;
+            rho1 = z;
+            wz = 1.f;
+        } else {
+            rho = c * (az - 0.5f * c);
+            rho1 = copysignf(c, z);
+            wz = c / az;
+        }
+    } else {
+        const float q = z * z;
+        rho = log1pf(q);
+        wz = 2.0f / (1.0f + q);
+        rho1 = z * wz;
+    }
+    g = rho1 * dz;
+    kappa = wz * inv_v;
+    return rho;
+}
+
+// FAST = 1: the Gaussian loss with a fixed scalar variance (the chi^2 of the
+// memory-bound workloads): a branch-free epilogue with the mask folded into a
+// per-pixel weight w in {0, 1}: z = (I - M)/s, sum w z^2 (loss = half of it),
+// g = -w z / s, count, and sum w R^2 (the curvature sums are 1/v times
+// these).  FAST = 0: any loss and variance model through pixel_loss.
+// HM: a mask is given.
+template <int MK, int FAST, int HM>
+__global__ void __launch_bounds__(kSNT, MK <= 1 ? 3 : 2) eval_small_kernel(const EvalArgs a,
+                                                                          const SmallGeom g) {
     if (a.done_flag != nullptr && *((volatile const int *)a.done_flag) != 0) return;
     constexpr int h = MK / 2, NWIN = 4 + 2 * h, NK = MK * MK;
     // per-lane float32 sums: dK (NK), then loss, dB0, count, kR^2, kappa
     constexpr int NS = NK + 5, NF = Halving<NS>::H5;
+    constexpr bool KREG = MK <= 3;   // kernel taps in registers (else shared memory)
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     SlotLayout sl;
@@ -141,6 +234,11 @@ __global__ void __launch_bounds__(kSNT, 2) eval_small_kernel(const EvalArgs a, c
     }
     const float B0 = a.Kpad[MK * g.kp];
     __syncthreads();
+    float kreg[KREG ? NK : 1];
+    if constexpr (KREG) {
+#pragma unroll
+        for (int i = 0; i < NK; ++i) kreg[i] = Ks[(i / MK) * 8 + i % MK];
+    }
 
     int kidx[NF];
 #pragma unroll
@@ -149,24 +247,55 @@ __global__ void __launch_bounds__(kSNT, 2) eval_small_kernel(const EvalArgs a, c
 #pragma unroll
     for (int j = 0; j < NF; ++j) acc[j] = 0.0;
 
+    // a fixed scalar variance: its reciprocal and root once per thread
+    const bool scalar_var = a.lp.var_model == 0 && a.var == nullptr;
+    const float sv_inv_v = 1.0f / a.lp.var_scalar;
+    const float sv_inv_s = sqrtf(sv_inv_v);
+
     const int gw = blockIdx.x * kSW + warp, tw = gridDim.x * kSW;
     for (int s = gw; s < g.n_strips; s += tw) {
         const int cb = (s % g.col_blocks) * kSColBlock;
         const int i0 = h + (s / g.col_blocks) * g.band_rows;
         const int i1 = min(i0 + g.band_rows, a.H - h);
         const int T = (i1 - i0) + 2 * h;     // slots of this strip
-        // columns of this lane in the valid region
-        const int j0 = cb + 4 * lane;
-        float s32[NS];
+        const StripCopy cp = strip_copy(a, cb, lane);
+        const size_t ld = (size_t)a.ld;
+        StripPtr sp;
+        sp.r1 = a.R + (size_t)(i0 - h) * ld + cp.rx1;
+        sp.r2 = a.R + (size_t)(i0 - h) * ld + cp.rx2;
+        sp.ti = a.I + (size_t)i0 * ld + cp.ix;
+        sp.tv = a.var ? a.var + (size_t)i0 * ld + cp.ix : nullptr;
+        sp.tf = a.flat ? a.flat + (size_t)i0 * ld + cp.ix : nullptr;
+        sp.tm = HM ? a.mask + (size_t)i0 * ld + cp.mx : nullptr;
+        const bool hv = a.var != nullptr, hf = a.flat != nullptr;
+        // valid-region columns of this lane's four pixels (1) or not (0)
+        float vcol[4];
 #pragma unroll
-        for (int k = 0; k < NS; ++k) s32[k] = 0.f;
+        for (int p = 0; p < 4; ++p) {
+            const int j = cb + 4 * lane + p;
+            vcol[p] = (j >= h && j < a.W - h) ? 1.f : 0.f;
+        }
+        // float32 sums over the strip (<= 64 rows): dK first, then loss, dB0,
+        // count, kR^2, kappa; for m <= 3 two-level (`in` over one chunk of MK
+        // rows, then `out`), for m = 5 directly into `out` (registers)
+        constexpr bool TWO = MK <= 3;
+        float out[NS], inb[TWO ? NS : 1];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) out[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < (TWO ? NS : 1); ++k) inb[k] = 0.f;
+        float *const in = TWO ? inb : out;
 
         __syncwarp();   // the previous strip's last reads of the ring are done
+        unsigned char *slot_st = ring;   // next slot to fill
 #pragma unroll 1
         for (int t = 0; t < kSDepth; ++t) {
-            if (t < T) stage_slot<MK>(ring + t * sl.bytes, sl, a, cb, i0, i1, t, lane);
+            if (t < T) stage_next<MK, FAST>(slot_st, sl, cp, sp, ld, t, lane, hv, hf, HM);
             cpa_commit();
+            slot_st += sl.bytes;
         }
+        unsigned char *slot = ring;      // slot of row t (refilled with row t + D)
+        unsigned char *const ring_end = ring + kSDepth * sl.bytes;
         float win[MK][NWIN];
 #pragma unroll
         for (int r = 0; r < MK; ++r)
@@ -181,7 +310,6 @@ __global__ void __launch_bounds__(kSNT, 2) eval_small_kernel(const EvalArgs a, c
                 if (t < T) {
                     cpa_wait_depth();
                     __syncwarp();
-                    unsigned char *slot = ring + (t % kSDepth) * sl.bytes;
                     read_window<MK>(reinterpret_cast<const float *>(slot), lane, win[u]);
                     float Iv[4], Vv[4], Fv[4];
                     uint32_t mk4 = 0xffffffffu;
@@ -189,25 +317,26 @@ __global__ void __launch_bounds__(kSNT, 2) eval_small_kernel(const EvalArgs a, c
                     if (row_out) {
                         const float4 i4 = *reinterpret_cast<const float4 *>(slot + sl.off_I + 16 * lane);
                         Iv[0] = i4.x; Iv[1] = i4.y; Iv[2] = i4.z; Iv[3] = i4.w;
-                        if (a.var) {
+                        if (!FAST && hv) {
                             const float4 v4 = *reinterpret_cast<const float4 *>(slot + sl.off_var + 16 * lane);
                             Vv[0] = v4.x; Vv[1] = v4.y; Vv[2] = v4.z; Vv[3] = v4.w;
                         }
-                        if (a.flat) {
+                        if (!FAST && hf) {
                             const float4 f4 = *reinterpret_cast<const float4 *>(slot + sl.off_flat + 16 * lane);
                             Fv[0] = f4.x; Fv[1] = f4.y; Fv[2] = f4.z; Fv[3] = f4.w;
                         }
-                        if (a.mask) mk4 = *reinterpret_cast<const uint32_t *>(slot + sl.off_mask + 4 * lane);
+                        if (HM) mk4 = *reinterpret_cast<const uint32_t *>(slot + sl.off_mask + 4 * lane);
                     }
                     __syncwarp();   // every lane has read slot t
-                    if (t + kSDepth < T)
-                        stage_slot<MK>(slot, sl, a, cb, i0, i1, t + kSDepth, lane);
+                    if (t + kSDepth < T) stage_next<MK, FAST>(slot, sl, cp, sp, ld, t + kSDepth, lane, hv, hf, HM);
                     cpa_commit();
+                    slot += sl.bytes;
+                    if (slot == ring_end) slot = ring;
                     if (row_out) {
                         // window rows a = 0..MK-1 of this output row sit in ring
-                        // slots (u + 1 + a) % MK (the newest row in slot u)
-                        // two partial sums per pixel (even / odd kernel rows)
-                        // so the forward has eight independent FMA chains
+                        // slots (u + 1 + a) % MK (the newest row in slot u); for
+                        // m = 5 two partial sums per pixel (even / odd kernel
+                        // rows) give eight independent FMA chains
                         float M[4], M2[4];
 #pragma unroll
                         for (int p = 0; p < 4; ++p) {
@@ -218,43 +347,60 @@ __global__ void __launch_bounds__(kSNT, 2) eval_small_kernel(const EvalArgs a, c
                         for (int aa = 0; aa < MK; ++aa) {
                             const int rs = (u + 1 + aa) % MK;
                             float kk[8];
-                            const float4 k0 = *reinterpret_cast<const float4 *>(Ks + 8 * aa);
-                            kk[0] = k0.x; kk[1] = k0.y; kk[2] = k0.z; kk[3] = k0.w;
-                            if (MK > 4) {
+                            if constexpr (KREG) {
+#pragma unroll
+                                for (int b = 0; b < MK; ++b) kk[b] = kreg[aa * MK + b];
+                            } else {
+                                const float4 k0 = *reinterpret_cast<const float4 *>(Ks + 8 * aa);
                                 const float4 k1 = *reinterpret_cast<const float4 *>(Ks + 8 * aa + 4);
+                                kk[0] = k0.x; kk[1] = k0.y; kk[2] = k0.z; kk[3] = k0.w;
                                 kk[4] = k1.x; kk[5] = k1.y; kk[6] = k1.z; kk[7] = k1.w;
                             }
 #pragma unroll
                             for (int b = 0; b < MK; ++b)
 #pragma unroll
                                 for (int p = 0; p < 4; ++p) {
-                                    if (aa & 1)
+                                    if (MK > 3 && (aa & 1))
                                         M2[p] = fmaf(kk[b], win[rs][p + b], M2[p]);
                                     else
                                         M[p] = fmaf(kk[b], win[rs][p + b], M[p]);
                                 }
                         }
+                        if (MK > 3) {
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) M[p] += M2[p];
+                            for (int p = 0; p < 4; ++p) M[p] += M2[p];
+                        }
                         float gp[4];
 #pragma unroll
                         for (int p = 0; p < 4; ++p) {
-                            const int j = j0 + p;
-                            const bool use = j >= h && j < a.W - h && ((mk4 >> (8 * p)) & 0xffu) != 0;
-                            float gv = 0.f;
-                            if (use) {
-                                float z, kap;
-                                const float ell = pixel_loss(a.lp, Iv[p], M[p],
-                                                             a.var ? Vv[p] : a.lp.var_scalar,
-                                                             a.flat ? Fv[p] : 1.0f, gv, z, kap);
-                                const float rc = win[(u + 1 + h) % MK][p + h];
-                                s32[NK] += ell;
-                                s32[NK + 1] += gv;
-                                s32[NK + 2] += 1.f;
-                                s32[NK + 3] = fmaf(kap * rc, rc, s32[NK + 3]);
-                                s32[NK + 4] += kap;
+                            const float rc = win[(u + 1 + h) % MK][p + h];
+                            float w = vcol[p];
+                            if (HM) w = ((mk4 >> (8 * p)) & 0xffu) ? w : 0.f;
+                            if constexpr (FAST != 0) {
+                                const float z = (Iv[p] - M[p]) * sv_inv_s;
+                                const float zw = z * w;
+                                in[NK] = fmaf(zw, z, in[NK]);
+                                gp[p] = zw * -sv_inv_s;
+                                in[NK + 1] += gp[p];
+                                in[NK + 2] += w;
+                                in[NK + 3] = fmaf(w * rc, rc, in[NK + 3]);
+                            } else {
+                                float gv = 0.f;
+                                if (w != 0.f) {
+                                    float z, kap;
+                                    const float ell =
+                                        scalar_var
+                                            ? pixel_loss_scalar(a.lp, sv_inv_v, sv_inv_s, Iv[p], M[p], gv, kap)
+                                            : pixel_loss(a.lp, Iv[p], M[p], hv ? Vv[p] : a.lp.var_scalar,
+                                                         hf ? Fv[p] : 1.0f, gv, z, kap);
+                                    in[NK] += ell;
+                                    in[NK + 1] += gv;
+                                    in[NK + 2] += 1.f;
+                                    in[NK + 3] = fmaf(kap * rc, rc, in[NK + 3]);
+                                    in[NK + 4] += kap;
+                                }
+                                gp[p] = gv;
                             }
-                            gp[p] = gv;
                         }
 #pragma unroll
                         for (int aa = 0; aa < MK; ++aa) {
@@ -263,24 +409,41 @@ __global__ void __launch_bounds__(kSNT, 2) eval_small_kernel(const EvalArgs a, c
                             for (int b = 0; b < MK; ++b)
 #pragma unroll
                                 for (int p = 0; p < 4; ++p)
-                                    s32[aa * MK + b] = fmaf(gp[p], win[rs][p + b], s32[aa * MK + b]);
+                                    in[aa * MK + b] = fmaf(gp[p], win[rs][p + b], in[aa * MK + b]);
                         }
                     }
                 }
             }
+            // end of a chunk of MK rows: into the strip sums
+            if constexpr (TWO) {
+#pragma unroll
+                for (int k = 0; k < NS; ++k) {
+                    out[k] += inb[k];
+                    inb[k] = 0.f;
+                }
+            }
         }
         cpa_wait_all();
-        // warp sums of this strip, float64 per lane
+        // warp sums of this strip in float64 (halving butterfly), per lane
         {
-            using Hv = Halving<NS>;
-            float w1[Hv::H1], w2[Hv::H2], w3[Hv::H3], w4[Hv::H4], w5[Hv::H5];
-            halve<NS, 16>(s32, w1, lane & 16);
-            halve<Hv::H1, 8>(w1, w2, lane & 8);
-            halve<Hv::H2, 4>(w2, w3, lane & 4);
-            halve<Hv::H3, 2>(w3, w4, lane & 2);
-            halve<Hv::H4, 1>(w4, w5, lane & 1);
+            if constexpr (FAST != 0) {
+                // loss = sum w z^2 / 2; curvature weight 1/v per used pixel
+                out[NK] *= 0.5f;
+                out[NK + 3] *= sv_inv_v;
+                out[NK + 4] = out[NK + 2] * sv_inv_v;
+            }
+            double d0[NS];
 #pragma unroll
-            for (int j = 0; j < NF; ++j) acc[j] += (double)w5[j];
+            for (int k = 0; k < NS; ++k) d0[k] = (double)out[k];
+            using Hv = Halving<NS>;
+            double w1[Hv::H1], w2[Hv::H2], w3[Hv::H3], w4[Hv::H4], w5[Hv::H5];
+            halve_d<NS, 16>(d0, w1, lane & 16);
+            halve_d<Hv::H1, 8>(w1, w2, lane & 8);
+            halve_d<Hv::H2, 4>(w2, w3, lane & 4);
+            halve_d<Hv::H3, 2>(w3, w4, lane & 2);
+            halve_d<Hv::H4, 1>(w4, w5, lane & 1);
+#pragma unroll
+            for (int j = 0; j < NF; ++j) acc[j] += w5[j];
         }
     }
 
@@ -311,8 +474,16 @@ __global__ void __launch_bounds__(kSNT, 2) eval_small_kernel(const EvalArgs a, c
 }
 
 template <int MK>
-const void *small_fn() {
-    return (const void *)&eval_small_kernel<MK>;
+const void *small_fn(int fast, int hm) {
+    if (fast) return hm ? (const void *)&eval_small_kernel<MK, 1, 1> : (const void *)&eval_small_kernel<MK, 1, 0>;
+    return hm ? (const void *)&eval_small_kernel<MK, 0, 1> : (const void *)&eval_small_kernel<MK, 0, 0>;
+}
+
+// the kernel instance for these arguments
+const void *small_pick(const EvalArgs &a, int mk) {
+    const int fast = a.lp.rho == 0 && a.lp.var_model == 0 && a.var == nullptr;
+    const int hm = a.mask != nullptr;
+    return mk == 1 ? small_fn<1>(fast, hm) : mk == 3 ? small_fn<3>(fast, hm) : small_fn<5>(fast, hm);
 }
 
 }  // namespace
@@ -335,7 +506,7 @@ int small_kernel_smem(const EvalArgs &a) {
 }
 
 cudaError_t small_kernel_prepare(const EvalArgs &a, int mk, int *occ) {
-    const void *fn = mk == 1 ? small_fn<1>() : mk == 3 ? small_fn<3>() : small_fn<5>();
+    const void *fn = small_pick(a, mk);
     const int smem = small_kernel_smem(a);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -351,8 +522,8 @@ SmallGeom small_geometry(const EvalArgs &a, int mk, int kp, int np, int grid) {
     const long long warps = (long long)grid * kSW;
     long long bands = warps / g.col_blocks;
     if (bands < 1) bands = 1;
-    // at most 1024 rows per strip: each lane's float32 sums cover <= 4096 px
-    if (bands < (Hv + 1023) / 1024) bands = (Hv + 1023) / 1024;
+    // at most 64 rows per strip: each lane's float32 sums cover <= 256 px
+    if (bands < (Hv + 63) / 64) bands = (Hv + 63) / 64;
     if (bands > Hv) bands = Hv;
     g.band_rows = (int)((Hv + bands - 1) / bands);
     const int nb = (Hv + g.band_rows - 1) / g.band_rows;
@@ -364,7 +535,7 @@ cudaError_t launch_eval_small(const EvalArgs &a, int mk, int kp, int np, int gri
                               cudaStream_t s) {
     const SmallGeom g = small_geometry(a, mk, kp, np, grid);
     const int smem = small_kernel_smem(a);
-    const void *fn = mk == 1 ? small_fn<1>() : mk == 3 ? small_fn<3>() : small_fn<5>();
+    const void *fn = small_pick(a, mk);
     void *params[] = {(void *)&a, (void *)&g};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kSNT), params, smem, s);
 }

@@ -106,9 +106,12 @@ __device__ __forceinline__ void tc_commit(uint64_t *b) {
                  :: "r"(su32(b)));
 }
 
-// Wait for the phase with parity `ph`; false after kTcWaitCycles or once the
-// other role has aborted (*other != 0).
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t ph, const int *other) {
+// Wait for the phase with parity `ph`; false after `limit` SM clock cycles or
+// once the other role has aborted (*other != 0).  Pipeline waits take the
+// launch's limit (TcArgs::wait_cycles); the drains before the CTA exits
+// (copies or MMAs still in flight) always take kTcWaitCycles.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t ph, const int *other,
+                                        long long limit = kTcWaitCycles) {
     const long long t0 = clock64();
     const volatile int *ab = other;
     for (;;) {
@@ -116,7 +119,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t ph, const int *o
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(su32(bar)), "r"(ph));
         if (done) return true;
-        if (*ab != 0 || clock64() - t0 > kTcWaitCycles) return false;
+        if (*ab != 0 || clock64() - t0 > limit) return false;
     }
 }
 
@@ -172,6 +175,7 @@ struct TcArgs {
     float *diff_out;     // (Hv x Wv) D = I - M
     int *status;         // set to 1 if a wait ran out
     int use_tma;         // 1: the window by TMA through `tmap`
+    long long wait_cycles;   // limit of each pipeline wait (SM clock cycles)
 };
 
 constexpr uint32_t kTcWindowBytes = kTcYT * kTcXT * 4;
@@ -239,11 +243,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int k = 0;
             for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++k) {
                 const int buf = k & 1;
-                if (!tc_wait(&S.tfull[buf], (uint32_t)((k >> 1) & 1), &S.prod_abort) ||
-                    (k >= 2 &&
-                     !tc_wait(&S.aempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.prod_abort))) {
+                if (!tc_wait(&S.tfull[buf], (uint32_t)((k >> 1) & 1), &S.prod_abort,
+                             a.wait_cycles) ||
+                    (k >= 2 && !tc_wait(&S.aempty[buf], (uint32_t)(((k - 2) >> 1) & 1),
+                                        &S.prod_abort, a.wait_cycles))) {
                     *reinterpret_cast<volatile int *>(&S.mma_abort) = 1;
                     atomicExch(a.status, 1);
+                    // the MMAs already issued (tiles < k) must finish before the
+                    // tensor memory is released: their last commit arrives on
+                    // afull of tile k - 1 (waited with the long limit)
+                    if (k > 0) {
+                        const int never = 0;
+                        tc_wait(&S.afull[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), &never);
+                    }
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
@@ -268,7 +280,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // returns false if the accumulators did not arrive
         auto epilogue = [&](int kk, int tile) {
             const int buf = kk & 1;
-            bool ok = tc_wait(&S.afull[buf], (uint32_t)((kk >> 1) & 1), &S.mma_abort);
+            bool ok = tc_wait(&S.afull[buf], (uint32_t)((kk >> 1) & 1), &S.mma_abort,
+                              a.wait_cycles);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -325,11 +338,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // the window has landed (TMA: the transaction count of wfull; cp.async:
             // each thread's own copies, then everyone's at the barrier)
             if (a.use_tma)
-                fail = fail || !tc_wait(&S.wfull, (uint32_t)(k & 1), &S.mma_abort);
+                fail = fail || !tc_wait(&S.wfull, (uint32_t)(k & 1), &S.mma_abort, a.wait_cycles);
             else
                 cp_async_wait<0>();
             if (k >= 2 && !fail)
-                fail = !tc_wait(&S.tempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.mma_abort);
+                fail = !tc_wait(&S.tempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.mma_abort,
+                                a.wait_cycles);
             if (producers_any(fail)) {
                 fail = true;
                 break;
@@ -404,7 +418,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int ld, int m,
                               const float *Kpad, int kp, float *diff_out, int *status,
-                              cudaStream_t s) {
+                              cudaStream_t s, long long wait_cycles) {
     if (m < 1 || m > kTcMaxM || (m & 1) == 0) return cudaErrorInvalidValue;
     // 2-D tiled map of R (x innermost): 160 x 64 float boxes, zero fill outside;
     // needs a 16-byte aligned base and row pitch; images smaller than one box
@@ -440,6 +454,7 @@ cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int 
     a.diff_out = diff_out;
     a.status = status;
     a.use_tma = use_tma;
+    a.wait_cycles = wait_cycles > 0 ? wait_cycles : kTcWaitCycles;
     int dev = 0, sms = 1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;

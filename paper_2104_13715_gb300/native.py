@@ -35,7 +35,8 @@ class Pair(ctypes.Structure):
     _fields_ = [("ref", ctypes.c_void_p), ("img", ctypes.c_void_p), ("mask", ctypes.c_void_p),
                 ("var", ctypes.c_void_p), ("flat", ctypes.c_void_p),
                 ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("ld", ctypes.c_int32),
-                ("m", ctypes.c_int32), ("mem", ctypes.c_int32), ("bg_degree", ctypes.c_int32)]
+                ("m", ctypes.c_int32), ("mem", ctypes.c_int32), ("bg_degree", ctypes.c_int32),
+                ("kernel_degree", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):
@@ -102,6 +103,9 @@ _SIGS = {
     "dia_fisher_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 4),
     "dia_set_accumulation": (ctypes.c_int32, [ctypes.c_int32]),
     "dia_set_small_kernel": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_set_tc_wait_cycles": (ctypes.c_int32, [ctypes.c_int64]),
+    "dia_pair_workspace_size": (ctypes.c_size_t, [_P(Pair), ctypes.c_int32]),
+    "dia_pair_fisher_workspace_size": (ctypes.c_size_t, [_P(Pair)]),
     "dia_time_eval": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_float), ctypes.c_void_p,
@@ -121,7 +125,7 @@ _SIGS = {
 }
 
 
-ABI_VERSION = 3   # the struct layouts below match include/dia.h of this version
+ABI_VERSION = 4   # the struct layouts below match include/dia.h of this version
 
 
 def _load():
@@ -230,13 +234,15 @@ def _img(t, H, W, name, dtype=torch.float32):
     return t
 
 
-def n_params(m, bg_degree=0):
-    """Entries of theta: m*m kernel pixels and (d+1)(d+2)/2 background
+def n_params(m, bg_degree=0, kernel_degree=0):
+    """Entries of theta: (dk+1)(dk+2)/2 kernels of m*m pixels (one unless the
+    kernel varies over the image with degree dk) and (d+1)(d+2)/2 background
     coefficients (Eq. 18; 1 = the constant B0)."""
-    return m * m + (bg_degree + 1) * (bg_degree + 2) // 2
+    return (kernel_degree + 1) * (kernel_degree + 2) // 2 * m * m + \
+        (bg_degree + 1) * (bg_degree + 2) // 2
 
 
-def make_pair(R, I, m, mask=None, var=None, flat=None, bg_degree=0):
+def make_pair(R, I, m, mask=None, var=None, flat=None, bg_degree=0, kernel_degree=0):
     """dia_pair over torch tensors (all on one CUDA device, or all on the host
     in pinned or pageable memory).  Returns (pair, keep-alive list)."""
     H, W = R.shape
@@ -256,7 +262,7 @@ def make_pair(R, I, m, mask=None, var=None, flat=None, bg_degree=0):
     p = Pair(R.data_ptr(), I.data_ptr(), mask.data_ptr() if mask is not None else None,
              var.data_ptr() if var is not None else None,
              flat.data_ptr() if flat is not None else None, H, W, ld, m,
-             MEM_HOST if host else MEM_DEVICE, bg_degree)
+             MEM_HOST if host else MEM_DEVICE, bg_degree, kernel_degree)
     return p, [R, I, mask, var, flat]
 
 
@@ -273,17 +279,26 @@ def workspace(H, W, m, ld=None, clip=False, host=False, device=None) -> torch.Te
     return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
 
 
+def pair_workspace(pair, clip=False, device=None) -> torch.Tensor:
+    """Workspace for this dia_pair (dia_pair_workspace_size: any kernel degree)."""
+    n = lib.dia_pair_workspace_size(ctypes.byref(pair), int(bool(clip)))
+    if n == 0:
+        raise DiaError(DIA_ERR_ARG, "dia_pair_workspace_size")
+    return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+
 def loss_grad(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, ws=None,
-              stream=None, bg_degree=0):
-    """One fused evaluation on the device: returns (loss[1], grad[n]) float64 tensors."""
-    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
+              stream=None, bg_degree=0, kernel_degree=0):
+    """One fused evaluation on the device: returns (loss[1], grad[n]) float64 tensors.
+    ``kernel_degree`` > 0: a spatially varying kernel of that degree."""
+    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree, kernel_degree)
     if not R.is_cuda:
         raise ValueError("loss_grad takes device tensors")
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
-    n = n_params(m, bg_degree)
+    n = n_params(m, bg_degree, kernel_degree)
     if theta.numel() != n:
         raise ValueError(f"theta must have {n} entries")
-    ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
+    ws = ws if ws is not None else pair_workspace(pair, device=R.device)
     loss = torch.empty(1, dtype=torch.float64, device=R.device)
     grad = torch.empty(n, dtype=torch.float64, device=R.device)
     st = lib.dia_loss_grad(ctypes.byref(pair), ctypes.byref(spec), _ptr(theta), _ptr(loss),
@@ -296,7 +311,7 @@ def time_eval(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, re
               flush=None, ws=None, stream=None, bg_degree=0) -> float:
     """dia_time_eval: mean device milliseconds of the fused evaluation kernel
     alone over `reps` launches (CUDA events on the stream), each after
-    overwriting the uint8 device tensor `flush` (if given) to evict L2."""
+    reading the uint8 device tensor `flush` (if given) through L2 to evict it."""
     pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
     ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
@@ -309,17 +324,17 @@ def time_eval(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, re
 
 
 def fisher(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, want_F=True,
-           want_cov=True, stream=None, bg_degree=0):
+           want_cov=True, stream=None, bg_degree=0, kernel_degree=0):
     """dia_fisher: observed Fisher information F (the Hessian of the loss at
     theta, Sec. 2.5) and the covariance estimate F^-1.  Returns dict(F, cov,
     info) with n x n float64 device tensors (None where not asked for; cov is
     NaN when F is not positive definite)."""
-    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
+    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree, kernel_degree)
     if not R.is_cuda:
         raise ValueError("fisher takes device tensors")
-    n = n_params(m, bg_degree)
+    n = n_params(m, bg_degree, kernel_degree)
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
-    nb = lib.dia_fisher_workspace_size(R.shape[0], R.shape[1], R.stride(0), m)
+    nb = lib.dia_pair_fisher_workspace_size(ctypes.byref(pair))
     if nb == 0:
         raise DiaError(DIA_ERR_ARG, "dia_fisher_workspace_size")
     ws = torch.empty(nb, dtype=torch.uint8, device=R.device)
@@ -352,10 +367,10 @@ def loss_grad_noalloc(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=
     return loss, grad
 
 
-def diff_image(R, I, m, theta, ws=None, stream=None, bg_degree=0):
-    pair, keep = make_pair(R, I, m, bg_degree=bg_degree)
+def diff_image(R, I, m, theta, ws=None, stream=None, bg_degree=0, kernel_degree=0):
+    pair, keep = make_pair(R, I, m, bg_degree=bg_degree, kernel_degree=kernel_degree)
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
-    ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
+    ws = ws if ws is not None else pair_workspace(pair, device=R.device)
     h = m // 2
     out = torch.empty((pair.H - 2 * h, pair.W - 2 * h), dtype=torch.float32, device=R.device)
     _check(lib.dia_diff_image(ctypes.byref(pair), _ptr(theta), _ptr(out), _ptr(ws), ws.numel(),
@@ -378,12 +393,13 @@ def diff_image_tc(R, I, m, theta, ws=None, stream=None):
 
 def fit(R, I, m, spec: LossSpec, opts: Opts = None, mask=None, var=None, flat=None,
         theta0=None, want_diff=True, want_mask=False, ws=None, stream=None, check=True,
-        bg_degree=0):
+        bg_degree=0, kernel_degree=0):
     """dia_fit.  Tensors on one CUDA device, or all on the host (the library
     then stages them through the workspace and returns host tensors).
-    ``bg_degree``: degree of the polynomial background (Eq. 18).
+    ``bg_degree``: degree of the polynomial background (Eq. 18);
+    ``kernel_degree``: degree of a spatially varying kernel (0: one kernel).
     Returns dict(theta, K, b0, diff, mask, info)."""
-    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
+    pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree, kernel_degree)
     host = pair.mem == MEM_HOST
     dev = R.device
     opts = opts if opts is not None else default_opts()
@@ -395,9 +411,8 @@ def fit(R, I, m, spec: LossSpec, opts: Opts = None, mask=None, var=None, flat=No
         o.init = 2
     clip = o.clip_passes > 0 or want_mask
     if ws is None:
-        ws = workspace(pair.H, pair.W, m, pair.ld, clip, host,
-                       device=None if host else dev)
-    n = n_params(m, bg_degree)
+        ws = pair_workspace(pair, clip, device=None if host else dev)
+    n = n_params(m, bg_degree, kernel_degree)
     if th0 is not None and th0.size != n:
         raise ValueError(f"theta0 must have {n} entries")
     h = m // 2

@@ -32,16 +32,17 @@ def render_stars(shape, xs, ys, fluxes, sigma, chunk: int = 20000) -> np.ndarray
     """Sum of pixel-integrated, unit-normalised Gaussian profiles.
 
     Pixel (i, j) covers [j-0.5, j+0.5) x [i-0.5, i+0.5); star coordinates are
-    continuous (x = column, y = row)."""
+    continuous (x = column, y = row).  ``sigma``: one PSF width, or one per star."""
     H, W = shape
     img = np.zeros(H * W, dtype=np.float64)
-    r = max(2, int(math.ceil(6.0 * sigma)))
+    sig_all = np.broadcast_to(np.asarray(sigma, np.float64), (len(xs),))
+    r = max(2, int(math.ceil(6.0 * float(np.max(sig_all)))) if len(xs) else 2)
     off = np.arange(-r, r + 1)
-    s2 = sigma * math.sqrt(2.0)
     for c0 in range(0, len(xs), chunk):
         x = np.asarray(xs[c0:c0 + chunk], np.float64)
         y = np.asarray(ys[c0:c0 + chunk], np.float64)
         f = np.asarray(fluxes[c0:c0 + chunk], np.float64)
+        s2 = (sig_all[c0:c0 + chunk] * math.sqrt(2.0))[:, None]
         cx = np.floor(x + 0.5).astype(np.int64)[:, None] + off[None, :]
         cy = np.floor(y + 0.5).astype(np.int64)[:, None] + off[None, :]
         px = 0.5 * (erf((cx + 0.5 - x[:, None]) / s2) - erf((cx - 0.5 - x[:, None]) / s2))
@@ -85,6 +86,11 @@ class PairSpec:
     ref_noise: bool = True           # reference with 10x less variance (Eq. 22-23)
     mask_frac: float = 0.0           # Bernoulli fraction of bad (masked) pixels
     cosmic_frac: float = 0.0         # unmasked outliers, +U(1e3, 1e4)
+    # a target PSF that changes over the image (what a spatially varying kernel
+    # fits): phi_K + a_x eta + a_y xi and a shift (dx, dy) + (b_x eta, b_y xi),
+    # eta, xi the star's normalised coordinates (x - (W-1)/2)/W, (y - (H-1)/2)/H
+    kernel_sigma_slope: tuple = (0.0, 0.0)
+    shift_slope: tuple = (0.0, 0.0)
     loss: dict = field(default_factory=dict)
 
 
@@ -103,10 +109,14 @@ def make_pair(spec: PairSpec, seed: int) -> dict:
         lo, hi = spec.flux
         fl = np.exp(rng.uniform(math.log(lo), math.log(hi), n))
     sr = fwhm_to_sigma(spec.fwhm_ref)
-    si = math.sqrt(sr * sr + spec.kernel_sigma ** 2)
+    eta = (xs - 0.5 * (W - 1)) / W
+    xi = (ys - 0.5 * (H - 1)) / H
+    sk = spec.kernel_sigma + spec.kernel_sigma_slope[0] * eta + spec.kernel_sigma_slope[1] * xi
+    si = np.sqrt(sr * sr + sk ** 2)
     R_nl = spec.sky + render_stars((H, W), xs, ys, fl, sr)
     I_nl = (spec.scale * spec.sky + spec.b0) + render_stars(
-        (H, W), xs + spec.shift[0], ys + spec.shift[1], fl * spec.scale, si)
+        (H, W), xs + spec.shift[0] + spec.shift_slope[0] * eta,
+        ys + spec.shift[1] + spec.shift_slope[1] * xi, fl * spec.scale, si)
     R = add_noise(R_nl, rng, spec.gain, spec.read, 0.1) if spec.ref_noise else R_nl.copy()
     I = add_noise(I_nl, rng, spec.gain, spec.read)
     mask = None

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(native):
 def test_status_strings_and_version(native):
     assert native.status_str(0) == "DIA_OK"
     assert native.status_str(9) == "DIA_ERR_UNSUPPORTED"
-    assert native.lib.dia_abi_version() == native.ABI_VERSION == 3
+    assert native.lib.dia_abi_version() == native.ABI_VERSION == 4
 
 
 def test_default_opts_are_the_paper_values(native):

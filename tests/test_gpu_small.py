@@ -77,8 +77,10 @@ def test_strip_splits_and_edges(nat, m, shape):
     d = field(H, W, m, seed=H + W + m, n_per_px=0.004)
     rng = np.random.default_rng(m)
     th = theta_start(m, d["I"], rng, jitter=0.4)
+    th[:-1] *= 1.5   # well away from the optimum (the 1e-5 test needs a gradient
+    #                  that is not a small difference of large float32 terms)
     ld = (W + 15) // 16 * 16
-    spec = SPECS["cauchy-fixed"]
+    spec = SPECS["huber-ccd"]
     L, g = _eval(nat, d, m, th, spec, ld=ld)
     Lt, gt = _eval(nat, d, m, th, spec, ld=ld, small=False)
     Lo, go = oracle.loss_grad(d["R"], d["I"], m, th, ospec(spec))

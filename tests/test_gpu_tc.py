@@ -45,6 +45,11 @@ def test_tc_difference_image_matches_the_oracle(nat, m, shape):
     assert D.shape == Do.shape
     bound = _bound(d, m, th)
     assert np.all(np.abs(D - Do) <= bound), np.max(np.abs(D - Do) / bound)
+    # and, where many taps average the split's rounding (m >= 7), a figure well
+    # inside the bound (measured ~3e-7 of max |I| at 4096^2, m = 25); a lost
+    # cross term of the split would exceed it
+    if m >= 7:
+        assert np.max(np.abs(D - Do)) <= 1e-5 * np.max(np.abs(d["I"]))
     Df = nat.diff_image(_t(d["R"]), _t(d["I"]), m, torch.from_numpy(th)).cpu().numpy()
     assert np.all(np.abs(D - Df) <= bound)
 
@@ -79,3 +84,33 @@ def test_tc_rejects_polynomial_background(nat):
                                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
                                    ws.numel(), None)
     assert st == nat.DIA_ERR_UNSUPPORTED
+
+
+def test_tc_wait_timeout_aborts_cleanly(nat):
+    """With a 300-cycle limit on the kernel's pipeline waits, the MMA role's
+    first wait (for a window that has to come from memory) runs out: every
+    role leaves (copies and MMAs in flight drained, tensor memory released)
+    and the call returns DIA_ERR_TIMEOUT.  The next call, with the default
+    limit, on the same stream and workspace gives the correct image."""
+    import ctypes
+    m = 11
+    d = field(200, 300, m, seed=3)
+    R, I = _t(d["R"]), _t(d["I"])
+    th = torch.from_numpy(np.append(np.full(m * m, 1.0 / (m * m)), 90.0))
+    pair, keep = nat.make_pair(R, I, m)
+    ws = nat.workspace(200, 300, m, device=R.device)
+    out = torch.empty((190, 290), dtype=torch.float32, device="cuda")
+    thd = th.cuda()
+    assert nat.lib.dia_set_tc_wait_cycles(-1) == nat.DIA_ERR_ARG
+    assert nat.lib.dia_set_tc_wait_cycles(300) == 0
+    try:
+        st = nat.lib.dia_diff_image_tc(ctypes.byref(pair), ctypes.c_void_p(thd.data_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), None)
+    finally:
+        assert nat.lib.dia_set_tc_wait_cycles(0) == 0
+    assert st == nat.DIA_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    D = nat.diff_image_tc(R, I, m, th, ws=ws).cpu().numpy()
+    Do = oracle.diff_image(d["R"], d["I"], m, th.numpy())
+    assert np.all(np.abs(D - Do) <= _bound(d, m, th.numpy()))

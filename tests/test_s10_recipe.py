@@ -106,3 +106,32 @@ def test_regime_populations_follow_the_paper_counts():
         got = sum(1 for k in inside if k == key) / n
         se = math.sqrt(p * (1 - p) / n)
         assert abs(got - p) <= 4 * se + 1e-3, (key, got, p)
+
+
+def test_per_star_psf_widths_and_a_varying_target():
+    """render_stars with one width per star equals the sum of single renders;
+    a target PSF that widens with eta (the input of the spatially varying
+    kernel tests) keeps each star's flux and widens the stars on the right."""
+    rng = np.random.default_rng(0)
+    xs, ys = rng.uniform(10, 50, 5), rng.uniform(10, 50, 5)
+    fl, sg = rng.uniform(100, 1000, 5), rng.uniform(0.8, 2.0, 5)
+    one = synth.render_stars((64, 64), xs, ys, fl, sg)
+    parts = sum(synth.render_stars((64, 64), xs[i:i + 1], ys[i:i + 1], fl[i:i + 1], sg[i])
+                for i in range(5))
+    np.testing.assert_allclose(one, parts, rtol=1e-9, atol=1e-4)   # window truncation at 6 sigma
+    np.testing.assert_allclose(one.sum(), fl.sum(), rtol=1e-6)
+    base = dict(size=(64, 200), n_stars=2, m=5, fwhm_ref=2.0, kernel_sigma=1.0, ref_noise=False,
+                read=0.0, sky=0.0)
+    flat = synth.make_pair(synth.PairSpec(**base), 3)["I_noiseless"]
+    var = synth.make_pair(synth.PairSpec(**base, kernel_sigma_slope=(1.5, 0.0)), 3)["I_noiseless"]
+    np.testing.assert_allclose(var.sum(), flat.sum(), rtol=1e-6)
+    # the widths differ from the constant-PSF render only through eta: a star
+    # rendered alone at the right edge is wider (lower peak) than at the left
+    W = 200
+    left = synth.render_stars((64, W), [20.0], [32.0], [1000.0], 1.0)
+    sl = np.sqrt(synth.fwhm_to_sigma(2.0) ** 2 + (1.0 + 1.5 * (20.0 - 0.5 * (W - 1)) / W) ** 2)
+    sr = np.sqrt(synth.fwhm_to_sigma(2.0) ** 2 + (1.0 + 1.5 * (180.0 - 0.5 * (W - 1)) / W) ** 2)
+    assert sl < sr
+    assert synth.render_stars((64, W), [180.0], [32.0], [1000.0], sr).max() < \
+        synth.render_stars((64, W), [20.0], [32.0], [1000.0], sl).max()
+    assert not np.allclose(var, flat)
