@@ -616,6 +616,9 @@ def run_batch(args, rank, world, local_rank):
     spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
     opts = nat.default_opts(timeout_s=900.0)
     stream = torch.cuda.current_stream(dev)
+    # work-item size per kernel-side group: autotuned on these pairs, cached
+    from paper_2104_13715_gb300 import autotune
+    tuned = autotune.tune_batch(items, spec, stream=stream)
     ws = None
     for _ in range(args.warmup):
         out = nat.fit_batch(items, spec, opts, ws=ws, stream=stream)
@@ -703,7 +706,8 @@ def run_batch(args, rank, world, local_rank):
                                  int(max(d["R"].shape[0] for d in ds_all))],
                        "m": sorted({d["m"] for d in ds_all}), "loss": "gauss",
                        "variance": "fixed",
-                       "sharding": "pairs split across ranks by cost, no collective"},
+                       "sharding": "pairs split across ranks by cost, no collective",
+                       "work_item_variants": {str(g): r["variant"] for g, r in tuned.items()}},
             "evals_per_s": evals_all / (ms / 1e3), "pairs_converged": int(ok),
             "gpu_launches": int(launches_all), "roofline": roof,
             "subset_fits_per_s": t, "adam_off": adam_off, "clocks": clocks}

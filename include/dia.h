@@ -362,12 +362,14 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
  * optimiser iteration of the whole batch in a few launches.  `pairs` is a
  * HOST array of npairs DIA_MEM_DEVICE pairs (each with its own H, W, ld, m,
  * maps); one loss spec and one dia_opts apply to all (clip_passes must be 0;
- * init 0 or 1).  Every optimiser iteration runs one persistent fused
- * evaluation kernel per group of kernel sides (1-7, 9-15, 17-23, 25-31;
- * parallel graph branches) over work items (a pair and two of its tiles,
- * largest first, from atomic queues), then two kernels with one CTA per
- * pair (line search and history; P v and the L-BFGS direction); converged
- * pairs drop out.  graph_iters iterations are replayed from a CUDA graph.
+ * init 0 or 1).  Every optimiser iteration compacts the work items of the
+ * pairs still running (a pair and a run of its tiles, largest first; the run
+ * length per kernel-side group is dia_select_batch_variant's), runs one
+ * persistent fused evaluation kernel per group of kernel sides (1-7, 9-15,
+ * 17-23, 25-31; parallel graph branches) over those items from atomic queues,
+ * then two kernels with one CTA per pair (line search and history; P v and
+ * the L-BFGS direction) in which converged pairs return at once.
+ * graph_iters iterations are replayed from a CUDA graph.
  * Outputs: theta_out (device, nullable) packs the pairs' theta vectors in
  * order, pair i at offset sum_{j<i} n_j with n_j = m_j^2 + (d_j+1)(d_j+2)/2
  * (d_j its bg_degree); diff_out (nullable HOST array of npairs device
@@ -377,6 +379,19 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
  * statuses are in infos.  The workspace (256-byte aligned device memory) is
  * dia_batch_workspace_size(pairs, npairs, opts) bytes (0 if invalid). */
 size_t dia_batch_workspace_size(const dia_pair *pairs, int32_t npairs, const dia_opts *opts);
+
+/* Work-item size of the batched evaluation, per kernel-side group (0: m 1-7,
+ * 1: 9-15, 2: 17-23, 3: 25-31): variant v (0..3) makes a work item of a pair
+ * with kernel side m cover about c_v * 441 / m^2 tiles of 32 x 128 pixels
+ * (c = 2, 1, 4, 8 for v = 0, 1, 2, 3; between 1 and 32 tiles), so items carry
+ * about equal work across sides.  dia_batch_chunk_tiles(m, v) gives that
+ * count.  The autotuner times the variants on a batch's own pairs and selects
+ * one per group (default 0).  Process-wide; the workspace size depends on the
+ * selection, so do not change it between dia_batch_workspace_size and
+ * dia_fit_batch.  Errors: DIA_ERR_ARG (group or variant out of range). */
+dia_status dia_select_batch_variant(int32_t group, int32_t variant);
+int32_t dia_get_batch_variant(int32_t group);
+int32_t dia_batch_chunk_tiles(int32_t m, int32_t variant);
 dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs, const dia_loss_spec *loss,
                          const dia_opts *opts, double *theta_out, float *const *diff_out,
                          dia_fit_info *infos, void *workspace, size_t workspace_bytes,

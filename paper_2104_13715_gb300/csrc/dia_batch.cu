@@ -9,6 +9,7 @@
 // Converged pairs are skipped by both kernels.  graph_iters iterations are
 // captured in a CUDA graph; the host polls the count of finished pairs.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -28,6 +29,8 @@ namespace dia {
 namespace {
 
 thread_local int g_batch_cuda = 0;
+// work-item size variant of each kernel-side group (dia_select_batch_variant)
+std::atomic<int> g_batch_variant[4] = {{0}, {0}, {0}, {0}};
 
 #define DB_CK(expr)                    \
     do {                               \
@@ -51,8 +54,8 @@ struct PairPlan {
 struct BatchPlan {
     std::vector<PairPlan> pp;
     std::vector<BatchItem> items;
-    size_t off_hdr, off_eas, off_mks, off_items, off_sa, off_red, off_thoff, off_pas, off_pairs,
-        off_parts, total;
+    size_t off_hdr, off_eas, off_mks, off_items, off_act, off_gbeg, off_sa, off_red, off_thoff,
+        off_pas, off_pairs, off_parts, total;
     long long total_parts;
     int history;
     int gbeg[5];   // items of kernel-side group g: [gbeg[g], gbeg[g+1])
@@ -78,7 +81,8 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
         const int h = p.m / 2, Hv = p.H - 2 * h, Wv = p.W - 2 * h;
         q.tiles_x = (Wv + kTW - 1) / kTW;
         q.n_tiles = q.tiles_x * ((Hv + kBTH - 1) / kBTH);
-        q.n_chunks = (q.n_tiles + kChunkTiles - 1) / kChunkTiles;
+        const int ct = batch_chunk(p.m, g_batch_variant[batch_group(p.m)].load());
+        q.n_chunks = (q.n_tiles + ct - 1) / ct;
         q.part_off = parts;
         parts += (long long)q.n_chunks * q.np;
         q.theta_off = thoff;
@@ -112,8 +116,8 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
         for (int c = 0; c < q.n_chunks; ++c) {
             BatchItem it;
             it.pair = i;
-            it.t0 = c * kChunkTiles;
-            it.t1 = std::min(q.n_tiles, (c + 1) * kChunkTiles);
+            it.t0 = c * ct;
+            it.t1 = std::min(q.n_tiles, (c + 1) * ct);
             it.pad = 0;
             it.part_off = q.part_off + (long long)c * q.np;
             P.items.push_back(it);
@@ -141,6 +145,10 @@ dia_status plan_batch(const dia_pair *pairs, int npairs, int history, int precon
     o = al(o + sizeof(int) * npairs);
     P.off_items = o;
     o = al(o + sizeof(BatchItem) * P.items.size());
+    P.off_act = o;   // compacted items of the running pairs
+    o = al(o + sizeof(BatchItem) * P.items.size());
+    P.off_gbeg = o;
+    o = al(o + sizeof(int) * 5);
     P.off_sa = o;
     o = al(o + sizeof(StepArgs) * npairs);
     P.off_red = o;
@@ -180,6 +188,22 @@ cudaStream_t batch_capture_stream() {
 }  // namespace dia
 
 using namespace dia;
+
+extern "C" dia_status dia_select_batch_variant(int32_t group, int32_t variant) {
+    if (group < 0 || group > 3 || variant < 0 || variant >= kBatchVariants) return DIA_ERR_ARG;
+    g_batch_variant[group].store(variant);
+    return DIA_OK;
+}
+
+extern "C" int32_t dia_get_batch_variant(int32_t group) {
+    return (group < 0 || group > 3) ? -1 : g_batch_variant[group].load();
+}
+
+extern "C" int32_t dia_batch_chunk_tiles(int32_t m, int32_t variant) {
+    if (m < 1 || m > DIA_MAX_M || (m & 1) == 0 || variant < 0 || variant >= kBatchVariants)
+        return 0;
+    return batch_chunk(m, variant);
+}
 
 extern "C" size_t dia_batch_workspace_size(const dia_pair *pairs, int32_t npairs,
                                            const dia_opts *opts) {
@@ -223,11 +247,14 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = (char *)workspace;
     // header ints: [2] pairs finished, [4+g] evaluation queue of group g,
-    // [8+g] forward-pass queue of group g
+    // [8+g] forward-pass queue of group g, [12+g] items of group g still
+    // running (compacted each iteration), [16+g] all items of group g
     int *hdr = (int *)(ws + P.off_hdr);
     EvalArgs *d_eas = (EvalArgs *)(ws + P.off_eas);
     int *d_mks = (int *)(ws + P.off_mks);
     BatchItem *d_items = (BatchItem *)(ws + P.off_items);
+    BatchItem *d_act = (BatchItem *)(ws + P.off_act);
+    int *d_gbeg = (int *)(ws + P.off_gbeg);
     StepArgs *d_sa = (StepArgs *)(ws + P.off_sa);
     BatchRed *d_red = (BatchRed *)(ws + P.off_red);
     long long *d_thoff = (long long *)(ws + P.off_thoff);
@@ -361,6 +388,12 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
         thoff[i] = q.theta_off;
     }
     DB_CK(cudaMemsetAsync(hdr, 0, 256, s));
+    {
+        int cnt[4];
+        for (int g = 0; g < 4; ++g) cnt[g] = P.gbeg[g + 1] - P.gbeg[g];
+        DB_CK(cudaMemcpyAsync(hdr + 16, cnt, sizeof(cnt), cudaMemcpyHostToDevice, s));
+        DB_CK(cudaMemcpyAsync(d_gbeg, P.gbeg, sizeof(int) * 5, cudaMemcpyHostToDevice, s));
+    }
     DB_CK(cudaMemcpyAsync(d_eas, eas.data(), sizeof(EvalArgs) * npairs, cudaMemcpyHostToDevice, s));
     DB_CK(cudaMemcpyAsync(d_mks, mks.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, s));
     DB_CK(cudaMemcpyAsync(d_items, P.items.data(), sizeof(BatchItem) * P.items.size(),
@@ -378,24 +411,35 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     DB_CK(cudaGetDevice(&dev));
     DB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int grid[4] = {0, 0, 0, 0}, n_it[4];
-    const BatchItem *g_items[4];
+    const int gsmem[4] = {batch_group_smem(0), batch_group_smem(1), batch_group_smem(2),
+                          batch_group_smem(3)};
+    const BatchItem *g_items[4], *g_act[4];
+    const int *g_nall[4], *g_nact[4];
     for (int g = 0; g < 4; ++g) {
         n_it[g] = P.gbeg[g + 1] - P.gbeg[g];
         g_items[g] = d_items + P.gbeg[g];
+        g_act[g] = d_act + P.gbeg[g];
+        g_nall[g] = hdr + 16 + g;
+        g_nact[g] = hdr + 12 + g;
         if (n_it[g] == 0) continue;
         for (int mode = 0; mode < 2; ++mode)
             DB_CK(cudaFuncSetAttribute(batch_kernel_ptr(g, mode, bg),
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem));
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       gsmem[g]));
         int occ = 1;
         DB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(g, kModeGrad, bg),
-                                                            kBW * 32, kBatchSmem));
+                                                            kBW * 32, gsmem[g]));
         grid[g] = std::min(n_it[g], sms * (occ < 1 ? 1 : occ));
     }
+    // mode kModeGrad walks the compacted items of the running pairs, the
+    // final forward pass every item
     auto launch_group = [&](int g, int mode, int *counter, cudaStream_t st) -> cudaError_t {
-        void *params[] = {(void *)&d_eas, (void *)&d_mks, (void *)&g_items[g], (void *)&n_it[g],
+        const BatchItem *its = mode == kModeGrad ? g_act[g] : g_items[g];
+        const int *nit = mode == kModeGrad ? g_nact[g] : g_nall[g];
+        void *params[] = {(void *)&d_eas, (void *)&d_mks, (void *)&its, (void *)&nit,
                           (void *)&counter, (void *)&d_parts};
         return cudaLaunchKernel(batch_kernel_ptr(g, mode, bg), dim3(grid[g]), dim3(kBW * 32), params,
-                                kBatchSmem, st);
+                                gsmem[g], st);
     };
 
     // initialisation: per-pair median and theta (Sec. 2.9)
@@ -417,8 +461,9 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     app(&max_n, sizeof max_n);
     app(&bg, sizeof bg);
     // the captured kernels take pointers into the workspace at these offsets
-    const size_t offs[] = {P.off_hdr, P.off_eas,   P.off_mks,   P.off_items, P.off_sa,
-                           P.off_red, P.off_thoff, P.off_pas,   P.off_pairs, P.off_parts};
+    const size_t offs[] = {P.off_hdr,   P.off_eas,  P.off_mks,   P.off_items, P.off_act,
+                           P.off_gbeg,  P.off_sa,   P.off_red,   P.off_thoff, P.off_pas,
+                           P.off_pairs, P.off_parts};
     app(offs, sizeof offs);
     app(P.gbeg, sizeof P.gbeg);
     cudaGraphExec_t gx = nullptr;
@@ -442,7 +487,9 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
             DB_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
             for (int it = 0; it < opts.graph_iters && e == cudaSuccess; ++it) {
-                e = cudaEventRecord(evf, cs);
+                // items of the pairs still running, then the group evaluations
+                e = launch_compact_items(d_items, d_eas, d_gbeg, d_act, hdr + 12, cs);
+                if (e == cudaSuccess) e = cudaEventRecord(evf, cs);
                 for (int g = 0; g < 4 && e == cudaSuccess; ++g) {
                     if (n_it[g] == 0) continue;
                     e = cudaStreamWaitEvent(side[g], evf, 0);
@@ -479,7 +526,7 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     long long launches = 1 + (opts.precond ? precond_launches(max_n) : 0);   // init (+ preconditioner)
     for (;;) {
         DB_CK(cudaGraphLaunch(gx, s));
-        launches += (long long)(n_groups + kStepLaunchesBatch) * opts.graph_iters;
+        launches += (long long)(1 + n_groups + kStepLaunchesBatch) * opts.graph_iters;
         DB_CK(cudaMemcpyAsync(&done_host, hdr + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
         DB_CK(cudaStreamSynchronize(s));
         if (done_host >= npairs) break;

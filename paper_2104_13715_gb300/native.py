@@ -103,6 +103,9 @@ _SIGS = {
     "dia_fisher_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 4),
     "dia_set_accumulation": (ctypes.c_int32, [ctypes.c_int32]),
     "dia_set_small_kernel": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_select_batch_variant": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
+    "dia_get_batch_variant": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_batch_chunk_tiles": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "dia_set_tc_wait_cycles": (ctypes.c_int32, [ctypes.c_int64]),
     "dia_pair_workspace_size": (ctypes.c_size_t, [_P(Pair), ctypes.c_int32]),
     "dia_pair_fisher_workspace_size": (ctypes.c_size_t, [_P(Pair)]),
@@ -176,6 +179,11 @@ def set_small_kernel(enable: bool) -> None:
     """dia_set_small_kernel: the streaming small-kernel evaluation (m <= 5)
     on (default) or off (the tiled kernel for every m)."""
     _check(lib.dia_set_small_kernel(1 if enable else 0), "dia_set_small_kernel")
+
+
+def select_batch_variant(group: int, variant: int) -> None:
+    """dia_select_batch_variant: work-item size variant of a kernel-side group."""
+    _check(lib.dia_select_batch_variant(group, variant), "dia_select_batch_variant")
 
 
 def get_small_kernel() -> bool:

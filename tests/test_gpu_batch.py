@@ -85,3 +85,60 @@ def test_batch_nonlinear_loss(nat):
         ref = oracle.newton(d["R"], d["I"], d["m"], th,
                             oracle.LossSpec("gauss", "ccd", sigma0=5.0, gain=1.0))
         _check(th, ref, float(np.median(d["I"])))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_work_item_variant_matches_the_oracle(nat, variant):
+    """Each work-item size (tiles per item, per kernel-side group) gives the
+    oracle's normal-equation optimum for every pair of an uneven batch."""
+    ds = _pairs(9, seed=4, side=(64, 300), m_range=(3, 31))
+    items = [_dev(d) for d in ds]
+    spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
+    try:
+        for g in range(4):
+            nat.select_batch_variant(g, variant)
+        out = nat.fit_batch(items, spec, nat.default_opts(timeout_s=300.0))
+    finally:
+        for g in range(4):
+            nat.select_batch_variant(g, 0)
+    for d, th, info in zip(ds, out["thetas"], out["infos"]):
+        assert info["status"] == 0, info
+        _check(th.cpu().numpy(), oracle.normal_solve(d["R"], d["I"], d["m"]),
+               float(np.median(d["I"])))
+
+
+def test_converged_pairs_leave_the_work_list(nat):
+    """A batch where one pair needs many more iterations than the others: the
+    result is the same as the pair fitted in a batch of its own (the pairs
+    that finished early drop out of the evaluation queue without changing
+    anyone's arithmetic)."""
+    ds = _pairs(6, seed=7, side=(64, 160), m_range=(7, 15))
+    items = [_dev(d) for d in ds]
+    spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
+    opts = nat.default_opts(timeout_s=300.0)
+    out = nat.fit_batch(items, spec, opts)
+    evals = [f["evals"] for f in out["infos"]]
+    k = int(np.argmax(evals))
+    assert max(evals) > min(evals)
+    alone = nat.fit_batch([items[k]], spec, opts)
+    assert alone["infos"][0]["evals"] == evals[k]
+    assert torch.equal(alone["thetas"][0], out["thetas"][k])
+
+
+def test_batch_autotune_selects_and_caches(tmp_path):
+    from paper_2104_13715_gb300 import autotune
+    from paper_2104_13715_gb300 import native as nat
+    ds = _pairs(6, seed=3, side=(64, 160), m_range=(7, 17))
+    items = [_dev(d) for d in ds]
+    spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
+    path = str(tmp_path / "tb.json")
+    try:
+        rec = autotune.tune_batch(items, spec, iters=8, cache_path=path)
+        for g, r in rec.items():
+            assert r["variant"] == int(np.argmin(r["times_ms"]))
+            assert nat.lib.dia_get_batch_variant(g) == r["variant"]
+        rec2 = autotune.tune_batch(items, spec, iters=8, cache_path=path)
+        assert {g: r["variant"] for g, r in rec2.items()} == {g: r["variant"] for g, r in rec.items()}
+    finally:
+        for g in range(4):
+            nat.select_batch_variant(g, 0)
