@@ -902,6 +902,46 @@ def run_tc_forward(args):
                       "useful": "2 m^2 flop per valid pixel"}), flush=True)
 
 
+def run_tc_eval(args):
+    """One loss+gradient evaluation of the workload at the box-car start in
+    two forms: dia_loss_grad (the fused float32 kernel) and dia_loss_grad_tc
+    (both contractions on the tensor cores), W + K calls each, CUDA events
+    around the K calls (each call includes its small launches; the
+    tensor-core call also reads back its status word); gradient error of each
+    against the other."""
+    import torch
+    from paper_2104_13715_gb300 import native as nat
+    d = synth.workload(args.workload, seed=args.seed, size=args.size)
+    m = d["m"]
+    dev = torch.device("cuda", 0)
+
+    def up(a, dt):
+        return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+
+    R, I = up(d["R"], torch.float32), up(d["I"], torch.float32)
+    mask, var = up(d.get("mask"), torch.uint8), up(d.get("var"), torch.float32)
+    spec = nat.loss_spec(**_loss_kw(d))
+    th = torch.full((m * m + 1,), 1.0 / (m * m), dtype=torch.float64)
+    th[-1] = float(np.median(d["I"]))
+    res, grads = {}, {}
+    for name, fn in (("fp32_fused", nat.loss_grad), ("tensor_cores", nat.loss_grad_tc)):
+        for _ in range(args.warmup):
+            L, g = fn(R, I, m, th, spec, mask=mask, var=var)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            L, g = fn(R, I, m, th, spec, mask=mask, var=var)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        grads[name] = g.cpu().numpy()
+        res[name] = {"ms": e0.elapsed_time(e1) / max(args.steps, 1)}
+    diff = float(np.max(np.abs(grads["tensor_cores"] - grads["fp32_fused"])) /
+                 np.max(np.abs(grads["fp32_fused"])))
+    print(json.dumps({"tc_eval": args.workload, "H": d["R"].shape[0], "W": d["R"].shape[1], "m": m,
+                      "results": res, "grad_diff_rel": diff}), flush=True)
+
+
 def run_kernel_only(args):
     """The fused loss+gradient kernel of the workload at the box-car start:
     its launches alone (dia_time_eval: CUDA events around each launch on the
@@ -1043,6 +1083,8 @@ def main():
                          "(--kernel-only)")
     ap.add_argument("--tc-forward", action="store_true",
                     help="time the forward pass on CUDA cores and on tensor cores")
+    ap.add_argument("--tc-eval", action="store_true",
+                    help="time the loss+gradient evaluation on CUDA cores and on tensor cores")
     ap.add_argument("--s10-study", type=int, default=0,
                     help="run the simulated-image accuracy study with this many simulations")
     ap.add_argument("--precision-study", action="store_true",
@@ -1058,6 +1100,9 @@ def main():
         return
     if args.tc_forward:
         run_tc_forward(args)
+        return
+    if args.tc_eval:
+        run_tc_eval(args)
         return
     if args.precision_study:
         run_precision_study(args)

@@ -327,6 +327,26 @@ dia_status dia_diff_image(const dia_pair *pair, const double *theta, float *diff
 dia_status dia_diff_image_tc(const dia_pair *pair, const double *theta, float *diff_out,
                              void *workspace, size_t workspace_bytes, void *stream);
 
+/* One loss + gradient evaluation with both contractions on the tensor cores
+ * (tcgen05.mma, sm_103a): the forward pass of dia_diff_image_tc (split bf16)
+ * gives D = I - M; a pass over the valid region forms the loss and g = dl/dM
+ * (float32, the same pixel terms as dia_loss_grad); the weight gradient
+ * dL/dK[a][b] = sum_i P_b[i + a][i], P_b[y][i] = sum_j W[y][j + b] g[i][j]
+ * over 64 x 128 tiles of g and their 96 x 160 R windows W, is one GEMM per
+ * kernel column b on the tensor cores with g and R scaled by powers of two and
+ * split into float16 hi + lo (three products, float32 accumulation in tensor
+ * memory), then sums along the diagonals (float32 per tile, float64 across
+ * tiles).  Same arguments and outputs as dia_loss_grad; constant background,
+ * one kernel (bg_degree = kernel_degree = 0) and m <= 31, else
+ * DIA_ERR_UNSUPPORTED.  The workspace is dia_tc_workspace_size(H, W, ld, m)
+ * bytes (the evaluation workspace plus the difference image, the g map and
+ * two partial rows per SM).  Synchronous: waits on `stream` and returns
+ * DIA_ERR_TIMEOUT if a bounded wait of a tensor-core kernel ran out. */
+size_t dia_tc_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m);
+dia_status dia_loss_grad_tc(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
+                            double *loss_out, double *grad_out, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
 /* Limit, in SM clock cycles, of each pipeline wait of dia_diff_image_tc's
  * kernel (an mbarrier wait of a producer or MMA role); 0 restores the default
  * (2e9 cycles, about one second).  A wait that runs out aborts every role of

@@ -20,6 +20,7 @@
 #include "dia_ops.cuh"
 #include "dia_small.h"
 #include "dia_svk.h"
+#include "dia_tc_grad.h"
 
 using namespace dia;
 
@@ -603,6 +604,76 @@ __global__ void l2_flush_read_kernel(const uint4 *p, size_t n16, unsigned *sink)
     if (acc == 0x9e3779b9u && sink) *sink = acc;
 }
 }  // namespace
+
+// Workspace of dia_loss_grad_tc after the evaluation workspace: the
+// difference image, the g map, two partial rows per SM and the scale / status
+// words.
+struct TcEvalLayout {
+    size_t base, D, G, parts, misc, total;
+    int rows;
+};
+
+static bool tc_eval_layout(int H, int W, int ld, int m, TcEvalLayout &T) {
+    T.base = dia_workspace_size(H, W, ld, m, 0, DIA_MEM_DEVICE);
+    if (T.base == 0) return false;
+    const int h = m / 2;
+    const size_t npx = (size_t)(H - 2 * h) * (W - 2 * h);
+    T.rows = 2 * device_sms();
+    size_t o = align_up(T.base);
+    T.D = o;
+    o = align_up(o + npx * 4);
+    T.G = o;
+    o = align_up(o + npx * 4);
+    T.parts = o;
+    o = align_up(o + (size_t)T.rows * red_size(m * m) * 8);
+    T.misc = o;
+    o = align_up(o + 16);
+    T.total = o;
+    return true;
+}
+
+size_t dia_tc_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m) {
+    if (!dims_ok(H, W, ld, m) || m > kTcGradMaxM) return 0;
+    TcEvalLayout T;
+    return tc_eval_layout(H, W, ld, m, T) ? T.total : 0;
+}
+
+dia_status dia_loss_grad_tc(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
+                            double *loss_out, double *grad_out, void *workspace,
+                            size_t workspace_bytes, void *stream) {
+    if (!pair || pair->mem != DIA_MEM_DEVICE || !loss || !theta || !loss_out || !grad_out)
+        return DIA_ERR_ARG;
+    if (pair->bg_degree != 0 || pair->kernel_degree != 0) return DIA_ERR_UNSUPPORTED;
+    dia_status rc = check_pair(pair);
+    if (rc != DIA_OK) return rc;
+    if (pair->m > kTcGradMaxM) return DIA_ERR_UNSUPPORTED;
+    TcEvalLayout T;
+    if (!tc_eval_layout(pair->H, pair->W, pair->ld, pair->m, T)) return DIA_ERR_ARG;
+    if (!workspace || workspace_bytes < T.total || ((uintptr_t)workspace % kAlign) != 0)
+        return DIA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    rc = setup(pair, loss, 0, workspace, T.base, s, c);
+    if (rc != DIA_OK) return rc;
+    char *ws = (char *)workspace;
+    float *D = (float *)(ws + T.D);
+    float *G = (float *)(ws + T.G);
+    double *parts = (double *)(ws + T.parts);
+    unsigned *amax = (unsigned *)(ws + T.misc);
+    int *status = (int *)(ws + T.misc + 8);
+    const int m = pair->m;
+    DIA_CK(cudaMemsetAsync(amax, 0, 16, s));
+    DIA_CK(launch_prep_kpad(theta, m, c.ki.kp, c.nb, c.kpad, s));
+    DIA_CK(launch_tc_forward(c.dp.ref, c.dp.img, c.dp.H, c.dp.W, c.dp.ld, m, c.kpad, c.ki.kp, D,
+                             status, s, g_tc_wait_cycles.load()));
+    DIA_CK(launch_tc_grad_eval(c.ea, m, D, G, amax, parts, red_size(m * m), T.rows / 2, status, s));
+    DIA_CK(launch_reduce(parts, T.rows, red_size(m * m), c.red, nullptr, s));
+    DIA_CK(launch_emit_loss_grad(c.red, m, 1, loss_out, grad_out, s));
+    int hs = 0;
+    DIA_CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DIA_CK(cudaStreamSynchronize(s));
+    return hs ? DIA_ERR_TIMEOUT : DIA_OK;
+}
 
 dia_status dia_time_eval(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
                          int32_t reps, void *flush_buf, size_t flush_bytes, float *ms_out,

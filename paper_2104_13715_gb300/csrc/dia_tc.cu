@@ -41,6 +41,7 @@
 
 #include "../../include/dia.h"
 #include "dia_ops.cuh"
+#include "dia_tc_ptx.cuh"
 
 namespace dia {
 
@@ -55,7 +56,6 @@ constexpr int kTcKC = 12;                  // 16-byte chunks of one Zk_b (>= (NO
 constexpr int kTcMaxM = 31;
 constexpr int kTcProducers = 128;          // warps 0-3
 constexpr int kTcThreads = kTcProducers + 32;
-constexpr long long kTcWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
 
 struct TcSmem {
     float f[kTcYT][kTcXT];                        // next tile's R window (cp.async)
@@ -70,58 +70,6 @@ struct TcSmem {
     int mma_abort;        // set by the MMA warp when a wait of its own ran out
     int prod_abort;       // set by a producer (read by the MMA warp's waits)
 };
-
-__device__ __forceinline__ uint32_t su32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// no-swizzle K-major shared-memory matrix descriptor (start, leading = K-direction
-// core-matrix stride, stride = M/N-direction 8-row stride; version 1)
-__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-// instruction descriptor, kind::f16: f32 accumulators, bf16 A and B, both K-major
-__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t taddr, uint64_t a, uint64_t b, uint32_t idesc,
-                                       int acc) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                 :: "r"(taddr), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t *b) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(su32(b)));
-}
-
-// Wait for the phase with parity `ph`; false after `limit` SM clock cycles or
-// once the other role has aborted (*other != 0).  Pipeline waits take the
-// launch's limit (TcArgs::wait_cycles); the drains before the CTA exits
-// (copies or MMAs still in flight) always take kTcWaitCycles.
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t ph, const int *other,
-                                        long long limit = kTcWaitCycles) {
-    const long long t0 = clock64();
-    const volatile int *ab = other;
-    for (;;) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(su32(bar)), "r"(ph));
-        if (done) return true;
-        if (*ab != 0 || clock64() - t0 > limit) return false;
-    }
-}
 
 // Barrier 1 over the 128 producer threads with an OR reduction of `fail`: every
 // producer gets the same answer, so they all leave the pipeline together.

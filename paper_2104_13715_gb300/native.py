@@ -107,6 +107,10 @@ _SIGS = {
     "dia_get_batch_variant": (ctypes.c_int32, [ctypes.c_int32]),
     "dia_batch_chunk_tiles": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "dia_set_tc_wait_cycles": (ctypes.c_int32, [ctypes.c_int64]),
+    "dia_tc_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 4),
+    "dia_loss_grad_tc": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]),
     "dia_pair_workspace_size": (ctypes.c_size_t, [_P(Pair), ctypes.c_int32]),
     "dia_pair_fisher_workspace_size": (ctypes.c_size_t, [_P(Pair)]),
     "dia_time_eval": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_int32,
@@ -397,6 +401,25 @@ def diff_image_tc(R, I, m, theta, ws=None, stream=None):
     _check(lib.dia_diff_image_tc(ctypes.byref(pair), _ptr(theta), _ptr(out), _ptr(ws),
                                  ws.numel(), _stream(stream)), "dia_diff_image_tc")
     return out
+
+
+def loss_grad_tc(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, stream=None):
+    """dia_loss_grad_tc: the evaluation with both contractions on the tensor
+    cores.  Returns (loss[1], grad[n]) float64 device tensors."""
+    pair, keep = make_pair(R, I, m, mask, var, flat)
+    if not R.is_cuda:
+        raise ValueError("loss_grad_tc takes device tensors")
+    theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
+    nb = lib.dia_tc_workspace_size(pair.H, pair.W, pair.ld, m)
+    if nb == 0:
+        raise DiaError(DIA_ERR_ARG, "dia_tc_workspace_size")
+    ws = torch.empty(nb, dtype=torch.uint8, device=R.device)
+    loss = torch.empty(1, dtype=torch.float64, device=R.device)
+    grad = torch.empty(m * m + 1, dtype=torch.float64, device=R.device)
+    st = lib.dia_loss_grad_tc(ctypes.byref(pair), ctypes.byref(spec), _ptr(theta), _ptr(loss),
+                              _ptr(grad), _ptr(ws), nb, _stream(stream))
+    _check(st, "dia_loss_grad_tc")
+    return loss, grad
 
 
 def fit(R, I, m, spec: LossSpec, opts: Opts = None, mask=None, var=None, flat=None,

@@ -114,3 +114,64 @@ def test_tc_wait_timeout_aborts_cleanly(nat):
     D = nat.diff_image_tc(R, I, m, th, ws=ws).cpu().numpy()
     Do = oracle.diff_image(d["R"], d["I"], m, th.numpy())
     assert np.all(np.abs(D - Do) <= _bound(d, m, th.numpy()))
+
+
+def _abscorr(Rabs, w, m):
+    """sum_p w_p |R|[p + (a, b)] for every kernel pixel (a, b): the
+    correlation of a valid-region weight map with |R|."""
+    from numpy.lib.stride_tricks import sliding_window_view
+    win = sliding_window_view(Rabs, (m, m))
+    return np.einsum("yx,yxab->ab", w, win).ravel()
+
+
+@pytest.mark.parametrize("m,name", [(3, "gauss-fixed"), (11, "gauss-ccd"), (19, "huber-fixed"),
+                                    (25, "cauchy-fixed"), (31, "gauss-emccd")])
+def test_tc_loss_grad_within_its_error_bound(nat, m, name):
+    """dia_loss_grad_tc against the FP64 oracle within the bound its arithmetic
+    gives: the forward pass's split-bf16 error |dM| <= 2^-14 (|K| * |R|)_p
+    moves g_p by at most |l''(M_p)| |dM_p|; the float16 split of the weight
+    gradient leaves ~2^-21 of each product (2^-19 taken); plus the float32
+    floor 1e-6 max |grad|.  Per parameter k:
+        |grad_k - grad*_k| <= sum_p |l''_p| |dM_p| |phi_k(p)| + 2^-19 sum_p |g_p| |phi_k(p)| + floor
+    with phi_k the R window pixel of k (1 for B0)."""
+    from tests._helpers import SPECS, ospec, theta_start
+    spec = SPECS[name]
+    d = field(200, 300, m, seed=60 + m)
+    rng = np.random.default_rng(m)
+    var = rng.uniform(50, 400, d["R"].shape).astype(np.float32) if spec["noise"] == "fixed" else None
+    th = theta_start(m, d["I"], rng, jitter=0.3)
+    L, g = nat.loss_grad_tc(_t(d["R"]), _t(d["I"]), m, torch.from_numpy(th), nat.loss_spec(**spec),
+                            var=None if var is None else _t(var))
+    g = g.cpu().numpy()
+    Lo, go = oracle.loss_grad(d["R"], d["I"], m, th, ospec(spec), var=var)
+    M = oracle.model(d["R"], th, m)
+    _, g1, g2, _ = oracle.pixel_terms(d["I"], M, m, ospec(spec), var=var)
+    dM = 2.0 ** -14 * oracle.model(np.abs(d["R"]), np.append(np.abs(th[:-1]), 0.0), m) + \
+        1e-6 * np.max(np.abs(d["I"]))
+    Rabs = np.abs(d["R"].astype(np.float64))
+    wf = np.abs(g2) * dM
+    bound = np.append(_abscorr(Rabs, wf, m), wf.sum())
+    bound += 2.0 ** -19 * np.append(_abscorr(Rabs, np.abs(g1), m), np.abs(g1).sum())
+    bound += 1e-6 * np.max(np.abs(go))
+    assert np.all(np.abs(g - go) <= bound), np.max(np.abs(g - go) / bound)
+    # the loss moves by at most sum_p |l'_p| |dM_p| (plus the float32 floor)
+    assert abs(L.item() - Lo) <= np.sum(np.abs(g1) * dM) + 1e-6 * abs(Lo)
+
+
+def test_tc_loss_grad_full_size_and_fp32_agree(nat):
+    """4096^2, m = 25, Cauchy loss with mask and variance map (the headline
+    workload) at the box-car start: the tensor-core evaluation's gradient is
+    within 1e-5 of the FP64 oracle's (max norm)."""
+    from paper_2104_13715_gb300 import synth
+    from tests._helpers import rel_inf
+    d = synth.workload("ccd4096_m25_cauchy_clip3", seed=0)
+    m = d["m"]
+    th = np.full(m * m + 1, 1.0 / (m * m))
+    th[-1] = float(np.median(d["I"]))
+    spec = dict(rho="cauchy", noise="fixed")
+    L, g = nat.loss_grad_tc(_t(d["R"]), _t(d["I"]), m, torch.from_numpy(th), nat.loss_spec(**spec),
+                            mask=_t(d["mask"], torch.uint8), var=_t(d["var"]))
+    Lo, go = oracle.loss_grad(d["R"], d["I"], m, th, oracle.LossSpec(rho="cauchy", noise="fixed"),
+                              mask=d["mask"], var=d["var"])
+    assert rel_inf(g.cpu().numpy(), go) <= 1e-5
+    assert L.item() == pytest.approx(Lo, rel=1e-5)

@@ -67,3 +67,70 @@ def test_descriptor_offsets_stay_in_their_arrays():
         assert last_a < (YT // 8) * XT * 8
         last_b = 2 * (nks - 1) * 64 + (NO // 8 - 1) * 64 + (16 // 8 - 1) * 64 + 63
         assert last_b < KC * 64
+
+
+# ---------------------------------------------------------------------------
+# The weight-gradient kernel (dia_tc_grad.cu): tiles of GI x GJ of g, the R
+# window in the same chunked layout (GYC chunks of 8 rows, GXT columns) read
+# as an MN-major A operand, the g tile as a K-major B operand.
+GI, GJ, GXT, GYC = 64, 128, 160, 12
+
+
+def _operand_mn(buf, start, lbo, sbo, rows, cols):
+    """An MN-major operand (rows = M or N, cols = K): core matrices of 8 K
+    rows of 16 bytes, each row holding 8 consecutive M elements; element
+    (n, k) at start + (n // 8) SBO + (k // 8) LBO + (k % 8) 16 B + (n % 8) 2 B."""
+    n = np.arange(rows)[:, None]
+    k = np.arange(cols)[None, :]
+    idx = start + (n // 8) * sbo + (k // 8) * lbo + (k % 8) * 8 + (n % 8)
+    return buf[idx]
+
+
+@pytest.mark.parametrize("m", [1, 3, 7, 13, 25, 31])
+def test_gradient_operands_and_diagonal_sums_give_the_correlation(m):
+    """dK[a][b] = sum_{i,j} g[i][j] W[i + a][j + b] from the kernel's operands:
+    P_b = A_b B^T with A_b the MN-major window shifted by b columns (16 b
+    bytes) and B the K-major g tile, summed over K steps of 16; then
+    dK[a][b] = sum_i P_b[i + a][i]."""
+    rng = np.random.default_rng(m)
+    Wwin = rng.normal(size=(GYC * 8, GXT))           # the window W[y][x]
+    g = rng.normal(size=(GI, GJ))
+    # T[yc][x][e] = W[8 yc + e][x] (one split), followed by the other split and
+    # the g tile so that rows of A beyond the window stay in the buffer
+    T = np.zeros((GYC, GXT, 8))
+    for yc in range(GYC):
+        for e in range(8):
+            T[yc, :, e] = Wwin[8 * yc + e]
+    # g tile K-major: [i / 8][j / 8][i % 8][j % 8]
+    Gs = np.zeros((GI // 8, GJ // 8, 8, 8))
+    for i in range(GI):
+        for j in range(GJ):
+            Gs[i // 8, j // 8, i % 8, j % 8] = g[i, j]
+    buf = np.concatenate([T.ravel(), np.full(T.size, np.nan), Gs.ravel(), Gs.ravel()])
+    gbase = 2 * T.size
+    dK = np.zeros((m, m))
+    for b in range(m):
+        P = np.zeros((128, GI))
+        for ks in range(GJ // 16):
+            A = _operand_mn(buf, b * 8 + ks * 128, 64, GXT * 8, 128, 16)   # (y, j)
+            B = _operand(buf, gbase + ks * 128, 64, (GJ // 8) * 64, GI, 16)   # (i, j)
+            P += np.nan_to_num(A) @ B.T
+        for a in range(m):
+            dK[a, b] = sum(P[i + a, i] for i in range(GI))
+    ref = np.array([[np.sum(g * Wwin[a:a + GI, b:b + GJ]) for b in range(m)] for a in range(m)])
+    np.testing.assert_allclose(dK, ref, rtol=1e-12, atol=1e-9)
+
+
+def test_gradient_descriptors_stay_in_shared_memory():
+    """Every byte the gradient kernel's descriptors reach lies inside its
+    operand arrays: A rows 96..127 of the second split run into the g tile
+    (ignored rows), the last column shift and K step stay inside a row."""
+    t_split = GYC * GXT * 16                       # bytes of one window split
+    g_bytes = 2 * GI * GJ * 2
+    m = 31
+    last_a = t_split + (m - 1) * 16 + (GJ // 16 - 1) * 256 + 15 * GXT * 16 + 128 + 127
+    assert last_a < 2 * t_split + g_bytes
+    last_b = g_bytes // 2 + (GJ // 16 - 1) * 256 + (GI // 8 - 1) * (GJ // 8) * 128 + 128 + 127
+    assert last_b < g_bytes
+    # the columns a K step reads: b + 16 ks + 15 < GXT
+    assert (m - 1) + 16 * (GJ // 16 - 1) + 15 < GXT
