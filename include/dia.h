@@ -214,8 +214,14 @@ const char *dia_status_str(int32_t status);
 /* Version of this ABI (DIA_ABI_VERSION). */
 int32_t dia_abi_version(void);
 
-/* CUDA error code of the last DIA_ERR_CUDA on this host thread (0 if none). */
+/* CUDA error code of the last DIA_ERR_CUDA on this host thread (0 if none).
+ * A tensor-core kernel's own bounds check reports -2 (forward pass) or -3
+ * (weight gradient) here: an index outside its buffers was skipped. */
 int32_t dia_last_cuda_error(void);
+
+/* Where the library caught that error: the source line of its C-ABI file
+ * (0 if none), for bug reports. */
+int32_t dia_last_cuda_error_site(void);
 
 /* Fill `opts` with the paper's defaults (values in the field comments). */
 dia_status dia_opts_default(dia_opts *opts);

@@ -27,6 +27,7 @@ using namespace dia;
 namespace {
 
 thread_local int g_last_cuda = 0;
+thread_local int g_last_cuda_site = 0;   // source line of this file that caught it
 
 // NVTX range for profilers (a no-op unless a tool is attached)
 struct NvtxRange {
@@ -47,6 +48,7 @@ std::atomic<long long> g_tc_wait_cycles{0};
         cudaError_t _e = (expr);                   \
         if (_e != cudaSuccess) {                   \
             g_last_cuda = (int)_e;                 \
+            g_last_cuda_site = __LINE__;           \
             return DIA_ERR_CUDA;                   \
         }                                          \
     } while (0)
@@ -520,6 +522,7 @@ dia_status dia_set_tc_wait_cycles(int64_t cycles) {
 }
 
 int32_t dia_last_cuda_error(void) { return g_last_cuda; }
+int32_t dia_last_cuda_error_site(void) { return g_last_cuda_site; }
 
 int32_t dia_kernel_variants(int32_t m) {
     if (m < 1 || m > DIA_MAX_M || (m & 1) == 0) return 0;
@@ -608,22 +611,35 @@ __global__ void l2_flush_read_kernel(const uint4 *p, size_t n16, unsigned *sink)
 // Workspace of dia_loss_grad_tc after the evaluation workspace: the
 // difference image, the g map, two partial rows per SM and the scale / status
 // words.
+// Workspace of dia_loss_grad_tc: the evaluation's own, then the g map over the
+// valid region padded to whole tiles of both kernels (Hp rows a multiple of
+// 128, Wp columns a multiple of 128), the partial rows of the forward pass and
+// of the gradient kernel, max |R|, max |g| and the status word.
+// status word of a tensor-core launch: 1 a wait ran out, 2 / 3 a kernel's own
+// bounds check failed (reported as a CUDA error with code -2 / -3)
+static dia_status tc_status(int hs) {
+    if (hs == 0) return DIA_OK;
+    if (hs == 1) return DIA_ERR_TIMEOUT;
+    g_last_cuda = -hs;
+    g_last_cuda_site = __LINE__;
+    return DIA_ERR_CUDA;
+}
+
 struct TcEvalLayout {
-    size_t base, D, G, parts, misc, total;
-    int rows;
+    size_t base, G, parts, misc, total;
+    int rows, Hp, Wp;
 };
 
 static bool tc_eval_layout(int H, int W, int ld, int m, TcEvalLayout &T) {
     T.base = dia_workspace_size(H, W, ld, m, 0, DIA_MEM_DEVICE);
     if (T.base == 0) return false;
     const int h = m / 2;
-    const size_t npx = (size_t)(H - 2 * h) * (W - 2 * h);
+    T.Hp = (H - 2 * h + 127) / 128 * 128;
+    T.Wp = (W - 2 * h + 127) / 128 * 128;
     T.rows = 2 * device_sms();
     size_t o = align_up(T.base);
-    T.D = o;
-    o = align_up(o + npx * 4);
     T.G = o;
-    o = align_up(o + npx * 4);
+    o = align_up(o + (size_t)T.Hp * T.Wp * 4);
     T.parts = o;
     o = align_up(o + (size_t)T.rows * red_size(m * m) * 8);
     T.misc = o;
@@ -656,23 +672,27 @@ dia_status dia_loss_grad_tc(const dia_pair *pair, const dia_loss_spec *loss, con
     rc = setup(pair, loss, 0, workspace, T.base, s, c);
     if (rc != DIA_OK) return rc;
     char *ws = (char *)workspace;
-    float *D = (float *)(ws + T.D);
     float *G = (float *)(ws + T.G);
     double *parts = (double *)(ws + T.parts);
     unsigned *amax = (unsigned *)(ws + T.misc);
     int *status = (int *)(ws + T.misc + 8);
-    const int m = pair->m;
+    const int m = pair->m, np = red_size(m * m), half = T.rows / 2;
+    const long long wc = g_tc_wait_cycles.load();
+    // rows of the g map below the forward pass's 32-row tiles stay 0
+    const int r0 = (pair->H - 2 * (m / 2) + 31) / 32 * 32;
     DIA_CK(cudaMemsetAsync(amax, 0, 16, s));
+    if (r0 < T.Hp) DIA_CK(cudaMemsetAsync(G + (size_t)r0 * T.Wp, 0, (size_t)(T.Hp - r0) * T.Wp * 4, s));
     DIA_CK(launch_prep_kpad(theta, m, c.ki.kp, c.nb, c.kpad, s));
-    DIA_CK(launch_tc_forward(c.dp.ref, c.dp.img, c.dp.H, c.dp.W, c.dp.ld, m, c.kpad, c.ki.kp, D,
-                             status, s, g_tc_wait_cycles.load()));
-    DIA_CK(launch_tc_grad_eval(c.ea, m, D, G, amax, parts, red_size(m * m), T.rows / 2, status, s));
-    DIA_CK(launch_reduce(parts, T.rows, red_size(m * m), c.red, nullptr, s));
+    DIA_CK(launch_tc_forward_gmap(c.ea, m, c.kpad, c.ki.kp, G, T.Wp, T.Hp, parts, np, half, amax,
+                                  status, s, wc));
+    DIA_CK(launch_tc_grad(c.ea.R, c.ea.H, c.ea.W, c.ea.ld, m, G, T.Wp, T.Hp, T.Wp, amax,
+                          parts + (size_t)half * np, np, half, status, wc, s));
+    DIA_CK(launch_reduce(parts, T.rows, np, c.red, nullptr, s));
     DIA_CK(launch_emit_loss_grad(c.red, m, 1, loss_out, grad_out, s));
     int hs = 0;
     DIA_CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     DIA_CK(cudaStreamSynchronize(s));
-    return hs ? DIA_ERR_TIMEOUT : DIA_OK;
+    return tc_status(hs);
 }
 
 dia_status dia_time_eval(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
@@ -741,14 +761,14 @@ dia_status dia_diff_image_tc(const dia_pair *pair, const double *theta, float *d
     dia_status rc = setup(pair, &ls, 0, workspace, workspace_bytes, s, c);
     if (rc != DIA_OK) return rc;
     int *status = (int *)c.red;   // scratch: the reduced-sum slots are unused here
-    DIA_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    DIA_CK(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));
     DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s));
     DIA_CK(launch_tc_forward(c.dp.ref, c.dp.img, c.dp.H, c.dp.W, c.dp.ld, pair->m, c.kpad,
                              c.ki.kp, diff_out, status, s, g_tc_wait_cycles.load()));
     int hs = 0;
     DIA_CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     DIA_CK(cudaStreamSynchronize(s));
-    return hs ? DIA_ERR_TIMEOUT : DIA_OK;
+    return tc_status(hs);
 }
 
 dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_opts *opts_in,

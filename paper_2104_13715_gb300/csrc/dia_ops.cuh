@@ -262,6 +262,16 @@ void precond_window(int H, int W, int m, bool single, int side, int *y0, int *y1
 cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int ld, int m,
                               const float *Kpad, int kp, float *diff_out, int *status,
                               cudaStream_t s, long long wait_cycles = 0);
+// The same pass in loss mode: instead of D, g = dl/dM into gmap (gmap_rows
+// rows of pitch gld, at least the tiles' padded height and width; rows of the
+// tiles past the valid region get 0),
+// partial rows [0, rows) of loss, dL/dB0, pixel count and curvature sums
+// (np = red_size(m*m) doubles each, 0 in the other slots), and max |R|,
+// max |g| (float bits) into amax[0..1] (zeroed by the caller)
+cudaError_t launch_tc_forward_gmap(const EvalArgs &ea, int m, const float *Kpad, int kp,
+                                   float *gmap, int gld, int gmap_rows, double *partials, int np,
+                                   int rows, unsigned *amax, int *status, cudaStream_t s,
+                                   long long wait_cycles = 0);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,

@@ -25,13 +25,13 @@
 // Persistent CTAs (one per SM), warp-specialised: the R window of the next
 // tile arrives by TMA (cp.async.bulk.tensor, 2-D tiled map, zero fill outside
 // the image; cp.async when the rows are not 16-byte aligned or the image is
-// smaller than one 160 x 64 box); warps 0-3 split
-// tile k's window into T[k & 1] (signalled on tfull) and, one tile behind, read the
-// accumulators of the previous tile from tensor memory and write D = I - M
-// (signalled on aempty); warp 4 owns the tensor memory (two 32-column
+// smaller than one 160 x 64 box); warps 0-3 split tile k's window into
+// T[k & 1] (signalled on tfull); warp 8 owns the tensor memory (two 32-column
 // accumulators) and, on one lane, issues each tile's m x (K steps) x 3 MMAs and
-// commits them to tempty (T buffer free) and afull (accumulators ready).  Every
-// wait is bounded and any failed wait aborts the whole CTA.
+// commits them to tempty (T buffer free) and afull (accumulators ready); warps
+// 4-7 read the accumulators back (signalled on aempty) and write D = I - M or,
+// in loss mode, g = dl/dM with the loss sums, their loads issued 8 rows at a
+// time.  Every wait is bounded and any failed wait aborts the whole CTA.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -55,7 +55,9 @@ constexpr int kTcYC = kTcYT / 8;           // 8-row chunks of the window
 constexpr int kTcKC = 12;                  // 16-byte chunks of one Zk_b (>= (NO + YT) / 8 + 1)
 constexpr int kTcMaxM = 31;
 constexpr int kTcProducers = 128;          // warps 0-3
-constexpr int kTcThreads = kTcProducers + 32;
+constexpr int kTcEpi = 128;                // warps 4-7
+constexpr int kTcMmaWarp = 8;
+constexpr int kTcThreads = kTcProducers + kTcEpi + 32;
 
 struct TcSmem {
     float f[kTcYT][kTcXT];                        // next tile's R window (cp.async)
@@ -64,11 +66,12 @@ struct TcSmem {
     uint64_t tfull[2];    // T buffer staged (128 producer arrivals)
     uint64_t tempty[2];   // T buffer read by its MMAs (tcgen05.commit)
     uint64_t afull[2];    // accumulators final (tcgen05.commit)
-    uint64_t aempty[2];   // accumulators read back (128 producer arrivals)
+    uint64_t aempty[2];   // accumulators read back (128 epilogue arrivals)
     uint64_t wfull;       // the TMA window copy landed (1 arrival + 40960 bytes)
+    uint64_t drain;       // every MMA issued has completed
+    double red[4][5];     // loss mode: per epilogue warp loss, dL/dB0, count, curvature sums
     uint32_t tslot;
-    int mma_abort;        // set by the MMA warp when a wait of its own ran out
-    int prod_abort;       // set by a producer (read by the MMA warp's waits)
+    int abort;            // set by any role whose wait ran out (every wait watches it)
 };
 
 // Barrier 1 over the 128 producer threads with an OR reduction of `fail`: every
@@ -121,9 +124,25 @@ struct TcArgs {
     const float *Kpad;   // m rows of kp floats, then B0
     int kp;
     float *diff_out;     // (Hv x Wv) D = I - M
-    int *status;         // set to 1 if a wait ran out
+    int *status;         // [0] 1 if a wait ran out, 2 if a bounds check failed; [1] its index
     int use_tma;         // 1: the window by TMA through `tmap`
     long long wait_cycles;   // limit of each pipeline wait (SM clock cycles)
+    // loss mode (gmap != nullptr; diff_out unused): g = dl/dM into gmap (pitch
+    // gld; 0 where masked and, inside the tiles, outside the valid region),
+    // this CTA's partial row (loss, dL/dB0, pixel count, curvature sums at
+    // their red_size(nk) slots, 0 elsewhere) and max |R|, max |g| into amax
+    float *gmap;
+    int gld;
+    const uint8_t *mask;
+    const float *var, *flat;
+    LossParams lp;
+    double *partials;
+    int np, nk;
+    unsigned *amax;
+    // extents for the kernel's own bounds checks: elements addressable in
+    // R / I / mask / var / flat, in the output (D or g map), partial rows
+    size_t n_img, n_out;
+    int rows;
 };
 
 constexpr uint32_t kTcWindowBytes = kTcYT * kTcXT * 4;
@@ -140,6 +159,14 @@ __device__ __forceinline__ void tc_tma_window(TcSmem &S, const CUtensorMap *tmap
                  : "memory");
 }
 
+__device__ __forceinline__ void tc_set_abort(TcSmem &S, int *status) {
+    *reinterpret_cast<volatile int *>(&S.abort) = 1;
+    atomicExch(status, 1);
+}
+
+// LK < 0: D = I - M; LK = 3 rho + var_model: loss mode for that loss, the
+// per-pixel arithmetic without branches (masked and outside pixels select 0)
+template <int LK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_forward_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -148,7 +175,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int m = a.m, h = m / 2;
     const int nks = (kTcNO + m - 1 + 15) / 16;   // K steps of 16 window rows
 
-    if (warp == 4) {
+    if (warp == kTcMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(su32(&S.tslot)), "r"(64));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -158,12 +185,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&S.tfull[i], kTcProducers);
             mbar_init(&S.tempty[i], 1);
             mbar_init(&S.afull[i], 1);
-            mbar_init(&S.aempty[i], kTcProducers);
+            mbar_init(&S.aempty[i], kTcEpi);
         }
         mbar_init(&S.wfull, 1);
+        mbar_init(&S.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
-        S.mma_abort = 0;
-        S.prod_abort = 0;
+        S.abort = 0;
     }
     // Zk_b[c][t][e] = K[8c + t + e - (NO - 1)][b] (0 outside the kernel)
     for (int i = tid; i < m * kTcKC * 64; i += kTcThreads) {
@@ -180,7 +207,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = S.tslot;
 
-    if (warp == 4) {
+    if (warp == kTcMmaWarp) {
+        // ---- MMA issue (one lane) ----
         if (lane == 0) {
             const uint32_t idesc = tc_idesc(kTcW, kTcNO);
             // A_b (ks): T + ((2 ks) XT + b) 16 bytes; B_b (ks): Zk_b + 2 ks 128 bytes
@@ -191,19 +219,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int k = 0;
             for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++k) {
                 const int buf = k & 1;
-                if (!tc_wait(&S.tfull[buf], (uint32_t)((k >> 1) & 1), &S.prod_abort,
-                             a.wait_cycles) ||
-                    (k >= 2 && !tc_wait(&S.aempty[buf], (uint32_t)(((k - 2) >> 1) & 1),
-                                        &S.prod_abort, a.wait_cycles))) {
-                    *reinterpret_cast<volatile int *>(&S.mma_abort) = 1;
-                    atomicExch(a.status, 1);
-                    // the MMAs already issued (tiles < k) must finish before the
-                    // tensor memory is released: their last commit arrives on
-                    // afull of tile k - 1 (waited with the long limit)
-                    if (k > 0) {
-                        const int never = 0;
-                        tc_wait(&S.afull[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), &never);
-                    }
+                if (!tc_wait(&S.tfull[buf], (uint32_t)((k >> 1) & 1), &S.abort, a.wait_cycles) ||
+                    (k >= 2 && !tc_wait(&S.aempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.abort,
+                                        a.wait_cycles))) {
+                    tc_set_abort(S, a.status);
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
@@ -222,19 +241,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc_commit(&S.tempty[buf]);
                 tc_commit(&S.afull[buf]);
             }
+            // every MMA issued completes before the shared and tensor memory go
+            tc_commit(&S.drain);
+            const int never = 0;
+            tc_wait(&S.drain, 0, &never);
         }
         __syncwarp();
-    } else {
-        // returns false if the accumulators did not arrive
-        auto epilogue = [&](int kk, int tile) {
-            const int buf = kk & 1;
-            bool ok = tc_wait(&S.afull[buf], (uint32_t)((kk >> 1) & 1), &S.mma_abort,
-                              a.wait_cycles);
+    } else if (warp >= kTcProducers / 32) {
+        // ---- epilogue: tensor memory lanes 32 (warp - 4) .. + 31 = output columns ----
+        const int ew = warp - kTcProducers / 32;
+        float gmax = 0.f;
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        bool ok = true;
+        int k = 0;
+        for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++k) {
+            const int buf = k & 1;
+            ok = tc_wait(&S.afull[buf], (uint32_t)((k >> 1) & 1), &S.abort, a.wait_cycles);
             ok = __all_sync(0xffffffffu, ok);
-            if (!ok) return false;
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             uint32_t v[kTcNO];
-            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * kTcNO);
+            const uint32_t ta = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * kTcNO);
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -249,21 +276,106 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(&S.aempty[buf]);
             const int y0 = (tile / a.tiles_x) * kTcNO, x0 = (tile % a.tiles_x) * kTcW;
-            const int x = x0 + 32 * warp + lane;
-            if (x < a.Wv) {
+            const int x = x0 + 32 * ew + lane;
+            const bool xin = x < a.Wv;
+            // 8 rows at a time: every load of the group is issued before the
+            // first is used (pixels outside the valid region read pixel 0)
+            if constexpr (LK >= 0) {
+                LossParams lq = a.lp;
+                lq.rho = LK / 3;
+                lq.var_model = LK % 3;
+                float l = 0.f, gs = 0.f, cnt = 0.f, kr = 0.f, ks = 0.f;
 #pragma unroll
-                for (int ip = 0; ip < kTcNO; ++ip) {
-                    const int y = y0 + kTcNO - 1 - ip;
-                    if (y < a.Hv) {
-                        const float Iv = __ldg(a.I + (size_t)(y + h) * a.ld + (x + h));
-                        a.diff_out[(size_t)y * a.Wv + x] = Iv - (__uint_as_float(v[ip]) + B0);
+                for (int c = 0; c < kTcNO / 8; ++c) {
+                    float Iv[8], vm[8], Fv[8], rv[8];
+                    uint32_t mk[8];
+                    bool in[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int y = y0 + kTcNO - 1 - (8 * c + e);
+                        in[e] = xin && y < a.Hv;
+                        size_t off = in[e] ? (size_t)(y + h) * a.ld + (x + h) : 0;
+                        if (off >= a.n_img) {
+                            tc_report_bad(a.status, 2, off);
+                            off = 0;
+                        }
+                        mk[e] = a.mask ? (uint32_t)a.mask[off] : 1u;
+                        Iv[e] = __ldg(a.I + off);
+                        vm[e] = a.var ? __ldg(a.var + off) : a.lp.var_scalar;
+                        Fv[e] = a.flat ? __ldg(a.flat + off) : 1.0f;
+                        rv[e] = __ldg(a.R + off);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int ip = 8 * c + e;
+                        const int y = y0 + kTcNO - 1 - ip;
+                        const bool use = in[e] && mk[e] != 0;
+                        float g, z, kap;
+                        const float ell = pixel_loss(lq, Iv[e], __uint_as_float(v[ip]) + B0, vm[e],
+                                                     Fv[e], g, z, kap);
+                        const float gv = use ? g : 0.f;
+                        l += use ? ell : 0.f;
+                        gs += gv;
+                        cnt += use ? 1.f : 0.f;
+                        kr = fmaf(use ? kap * rv[e] : 0.f, rv[e], kr);
+                        ks += use ? kap : 0.f;
+                        gmax = fmaxf(gmax, fabsf(gv));
+                        const size_t gi = (size_t)y * a.gld + x;
+                        if (gi < a.n_out)
+                            a.gmap[gi] = gv;
+                        else
+                            tc_report_bad(a.status, 2, gi);
+                    }
+                }
+                acc[0] += l;
+                acc[1] += gs;
+                acc[2] += cnt;
+                acc[3] += kr;
+                acc[4] += ks;
+            } else if (xin) {
+#pragma unroll
+                for (int c = 0; c < kTcNO / 8; ++c) {
+                    float Iv[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int y = y0 + kTcNO - 1 - (8 * c + e);
+                        const size_t off = (size_t)(y + h) * a.ld + (x + h);
+                        Iv[e] = (y < a.Hv && off < a.n_img) ? __ldg(a.I + off) : 0.f;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int ip = 8 * c + e;
+                        const int y = y0 + kTcNO - 1 - ip;
+                        const size_t di = (size_t)y * a.Wv + x;
+                        if (y < a.Hv) {
+                            if (di < a.n_out)
+                                a.diff_out[di] = Iv[e] - (__uint_as_float(v[ip]) + B0);
+                            else
+                                tc_report_bad(a.status, 2, di);
+                        }
                     }
                 }
             }
-            return true;
-        };
+        }
+        if (!ok && lane == 0) tc_set_abort(S, a.status);
+        if constexpr (LK >= 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            }
+            if (lane == 0) {
+                if (gmax > 0.f) atomicMax(a.amax + 1, __float_as_uint(gmax));
+#pragma unroll
+                for (int q = 0; q < 5; ++q) S.red[ew][q] = acc[q];
+            }
+        }
+    } else {
+        // ---- producers: the window of each tile, split into T[k & 1] ----
         const bool vec = ((a.ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.R) & 15) == 0);
         const int ylim = kTcNO + m - 1;   // window rows with a nonzero kernel weight
+        float rmax = 0.f;                 // loss mode: max |R| over the windows
         auto origin = [&](int tile, int &y0, int &x0) {
             y0 = (tile / a.tiles_x) * kTcNO;
             x0 = (tile % a.tiles_x) * kTcW;
@@ -280,17 +392,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
         bool fail = false;
-        int k = 0, prev = -1;
+        int k = 0;
         for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++k) {
             const int buf = k & 1;
             // the window has landed (TMA: the transaction count of wfull; cp.async:
             // each thread's own copies, then everyone's at the barrier)
             if (a.use_tma)
-                fail = fail || !tc_wait(&S.wfull, (uint32_t)(k & 1), &S.mma_abort, a.wait_cycles);
+                fail = fail || !tc_wait(&S.wfull, (uint32_t)(k & 1), &S.abort, a.wait_cycles);
             else
                 cp_async_wait<0>();
             if (k >= 2 && !fail)
-                fail = !tc_wait(&S.tempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.mma_abort,
+                fail = !tc_wait(&S.tempty[buf], (uint32_t)(((k - 2) >> 1) & 1), &S.abort,
                                 a.wait_cycles);
             if (producers_any(fail)) {
                 fail = true;
@@ -302,7 +414,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int yc = u / kTcXT, x = u % kTcXT;
                 __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) split_bf16(S.f[8 * yc + e][x], hi[e], lo[e]);
+                for (int e = 0; e < 8; ++e) {
+                    const float rv = S.f[8 * yc + e][x];
+                    rmax = fmaxf(rmax, fabsf(rv));
+                    split_bf16(rv, hi[e], lo[e]);
+                }
                 *reinterpret_cast<uint4 *>(&S.t[buf][0][yc][x][0]) = *reinterpret_cast<const uint4 *>(hi);
                 *reinterpret_cast<uint4 *>(&S.t[buf][1][yc][x][0]) = *reinterpret_cast<const uint4 *>(lo);
             }
@@ -322,10 +438,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc_prefetch(S.f, a.R, a.H, a.W, a.ld, y0, x0, ylim, vec);
                 }
             }
-            if (prev >= 0 && !epilogue(k - 1, prev)) fail = true;
-            prev = tile;
         }
-        if (!fail && prev >= 0 && !epilogue(k - 1, prev)) fail = true;
         cp_async_wait<0>();
         // after a failure, the last window requested must land (or its wait run
         // out) before the CTA's shared memory is released
@@ -333,14 +446,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int never = 0;
             tc_wait(&S.wfull, (uint32_t)((tma_issued - 1) & 1), &never);
         }
-        if (fail) {
-            *reinterpret_cast<volatile int *>(&S.prod_abort) = 1;
-            if (lane == 0) atomicExch(a.status, 1);
+        if (fail && lane == 0) tc_set_abort(S, a.status);
+        if (a.gmap != nullptr) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+            if (lane == 0 && rmax > 0.f) atomicMax(a.amax, __float_as_uint(rmax));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 4)
+    if (a.gmap != nullptr && (int)blockIdx.x < a.rows) {
+        double *out = a.partials + (size_t)blockIdx.x * a.np;
+        const int c0 = red_count(a.nk);
+        for (int k = tid; k < a.np; k += kTcThreads) {
+            int q = -1;
+            if (k == 0) q = 0;
+            else if (k == a.nk + 1) q = 1;
+            else if (k >= c0 && k < c0 + 3) q = 2 + (k - c0);
+            double t = 0.0;
+            if (q >= 0)
+                for (int w = 0; w < 4; ++w) t += S.red[w][q];
+            out[k] = t;
+        }
+    }
+    if (warp == kTcMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64));
 }
 
@@ -364,10 +493,59 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
+static cudaError_t tc_forward_launch(TcArgs &a, const float *R, int H, int W, int ld, int m,
+                                     cudaStream_t s, int rows);
+
 cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int ld, int m,
                               const float *Kpad, int kp, float *diff_out, int *status,
                               cudaStream_t s, long long wait_cycles) {
     if (m < 1 || m > kTcMaxM || (m & 1) == 0) return cudaErrorInvalidValue;
+    TcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.I = I;
+    a.Kpad = Kpad;
+    a.kp = kp;
+    a.diff_out = diff_out;
+    a.status = status;
+    a.wait_cycles = wait_cycles > 0 ? wait_cycles : kTcWaitCycles;
+    a.n_out = (size_t)(H - 2 * (m / 2)) * (W - 2 * (m / 2));
+    return tc_forward_launch(a, R, H, W, ld, m, s, 0);
+}
+
+cudaError_t launch_tc_forward_gmap(const EvalArgs &ea, int m, const float *Kpad, int kp,
+                                   float *gmap, int gld, int gmap_rows, double *partials, int np,
+                                   int rows, unsigned *amax, int *status, cudaStream_t s,
+                                   long long wait_cycles) {
+    const int hv = ea.H - 2 * (m / 2);
+    if (m < 1 || m > kTcMaxM || (m & 1) == 0 || !gmap || !partials || !amax || rows < 1 ||
+        gld < ((ea.W - 2 * (m / 2) + kTcW - 1) / kTcW) * kTcW ||
+        gmap_rows < (hv + kTcNO - 1) / kTcNO * kTcNO)
+        return cudaErrorInvalidValue;
+    TcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.I = ea.I;
+    a.Kpad = Kpad;
+    a.kp = kp;
+    a.status = status;
+    a.wait_cycles = wait_cycles > 0 ? wait_cycles : kTcWaitCycles;
+    a.gmap = gmap;
+    a.gld = gld;
+    a.mask = ea.mask;
+    a.var = ea.var;
+    a.flat = ea.flat;
+    a.lp = ea.lp;
+    a.partials = partials;
+    a.np = np;
+    a.nk = m * m;
+    a.amax = amax;
+    a.n_out = (size_t)gmap_rows * gld;
+    return tc_forward_launch(a, ea.R, ea.H, ea.W, ea.ld, m, s, rows);
+}
+
+// the launch itself: tensor map, tiling, grid (rows > 0: the loss mode's
+// partial rows, those past the grid cleared)
+static cudaError_t tc_forward_launch(TcArgs &a, const float *R, int H, int W, int ld, int m,
+                                     cudaStream_t s, int rows) {
     // 2-D tiled map of R (x innermost): 160 x 64 float boxes, zero fill outside;
     // needs a 16-byte aligned base and row pitch; images smaller than one box
     // take the cp.async path
@@ -386,9 +564,7 @@ cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int 
                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             use_tma = 1;
     }
-    TcArgs a;
     a.R = R;
-    a.I = I;
     a.H = H;
     a.W = W;
     a.ld = ld;
@@ -397,23 +573,48 @@ cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int 
     a.Wv = W - 2 * (m / 2);
     a.tiles_x = (a.Wv + kTcW - 1) / kTcW;
     a.n_tiles = a.tiles_x * ((a.Hv + kTcNO - 1) / kTcNO);
-    a.Kpad = Kpad;
-    a.kp = kp;
-    a.diff_out = diff_out;
-    a.status = status;
     a.use_tma = use_tma;
-    a.wait_cycles = wait_cycles > 0 ? wait_cycles : kTcWaitCycles;
+    a.n_img = (size_t)(H - 1) * ld + W;
     int dev = 0, sms = 1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int smem = tc_smem_bytes();
-    e = cudaFuncSetAttribute(tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int cap = rows > 0 ? (rows < sms ? rows : sms) : sms;
+    const int grid = a.n_tiles < cap ? a.n_tiles : cap;
+    a.rows = rows;
+    int lk = -1;
+    if (a.gmap) {
+        if (a.lp.rho < 0 || a.lp.rho > 2 || a.lp.var_model < 0 || a.lp.var_model > 2)
+            return cudaErrorInvalidValue;
+        lk = 3 * a.lp.rho + a.lp.var_model;
+    }
+    switch (lk) {
+#define DIA_TC_CASE(L)                                                                          \
+    case L:                                                                                     \
+        e = cudaFuncSetAttribute(tc_forward_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 smem);                                                         \
+        if (e == cudaSuccess) tc_forward_kernel<L><<<grid, kTcThreads, smem, s>>>(a, tmap);    \
+        break;
+        DIA_TC_CASE(-1)
+        DIA_TC_CASE(0)
+        DIA_TC_CASE(1)
+        DIA_TC_CASE(2)
+        DIA_TC_CASE(3)
+        DIA_TC_CASE(4)
+        DIA_TC_CASE(5)
+        DIA_TC_CASE(6)
+        DIA_TC_CASE(7)
+        DIA_TC_CASE(8)
+#undef DIA_TC_CASE
+        default: return cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess) return e;
-    const int grid = a.n_tiles < sms ? a.n_tiles : sms;
-    tc_forward_kernel<<<grid, kTcThreads, smem, s>>>(a, tmap);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && rows > grid)
+        e = cudaMemsetAsync(a.partials + (size_t)grid * a.np, 0, (size_t)(rows - grid) * a.np * 8, s);
+    return e;
 }
 
 }  // namespace dia

@@ -66,4 +66,12 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t ph, const int *o
     }
 }
 
+// A kernel's own bounds check failed: status[0] <- code (2 forward pass, 3
+// weight gradient), status[1] <- the low bits of the offending index; the
+// access itself is skipped.
+__device__ __forceinline__ void tc_report_bad(int *status, int code, size_t idx) {
+    atomicExch(status, code);
+    atomicExch(status + 1, (int)(idx & 0x7fffffff));
+}
+
 }  // namespace dia

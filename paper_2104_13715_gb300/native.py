@@ -83,6 +83,7 @@ _SIGS = {
     "dia_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "dia_abi_version": (ctypes.c_int32, []),
     "dia_last_cuda_error": (ctypes.c_int32, []),
+    "dia_last_cuda_error_site": (ctypes.c_int32, []),
     "dia_opts_default": (ctypes.c_int32, [_P(Opts)]),
     "dia_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 6),
     "dia_kernel_variants": (ctypes.c_int32, [ctypes.c_int32]),
@@ -158,7 +159,8 @@ class DiaError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
         name = lib.dia_status_str(status).decode()
-        extra = f" (cuda error {lib.dia_last_cuda_error()})" if status == DIA_ERR_CUDA else ""
+        extra = (f" (cuda error {lib.dia_last_cuda_error()} at site {lib.dia_last_cuda_error_site()})"
+                 if status == DIA_ERR_CUDA else "")
         super().__init__(f"{what}: {name}{extra}")
 
 

@@ -70,15 +70,16 @@ def test_descriptor_offsets_stay_in_their_arrays():
 
 
 # ---------------------------------------------------------------------------
-# The weight-gradient kernel (dia_tc_grad.cu): tiles of GI x GJ of g, the R
-# window in the same chunked layout (GYC chunks of 8 rows, GXT columns) read
-# as an MN-major A operand, the g tile as a K-major B operand.
-GI, GJ, GXT, GYC = 64, 128, 160, 12
+# The weight-gradient kernel (dia_tc_grad.cu): tiles of GI x GJ of g as the
+# K-major A operand, the R window (GWY rows x GWX columns, chunks of 8 rows)
+# as the MN-major B operand whose start moves by one column per kernel column
+# b, and the epilogue's diagonal sums by warp shuffles.
+GI, GJ, GWY, GWX = 128, 64, 160, 96
 
 
 def _operand_mn(buf, start, lbo, sbo, rows, cols):
     """An MN-major operand (rows = M or N, cols = K): core matrices of 8 K
-    rows of 16 bytes, each row holding 8 consecutive M elements; element
+    rows of 16 bytes, each row holding 8 consecutive M / N elements; element
     (n, k) at start + (n // 8) SBO + (k // 8) LBO + (k % 8) 16 B + (n % 8) 2 B."""
     n = np.arange(rows)[:, None]
     k = np.arange(cols)[None, :]
@@ -86,51 +87,66 @@ def _operand_mn(buf, start, lbo, sbo, rows, cols):
     return buf[idx]
 
 
+def _grad_operands(Wwin, g):
+    """The two stage arrays in float16-element units: the window T[y/8][x][y%8]
+    and the g tile [i/8][j/8][i%8][j%8]."""
+    T = Wwin.reshape(GWY // 8, 8, GWX).transpose(0, 2, 1).ravel()
+    Gs = g.reshape(GI // 8, 8, GJ // 8, 8).transpose(0, 2, 1, 3).ravel()
+    return T, Gs
+
+
+def _epilogue_diagonals(P, m):
+    """The epilogue warps' sums: warp w, lane L holds v[c] = P[32w + L][32w + c]
+    (c < 64); lane a adds, in order of c, the value lane c - a holds at c when
+    0 <= c - a < 32.  Returns the per-warp sums [w][a] for a < m."""
+    out = np.zeros((4, m))
+    for w in range(4):
+        v = P[32 * w:32 * w + 32, 32 * w:32 * w + 64]
+        for a in range(m):
+            for c in range(64):
+                src = c - a
+                if 0 <= src < 32:
+                    out[w, a] += v[src, c]
+    return out
+
+
 @pytest.mark.parametrize("m", [1, 3, 7, 13, 25, 31])
 def test_gradient_operands_and_diagonal_sums_give_the_correlation(m):
     """dK[a][b] = sum_{i,j} g[i][j] W[i + a][j + b] from the kernel's operands:
-    P_b = A_b B^T with A_b the MN-major window shifted by b columns (16 b
-    bytes) and B the K-major g tile, summed over K steps of 16; then
-    dK[a][b] = sum_i P_b[i + a][i]."""
+    P_b = A B_b^T with A the K-major g tile and B_b the MN-major window moved
+    by b columns (16 b bytes), summed over K steps of 16; then the epilogue's
+    shuffle sums along the diagonals y - i = a of each warp's 32 rows."""
     rng = np.random.default_rng(m)
-    Wwin = rng.normal(size=(GYC * 8, GXT))           # the window W[y][x]
+    Wwin = rng.normal(size=(GWY, GWX))
     g = rng.normal(size=(GI, GJ))
-    # T[yc][x][e] = W[8 yc + e][x] (one split), followed by the other split and
-    # the g tile so that rows of A beyond the window stay in the buffer
-    T = np.zeros((GYC, GXT, 8))
-    for yc in range(GYC):
-        for e in range(8):
-            T[yc, :, e] = Wwin[8 * yc + e]
-    # g tile K-major: [i / 8][j / 8][i % 8][j % 8]
-    Gs = np.zeros((GI // 8, GJ // 8, 8, 8))
-    for i in range(GI):
-        for j in range(GJ):
-            Gs[i // 8, j // 8, i % 8, j % 8] = g[i, j]
-    buf = np.concatenate([T.ravel(), np.full(T.size, np.nan), Gs.ravel(), Gs.ravel()])
-    gbase = 2 * T.size
+    T, Gs = _grad_operands(Wwin, g)
     dK = np.zeros((m, m))
     for b in range(m):
-        P = np.zeros((128, GI))
+        P = np.zeros((GI, GWY))
         for ks in range(GJ // 16):
-            A = _operand_mn(buf, b * 8 + ks * 128, 64, GXT * 8, 128, 16)   # (y, j)
-            B = _operand(buf, gbase + ks * 128, 64, (GJ // 8) * 64, GI, 16)   # (i, j)
-            P += np.nan_to_num(A) @ B.T
-        for a in range(m):
-            dK[a, b] = sum(P[i + a, i] for i in range(GI))
+            A = _operand(Gs, ks * 128, 64, (GJ // 8) * 64, GI, 16)              # (i, j)
+            B = _operand_mn(T, (16 * ks + b) * 8, 64, GWX * 8, GWY, 16)          # (y, x)
+            P += A @ B.T
+        dK[:, b] = _epilogue_diagonals(P, m).sum(axis=0)
     ref = np.array([[np.sum(g * Wwin[a:a + GI, b:b + GJ]) for b in range(m)] for a in range(m)])
     np.testing.assert_allclose(dK, ref, rtol=1e-12, atol=1e-9)
 
 
-def test_gradient_descriptors_stay_in_shared_memory():
-    """Every byte the gradient kernel's descriptors reach lies inside its
-    operand arrays: A rows 96..127 of the second split run into the g tile
-    (ignored rows), the last column shift and K step stay inside a row."""
-    t_split = GYC * GXT * 16                       # bytes of one window split
-    g_bytes = 2 * GI * GJ * 2
+def test_gradient_descriptors_and_accumulators_stay_in_bounds():
+    """Every element the gradient kernel's descriptors reach lies inside its
+    own split array, every window row a diagonal needs is multiplied, and the
+    epilogue's tensor-memory columns stay inside their accumulator buffer."""
     m = 31
-    last_a = t_split + (m - 1) * 16 + (GJ // 16 - 1) * 256 + 15 * GXT * 16 + 128 + 127
-    assert last_a < 2 * t_split + g_bytes
-    last_b = g_bytes // 2 + (GJ // 16 - 1) * 256 + (GI // 8 - 1) * (GJ // 8) * 128 + 128 + 127
-    assert last_b < g_bytes
-    # the columns a K step reads: b + 16 ks + 15 < GXT
-    assert (m - 1) + 16 * (GJ // 16 - 1) + 15 < GXT
+    nks = GJ // 16
+    last_b = (16 * (nks - 1) + (m - 1)) * 8 + (GWY // 8 - 1) * GWX * 8 + 64 + 7 * 8 + 7
+    assert last_b < (GWY // 8) * GWX * 8
+    last_a = (nks - 1) * 128 + (GI // 8 - 1) * (GJ // 8) * 64 + 64 + 7 * 8 + 7
+    assert last_a < GI * GJ
+    assert GI - 1 + m - 1 < GWY and GJ - 1 + m - 1 < GWX
+    # lane rows 32w .. 32w + 31 need columns up to 32w + 31 + m - 1 < 32w + 64
+    assert 31 + m - 1 < 64 and 32 * 3 + 63 < GWY
+    # accumulator buffers at 0 and 256, 160 columns each, 512 allocated
+    assert 256 + GWY <= 512
+    # shared memory: two stages of (g hi/lo, window hi/lo) + float64 sums
+    stage = 2 * GI * GJ * 2 + 2 * GWY * GWX * 2
+    assert 2 * stage + 4 * 31 * 32 * 8 + 128 <= 232448
