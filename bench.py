@@ -278,7 +278,8 @@ def _config(args, d):
             "optimizer": "Adam -> L-BFGS (Gauss-Newton preconditioned, library defaults)"}
 
 
-def oracle_check(nat, d, R, I, m, spec, opts, mask, var, ws, stream, out_plain, th_init):
+def oracle_check(nat, d, R, I, m, spec, opts, mask, var, ws, stream, out_plain, th_init,
+                 out_tc=None):
     """K, B0 and difference-image errors of the fit against the FP64 oracle's
     optimum theta*: theta* = theta_gpu + one Newton step with the oracle's
     exact FP64 Hessian, on the mask the fit itself returned (its clip
@@ -308,7 +309,14 @@ def oracle_check(nat, d, R, I, m, spec, opts, mask, var, ws, stream, out_plain, 
     sumK = abs(ref[:-1].sum())
     th_pl = out_plain["theta"].cpu().numpy()
     gi = np.max(np.abs(g_ini))
-    return {"err_K": float(np.max(np.abs(th[:-1] - ref[:-1])) / sumK),
+    tc = {}
+    if out_tc is not None:
+        th_tc = out_tc["theta"].cpu().numpy()
+        tc = {"tc_K_err_rel_sumK": float(np.max(np.abs(th_tc[:-1] - ref[:-1])) / sumK),
+              "tc_B0_err_rel_sky": float(abs(th_tc[-1] - ref[-1]) / sky),
+              "tc_D_err_rel_maxI": float(np.max(np.abs(out_tc["diff"].cpu().numpy() - D_ref)) /
+                                         np.max(np.abs(d["I"])))}
+    return {**tc, "err_K": float(np.max(np.abs(th[:-1] - ref[:-1])) / sumK),
             "err_B0": float(abs(th[-1] - ref[-1]) / sky),
             "err_D": float(np.max(np.abs(D - D_ref)) / sig_med),
             "err_D_rel_maxI": float(np.max(np.abs(D - D_ref)) / np.max(np.abs(d["I"]))),
@@ -549,6 +557,41 @@ def run_ours(args, rank, world, local_rank):
              "fits_per_s": n_pl / (ms_pl / 1e3), "evals_per_fit": ev_pl / n_pl,
              "what": "the same fit, optimiser iterations launched one by one (use_graph = 0)"}
 
+    # the same fits with both contractions on the tensor cores (dia_set_eval_form)
+    tc_form, out_tc = None, None
+    if not args.no_tc_form and m <= 31 and "bg_degree" not in d["loss"]:
+        nat.set_eval_form(nat.EVAL_TC)
+        try:
+            ws_tc = nat.workspace(H, W, m, clip=clip, device=dev)
+            step_tc = lambda: nat.fit(R, I, m, spec, opts, mask=mask, var=var, ws=ws_tc,
+                                      stream=stream, want_diff=True)
+            step_tc()
+            torch.cuda.synchronize(dev)
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n_tc, ev_tc, l_tc = max(1, min(args.steps, 3)), 0, 0
+            q0.record(stream)
+            for _ in range(n_tc):
+                out_tc = step_tc()
+                ev_tc += out_tc["info"]["evals"]
+                l_tc += out_tc["info"]["kernel_launches"]
+            q1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_tc = q0.elapsed_time(q1)
+            flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+            t_tc = nat.time_eval(R, I, m, th0, spec, mask=mask, var=var, reps=args.kernel_evals,
+                                 flush=flush, ws=ws_tc, stream=stream)
+            del flush, ws_tc
+        finally:
+            nat.set_eval_form(nat.EVAL_FP32)
+        tc_form = {"value": ev_tc / (ms_tc / 1e3), "unit": "evals/s",
+                   "fits_per_s": n_tc / (ms_tc / 1e3), "evals_per_fit": ev_tc / n_tc,
+                   "eval_ms": t_tc, "eval_ms_fp32": t_eval * 1e3,
+                   "gpu_launches_per_fit": l_tc / n_tc, "status": out_tc["info"]["status"],
+                   "what": "the same fits with dia_set_eval_form(DIA_EVAL_TC): forward pass "
+                           "(split bf16) with the g map and loss sums in its epilogue, weight "
+                           "gradient (split fp16) on the tensor cores; eval_ms from "
+                           "dia_time_eval as for the roofline"}
+
     # error vs the FP64 oracle: one Newton step (exact FP64 Hessian) from the
     # fitted theta on the fit's own final mask gives the oracle's optimum
     # theta* to second order; K, B0 and D are compared with it (outside the
@@ -556,7 +599,10 @@ def run_ours(args, rank, world, local_rank):
     err = None
     if rank == 0 and not args.no_oracle_check:
         err = oracle_check(nat, d, R, I, m, spec, opts, mask, var, ws, stream, out_pl,
-                           th0.cpu().numpy())
+                           th0.cpu().numpy(), out_tc)
+        if tc_form is not None:
+            for k in ("tc_K_err_rel_sumK", "tc_B0_err_rel_sky", "tc_D_err_rel_maxI"):
+                tc_form[k[3:]] = err.pop(k, None)
         plain["K_err_rel_sumK"] = err.pop("plain_K_err_rel_sumK", None)
 
     batch_sub = None
@@ -574,6 +620,7 @@ def run_ours(args, rank, world, local_rank):
             "kernel_tile": {**nat.kernel_variant_desc(m), "variant": tuned.get("variant")},
             "fits_per_s": fits_per_s,
             "vs_plain": value / plain["value"], "plain": plain, "batch_subset": batch_sub,
+            "tc_form": tc_form,
             "evals_per_fit": evals_all / (args.steps * world),
             "adam_off": adam_off,
             "fit_info": {k: last.get(k) for k in ("status", "adam_iters", "lbfgs_iters", "evals",
@@ -753,7 +800,9 @@ def run_reference_batch(args, rank, world):
 
 def run_precision_study(args):
     """Precision study: the FP32 fused path with float64 cross-block
-    accumulation against the pure-float32 accumulation form, on the 2048^2
+    accumulation against the pure-float32 accumulation form and the
+    tensor-core evaluation form (split bf16 forward, split fp16 weight
+    gradient, float64 across tiles), on the 2048^2
     high-dynamic-range field (m = 21, CCD negative log-likelihood).  For each
     form: fit, then K, B0 and difference-image errors against the FP64
     oracle's Newton optimum (polished from the float64 form's theta), and the
@@ -775,14 +824,17 @@ def run_precision_study(args):
     th_start[:-1] *= 1.0 + 0.3 * rng.uniform(-1, 1, m * m)
     _, g_or = oracle.loss_grad(d["R"], d["I"], m, th_start, ospec)
     forms = {}
-    for mode, label in ((nat.ACCUM_FP64, "fp32_pixels_fp64_accumulation"),
-                        (nat.ACCUM_FP32, "pure_fp32_accumulation")):
+    for mode, form, label in ((nat.ACCUM_FP64, nat.EVAL_FP32, "fp32_pixels_fp64_accumulation"),
+                              (nat.ACCUM_FP32, nat.EVAL_FP32, "pure_fp32_accumulation"),
+                              (nat.ACCUM_FP64, nat.EVAL_TC, "tensor_core_split_precision")):
         nat.set_accumulation(mode)
+        nat.set_eval_form(form)
         try:
             _, g = nat.loss_grad(R, I, m, torch.from_numpy(th_start), spec)
             out = nat.fit(R, I, m, spec, nat.default_opts())
         finally:
             nat.set_accumulation(nat.ACCUM_FP64)
+            nat.set_eval_form(nat.EVAL_FP32)
         forms[label] = {"theta": out["theta"].cpu().numpy(), "diff": out["diff"].cpu().numpy(),
                         "info": out["info"],
                         "grad_err": float(np.max(np.abs(g.cpu().numpy() - g_or)) /
@@ -801,7 +853,6 @@ def run_precision_study(args):
             "diff_err_rel_maxI": float(np.max(np.abs(f["diff"] - D_ref)) / np.max(np.abs(d["I"]))),
             "grad_err_rel_at_start": f["grad_err"],
             "evals": f["info"]["evals"], "reason": f["info"]["reason"]}
-    res["tensor_core_split_tf32_form"] = "not built"
     print(json.dumps({"precision_study": name, "H": d["R"].shape[0], "W": d["R"].shape[1],
                       "m": m, "loss": "gauss", "variance": "ccd", "results": res,
                       "oracle": f"FP64 Newton polish from the float64-accumulation fit, "
@@ -1083,6 +1134,8 @@ def main():
                          "(--kernel-only)")
     ap.add_argument("--tc-forward", action="store_true",
                     help="time the forward pass on CUDA cores and on tensor cores")
+    ap.add_argument("--no-tc-form", action="store_true",
+                    help="skip the tensor-core evaluation form's fits in the default run")
     ap.add_argument("--tc-eval", action="store_true",
                     help="time the loss+gradient evaluation on CUDA cores and on tensor cores")
     ap.add_argument("--s10-study", type=int, default=0,

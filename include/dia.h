@@ -252,6 +252,27 @@ int32_t dia_kernel_variants(int32_t m);
 #define DIA_ACCUM_FP32 1
 dia_status dia_set_accumulation(int32_t mode);
 int32_t dia_get_accumulation(void);
+
+/* Form of the gradient-mode evaluations (loss and dL/dtheta, Eq. 8 / Eq. 13)
+ * of dia_loss_grad, dia_fit and dia_time_eval:
+ *   DIA_EVAL_FP32 (default) -- the fused float32 CUDA-core kernels;
+ *   DIA_EVAL_TC -- both contractions on the tensor cores, the kernels of
+ *     dia_loss_grad_tc (split-precision products, float64 across tiles),
+ *     wherever they apply: m <= 31, constant background, one kernel
+ *     (bg_degree = kernel_degree = 0); elsewhere the float32 form runs.
+ * While DIA_EVAL_TC is set, dia_workspace_size and dia_pair_workspace_size
+ * include its g map (the valid region padded to multiples of 128), two
+ * partial rows per SM and a status word: size the workspace after choosing
+ * the form.  dia_loss_grad then waits on its stream to read the status word;
+ * a bounded wait of a tensor-core kernel that ran out is reported as
+ * DIA_ERR_TIMEOUT (by dia_fit at its end).  The optimiser, the
+ * preconditioner, sigma clipping and the outputs are the same in both forms.
+ * Process-wide; not safe to change while another host thread launches work.
+ * Returns DIA_ERR_ARG for any other value. */
+#define DIA_EVAL_FP32 0
+#define DIA_EVAL_TC 1
+dia_status dia_set_eval_form(int32_t form);
+int32_t dia_get_eval_form(void);
 /* Streaming form of the fused evaluation for small kernels (m = 1, 3, 5: the
  * memory-bound end of the kernel-size sweep of Sec. 5.3, where each pixel
  * costs 2 m^2 FMAs against 8-17 bytes of input).  Enabled (1, default), the
@@ -334,20 +355,24 @@ dia_status dia_diff_image_tc(const dia_pair *pair, const double *theta, float *d
                              void *workspace, size_t workspace_bytes, void *stream);
 
 /* One loss + gradient evaluation with both contractions on the tensor cores
- * (tcgen05.mma, sm_103a): the forward pass of dia_diff_image_tc (split bf16)
- * gives D = I - M; a pass over the valid region forms the loss and g = dl/dM
- * (float32, the same pixel terms as dia_loss_grad); the weight gradient
- * dL/dK[a][b] = sum_i P_b[i + a][i], P_b[y][i] = sum_j W[y][j + b] g[i][j]
- * over 64 x 128 tiles of g and their 96 x 160 R windows W, is one GEMM per
- * kernel column b on the tensor cores with g and R scaled by powers of two and
- * split into float16 hi + lo (three products, float32 accumulation in tensor
- * memory), then sums along the diagonals (float32 per tile, float64 across
- * tiles).  Same arguments and outputs as dia_loss_grad; constant background,
- * one kernel (bg_degree = kernel_degree = 0) and m <= 31, else
- * DIA_ERR_UNSUPPORTED.  The workspace is dia_tc_workspace_size(H, W, ld, m)
- * bytes (the evaluation workspace plus the difference image, the g map and
- * two partial rows per SM).  Synchronous: waits on `stream` and returns
- * DIA_ERR_TIMEOUT if a bounded wait of a tensor-core kernel ran out. */
+ * (tcgen05.mma, sm_103a).  The forward pass of dia_diff_image_tc (split bf16)
+ * forms, in its epilogue, the loss terms and g = dl/dM (float32, the same
+ * pixel terms as dia_loss_grad; 0 where masked) into a g map padded to whole
+ * tiles, with max |R| and max |g|; the weight gradient
+ * dL/dK[a][b] = sum_i P_b[i][i + a], P_b[i][y] = sum_j g[i][j] W[y][j + b],
+ * over 128 x 64 tiles of g and their 160 x 96 R windows W, is one GEMM per
+ * kernel column b (M = 128 tile rows, N = 160 window rows) with g and R
+ * scaled by powers of two and split into float16 hi + lo (three products,
+ * float32 accumulation in tensor memory), then sums along the diagonals
+ * (float32 per tile and column, float64 across tiles).  Same arguments and
+ * outputs as dia_loss_grad; constant background, one kernel (bg_degree =
+ * kernel_degree = 0) and m <= 31, else DIA_ERR_UNSUPPORTED.  The workspace
+ * is dia_tc_workspace_size(H, W, ld, m) bytes (the evaluation workspace plus
+ * the g map and two partial rows per SM).  Synchronous: waits on `stream` and
+ * returns DIA_ERR_TIMEOUT if a bounded wait of a tensor-core kernel ran out,
+ * DIA_ERR_CUDA with dia_last_cuda_error() = -2 / -3 if a kernel's own bounds
+ * check failed.  dia_set_eval_form(DIA_EVAL_TC) makes dia_loss_grad and
+ * dia_fit use the same kernels. */
 size_t dia_tc_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m);
 dia_status dia_loss_grad_tc(const dia_pair *pair, const dia_loss_spec *loss, const double *theta,
                             double *loss_out, double *grad_out, void *workspace,

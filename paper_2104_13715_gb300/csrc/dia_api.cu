@@ -42,6 +42,13 @@ std::atomic<int> g_accumulation{DIA_ACCUM_FP64};
 std::atomic<int> g_small_kernel{1};
 // limit of the tensor-core kernel's pipeline waits (dia_set_tc_wait_cycles; 0 = default)
 std::atomic<long long> g_tc_wait_cycles{0};
+// form of the gradient-mode evaluations (dia_set_eval_form)
+std::atomic<int> g_eval_form{DIA_EVAL_FP32};
+
+// the tensor-core evaluation serves these pairs (else the float32 form runs)
+bool tc_form_applies(int m, int bg_degree, int kdeg) {
+    return g_eval_form.load() == DIA_EVAL_TC && m <= kTcGradMaxM && bg_degree == 0 && kdeg == 0;
+}
 
 #define DIA_CK(expr)                               \
     do {                                           \
@@ -61,10 +68,21 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 struct Layout {
     size_t state, sel, hist, red, partials, theta, trial, grad, glo, m1, m2, dir, pg, S, Y, PY, SY,
         YPY, pdiag, pc_args, pc_part, pc_A64, pc_X64, pc_P, kpad, mask, stage_R, stage_I, stage_var, stage_flat, stage_mask, stage_diff, stage_out,
-        total;
+        tc_G, tc_parts, tc_misc, total;
     int G, n_tiles, tiles_x, np, n, kp;
     int pc_chunks;   // chunk partials the preconditioner's Hessian sum may use
+    // tensor-core evaluation form: its g map (Hp x Wp, padded to whole tiles of
+    // both kernels), tc_rows partial rows (half from each kernel), max |R|,
+    // max |g| and the status word
+    int tc, tc_Hp, tc_Wp, tc_rows;
 };
+
+int device_sms() {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
 
 // Preconditioner window of a spatially varying kernel: the whole valid region
 // (the coefficient kernels are only told apart by the variation of eta^p xi^q
@@ -86,7 +104,7 @@ void svk_precond_window(int H, int W, int m, int n, int *y0, int *y1, int *x0, i
 int n_coef_of(int kdeg) { return n_background(kdeg); }
 
 bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInfo &ki, Layout &L,
-                 int kdeg = 0) {
+                 int kdeg = 0, int tc = 0) {
     const int h = m / 2, Hv = H - 2 * h, Wv = W - 2 * h;
     const int nc = n_coef_of(kdeg);
     L.tiles_x = (Wv + kTW - 1) / kTW;
@@ -163,15 +181,16 @@ bool make_layout(int H, int W, int ld, int m, int clip, int mem, const KernelInf
         L.stage_R = L.stage_I = L.stage_var = L.stage_flat = L.stage_mask = L.stage_diff =
             L.stage_out = 0;
     }
+    // last, so that the other offsets do not depend on the evaluation form
+    L.tc = tc;
+    L.tc_Hp = (Hv + 127) / 128 * 128;
+    L.tc_Wp = (Wv + 127) / 128 * 128;
+    L.tc_rows = tc ? 2 * device_sms() : 0;
+    L.tc_G = tc ? take((size_t)L.tc_Hp * L.tc_Wp * 4) : 0;
+    L.tc_parts = tc ? take((size_t)L.tc_rows * L.np * 8) : 0;
+    L.tc_misc = tc ? take(16) : 0;
     L.total = o;
     return true;
-}
-
-int device_sms() {
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
 }
 
 std::mutex g_attr_mu;
@@ -214,6 +233,11 @@ struct Ctx {
     int kdeg, nc;   // spatially varying kernel: degree and coefficient kernels (0, 1: constant)
     SvkArgs sv;
     int svk_grid;   // grid of the spatially varying kernel's evaluations
+    int tc;         // gradient-mode evaluations on the tensor cores (dia_set_eval_form)
+    float *tc_G;
+    double *tc_parts;
+    unsigned *tc_amax;
+    int *tc_status;
 };
 
 // Picks the streaming small-kernel form (dia_small.cu) for the gradient-mode
@@ -231,7 +255,24 @@ cudaError_t choose_small(Ctx &c, const EvalArgs &ea) {
     return cudaSuccess;
 }
 
+// The tensor-core evaluation: max |R|, max |g| cleared, the forward pass in
+// loss mode (g map, loss sums), the weight-gradient kernel; partial rows in
+// c.tc_parts.  Both kernels return at once when ea.done_flag is set.
+cudaError_t launch_tc_eval(const Ctx &c, const EvalArgs &ea, cudaStream_t s) {
+    const int m = c.dp.m, half = c.L.tc_rows / 2;
+    const long long wc = g_tc_wait_cycles.load();
+    cudaError_t e = cudaMemsetAsync(c.tc_amax, 0, 8, s);
+    if (e != cudaSuccess) return e;
+    e = launch_tc_forward_gmap(ea, m, c.kpad, c.ki.kp, c.tc_G, c.L.tc_Wp, c.L.tc_Hp, c.tc_parts,
+                               c.L.np, half, c.tc_amax, c.tc_status, s, wc, ea.done_flag);
+    if (e != cudaSuccess) return e;
+    return launch_tc_grad(ea.R, ea.H, ea.W, ea.ld, m, c.tc_G, c.L.tc_Wp, c.L.tc_Hp, c.L.tc_Wp,
+                          c.tc_amax, c.tc_parts + (size_t)half * c.L.np, c.L.np, half,
+                          c.tc_status, wc, s, ea.done_flag);
+}
+
 cudaError_t launch_grad(const Ctx &c, const EvalArgs &ea, cudaStream_t s) {
+    if (c.tc) return launch_tc_eval(c, ea, s);
     if (c.kdeg > 0) return launch_eval_svk(ea, c.sv, c.dp.m, kModeGrad, c.svk_grid, s);
     if (c.small_grid > 0) return launch_eval_small(ea, c.dp.m, c.ki.kp, c.L.np, c.small_grid, s);
     return launch_eval(c.ki, kModeGrad, ea, c.grid, s);
@@ -244,7 +285,32 @@ cudaError_t launch_fwd(const Ctx &c, const EvalArgs &ea, cudaStream_t s) {
 }
 
 int grad_grid(const Ctx &c) {
+    if (c.tc) return c.L.tc_rows;
     return c.kdeg > 0 ? c.svk_grid : (c.small_grid > 0 ? c.small_grid : c.grid);
+}
+
+// the partial rows the gradient-mode evaluation writes
+double *grad_partials(const Ctx &c) { return c.tc ? c.tc_parts : c.partials; }
+
+// kernels one gradient-mode evaluation launches
+int grad_launches(const Ctx &c) { return c.tc ? 2 : 1; }
+
+// after a tensor-core evaluation: its status word (waits on the stream)
+dia_status tc_eval_status(const Ctx &c, cudaStream_t s) {
+    if (!c.tc) return DIA_OK;
+    int hs[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(hs, c.tc_status, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        g_last_cuda_site = __LINE__;
+        return DIA_ERR_CUDA;
+    }
+    if (hs[0] == 0) return DIA_OK;
+    if (hs[0] == 1) return DIA_ERR_TIMEOUT;
+    g_last_cuda = -hs[0];
+    g_last_cuda_site = __LINE__;
+    return DIA_ERR_CUDA;
 }
 
 dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void *workspace,
@@ -263,7 +329,8 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     c.kdeg = pair->kernel_degree;
     c.nc = n_coef_of(c.kdeg);
     if (c.nc * pair->m * pair->m + n_background(pair->bg_degree) > kMaxN) return DIA_ERR_UNSUPPORTED;
-    make_layout(pair->H, pair->W, pair->ld, pair->m, clip, pair->mem, c.ki, c.L, c.kdeg);
+    make_layout(pair->H, pair->W, pair->ld, pair->m, clip, pair->mem, c.ki, c.L, c.kdeg,
+                loss && tc_form_applies(pair->m, pair->bg_degree, c.kdeg) ? 1 : 0);
     if (!workspace || ws_bytes < c.L.total || ((uintptr_t)workspace % kAlign) != 0)
         return DIA_ERR_WORKSPACE;
     c.ws = (char *)workspace;
@@ -364,6 +431,26 @@ dia_status setup(const dia_pair *pair, const dia_loss_spec *loss, int clip, void
     c.ob.P = nullptr;
     c.ob.ldp = pc_ldp(c.nc * pair->m * pair->m + c.nb);
     DIA_CK(choose_small(c, c.ea));
+    c.tc = c.L.tc;
+    c.tc_G = nullptr;
+    c.tc_parts = nullptr;
+    c.tc_amax = nullptr;
+    c.tc_status = nullptr;
+    if (c.tc) {
+        c.small_grid = 0;
+        c.tc_G = (float *)(c.ws + c.L.tc_G);
+        c.tc_parts = (double *)(c.ws + c.L.tc_parts);
+        c.tc_amax = (unsigned *)(c.ws + c.L.tc_misc);
+        c.tc_status = (int *)(c.ws + c.L.tc_misc + 8);
+        DIA_CK(cudaMemsetAsync(c.ws + c.L.tc_misc, 0, 16, s));
+        // rows of the g map below the forward pass's 32-row tiles stay 0
+        const int r0 = (H - 2 * h + 31) / 32 * 32;
+        if (r0 < c.L.tc_Hp)
+            DIA_CK(cudaMemsetAsync(c.tc_G + (size_t)r0 * c.L.tc_Wp, 0,
+                                   (size_t)(c.L.tc_Hp - r0) * c.L.tc_Wp * 4, s));
+        DIA_CK(tc_forward_prepare(a.lp.rho, a.lp.var_model));
+        DIA_CK(tc_grad_prepare());
+    }
     return DIA_OK;
 }
 
@@ -397,7 +484,7 @@ void append(std::string &k, const T &v) {
 cudaError_t enqueue_iteration(const Ctx &c, const EvalArgs &ea, const StepArgs &sa, cudaStream_t s) {
     cudaError_t e = launch_grad(c, ea, s);
     if (e != cudaSuccess) return e;
-    e = launch_reduce(c.partials, grad_grid(c), c.L.np, c.red, &c.st->done, s, ea.acc32);
+    e = launch_reduce(grad_partials(c), grad_grid(c), c.L.np, c.red, &c.st->done, s, ea.acc32);
     if (e != cudaSuccess) return e;
     return launch_step(sa, s);
 }
@@ -415,6 +502,9 @@ dia_status get_graph(const Ctx &c, const EvalArgs &ea, const StepArgs &sa, int i
     append(key, c.small_grid);
     append(key, c.svk_grid);
     append(key, c.sv);
+    append(key, c.tc);
+    append(key, c.tc_G);
+    append(key, c.L.tc_rows);
     append(key, c.ki);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it)
@@ -507,6 +597,14 @@ dia_status dia_set_accumulation(int32_t mode) {
 
 int32_t dia_get_accumulation(void) { return g_accumulation.load(); }
 
+dia_status dia_set_eval_form(int32_t form) {
+    if (form != DIA_EVAL_FP32 && form != DIA_EVAL_TC) return DIA_ERR_ARG;
+    g_eval_form.store(form);
+    return DIA_OK;
+}
+
+int32_t dia_get_eval_form(void) { return g_eval_form.load(); }
+
 dia_status dia_set_small_kernel(int32_t enable) {
     if (enable != 0 && enable != 1) return DIA_ERR_ARG;
     g_small_kernel.store(enable);
@@ -560,7 +658,7 @@ size_t dia_workspace_size(int32_t H, int32_t W, int32_t ld, int32_t m, int32_t c
     KernelInfo ki;
     if (!kernel_info(m, &ki)) return 0;
     Layout L;
-    make_layout(H, W, ld, m, clip != 0, mem, ki, L);
+    make_layout(H, W, ld, m, clip != 0, mem, ki, L, 0, tc_form_applies(m, 0, 0) ? 1 : 0);
     return L.total;
 }
 
@@ -572,7 +670,8 @@ size_t dia_pair_workspace_size(const dia_pair *pair, int32_t clip) {
     if (!kernel_info(pair->m, &ki)) return 0;
     Layout L;
     make_layout(pair->H, pair->W, pair->ld, pair->m, clip != 0, pair->mem, ki, L,
-                pair->kernel_degree);
+                pair->kernel_degree,
+                tc_form_applies(pair->m, pair->bg_degree, pair->kernel_degree) ? 1 : 0);
     return L.total;
 }
 
@@ -587,9 +686,9 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss, const 
     if (rc != DIA_OK) return rc;
     DIA_CK(launch_prep_kpad(theta, pair->m, c.ki.kp, c.nb, c.kpad, s, c.nc));
     DIA_CK(launch_grad(c, c.ea, s));
-    DIA_CK(launch_reduce(c.partials, grad_grid(c), c.L.np, c.red, nullptr, s, c.ea.acc32));
+    DIA_CK(launch_reduce(grad_partials(c), grad_grid(c), c.L.np, c.red, nullptr, s, c.ea.acc32));
     DIA_CK(launch_emit_loss_grad(c.red, pair->m, c.nb, loss_out, grad_out, s, c.nc));
-    return DIA_OK;
+    return tc_eval_status(c, s);
 }
 
 namespace {
@@ -927,7 +1026,7 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
             } else {
                 for (int i = 0; i < opts.graph_iters; ++i) DIA_CK(enqueue_iteration(c, ea, sa, s));
             }
-            launches += (2LL + kStepLaunches) * opts.graph_iters;
+            launches += (1LL + grad_launches(c) + kStepLaunches) * opts.graph_iters;
             DIA_CK(cudaMemcpyAsync(&hs, c.st, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
             DIA_CK(cudaStreamSynchronize(s));
             if (hs.done) break;
@@ -944,6 +1043,12 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     DIA_CK(cudaMemcpyAsync(&hs, c.st, sizeof(FitState), cudaMemcpyDeviceToHost, s));
     DIA_CK(cudaStreamSynchronize(s));
     if (status == DIA_OK) status = hs.status;
+    {
+        // a tensor-core evaluation whose bounded wait ran out (or whose own
+        // bounds check failed) invalidates the fit
+        const dia_status ts = tc_eval_status(c, s);
+        if (ts != DIA_OK) status = ts;
+    }
 
     // outputs at the accepted theta (Kpad holds it after the pass finished)
     if (diff_out) {

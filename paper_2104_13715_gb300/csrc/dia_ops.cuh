@@ -271,7 +271,11 @@ cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int 
 cudaError_t launch_tc_forward_gmap(const EvalArgs &ea, int m, const float *Kpad, int kp,
                                    float *gmap, int gld, int gmap_rows, double *partials, int np,
                                    int rows, unsigned *amax, int *status, cudaStream_t s,
-                                   long long wait_cycles = 0);
+                                   long long wait_cycles = 0, const int *done = nullptr);
+// sets the tensor-core forward kernels' shared-memory attribute (D mode and
+// the loss mode of (rho, var_model)) so that later launches, also inside a
+// graph capture, need no attribute call
+cudaError_t tc_forward_prepare(int rho, int var_model);
 // P g (and P y_new) for every fit with a direction pending (dia_precond.cu)
 cudaError_t launch_pc_apply(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_init(FitState *st, OptBuffers b, float *Kpad, int mk, int kp, int nb,

@@ -37,6 +37,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "../../include/dia.h"
@@ -143,6 +144,7 @@ struct TcArgs {
     // R / I / mask / var / flat, in the output (D or g map), partial rows
     size_t n_img, n_out;
     int rows;
+    const int *done;     // nullable: nonzero -> return at once (a converged fit's graph)
 };
 
 constexpr uint32_t kTcWindowBytes = kTcYT * kTcXT * 4;
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_forward_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
+    if (a.done != nullptr && *reinterpret_cast<const volatile int *>(a.done) != 0) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = a.m, h = m / 2;
     const int nks = (kTcNO + m - 1 + 15) / 16;   // K steps of 16 window rows
@@ -515,7 +518,7 @@ cudaError_t launch_tc_forward(const float *R, const float *I, int H, int W, int 
 cudaError_t launch_tc_forward_gmap(const EvalArgs &ea, int m, const float *Kpad, int kp,
                                    float *gmap, int gld, int gmap_rows, double *partials, int np,
                                    int rows, unsigned *amax, int *status, cudaStream_t s,
-                                   long long wait_cycles) {
+                                   long long wait_cycles, const int *done) {
     const int hv = ea.H - 2 * (m / 2);
     if (m < 1 || m > kTcMaxM || (m & 1) == 0 || !gmap || !partials || !amax || rows < 1 ||
         gld < ((ea.W - 2 * (m / 2) + kTcW - 1) / kTcW) * kTcW ||
@@ -539,7 +542,45 @@ cudaError_t launch_tc_forward_gmap(const EvalArgs &ea, int m, const float *Kpad,
     a.nk = m * m;
     a.amax = amax;
     a.n_out = (size_t)gmap_rows * gld;
+    a.done = done;
     return tc_forward_launch(a, ea.R, ea.H, ea.W, ea.ld, m, s, rows);
+}
+
+// the shared-memory attribute of tc_forward_kernel<lk>, set once per process
+// (before any graph capture when tc_forward_prepare is called first)
+static cudaError_t tc_forward_attr(int lk) {
+    static std::atomic<int> done[10];
+    std::atomic<int> &d = done[lk + 1];
+    if (d.load()) return cudaSuccess;
+    const int smem = tc_smem_bytes();
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (lk) {
+#define DIA_TC_ATTR(L)                                                                          \
+    case L:                                                                                     \
+        e = cudaFuncSetAttribute(tc_forward_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 smem);                                                         \
+        break;
+        DIA_TC_ATTR(-1)
+        DIA_TC_ATTR(0)
+        DIA_TC_ATTR(1)
+        DIA_TC_ATTR(2)
+        DIA_TC_ATTR(3)
+        DIA_TC_ATTR(4)
+        DIA_TC_ATTR(5)
+        DIA_TC_ATTR(6)
+        DIA_TC_ATTR(7)
+        DIA_TC_ATTR(8)
+#undef DIA_TC_ATTR
+        default: break;
+    }
+    if (e == cudaSuccess) d.store(1);
+    return e;
+}
+
+cudaError_t tc_forward_prepare(int rho, int var_model) {
+    if (rho < 0 || rho > 2 || var_model < 0 || var_model > 2) return cudaErrorInvalidValue;
+    cudaError_t e = tc_forward_attr(-1);
+    return e == cudaSuccess ? tc_forward_attr(3 * rho + var_model) : e;
 }
 
 // the launch itself: tensor map, tiling, grid (rows > 0: the loss mode's
@@ -593,8 +634,7 @@ static cudaError_t tc_forward_launch(TcArgs &a, const float *R, int H, int W, in
     switch (lk) {
 #define DIA_TC_CASE(L)                                                                          \
     case L:                                                                                     \
-        e = cudaFuncSetAttribute(tc_forward_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 smem);                                                         \
+        e = tc_forward_attr(L);                                                                 \
         if (e == cudaSuccess) tc_forward_kernel<L><<<grid, kTcThreads, smem, s>>>(a, tmap);    \
         break;
         DIA_TC_CASE(-1)

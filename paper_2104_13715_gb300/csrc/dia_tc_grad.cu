@@ -33,6 +33,7 @@
 //              warp shuffles: lane a of a warp collects diagonal a, so every
 //              sum has a fixed order and the result does not depend on timing.
 #include <cuda_fp16.h>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 
@@ -100,6 +101,7 @@ struct GradArgs {
     long long wait_cycles;
     size_t n_img, n_g;     // elements addressable in R and in G (bounds checks)
     int rows;              // partial rows
+    const int *done;       // nullable: nonzero -> return at once (a converged fit's graph)
 };
 
 __device__ __forceinline__ void set_abort(GradSmem &S, int *status) {
@@ -110,6 +112,7 @@ __device__ __forceinline__ void set_abort(GradSmem &S, int *status) {
 __global__ void __launch_bounds__(kGThreads, 1) tc_grad_kernel(const GradArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     GradSmem &S = *reinterpret_cast<GradSmem *>(smem_raw);
+    if (a.done != nullptr && *reinterpret_cast<const volatile int *>(a.done) != 0) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = a.m;
     if (warp == kGMmaWarp) {
@@ -335,9 +338,19 @@ __global__ void __launch_bounds__(kGThreads, 1) tc_grad_kernel(const GradArgs a)
 
 int tc_grad_smem_bytes() { return (int)sizeof(GradSmem); }
 
+cudaError_t tc_grad_prepare() {
+    static std::atomic<int> done{0};
+    if (done.load()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(tc_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc_grad_smem_bytes());
+    if (e == cudaSuccess) done.store(1);
+    return e;
+}
+
 cudaError_t launch_tc_grad(const float *R, int H, int W, int ld, int m, const float *G, int gld,
                            int Hp, int Wp, const unsigned *amax, double *partials, int np,
-                           int rows, int *status, long long wait_cycles, cudaStream_t s) {
+                           int rows, int *status, long long wait_cycles, cudaStream_t s,
+                           const int *done) {
     if (m < 1 || m > kGMaxM || (m & 1) == 0 || (gld & 3) != 0 || Hp % kGI != 0 ||
         Wp % kGJ != 0 || gld < Wp || (reinterpret_cast<uintptr_t>(G) & 15) != 0 || rows < 1)
         return cudaErrorInvalidValue;
@@ -359,8 +372,9 @@ cudaError_t launch_tc_grad(const float *R, int H, int W, int ld, int m, const fl
     a.n_img = (size_t)(H - 1) * ld + W;
     a.n_g = (size_t)Hp * gld;
     a.rows = rows;
+    a.done = done;
     const int smem = tc_grad_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(tc_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = tc_grad_prepare();
     if (e != cudaSuccess) return e;
     const int grid = a.n_tiles < rows ? a.n_tiles : rows;
     tc_grad_kernel<<<grid, kGThreads, smem, s>>>(a);

@@ -120,6 +120,8 @@ _SIGS = {
                                        ctypes.c_size_t, ctypes.c_void_p]),
     "dia_get_small_kernel": (ctypes.c_int32, []),
     "dia_get_accumulation": (ctypes.c_int32, []),
+    "dia_set_eval_form": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_get_eval_form": (ctypes.c_int32, []),
     "dia_fisher": (ctypes.c_int32, [_P(Pair), _P(LossSpec), ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, _P(FisherInfo), ctypes.c_void_p,
                                     ctypes.c_size_t, ctypes.c_void_p]),
@@ -179,6 +181,20 @@ ACCUM_FP64, ACCUM_FP32 = 0, 1
 def set_accumulation(mode: int) -> None:
     """dia_set_accumulation: ACCUM_FP64 (default) or ACCUM_FP32 (comparison form)."""
     _check(lib.dia_set_accumulation(int(mode)), "dia_set_accumulation")
+
+
+EVAL_FP32, EVAL_TC = 0, 1
+
+
+def set_eval_form(form: int) -> None:
+    """dia_set_eval_form: EVAL_FP32 (default, fused float32 kernels) or EVAL_TC
+    (both contractions on the tensor cores where they apply).  Size any
+    workspace after choosing the form."""
+    _check(lib.dia_set_eval_form(int(form)), "dia_set_eval_form")
+
+
+def get_eval_form() -> int:
+    return int(lib.dia_get_eval_form())
 
 
 def set_small_kernel(enable: bool) -> None:
