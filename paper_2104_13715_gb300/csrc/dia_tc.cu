@@ -49,6 +49,8 @@ namespace dia {
 namespace {
 
 constexpr int kTcNO = 32;                  // output rows per tile (MMA N)
+constexpr int kTcChains = 1;               // accumulators per tile (kernel column b % kTcChains)
+constexpr int kTcCols = 2 * kTcChains * kTcNO;   // tensor-memory columns: 2 buffers
 constexpr int kTcW = 128;                  // output columns per tile (MMA M)
 constexpr int kTcXT = kTcW + 32;           // R window columns (m <= 33)
 constexpr int kTcYT = 64;                  // R window rows (NO + m - 1 <= 64)
@@ -161,6 +163,54 @@ __device__ __forceinline__ void tc_tma_window(TcSmem &S, const CUtensorMap *tmap
                  : "memory");
 }
 
+// One tile's MMAs: for every kernel column b, NKS K steps x 3 split products
+// into chain b % kTcChains.  Descriptor starts advance by adds on the encoded
+// address field (b: 16 bytes of the window, one Zk_b array; ks: two 8-row
+// chunks of the window, two 128-byte Zk blocks), so the issue loop stays
+// short: at N = 32 the instruction issue, not the tensor pipe, bounds it.
+template <int NKS>
+__device__ __forceinline__ void tc_issue_tile(uint32_t acc0, uint64_t tbuf, uint64_t dz0,
+                                              uint32_t idesc, int m) {
+    // only the low word (encoded start address, LBO) changes; the start field
+    // (address / 16 < 2^14 for shared memory) never carries into the LBO field
+    constexpr uint32_t kTsplit = (uint32_t)(kTcYC * kTcXT * 8 * 2) >> 4;
+    constexpr uint32_t kZsplit = (uint32_t)(kTcMaxM * kTcKC * 64 * 2) >> 4;
+    constexpr uint32_t kZb = (uint32_t)(kTcKC * 64 * 2) >> 4;
+    const uint32_t thi = (uint32_t)(tbuf >> 32), zhi = (uint32_t)(dz0 >> 32);
+    const uint32_t tlo0 = (uint32_t)tbuf, zlo0 = (uint32_t)dz0;
+    auto d64 = [](uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; };
+    for (int b = 0; b < m; ++b) {
+        const uint32_t acc = acc0 + (uint32_t)((b % kTcChains) * kTcNO);
+        const uint32_t tb = tlo0 + (uint32_t)b;          // 16 bytes per column
+        const uint32_t zb = zlo0 + (uint32_t)b * kZb;
+#pragma unroll
+        for (int ks = 0; ks < NKS; ++ks) {
+            const uint32_t ahi = tb + (uint32_t)((2 * ks * kTcXT * 16) >> 4), alo = ahi + kTsplit;
+            const uint32_t bhi = zb + (uint32_t)((2 * ks * 128) >> 4), blo = bhi + kZsplit;
+            if (ks == 0)
+                tc_mma(acc, d64(ahi, thi), d64(bhi, zhi), idesc, b >= kTcChains ? 1 : 0);
+            else
+                tc_mma_acc(acc, d64(ahi, thi), d64(bhi, zhi), idesc);
+            tc_mma_acc(acc, d64(ahi, thi), d64(blo, zhi), idesc);
+            tc_mma_acc(acc, d64(alo, thi), d64(bhi, zhi), idesc);
+        }
+    }
+}
+
+// 32 consecutive tensor-memory columns of this warp's 32 lanes into v
+__device__ __forceinline__ void tc_ld32(uint32_t (&v)[32], uint32_t ta) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                   "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+                   "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]),
+                   "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(ta));
+}
+
 __device__ __forceinline__ void tc_set_abort(TcSmem &S, int *status) {
     *reinterpret_cast<volatile int *>(&S.abort) = 1;
     atomicExch(status, 1);
@@ -180,7 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     if (warp == kTcMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(su32(&S.tslot)), "r"(64));
+                     :: "r"(su32(&S.tslot)), "r"(kTcCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -217,8 +267,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // A_b (ks): T + ((2 ks) XT + b) 16 bytes; B_b (ks): Zk_b + 2 ks 128 bytes
             const uint64_t dt0 = tc_desc(su32(&S.t[0][0][0][0][0]), kTcXT * 16, 128);
             const uint64_t dz0 = tc_desc(su32(&S.zk[0][0][0]), 128, 128);
-            constexpr uint32_t kTbuf = sizeof(S.t[0]), kTsplit = sizeof(S.t[0][0]);
-            constexpr uint32_t kZsplit = sizeof(S.zk[0]), kZb = sizeof(S.zk[0][0]);
+            constexpr uint32_t kTbuf = sizeof(S.t[0]);
+            static_assert(sizeof(S.t[0][0]) == kTcYC * kTcXT * 8 * 2 &&
+                          sizeof(S.zk[0]) == kTcMaxM * kTcKC * 64 * 2 &&
+                          sizeof(S.zk[0][0]) == kTcKC * 64 * 2, "tc_issue_tile strides");
             int k = 0;
             for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++k) {
                 const int buf = k & 1;
@@ -229,18 +281,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t acc = tmem + (uint32_t)(buf * kTcNO);
-                for (int b = 0; b < m; ++b) {
-                    const uint64_t tb = dt0 + ((buf * kTbuf + b * 16) >> 4);
-                    const uint64_t zb = dz0 + ((b * kZb) >> 4);
-                    for (int ks = 0; ks < nks; ++ks) {
-                        const uint64_t ahi = tb + ((2 * ks * kTcXT * 16) >> 4), alo = ahi + (kTsplit >> 4);
-                        const uint64_t bhi = zb + ((2 * ks * 128) >> 4), blo = bhi + (kZsplit >> 4);
-                        tc_mma(acc, ahi, bhi, idesc, (b > 0 || ks > 0) ? 1 : 0);
-                        tc_mma(acc, ahi, blo, idesc, 1);
-                        tc_mma(acc, alo, bhi, idesc, 1);
-                    }
-                }
+                // kernel column b accumulates into chain b % kTcChains: consecutive
+                // columns' products go to independent accumulators
+                const uint32_t acc0 = tmem + (uint32_t)(buf * kTcChains * kTcNO);
+                const uint64_t tbuf = dt0 + ((buf * kTbuf) >> 4);
+                if (nks == 2)
+                    tc_issue_tile<2>(acc0, tbuf, dz0, idesc, m);
+                else if (nks == 3)
+                    tc_issue_tile<3>(acc0, tbuf, dz0, idesc, m);
+                else
+                    tc_issue_tile<4>(acc0, tbuf, dz0, idesc, m);
                 tc_commit(&S.tempty[buf]);
                 tc_commit(&S.afull[buf]);
             }
@@ -263,19 +313,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // the sum of the chains (in chain order; chains past m were never written)
             uint32_t v[kTcNO];
-            const uint32_t ta = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * kTcNO);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                           "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                           "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-                           "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                           "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]),
-                           "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                         : "r"(ta));
+            const uint32_t ta = tmem + ((uint32_t)(32 * ew) << 16) +
+                                (uint32_t)(buf * kTcChains * kTcNO);
+            tc_ld32(v, ta);
             asm volatile("tcgen05.wait::ld.sync.aligned;");
+            for (int c = 1; c < kTcChains && c < m; ++c) {
+                uint32_t w[kTcNO];
+                tc_ld32(w, ta + (uint32_t)(c * kTcNO));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int q = 0; q < kTcNO; ++q)
+                    v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+            }
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(&S.aempty[buf]);
             const int y0 = (tile / a.tiles_x) * kTcNO, x0 = (tile % a.tiles_x) * kTcW;
@@ -473,7 +524,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     }
     if (warp == kTcMmaWarp)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
 }
 
 }  // namespace

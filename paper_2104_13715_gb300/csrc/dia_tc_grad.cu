@@ -22,16 +22,21 @@
 // across tiles in float64.
 //
 // Persistent CTAs (one per SM), warp-specialised, every wait bounded:
-//   warps 5-8  stage tile k's operands (scaled, split) into stage k & 1 and
+//   warps 9-12 stage tile k's operands (scaled, split) into stage k & 1 and
 //              arrive on full[k & 1]; they wait on empty[] before reuse;
-//   warp 4     owns the tensor memory and, on one lane, issues per kernel
+//   warp 8     owns the tensor memory and, on one lane, issues per kernel
 //              column b the 4 K steps x 3 split products into accumulator
-//              buffer (round & 1) (128 lanes x 160 columns), commits it to
-//              afull[], and after the tile's last column commits empty[];
-//   warps 0-3  read each accumulator buffer back (lanes 32w .. 32w + 31 = tile
-//              rows), release it on aempty[], and form the diagonal sums with
-//              warp shuffles: lane a of a warp collects diagonal a, so every
-//              sum has a fixed order and the result does not depend on timing.
+//              buffer (round % 3) (128 lanes x 160 columns; three buffers so
+//              that the products run up to two columns ahead of the read-back),
+//              commits it to afull[], and after the tile's last column
+//              commits empty[];
+//   warps 0-7  read each accumulator buffer back (warps q and q + 4: lanes
+//              32q .. 32q + 31 = tile rows, columns 32q .. 32q + 31 and
+//              32q + 32 .. 32q + 63), release it on aempty[], and form the
+//              diagonal sums with warp shuffles: lane a of a warp collects
+//              diagonal a; warp q hands its sums to warp q + 4 through shared
+//              memory at a named barrier of the pair, so every sum has a fixed
+//              order and the result does not depend on timing.
 #include <cuda_fp16.h>
 #include <atomic>
 #include <cstdint>
@@ -52,12 +57,13 @@ constexpr int kGWY = kGI + 32;         // window rows (MMA N): 128 + m - 1 <= 16
 constexpr int kGWX = kGJ + 32;         // window columns
 constexpr int kGYC = kGWY / 8;
 constexpr int kGMaxM = kTcGradMaxM;
-constexpr int kGEpi = 128;             // warps 0-3
-constexpr int kGMmaWarp = 4;
-constexpr int kGProd = 128;            // warps 5-8
+constexpr int kGEpi = 256;             // warps 0-7: warps q and q + 4 share lanes 32q .. 32q + 31
+constexpr int kGMmaWarp = 8;
+constexpr int kGProd = 128;            // warps 9-12
 constexpr int kGProd0 = kGEpi + 32;
 constexpr int kGThreads = kGProd0 + kGProd;
-constexpr int kGAcc = 256;             // tensor-memory columns per accumulator buffer
+constexpr int kGAcc = kGWY;            // tensor-memory columns per accumulator buffer
+constexpr int kGBufs = 3;              // accumulator buffers (3 x 160 of the 512 columns)
 
 struct GradStage {
     __half g[2][kGI / 8][kGJ / 8][8][8];   // [hi|lo][i/8][j/8][i%8][j%8]
@@ -66,11 +72,12 @@ struct GradStage {
 
 struct GradSmem {
     GradStage st[2];
-    double s64[4][kGMaxM][32];   // per epilogue warp: [b][a] float64 totals
+    double s64[4][kGMaxM][32];   // per lane quarter: [b][a] float64 totals
+    float spart[2][4][32];       // warp q's partial diagonal sums for warp q + 4 (by round parity)
     uint64_t full[2];            // stage staged (kGProd arrivals)
     uint64_t empty[2];           // stage read by its MMAs (tcgen05.commit)
-    uint64_t afull[2];           // accumulator buffer final (tcgen05.commit)
-    uint64_t aempty[2];          // accumulator buffer read back (kGEpi arrivals)
+    uint64_t afull[kGBufs];      // accumulator buffer final (tcgen05.commit)
+    uint64_t aempty[kGBufs];     // accumulator buffer read back (kGEpi arrivals)
     uint64_t drain;              // every MMA issued has completed
     uint32_t tslot;
     int abort;                   // set by any role whose wait ran out
@@ -104,6 +111,20 @@ struct GradArgs {
     const int *done;       // nullable: nonzero -> return at once (a converged fit's graph)
 };
 
+// Named barrier 1 + q over the 64 threads of epilogue warps q and q + 4 with an
+// OR reduction of `pred` (the pair leaves its loop together), and the plain
+// barrier of the pair.
+__device__ __forceinline__ bool pair_any(int q, bool pred) {
+    uint32_t any;
+    asm volatile("{\n\t.reg .pred c, p;\n\tsetp.ne.u32 c, %1, 0;\n\t"
+                 "bar.red.or.pred p, %2, 64, c;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(any) : "r"((uint32_t)pred), "r"(1 + q) : "memory");
+    return any != 0;
+}
+__device__ __forceinline__ void pair_sync(int q) {
+    asm volatile("bar.sync %0, 64;" :: "r"(1 + q) : "memory");
+}
+
 __device__ __forceinline__ void set_abort(GradSmem &S, int *status) {
     *reinterpret_cast<volatile int *>(&S.abort) = 1;
     atomicExch(status, 1);
@@ -124,6 +145,8 @@ __global__ void __launch_bounds__(kGThreads, 1) tc_grad_kernel(const GradArgs a)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&S.full[i], kGProd);
             mbar_init(&S.empty[i], 1);
+        }
+        for (int i = 0; i < kGBufs; ++i) {
             mbar_init(&S.afull[i], 1);
             mbar_init(&S.aempty[i], kGEpi);
         }
@@ -137,52 +160,58 @@ __global__ void __launch_bounds__(kGThreads, 1) tc_grad_kernel(const GradArgs a)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = S.tslot;
 
-    if (warp < 4) {
+    if (warp < 8) {
         // ---- epilogue: diagonal sums of P_b, lane a <- diagonal a ----
         const double unscale = 1.0 / ((double)pow2_scale(__uint_as_float(a.amax[0])) *
                                       (double)pow2_scale(__uint_as_float(a.amax[1])));
+        const int q = warp & 3, half = warp >> 2;   // lane quarter, column half
         uint32_t rc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
             for (int b = 0; b < m; ++b, ++rc) {
-                const uint32_t hb = rc & 1u;
-                ok = tc_wait(&S.afull[hb], (rc >> 1) & 1u, &S.abort, a.wait_cycles);
-                ok = __all_sync(0xffffffffu, ok);
+                const uint32_t hb = rc % kGBufs, use = rc / kGBufs;
+                ok = tc_wait(&S.afull[hb], use & 1u, &S.abort, a.wait_cycles);
+                // both warps of the pair take the same decision (barrier 1 + q)
+                ok = !pair_any(q, !ok);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                // columns 32w .. 32w + 63 hold y - i in [-31, 63] for this warp's rows
-                uint32_t v[64];
-                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) +
-                                    hb * (uint32_t)kGAcc + (uint32_t)(32 * warp);
-#define DIA_LD32(off, o)                                                                      \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                    \
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"                    \
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"   \
-                 : "=r"(v[o + 0]), "=r"(v[o + 1]), "=r"(v[o + 2]), "=r"(v[o + 3]),            \
-                   "=r"(v[o + 4]), "=r"(v[o + 5]), "=r"(v[o + 6]), "=r"(v[o + 7]),            \
-                   "=r"(v[o + 8]), "=r"(v[o + 9]), "=r"(v[o + 10]), "=r"(v[o + 11]),          \
-                   "=r"(v[o + 12]), "=r"(v[o + 13]), "=r"(v[o + 14]), "=r"(v[o + 15]),        \
-                   "=r"(v[o + 16]), "=r"(v[o + 17]), "=r"(v[o + 18]), "=r"(v[o + 19]),        \
-                   "=r"(v[o + 20]), "=r"(v[o + 21]), "=r"(v[o + 22]), "=r"(v[o + 23]),        \
-                   "=r"(v[o + 24]), "=r"(v[o + 25]), "=r"(v[o + 26]), "=r"(v[o + 27]),        \
-                   "=r"(v[o + 28]), "=r"(v[o + 29]), "=r"(v[o + 30]), "=r"(v[o + 31])         \
-                 : "r"(ta + (off)))
-                DIA_LD32(0u, 0);
-                DIA_LD32(32u, 32);
-#undef DIA_LD32
+                // columns 32q + 32 half + c (c < 32) of this warp's rows 32q + lane
+                uint32_t v[32];
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + hb * (uint32_t)kGAcc +
+                                    (uint32_t)(32 * q + 32 * half);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+                               "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                               "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]),
+                               "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                             : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 mbar_arrive(&S.aempty[hb]);
-                // v[c] = P_b[32w + lane][32w + c]; lane a takes from lane c - a
-                // the value of column c (its diagonal is c - (c - a) = a)
-                float acc = 0.f;
+                // v[c] = P_b[32q + lane][32q + 32 half + c]; lane a takes from lane
+                // 32 half + c - a the value of column c (its diagonal is a); four
+                // partial sums (c mod 4) keep the dependent adds short, combined in
+                // a fixed order
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int c = 0; c < 64; ++c) {
-                    const int src = c - lane;
+                for (int c = 0; c < 32; ++c) {
+                    const int src = 32 * half + c - lane;
                     const float t = __shfl_sync(0xffffffffu, __uint_as_float(v[c]), src & 31);
-                    if (src >= 0 && src < 32) acc += t;
+                    if ((unsigned)src < 32u) acc[c & 3] += t;
                 }
-                if (lane < m) S.s64[warp][b][lane] += (double)acc * unscale;
+                const float accs = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+                float* const slot = &S.spart[rc & 1][q][lane];
+                if (half == 0) {
+                    *slot = accs;
+                    pair_sync(q);
+                } else {
+                    pair_sync(q);
+                    if (lane < m) S.s64[q][b][lane] += (double)(*slot + accs) * unscale;
+                }
             }
         }
         if (!ok && lane == 0) set_abort(S, a.status);
@@ -201,11 +230,16 @@ __global__ void __launch_bounds__(kGThreads, 1) tc_grad_kernel(const GradArgs a)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t g0 = su32(&S.st[s].g[0][0][0][0][0]);
-                const uint32_t t0 = su32(&S.st[s].t[0][0][0][0]);
+                // descriptor bases of this stage; per (b, ks) only the encoded
+                // start address advances (by adds: ks 256 B of g, 16 ks + b
+                // window columns of 16 B)
+                const uint64_t dahi = tc_desc(su32(&S.st[s].g[0][0][0][0][0]), 128, (kGJ / 8) * 128);
+                const uint64_t dalo = dahi + (uint64_t)(kGs >> 4);
+                const uint64_t dbhi = tc_desc(su32(&S.st[s].t[0][0][0][0]), 128, kGWX * 16);
+                const uint64_t dblo = dbhi + (uint64_t)(kTs >> 4);
                 for (int b = 0; b < m; ++b, ++rc) {
-                    const uint32_t hb = rc & 1u;
-                    if (!tc_wait(&S.aempty[hb], ((rc >> 1) & 1u) ^ 1u, &S.abort, a.wait_cycles)) {
+                    const uint32_t hb = rc % kGBufs, use = rc / kGBufs;
+                    if (!tc_wait(&S.aempty[hb], (use & 1u) ^ 1u, &S.abort, a.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -215,15 +249,13 @@ __global__ void __launch_bounds__(kGThreads, 1) tc_grad_kernel(const GradArgs a)
                     for (int ks = 0; ks < kGJ / 16; ++ks) {
                         // A: g tile K-major, K core step 128 B, 8-row step (kGJ / 8) 128 B;
                         // B: window MN-major, K core step 8 columns = 128 B, 8-row step kGWX 16 B
-                        const uint32_t ga = g0 + (uint32_t)(ks * 256);
-                        const uint32_t tb = t0 + (uint32_t)((16 * ks + b) * 16);
-                        const uint64_t ahi = tc_desc(ga, 128, (kGJ / 8) * 128);
-                        const uint64_t alo = tc_desc(ga + kGs, 128, (kGJ / 8) * 128);
-                        const uint64_t bhi = tc_desc(tb, 128, kGWX * 16);
-                        const uint64_t blo = tc_desc(tb + kTs, 128, kGWX * 16);
-                        tc_mma(acc, ahi, bhi, idesc, ks > 0 ? 1 : 0);
-                        tc_mma(acc, ahi, blo, idesc, 1);
-                        tc_mma(acc, alo, bhi, idesc, 1);
+                        const uint64_t ao = (uint64_t)(ks * 16), bo = (uint64_t)(16 * ks + b);
+                        if (ks == 0)
+                            tc_mma(acc, dahi, dbhi + bo, idesc, 0);
+                        else
+                            tc_mma_acc(acc, dahi + ao, dbhi + bo, idesc);
+                        tc_mma_acc(acc, dahi + ao, dblo + bo, idesc);
+                        tc_mma_acc(acc, dalo + ao, dbhi + bo, idesc);
                     }
                     tc_commit(&S.afull[hb]);
                 }
@@ -252,28 +284,29 @@ __global__ void __launch_bounds__(kGThreads, 1) tc_grad_kernel(const GradArgs a)
             GradStage &st = S.st[s];
             // g tile: unit (i, jc) = 8 columns of row i, i % 8 fastest (the
             // 16-byte stores of a warp fill 512 contiguous bytes)
-            {
-                float4 gv[8][2];
+#pragma unroll 1
+            for (int q0 = 0; q0 < 8; q0 += 4) {
+                float4 gv[4][2];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int u = p + kGProd * q;
+                for (int qq = 0; qq < 4; ++qq) {
+                    const int q = q0 + qq, u = p + kGProd * q;
                     const int i = 8 * (u >> 6) + (u & 7), jc = (u >> 3) & 7;
                     const size_t gi = (size_t)(y0 + i) * a.gld + x0 + 8 * jc;
                     if (gi + 8 <= a.n_g) {
                         const float4 *src = reinterpret_cast<const float4 *>(a.G + gi);
-                        gv[q][0] = __ldg(src);
-                        gv[q][1] = __ldg(src + 1);
+                        gv[qq][0] = __ldg(src);
+                        gv[qq][1] = __ldg(src + 1);
                     } else {
                         tc_report_bad(a.status, 3, gi);
-                        gv[q][0] = gv[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        gv[qq][0] = gv[qq][1] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int u = p + kGProd * q;
+                for (int qq = 0; qq < 4; ++qq) {
+                    const int q = q0 + qq, u = p + kGProd * q;
                     const int i = 8 * (u >> 6) + (u & 7), jc = (u >> 3) & 7;
-                    const float f[8] = {gv[q][0].x, gv[q][0].y, gv[q][0].z, gv[q][0].w,
-                                        gv[q][1].x, gv[q][1].y, gv[q][1].z, gv[q][1].w};
+                    const float f[8] = {gv[qq][0].x, gv[qq][0].y, gv[qq][0].z, gv[qq][0].w,
+                                        gv[qq][1].x, gv[qq][1].y, gv[qq][1].z, gv[qq][1].w};
                     __align__(16) __half hi[8], lo[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) split_f16(f[e] * sG, hi[e], lo[e]);

@@ -40,6 +40,13 @@ __device__ __forceinline__ void tc_mma(uint32_t taddr, uint64_t a, uint64_t b, u
                  :: "r"(taddr), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// the same MMA accumulating unconditionally (no predicate set-up: the issue
+// loop's cost per MMA bounds small-N products)
+__device__ __forceinline__ void tc_mma_acc(uint32_t taddr, uint64_t a, uint64_t b, uint32_t idesc) {
+    asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;"
+                 :: "r"(taddr), "l"(a), "l"(b), "r"(idesc));
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *b, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(b)), "r"(count));
 }

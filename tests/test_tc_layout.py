@@ -145,8 +145,9 @@ def test_gradient_descriptors_and_accumulators_stay_in_bounds():
     assert GI - 1 + m - 1 < GWY and GJ - 1 + m - 1 < GWX
     # lane rows 32w .. 32w + 31 need columns up to 32w + 31 + m - 1 < 32w + 64
     assert 31 + m - 1 < 64 and 32 * 3 + 63 < GWY
-    # accumulator buffers at 0 and 256, 160 columns each, 512 allocated
-    assert 256 + GWY <= 512
+    # three accumulator buffers of 160 columns at 0, 160, 320 (512 allocated);
+    # the epilogue's loads reach column 160 b + 32 w + 63
+    assert 3 * GWY <= 512 and 2 * GWY + 32 * 3 + 63 < 512
     # shared memory: two stages of (g hi/lo, window hi/lo) + float64 sums
     stage = 2 * GI * GJ * 2 + 2 * GWY * GWX * 2
-    assert 2 * stage + 4 * 31 * 32 * 8 + 128 <= 232448
+    assert 2 * stage + 4 * 31 * 32 * 8 + 2 * 4 * 32 * 4 + 128 <= 232448
