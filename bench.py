@@ -1026,6 +1026,10 @@ def run_kernel_only(args):
                   stream=s)
     ms_k = nat.time_eval(R, I, m, th, spec, mask=mask, var=var, reps=args.steps, flush=flush,
                          ws=ws, stream=s)
+    # the same launches back to back between one pair of events (inputs larger
+    # than L2 stand in for the flush; no launch gaps in the figure)
+    ms_b2b = nat.time_eval(R, I, m, th, spec, mask=mask, var=var, reps=args.steps, flush=None,
+                           ws=ws, stream=s)
     for _ in range(args.warmup):
         nat.loss_grad(R, I, m, th, spec, mask=mask, var=var, ws=ws, stream=s)
     torch.cuda.synchronize(dev)
@@ -1053,6 +1057,12 @@ def run_kernel_only(args):
                       "ms_per_call": ms_call,
                       "gbs_algorithmic": gbs, "hbm_frac": gbs / float(peaks["hbm_gbs"]),
                       "tflops_algorithmic": tfl, "fp32_frac": tfl / peak_tf,
+                      "back_to_back": {"ms_per_launch": ms_b2b,
+                                       "hbm_frac": nbytes / ms_b2b / 1e6 / float(peaks["hbm_gbs"]),
+                                       "fp32_frac": flops / ms_b2b / 1e9 / peak_tf,
+                                       "inputs_vs_l2": f"{nbytes / 2**20:.0f} MiB of inputs, "
+                                                       f"{L2_BYTES / 2**20:.0f} MiB L2",
+                                       "valid": nbytes > L2_BYTES},
                       "bytes_algorithmic": nbytes, "flops_algorithmic": flops,
                       "peaks": f"{peaks['hbm_gbs']} GB/s HBM copy, {peak_tf:.1f} TFLOP/s FP32 "
                                f"({src})"}), flush=True)

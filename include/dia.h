@@ -323,12 +323,15 @@ dia_status dia_loss_grad(const dia_pair *pair, const dia_loss_spec *loss,
 /* Device time of the fused evaluation kernel alone (the gradient-mode
  * launch dia_loss_grad makes: the streaming small-kernel form or the tiled
  * kernel, as dia_set_small_kernel and the pair decide), for roofline figures
- * and the tile autotuner.  The float32 copy of theta is prepared once, then
- * `reps` launches are each bracketed by CUDA events on `stream`; if
- * flush_bytes > 0, flush_buf (device, 16-byte aligned, flush_bytes; make it
+ * and the tile autotuner.  The float32 copy of theta is prepared once, then:
+ * if flush_bytes > 0, `reps` launches are each bracketed by CUDA events on
+ * `stream`, and flush_buf (device, 16-byte aligned, flush_bytes; make it
  * larger than the L2 cache; its contents are only read) is read through L2
  * before every launch, so each launch reads its inputs from HBM and finds no
- * dirty lines to write back.  *ms_out (HOST) receives the mean milliseconds per launch.  The
+ * dirty lines to write back; if flush_bytes == 0, the `reps` launches run back
+ * to back between one pair of events (no launch gaps in the figure; inputs
+ * larger than the L2 cache stand in for the flush).  *ms_out (HOST) receives
+ * the mean milliseconds per launch.  The
  * partial sums are left in the workspace (no reduction runs).  Synchronous.
  * Errors: DIA_ERR_ARG (reps outside 1..100000, flush_bytes without a buffer,
  * bad pair or loss), DIA_ERR_WORKSPACE, DIA_ERR_CUDA. */

@@ -809,8 +809,18 @@ dia_status dia_time_eval(const dia_pair *pair, const dia_loss_spec *loss, const 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     DIA_CK(cudaEventCreate(&e0));
     cudaError_t e = cudaEventCreate(&e1);
+    int reps_timed = 0;
     float total = 0.f;
-    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    if (flush_bytes == 0) {
+        // back to back between one pair of events
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_grad(c, c.ea, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
+        reps_timed = reps;
+    }
+    for (int r = 0; r < reps && e == cudaSuccess && flush_bytes > 0; ++r) {
         if (flush_bytes >= 16) {
             l2_flush_read_kernel<<<device_sms() * 8, 256, 0, s>>>((const uint4 *)flush_buf,
                                                                   flush_bytes / 16, nullptr);
@@ -827,7 +837,7 @@ dia_status dia_time_eval(const dia_pair *pair, const dia_loss_spec *loss, const 
     cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     DIA_CK(e);
-    *ms_out = total / (float)reps;
+    *ms_out = total / (float)(reps_timed > 0 ? reps_timed : reps);
     return DIA_OK;
 }
 

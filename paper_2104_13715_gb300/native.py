@@ -341,7 +341,8 @@ def time_eval(R, I, m, theta, spec: LossSpec, mask=None, var=None, flat=None, re
               flush=None, ws=None, stream=None, bg_degree=0) -> float:
     """dia_time_eval: mean device milliseconds of the fused evaluation kernel
     alone over `reps` launches (CUDA events on the stream), each after
-    reading the uint8 device tensor `flush` (if given) through L2 to evict it."""
+    reading the uint8 device tensor `flush` (if given) through L2 to evict it;
+    without `flush`, the launches run back to back between one pair of events."""
     pair, keep = make_pair(R, I, m, mask, var, flat, bg_degree)
     theta = theta.to(device=R.device, dtype=torch.float64).contiguous()
     ws = ws if ws is not None else workspace(pair.H, pair.W, m, pair.ld, device=R.device)
