@@ -168,3 +168,37 @@ def test_clip_threshold_is_checked_when_clipping(native, kappa):
     o.clip_kappa = kappa
     assert native.lib.dia_fit(ctypes.byref(p), ctypes.byref(spec), ctypes.byref(o), None, None,
                               None, None, None, None, None, 0, None) == native.DIA_ERR_ARG
+
+
+def test_eval_form_switch_and_workspace_growth(native):
+    """dia_set_eval_form takes DIA_EVAL_FP32 / DIA_EVAL_TC only; while the
+    tensor-core form is set, the workspace of a pair it serves (m <= 31,
+    constant background, one kernel) grows by at least the padded g map and
+    keeps its size for m = 33 and for a polynomial background."""
+    import torch
+    assert native.lib.dia_set_eval_form(-1) == native.DIA_ERR_ARG
+    assert native.lib.dia_set_eval_form(2) == native.DIA_ERR_ARG
+    assert native.get_eval_form() == native.EVAL_FP32
+    H, W = 1000, 1100
+    base = native.lib.dia_workspace_size(H, W, W, 25, 0, 0)
+    base33 = native.lib.dia_workspace_size(H, W, W, 33, 0, 0)
+    R = torch.zeros((H, W))
+    p_bg, _ = native.make_pair(R, R, 25, bg_degree=1)
+    base_bg = native.lib.dia_pair_workspace_size(ctypes.byref(p_bg), 0)
+    native.set_eval_form(native.EVAL_TC)
+    try:
+        assert native.get_eval_form() == native.EVAL_TC
+        # 976 x 1076 valid pixels padded to 1024 x 1152
+        assert native.lib.dia_workspace_size(H, W, W, 25, 0, 0) >= base + 1024 * 1152 * 4
+        assert native.lib.dia_workspace_size(H, W, W, 33, 0, 0) == base33
+        assert native.lib.dia_pair_workspace_size(ctypes.byref(p_bg), 0) == base_bg
+    finally:
+        native.set_eval_form(native.EVAL_FP32)
+    assert native.lib.dia_workspace_size(H, W, W, 25, 0, 0) == base
+
+
+def test_error_site_is_zero_before_any_cuda_error(native):
+    """dia_last_cuda_error_site names the library line that caught the last
+    CUDA error of this host thread, 0 while there has been none."""
+    assert native.lib.dia_last_cuda_error() == 0
+    assert native.lib.dia_last_cuda_error_site() == 0
