@@ -996,6 +996,51 @@ def run_tc_eval(args):
                       "results": res, "grad_diff_rel": diff}), flush=True)
 
 
+def run_tc_sweep(args):
+    """Kernel sizes m = 7 .. 31 on a 4096^2 field (the Cauchy-loss workload's
+    recipe with its mask and variance map, the kernel side varied): one
+    loss+gradient evaluation in the fused float32 form and in the tensor-core
+    form (dia_set_eval_form), each launch set timed alone with dia_time_eval
+    after reading 2 x L2 through the cache, and the gradients' difference."""
+    import torch
+    from paper_2104_13715_gb300 import native as nat
+    dev = torch.device("cuda", 0)
+    base = synth.WORKLOADS["ccd4096_m25_cauchy_clip3"]
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    rows = []
+    for m in (7, 11, 15, 19, 25, 31):
+        spec_m = synth.PairSpec(**{**base.__dict__, "m": m})
+        d = synth.make_pair(spec_m, args.seed)
+
+        def up(a, dt):
+            return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+
+        R, I = up(d["R"], torch.float32), up(d["I"], torch.float32)
+        mask, var = up(d.get("mask"), torch.uint8), up(d.get("var"), torch.float32)
+        spec = nat.loss_spec(**_loss_kw(d))
+        th = torch.full((m * m + 1,), 1.0 / (m * m), dtype=torch.float64, device=dev)
+        th[-1] = float(np.median(d["I"]))
+        res = {"m": m}
+        grads = {}
+        for form, name in ((nat.EVAL_FP32, "fp32"), (nat.EVAL_TC, "tc")):
+            nat.set_eval_form(form)
+            try:
+                ws = nat.workspace(*d["R"].shape, m, device=dev)
+                nat.time_eval(R, I, m, th, spec, mask=mask, var=var, reps=2, flush=flush, ws=ws)
+                res[name + "_ms"] = nat.time_eval(R, I, m, th, spec, mask=mask, var=var,
+                                                  reps=args.steps, flush=flush, ws=ws)
+                grads[name] = nat.loss_grad(R, I, m, th, spec, mask=mask, var=var, ws=ws)[1].cpu().numpy()
+                del ws
+            finally:
+                nat.set_eval_form(nat.EVAL_FP32)
+        res["tc_speedup"] = res["fp32_ms"] / res["tc_ms"]
+        res["grad_diff_rel"] = float(np.max(np.abs(grads["tc"] - grads["fp32"])) /
+                                     np.max(np.abs(grads["fp32"])))
+        rows.append(res)
+        print(json.dumps(res), flush=True)
+    print(json.dumps({"tc_sweep": "4096^2 Cauchy, mask, variance map", "rows": rows}), flush=True)
+
+
 def run_kernel_only(args):
     """The fused loss+gradient kernel of the workload at the box-car start:
     its launches alone (dia_time_eval: CUDA events around each launch on the
@@ -1149,6 +1194,8 @@ def main():
                     help="time the forward pass on CUDA cores and on tensor cores")
     ap.add_argument("--no-tc-form", action="store_true",
                     help="skip the tensor-core evaluation form's fits in the default run")
+    ap.add_argument("--tc-sweep", action="store_true",
+                    help="float32 vs tensor-core evaluation over kernel sides 7..31 at 4096^2")
     ap.add_argument("--tc-eval", action="store_true",
                     help="time the loss+gradient evaluation on CUDA cores and on tensor cores")
     ap.add_argument("--s10-study", type=int, default=0,
@@ -1169,6 +1216,9 @@ def main():
         return
     if args.tc_eval:
         run_tc_eval(args)
+        return
+    if args.tc_sweep:
+        run_tc_sweep(args)
         return
     if args.precision_study:
         run_precision_study(args)

@@ -259,7 +259,11 @@ int32_t dia_get_accumulation(void);
  *   DIA_EVAL_TC -- both contractions on the tensor cores, the kernels of
  *     dia_loss_grad_tc (split-precision products, float64 across tiles),
  *     wherever they apply: m <= 31, constant background, one kernel
- *     (bg_degree = kernel_degree = 0); elsewhere the float32 form runs.
+ *     (bg_degree = kernel_degree = 0); elsewhere the float32 form runs;
+ *   DIA_EVAL_AUTO -- the tensor-core form where it applies and was measured
+ *     faster than the float32 form (19 <= m <= 31: 1.27x at m = 19, 1.38x at
+ *     m = 25, 1.9x at m = 31 for a 4096^2 pair; slower below m = 15), the
+ *     float32 form elsewhere.
  * While DIA_EVAL_TC is set, dia_workspace_size and dia_pair_workspace_size
  * include its g map (the valid region padded to multiples of 128), two
  * partial rows per SM and a status word: size the workspace after choosing
@@ -271,6 +275,7 @@ int32_t dia_get_accumulation(void);
  * Returns DIA_ERR_ARG for any other value. */
 #define DIA_EVAL_FP32 0
 #define DIA_EVAL_TC 1
+#define DIA_EVAL_AUTO 2
 dia_status dia_set_eval_form(int32_t form);
 int32_t dia_get_eval_form(void);
 /* Streaming form of the fused evaluation for small kernels (m = 1, 3, 5: the

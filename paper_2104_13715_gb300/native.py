@@ -183,12 +183,13 @@ def set_accumulation(mode: int) -> None:
     _check(lib.dia_set_accumulation(int(mode)), "dia_set_accumulation")
 
 
-EVAL_FP32, EVAL_TC = 0, 1
+EVAL_FP32, EVAL_TC, EVAL_AUTO = 0, 1, 2
 
 
 def set_eval_form(form: int) -> None:
-    """dia_set_eval_form: EVAL_FP32 (default, fused float32 kernels) or EVAL_TC
-    (both contractions on the tensor cores where they apply).  Size any
+    """dia_set_eval_form: EVAL_FP32 (default, fused float32 kernels), EVAL_TC
+    (both contractions on the tensor cores where they apply) or EVAL_AUTO (the
+    tensor cores where they were measured faster: 19 <= m <= 31).  Size any
     workspace after choosing the form."""
     _check(lib.dia_set_eval_form(int(form)), "dia_set_eval_form")
 

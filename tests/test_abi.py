@@ -177,7 +177,7 @@ def test_eval_form_switch_and_workspace_growth(native):
     keeps its size for m = 33 and for a polynomial background."""
     import torch
     assert native.lib.dia_set_eval_form(-1) == native.DIA_ERR_ARG
-    assert native.lib.dia_set_eval_form(2) == native.DIA_ERR_ARG
+    assert native.lib.dia_set_eval_form(3) == native.DIA_ERR_ARG
     assert native.get_eval_form() == native.EVAL_FP32
     H, W = 1000, 1100
     base = native.lib.dia_workspace_size(H, W, W, 25, 0, 0)
@@ -202,3 +202,17 @@ def test_error_site_is_zero_before_any_cuda_error(native):
     CUDA error of this host thread, 0 while there has been none."""
     assert native.lib.dia_last_cuda_error() == 0
     assert native.lib.dia_last_cuda_error_site() == 0
+
+
+def test_auto_eval_form_takes_the_tensor_cores_from_m_19(native):
+    """DIA_EVAL_AUTO sizes the tensor-core regions only for 19 <= m <= 31."""
+    H, W = 600, 640
+    base = {m: native.lib.dia_workspace_size(H, W, W, m, 0, 0) for m in (15, 17, 19, 31)}
+    native.set_eval_form(native.EVAL_AUTO)
+    try:
+        assert native.lib.dia_workspace_size(H, W, W, 15, 0, 0) == base[15]
+        assert native.lib.dia_workspace_size(H, W, W, 17, 0, 0) == base[17]
+        assert native.lib.dia_workspace_size(H, W, W, 19, 0, 0) > base[19]
+        assert native.lib.dia_workspace_size(H, W, W, 31, 0, 0) > base[31]
+    finally:
+        native.set_eval_form(native.EVAL_FP32)

@@ -43,7 +43,7 @@ def _ospec(d):
 def test_form_switch_and_workspace(nat):
     """The switch takes the two forms only; the workspace grows by the
     tensor-core regions for kernels it serves and not for m > 31."""
-    assert nat.lib.dia_set_eval_form(2) == nat.DIA_ERR_ARG
+    assert nat.lib.dia_set_eval_form(3) == nat.DIA_ERR_ARG
     nat.set_eval_form(nat.EVAL_FP32)
     n32 = nat.lib.dia_workspace_size(1000, 1100, 1100, 25, 0, 0)
     n32_big = nat.lib.dia_workspace_size(1000, 1100, 1100, 33, 0, 0)
@@ -145,3 +145,23 @@ def test_unsupported_pairs_keep_the_float32_form(nat):
         nat.set_eval_form(nat.EVAL_FP32)
     assert L1.item() == L0.item()
     np.testing.assert_array_equal(g1.cpu().numpy(), g0.cpu().numpy())
+
+
+@pytest.mark.parametrize("m,expect_tc", [(15, False), (19, True)])
+def test_auto_form_picks_the_tensor_cores_from_m_19(nat, m, expect_tc):
+    """DIA_EVAL_AUTO: dia_loss_grad gives the tensor-core entry's result
+    bit for bit at m = 19 and the float32 form's at m = 15."""
+    spec = nat.loss_spec(**SPECS["gauss-ccd"])
+    d = field(260, 300, m, seed=7 * m)
+    th = theta_start(m, d["I"], np.random.default_rng(m), jitter=0.2)
+    args = (_t(d["R"]), _t(d["I"]), m, torch.from_numpy(th), spec)
+    L_tc, g_tc = nat.loss_grad_tc(*args)
+    L_32, g_32 = nat.loss_grad(*args)
+    nat.set_eval_form(nat.EVAL_AUTO)
+    try:
+        L, g = nat.loss_grad(*args)
+    finally:
+        nat.set_eval_form(nat.EVAL_FP32)
+    Le, ge = (L_tc, g_tc) if expect_tc else (L_32, g_32)
+    assert L.item() == Le.item()
+    np.testing.assert_array_equal(g.cpu().numpy(), ge.cpu().numpy())
