@@ -49,8 +49,7 @@ namespace dia {
 namespace {
 
 constexpr int kTcNO = 32;                  // output rows per tile (MMA N)
-constexpr int kTcChains = 1;               // accumulators per tile (kernel column b % kTcChains)
-constexpr int kTcCols = 2 * kTcChains * kTcNO;   // tensor-memory columns: 2 buffers
+constexpr int kTcCols = 2 * kTcNO;         // tensor-memory columns: two accumulator buffers
 constexpr int kTcW = 128;                  // output columns per tile (MMA M)
 constexpr int kTcXT = kTcW + 32;           // R window columns (m <= 33)
 constexpr int kTcYT = 64;                  // R window rows (NO + m - 1 <= 64)
@@ -164,12 +163,12 @@ __device__ __forceinline__ void tc_tma_window(TcSmem &S, const CUtensorMap *tmap
 }
 
 // One tile's MMAs: for every kernel column b, NKS K steps x 3 split products
-// into chain b % kTcChains.  Descriptor starts advance by adds on the encoded
+// into the accumulator at acc.  Descriptor starts advance by adds on the encoded
 // address field (b: 16 bytes of the window, one Zk_b array; ks: two 8-row
 // chunks of the window, two 128-byte Zk blocks), so the issue loop stays
 // short: at N = 32 the instruction issue, not the tensor pipe, bounds it.
 template <int NKS>
-__device__ __forceinline__ void tc_issue_tile(uint32_t acc0, uint64_t tbuf, uint64_t dz0,
+__device__ __forceinline__ void tc_issue_tile(uint32_t acc, uint64_t tbuf, uint64_t dz0,
                                               uint32_t idesc, int m) {
     // only the low word (encoded start address, LBO) changes; the start field
     // (address / 16 < 2^14 for shared memory) never carries into the LBO field
@@ -180,7 +179,6 @@ __device__ __forceinline__ void tc_issue_tile(uint32_t acc0, uint64_t tbuf, uint
     const uint32_t tlo0 = (uint32_t)tbuf, zlo0 = (uint32_t)dz0;
     auto d64 = [](uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; };
     for (int b = 0; b < m; ++b) {
-        const uint32_t acc = acc0 + (uint32_t)((b % kTcChains) * kTcNO);
         const uint32_t tb = tlo0 + (uint32_t)b;          // 16 bytes per column
         const uint32_t zb = zlo0 + (uint32_t)b * kZb;
 #pragma unroll
@@ -188,7 +186,7 @@ __device__ __forceinline__ void tc_issue_tile(uint32_t acc0, uint64_t tbuf, uint
             const uint32_t ahi = tb + (uint32_t)((2 * ks * kTcXT * 16) >> 4), alo = ahi + kTsplit;
             const uint32_t bhi = zb + (uint32_t)((2 * ks * 128) >> 4), blo = bhi + kZsplit;
             if (ks == 0)
-                tc_mma(acc, d64(ahi, thi), d64(bhi, zhi), idesc, b >= kTcChains ? 1 : 0);
+                tc_mma(acc, d64(ahi, thi), d64(bhi, zhi), idesc, b > 0 ? 1 : 0);
             else
                 tc_mma_acc(acc, d64(ahi, thi), d64(bhi, zhi), idesc);
             tc_mma_acc(acc, d64(ahi, thi), d64(blo, zhi), idesc);
@@ -281,9 +279,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                // kernel column b accumulates into chain b % kTcChains: consecutive
-                // columns' products go to independent accumulators
-                const uint32_t acc0 = tmem + (uint32_t)(buf * kTcChains * kTcNO);
+                const uint32_t acc0 = tmem + (uint32_t)(buf * kTcNO);
                 const uint64_t tbuf = dt0 + ((buf * kTbuf) >> 4);
                 if (nks == 2)
                     tc_issue_tile<2>(acc0, tbuf, dz0, idesc, m);
@@ -313,20 +309,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // the sum of the chains (in chain order; chains past m were never written)
             uint32_t v[kTcNO];
-            const uint32_t ta = tmem + ((uint32_t)(32 * ew) << 16) +
-                                (uint32_t)(buf * kTcChains * kTcNO);
-            tc_ld32(v, ta);
+            tc_ld32(v, tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * kTcNO));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            for (int c = 1; c < kTcChains && c < m; ++c) {
-                uint32_t w[kTcNO];
-                tc_ld32(w, ta + (uint32_t)(c * kTcNO));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                for (int q = 0; q < kTcNO; ++q)
-                    v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
-            }
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(&S.aempty[buf]);
             const int y0 = (tile / a.tiles_x) * kTcNO, x0 = (tile % a.tiles_x) * kTcW;
