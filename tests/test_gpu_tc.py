@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import oracle
-from tests._helpers import field
+from tests._helpers import SPECS, field, ospec, rel_inf, theta_start
 
 pytestmark = pytest.mark.gpu
 
@@ -173,5 +173,57 @@ def test_tc_loss_grad_full_size_and_fp32_agree(nat):
                             mask=_t(d["mask"], torch.uint8), var=_t(d["var"]))
     Lo, go = oracle.loss_grad(d["R"], d["I"], m, th, oracle.LossSpec(rho="cauchy", noise="fixed"),
                               mask=d["mask"], var=d["var"])
+    assert rel_inf(g.cpu().numpy(), go) <= 1e-5
+    assert L.item() == pytest.approx(Lo, rel=1e-5)
+
+
+def test_tc_loss_grad_wait_timeout_aborts_cleanly(nat):
+    """dia_loss_grad_tc with a 300-cycle wait limit: the forward pass's first
+    waits run out and so do the weight-gradient kernel's (its MMA lane drains
+    what it issued, the read-back pairs leave together); the call returns
+    DIA_ERR_TIMEOUT.  With the default limit restored, the next call on the
+    same tensors gives the oracle's gradient."""
+    import ctypes
+    m = 13
+    d = field(300, 420, m, seed=31)
+    spec = SPECS["gauss-ccd"]
+    th = theta_start(m, d["I"], np.random.default_rng(3), jitter=0.2)
+    R, I = _t(d["R"]), _t(d["I"])
+    pair, keep = nat.make_pair(R, I, m)
+    nb = nat.lib.dia_tc_workspace_size(pair.H, pair.W, pair.ld, m)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    thd = torch.from_numpy(th).cuda()
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty(m * m + 1, dtype=torch.float64, device="cuda")
+    sp = nat.loss_spec(**spec)
+    assert nat.lib.dia_set_tc_wait_cycles(300) == 0
+    try:
+        st = nat.lib.dia_loss_grad_tc(ctypes.byref(pair), ctypes.byref(sp),
+                                      ctypes.c_void_p(thd.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                      ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                      nb, None)
+    finally:
+        assert nat.lib.dia_set_tc_wait_cycles(0) == 0
+    assert st == nat.DIA_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    L, g = nat.loss_grad_tc(R, I, m, torch.from_numpy(th), sp)
+    Lo, go = oracle.loss_grad(d["R"], d["I"], m, th, ospec(spec))
+    assert rel_inf(g.cpu().numpy(), go) <= 1e-5
+
+
+def test_tc_loss_grad_with_flat_field_and_mask(nat):
+    """CCD variance with a flat field (v = s0^2 / F^2 + M / (G F)) and a mask
+    through the tensor-core evaluation, against the oracle (1e-5 max norm)."""
+    from tests._helpers import ospec, rel_inf, theta_start
+    m = 21
+    spec = SPECS["gauss-ccd"]
+    d = field(280, 360, m, seed=44)
+    rng = np.random.default_rng(5)
+    flat = rng.uniform(0.85, 1.15, d["R"].shape).astype(np.float32)
+    mask = (rng.random(d["R"].shape) > 0.07).astype(np.uint8)
+    th = theta_start(m, d["I"], rng, jitter=0.3)
+    L, g = nat.loss_grad_tc(_t(d["R"]), _t(d["I"]), m, torch.from_numpy(th), nat.loss_spec(**spec),
+                            mask=_t(mask, torch.uint8), flat=_t(flat))
+    Lo, go = oracle.loss_grad(d["R"], d["I"], m, th, ospec(spec), mask=mask, flat=flat)
     assert rel_inf(g.cpu().numpy(), go) <= 1e-5
     assert L.item() == pytest.approx(Lo, rel=1e-5)
