@@ -20,12 +20,15 @@
 //      window and reused by all QF output rows and all m kernel columns;
 //      K is read from shared memory as warp-uniform (broadcast) float4 loads;
 //   3. epilogue: M stays in registers, the loss terms and g_p are formed in
-//      float32 and g_p is written to a shared-memory tile (never to HBM);
-//   4. backward: with m = NW*KF + RM, warp w owns kernel rows [w*KF, (w+1)*KF)
-//      over the whole tile plus the RM last rows on its own QF-row slice
-//      (equal work per warp); lanes split the columns; each R row window is
-//      reused by every kernel row it feeds, the m column offsets and the
-//      four pixels of the lane;
+//      float32 (a fixed scalar variance with 1/v and sqrt(1/v) formed once per
+//      thread) and g_p is written to a shared-memory tile (never to HBM);
+//   4. backward (SPLIT 0, 1): with m = NW*KF + RM, warp w owns kernel rows
+//      [w*KF, (w+1)*KF) over the whole tile plus the RM last rows on its own
+//      QF-row slice (equal work per warp); lanes split the columns; each R row
+//      window is reused by every kernel row it feeds, the m column offsets and
+//      the four pixels of the lane.  SPLIT 2 (own rows): each warp takes every
+//      kernel row over its own QF output rows, g still in registers, in passes
+//      of about 64 accumulators per lane;
 //   5. dK: per-lane float32 sums over one tile, reduced over the warp by a
 //      halving butterfly and added to per-warp Kahan-compensated float32
 //      shared accumulators; loss sums: per-lane float32 over <= 4096 pixels,
@@ -39,6 +42,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace dia {
@@ -178,6 +182,43 @@ __device__ __forceinline__ float pixel_loss(const LossParams &lp, float I, float
     return ell;
 }
 
+// The pixel loss of a fixed scalar variance (var_model 0, no variance map)
+// with inv_v = 1/v and inv_s = sqrt(1/v) formed once per thread by the same
+// correctly rounded operations: for finite inputs it returns exactly what
+// pixel_loss does (there dv = 0, so dz reduces to -inv_s).
+__device__ __forceinline__ float pixel_loss_fixed(const LossParams &lp, float inv_v, float inv_s,
+                                                  float I, float M, float &g, float &z,
+                                                  float &kappa) {
+    const float r = I - M;
+    z = r * inv_s;
+    const float dz = -inv_s;
+    float rho, rho1, wz;
+    if (lp.rho == 0) {
+        rho = 0.5f * z * z;
+        rho1 = z;
+        wz = 1.f;
+    } else if (lp.rho == 1) {
+        const float c = lp.huber_c, az = fabsf(z);
+        if (az <= c) {
+            rho = 0.5f * z * z;
+            rho1 = z;
+            wz = 1.f;
+        } else {
+            rho = c * (az - 0.5f * c);
+            rho1 = copysignf(c, z);
+            wz = c / az;
+        }
+    } else {
+        const float q = z * z;
+        rho = log1pf(q);
+        wz = 2.0f / (1.0f + q);
+        rho1 = z * wz;
+    }
+    g = rho1 * dz;
+    kappa = wz * inv_v;
+    return rho;
+}
+
 // Asynchronous global -> shared copies (cp.async); a source size below the
 // copy size fills the rest with zeros.
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
@@ -279,9 +320,19 @@ __device__ __forceinline__ int halving_index(int lane, int j) {
     return p;
 }
 
+// Kernel rows per pass of the own-rows backward (SPLIT = 2): about 64 float32
+// dK accumulators per lane, MK rows split into ceil(MK*MK/64) nearly equal passes.
+__host__ __device__ constexpr int own_rows_per_pass(int mk) {
+    return (mk + (mk * mk + 63) / 64 - 1) / ((mk * mk + 63) / 64);
+}
+
 // SPLIT selects how the backward's kernel rows are shared among the warps:
 // 0 = whole rows, ceil(MK/NW) or floor(MK/NW) per warp; 1 = MK = NW*KF + RM
-// with KF whole rows per warp and the RM last rows split by tile-row slices.
+// with KF whole rows per warp and the RM last rows split by tile-row slices;
+// 2 = own rows: each warp takes every kernel row over the QF output rows of
+// its forward pass, with g still in registers, in passes of NQ kernel rows
+// (each R row window then serves up to QF*NQ*MK*4 FMAs; the price is one warp
+// reduction of MK*MK values per tile).
 template <int MK, int NW, int QF, int SPLIT, int F2 = 0>
 struct EvalShape {
     static constexpr int TH = NW * QF;
@@ -292,9 +343,13 @@ struct EvalShape {
     // backward split: MK = NW*KF + RM; warp w owns kernel rows [w*KF, (w+1)*KF)
     // over the whole tile and the RM last rows on its own QF-row slice, so
     // every warp does the same work
-    static constexpr int KF = SPLIT ? MK / NW : (MK + NW - 1) / NW;
-    static constexpr int RM = SPLIT ? MK % NW : 0;
-    static constexpr int QB = KF + RM;                   // dK rows held per lane
+    static constexpr int KF = SPLIT == 2 ? 0 : SPLIT ? MK / NW : (MK + NW - 1) / NW;
+    static constexpr int RM = SPLIT == 1 ? MK % NW : 0;
+    static constexpr int QB = SPLIT == 2 ? MK : KF + RM;   // dK rows summed per warp
+    // own rows: kernel rows per pass, full passes, rows of the last (short) pass
+    static constexpr int NQ = own_rows_per_pass(MK);
+    static constexpr int NPF = MK / NQ;
+    static constexpr int NQL = MK - NPF * NQ;
     static constexpr int NP = red_size(MK * MK);         // partials per CTA
     static constexpr int NT = NW * 32;
     // shared memory layout (bytes)
@@ -312,6 +367,7 @@ struct EvalShape {
     // float64 per-warp {loss, dB0, count, kR^2, k, background moments}
     static constexpr int SZ_D = kAccW * NW * 8;
     // float32 Kahan pairs (sum, compensation) of each warp's QB x MK dK rows
+    // (all MK x MK for the own-rows backward)
     static constexpr int NK = QB * MK;
     static constexpr int OFF_KS = OFF_D + SZ_D;
     static constexpr int SZ_KS = NW * 2 * NK * 4;
@@ -477,6 +533,66 @@ __device__ __forceinline__ void bwd_rows(const float *rrow, const float *g0, con
     }
 }
 
+// Own-rows backward, one pass of NQ kernel rows: dk[j][b] += sum_q sum_p
+// gq[q][p] R[r][x+p+b] with r = j + q rows below rrow (rrow: the R row of the
+// warp's first output row plus the pass's first kernel row, at this lane's
+// pixel column).  Every (j, q) pair with j + q = s uses the window of row s,
+// loaded once; all indices are compile-time, so dk stays in registers.
+template <int MK, int NQ, int QF, int RP, int RWIN>
+__device__ __forceinline__ void own_pass(const float *rrow, const float (&gq)[QF][4],
+                                         float (&dk)[NQ * MK]) {
+#pragma unroll
+    for (int i = 0; i < NQ * MK; ++i) dk[i] = 0.f;
+#pragma unroll
+    for (int s = 0; s < NQ + QF - 1; ++s) {
+        float win[RWIN];
+        load_win<RWIN>(win, rrow + s * RP);
+        // pixel p outer: consecutive FMAs update different accumulators
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+#pragma unroll
+            for (int q = 0; q < QF; ++q) {
+                const int j = s - q;
+                if (j >= 0 && j < NQ) {
+#pragma unroll
+                    for (int b = 0; b < MK; ++b)
+                        dk[j * MK + b] = fmaf(gq[q][p], win[p + b], dk[j * MK + b]);
+                }
+            }
+        }
+    }
+}
+
+// Warp sum of N per-lane values (halving) added to this warp's float32 Kahan
+// pairs sum[i], comp[i] (plain float32 sums with acc32); kidx from
+// halving_index<N>.
+template <int N>
+__device__ __forceinline__ void warp_kahan_add(const float (&v)[N], const int (&kidx)[Halving<N>::H5],
+                                               float *sum, float *comp, int acc32, int lane) {
+    using Hv = Halving<N>;
+    float w1[Hv::H1], w2[Hv::H2], w3[Hv::H3], w4[Hv::H4], w5[Hv::H5];
+    halve<N, 16>(v, w1, lane & 16);
+    halve<Hv::H1, 8>(w1, w2, lane & 8);
+    halve<Hv::H2, 4>(w2, w3, lane & 4);
+    halve<Hv::H3, 2>(w3, w4, lane & 2);
+    halve<Hv::H4, 1>(w4, w5, lane & 1);
+#pragma unroll
+    for (int j = 0; j < Hv::H5; ++j) {
+        const int ix = kidx[j];
+        if (ix >= 0) {
+            float *sm = sum + ix, *cm = comp + ix;
+            if (acc32) {
+                *sm += w5[j];
+            } else {
+                const float y = w5[j] - *cm;
+                const float t = *sm + y;
+                *cm = (t - *sm) - y;
+                *sm = t;
+            }
+        }
+    }
+}
+
 // The fused pass over tiles t_begin, t_begin + t_step, ... < t_end of one
 // pair; the CTA's partial sums (m*m + 5 float64) go to `out`.  Called by
 // the single-pair kernel (tiles strided over the grid) and by the batched
@@ -557,11 +673,29 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     // dK of one tile: per-lane float32 sums over the tile's 4 x TH pixels,
     // reduced over the warp by halving and added (Kahan-compensated float32)
     // to this warp's shared accumulators
-    constexpr int NK = S::NK, NF = Halving<NK>::H5;
+    constexpr int NK = S::NK;
+    constexpr int NKO = SPLIT == 2 ? 1 : NK;   // values of the row-split backward's tile reduction
+    constexpr int NF = Halving<NKO>::H5;
     float *ksum_w = kahan + warp * 2 * NK;
     int kidx[NF];
 #pragma unroll
-    for (int j = 0; j < NF; ++j) kidx[j] = halving_index<NK>(lane, j);
+    for (int j = 0; j < NF; ++j) kidx[j] = halving_index<NKO>(lane, j);
+    // own rows: the reduction index maps of a full pass and of the short last one
+    constexpr int NQ = S::NQ, NQL = S::NQL, NQLH = NQL > 0 ? NQL : 1;
+    constexpr int NFQ = SPLIT == 2 ? Halving<NQ * MK>::H5 : 1;
+    constexpr int NFL = SPLIT == 2 ? Halving<NQLH * MK>::H5 : 1;
+    int kidq[NFQ], kidl[NFL];
+    if constexpr (SPLIT == 2) {
+#pragma unroll
+        for (int j = 0; j < NFQ; ++j) kidq[j] = halving_index<NQ * MK>(lane, j);
+#pragma unroll
+        for (int j = 0; j < NFL; ++j) kidl[j] = halving_index<NQLH * MK>(lane, j);
+    }
+
+    // a fixed scalar variance: 1/v and sqrt(1/v) once per thread
+    const bool scalar_var = args.lp.var_model == 0 && args.var == nullptr;
+    const float sv_inv_v = 1.0f / args.lp.var_scalar;
+    const float sv_inv_s = sqrtf(sv_inv_v);
 
     // ---- 1. R tiles (+ halo) are staged with cp.async, the next tile's copy
     // overlapping the current tile's compute (two buffers)
@@ -720,91 +854,103 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             }
         }
 
-        // ---- 3. epilogue: loss terms, g -> shared tile
+        // ---- 3. epilogue: loss terms, g -> shared tile (two instances: a fixed
+        // scalar variance with its reciprocals from registers, and the general form)
+        auto epilogue = [&](auto sv_tag) {
+            constexpr bool SV = decltype(sv_tag)::value;
 #pragma unroll
-        for (int q = 0; q < QF; ++q) {
-            const int yl = warp * QF + q;
-            const int y = ty0 + yl;
+            for (int q = 0; q < QF; ++q) {
+                const int yl = warp * QF + q;
+                const int y = ty0 + yl;
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int xl = 4 * lane + p;
-                const int x = tx0 + xl;
-                float gval = 0.f;
-                if (y < args.Hv && x < args.Wv) {
-                    const size_t off = (size_t)(y + H2) * args.ld + (x + H2);
-                    const bool use = (args.mask == nullptr) || (args.mask[off] != 0);
-                    const float M = acc[q][p] + (poly ? gt[yl * kTW + xl] : B0);
-                    const float Iv = __ldg(args.I + off);
-                    const float vm = args.var ? __ldg(args.var + off) : args.lp.var_scalar;
-                    const float F = args.flat ? __ldg(args.flat + off) : 1.0f;
-                    float g, z, kap;
-                    const float ell = pixel_loss(args.lp, Iv, M, vm, F, g, z, kap);
-                    if (MODE == kModeGrad) {
-                        if (use) {
-                            const float rc = Rs[(yl + H2) * RP + xl + H2];
-                            lsum += ell;
-                            gsum += g;
-                            cnt += 1.f;
-                            ksum += kap;
-                            kr2sum = fmaf(kap * rc, rc, kr2sum);
-                            gval = g;
+                for (int p = 0; p < 4; ++p) {
+                    const int xl = 4 * lane + p;
+                    const int x = tx0 + xl;
+                    float gval = 0.f;
+                    if (y < args.Hv && x < args.Wv) {
+                        const size_t off = (size_t)(y + H2) * args.ld + (x + H2);
+                        const bool use = (args.mask == nullptr) || (args.mask[off] != 0);
+                        const float M = acc[q][p] + (poly ? gt[yl * kTW + xl] : B0);
+                        const float Iv = __ldg(args.I + off);
+                        float g, z, kap, ell;
+                        if constexpr (SV) {
+                            ell = pixel_loss_fixed(args.lp, sv_inv_v, sv_inv_s, Iv, M, g, z, kap);
+                        } else {
+                            const float vm = args.var ? __ldg(args.var + off) : args.lp.var_scalar;
+                            const float F = args.flat ? __ldg(args.flat + off) : 1.0f;
+                            ell = pixel_loss(args.lp, Iv, M, vm, F, g, z, kap);
                         }
-                    } else {
-                        if (args.diff_out) args.diff_out[(size_t)y * args.Wv + x] = Iv - M;
-                        if (args.mask_out && use && fabsf(z) > args.clip_kappa) args.mask_out[off] = 0;
+                        if (MODE == kModeGrad) {
+                            if (use) {
+                                const float rc = Rs[(yl + H2) * RP + xl + H2];
+                                lsum += ell;
+                                gsum += g;
+                                cnt += 1.f;
+                                ksum += kap;
+                                kr2sum = fmaf(kap * rc, rc, kr2sum);
+                                gval = g;
+                            }
+                        } else {
+                            if (args.diff_out) args.diff_out[(size_t)y * args.Wv + x] = Iv - M;
+                            if (args.mask_out && use && fabsf(z) > args.clip_kappa) args.mask_out[off] = 0;
+                        }
+                    }
+                    if (MODE == kModeGrad) {
+                        // the own-rows backward keeps g in acc; the g tile serves the
+                        // row-split backward and the background moments
+                        if (SPLIT != 2 || poly) gt[yl * kTW + xl] = gval;
+                        if constexpr (SPLIT == 2) acc[q][p] = gval;
                     }
                 }
-                if (MODE == kModeGrad) gt[yl * kTW + xl] = gval;
             }
-        }
+        };
+        if (scalar_var)
+            epilogue(std::true_type{});
+        else
+            epilogue(std::false_type{});
         if (MODE != kModeGrad) {
             __syncthreads();  // the R buffer is refilled two tiles later
             continue;
         }
-        __syncthreads();  // g tile complete
+        if (SPLIT != 2 || poly) __syncthreads();  // g tile complete
         if (poly) bg_moments(bc, args.acc32, gt, QF, ty0, tx0, acc64 + kAccW * warp, warp, lane);
 
         // ---- 4. backward: dK[a][b] += sum_{y,x} g[y][x] R[y+a][x+b]
-        float dk[NK];
-#pragma unroll
-        for (int i = 0; i < NK; ++i) dk[i] = 0.f;
-        const float *gzero = gs + 4 * lane;   // a zero row above the g tile
-        if (KF > 0 && nq == KF)
-            bwd_rows<MK, QB, 0, (KF > 0 ? KF : 1), RP, RWIN, false, TH, PF>(
-                Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 1, dk);
-        else if (KF > 1 && nq == KF - 1)   // SPLIT 0: the warps with one row fewer
-            bwd_rows<MK, QB, 0, (KF > 1 ? KF - 1 : 1), RP, RWIN, false, TH, PF>(
-                Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 2, dk);
-        if (RM > 0) {
-            const int ys = warp * QF;          // this warp's slice of the tile rows
-            bwd_rows<MK, QB, KF, (RM > 0 ? RM : 1), RP, RWIN, true, QF, 0>(
-                Rs + (NW * KF + ys) * RP + 4 * lane, gt + ys * kTW + 4 * lane, gzero,
-                QF + RM - 1, dk);
-        }
-        // ---- 5. warp-reduce this tile's dK and add it to the warp's accumulators
-        {
-            using Hv = Halving<NK>;
-            float w1[Hv::H1], w2[Hv::H2], w3[Hv::H3], w4[Hv::H4], w5[Hv::H5];
-            halve<NK, 16>(dk, w1, lane & 16);
-            halve<Hv::H1, 8>(w1, w2, lane & 8);
-            halve<Hv::H2, 4>(w2, w3, lane & 4);
-            halve<Hv::H3, 2>(w3, w4, lane & 2);
-            halve<Hv::H4, 1>(w4, w5, lane & 1);
-#pragma unroll
-            for (int j = 0; j < NF; ++j) {
-                const int ix = kidx[j];
-                if (ix >= 0) {
-                    float *sm = ksum_w + ix, *cm = ksum_w + NK + ix;
-                    if (args.acc32) {
-                        *sm += w5[j];
-                    } else {
-                        const float y = w5[j] - *cm;
-                        const float t = *sm + y;
-                        *cm = (t - *sm) - y;
-                        *sm = t;
-                    }
-                }
+        if constexpr (SPLIT == 2) {
+            // own rows: the warp's QF output rows, every kernel row, passes of NQ
+            const float *rw = Rs + (warp * QF) * RP + 4 * lane;
+#pragma unroll 1
+            for (int ps = 0; ps < S::NPF; ++ps) {
+                float dq[NQ * MK];
+                own_pass<MK, NQ, QF, RP, RWIN>(rw + ps * NQ * RP, acc, dq);
+                warp_kahan_add<NQ * MK>(dq, kidq, ksum_w + ps * NQ * MK, ksum_w + NK + ps * NQ * MK,
+                                        args.acc32, lane);
             }
+            if constexpr (NQL > 0) {
+                float dl[NQLH * MK];
+                own_pass<MK, NQLH, QF, RP, RWIN>(rw + S::NPF * NQ * RP, acc, dl);
+                warp_kahan_add<NQLH * MK>(dl, kidl, ksum_w + S::NPF * NQ * MK,
+                                          ksum_w + NK + S::NPF * NQ * MK, args.acc32, lane);
+            }
+        } else {
+            float dk[NK];
+#pragma unroll
+            for (int i = 0; i < NK; ++i) dk[i] = 0.f;
+            const float *gzero = gs + 4 * lane;   // a zero row above the g tile
+            if (KF > 0 && nq == KF)
+                bwd_rows<MK, QB, 0, (KF > 0 ? KF : 1), RP, RWIN, false, TH, PF>(
+                    Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 1, dk);
+            else if (KF > 1 && nq == KF - 1)   // SPLIT 0: the warps with one row fewer
+                bwd_rows<MK, QB, 0, (KF > 1 ? KF - 1 : 1), RP, RWIN, false, TH, PF>(
+                    Rs + a_lo * RP + 4 * lane, gt + 4 * lane, gzero, TH + KF - 2, dk);
+            if (RM > 0) {
+                const int ys = warp * QF;          // this warp's slice of the tile rows
+                bwd_rows<MK, QB, KF, (RM > 0 ? RM : 1), RP, RWIN, true, QF, 0>(
+                    Rs + (NW * KF + ys) * RP + 4 * lane, gt + ys * kTW + 4 * lane, gzero,
+                    QF + RM - 1, dk);
+            }
+            // ---- 5. warp-reduce this tile's dK and add it to the warp's accumulators
+            warp_kahan_add<NK>(dk, kidx, ksum_w, ksum_w + NK, args.acc32, lane);
         }
         if (++since_flush == S::FLUSH) {
             flush();
@@ -817,12 +963,13 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
     if (MODE == kModeGrad) {
         if (since_flush > 0) flush();
         __syncthreads();
-        // rows with one owner warp (w, qb < nq(w)); the RM shared rows summed
-        // over the warps' copies in a fixed order
+        // rows with one owner warp (w, qb < nq(w)); the RM shared rows (every
+        // row with the own-rows backward) summed over the warps' copies in a
+        // fixed order
         for (int i = tid; i < MK * MK; i += S::NT) {
             const int a = i / MK, b = i - a * MK;
             double t = 0.0;
-            if (a < MK - RM) {
+            if (SPLIT != 2 && a < MK - RM) {
                 int w = SPLIT ? a / KF : 0;
                 if (!SPLIT) {
                     while (w + 1 < NW && ((w + 1) * MK) / NW <= a) ++w;
@@ -831,7 +978,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
                 const float *kw = kahan + w * 2 * NK;
                 t = (double)kw[qb * MK + b] - (double)kw[NK + qb * MK + b];
             } else {
-                const int qb = KF + (a - (MK - RM));
+                const int qb = SPLIT == 2 ? a : KF + (a - (MK - RM));
                 float t32 = 0.f;
                 for (int w = 0; w < NW; ++w) {
                     const float *kw = kahan + w * 2 * NK;

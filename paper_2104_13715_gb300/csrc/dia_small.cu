@@ -166,41 +166,6 @@ __device__ __forceinline__ void read_window(const float *Rs, int lane, float (&w
     }
 }
 
-// Pixel terms with a fixed scalar variance: 1/v and its square root are the
-// same for every pixel, so they are formed once per thread (the same float32
-// operations as pixel_loss, hoisted: identical results).
-__device__ __forceinline__ float pixel_loss_scalar(const LossParams &lp, float inv_v, float inv_s,
-                                                   float I, float M, float &g, float &kappa) {
-    const float r = I - M;
-    const float z = r * inv_s;
-    const float dz = -inv_s;
-    float rho, rho1, wz;
-    if (lp.rho == 0) {
-        rho = 0.5f * z * z;
-        rho1 = z;
-        wz = 1.f;
-    } else if (lp.rho == 1) {
-        const float c = lp.huber_c, az = fabsf(z);
-        if (az <= c) {
-            rho = 0.5f * z * z;
-            rho1 = z;
-            wz = 1.f;
-        } else {
-            rho = c * (az - 0.5f * c);
-            rho1 = copysignf(c, z);
-            wz = c / az;
-        }
-    } else {
-        const float q = z * z;
-        rho = log1pf(q);
-        wz = 2.0f / (1.0f + q);
-        rho1 = z * wz;
-    }
-    g = rho1 * dz;
-    kappa = wz * inv_v;
-    return rho;
-}
-
 // FAST = 1: the Gaussian loss with a fixed scalar variance (the chi^2 of the
 // memory-bound workloads): a branch-free epilogue with the mask folded into a
 // per-pixel weight w in {0, 1}: z = (I - M)/s, sum w z^2 (loss = half of it),
@@ -390,7 +355,7 @@ __global__ void __launch_bounds__(kSNT, MK <= 1 ? 3 : 2) eval_small_kernel(const
                                     float z, kap;
                                     const float ell =
                                         scalar_var
-                                            ? pixel_loss_scalar(a.lp, sv_inv_v, sv_inv_s, Iv[p], M[p], gv, kap)
+                                            ? pixel_loss_fixed(a.lp, sv_inv_v, sv_inv_s, Iv[p], M[p], gv, z, kap)
                                             : pixel_loss(a.lp, Iv[p], M[p], hv ? Vv[p] : a.lp.var_scalar,
                                                          hf ? Fv[p] : 1.0f, gv, z, kap);
                                     in[NK] += ell;

@@ -7,7 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel side -> list of tile variants (NW warps, QF output rows per warp in the
 # forward pass, PF = 1 to load the next R-row window while the current one is used,
 # SPLIT = backward row split: 0 whole rows ceil/floor per warp, 1 equal work
-# with the MK % NW last rows split by tile-row slices, F2 = 1 for packed float2
+# with the MK % NW last rows split by tile-row slices, 2 own rows (each warp
+# every kernel row over its forward rows, g in registers), F2 = 1 for packed float2
 # FMAs pairing output rows in the forward; 0 if omitted).
 # Variant 0 is the default; the autotuner may pick another at run time.
 VARIANTS = {
@@ -15,18 +16,18 @@ VARIANTS = {
     3: [(8, 4, 0, 0), (8, 2, 0, 0), (8, 8, 0, 0), (4, 4, 0, 0)],
     5: [(8, 2, 0, 0), (8, 4, 0, 0), (8, 8, 0, 0), (4, 4, 0, 0)],
     7: [(8, 4, 0, 0), (8, 8, 0, 0), (8, 4, 0, 0, 1)],
-    9: [(8, 4, 0, 1), (8, 8, 0, 1), (8, 4, 0, 1, 1)],
+    9: [(8, 4, 0, 2, 1), (8, 4, 0, 1), (8, 8, 0, 1), (8, 4, 0, 1, 1), (8, 4, 0, 2)],
     11: [(8, 4, 0, 1, 1), (8, 4, 1, 1), (8, 4, 0, 1), (12, 4, 0, 0)],
-    13: [(12, 4, 1, 1), (12, 4, 0, 1), (13, 4, 0, 0), (12, 4, 1, 1, 1)],
-    15: [(12, 4, 1, 1), (12, 4, 0, 1), (12, 4, 1, 1, 1)],
+    13: [(12, 4, 1, 1), (12, 4, 0, 1), (13, 4, 0, 0), (12, 4, 1, 1, 1), (12, 4, 0, 2, 1)],
+    15: [(12, 4, 0, 2, 1), (12, 4, 1, 1), (12, 4, 0, 1), (12, 4, 1, 1, 1)],
     17: [(8, 4, 0, 1), (8, 4, 1, 1), (8, 4, 1, 1, 1)],
     19: [(8, 4, 1, 1), (8, 4, 0, 1), (10, 4, 0, 0), (8, 4, 1, 1, 1), (8, 4, 0, 1, 1)],
     21: [(8, 4, 0, 0, 1), (8, 4, 0, 0), (8, 4, 1, 0), (7, 4, 0, 0)],
     23: [(8, 4, 0, 0), (8, 4, 1, 0), (8, 4, 1, 0, 1)],
     25: [(12, 4, 1, 1, 1), (12, 4, 0, 1), (12, 4, 1, 1), (13, 4, 0, 0), (12, 2, 0, 1),
          (12, 4, 0, 1, 1), (13, 4, 0, 0, 1)],
-    27: [(9, 4, 0, 0), (9, 4, 1, 0)],
-    29: [(10, 4, 0, 0), (10, 4, 1, 0)],
+    27: [(8, 4, 0, 2, 1), (9, 4, 0, 0), (9, 4, 1, 0)],
+    29: [(8, 4, 0, 2, 1), (10, 4, 0, 0), (10, 4, 1, 0)],
     31: [(8, 4, 0, 0), (8, 4, 1, 0)],
 }
 GROUPS = [[1, 3, 5, 7], [9, 11], [13, 15], [17], [19], [21], [23], [25], [27], [29], [31]]

@@ -9,7 +9,7 @@ from scipy import signal
 
 import oracle
 from paper_2104_13715_gb300 import synth
-from tests._helpers import SPECS, field, ospec
+from tests._helpers import SPECS, field, ospec, theta_start
 
 pytestmark = pytest.mark.gpu
 
@@ -262,3 +262,37 @@ def test_noiseless_transforms_reach_float32_precision(nat):
         eps_b = abs(th[-1] - B0) / B0
         assert eps_p <= 10 * gold["eps_P_max"] and eps_b <= 10 * gold["eps_B0_max"], \
             (name, eps_p, eps_b)
+
+
+
+@pytest.mark.parametrize("name", ["cauchy-fixed", "gauss-fixed", "huber-fixed"])
+def test_scalar_variance_path_is_bitwise_the_map_path(nat, name):
+    """A fixed scalar variance takes 1/v and sqrt(1/v) from registers, formed
+    once per thread; a variance map forms them per pixel with the same
+    correctly rounded operations.  A map filled with the scalar therefore gives
+    the same loss, gradient, fitted theta, evaluation count, clipped mask and
+    difference image, bit for bit, and theta meets the oracle's optimum."""
+    m = 11
+    d = field(230, 210, m, seed=21)
+    rng = np.random.default_rng(21)
+    mask = (rng.random(d["R"].shape) > 0.03).astype(np.uint8)
+    v = 2.7
+    dev = torch.device("cuda")
+    t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    R, I, Mk = t(d["R"]), t(d["I"]), t(mask, torch.uint8)
+    V = torch.full_like(R, v)
+    spec = nat.loss_spec(**{**SPECS[name], "var": v})
+    th0 = torch.from_numpy(theta_start(m, d["I"], rng, jitter=0.3))
+    L1, g1 = nat.loss_grad(R, I, m, th0, spec, mask=Mk)
+    L2, g2 = nat.loss_grad(R, I, m, th0, spec, mask=Mk, var=V)
+    assert L1.item() == L2.item() and torch.equal(g1, g2)
+    opts = nat.default_opts(clip_passes=1, clip_kappa=4.0)
+    a = nat.fit(R, I, m, spec, opts, mask=Mk, want_mask=True)
+    b = nat.fit(R, I, m, spec, opts, mask=Mk, var=V, want_mask=True)
+    assert a["info"]["status"] == 0 and a["info"]["evals"] == b["info"]["evals"]
+    assert torch.equal(a["theta"], b["theta"])
+    assert torch.equal(a["diff"], b["diff"]) and torch.equal(a["mask"], b["mask"])
+    th = a["theta"].cpu().numpy()
+    ref = oracle.newton(d["R"], d["I"], m, th, ospec({**SPECS[name], "var": v}),
+                        mask=a["mask"].cpu().numpy())
+    _check(th, ref, float(np.median(d["I"])))
