@@ -1118,8 +1118,9 @@ def run_kernel_only(args):
 
 def run_m_sweep(args):
     """The kernel-size sweep of the paper's speed tests (Sec. 5.3, a 1000^2
-    crop fitted with kernels of increasing size): a 1000^2 field (lg rho = 1.5
-    per 100^2 px, phi_R = 1, phi_K = 1.5, sky 100, the Sec. 5.2 recipe) fitted
+    crop fitted with kernels of increasing size): a 1000^2 field (--size for
+    another side; lg rho = 1.5 per 100^2 px, phi_R = 1, phi_K = 1.5, sky 100,
+    the Sec. 5.2 recipe) fitted
     with the fixed-variance chi^2 for every odd m in 3..31.  Per m: the fused
     evaluation kernel alone (dia_time_eval, L2 flushed before each launch) in
     algorithmic TFLOP/s and GB/s against the FP32 pipe and the measured HBM
@@ -1133,8 +1134,9 @@ def run_m_sweep(args):
     peak_tf = sms * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     rows = []
+    S = args.size or 1000   # the paper's 1000^2 crop; --size for a larger field
     for m in range(3, 32, 2):
-        spec_p = synth.PairSpec(size=(1000, 1000), n_stars=int(round(10 ** 1.5 * 100)), m=m,
+        spec_p = synth.PairSpec(size=(S, S), n_stars=int(round(10 ** 1.5 * S * S / 1e4)), m=m,
                                 fwhm_ref=2.0 * math.sqrt(2 * math.log(2.0)), kernel_sigma=1.5,
                                 sky=100.0, flux_law="paper", read=5.0, gain=1.0)
         d = synth.make_pair(spec_p, args.seed + m)
@@ -1143,13 +1145,13 @@ def run_m_sweep(args):
         spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
         th = torch.full((m * m + 1,), 1.0 / (m * m), dtype=torch.float64, device=dev)
         th[-1] = float(np.median(d["I"]))
-        ws = nat.workspace(1000, 1000, m, device=dev)
+        ws = nat.workspace(S, S, m, device=dev)
         nat.time_eval(R, I, m, th, spec, reps=3, flush=flush, ws=ws)
         ms = nat.time_eval(R, I, m, th, spec, reps=args.steps, flush=flush, ws=ws)
         h = m // 2
-        npx = (1000 - 2 * h) ** 2
+        npx = (S - 2 * h) ** 2
         tfl = 4.0 * m * m * npx / ms / 1e9
-        gbs = 1000 * 1000 * 8 / ms / 1e6
+        gbs = S * S * 8 / ms / 1e6
         nat.fit(R, I, m, spec, want_diff=False)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -1161,7 +1163,7 @@ def run_m_sweep(args):
                      "form": "streaming small-kernel" if m <= 5 else "tiled",
                      "fit_ms": fit_ms, "fit_evals": out["info"]["evals"],
                      "fit_status": out["info"]["status"]})
-    print(json.dumps({"m_sweep": "1000x1000 chi^2, Sec. 5.3 recipe", "rows": rows,
+    print(json.dumps({"m_sweep": f"{S}x{S} chi^2, Sec. 5.3 recipe", "rows": rows,
                       "peaks": f"{peaks['hbm_gbs']} GB/s HBM copy, {peak_tf:.1f} TFLOP/s FP32 "
                                f"({src})"}), flush=True)
 
@@ -1185,7 +1187,7 @@ def main():
     ap.add_argument("--no-batch-subset", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the fused loss+gradient kernel alone (ncu driver)")
-    ap.add_argument("--size", type=int, default=None, help="image side override (--kernel-only)")
+    ap.add_argument("--size", type=int, default=None, help="image side override (--kernel-only, --m-sweep)")
     ap.add_argument("--variant", type=int, default=None, help="tile variant (--kernel-only)")
     ap.add_argument("--tiled", action="store_true",
                     help="the tiled kernel even where the streaming small-kernel form applies "

@@ -183,6 +183,15 @@ WORKLOADS = {
         size=(4096, 4096), n_stars=60000, m=5, fwhm_ref=2.0, kernel_sigma=0.8,
         scale=1.0, b0=20.0, sky=100.0, read=5.0, gain=1.0,
         loss=dict(rho="gauss", noise="fixed", var=1.0)),
+    # mid-size kernels on the same 4096^2 chi^2 field (kernel-side studies)
+    "ccd4096_m9_chi2": PairSpec(
+        size=(4096, 4096), n_stars=60000, m=9, fwhm_ref=2.0, kernel_sigma=1.2,
+        scale=1.0, b0=20.0, sky=100.0, read=5.0, gain=1.0,
+        loss=dict(rho="gauss", noise="fixed", var=1.0)),
+    "ccd4096_m13_chi2": PairSpec(
+        size=(4096, 4096), n_stars=60000, m=13, fwhm_ref=2.0, kernel_sigma=1.5,
+        scale=1.0, b0=20.0, sky=100.0, read=5.0, gain=1.0,
+        loss=dict(rho="gauss", noise="fixed", var=1.0)),
     # 2048^2 high-dynamic-range field, 21x21 kernel, CCD NLL
     "hdr2048_m21_nll": PairSpec(
         size=(2048, 2048), n_stars=15000, m=21, fwhm_ref=2.0,
