@@ -36,20 +36,6 @@ namespace {
 
 constexpr int kB = kPcB;
 
-// Weight of target pixel q (offset in the pitched image): mask / variance at M = I.
-__device__ __forceinline__ float pc_weight(const PrecondArgs &a, size_t q) {
-    float v;
-    if (a.lp.var_model == 0) {
-        v = a.var ? a.var[q] : a.lp.var_scalar;
-    } else {
-        const float F = a.flat ? a.flat[q] : 1.f, Iv = fmaxf(a.I[q], 0.f);
-        v = a.lp.var_model == 1 ? a.lp.s0sq / (F * F) + Iv * a.lp.inv_gain / F
-                                : a.lp.excess * Iv * a.lp.inv_gain / F;
-        v = fmaxf(v, a.lp.var_floor);
-    }
-    return (a.mask && a.mask[q] == 0) ? 0.f : 1.0f / v;
-}
-
 constexpr int kGnThreads = 256;
 constexpr int kGnKB = 32;          // pixels per shared-memory batch
 constexpr int kPadCol = -1000;     // column code of the zero padding beyond n
@@ -92,15 +78,73 @@ __device__ __forceinline__ double reg_hess(const PrecondArgs &a, int u, int v) {
     return a.reg2 * s;
 }
 
-__global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, int npairs) {
-    __shared__ __align__(16) float sA[kGnKB][kGnT], sB[kGnKB][kGnT];
+// Per-pixel data of one batch: the pixel's offset in R, its weight and the
+// Eq. 18 / Eq. 19 bases.  The global loads (weight inputs) are issued one
+// batch early and the values formed after the FMA loop of the current batch.
+struct GnPixLoads {
+    float var, I, flat, wm;
+    int mask;
+};
+
+__device__ __forceinline__ void gn_pix_load(const PrecondArgs &a, long long k, long long k1, int wx,
+                                            int h, int ld, GnPixLoads &L) {
+    L.var = 0.f;
+    L.I = 0.f;
+    L.flat = 1.f;
+    L.wm = 0.f;
+    L.mask = 1;
+    if (k >= k1) return;
+    const int py = a.y0 + (int)(k / wx), px = a.x0 + (int)(k % wx);
+    if (a.wmap) {
+        L.wm = a.wmap[(size_t)py * a.wmap_ld + px];
+        return;
+    }
+    const size_t q = (size_t)(py + h) * ld + (px + h);
+    if (a.lp.var_model == 0) {
+        if (a.var) L.var = a.var[q];
+    } else {
+        L.I = a.I[q];
+        if (a.flat) L.flat = a.flat[q];
+    }
+    if (a.mask) L.mask = a.mask[q];
+}
+
+// Weight of a target pixel from its loaded values: mask / variance at M = I
+// (or the given per-pixel weight).
+__device__ __forceinline__ float gn_pix_weight(const PrecondArgs &a, const GnPixLoads &L) {
+    if (a.wmap) return L.wm;
+    float v;
+    if (a.lp.var_model == 0) {
+        v = a.var ? L.var : a.lp.var_scalar;
+    } else {
+        const float F = a.flat ? L.flat : 1.f, Iv = fmaxf(L.I, 0.f);
+        v = a.lp.var_model == 1 ? a.lp.s0sq / (F * F) + Iv * a.lp.inv_gain / F
+                                : a.lp.excess * Iv * a.lp.inv_gain / F;
+        v = fmaxf(v, a.lp.var_floor);
+    }
+    return (a.mask && L.mask == 0) ? 0.f : 1.0f / v;
+}
+
+// Sum of w_p phi_p phi_p^T over one 64 x 64 block (U, V) of the upper triangle
+// and one chunk of window pixels; 16 x 16 threads of 4 x 4 entries each.
+// Software-pipelined over batches of kGnKB pixels with one barrier per batch:
+// while the FMA loop runs on batch i, every thread's phi loads of batch i+1
+// and the per-pixel loads of batch i+2 are in flight; the products and their
+// order (and the float64 flushes every a.flush batches) are those of a plain
+// batch-by-batch loop.
+__global__ void __launch_bounds__(kGnThreads, 2) gn_kernel(const PrecondArgs *pas, int npairs) {
+    __shared__ __align__(16) float sA[2][kGnKB][kGnT], sB[2][kGnKB][kGnT];
     __shared__ int offU[kGnT], offV[kGnT];
-    __shared__ long long sBase[kGnKB];
-    __shared__ float sW[kGnKB];
-    __shared__ float sBg[kGnKB][kBgMax];   // background basis eta^i xi^j of each pixel
-    __shared__ float sKb[kGnKB][6];        // basis of a spatially varying kernel (degree <= 2)
+    __shared__ long long sBase[2][kGnKB];
+    __shared__ float sW[2][kGnKB];
+    __shared__ float sBg[2][kGnKB][kBgMax];   // background basis eta^i xi^j of each pixel
+    __shared__ float sKb[2][kGnKB][6];        // basis of a spatially varying kernel (degree <= 2)
     __shared__ unsigned char cU[kGnT], cV[kGnT];   // coefficient kernel of column u, v
+    constexpr int kRows = kGnThreads / kGnT;        // batch rows one pass of the threads covers
+    constexpr int kPer = kGnKB / kRows;             // phi values per thread and operand
+    static_assert(kGnThreads % kGnT == 0 && kGnKB % kRows == 0, "gather layout");
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int ul = tid & (kGnT - 1), kr = tid / kGnT;   // this thread's column and first row
     for (int p = blockIdx.y; p < npairs; p += gridDim.y) {
         const PrecondArgs &a = pas[p];
         const int m = a.m, nk1 = m * m, nk = n_background(a.kdeg) * nk1, n = pc_n(a), h = m / 2,
@@ -140,83 +184,120 @@ __global__ void __launch_bounds__(kGnThreads) gn_kernel(const PrecondArgs *pas, 
             }
         const long long k0 = (long long)chunk * ((npx + nch - 1) / nch);
         const long long k1 = min(npx, k0 + (npx + nch - 1) / nch);
-        int nb = 0;
-        for (long long kb = k0; kb < k1; kb += kGnKB) {
-            __syncthreads();
-            if (tid < kGnKB) {
-                const long long k = kb + tid;
-                if (k < k1) {
-                    const int py = a.y0 + (int)(k / wx), px = a.x0 + (int)(k % wx);
-                    sBase[tid] = (long long)py * ld + px;
-                    sW[tid] = a.wmap ? a.wmap[(size_t)py * a.wmap_ld + px]
-                                     : pc_weight(a, (size_t)(py + h) * ld + (px + h));
-                    // basis of Eq. 18 in the coefficient order (power of xi fastest)
-                    const float eta = fmaf((float)px, a.eta_s, a.eta0);
-                    const float xi = fmaf((float)py, a.xi_s, a.xi0);
-                    int c = 0;
-                    float ep = 1.f;
-                    for (int i = 0; i <= deg; ++i) {
-                        float t = ep;
-                        for (int j = 0; j <= deg - i; ++j) {
-                            sBg[tid][c++] = t;
-                            t *= xi;
-                        }
-                        ep *= eta;
+        const int nbat = k1 > k0 ? (int)((k1 - k0 + kGnKB - 1) / kGnKB) : 0;
+
+        // per-pixel data of batch j into buffer j & 1 (threads < kGnKB)
+        auto pix_store = [&](int j, const GnPixLoads &L) {
+            const int sb = j & 1;
+            const long long k = k0 + (long long)j * kGnKB + tid;
+            if (k < k1) {
+                const int py = a.y0 + (int)(k / wx), px = a.x0 + (int)(k % wx);
+                sBase[sb][tid] = (long long)py * ld + px;
+                sW[sb][tid] = gn_pix_weight(a, L);
+                // basis of Eq. 18 in the coefficient order (power of xi fastest)
+                const float eta = fmaf((float)px, a.eta_s, a.eta0);
+                const float xi = fmaf((float)py, a.xi_s, a.xi0);
+                int c = 0;
+                float ep = 1.f;
+                for (int i = 0; i <= deg; ++i) {
+                    float t = ep;
+                    for (int jj = 0; jj <= deg - i; ++jj) {
+                        sBg[sb][tid][c++] = t;
+                        t *= xi;
                     }
-                    // the same basis for the coefficient kernels (degree kdeg)
-                    c = 0;
-                    ep = 1.f;
-                    for (int i = 0; i <= kdeg; ++i) {
-                        float t = ep;
-                        for (int j = 0; j <= kdeg - i; ++j) {
-                            sKb[tid][c++] = t;
-                            t *= xi;
-                        }
-                        ep *= eta;
-                    }
-                } else {
-                    sBase[tid] = -1;
-                    sW[tid] = 0.f;
+                    ep *= eta;
                 }
+                // the same basis for the coefficient kernels (degree kdeg)
+                c = 0;
+                ep = 1.f;
+                for (int i = 0; i <= kdeg; ++i) {
+                    float t = ep;
+                    for (int jj = 0; jj <= kdeg - i; ++jj) {
+                        sKb[sb][tid][c++] = t;
+                        t *= xi;
+                    }
+                    ep *= eta;
+                }
+            } else {
+                sBase[sb][tid] = -1;
+                sW[sb][tid] = 0.f;
             }
-            __syncthreads();
-            for (int e = tid; e < kGnKB * kGnT; e += kGnThreads) {
-                const int kk = e / kGnT, ul = e % kGnT;
-                const long long base = sBase[kk];
-                float va = 0.f, vb = 0.f;
+        };
+        // phi_u, phi_v of this thread's column for the rows of batch buffer sb
+        auto gather = [&](int sb, float (&va)[kPer], float (&vb)[kPer]) {
+            const int ou = offU[ul], ov = offV[ul];
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int kk = kr + r * kRows;
+                const long long base = sBase[sb][kk];
+                float x = 0.f, y = 0.f;
                 if (base >= 0) {
-                    const int ou = offU[ul], ov = offV[ul];
-                    va = ou >= 0 ? a.R[base + ou] : (ou > kPadCol ? sBg[kk][-1 - ou] : 0.f);
-                    vb = ov >= 0 ? a.R[base + ov] : (ov > kPadCol ? sBg[kk][-1 - ov] : 0.f);
+                    x = ou >= 0 ? a.R[base + ou] : (ou > kPadCol ? sBg[sb][kk][-1 - ou] : 0.f);
+                    y = ov >= 0 ? a.R[base + ov] : (ov > kPadCol ? sBg[sb][kk][-1 - ov] : 0.f);
                     if (kdeg > 0) {   // column of coefficient kernel c: eta^p xi^q R
-                        if (ou >= 0) va *= sKb[kk][cU[ul]];
-                        if (ov >= 0) vb *= sKb[kk][cV[ul]];
+                        if (ou >= 0) x *= sKb[sb][kk][cU[ul]];
+                        if (ov >= 0) y *= sKb[sb][kk][cV[ul]];
                     }
                 }
-                sA[kk][ul] = sW[kk] * va;
-                sB[kk][ul] = vb;
+                va[r] = x;
+                vb[r] = y;
             }
-            __syncthreads();
+        };
+        auto put = [&](int sb, const float (&va)[kPer], const float (&vb)[kPer]) {
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int kk = kr + r * kRows;
+                sA[sb][kk][ul] = sW[sb][kk] * va[r];
+                sB[sb][kk][ul] = vb[r];
+            }
+        };
+
+        // prologue: per-pixel data of batches 0 and 1, phi of batch 0
+        GnPixLoads L;
+        if (tid < kGnKB) {
+            gn_pix_load(a, k0 + tid, k1, wx, h, ld, L);
+            pix_store(0, L);
+            gn_pix_load(a, k0 + kGnKB + tid, k1, wx, h, ld, L);
+            pix_store(1, L);
+        }
+        __syncthreads();
+        float va[kPer], vb[kPer];
+        if (nbat > 0) {
+            gather(0, va, vb);
+            put(0, va, vb);
+        }
+        __syncthreads();
+        int nb = 0;
+        for (int i = 0; i < nbat; ++i) {
+            const int cur = i & 1, nxt = cur ^ 1;
+            const bool more = i + 1 < nbat;
+            if (more) gather(nxt, va, vb);   // phi of batch i + 1 (in flight)
+            if (tid < kGnKB) gn_pix_load(a, k0 + (long long)(i + 2) * kGnKB + tid, k1, wx, h, ld, L);
 #pragma unroll 8
             for (int kk = 0; kk < kGnKB; ++kk) {
-                const float4 av = *reinterpret_cast<const float4 *>(&sA[kk][ty * 4]);
-                const float4 bv = *reinterpret_cast<const float4 *>(&sB[kk][tx * 4]);
+                const float4 av = *reinterpret_cast<const float4 *>(&sA[cur][kk][ty * 4]);
+                const float4 bv = *reinterpret_cast<const float4 *>(&sB[cur][kk][tx * 4]);
                 const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+                    for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(ar[ii], br[jj], acc[ii][jj]);
             }
             if (++nb == a.flush) {
                 nb = 0;
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        acc64[i][j] += acc[i][j];
-                        acc[i][j] = 0.f;
+                    for (int jj = 0; jj < 4; ++jj) {
+                        acc64[ii][jj] += acc[ii][jj];
+                        acc[ii][jj] = 0.f;
                     }
             }
+            if (more) put(nxt, va, vb);
+            // per-pixel data of batch i + 2 replaces that of batch i (read by the
+            // phi of batch i, before the last barrier)
+            if (tid < kGnKB) pix_store(i + 2, L);
+            __syncthreads();
         }
         const double inv = a.scale;
         const int np = pc_np(n);
