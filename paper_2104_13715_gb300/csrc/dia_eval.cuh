@@ -817,10 +817,11 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
             }
         }
         // the first and last QF-1 R rows feed only some output rows (with
-        // MK < QF - 1 there is no interior and every row is done here once)
+        // MK < QF - 1 there is no interior and every row is done here once);
+        // unrolled, so that each row's kernel rows are compile-time (no branches)
         constexpr bool kSplit = MK >= QF - 1;
         constexpr int kEdges = kSplit ? 2 * (QF - 1) : (QF + MK - 1);
-#pragma unroll 1
+#pragma unroll
         for (int e = 0; e < kEdges; ++e) {
             const int r = kSplit ? ((e < QF - 1) ? e : (MK + e - (QF - 1))) : e;
             float win[RWIN];
