@@ -504,6 +504,8 @@ def run_ours(args, rank, world, local_rank):
         hV = torch.from_numpy(d["var"]).pin_memory() if d.get("var") is not None else None
         wsh = nat.workspace(H, W, m, clip=clip, host=True, device=dev)
         out = nat.fit(hR, hI, m, spec, opts, mask=hM, var=hV, ws=wsh, stream=stream)
+        out = None
+        out = nat.fit(hR, hI, m, spec, opts, mask=hM, var=hV, ws=wsh, stream=stream)
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
@@ -512,6 +514,10 @@ def run_ours(args, rank, world, local_rank):
         n2 = max(1, min(args.steps, 3))
         g0.record(stream)
         for _ in range(n2):
+            # the previous result is released first, so that its pinned output
+            # buffers return to PyTorch's host cache and are reused, as a caller
+            # keeping one set of output buffers would
+            out = None
             out = nat.fit(hR, hI, m, spec, opts, mask=hM, var=hV, ws=wsh, stream=stream)
             ev2 += out["info"]["evals"]
         g1.record(stream)
