@@ -942,7 +942,6 @@ dia_status dia_fit(const dia_pair *pair, const dia_loss_spec *loss, const dia_op
     // preconditioner of L-BFGS: the inverse of the Gauss-Newton Hessian over
     // a centred window of valid target pixels (dia_precond.cu)
     {
-        const int Hv = H - 2 * h, Wv = W - 2 * h;
         if (opts.precond) {
             NvtxRange range_pc("dia_fit preconditioner");
             PrecondArgs pa;

@@ -969,8 +969,21 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
         // fixed order
         for (int i = tid; i < MK * MK; i += S::NT) {
             const int a = i / MK, b = i - a * MK;
-            double t = 0.0;
-            if (SPLIT != 2 && a < MK - RM) {
+            // row qb of every warp's accumulators, summed in warp order
+            auto all_warps = [&](int qb) {
+                double t = 0.0;
+                float t32 = 0.f;
+                for (int w = 0; w < NW; ++w) {
+                    const float *kw = kahan + w * 2 * NK;
+                    t += (double)kw[qb * MK + b] - (double)kw[NK + qb * MK + b];
+                    t32 += kw[qb * MK + b];
+                }
+                return args.acc32 ? (double)t32 : t;
+            };
+            double t;
+            if constexpr (SPLIT == 2) {
+                t = all_warps(a);
+            } else if (a < MK - RM) {
                 int w = SPLIT ? a / KF : 0;
                 if (!SPLIT) {
                     while (w + 1 < NW && ((w + 1) * MK) / NW <= a) ++w;
@@ -979,14 +992,7 @@ __device__ __forceinline__ void process_tiles(const EvalArgs &args, unsigned cha
                 const float *kw = kahan + w * 2 * NK;
                 t = (double)kw[qb * MK + b] - (double)kw[NK + qb * MK + b];
             } else {
-                const int qb = SPLIT == 2 ? a : KF + (a - (MK - RM));
-                float t32 = 0.f;
-                for (int w = 0; w < NW; ++w) {
-                    const float *kw = kahan + w * 2 * NK;
-                    t += (double)kw[qb * MK + b] - (double)kw[NK + qb * MK + b];
-                    t32 += kw[qb * MK + b];
-                }
-                if (args.acc32) t = (double)t32;
+                t = all_warps(KF + (a - (MK - RM)));
             }
             out[1 + i] = t;
         }
