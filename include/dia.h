@@ -450,6 +450,23 @@ size_t dia_batch_workspace_size(const dia_pair *pairs, int32_t npairs, const dia
  * dia_fit_batch.  Errors: DIA_ERR_ARG (group or variant out of range). */
 dia_status dia_select_batch_variant(int32_t group, int32_t variant);
 int32_t dia_get_batch_variant(int32_t group);
+
+/* Kernel-level timing of the batched evaluation (no counterpart in the
+ * paper: a measurement hook).  With reps > 0, every later dia_fit_batch call
+ * times, after its initialisation and before its first iteration, each
+ * kernel-side group's evaluation kernel alone over all of that group's work
+ * items at the starting theta.  It does one untimed launch, then reps
+ * launches between CUDA events on the call's stream.  These launches write
+ * only partial sums that the first iteration rewrites, so the fit's results
+ * are unchanged; they add (reps + 1) launches per group.  reps = 0 (the
+ * default) turns it off.  Process-wide.  Errors: DIA_ERR_ARG (reps outside
+ * [0, 1000]).
+ * dia_get_batch_eval_timing: the last timed call's mean milliseconds per
+ * launch and algorithmic flop (4 m^2 per valid pixel, masks not subtracted)
+ * for groups 0..3 (kernel sides 1-7, 9-15, 17-23, 25-31), into HOST arrays of
+ * 4; 0 for a group without pairs.  Errors: DIA_ERR_ARG (NULL output). */
+dia_status dia_set_batch_eval_timing(int32_t reps);
+dia_status dia_get_batch_eval_timing(float *ms_out, double *flop_out);
 int32_t dia_batch_chunk_tiles(int32_t m, int32_t variant);
 dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs, const dia_loss_spec *loss,
                          const dia_opts *opts, double *theta_out, float *const *diff_out,

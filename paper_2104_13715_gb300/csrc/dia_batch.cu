@@ -31,6 +31,13 @@ namespace {
 thread_local int g_batch_cuda = 0;
 // work-item size variant of each kernel-side group (dia_select_batch_variant)
 std::atomic<int> g_batch_variant[4] = {{0}, {0}, {0}, {0}};
+// kernel-level timing of the batched evaluation (dia_set_batch_eval_timing):
+// repetitions per group (0: off), and the last timed call's per-group mean
+// milliseconds and algorithmic flop
+std::atomic<int> g_batch_time_reps{0};
+std::mutex g_bt_mu;
+float g_bt_ms[4] = {0.f, 0.f, 0.f, 0.f};
+double g_bt_flop[4] = {0.0, 0.0, 0.0, 0.0};
 
 #define DB_CK(expr)                    \
     do {                               \
@@ -197,6 +204,22 @@ extern "C" dia_status dia_select_batch_variant(int32_t group, int32_t variant) {
 
 extern "C" int32_t dia_get_batch_variant(int32_t group) {
     return (group < 0 || group > 3) ? -1 : g_batch_variant[group].load();
+}
+
+extern "C" dia_status dia_set_batch_eval_timing(int32_t reps) {
+    if (reps < 0 || reps > 1000) return DIA_ERR_ARG;
+    dia::g_batch_time_reps.store(reps);
+    return DIA_OK;
+}
+
+extern "C" dia_status dia_get_batch_eval_timing(float *ms_out, double *flop_out) {
+    if (!ms_out || !flop_out) return DIA_ERR_ARG;
+    std::lock_guard<std::mutex> lk(dia::g_bt_mu);
+    for (int g = 0; g < 4; ++g) {
+        ms_out[g] = dia::g_bt_ms[g];
+        flop_out[g] = dia::g_bt_flop[g];
+    }
+    return DIA_OK;
 }
 
 extern "C" int32_t dia_batch_chunk_tiles(int32_t m, int32_t variant) {
@@ -448,6 +471,57 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     // per-pair Gauss-Newton preconditioners (after init, which clears the state)
     if (opts.precond) DB_CK(launch_precond(d_pas, pas.data(), npairs, s));
 
+    // optional kernel-level timing: each group's evaluation kernel alone over
+    // all its work items at the starting theta, between CUDA events on the
+    // stream (one untimed launch first).  The launches write only the items'
+    // partial sums, which the first iteration rewrites, and the queue
+    // counters are cleared again, so the fit is unchanged.
+    long long timing_launches = 0;
+    if (const int treps = g_batch_time_reps.load(); treps > 0) {
+        float ms_g[4] = {0.f, 0.f, 0.f, 0.f};
+        double fl_g[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < npairs; ++i) {
+            const int mk = pairs[i].m, h = mk / 2;
+            fl_g[batch_group(mk)] +=
+                4.0 * mk * mk * (double)(pairs[i].H - 2 * h) * (double)(pairs[i].W - 2 * h);
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        auto launch_all = [&](int g) -> cudaError_t {
+            int *counter = hdr + 4 + g;
+            const BatchItem *its = g_items[g];
+            const int *nit = g_nall[g];
+            void *params[] = {(void *)&d_eas, (void *)&d_mks, (void *)&its, (void *)&nit,
+                              (void *)&counter, (void *)&d_parts};
+            return cudaLaunchKernel(batch_kernel_ptr(g, kModeGrad, bg), dim3(grid[g]),
+                                    dim3(kBW * 32), params, gsmem[g], s);
+        };
+        for (int g = 0; g < 4 && e == cudaSuccess; ++g) {
+            if (n_it[g] == 0) continue;
+            for (int r = -1; r < treps && e == cudaSuccess; ++r) {
+                e = cudaMemsetAsync(hdr + 4 + g, 0, sizeof(int), s);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = launch_all(g);
+                timing_launches += 1;
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (r >= 0) ms_g[g] += ms / (float)treps;
+            }
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(hdr + 4, 0, 4 * sizeof(int), s);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        DB_CK(e);
+        std::lock_guard<std::mutex> lk(g_bt_mu);
+        for (int g = 0; g < 4; ++g) {
+            g_bt_ms[g] = ms_g[g];
+            g_bt_flop[g] = n_it[g] > 0 ? fl_g[g] : 0.0;
+        }
+    }
+
     // the iteration graph (cached per workspace / batch shape / settings); the
     // group kernels are parallel branches, joined before the optimiser step
     std::string key;
@@ -523,7 +597,8 @@ extern "C" dia_status dia_fit_batch(const dia_pair *pairs, int32_t npairs,
     const auto t0 = std::chrono::steady_clock::now();
     int status = DIA_OK;
     int done_host = 0;
-    long long launches = 1 + (opts.precond ? precond_launches(max_n) : 0);   // init (+ preconditioner)
+    // init (+ preconditioner, + timed evaluations)
+    long long launches = 1 + (opts.precond ? precond_launches(max_n) : 0) + timing_launches;
     for (;;) {
         DB_CK(cudaGraphLaunch(gx, s));
         launches += (long long)(1 + n_groups + kStepLaunchesBatch) * opts.graph_iters;

@@ -106,6 +106,9 @@ _SIGS = {
     "dia_set_small_kernel": (ctypes.c_int32, [ctypes.c_int32]),
     "dia_select_batch_variant": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "dia_get_batch_variant": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_set_batch_eval_timing": (ctypes.c_int32, [ctypes.c_int32]),
+    "dia_get_batch_eval_timing": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_float),
+                                                   ctypes.POINTER(ctypes.c_double)]),
     "dia_batch_chunk_tiles": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "dia_set_tc_wait_cycles": (ctypes.c_int32, [ctypes.c_int64]),
     "dia_tc_workspace_size": (ctypes.c_size_t, [ctypes.c_int32] * 4),
@@ -202,6 +205,21 @@ def set_small_kernel(enable: bool) -> None:
     """dia_set_small_kernel: the streaming small-kernel evaluation (m <= 5)
     on (default) or off (the tiled kernel for every m)."""
     _check(lib.dia_set_small_kernel(1 if enable else 0), "dia_set_small_kernel")
+
+
+def set_batch_eval_timing(reps: int) -> None:
+    """dia_set_batch_eval_timing: kernel-level timing of each group's batched
+    evaluation kernel inside later fit_batch calls (0: off)."""
+    _check(lib.dia_set_batch_eval_timing(int(reps)), "dia_set_batch_eval_timing")
+
+
+def batch_eval_timing() -> dict:
+    """dia_get_batch_eval_timing: per kernel-side group (0..3) the mean ms per
+    launch and the algorithmic flop of the last timed fit_batch call."""
+    ms = (ctypes.c_float * 4)()
+    fl = (ctypes.c_double * 4)()
+    _check(lib.dia_get_batch_eval_timing(ms, fl), "dia_get_batch_eval_timing")
+    return {"ms": [float(x) for x in ms], "flop": [float(x) for x in fl]}
 
 
 def select_batch_variant(group: int, variant: int) -> None:

@@ -142,3 +142,37 @@ def test_batch_autotune_selects_and_caches(tmp_path):
     finally:
         for g in range(4):
             nat.select_batch_variant(g, 0)
+
+
+def test_batch_eval_timing_leaves_the_fit_unchanged(nat):
+    """dia_set_batch_eval_timing: the timed launches of each group's evaluation
+    kernel (before the first iteration) change no result bit; every group with
+    pairs reports a positive time and exactly sum 4 m^2 (valid px) flop, the
+    others zero; reps outside [0, 1000] are rejected."""
+    ds = _pairs(10, seed=4, side=(64, 160), m_range=(5, 27))
+    items = [_dev(d) for d in ds]
+    spec = nat.loss_spec(rho="gauss", noise="fixed", var=1.0)
+    opts = nat.default_opts(timeout_s=120.0)
+    ref = nat.fit_batch(items, spec, opts)
+    nat.set_batch_eval_timing(3)
+    try:
+        out = nat.fit_batch(items, spec, opts)
+        bt = nat.batch_eval_timing()
+    finally:
+        nat.set_batch_eval_timing(0)
+    for k in range(len(ds)):
+        assert torch.equal(out["thetas"][k], ref["thetas"][k])
+        assert out["infos"][k]["evals"] == ref["infos"][k]["evals"]
+        assert out["infos"][k]["kernel_launches"] > ref["infos"][k]["kernel_launches"]
+    group = lambda m: 0 if m <= 7 else 1 if m <= 15 else 2 if m <= 23 else 3
+    flop = [0.0] * 4
+    for d in ds:
+        m, h = d["m"], d["m"] // 2
+        flop[group(m)] += 4.0 * m * m * (d["R"].shape[0] - 2 * h) * (d["R"].shape[1] - 2 * h)
+    for g in range(4):
+        assert bt["flop"][g] == pytest.approx(flop[g], rel=1e-12)
+        assert (bt["ms"][g] > 0.0) == (flop[g] > 0.0)
+    with pytest.raises(nat.DiaError):
+        nat.set_batch_eval_timing(-1)
+    with pytest.raises(nat.DiaError):
+        nat.set_batch_eval_timing(1001)
