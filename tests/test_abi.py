@@ -216,3 +216,18 @@ def test_auto_eval_form_takes_the_tensor_cores_from_m_19(native):
         assert native.lib.dia_workspace_size(H, W, W, 31, 0, 0) > base[31]
     finally:
         native.set_eval_form(native.EVAL_FP32)
+
+
+def test_batch_eval_timing_arguments(native):
+    """dia_set_batch_eval_timing takes 0..1000 repetitions and
+    dia_get_batch_eval_timing needs both output arrays (host-only calls)."""
+    lib = native.lib
+    assert lib.dia_set_batch_eval_timing(-1) == native.DIA_ERR_ARG
+    assert lib.dia_set_batch_eval_timing(1001) == native.DIA_ERR_ARG
+    assert lib.dia_set_batch_eval_timing(3) == native.DIA_OK
+    assert lib.dia_set_batch_eval_timing(0) == native.DIA_OK
+    ms = (ctypes.c_float * 4)()
+    fl = (ctypes.c_double * 4)()
+    assert lib.dia_get_batch_eval_timing(None, fl) == native.DIA_ERR_ARG
+    assert lib.dia_get_batch_eval_timing(ms, None) == native.DIA_ERR_ARG
+    assert lib.dia_get_batch_eval_timing(ms, fl) == native.DIA_OK
