@@ -11,11 +11,12 @@ constexpr int kBQF = 4;            // output rows per warp in the forward pass
 constexpr int kBTH = kBW * kBQF;   // tile rows
 constexpr int kMaxChunkTiles = 32;  // longest run of tiles in one work item
 
-// per kernel side: prefetch flag and backward split of the batched kernel
-#define DIA_BATCH_SIDES(X)                                                                    \
-    X(1, 0, 0) X(3, 0, 0) X(5, 0, 0) X(7, 0, 0) X(9, 0, 1) X(11, 1, 1) X(13, 1, 1) X(15, 0, 0) \
-        X(17, 0, 1) X(19, 1, 1) X(21, 0, 0) X(23, 0, 0) X(25, 0, 1) X(27, 0, 0) X(29, 0, 0)   \
-            X(31, 0, 0)
+// per kernel side: prefetch flag, backward split and packed-float2 forward
+// (F2: bitwise the scalar forward) of the batched kernel
+#define DIA_BATCH_SIDES(X)                                                                   \
+    X(1, 0, 0, 0) X(3, 0, 0, 0) X(5, 0, 0, 0) X(7, 0, 0, 1) X(9, 0, 1, 1) X(11, 1, 1, 1)     \
+        X(13, 1, 1, 1) X(15, 0, 0, 1) X(17, 0, 1, 1) X(19, 1, 1, 1) X(21, 0, 0, 1)           \
+            X(23, 0, 0, 1) X(25, 0, 1, 1) X(27, 0, 0, 1) X(29, 0, 0, 1) X(31, 0, 0, 1)
 
 
 constexpr int np_of(int mk) { return red_size(mk * mk); }
@@ -42,9 +43,9 @@ __host__ __device__ constexpr int batch_group(int mk) { return mk <= 7 ? 0 : mk 
 // shared memory of the kernel of group g (its largest side)
 constexpr int batch_group_smem(int g) {
     int mx = 0;
-#define DIA_SMEM_G(MKV, PFV, SPV)                                                                 \
-    if (batch_group(MKV) == g && EvalShape<MKV, kBW, kBQF, SPV>::SMEM > mx)                     \
-        mx = EvalShape<MKV, kBW, kBQF, SPV>::SMEM;
+#define DIA_SMEM_G(MKV, PFV, SPV, F2V)                                                            \
+    if (batch_group(MKV) == g && EvalShape<MKV, kBW, kBQF, SPV, F2V>::SMEM > mx)                \
+        mx = EvalShape<MKV, kBW, kBQF, SPV, F2V>::SMEM;
     DIA_BATCH_SIDES(DIA_SMEM_G)
 #undef DIA_SMEM_G
     return mx;
@@ -80,10 +81,10 @@ __global__ void __launch_bounds__(kBW * 32, GROUP <= 1 ? 2 : 1)
         if (!skip) {
             double *out = MODE == kModeGrad ? partials + item.part_off : nullptr;
             switch (mks[item.pair]) {
-#define DIA_CASE(MKV, PFV, SPV)                                                              \
+#define DIA_CASE(MKV, PFV, SPV, F2V)                                                         \
     case MKV:                                                                                \
         if constexpr (batch_group(MKV) == GROUP)                                             \
-            process_tiles<MKV, kBW, kBQF, PFV, SPV, MODE, 0, BG>(s_ea, smem, item.t0, item.t1, 1, out); \
+            process_tiles<MKV, kBW, kBQF, PFV, SPV, MODE, F2V, BG>(s_ea, smem, item.t0, item.t1, 1, out); \
         break;
                 DIA_BATCH_SIDES(DIA_CASE)
 #undef DIA_CASE
