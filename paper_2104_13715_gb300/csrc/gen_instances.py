@@ -33,10 +33,12 @@ VARIANTS = {
 GROUPS = [[1, 3, 5, 7], [9, 11], [13, 15], [17], [19], [21], [23], [25], [27], [29], [31]]
 
 
-def main():
-    for f in os.listdir(HERE):
+def main(out=HERE):
+    """Write the instantiation units and dia_dispatch.cu into `out` (by
+    default beside this script, replacing the previous units)."""
+    for f in os.listdir(out):
         if f.startswith("dia_eval_m") and f.endswith(".cu"):
-            os.remove(os.path.join(HERE, f))
+            os.remove(os.path.join(out, f))
     for grp in GROUPS:
         lines = [f"// Fused evaluation kernels for kernel sides {grp} (generated by gen_instances.py)",
                  '#include "dia_eval_inst.cuh"', ""]
@@ -45,7 +47,7 @@ def main():
                 nw, qf, mb, sp = t[:4]
                 f2 = t[4] if len(t) > 4 else 0
                 lines.append(f"DIA_EVAL_INST({mk}, {v}, {nw}, {qf}, {mb}, {sp}, {f2})")
-        with open(os.path.join(HERE, f"dia_eval_m{grp[0]:02d}.cu"), "w") as fh:
+        with open(os.path.join(out, f"dia_eval_m{grp[0]:02d}.cu"), "w") as fh:
             fh.write("\n".join(lines) + "\n")
     decl, cases = [], []
     for mk, vs in VARIANTS.items():
@@ -97,7 +99,7 @@ bool kernel_info(int mk, KernelInfo *o) {{ return kernel_info_variant(mk, select
 
 }}  // namespace dia
 """
-    with open(os.path.join(HERE, "dia_dispatch.cu"), "w") as fh:
+    with open(os.path.join(out, "dia_dispatch.cu"), "w") as fh:
         fh.write(src)
 
 
